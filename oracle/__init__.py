@@ -1,0 +1,22 @@
+"""CPU oracle for block-tridiagonal selected inversion (test infrastructure).
+
+This package is test infrastructure only: the test-suite, the smoke check and the
+benchmark's CPU-baseline leg may import it; the library path never does, and it shares no
+code with the CUDA kernels.  Everything is plain numpy / scipy in float64 / complex128.
+
+What it computes (the plain definitions the recursive Green's function method reaches):
+  * Sec. 2, Eq. 1 and Table 2: for each energy the quadratic system
+        (M - B^R) X^<> (M - B^R)^H = B^<>,   X^R = (M - B^R)^{-1},
+    solved by *dense* inversion of the full N_B*N_BS matrix and one dense triple product.
+  * Sec. 3.1 (retarded OBC, Eq. 4): the lead surface function x = (m - n x n')^{-1}, by
+    Sancho-Rubio decimation (the paper cites Sancho et al. 1985 and does not print it), and
+    independently by the direct eigen-decomposition route (Eq. 6, polynomial eigenproblem).
+  * Sec. 3.1 (lesser/greater OBC): fluctuation-dissipation from the retarded boundary block.
+  * Sec. 4.2: the symmetrisation X_ij <- (X_ij - X_ji^*)/2.
+  * Table 2, right column: the W system M = I, B^R = V P^R, B^<> = V P^<> V^H, W^R = X^R V.
+
+Pins (tests/test_oracle_pins.py) tie every function to something other than itself: closed
+forms of the 1D chain, integer transmission, the eigen-route surface function, algebraic
+identities, brute force on tiny cases.
+"""
+from .negf import *  # noqa: F401,F403

@@ -1,0 +1,353 @@
+"""Dense CPU oracle (test infrastructure only; see the package docstring).
+
+Notation follows the paper: M(E) = E S - H (Table 2), B^R_scatt = Sigma^R, B^<> = Sigma^<>,
+M~ = M - B^R_scatt - B^R_OBC (Table 2), x^R the lead surface function of Eq. 4 with blocks
+m, n, n' of M - B^R_scatt.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+
+__all__ = [
+    "fermi", "bt_dense", "sancho_rubio", "surface_gf_eig", "lead_blocks", "obc_self_energies",
+    "assemble_g", "selected_blocks", "symmetrize_lesser", "solve_g", "assemble_w", "solve_w",
+    "transmission", "bond_currents", "block_rows_banded", "solve_g_sampled",
+]
+
+
+def fermi(E, mu, kT):
+    """Fermi-Dirac occupation 1 / (1 + exp((E - mu)/kT)), evaluated without overflow."""
+    x = (np.asarray(E, dtype=np.float64) - mu) / kT
+    ex = np.exp(-np.abs(x))
+    return np.where(x > 0, ex / (1.0 + ex), 1.0 / (1.0 + ex))
+
+
+def bt_dense(diag, upper, lower=None, lower_sign=1.0):
+    """Dense n x n matrix from BT blocks.  lower=None means block (i+1,i) = lower_sign * upper[i]^H
+    (lower_sign = +1 Hermitian pattern, -1 anti-Hermitian pattern)."""
+    nb, bs = diag.shape[0], diag.shape[1]
+    A = np.zeros((nb * bs, nb * bs), dtype=np.complex128)
+    for i in range(nb):
+        A[i * bs:(i + 1) * bs, i * bs:(i + 1) * bs] = diag[i]
+    for i in range(nb - 1):
+        A[i * bs:(i + 1) * bs, (i + 1) * bs:(i + 2) * bs] = upper[i]
+        lo = lower[i] if lower is not None else lower_sign * np.conj(upper[i].T)
+        A[(i + 1) * bs:(i + 2) * bs, i * bs:(i + 1) * bs] = lo
+    return A
+
+
+def sancho_rubio(m, n, n_prime, tol=1e-14, maxit=100):
+    """Surface function x solving x = (m - n x n')^{-1} (Eq. 4) by Sancho-Rubio decimation.
+
+    Decimation of every second cell of the semi-infinite chain with diagonal blocks m,
+    coupling n (cell j -> j+1, away from the device) and n' (j+1 -> j).  With g = e^{-1}:
+        e_s <- e_s - a g b,   e <- e - a g b - b g a,   a <- -a g a,   b <- -b g b
+    starting from a = n, b = n', e = e_s = m; stop when max|a|, max|b| <= tol * max|n|.
+    Returns (x = e_s^{-1}, iterations, converged).
+    """
+    a = np.array(n, dtype=np.complex128)
+    b = np.array(n_prime, dtype=np.complex128)
+    e = np.array(m, dtype=np.complex128)
+    es = e.copy()
+    ref = max(np.abs(a).max(), np.abs(b).max())
+    if ref == 0.0:
+        return np.linalg.inv(es), 0, True
+    it = 0
+    converged = False
+    while it < maxit:
+        it += 1
+        g = np.linalg.inv(e)
+        agb = a @ g @ b
+        bga = b @ g @ a
+        es = es - agb
+        e = e - agb - bga
+        a = -(a @ g @ a)
+        b = -(b @ g @ b)
+        if max(np.abs(a).max(), np.abs(b).max()) <= tol * ref:
+            converged = True
+            break
+    return np.linalg.inv(es), it, converged
+
+
+def surface_gf_eig(m, n, n_prime):
+    """Surface function of Eq. 4 by the direct route (Eq. 6 with N_U = 1): solve the
+    linearised quadratic eigenproblem (n' lam^{-1} + m + n lam) phi = 0, keep the bs modes
+    with |lam| < 1 (decaying away from the device), T = Phi Lam Phi^{-1}, x = (m + n T)^{-1}."""
+    bs = m.shape[0]
+    I = np.eye(bs)
+    Z = np.zeros((bs, bs))
+    A = np.block([[Z, I], [-n_prime, -m]])
+    B = np.block([[I, Z], [Z, n]])
+    lam, vec = sla.eig(A, B)
+    order = np.argsort(np.abs(lam))
+    keep = order[:bs]
+    if not np.all(np.abs(lam[keep]) < 1.0):
+        raise ValueError("fewer than bs decaying modes")
+    Phi = vec[:bs, keep]
+    T = Phi @ np.diag(lam[keep]) @ np.linalg.inv(Phi)
+    return np.linalg.inv(m + n @ T)
+
+
+def _M_blocks(sysg, e):
+    """Blocks of M - B^R_scatt at energy index e: (diag [N,b,b], upper, lower)."""
+    z = sysg.energies[e] + 1j * sysg.eta
+    nb, bs = sysg.nb, sysg.bs
+    I = np.eye(bs)
+    diag = z * I[None] - sysg.H_diag
+    upper = -sysg.H_upper
+    lower = -np.conj(np.swapaxes(sysg.H_upper, 1, 2))
+    if sysg.sigR_diag is not None:
+        diag = diag - np.stack([np.diag(sysg.sigR_diag[e, i]) for i in range(nb)])
+    return diag, upper, lower
+
+
+def lead_blocks(sysg, e):
+    """(m, n, n') of the left and right leads: the edge cells of M - B^R_scatt repeated
+    periodically.  Left lead: m = M_11, n = M_21, n' = M_12.  Right: m = M_NN,
+    n = M_{N-1,N}, n' = M_{N,N-1}."""
+    d, u, l = _M_blocks(sysg, e)
+    left = (d[0], l[0], u[0])
+    right = (d[-1], u[-1], l[-1])
+    return left, right
+
+
+def obc_self_energies(sysg, e, tol=1e-14, maxit=100):
+    """Boundary blocks B_OBC at energy index e.  Retarded: n x n' with x from Eq. 4 (Sancho-
+    Rubio).  Lesser/greater by fluctuation-dissipation:
+        B^<_c = -f_c (B^R_c - B^R_c^H),  B^>_c = (1 - f_c)(B^R_c - B^R_c^H).
+    Returns dict with keys R_L, R_R, L_L, L_R, G_L, G_R, it_L, it_R, ok."""
+    if sysg.nb < 2:
+        raise ValueError("contacts from the edge blocks need at least two blocks")
+    (mL, nL, npL), (mR, nR, npR) = lead_blocks(sysg, e)
+    xL, itL, okL = sancho_rubio(mL, nL, npL, tol, maxit)
+    xR, itR, okR = sancho_rubio(mR, nR, npR, tol, maxit)
+    SL = nL @ xL @ npL
+    SR = nR @ xR @ npR
+    E = sysg.energies[e]
+    fL = float(fermi(E, sysg.mu_left, sysg.kT))
+    fR = float(fermi(E, sysg.mu_right, sysg.kT))
+    gL = SL - SL.conj().T
+    gR = SR - SR.conj().T
+    return dict(R_L=SL, R_R=SR, L_L=-fL * gL, L_R=-fR * gR, G_L=(1 - fL) * gL, G_R=(1 - fR) * gR,
+                it_L=itL, it_R=itR, ok=okL and okR)
+
+
+def assemble_g(sysg, e, tol=1e-14, maxit=100):
+    """Dense M~ = E S - H - Sigma^R_scatt - Sigma^R_OBC and B^<> = Sigma^<>_scatt + Sigma^<>_OBC
+    (Table 2; the element-wise G assembly of Sec. 3.2.1)."""
+    d, u, l = _M_blocks(sysg, e)
+    nb, bs = sysg.nb, sysg.bs
+    M = bt_dense(d, u, l)
+    n = nb * bs
+    BL = np.zeros((n, n), dtype=np.complex128)
+    BG = np.zeros((n, n), dtype=np.complex128)
+    if sysg.sigL_diag is not None:
+        BL += np.diag(sysg.sigL_diag[e].reshape(-1))
+    if sysg.sigG_diag is not None:
+        BG += np.diag(sysg.sigG_diag[e].reshape(-1))
+    info = {}
+    if sysg.obc:
+        o = obc_self_energies(sysg, e, tol, maxit)
+        M[:bs, :bs] -= o["R_L"]
+        M[-bs:, -bs:] -= o["R_R"]
+        BL[:bs, :bs] += o["L_L"]
+        BL[-bs:, -bs:] += o["L_R"]
+        BG[:bs, :bs] += o["G_L"]
+        BG[-bs:, -bs:] += o["G_R"]
+        info = o
+    return M, BL, BG, info
+
+
+def selected_blocks(X, nb, bs):
+    """Diagonal, upper (i,i+1) and lower (i+1,i) blocks of a dense matrix."""
+    diag = np.stack([X[i * bs:(i + 1) * bs, i * bs:(i + 1) * bs] for i in range(nb)])
+    if nb > 1:
+        upper = np.stack([X[i * bs:(i + 1) * bs, (i + 1) * bs:(i + 2) * bs] for i in range(nb - 1)])
+        lower = np.stack([X[(i + 1) * bs:(i + 2) * bs, i * bs:(i + 1) * bs] for i in range(nb - 1)])
+    else:
+        upper = np.zeros((0, bs, bs), dtype=X.dtype)
+        lower = np.zeros((0, bs, bs), dtype=X.dtype)
+    return diag, upper, lower
+
+
+def symmetrize_lesser(X):
+    """Sec. 4.2: X_ij <- (X_ij - X_ji^*)/2 on the whole matrix."""
+    return 0.5 * (X - X.conj().T)
+
+
+def solve_g(sysg, e, symmetrize=True, tol=1e-14, maxit=100):
+    """Selected blocks of X^R = M~^{-1} and X^<> = X^R B^<> X^R^H at energy index e, by dense
+    inversion (Eq. 1).  Returns dict: R_diag, R_upper, R_lower, L_diag, L_upper, G_diag,
+    G_upper (lesser/greater lower blocks are -upper^H), plus 'info' from the OBC."""
+    M, BL, BG, info = assemble_g(sysg, e, tol, maxit)
+    XR = np.linalg.inv(M)
+    XL = XR @ BL @ XR.conj().T
+    XG = XR @ BG @ XR.conj().T
+    if symmetrize:
+        XL = symmetrize_lesser(XL)
+        XG = symmetrize_lesser(XG)
+    nb, bs = sysg.nb, sysg.bs
+    Rd, Ru, Rl = selected_blocks(XR, nb, bs)
+    Ld, Lu, _ = selected_blocks(XL, nb, bs)
+    Gd, Gu, _ = selected_blocks(XG, nb, bs)
+    return dict(R_diag=Rd, R_upper=Ru, R_lower=Rl, L_diag=Ld, L_upper=Lu, G_diag=Gd, G_upper=Gu,
+                info=info, XR=XR, XL=XL, XG=XG, M=M, BL=BL, BG=BG)
+
+
+# ----------------------------------------------------------------------------------------------
+# W system (Table 2, right column)
+# ----------------------------------------------------------------------------------------------
+
+def assemble_w(wsys, e):
+    """Dense M~ = I - V P^R and B^<> = V P^<> V^H (Sec. 3.2.1, W assembly)."""
+    nb, bs = wsys.nb, wsys.bs
+    V = bt_dense(wsys.V_diag, wsys.V_upper)
+    PRd, PRu, PRl, PLd, PLu, PGd, PGu = wsys.P_blocks(e)
+    PR = bt_dense(PRd, PRu, PRl)
+    PL = bt_dense(PLd, PLu, lower_sign=-1.0)
+    PG = bt_dense(PGd, PGu, lower_sign=-1.0)
+    n = nb * bs
+    M = np.eye(n) - V @ PR
+    BL = V @ PL @ V.conj().T
+    BG = V @ PG @ V.conj().T
+    return M, BL, BG, V
+
+
+def solve_w(wsys, e, symmetrize=True):
+    """W^R = (I - V P^R)^{-1} V and W^<> = X^R (V P^<> V^H) X^R^H, selected blocks."""
+    M, BL, BG, V = assemble_w(wsys, e)
+    XR = np.linalg.inv(M)
+    WR = XR @ V
+    WL = XR @ BL @ XR.conj().T
+    WG = XR @ BG @ XR.conj().T
+    if symmetrize:
+        WL = symmetrize_lesser(WL)
+        WG = symmetrize_lesser(WG)
+    nb, bs = wsys.nb, wsys.bs
+    Rd, Ru, Rl = selected_blocks(WR, nb, bs)
+    Ld, Lu, _ = selected_blocks(WL, nb, bs)
+    Gd, Gu, _ = selected_blocks(WG, nb, bs)
+    XRd, XRu, XRl = selected_blocks(XR, nb, bs)
+    return dict(R_diag=Rd, R_upper=Ru, R_lower=Rl, L_diag=Ld, L_upper=Lu, G_diag=Gd, G_upper=Gu,
+                XR_diag=XRd, XR_upper=XRu, XR_lower=XRl, M=M, BL=BL, BG=BG, XR=XR, WR=WR)
+
+
+# ----------------------------------------------------------------------------------------------
+# Observables (Sec. 3.4) used as invariants
+# ----------------------------------------------------------------------------------------------
+
+def transmission(sysg, e):
+    """Landauer transmission T = Tr[Gam_L G^R_1N Gam_R G^A_N1] with Gam_c = i(B^R_c - B^R_c^H)."""
+    M, _, _, o = assemble_g(sysg, e)
+    bs = sysg.bs
+    XR = np.linalg.inv(M)
+    GamL = 1j * (o["R_L"] - o["R_L"].conj().T)
+    GamR = 1j * (o["R_R"] - o["R_R"].conj().T)
+    G1N = XR[:bs, -bs:]
+    return float(np.real(np.trace(GamL @ G1N @ GamR @ G1N.conj().T)))
+
+
+def bond_currents(H_upper, L_upper):
+    """Bond current between cells i and i+1: I_i = 2 Re Tr[H_{i,i+1} G^<_{i+1,i}] with
+    G^<_{i+1,i} = -(G^<_{i,i+1})^H (anti-Hermiticity)."""
+    out = []
+    for i in range(H_upper.shape[0]):
+        Glow = -np.conj(L_upper[i].T)
+        out.append(2.0 * np.real(np.trace(H_upper[i] @ Glow)))
+    return np.array(out)
+
+
+# ----------------------------------------------------------------------------------------------
+# Sampled blocks for devices too large for a dense inverse: rows of M~^{-1} by banded LU
+# ----------------------------------------------------------------------------------------------
+
+def _band_storage(A_diag, A_upper, A_lower, transpose):
+    """LAPACK band storage of a BT matrix (or its transpose) with l = u = 2 bs - 1."""
+    nb, bs = A_diag.shape[0], A_diag.shape[1]
+    n = nb * bs
+    kl = ku = 2 * bs - 1
+    ab = np.zeros((kl + ku + 1, n), dtype=np.complex128)
+
+    def put(block, r0, c0):
+        if transpose:
+            block = block.T
+            r0, c0 = c0, r0
+        rr, cc = np.meshgrid(np.arange(bs) + r0, np.arange(bs) + c0, indexing="ij")
+        ab[ku + rr - cc, cc] = block
+
+    for i in range(nb):
+        put(A_diag[i], i * bs, i * bs)
+    for i in range(nb - 1):
+        put(A_upper[i], i * bs, (i + 1) * bs)
+        put(A_lower[i], (i + 1) * bs, i * bs)
+    return ab, kl, ku
+
+
+def block_rows_banded(A_diag, A_upper, A_lower, rows):
+    """Full block rows `rows` of A^{-1} for a BT matrix A, by banded LU of A^T (LAPACK gbsv):
+    row block i of A^{-1} is (A^{-T} E_i)^T.  Returns {i: [bs, n] array}."""
+    nb, bs = A_diag.shape[0], A_diag.shape[1]
+    n = nb * bs
+    ab, kl, ku = _band_storage(A_diag, A_upper, A_lower, transpose=True)
+    rhs = np.zeros((n, bs * len(rows)), dtype=np.complex128)
+    for k, i in enumerate(rows):
+        rhs[i * bs:(i + 1) * bs, k * bs:(k + 1) * bs] = np.eye(bs)
+    Z = sla.solve_banded((kl, ku), ab, rhs, check_finite=False)
+    return {i: Z[:, k * bs:(k + 1) * bs].T.copy() for k, i in enumerate(rows)}
+
+
+def solve_g_sampled(sysg, e, blocks, symmetrize=True, tol=1e-14, maxit=100):
+    """Selected blocks at energy index e for block indices `blocks` without a dense inverse:
+    rows i and i+1 of X^R by banded LU, then X^<>_{ij} = X^R[i,:] B^<> X^R[j,:]^H with the
+    (block-diagonal) B^<> of the G system.  Returns {i: dict(R_diag, R_upper, R_lower, L_diag,
+    L_upper, G_diag, G_upper)} (upper/lower entries only when i+1 < N)."""
+    nb, bs = sysg.nb, sysg.bs
+    d, u, l = _M_blocks(sysg, e)
+    d = d.copy()
+    bl = [np.zeros((bs, bs), np.complex128) for _ in range(nb)]
+    bg = [np.zeros((bs, bs), np.complex128) for _ in range(nb)]
+    for i in range(nb):
+        if sysg.sigL_diag is not None:
+            bl[i] += np.diag(sysg.sigL_diag[e, i])
+        if sysg.sigG_diag is not None:
+            bg[i] += np.diag(sysg.sigG_diag[e, i])
+    if sysg.obc:
+        o = obc_self_energies(sysg, e, tol, maxit)
+        d[0] -= o["R_L"]
+        d[-1] -= o["R_R"]
+        bl[0] += o["L_L"]
+        bl[-1] += o["L_R"]
+        bg[0] += o["G_L"]
+        bg[-1] += o["G_R"]
+    need = sorted(set(list(blocks) + [i + 1 for i in blocks if i + 1 < nb]))
+    rows = block_rows_banded(d, u, l, need)
+
+    def quad(ri, rj, bb):
+        acc = np.zeros((bs, bs), np.complex128)
+        for k in range(nb):
+            acc += ri[:, k * bs:(k + 1) * bs] @ bb[k] @ rj[:, k * bs:(k + 1) * bs].conj().T
+        return acc
+
+    out = {}
+    for i in blocks:
+        ri = rows[i]
+        r = dict(R_diag=ri[:, i * bs:(i + 1) * bs])
+        Ld = quad(ri, ri, bl)
+        Gd = quad(ri, ri, bg)
+        if symmetrize:
+            Ld = 0.5 * (Ld - Ld.conj().T)
+            Gd = 0.5 * (Gd - Gd.conj().T)
+        r["L_diag"], r["G_diag"] = Ld, Gd
+        if i + 1 < nb:
+            rj = rows[i + 1]
+            r["R_upper"] = ri[:, (i + 1) * bs:(i + 2) * bs]
+            r["R_lower"] = rj[:, i * bs:(i + 1) * bs]
+            Lu = quad(ri, rj, bl)
+            Gu = quad(ri, rj, bg)
+            if symmetrize:
+                Lu = 0.5 * (Lu - quad(rj, ri, bl).conj().T)
+                Gu = 0.5 * (Gu - quad(rj, ri, bg).conj().T)
+            r["L_upper"], r["G_upper"] = Lu, Gu
+        out[i] = r
+    return out
