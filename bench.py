@@ -1,0 +1,368 @@
+#!/usr/bin/env python
+"""Benchmark of block-tridiagonal selected inversion (RGF + Sancho-Rubio contacts) on GB300.
+
+Workload (default): the nanoribbon-shaped G system, 40 blocks of 416 (sparse-in-dense H, diagonal
+scattering self-energies), 512 energies on [-4, 4].  One step = one bt_selinv_solve over a batch
+of `--energies-per-step` consecutive grid energies (all hot-path stages: assembly, decimation,
+forward and backward sweeps, symmetrised write-out).  Inputs are resident in HBM before the timed
+region; the per-step working set (>10 GB) exceeds L2, so no flush is needed.
+
+Prints ONE JSON line (rank 0).  Multi-GPU (torchrun): every rank solves its own energies (weak
+scaling, no data-path collective); time = max over ranks.
+`--impl reference`: times the CPU oracle on a bounded sample instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "BT selected-inversion energy points/s, FP64-eq TFLOP/s vs peak, p50/p99 latency"
+UNIT = "energy points/s"
+# FP64 roofline denominator: nominal GB300 FP64 rate (1.25 TFLOP/s, profiling recipe table); the
+# FP64 FMA pipe measured 1.20 TFLOP/s on this machine.
+FP64_PEAK_TFLOPS = 1.25
+# dram bytes (read + write) per launch of the dominant kernel from the committed ncu capture of
+# the same launch shape (profiles/); None until captured for the current kernel.
+ZGEMM_TRAFFIC_BYTES = None
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=["nanoribbon", "random8x32"], default="nanoribbon")
+    p.add_argument("--energies-per-step", type=int, default=16)
+    p.add_argument("--precision", choices=["fp64", "split"], default="fp64")
+    p.add_argument("--slices", type=int, default=0)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample-blocks", type=int, default=10)
+    return p.parse_args()
+
+
+def make_workload(name):
+    import synthetic
+    if name == "nanoribbon":
+        return synthetic.nanoribbon_40x416(), "nanoribbon G system 40x416, 512 energies on [-4,4]"
+    return synthetic.random_device_8x32(), "random device 8x32, 64 energies on [-3,3]"
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index: int):
+        self.proc = None
+        self.index = index
+        self.path = None
+
+    def start(self):
+        try:
+            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{self.index}.csv")
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle on a bounded sample (cpu_baseline and the reference arm)
+# ------------------------------------------------------------------------------------------
+def cpu_oracle_sample(sysg, sample_blocks: int, energy_index: int):
+    """Dense oracle (numpy LAPACK, all host threads) on one energy of the device truncated to its
+    first `sample_blocks` blocks; returns (seconds, scale) with scale = dense-cost ratio to the
+    full device, so full-energy seconds ~= seconds * scale."""
+    import dataclasses
+
+    import numpy as np
+
+    import oracle
+    nb = sysg.nb
+    k = min(sample_blocks, nb)
+    sub = dataclasses.replace(sysg, H_diag=sysg.H_diag[:k], H_upper=sysg.H_upper[:k - 1],
+                              energies=sysg.energies[energy_index:energy_index + 1],
+                              sigR_diag=None if sysg.sigR_diag is None else sysg.sigR_diag[energy_index:energy_index + 1, :k],
+                              sigL_diag=None if sysg.sigL_diag is None else sysg.sigL_diag[energy_index:energy_index + 1, :k],
+                              sigG_diag=None if sysg.sigG_diag is None else sysg.sigG_diag[energy_index:energy_index + 1, :k])
+    t0 = time.perf_counter()
+    oracle.solve_g(sub, 0)
+    dt = time.perf_counter() - t0
+    return dt, (nb / k) ** 3, k
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    sysg, wl = make_workload(args.workload)
+    n_steps = args.steps + args.warmup
+    times = []
+    for s in range(n_steps):
+        dt, scale, k = cpu_oracle_sample(sysg, args.cpu_sample_blocks, (s * 37) % len(sysg.energies))
+        if s >= args.warmup:
+            times.append(dt * scale)
+    per_energy = statistics.median(times)
+    value = 1.0 / per_energy
+    sample = (f"dense oracle on 1 energy of the {wl} truncated to its first {k} blocks per step, "
+              f"seconds x (nb/{k})^3 dense-cost ratio = one full energy")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_energy * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl, "energies_per_step": 1, "precision": "fp64", "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2508_19138_gb300 as pkg
+    from paper_2508_19138_gb300.highlevel import GSolver
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    pkg.library()
+    sysg, wl = make_workload(args.workload)
+    nE = len(sysg.energies)
+    eps = min(args.energies_per_step, nE)
+    # interleave the grid so that every batch of eps energies spans the whole energy window
+    nbat = max(1, nE // eps)
+    perm = (np.arange(nbat)[:, None] + nbat * np.arange(eps)[None, :]).ravel()
+    sysg = sysg.subset(perm)
+    wl += f"; each step = {eps} energies strided across the grid"
+    precision = pkg.BT_SPLIT if args.precision == "split" else pkg.BT_FP64
+    stream = torch.cuda.Stream()
+    solver = GSolver(sysg.nb, sysg.bs, eps, sysg.eta, sysg.kT, sysg.mu_left, sysg.mu_right, obc=True,
+                     precision=precision, split_slices=args.slices, stream=stream)
+    with torch.cuda.stream(stream):
+        solver.set_inputs(sysg.H_diag, sysg.H_upper, sysg.sigR_diag, sysg.sigL_diag, sysg.sigG_diag)
+        outs, status = solver.allocate_outputs(eps)
+    torch.cuda.synchronize()
+    n_batches = max(1, nE // eps)
+
+    def batch_range(step):
+        j = (rank * 7919 + step) % n_batches
+        return j * eps, j * eps + eps
+
+    def one_step(step):
+        e0, e1 = batch_range(step)
+        solver.solve(sysg.energies[e0:e1], outs, status, sig_range=(e0, e1))
+
+    # warm-up
+    for w in range(args.warmup):
+        one_step(w)
+    torch.cuda.synchronize()
+    st0 = solver.stats()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier()
+    ev[0].record(stream)
+    for s in range(args.steps):
+        one_step(args.warmup + s)
+        ev[s + 1].record(stream)
+    barrier()
+    clk = clocks.stop()
+    st1 = solver.stats()
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    bad = int((status.cpu().numpy() != 0).sum())
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms_max = float(t.item())
+    value = eps * args.steps * world / (total_ms_max / 1e3)
+    flops_step = st1["flops_model"]
+    launches = int(st1["kernel_launches"] - st0["kernel_launches"])
+
+    # ---- dominant-kernel roofline: the FP64 complex GEMM at the sweep's launch shape ----
+    bs = sysg.bs
+    A = torch.randn(eps, bs, bs, dtype=torch.complex128, device="cuda")
+    B = torch.randn(eps, bs, bs, dtype=torch.complex128, device="cuda")
+    Cm = torch.empty_like(A)
+    reps = 5
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            pkg.bt_zgemm_batched(bs, bs, bs, 1.0, A, bs, bs * bs, 0, B, bs, bs * bs, 0, 0.0, Cm, bs, bs * bs, eps,
+                                 stream=stream)
+        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k0.record(stream)
+        for _ in range(reps):
+            pkg.bt_zgemm_batched(bs, bs, bs, 1.0, A, bs, bs * bs, 0, B, bs, bs * bs, 0, 0.0, Cm, bs, bs * bs, eps,
+                                 stream=stream)
+        k1.record(stream)
+    torch.cuda.synchronize()
+    kms = k0.elapsed_time(k1) / reps
+    achieved = 8.0 * bs ** 3 * eps / (kms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": ZGEMM_TRAFFIC_BYTES,
+                "kernel": f"zgemm_kernel (FP64 DFMA) {bs}^3 x {eps}", "launch_ms": kms,
+                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe); measured FP64 FMA probe 1.20"}
+    del A, B, Cm
+
+    # ---- end to end through the host-buffer entry point ----
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, pkg, sysg, solver, eps, rank, world, barrier, dist)
+
+    line = None
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == pkg.BT_FP64 else "f64+bf16-sliced",
+                "data": "synthetic",
+                "config": {"workload": wl, "nb": sysg.nb, "bs": sysg.bs, "grid_energies": nE,
+                           "energies_per_step": eps, "precision": args.precision,
+                           "l2": "per-step working set > 10 GB exceeds L2; no flush",
+                           "parallelism": f"energy replicas x{world} (no collective)"},
+                "fp64_eq_tflops": flops_step / (statistics.median(step_ms) / 1e3) / 1e12,
+                "fp64_eq_frac_of_peak": flops_step / (statistics.median(step_ms) / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+                "decim_iterations_per_step": (st1["decim_iterations"] - st0["decim_iterations"]) / args.steps,
+                "nonzero_status": bad, "roofline": roofline, "clocks": clk, "gpu_launches": launches,
+                "e2e": e2e}
+        if not args.no_cpu_baseline and world == 1:
+            dt, scale, k = cpu_oracle_sample(sysg, args.cpu_sample_blocks, 101 % nE)
+            line["cpu_baseline"] = {
+                "value": 1.0 / (dt * scale), "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+                "sample": (f"dense oracle on 1 energy of the workload truncated to its first {k} of {sysg.nb} "
+                           f"blocks: {dt:.2f} s, x(nb/{k})^3 = {scale:.0f} dense-cost ratio per full energy")}
+    solver.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_e2e(args, pkg, sysg, solver, eps, rank, world, barrier, dist):
+    """Same steps through bt_selinv_solve_host: pinned host inputs, host outputs, copies inside."""
+    import numpy as np
+    import torch
+
+    from paper_2508_19138_gb300 import BT, BTOut, BT_LAYOUT_BLOCKS, BT_LAYOUT_DIAGVEC, BT_SYM_ANTIHERMITIAN, \
+        BT_SYM_GENERAL, BT_SYM_HERMITIAN, bt_selinv_solve_host
+
+    nb, bs = sysg.nb, sysg.bs
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    Hd, Hu = pin(sysg.H_diag), pin(sysg.H_upper)
+    H = BT(Hd, Hu, None, BT_LAYOUT_BLOCKS, BT_SYM_HERMITIAN, False)
+    sR, sL, sG = pin(sysg.sigR_diag), pin(sysg.sigL_diag), pin(sysg.sigG_diag)
+    mk = lambda shape: torch.empty(shape, dtype=torch.complex128).pin_memory()
+    oR = BTOut(mk((eps, nb, bs, bs)), mk((eps, nb - 1, bs, bs)), mk((eps, nb - 1, bs, bs)))
+    oL = BTOut(mk((eps, nb, bs, bs)), mk((eps, nb - 1, bs, bs)), None)
+    oG = BTOut(mk((eps, nb, bs, bs)), mk((eps, nb - 1, bs, bs)), None)
+    status = torch.zeros(eps, dtype=torch.int32).pin_memory()
+    nE = len(sysg.energies)
+    n_batches = max(1, nE // eps)
+
+    def step(s):
+        j = (rank * 7919 + s + 3) % n_batches
+        e0, e1 = j * eps, j * eps + eps
+        bt_selinv_solve_host(solver.ctx, H, None, BT(sR[e0:e1], None, None, BT_LAYOUT_DIAGVEC, BT_SYM_GENERAL, True),
+                             BT(sL[e0:e1], None, None, BT_LAYOUT_DIAGVEC, BT_SYM_ANTIHERMITIAN, True),
+                             BT(sG[e0:e1], None, None, BT_LAYOUT_DIAGVEC, BT_SYM_ANTIHERMITIAN, True),
+                             sysg.energies[e0:e1], oR, oL, oG, status)
+
+    step(0)  # warm (staging allocation)
+    barrier()
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        step(1 + s)
+    barrier()
+    dt = time.perf_counter() - t0
+    t = torch.tensor([dt], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dt = float(t.item())
+    c16 = 16
+    h2d = (Hd.numel() + Hu.numel()) * c16 + 3 * eps * nb * bs * c16 + 8 * eps
+    d2h = (oR.diag.numel() + oR.upper.numel() + oR.lower.numel() + 2 * (oL.diag.numel() + oL.upper.numel())) * c16 \
+        + 4 * eps
+    return {"value": eps * args.steps * world / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "entry_point": "bt_selinv_solve_host (pinned host buffers)"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,216 @@
+/*
+ * bt_selinv.h -- C ABI of the GB300 (sm_103a) block-tridiagonal selected-inversion library.
+ *
+ * The library computes, for a batch of energies, the selected blocks of the solution of the
+ * quadratic system of Sec. 2, Eq. 1 of "QuaTrEx: ... NEGF+scGW" (arXiv 2508.19138):
+ *
+ *     (M - B^R) X^<> (M - B^R)^H = B^<>,      X^R = (M - B^R)^{-1} = M~^{-1},
+ *
+ * with the quantities of Table 2:
+ *   electrons (BT_SYS_G):          M = E S - H,  B^R = Sigma^R,   B^<> = Sigma^<>
+ *   screened Coulomb (BT_SYS_W):   M = I,        B^R = V P^R,     B^<> = V P^<> V^H
+ * plus the open-boundary blocks B_OBC of Sec. 3.1 (Eq. 4, Sancho-Rubio decimation; lesser /
+ * greater by fluctuation-dissipation).  The solver is the recursive Green's function method
+ * of Sec. 3.2.2 (forward pass Eq. 8-9, backward pass Eq. 10-11), with the symmetrisation of
+ * Sec. 4.2.  Outputs are the diagonal and first off-diagonal blocks.
+ *
+ * Conventions shared by every entry point:
+ *   - complex numbers are complex128: two doubles (re, im), the layout of cuDoubleComplex,
+ *     std::complex<double> and torch.complex128;
+ *   - a block is bs x bs, row-major; block arrays are [nb][bs][bs] (diagonal blocks) and
+ *     [nb-1][bs][bs] (upper blocks (i,i+1) or lower blocks (i+1,i)), with a leading
+ *     [n_energies] dimension for per-energy data;
+ *   - unless an entry point says otherwise all data pointers are DEVICE pointers owned by the
+ *     caller; the library owns only its workspace (allocated in bt_selinv_create);
+ *   - calls are asynchronous on the stream given at creation; the return code reports
+ *     argument and launch errors, numerical failures are reported per energy in a device
+ *     status array (bt_status codes);
+ *   - no C++ exception crosses this boundary; a context is bound to one stream and is not
+ *     thread-safe.
+ */
+#ifndef BT_SELINV_H
+#define BT_SELINV_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define BT_API __attribute__((visibility("default")))
+#else
+#define BT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BT_OK = 0,
+  BT_ERR_INVALID_ARG = 1,   /* a size, pointer or flag is out of range                      */
+  BT_ERR_OOM = 2,           /* cudaMalloc of the workspace failed                            */
+  BT_ERR_BUDGET = 3,        /* the workspace would exceed hbm_budget_bytes                   */
+  BT_ERR_CUDA = 4,          /* a CUDA runtime call or kernel launch failed                   */
+  BT_ERR_SINGULAR = 5,      /* per energy: a zero pivot in a block inversion                 */
+  BT_ERR_NOT_CONVERGED = 6, /* per energy: decimation reached decim_maxit                    */
+  BT_ERR_NONFINITE = 7,     /* per energy: NaN / Inf in an input or a pivot                  */
+  BT_ERR_TIMEOUT = 8,       /* a bounded device wait expired                                 */
+  BT_ERR_UNSUPPORTED = 9    /* valid request this build does not implement                   */
+} bt_status;
+
+typedef enum { BT_SYS_G = 0, BT_SYS_W = 1 } bt_system;           /* Table 2 columns      */
+typedef enum { BT_FP64 = 0, BT_SPLIT = 1 } bt_precision;         /* see bt_selinv_desc   */
+typedef enum { BT_LAYOUT_BLOCKS = 0, BT_LAYOUT_DIAGVEC = 1 } bt_layout;
+typedef enum { BT_SYM_GENERAL = 0, BT_SYM_HERMITIAN = 1, BT_SYM_ANTIHERMITIAN = 2 } bt_symmetry;
+
+/* A block-tridiagonal input operand.
+ *   diag   BT_LAYOUT_BLOCKS : [nb][bs][bs] diagonal blocks
+ *          BT_LAYOUT_DIAGVEC: [nb][bs] the diagonal entries only (a diagonal matrix; upper and
+ *                             lower must be NULL)
+ *   upper  [nb-1][bs][bs] blocks (i,i+1); NULL means all off-diagonal blocks are zero
+ *   lower  [nb-1][bs][bs] blocks (i+1,i); read only when symmetry == BT_SYM_GENERAL, else
+ *          block (i+1,i) is upper[i]^H (HERMITIAN) or -upper[i]^H (ANTIHERMITIAN)
+ *   per_energy  0: one operand shared by every energy; 1: each pointer addresses
+ *          [n_energies][...] with the per-energy extent given above
+ * Pointers are device pointers (host pointers for bt_selinv_solve_host).  diag may be NULL
+ * only for optional operands (then the whole operand is zero). */
+typedef struct {
+  const void* diag;
+  const void* upper;
+  const void* lower;
+  int layout;
+  int symmetry;
+  int per_energy;
+} bt_bt;
+
+/* An output operand: [n_energies][nb][bs][bs] diagonal blocks, [n_energies][nb-1][bs][bs]
+ * upper (i,i+1) and lower (i+1,i) blocks.  A NULL pointer means "do not write". */
+typedef struct {
+  void* diag;
+  void* upper;
+  void* lower;
+} bt_bt_out;
+
+typedef struct {
+  int nb;              /* number of diagonal blocks N_B >= 1                                  */
+  int bs;              /* block size N_BS >= 1                                                */
+  int max_energies;    /* energies processed per chunk; sizes the workspace                   */
+  int system;          /* bt_system                                                            */
+  int precision;       /* BT_FP64: every product in FP64.  BT_SPLIT: the off-diagonal block
+                          products of the sweeps as sliced (Ozaki) products on the bf16 tensor
+                          cores with exact fp32 accumulation; inversions, decimation and
+                          symmetrisation stay FP64                                              */
+  int split_slices;    /* BT_SPLIT: slices per operand (0 = default 6, range 2..8)            */
+  int symmetrize;      /* 1: lesser/greater diagonal blocks returned as (X - X^H)/2 (Sec. 4.2) */
+  int obc;             /* 1: Sancho-Rubio contacts on both ends (G only, nb >= 2)             */
+  double eta;          /* G: z = E + i eta                                                     */
+  double kT;           /* contact temperature (energy units of H)                              */
+  double mu_left;      /* contact Fermi levels                                                 */
+  double mu_right;
+  double decim_tol;    /* decimation stops when max|a|,max|b| <= decim_tol * max|n| (<=0: 1e-14) */
+  int decim_maxit;     /* decimation iteration cap (<= 0: 100)                                 */
+  size_t hbm_budget_bytes; /* 0 = unlimited; otherwise the workspace must fit                  */
+} bt_selinv_desc;
+
+typedef struct bt_ctx bt_ctx;
+
+typedef struct {
+  long long solves;            /* bt_selinv_solve calls completed (host count)                */
+  long long energies;          /* energies processed                                          */
+  long long decim_iterations;  /* sum over chunks of the decimation iterations executed       */
+  double flops_model;          /* minimal-model flops of the last solve (8 b^3 per block
+                                  product or inversion, actual decimation iterations)         */
+  size_t workspace_bytes;
+  long long kernel_launches;   /* kernels this context launched (all solves)                  */
+} bt_stats;
+
+/* Sizes of the workspace bt_selinv_create would allocate for `desc`. */
+BT_API bt_status bt_selinv_workspace_bytes(const bt_selinv_desc* desc, size_t* bytes);
+
+/* Validate `desc`, allocate the workspace on the current device, bind `cuda_stream`
+ * (a cudaStream_t; NULL = default stream).  On success *out owns the workspace. */
+BT_API bt_status bt_selinv_create(const bt_selinv_desc* desc, void* cuda_stream, bt_ctx** out);
+
+/* Selected inversion for n_energies energies (processed in chunks of max_energies).
+ *   H       G: Hamiltonian H (BLOCKS, Hermitian or general, shared or per energy)
+ *           W: bare Coulomb V (BLOCKS, Hermitian, shared)
+ *   S       G: overlap (NULL = identity); W: must be NULL
+ *   sigR    G: retarded scattering self-energy Sigma^R (NULL = 0; BLOCKS or DIAGVEC)
+ *           W: retarded polarisation P^R (BLOCKS, per energy)
+ *   sigL/G  G: Sigma^< / Sigma^> (NULL = 0); W: P^< / P^> (BLOCKS, per energy, anti-Hermitian)
+ *   energies_host  [n_energies] energies E (host memory; read before the call returns)
+ *   outR    G: X^R = G^R blocks (diag, upper, lower); W: W^R = X^R V blocks
+ *   outL/G  G: G^< / G^> (diag, upper; lower = -upper^H is not written); W: W^< / W^>
+ *   status_device  [n_energies] ints, BT_OK or the first numerical failure of that energy
+ * Returns BT_OK when every launch was issued. */
+BT_API bt_status bt_selinv_solve(bt_ctx* ctx, const bt_bt* H, const bt_bt* S, const bt_bt* sigR,
+                          const bt_bt* sigL, const bt_bt* sigG, const double* energies_host,
+                          int n_energies, const bt_bt_out* outR, const bt_bt_out* outL,
+                          const bt_bt_out* outG, int* status_device);
+
+/* Same as bt_selinv_solve, but every data pointer (inputs, outputs, status) is HOST memory.
+ * Inputs are copied to the device chunk by chunk, outputs copied back; the call returns
+ * after the last copy completed (synchronous).  Pinned host memory gives full copy speed. */
+BT_API bt_status bt_selinv_solve_host(bt_ctx* ctx, const bt_bt* H, const bt_bt* S, const bt_bt* sigR,
+                               const bt_bt* sigL, const bt_bt* sigG, const double* energies_host,
+                               int n_energies, const bt_bt_out* outR, const bt_bt_out* outL,
+                               const bt_bt_out* outG, int* status_host);
+
+BT_API bt_status bt_selinv_get_stats(const bt_ctx* ctx, bt_stats* out);
+BT_API bt_status bt_selinv_destroy(bt_ctx* ctx);
+/* Text of the last error recorded on ctx (or of the last failed create when ctx is NULL). */
+BT_API const char* bt_selinv_last_error(const bt_ctx* ctx);
+
+/* ---------------------------------------------------------------------------------------
+ * Building blocks, exported for callers that assemble their own sweeps (and for tests).
+ * ------------------------------------------------------------------------------------- */
+
+enum { BT_OP_N = 0, BT_OP_C = 1 };  /* op(X) = X or X^H (conjugate transpose) */
+
+/* C[b] = alpha * op(A[b]) * op(B[b]) + beta * C[b] for b < batch, complex128, FP64 arithmetic
+ * (the dense products of Eq. 8-11).  op(A) is m x k, op(B) is k x n, C is m x n, all row-major
+ * with leading dimensions lda/ldb/ldc (elements); strideX is the element distance between
+ * batch entries (0 = the same matrix for every batch entry).  beta = 0 does not read C.
+ * C must not alias A or B. */
+BT_API bt_status bt_zgemm_batched(int m, int n, int k, double alpha_re, double alpha_im,
+                           const void* A, int lda, long long strideA, int opA,
+                           const void* B, int ldb, long long strideB, int opB,
+                           double beta_re, double beta_im, void* C, int ldc, long long strideC,
+                           int batch, void* stream);
+
+/* Same product with the sliced split-precision scheme used by BT_SPLIT: each operand is
+ * scaled per row (A) / per column (B) by a power of two and cut into `slices` 7-bit integer
+ * slices held exactly in bf16; slice products run on the tcgen05 tensor cores with fp32
+ * accumulation that is exact for k <= 1024 (per k-chunk), and are summed in FP64.
+ * Any m, n, k >= 1: ragged edges are zero padded.
+ * `workspace` must hold bt_split_zgemm_workspace_bytes(m, n, k, slices, batch) bytes. */
+BT_API bt_status bt_split_zgemm_workspace_bytes(int m, int n, int k, int slices, int batch, size_t* bytes);
+BT_API bt_status bt_split_zgemm_batched(int m, int n, int k, double alpha_re, double alpha_im,
+                                 const void* A, int lda, long long strideA, int opA,
+                                 const void* B, int ldb, long long strideB, int opB,
+                                 double beta_re, double beta_im, void* C, int ldc, long long strideC,
+                                 int batch, int slices, void* workspace, size_t workspace_bytes,
+                                 void* stream);
+
+/* In-place inverse of `batch` n x n complex128 matrices (A + b*strideA), Gauss-Jordan
+ * elimination with partial (row) pivoting -- the block LU of the forward pass (Eq. 8) carried
+ * to the full inverse; pivots chosen by max |re| + |im|, first index on ties.
+ * info_device[b] = 0, or BT_ERR_SINGULAR / BT_ERR_NONFINITE (matrix b is then undefined).
+ * `workspace` must hold bt_zinv_workspace_bytes(n, batch) bytes (may be 0 for small n). */
+BT_API bt_status bt_zinv_workspace_bytes(int n, int batch, size_t* bytes);
+BT_API bt_status bt_zinv_batched(int n, void* A, long long strideA, int batch, int* info_device,
+                          void* workspace, size_t workspace_bytes, void* stream);
+
+/* Surface Green's function of semi-infinite leads, x = (m - n x n')^{-1} (Eq. 4), by
+ * Sancho-Rubio decimation for `batch` independent leads (m, n, n' each [batch][bs][bs]).
+ * Writes x [batch][bs][bs] and the boundary block sigma = n x n' [batch][bs][bs];
+ * iters_device[b] = iterations used, info_device[b] = 0 / BT_ERR_NOT_CONVERGED / _SINGULAR.
+ * `workspace` must hold bt_decimate_workspace_bytes(bs, batch) bytes. */
+BT_API bt_status bt_decimate_workspace_bytes(int bs, int batch, size_t* bytes);
+BT_API bt_status bt_decimate_batched(int bs, int batch, const void* m, const void* n, const void* n_prime,
+                              double tol, int maxit, void* x, void* sigma, int* iters_device,
+                              int* info_device, void* workspace, size_t workspace_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BT_SELINV_H */

@@ -1,0 +1,89 @@
+// Shared device/host helpers of the sm_103a kernels: complex128 arithmetic on double2,
+// launch checks, and the internal launcher declarations used across translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include "../../include/bt_selinv.h"
+
+typedef double2 zd;  // complex128: x = re, y = im
+
+__host__ __device__ __forceinline__ zd zmake(double r, double i) { zd z; z.x = r; z.y = i; return z; }
+__host__ __device__ __forceinline__ zd zadd(zd a, zd b) { return zmake(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ zd zsub(zd a, zd b) { return zmake(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ zd zmul(zd a, zd b) {
+  return zmake(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ zd zconj(zd a) { return zmake(a.x, -a.y); }
+__host__ __device__ __forceinline__ zd zscale(zd a, double s) { return zmake(a.x * s, a.y * s); }
+// acc += a * b with four fused multiply-adds
+__device__ __forceinline__ void zfma(zd& acc, zd a, zd b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+// 1 / a, scaled to avoid overflow of |a|^2 (Smith's method)
+__host__ __device__ __forceinline__ zd zinv(zd a) {
+  double ar = a.x, ai = a.y;
+  if (fabs(ar) >= fabs(ai)) {
+    double r = ai / ar, d = ar + ai * r;
+    return zmake(1.0 / d, -r / d);
+  } else {
+    double r = ar / ai, d = ai + ar * r;
+    return zmake(r / d, -1.0 / d);
+  }
+}
+__host__ __device__ __forceinline__ double zabs1(zd a) { return fabs(a.x) + fabs(a.y); }
+
+#define BT_CUDA_TRY(expr)                                      \
+  do {                                                         \
+    cudaError_t _e = (expr);                                   \
+    if (_e != cudaSuccess) return BT_ERR_CUDA;                 \
+  } while (0)
+
+#define BT_TRY(expr)                                           \
+  do {                                                         \
+    bt_status _s = (expr);                                     \
+    if (_s != BT_OK) return _s;                                \
+  } while (0)
+
+namespace bt {
+
+// Kernel launches issued by this library (process-wide counter).
+void count_launch();
+long long launches_total();
+
+// One GEMM operand: element (r, c) of op(X) for batch entry b is
+//   op == BT_OP_N : X[b*stride + r*ld + c]
+//   op == BT_OP_C : conj(X[b*stride + c*ld + r])
+struct Operand {
+  const zd* p;
+  int ld;
+  long long stride;
+  int op;
+};
+
+// C[b] = alpha op(A[b]) op(B[b]) + beta C[b]; rows m, cols n, depth k.  active[b] == 0 skips
+// batch entry b (active may be null).  FP64 (DFMA) kernel.
+bt_status zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A, Operand B, zd beta,
+                zd* C, int ldc, long long strideC, int batch, const int* active);
+
+// Split-precision (sliced bf16 tensor-core) variant of zgemm; see split_gemm.cu.
+size_t split_workspace_bytes(int m, int n, int k, int slices, int batch);
+bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A, Operand B, zd beta,
+                      zd* C, int ldc, long long strideC, int batch, int slices, void* ws,
+                      size_t ws_bytes, const int* active);
+
+// In-place batched inverse (Gauss-Jordan, partial pivoting).  info[b] |= error code.
+size_t zinv_workspace_bytes(int n, int batch);
+bt_status zinv(cudaStream_t st, int n, zd* A, long long strideA, int batch, int* info, void* ws,
+               size_t ws_bytes, const int* active);
+
+// Sancho-Rubio decimation for `batch` leads.
+size_t decimate_workspace_bytes(int bs, int batch);
+bt_status decimate(cudaStream_t st, int bs, int batch, const zd* m, const zd* n, const zd* np,
+                   double tol, int maxit, zd* x, zd* sigma, int* iters, int* info, void* ws,
+                   size_t ws_bytes, int* iters_host_max, int* h_pinned);
+
+}  // namespace bt

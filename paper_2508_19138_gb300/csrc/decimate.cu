@@ -1,0 +1,222 @@
+// Sancho-Rubio decimation for the retarded open-boundary condition (Sec. 3.1, Eq. 4):
+//     x = (m - n x n')^{-1}
+// for a batch of independent semi-infinite leads (cells with diagonal block m, coupling n from a
+// cell to the next one away from the device and n' back).  Every iteration removes every second
+// cell of the lead (Sancho, Lopez Sancho, Rubio 1985, the method the paper cites):
+//     g = e^{-1};  e_s -= a g b;  e -= a g b + b g a;  a <- -a g a;  b <- -b g b
+// from a = n, b = n', e = e_s = m, until max|a|, max|b| <= tol * max(|n|, |n'|); then
+// x = e_s^{-1} and the boundary block sigma = n x n'.
+//
+// The per-lead convergence test is a warp-shuffle max-|.| reduction followed by a block
+// reduction; converged leads drop out of every later launch through an `active` mask, and
+// the host stops as soon as the device-side count of active leads reaches zero.  The loop is
+// bounded by maxit; leads still active then get BT_ERR_NOT_CONVERGED (never a hang).
+#include "bt_common.cuh"
+
+namespace bt {
+namespace {
+
+constexpr int NT = 256;
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+  return v;
+}
+
+// block-wide max of v (NaN-propagating: any NaN makes the result NaN)
+__device__ double block_max(double v, double* sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int nan = isnan(v);
+  nan = __syncthreads_or(nan);
+  v = warp_max(v);
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+    r = warp_max(r);
+    if (lane == 0) sh[0] = r;
+  }
+  __syncthreads();
+  r = sh[0];
+  __syncthreads();
+  return nan ? __longlong_as_double(0x7ff8000000000000ULL) : r;
+}
+
+__device__ __forceinline__ double zmod(zd a) { return sqrt(a.x * a.x + a.y * a.y); }
+
+// ref[l] = max(max|n|, max|n'|)
+__global__ void __launch_bounds__(NT) ref_kernel(int bs2, const zd* __restrict__ n, const zd* __restrict__ np,
+                                                 double* __restrict__ ref) {
+  __shared__ double sh[32];
+  const int l = blockIdx.x;
+  double v = 0.0;
+  for (int e = threadIdx.x; e < bs2; e += blockDim.x)
+    v = fmax(v, fmax(zmod(n[(long long)l * bs2 + e]), zmod(np[(long long)l * bs2 + e])));
+  v = block_max(v, sh);
+  if (threadIdx.x == 0) ref[l] = v;
+}
+
+// convergence test of one iteration: lead l leaves the active set once max|a|,|b| <= tol*ref
+__global__ void __launch_bounds__(NT) check_kernel(int bs2, const zd* __restrict__ a, const zd* __restrict__ b,
+                                                   const double* __restrict__ ref, double tol, int it,
+                                                   int* __restrict__ active, int* __restrict__ iters,
+                                                   int* __restrict__ info, int* __restrict__ n_active) {
+  __shared__ double sh[32];
+  const int l = blockIdx.x;
+  if (active[l] == 0) return;
+  double v = 0.0;
+  for (int e = threadIdx.x; e < bs2; e += blockDim.x)
+    v = fmax(v, fmax(zmod(a[(long long)l * bs2 + e]), zmod(b[(long long)l * bs2 + e])));
+  v = block_max(v, sh);
+  if (threadIdx.x == 0) {
+    iters[l] = it;
+    if (isnan(v) || info[l] != 0) {
+      if (info[l] == 0) info[l] = BT_ERR_NONFINITE;
+      active[l] = 0;
+    } else if (v <= tol * ref[l]) {
+      active[l] = 0;
+    } else {
+      atomicAdd(n_active, 1);
+    }
+  }
+}
+
+// es -= t; e -= t  (active leads only)
+__global__ void sub2_kernel(long long bs2, int batch, const zd* __restrict__ t, zd* __restrict__ es,
+                            zd* __restrict__ e, const int* __restrict__ active) {
+  const int l = blockIdx.y;
+  if (active[l] == 0) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < bs2; i += (long long)gridDim.x * blockDim.x) {
+    const long long o = (long long)l * bs2 + i;
+    es[o] = zsub(es[o], t[o]);
+    e[o] = zsub(e[o], t[o]);
+  }
+}
+
+__global__ void init_kernel(int batch, int* active, int* iters, int* info) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l < batch) { active[l] = 1; iters[l] = 0; info[l] = 0; }
+}
+
+__global__ void finish_kernel(int batch, const int* active, int* info) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l < batch && active[l] != 0 && info[l] == 0) info[l] = BT_ERR_NOT_CONVERGED;
+}
+
+struct DecimWs {
+  zd *a, *b, *a2, *b2, *e, *es, *g, *ag, *bg, *t;
+  double* ref;
+  int* active;
+  int* n_active;
+  void* inv_ws;
+  size_t inv_bytes;
+};
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+size_t carve(void* base, int bs, int batch, DecimWs* w) {
+  const size_t mat = align256((size_t)batch * bs * bs * sizeof(zd));
+  char* p = static_cast<char*>(base);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { char* q = p ? p + off : nullptr; off += align256(bytes); return q; };
+  zd** mats[] = {&w->a, &w->b, &w->a2, &w->b2, &w->e, &w->es, &w->g, &w->ag, &w->bg, &w->t};
+  for (zd** m : mats) *m = reinterpret_cast<zd*>(take(mat));
+  w->ref = reinterpret_cast<double*>(take(sizeof(double) * batch));
+  w->active = reinterpret_cast<int*>(take(sizeof(int) * batch));
+  w->n_active = reinterpret_cast<int*>(take(sizeof(int)));
+  w->inv_bytes = zinv_workspace_bytes(bs, batch);
+  w->inv_ws = take(w->inv_bytes);
+  return off;
+}
+
+}  // namespace
+
+size_t decimate_workspace_bytes(int bs, int batch) {
+  DecimWs w;
+  return carve(nullptr, bs, batch, &w);
+}
+
+bt_status decimate(cudaStream_t st, int bs, int batch, const zd* m, const zd* n, const zd* np, double tol,
+                   int maxit, zd* x, zd* sigma, int* iters, int* info, void* ws, size_t ws_bytes,
+                   int* iters_host_max, int* h_pinned) {
+  if (bs <= 0 || batch <= 0 || maxit <= 0 || batch > 65535) return BT_ERR_INVALID_ARG;
+  if (!ws || ws_bytes < decimate_workspace_bytes(bs, batch)) return BT_ERR_INVALID_ARG;
+  DecimWs w;
+  carve(ws, bs, batch, &w);
+  const long long bs2 = (long long)bs * bs;
+  const size_t mat_bytes = (size_t)batch * bs2 * sizeof(zd);
+  BT_CUDA_TRY(cudaMemcpyAsync(w.a, n, mat_bytes, cudaMemcpyDeviceToDevice, st));
+  BT_CUDA_TRY(cudaMemcpyAsync(w.b, np, mat_bytes, cudaMemcpyDeviceToDevice, st));
+  BT_CUDA_TRY(cudaMemcpyAsync(w.e, m, mat_bytes, cudaMemcpyDeviceToDevice, st));
+  BT_CUDA_TRY(cudaMemcpyAsync(w.es, m, mat_bytes, cudaMemcpyDeviceToDevice, st));
+  init_kernel<<<(batch + 255) / 256, 256, 0, st>>>(batch, w.active, iters, info); count_launch();
+  ref_kernel<<<batch, NT, 0, st>>>((int)bs2, n, np, w.ref); count_launch();
+  BT_CUDA_TRY(cudaGetLastError());
+
+  int* h_active = h_pinned;
+  if (!h_active) BT_CUDA_TRY(cudaMallocHost(&h_active, sizeof(int)));
+  const zd one = zmake(1.0, 0.0), mone = zmake(-1.0, 0.0), zero = zmake(0.0, 0.0);
+  const long long S = bs2;
+  int it = 0;
+  bt_status rc = BT_OK;
+  for (it = 1; it <= maxit; ++it) {
+    if (cudaMemcpyAsync(w.g, w.e, mat_bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) { rc = BT_ERR_CUDA; break; }
+    if ((rc = zinv(st, bs, w.g, S, batch, info, w.inv_ws, w.inv_bytes, w.active)) != BT_OK) break;
+    // ag = a g, bg = b g
+    if ((rc = zgemm(st, bs, bs, bs, one, Operand{w.a, bs, S, BT_OP_N}, Operand{w.g, bs, S, BT_OP_N}, zero, w.ag, bs, S, batch, w.active)) != BT_OK) break;
+    if ((rc = zgemm(st, bs, bs, bs, one, Operand{w.b, bs, S, BT_OP_N}, Operand{w.g, bs, S, BT_OP_N}, zero, w.bg, bs, S, batch, w.active)) != BT_OK) break;
+    // t = a g b; es -= t; e -= t
+    if ((rc = zgemm(st, bs, bs, bs, one, Operand{w.ag, bs, S, BT_OP_N}, Operand{w.b, bs, S, BT_OP_N}, zero, w.t, bs, S, batch, w.active)) != BT_OK) break;
+    {
+      dim3 g((unsigned)((bs2 + 255) / 256 < 64 ? (bs2 + 255) / 256 : 64), batch);
+      sub2_kernel<<<g, 256, 0, st>>>(bs2, batch, w.t, w.es, w.e, w.active); count_launch();
+    }
+    // e -= b g a
+    if ((rc = zgemm(st, bs, bs, bs, mone, Operand{w.bg, bs, S, BT_OP_N}, Operand{w.a, bs, S, BT_OP_N}, one, w.e, bs, S, batch, w.active)) != BT_OK) break;
+    // a2 = -a g a, b2 = -b g b
+    if ((rc = zgemm(st, bs, bs, bs, mone, Operand{w.ag, bs, S, BT_OP_N}, Operand{w.a, bs, S, BT_OP_N}, zero, w.a2, bs, S, batch, w.active)) != BT_OK) break;
+    if ((rc = zgemm(st, bs, bs, bs, mone, Operand{w.bg, bs, S, BT_OP_N}, Operand{w.b, bs, S, BT_OP_N}, zero, w.b2, bs, S, batch, w.active)) != BT_OK) break;
+    std::swap(w.a, w.a2);
+    std::swap(w.b, w.b2);
+    if (cudaMemsetAsync(w.n_active, 0, sizeof(int), st) != cudaSuccess) { rc = BT_ERR_CUDA; break; }
+    check_kernel<<<batch, NT, 0, st>>>((int)bs2, w.a, w.b, w.ref, tol, it, w.active, iters, info, w.n_active); count_launch();
+    if (cudaGetLastError() != cudaSuccess) { rc = BT_ERR_CUDA; break; }
+    if (cudaMemcpyAsync(h_active, w.n_active, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) { rc = BT_ERR_CUDA; break; }
+    if (cudaStreamSynchronize(st) != cudaSuccess) { rc = BT_ERR_CUDA; break; }
+    if (*h_active == 0) break;
+  }
+  if (!h_pinned) cudaFreeHost(h_active);
+  if (rc != BT_OK) return rc;
+  if (iters_host_max) *iters_host_max = it > maxit ? maxit : it;
+  finish_kernel<<<(batch + 255) / 256, 256, 0, st>>>(batch, w.active, info); count_launch();
+  BT_CUDA_TRY(cudaGetLastError());
+  // x = e_s^{-1};  sigma = n x n'
+  BT_CUDA_TRY(cudaMemcpyAsync(x, w.es, mat_bytes, cudaMemcpyDeviceToDevice, st));
+  BT_TRY(zinv(st, bs, x, S, batch, info, w.inv_ws, w.inv_bytes, nullptr));
+  if (sigma) {
+    BT_TRY(zgemm(st, bs, bs, bs, one, Operand{n, bs, S, BT_OP_N}, Operand{x, bs, S, BT_OP_N}, zero, w.t, bs, S, batch, nullptr));
+    BT_TRY(zgemm(st, bs, bs, bs, one, Operand{w.t, bs, S, BT_OP_N}, Operand{np, bs, S, BT_OP_N}, zero, sigma, bs, S, batch, nullptr));
+  }
+  return BT_OK;
+}
+
+}  // namespace bt
+
+extern "C" bt_status bt_decimate_workspace_bytes(int bs, int batch, size_t* bytes) {
+  if (!bytes || bs <= 0 || batch <= 0) return BT_ERR_INVALID_ARG;
+  *bytes = bt::decimate_workspace_bytes(bs, batch);
+  return BT_OK;
+}
+
+extern "C" bt_status bt_decimate_batched(int bs, int batch, const void* m, const void* n, const void* n_prime,
+                                         double tol, int maxit, void* x, void* sigma, int* iters_device,
+                                         int* info_device, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!m || !n || !n_prime || !x || !iters_device || !info_device) return BT_ERR_INVALID_ARG;
+  if (!(tol > 0.0)) tol = 1e-14;
+  if (maxit <= 0) maxit = 100;
+  return bt::decimate(static_cast<cudaStream_t>(stream), bs, batch, static_cast<const zd*>(m),
+                      static_cast<const zd*>(n), static_cast<const zd*>(n_prime), tol, maxit, static_cast<zd*>(x),
+                      static_cast<zd*>(sigma), iters_device, info_device, workspace, workspace_bytes, nullptr, nullptr);
+}

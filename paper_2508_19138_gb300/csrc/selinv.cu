@@ -1,0 +1,946 @@
+// Context, workspace and the recursive Green's function sweeps (Sec. 3.2.2) behind the C ABI.
+//
+// For a chunk of Ec energies every step below is ONE batched launch over the chunk (the
+// energies are the data-parallel axis, Sec. 3.3 / 4.4):
+//   a1  assembly of M~ = M - B^R_scatt - B^R_OBC and B^<> (Table 2, Sec. 3.2.1);
+//       W system: V P^R and V P^<> V^H as block-tridiagonal products
+//   a2  contact decimation (Eq. 4) for the 2 Ec leads, fluctuation-dissipation for B^<>_OBC
+//   a3  forward pass, Eq. 8 (x^R_i) and Eq. 9 (x^<>_i, with y_i = M~_{i,i-1} x^R_{i-1} B_{i-1,i})
+//   a4  backward pass, Eq. 10 (X^R_i), Eq. 11 (X^<>_i with Y_i, Z_i); first off-diagonal blocks
+//         X^R_{i,i+1} = -x^R_i M~_{i,i+1} X^R_{i+1},   X^R_{i+1,i} = -X^R_{i+1} M~_{i+1,i} x^R_i
+//         X^<>_{i,i+1} = -x^R_i M~_{i,i+1} X^<>_{i+1} - x^<>_i (X^R_{i+1} M~_{i+1,i})^H
+//                        + x^R_i B^<>_{i,i+1} (X^R_{i+1})^H
+//       W system: W^R = X^R V on the selected blocks (needs X^R_{i,i+-2})
+//   a5  symmetrised write-out of the diagonal lesser/greater blocks (Sec. 4.2)
+// All products go through prod(), which runs the FP64 DFMA kernel or, with BT_SPLIT, the
+// sliced bf16 tensor-core product.  Inversions and decimation are always FP64.
+#include <algorithm>
+#include <cstring>
+#include <functional>
+#include <string>
+#include <vector>
+
+#include "elementwise.cuh"
+
+struct bt_ctx {
+  bt_selinv_desc d{};
+  cudaStream_t st = nullptr;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  // chunk workspace (E = max_energies, B2 = bs^2)
+  zd *xR = nullptr, *xL = nullptr, *xG = nullptr;     // [E][N][B2]
+  zd *Mu = nullptr, *Ml = nullptr;                    // [E][N-1][B2] assembled off-diagonal M~ (general / W)
+  zd *XRu = nullptr, *XRl = nullptr;                  // [E][N-1][B2] kept for the W products
+  zd *Md = nullptr;                                   // [E][N][B2] W: assembled M~ diagonal
+  zd *BdL = nullptr, *BdG = nullptr, *BuL = nullptr, *BuG = nullptr;  // W: B^<> blocks
+  zd *Td = nullptr, *Tu = nullptr, *Tl = nullptr;     // W: V P products [E][N or N-1][B2]
+  zd *X2u = nullptr, *X2l = nullptr;                  // W: X^R_{i,i+2}, X^R_{i+2,i} [E][N-2][B2]
+  zd* t[12] = {};                                     // [E][B2] temporaries
+  zd *lead_m = nullptr, *lead_n = nullptr, *lead_np = nullptr, *lead_x = nullptr, *lead_sig = nullptr;
+  zd *obcL = nullptr, *obcG = nullptr;                // [2E][B2]
+  int *lead_iters = nullptr, *lead_info = nullptr;    // [2E]
+  zd* z = nullptr;
+  double *fL = nullptr, *fR = nullptr, *Edev = nullptr;
+  void* inv_ws = nullptr;
+  size_t inv_bytes = 0;
+  void* dec_ws = nullptr;
+  size_t dec_bytes = 0;
+  void* split_ws = nullptr;
+  size_t split_bytes = 0;
+  int* h_pinned = nullptr;
+  double* h_E = nullptr;
+  // host-buffer entry point staging (allocated on first use)
+  char* stage = nullptr;
+  size_t stage_bytes = 0;
+  std::string err;
+  bt_stats stats{};
+  double flops = 0.0;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+size_t al(size_t x) { return (x + 255) / 256 * 256; }
+
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(char* b) : base(b) {}
+  template <class T>
+  T* take(size_t count) {
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += al(count * sizeof(T));
+    return p;
+  }
+};
+
+bool is_split(const bt_selinv_desc& d) { return d.precision == BT_SPLIT; }
+int slices_of(const bt_selinv_desc& d) { return d.split_slices > 0 ? d.split_slices : 6; }
+
+// Lays out the workspace; with base == nullptr only measures it.
+size_t layout(bt_ctx* c, const bt_selinv_desc& d, char* base) {
+  Carver cv(base);
+  const size_t E = (size_t)d.max_energies, N = (size_t)d.nb, B2 = (size_t)d.bs * d.bs;
+  const size_t N1 = N > 1 ? N - 1 : 1;
+  bt_ctx tmp;
+  bt_ctx* x = c ? c : &tmp;
+  x->xR = cv.take<zd>(E * N * B2);
+  x->xL = cv.take<zd>(E * N * B2);
+  x->xG = cv.take<zd>(E * N * B2);
+  x->Mu = cv.take<zd>(E * N1 * B2);
+  x->Ml = cv.take<zd>(E * N1 * B2);
+  for (int i = 0; i < 12; ++i) x->t[i] = cv.take<zd>(E * B2);
+  if (d.system == BT_SYS_W) {
+    x->XRu = cv.take<zd>(E * N1 * B2);
+    x->XRl = cv.take<zd>(E * N1 * B2);
+    x->Md = cv.take<zd>(E * N * B2);
+    x->BdL = cv.take<zd>(E * N * B2);
+    x->BdG = cv.take<zd>(E * N * B2);
+    x->BuL = cv.take<zd>(E * N1 * B2);
+    x->BuG = cv.take<zd>(E * N1 * B2);
+    x->Td = cv.take<zd>(E * N * B2);
+    x->Tu = cv.take<zd>(E * N1 * B2);
+    x->Tl = cv.take<zd>(E * N1 * B2);
+    const size_t N2 = N > 2 ? N - 2 : 1;
+    x->X2u = cv.take<zd>(E * N2 * B2);
+    x->X2l = cv.take<zd>(E * N2 * B2);
+  }
+  if (d.obc) {
+    x->lead_m = cv.take<zd>(2 * E * B2);
+    x->lead_n = cv.take<zd>(2 * E * B2);
+    x->lead_np = cv.take<zd>(2 * E * B2);
+    x->lead_x = cv.take<zd>(2 * E * B2);
+    x->lead_sig = cv.take<zd>(2 * E * B2);
+    x->obcL = cv.take<zd>(2 * E * B2);
+    x->obcG = cv.take<zd>(2 * E * B2);
+    x->lead_iters = cv.take<int>(2 * E);
+    x->lead_info = cv.take<int>(2 * E);
+    x->dec_bytes = bt::decimate_workspace_bytes(d.bs, (int)(2 * E));
+    x->dec_ws = cv.take<char>(x->dec_bytes);
+  }
+  x->z = cv.take<zd>(E);
+  x->fL = cv.take<double>(E);
+  x->fR = cv.take<double>(E);
+  x->Edev = cv.take<double>(E);
+  x->inv_bytes = bt::zinv_workspace_bytes(d.bs, (int)E);
+  x->inv_ws = cv.take<char>(x->inv_bytes);
+  if (is_split(d)) {
+    x->split_bytes = bt::split_workspace_bytes(d.bs, d.bs, d.bs, slices_of(d), (int)E);
+    x->split_ws = cv.take<char>(x->split_bytes);
+  }
+  return cv.off;
+}
+
+bt_status validate_desc(const bt_selinv_desc* d, std::string* why) {
+  auto fail = [&](const char* m) { if (why) *why = m; return BT_ERR_INVALID_ARG; };
+  if (!d) return fail("desc is NULL");
+  if (d->nb < 1) return fail("nb must be >= 1");
+  if (d->bs < 1) return fail("bs must be >= 1");
+  if (d->max_energies < 1 || d->max_energies > 32767) return fail("max_energies must be in [1, 32767]");
+  if (d->system != BT_SYS_G && d->system != BT_SYS_W) return fail("unknown system");
+  if (d->precision != BT_FP64 && d->precision != BT_SPLIT) return fail("unknown precision");
+  if (d->precision == BT_SPLIT && (d->split_slices != 0 && (d->split_slices < 2 || d->split_slices > 8)))
+    return fail("split_slices must be 0 or in [2, 8]");
+  if (d->obc && d->system != BT_SYS_G) return fail("Sancho-Rubio contacts are defined for the G system only");
+  if (d->obc && d->nb < 2) return fail("contacts from the edge blocks need nb >= 2");
+  if (d->obc && !(d->kT > 0.0)) return fail("kT must be > 0 with contacts");
+  if (!(d->eta >= 0.0)) return fail("eta must be >= 0");
+  if ((double)d->bs * d->bs * d->nb > 4.0e12) return fail("problem too large");
+  return BT_OK;
+}
+
+struct Blk {  // one block operand for the chunk: pointer at energy 0 of the chunk, energy stride
+  const zd* p = nullptr;
+  long long es = 0;
+  int op = BT_OP_N;
+  double f = 1.0;  // real factor folded into alpha
+  bool valid() const { return p != nullptr; }
+};
+
+inline bt::Operand opnd(const Blk& b, int bs) { return bt::Operand{b.p, bs, b.es, b.op}; }
+inline Blk flip(Blk b) { b.op = b.op == BT_OP_N ? BT_OP_C : BT_OP_N; return b; }
+inline Blk ws_blk(const zd* p, long long es) { Blk b; b.p = p; b.es = es; return b; }
+
+struct Sweep {
+  bt_ctx* c;
+  int Ec;
+  int N, bs;
+  long long B2;
+  bool needL, needG, needRlower, keepRoff, has_boff;
+  std::function<bt_status(int, zd*, long long)> asmM;              // M~_ii -> dst (energy stride)
+  std::function<bt_status(int, int, zd*, long long)> asmB;         // B_ii (which 0:<,1:>) -> dst
+  std::function<Blk(int)> Mu, Ml;                                  // M~_{i,i+1}, M~_{i+1,i}
+  std::function<Blk(int, int)> Bu;                                 // B_{i,i+1} (which)
+  // outputs for this chunk (nullptr = not requested)
+  zd *oRu = nullptr, *oRl = nullptr, *oLu = nullptr, *oGu = nullptr;
+  long long oes_u = 0;  // energy stride of upper/lower outputs
+  // W system: X^R_{i,i+2} and X^R_{i+2,i} (need keepRoff), [E][N-2][B2]
+  zd *X2u = nullptr, *X2l = nullptr;
+};
+
+bt_status set_err(bt_ctx* c, bt_status s, const char* what) {
+  if (s != BT_OK && c) c->err = what;
+  return s;
+}
+
+// C = alpha op(A) op(B) + beta C for the chunk (bs x bs blocks)
+bt_status prod(bt_ctx* c, int Ec, double alpha, const Blk& A, const Blk& B, double beta, zd* C, long long sC,
+               bool allow_split = true) {
+  const int bs = c->d.bs;
+  const double a = alpha * A.f * B.f;
+  c->flops += 8.0 * bs * (double)bs * bs * Ec;
+  if (allow_split && is_split(c->d))
+    return bt::split_zgemm(c->st, bs, bs, bs, zmake(a, 0.0), opnd(A, bs), opnd(B, bs), zmake(beta, 0.0), C, bs, sC,
+                           Ec, slices_of(c->d), c->split_ws, c->split_bytes, nullptr);
+  return bt::zgemm(c->st, bs, bs, bs, zmake(a, 0.0), opnd(A, bs), opnd(B, bs), zmake(beta, 0.0), C, bs, sC, Ec,
+                   nullptr);
+}
+
+bt_status inv(bt_ctx* c, int Ec, zd* A, long long sA, int* info) {
+  const int bs = c->d.bs;
+  c->flops += 8.0 * bs * (double)bs * bs * Ec;
+  return bt::zinv(c->st, bs, A, sA, Ec, info, c->inv_ws, c->inv_bytes, nullptr);
+}
+
+// Forward (Eq. 8-9) and backward (Eq. 10-11) passes for one chunk.  x^R, x^<> live in
+// c->xR/xL/xG and are overwritten by X^R, X^<> in the backward pass.
+bt_status run_sweep(Sweep& s, int* status) {
+  bt_ctx* c = s.c;
+  const int Ec = s.Ec, N = s.N, bs = s.bs;
+  const long long B2 = s.B2, NB2 = (long long)N * B2;
+  zd** t = c->t;
+  auto xR = [&](int i) { return c->xR + i * B2; };
+  auto xLG = [&](int w, int i) { return (w == 0 ? c->xL : c->xG) + i * B2; };
+  auto X = [&](zd* p, long long es) { return ws_blk(p, es); };
+  const bool need[2] = {s.needL, s.needG};
+
+  // ---------------- forward pass ----------------
+  for (int i = 0; i < N; ++i) {
+    zd* T1 = t[0];
+    if (i > 0) BT_TRY(prod(c, Ec, 1.0, s.Ml(i - 1), X(xR(i - 1), NB2), 0.0, T1, B2));  // M~_{i,i-1} x^R_{i-1}
+    BT_TRY(s.asmM(i, xR(i), NB2));
+    if (i > 0) BT_TRY(prod(c, Ec, -1.0, X(T1, B2), s.Mu(i - 1), 1.0, xR(i), NB2));      // - ... M~_{i-1,i}
+    BT_TRY(inv(c, Ec, xR(i), NB2, status));
+    for (int w = 0; w < 2; ++w) {
+      if (!need[w]) continue;
+      zd *Bt = t[1], *Tq = t[2], *Y = t[3];
+      BT_TRY(s.asmB(i, w, Bt, B2));
+      if (i > 0) {
+        BT_TRY(prod(c, Ec, 1.0, s.Ml(i - 1), X(xLG(w, i - 1), NB2), 0.0, Tq, B2));        // M~_{i,i-1} x^<>_{i-1}
+        BT_TRY(prod(c, Ec, 1.0, X(Tq, B2), flip(s.Ml(i - 1)), 1.0, Bt, B2));              // ... M~_{i,i-1}^H
+        if (s.has_boff) {
+          Blk bu = s.Bu(i - 1, w);
+          if (bu.valid()) {
+            BT_TRY(prod(c, Ec, 1.0, X(T1, B2), bu, 0.0, Y, B2));                          // y_i
+            BT_TRY(bt::add_antiherm(c->st, bs, Ec, Bt, B2, Y, B2, -1.0));                  // - (y - y^H)
+          }
+        }
+      }
+      BT_TRY(prod(c, Ec, 1.0, X(xR(i), NB2), X(Bt, B2), 0.0, Tq, B2));
+      BT_TRY(prod(c, Ec, 1.0, X(Tq, B2), flip(X(xR(i), NB2)), 0.0, xLG(w, i), NB2));     // x^R (...) x^R^H
+    }
+  }
+  // ---------------- backward pass ----------------
+  const long long N1B2 = (long long)(N - 1) * B2;
+  for (int i = N - 2; i >= 0; --i) {
+    zd *U1 = t[0], *W1 = t[1], *V1 = t[2], *P = t[3], *Zt = t[4], *Z = t[5], *Yb = t[6];
+    zd* XB[2] = {t[7], t[8]};
+    zd* XRn = xR(i + 1);
+    BT_TRY(prod(c, Ec, 1.0, X(xR(i), NB2), s.Mu(i), 0.0, U1, B2));                 // x^R_i M~_{i,i+1}
+    BT_TRY(prod(c, Ec, 1.0, s.Ml(i), X(xR(i), NB2), 0.0, W1, B2));                 // M~_{i+1,i} x^R_i
+    // X^R_{i,i+1}
+    zd* XRu;
+    long long esu;
+    if (s.keepRoff) { XRu = c->XRu + i * B2; esu = N1B2; }
+    else if (s.oRu) { XRu = s.oRu + i * B2; esu = s.oes_u; }
+    else { XRu = t[9]; esu = B2; }
+    BT_TRY(prod(c, Ec, -1.0, X(U1, B2), X(XRn, NB2), 0.0, XRu, esu));
+    if (s.keepRoff && s.oRu) BT_TRY(bt::write_blocks(c->st, bs, 1, Ec, XRu, 0, esu, s.oRu + i * B2, 0, s.oes_u, 0));
+    if (s.needRlower || s.keepRoff) {
+      zd* XRl;
+      long long esl;
+      if (s.keepRoff) { XRl = c->XRl + i * B2; esl = N1B2; }
+      else { XRl = s.oRl + i * B2; esl = s.oes_u; }
+      BT_TRY(prod(c, Ec, -1.0, X(XRn, NB2), X(W1, B2), 0.0, XRl, esl));
+      if (s.keepRoff && s.oRl) BT_TRY(bt::write_blocks(c->st, bs, 1, Ec, XRl, 0, esl, s.oRl + i * B2, 0, s.oes_u, 0));
+    }
+    if (s.X2u && i + 2 < N) {
+      // X^R_{i,i+2} = -x^R_i M~_{i,i+1} X^R_{i+1,i+2};  X^R_{i+2,i} = -X^R_{i+2,i+1} M~_{i+1,i} x^R_i
+      const long long N2B2 = (long long)(N - 2) * B2;
+      BT_TRY(prod(c, Ec, -1.0, X(U1, B2), X(c->XRu + (i + 1) * B2, N1B2), 0.0, s.X2u + i * B2, N2B2));
+      BT_TRY(prod(c, Ec, -1.0, X(c->XRl + (i + 1) * B2, N1B2), X(W1, B2), 0.0, s.X2l + i * B2, N2B2));
+    }
+    const bool anyLG = s.needL || s.needG;
+    if (anyLG) BT_TRY(prod(c, Ec, 1.0, X(XRn, NB2), s.Ml(i), 0.0, V1, B2));        // X^R_{i+1} M~_{i+1,i}
+    if (anyLG && s.has_boff) {
+      for (int w = 0; w < 2; ++w) {
+        if (!need[w]) continue;
+        Blk bu = s.Bu(i, w);
+        if (bu.valid()) BT_TRY(prod(c, Ec, 1.0, X(xR(i), NB2), bu, 0.0, XB[w], B2)); // x^R_i B_{i,i+1}
+      }
+    }
+    BT_TRY(prod(c, Ec, -1.0, X(XRu, esu), X(W1, B2), 1.0, xR(i), NB2));            // X^R_i (Eq. 10)
+    for (int w = 0; w < 2; ++w) {
+      if (!need[w]) continue;
+      zd* xLi = xLG(w, i);
+      zd* XLn = xLG(w, i + 1);
+      zd* oU = w == 0 ? s.oLu : s.oGu;
+      const bool bu_valid = s.has_boff && s.Bu(i, w).valid();
+      BT_TRY(prod(c, Ec, 1.0, X(U1, B2), X(XLn, NB2), 0.0, P, B2));                 // x^R M X^<>_{i+1}
+      if (oU) {
+        zd* d = oU + i * B2;
+        BT_TRY(prod(c, Ec, -1.0, X(xLi, NB2), flip(X(V1, B2)), 0.0, d, s.oes_u));  // - x^<> (X^R M)^H
+        BT_TRY(bt::axpby(c->st, B2, Ec, -1.0, P, B2, 1.0, d, s.oes_u));             // - x^R M X^<>
+        if (bu_valid)
+          BT_TRY(prod(c, Ec, 1.0, X(XB[w], B2), flip(X(XRn, NB2)), 1.0, d, s.oes_u));  // + x^R B X^R^H
+      }
+      BT_TRY(prod(c, Ec, 1.0, s.Ml(i), X(xLi, NB2), 0.0, Zt, B2));                  // M~_{i+1,i} x^<>_i
+      BT_TRY(prod(c, Ec, -1.0, X(XRu, esu), X(Zt, B2), 0.0, Z, B2));                // Z_i
+      BT_TRY(prod(c, Ec, 1.0, X(P, B2), flip(X(U1, B2)), 1.0, xLi, NB2));           // + x M X M^H x^H
+      BT_TRY(bt::add_antiherm(c->st, bs, Ec, xLi, NB2, Z, B2, 1.0));                // + (Z - Z^H)
+      if (bu_valid) {
+        BT_TRY(prod(c, Ec, -1.0, X(XB[w], B2), flip(X(XRu, esu)), 0.0, Yb, B2));    // Y_i
+        BT_TRY(bt::add_antiherm(c->st, bs, Ec, xLi, NB2, Yb, B2, -1.0));            // - (Y - Y^H)
+      }
+    }
+  }
+  return BT_OK;
+}
+
+}  // namespace
+
+// ======================================================================================
+// C ABI
+// ======================================================================================
+
+extern "C" bt_status bt_selinv_workspace_bytes(const bt_selinv_desc* desc, size_t* bytes) {
+  std::string why;
+  if (!bytes) return BT_ERR_INVALID_ARG;
+  bt_status s = validate_desc(desc, &why);
+  if (s != BT_OK) return s;
+  *bytes = layout(nullptr, *desc, nullptr);
+  return BT_OK;
+}
+
+extern "C" bt_status bt_selinv_create(const bt_selinv_desc* desc, void* cuda_stream, bt_ctx** out) {
+  g_create_error.clear();
+  if (!out) { g_create_error = "out is NULL"; return BT_ERR_INVALID_ARG; }
+  *out = nullptr;
+  std::string why;
+  bt_status s = validate_desc(desc, &why);
+  if (s != BT_OK) { g_create_error = why; return s; }
+  bt_selinv_desc d = *desc;
+  if (!(d.decim_tol > 0.0)) d.decim_tol = 1e-14;
+  if (d.decim_maxit <= 0) d.decim_maxit = 100;
+  const size_t need = layout(nullptr, d, nullptr);
+  if (d.hbm_budget_bytes && need > d.hbm_budget_bytes) {
+    g_create_error = "workspace exceeds hbm_budget_bytes";
+    return BT_ERR_BUDGET;
+  }
+  bt_ctx* c = new (std::nothrow) bt_ctx();
+  if (!c) { g_create_error = "host allocation failed"; return BT_ERR_OOM; }
+  c->d = d;
+  c->st = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaMalloc(&c->ws, need) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    g_create_error = "cudaMalloc of the workspace failed";
+    return BT_ERR_OOM;
+  }
+  c->ws_bytes = need;
+  layout(c, d, c->ws);
+  if (cudaMallocHost(&c->h_pinned, 64) != cudaSuccess || cudaMallocHost(&c->h_E, sizeof(double) * d.max_energies) != cudaSuccess) {
+    cudaGetLastError();
+    bt_selinv_destroy(c);
+    g_create_error = "pinned host allocation failed";
+    return BT_ERR_OOM;
+  }
+  c->stats.workspace_bytes = need;
+  *out = c;
+  return BT_OK;
+}
+
+extern "C" bt_status bt_selinv_destroy(bt_ctx* c) {
+  if (!c) return BT_OK;
+  if (c->ws) cudaFree(c->ws);
+  if (c->stage) cudaFree(c->stage);
+  if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  if (c->h_E) cudaFreeHost(c->h_E);
+  delete c;
+  return BT_OK;
+}
+
+extern "C" const char* bt_selinv_last_error(const bt_ctx* c) {
+  if (!c) return g_create_error.c_str();
+  return c->err.c_str();
+}
+
+extern "C" bt_status bt_selinv_get_stats(const bt_ctx* c, bt_stats* out) {
+  if (!c || !out) return BT_ERR_INVALID_ARG;
+  *out = c->stats;
+  return BT_OK;
+}
+
+namespace {
+
+// per-energy element extents of a bt_bt operand
+long long diag_extent(const bt_bt& b, int nb, int bs) {
+  return b.layout == BT_LAYOUT_DIAGVEC ? (long long)nb * bs : (long long)nb * bs * bs;
+}
+long long off_extent(int nb, int bs) { return (long long)(nb > 1 ? nb - 1 : 0) * bs * bs; }
+
+bt_status validate_operand(const bt_bt* b, bool required, bool allow_diagvec, const char* name, std::string* why) {
+  if (!b) {
+    if (required) { *why = std::string(name) + " is required"; return BT_ERR_INVALID_ARG; }
+    return BT_OK;
+  }
+  if (!b->diag && required) { *why = std::string(name) + ".diag is required"; return BT_ERR_INVALID_ARG; }
+  if (b->layout != BT_LAYOUT_BLOCKS && b->layout != BT_LAYOUT_DIAGVEC) { *why = std::string(name) + ": bad layout"; return BT_ERR_INVALID_ARG; }
+  if (b->layout == BT_LAYOUT_DIAGVEC && !allow_diagvec) { *why = std::string(name) + ": diagonal-vector layout not accepted"; return BT_ERR_INVALID_ARG; }
+  if (b->layout == BT_LAYOUT_DIAGVEC && (b->upper || b->lower)) { *why = std::string(name) + ": diagonal-vector layout has no off-diagonal blocks"; return BT_ERR_INVALID_ARG; }
+  if (b->symmetry < BT_SYM_GENERAL || b->symmetry > BT_SYM_ANTIHERMITIAN) { *why = std::string(name) + ": bad symmetry"; return BT_ERR_INVALID_ARG; }
+  if (b->upper && b->symmetry == BT_SYM_GENERAL && !b->lower) { *why = std::string(name) + ": general symmetry needs lower blocks"; return BT_ERR_INVALID_ARG; }
+  return BT_OK;
+}
+
+// Offset an operand to energy e0 of the solve.
+const zd* at_energy(const void* p, int per_energy, long long extent, long long e0) {
+  if (!p) return nullptr;
+  const zd* q = static_cast<const zd*>(p);
+  return per_energy ? q + extent * e0 : q;
+}
+
+bt_status solve_chunk_g(bt_ctx* c, const bt_bt* H, const bt_bt* S, const bt_bt* sR, const bt_bt* sL, const bt_bt* sG,
+                        long long e0, int Ec, const bt_bt_out* oR, const bt_bt_out* oL, const bt_bt_out* oG,
+                        int* status) {
+  const bt_selinv_desc& d = c->d;
+  const int N = d.nb, bs = d.bs;
+  const long long B2 = (long long)bs * bs, NB2 = N * B2, N1B2 = (long long)(N > 1 ? N - 1 : 0) * B2;
+  cudaStream_t st = c->st;
+  auto dstride = [&](const bt_bt* b) { return b && b->per_energy ? diag_extent(*b, N, bs) : 0LL; };
+  auto ostride = [&](const bt_bt* b) { return b && b->per_energy ? off_extent(N, bs) : 0LL; };
+  const zd* Hd = at_energy(H->diag, H->per_energy, diag_extent(*H, N, bs), e0);
+  const zd* Hu = at_energy(H->upper, H->per_energy, off_extent(N, bs), e0);
+  const zd* Hl = at_energy(H->lower, H->per_energy, off_extent(N, bs), e0);
+  const zd *Sd = nullptr, *Su = nullptr, *Sl = nullptr;
+  if (S) {
+    Sd = at_energy(S->diag, S->per_energy, diag_extent(*S, N, bs), e0);
+    Su = at_energy(S->upper, S->per_energy, off_extent(N, bs), e0);
+    Sl = at_energy(S->lower, S->per_energy, off_extent(N, bs), e0);
+  }
+  const zd *Rd = nullptr, *Ru = nullptr, *Rl = nullptr;
+  if (sR) {
+    Rd = at_energy(sR->diag, sR->per_energy, diag_extent(*sR, N, bs), e0);
+    Ru = at_energy(sR->upper, sR->per_energy, off_extent(N, bs), e0);
+    Rl = at_energy(sR->lower, sR->per_energy, off_extent(N, bs), e0);
+  }
+  const bt_bt* sLG[2] = {sL, sG};
+  const zd *LGd[2] = {nullptr, nullptr}, *LGu[2] = {nullptr, nullptr};
+  for (int w = 0; w < 2; ++w)
+    if (sLG[w]) {
+      LGd[w] = at_energy(sLG[w]->diag, sLG[w]->per_energy, diag_extent(*sLG[w], N, bs), e0);
+      LGu[w] = at_energy(sLG[w]->upper, sLG[w]->per_energy, off_extent(N, bs), e0);
+    }
+
+  // energies -> z, Fermi factors
+  BT_TRY(bt::energy_setup(st, Ec, c->Edev, d.eta, d.mu_left, d.mu_right, d.kT, c->z, c->fL, c->fR));
+
+  // Does M~ have per-energy off-diagonal blocks?  (S or Sigma^R with off-diagonal blocks, or
+  // a per-energy H): then they are assembled into c->Mu / c->Ml, else M~_{i,i+1} = -H_{i,i+1}.
+  const bool general_off = (S && Su) || (sR && Ru) || H->per_energy;
+  auto h_off = [&](int i, bool upper, bt::MBlockArgs& a) {
+    // a.H := H_{i,i+1} (upper) or H_{i+1,i} (lower)
+    if (upper) { a.H = Hu ? Hu + i * B2 : nullptr; a.H_stride = ostride(H); return; }
+    if (H->symmetry == BT_SYM_GENERAL) { a.H = Hl ? Hl + i * B2 : nullptr; a.H_stride = ostride(H); return; }
+    a.H = Hu ? Hu + i * B2 : nullptr;
+    a.H_stride = ostride(H);
+    a.H_conjT = 1;
+    a.H_sign = H->symmetry == BT_SYM_ANTIHERMITIAN ? -1.0 : 1.0;
+  };
+  auto off_args = [&](int i, bool upper, zd* out, long long out_stride) {
+    bt::MBlockArgs a;
+    a.out = out;
+    a.out_stride = out_stride;
+    a.z = c->z;
+    h_off(i, upper, a);
+    if (S && Su) {  // overlap: Hermitian unless given in full
+      a.use_z = 1;
+      if (upper || S->symmetry == BT_SYM_GENERAL) { a.S = (upper ? Su : Sl) + i * B2; }
+      else { a.S = Su + i * B2; a.S_conjT = 1; }
+      a.S_stride = ostride(S);
+    }
+    if (sR && Ru) {
+      if (upper || sR->symmetry == BT_SYM_GENERAL) { a.sig = (upper ? Ru : Rl) + i * B2; }
+      else { a.sig = Ru + i * B2; a.sig_conjT = 1; a.sig_sign = sR->symmetry == BT_SYM_ANTIHERMITIAN ? -1.0 : 1.0; }
+      a.sig_stride = ostride(sR);
+    }
+    return a;
+  };
+  if (general_off) {
+    for (int i = 0; i < N - 1; ++i) {
+      BT_TRY(bt::assemble_m(st, bs, Ec, off_args(i, true, c->Mu + i * B2, N1B2)));
+      BT_TRY(bt::assemble_m(st, bs, Ec, off_args(i, false, c->Ml + i * B2, N1B2)));
+    }
+  }
+  auto diag_args = [&](int i, zd* out, long long out_stride, bool with_obc) {
+    bt::MBlockArgs a;
+    a.out = out;
+    a.out_stride = out_stride;
+    a.z = c->z;
+    a.use_z = 1;
+    if (S && Sd) { a.S = Sd + i * B2; a.S_stride = dstride(S); }
+    else a.S_identity = 1;
+    a.H = Hd + i * B2;
+    a.H_stride = dstride(H);
+    if (sR && Rd) {
+      if (sR->layout == BT_LAYOUT_DIAGVEC) { a.sigvec = Rd + (long long)i * bs; a.sigvec_stride = dstride(sR); }
+      else { a.sig = Rd + i * B2; a.sig_stride = dstride(sR); }
+    }
+    if (with_obc && d.obc) {
+      a.obc_stride = B2;
+      if (i == 0) a.obc1 = c->lead_sig;
+      if (i == N - 1) a.obc2 = c->lead_sig + (long long)Ec * B2;
+    }
+    return a;
+  };
+
+  // ---------------- a2: contacts ----------------
+  if (d.obc) {
+    // left lead: m = M_11, n = M_21, n' = M_12;  right lead: m = M_NN, n = M_{N-1,N}, n' = M_{N,N-1}
+    BT_TRY(bt::assemble_m(st, bs, Ec, diag_args(0, c->lead_m, B2, false)));
+    BT_TRY(bt::assemble_m(st, bs, Ec, diag_args(N - 1, c->lead_m + Ec * B2, B2, false)));
+    BT_TRY(bt::assemble_m(st, bs, Ec, off_args(0, false, c->lead_n, B2)));
+    BT_TRY(bt::assemble_m(st, bs, Ec, off_args(0, true, c->lead_np, B2)));
+    BT_TRY(bt::assemble_m(st, bs, Ec, off_args(N - 2, true, c->lead_n + Ec * B2, B2)));
+    BT_TRY(bt::assemble_m(st, bs, Ec, off_args(N - 2, false, c->lead_np + Ec * B2, B2)));
+    int it_max = 0;
+    bt_status s = bt::decimate(st, bs, 2 * Ec, c->lead_m, c->lead_n, c->lead_np, d.decim_tol, d.decim_maxit, c->lead_x,
+                               c->lead_sig, c->lead_iters, c->lead_info, c->dec_ws, c->dec_bytes, &it_max,
+                               c->h_pinned);
+    if (s != BT_OK) return set_err(c, s, "decimation failed to launch");
+    c->stats.decim_iterations += it_max;
+    c->flops += 2.0 * Ec * (7.0 * it_max + 3.0) * 8.0 * bs * (double)bs * bs;
+    BT_TRY(bt::merge_status(st, Ec, c->lead_info, 2, Ec, status));
+    BT_TRY(bt::obc_lesser_greater(st, bs, Ec, c->lead_sig, c->fL, c->fR, c->obcL, c->obcG));
+  }
+
+  // ---------------- a1 + a3 + a4 ----------------
+  Sweep sw;
+  sw.c = c;
+  sw.Ec = Ec;
+  sw.N = N;
+  sw.bs = bs;
+  sw.B2 = B2;
+  sw.needL = oL && (oL->diag || oL->upper);
+  sw.needG = oG && (oG->diag || oG->upper);
+  sw.needRlower = oR && oR->lower;
+  sw.keepRoff = false;
+  sw.has_boff = (LGu[0] != nullptr) || (LGu[1] != nullptr);
+  sw.oRu = oR && oR->upper ? static_cast<zd*>(oR->upper) + e0 * N1B2 : nullptr;
+  sw.oRl = oR && oR->lower ? static_cast<zd*>(oR->lower) + e0 * N1B2 : nullptr;
+  sw.oLu = oL && oL->upper ? static_cast<zd*>(oL->upper) + e0 * N1B2 : nullptr;
+  sw.oGu = oG && oG->upper ? static_cast<zd*>(oG->upper) + e0 * N1B2 : nullptr;
+  sw.oes_u = N1B2;
+  sw.asmM = [&](int i, zd* dst, long long es) { return bt::assemble_m(st, bs, Ec, diag_args(i, dst, es, true)); };
+  sw.asmB = [&](int i, int w, zd* dst, long long es) {
+    bt::BBlockArgs a;
+    a.out = dst;
+    a.out_stride = es;
+    if (LGd[w]) {
+      if (sLG[w]->layout == BT_LAYOUT_DIAGVEC) { a.sigvec = LGd[w] + (long long)i * bs; a.sigvec_stride = dstride(sLG[w]); }
+      else { a.sig = LGd[w] + i * B2; a.sig_stride = dstride(sLG[w]); }
+    }
+    if (d.obc) {
+      const zd* ob = w == 0 ? c->obcL : c->obcG;
+      a.obc_stride = B2;
+      if (i == 0) a.obc1 = ob;
+      if (i == N - 1) a.obc2 = ob + (long long)Ec * B2;
+    }
+    return bt::assemble_b(st, bs, Ec, a);
+  };
+  if (general_off) {
+    sw.Mu = [&](int i) { return ws_blk(c->Mu + i * B2, N1B2); };
+    sw.Ml = [&](int i) { return ws_blk(c->Ml + i * B2, N1B2); };
+  } else {
+    sw.Mu = [&](int i) { Blk b; b.p = Hu + i * B2; b.es = 0; b.op = BT_OP_N; b.f = -1.0; return b; };
+    sw.Ml = [&](int i) {
+      Blk b;
+      b.es = 0;
+      if (H->symmetry == BT_SYM_GENERAL) { b.p = Hl + i * B2; b.op = BT_OP_N; b.f = -1.0; }
+      else { b.p = Hu + i * B2; b.op = BT_OP_C; b.f = H->symmetry == BT_SYM_ANTIHERMITIAN ? 1.0 : -1.0; }
+      return b;
+    };
+  }
+  sw.Bu = [&](int i, int w) {
+    Blk b;
+    if (LGu[w]) { b.p = LGu[w] + i * B2; b.es = ostride(sLG[w]); }
+    return b;
+  };
+  if (N > 1 && !Hu) return set_err(c, BT_ERR_INVALID_ARG, "H.upper is required for nb > 1");
+  BT_TRY(run_sweep(sw, status));
+
+  // ---------------- a5: write-out ----------------
+  if (oR && oR->diag)
+    BT_TRY(bt::write_blocks(st, bs, N, Ec, c->xR, B2, NB2, static_cast<zd*>(oR->diag) + e0 * NB2, B2, NB2, 0));
+  if (oL && oL->diag)
+    BT_TRY(bt::write_blocks(st, bs, N, Ec, c->xL, B2, NB2, static_cast<zd*>(oL->diag) + e0 * NB2, B2, NB2, d.symmetrize ? 1 : 0));
+  if (oG && oG->diag)
+    BT_TRY(bt::write_blocks(st, bs, N, Ec, c->xG, B2, NB2, static_cast<zd*>(oG->diag) + e0 * NB2, B2, NB2, d.symmetrize ? 1 : 0));
+  return BT_OK;
+}
+
+
+// W system (Table 2, right column): M~ = I - V P^R, B^<> = V P^<> V^H as block-tridiagonal
+// products (Sec. 3.2.1; exact when the cell is longer than 3 r_cut), the RGF sweep on them, and
+// W^R = X^R V on the selected blocks (X^R_{i,i+-2} from the backward pass).  W^<> = X^<>.
+bt_status solve_chunk_w(bt_ctx* c, const bt_bt* V, const bt_bt* PR, const bt_bt* PL, const bt_bt* PG, long long e0,
+                        int Ec, const bt_bt_out* oR, const bt_bt_out* oL, const bt_bt_out* oG, int* status) {
+  const bt_selinv_desc& d = c->d;
+  const int N = d.nb, bs = d.bs;
+  const long long B2 = (long long)bs * bs, NB2 = N * B2, N1B2 = (long long)(N > 1 ? N - 1 : 0) * B2;
+  const long long N2B2 = (long long)(N > 2 ? N - 2 : 0) * B2;
+  cudaStream_t st = c->st;
+  const zd* Vd = static_cast<const zd*>(V->diag);
+  const zd* Vu = static_cast<const zd*>(V->upper);
+  auto Vb = [&](int i, int j) {  // V_{ij}, |i-j| <= 1, V Hermitian
+    Blk b;
+    b.es = 0;
+    if (i == j) { b.p = Vd + i * B2; }
+    else if (j == i + 1) { b.p = Vu + i * B2; }
+    else { b.p = Vu + j * B2; b.op = BT_OP_C; }
+    return b;
+  };
+  auto Vh = [&](int i, int j) { return flip(Vb(i, j)); };  // (V_{ij})^H
+  struct PT { const zd *d, *u, *l; long long ed, eo; int sym; };
+  auto mkP = [&](const bt_bt* P) {
+    PT p{};
+    if (!P) return p;
+    p.ed = P->per_energy ? NB2 : 0;
+    p.eo = P->per_energy ? N1B2 : 0;
+    p.d = at_energy(P->diag, P->per_energy, NB2, e0);
+    p.u = at_energy(P->upper, P->per_energy, N1B2, e0);
+    p.l = at_energy(P->lower, P->per_energy, N1B2, e0);
+    p.sym = P->symmetry;
+    return p;
+  };
+  auto Pb = [&](const PT& p, int i, int j) {  // P_{ij} for energy 0 of the chunk
+    Blk b;
+    if (i == j) { b.p = p.d + i * B2; b.es = p.ed; }
+    else if (j == i + 1) { b.p = p.u + i * B2; b.es = p.eo; }
+    else if (p.sym == BT_SYM_GENERAL) { b.p = p.l + j * B2; b.es = p.eo; }
+    else { b.p = p.u + j * B2; b.es = p.eo; b.op = BT_OP_C; b.f = p.sym == BT_SYM_ANTIHERMITIAN ? -1.0 : 1.0; }
+    return b;
+  };
+  auto W = [&](zd* p, long long es) { return ws_blk(p, es); };
+
+  // ---- a1 (W): M~ = I - V P^R ----
+  const PT pr = mkP(PR);
+  for (int i = 0; i < N; ++i) {
+    zd* md = c->Md + i * B2;
+    BT_TRY(prod(c, Ec, -1.0, Vb(i, i), Pb(pr, i, i), 0.0, md, NB2));
+    if (i > 0) BT_TRY(prod(c, Ec, -1.0, Vb(i, i - 1), Pb(pr, i - 1, i), 1.0, md, NB2));
+    if (i + 1 < N) BT_TRY(prod(c, Ec, -1.0, Vb(i, i + 1), Pb(pr, i + 1, i), 1.0, md, NB2));
+    BT_TRY(bt::shift_diag(st, bs, Ec, md, NB2, 1.0));
+    if (i + 1 < N) {
+      zd* mu = c->Mu + i * B2;
+      zd* ml = c->Ml + i * B2;
+      BT_TRY(prod(c, Ec, -1.0, Vb(i, i), Pb(pr, i, i + 1), 0.0, mu, N1B2));
+      BT_TRY(prod(c, Ec, -1.0, Vb(i, i + 1), Pb(pr, i + 1, i + 1), 1.0, mu, N1B2));
+      BT_TRY(prod(c, Ec, -1.0, Vb(i + 1, i), Pb(pr, i, i), 0.0, ml, N1B2));
+      BT_TRY(prod(c, Ec, -1.0, Vb(i + 1, i + 1), Pb(pr, i + 1, i), 1.0, ml, N1B2));
+    }
+  }
+  // ---- a1 (W): B^<> = (V P^<>) V^H, diagonal and upper blocks ----
+  const bool needL = oL && (oL->diag || oL->upper);
+  const bool needG = oG && (oG->diag || oG->upper);
+  const bool need[2] = {needL, needG};
+  const PT plg[2] = {mkP(PL), mkP(PG)};
+  zd* Bd[2] = {c->BdL, c->BdG};
+  zd* Bu[2] = {c->BuL, c->BuG};
+  for (int w = 0; w < 2; ++w) {
+    if (!need[w]) continue;
+    const PT& p = plg[w];
+    for (int i = 0; i < N; ++i) {  // T = V P^<>
+      zd* td = c->Td + i * B2;
+      BT_TRY(prod(c, Ec, 1.0, Vb(i, i), Pb(p, i, i), 0.0, td, NB2));
+      if (i > 0) BT_TRY(prod(c, Ec, 1.0, Vb(i, i - 1), Pb(p, i - 1, i), 1.0, td, NB2));
+      if (i + 1 < N) BT_TRY(prod(c, Ec, 1.0, Vb(i, i + 1), Pb(p, i + 1, i), 1.0, td, NB2));
+      if (i + 1 < N) {
+        zd* tu = c->Tu + i * B2;
+        zd* tl = c->Tl + i * B2;
+        BT_TRY(prod(c, Ec, 1.0, Vb(i, i), Pb(p, i, i + 1), 0.0, tu, N1B2));
+        BT_TRY(prod(c, Ec, 1.0, Vb(i, i + 1), Pb(p, i + 1, i + 1), 1.0, tu, N1B2));
+        BT_TRY(prod(c, Ec, 1.0, Vb(i + 1, i), Pb(p, i, i), 0.0, tl, N1B2));
+        BT_TRY(prod(c, Ec, 1.0, Vb(i + 1, i + 1), Pb(p, i + 1, i), 1.0, tl, N1B2));
+      }
+    }
+    for (int i = 0; i < N; ++i) {  // B = T V^H
+      zd* bd = Bd[w] + i * B2;
+      BT_TRY(prod(c, Ec, 1.0, W(c->Td + i * B2, NB2), Vh(i, i), 0.0, bd, NB2));
+      if (i > 0) BT_TRY(prod(c, Ec, 1.0, W(c->Tl + (i - 1) * B2, N1B2), Vh(i, i - 1), 1.0, bd, NB2));
+      if (i + 1 < N) BT_TRY(prod(c, Ec, 1.0, W(c->Tu + i * B2, N1B2), Vh(i, i + 1), 1.0, bd, NB2));
+      if (i + 1 < N) {
+        zd* bu = Bu[w] + i * B2;
+        BT_TRY(prod(c, Ec, 1.0, W(c->Td + i * B2, NB2), Vh(i + 1, i), 0.0, bu, N1B2));
+        BT_TRY(prod(c, Ec, 1.0, W(c->Tu + i * B2, N1B2), Vh(i + 1, i + 1), 1.0, bu, N1B2));
+      }
+    }
+  }
+  // ---- a3 + a4 ----
+  Sweep sw;
+  sw.c = c;
+  sw.Ec = Ec;
+  sw.N = N;
+  sw.bs = bs;
+  sw.B2 = B2;
+  sw.needL = needL;
+  sw.needG = needG;
+  sw.needRlower = true;
+  sw.keepRoff = true;
+  sw.has_boff = N > 1;
+  sw.oLu = oL && oL->upper ? static_cast<zd*>(oL->upper) + e0 * N1B2 : nullptr;
+  sw.oGu = oG && oG->upper ? static_cast<zd*>(oG->upper) + e0 * N1B2 : nullptr;
+  sw.oes_u = N1B2;
+  sw.X2u = N > 2 ? c->X2u : nullptr;
+  sw.X2l = N > 2 ? c->X2l : nullptr;
+  sw.asmM = [&](int i, zd* dst, long long es) {
+    return bt::write_blocks(st, bs, 1, Ec, c->Md + i * B2, 0, NB2, dst, 0, es, 0);
+  };
+  sw.asmB = [&](int i, int w, zd* dst, long long es) {
+    return bt::write_blocks(st, bs, 1, Ec, Bd[w] + i * B2, 0, NB2, dst, 0, es, 0);
+  };
+  sw.Mu = [&](int i) { return ws_blk(c->Mu + i * B2, N1B2); };
+  sw.Ml = [&](int i) { return ws_blk(c->Ml + i * B2, N1B2); };
+  sw.Bu = [&](int i, int w) { return ws_blk(Bu[w] + i * B2, N1B2); };
+  BT_TRY(run_sweep(sw, status));
+
+  // ---- W^R = X^R V on the selected blocks ----
+  if (oR && (oR->diag || oR->upper || oR->lower)) {
+    auto XRd = [&](int i) { return W(c->xR + i * B2, NB2); };
+    auto XRu = [&](int i) { return W(c->XRu + i * B2, N1B2); };
+    auto XRl = [&](int i) { return W(c->XRl + i * B2, N1B2); };
+    auto X2u = [&](int i) { return W(c->X2u + i * B2, N2B2); };
+    auto X2l = [&](int i) { return W(c->X2l + i * B2, N2B2); };
+    for (int i = 0; i < N; ++i) {
+      if (oR->diag) {
+        zd* o = static_cast<zd*>(oR->diag) + (e0 * N + i) * B2;
+        BT_TRY(prod(c, Ec, 1.0, XRd(i), Vb(i, i), 0.0, o, NB2));
+        if (i > 0) BT_TRY(prod(c, Ec, 1.0, XRl(i - 1), Vb(i - 1, i), 1.0, o, NB2));
+        if (i + 1 < N) BT_TRY(prod(c, Ec, 1.0, XRu(i), Vb(i + 1, i), 1.0, o, NB2));
+      }
+      if (i + 1 < N && oR->upper) {
+        zd* o = static_cast<zd*>(oR->upper) + (e0 * (N - 1) + i) * B2;
+        BT_TRY(prod(c, Ec, 1.0, XRd(i), Vb(i, i + 1), 0.0, o, N1B2));
+        BT_TRY(prod(c, Ec, 1.0, XRu(i), Vb(i + 1, i + 1), 1.0, o, N1B2));
+        if (i + 2 < N) BT_TRY(prod(c, Ec, 1.0, X2u(i), Vb(i + 2, i + 1), 1.0, o, N1B2));
+      }
+      if (i + 1 < N && oR->lower) {
+        zd* o = static_cast<zd*>(oR->lower) + (e0 * (N - 1) + i) * B2;
+        BT_TRY(prod(c, Ec, 1.0, XRl(i), Vb(i, i), 0.0, o, N1B2));
+        BT_TRY(prod(c, Ec, 1.0, XRd(i + 1), Vb(i + 1, i), 1.0, o, N1B2));
+        if (i > 0) BT_TRY(prod(c, Ec, 1.0, X2l(i - 1), Vb(i - 1, i), 1.0, o, N1B2));
+      }
+    }
+  }
+  // ---- a5 ----
+  if (oL && oL->diag)
+    BT_TRY(bt::write_blocks(st, bs, N, Ec, c->xL, B2, NB2, static_cast<zd*>(oL->diag) + e0 * NB2, B2, NB2, d.symmetrize ? 1 : 0));
+  if (oG && oG->diag)
+    BT_TRY(bt::write_blocks(st, bs, N, Ec, c->xG, B2, NB2, static_cast<zd*>(oG->diag) + e0 * NB2, B2, NB2, d.symmetrize ? 1 : 0));
+  (void)status;
+  return BT_OK;
+}
+
+bt_status check_solve_args(bt_ctx* c, const bt_bt* H, const bt_bt* S, const bt_bt* sR, const bt_bt* sL, const bt_bt* sG,
+                           const double* E, int n, const bt_bt_out* oR, const bt_bt_out* oL, const bt_bt_out* oG,
+                           const int* status) {
+  std::string why;
+  auto fail = [&](const std::string& m) { c->err = m; return BT_ERR_INVALID_ARG; };
+  if (n < 0) return fail("n_energies < 0");
+  if (n > 0 && !E) return fail("energies_host is NULL");
+  if (n > 0 && !status) return fail("status array is NULL");
+  bt_status s;
+  if ((s = validate_operand(H, true, false, c->d.system == BT_SYS_G ? "H" : "V", &why)) != BT_OK) return fail(why);
+  if (c->d.nb > 1 && !H->upper) return fail("H/V upper blocks are required for nb > 1");
+  if (c->d.system == BT_SYS_G) {
+    if ((s = validate_operand(S, false, false, "S", &why)) != BT_OK) return fail(why);
+    if ((s = validate_operand(sR, false, true, "sigR", &why)) != BT_OK) return fail(why);
+    if ((s = validate_operand(sL, false, true, "sigL", &why)) != BT_OK) return fail(why);
+    if ((s = validate_operand(sG, false, true, "sigG", &why)) != BT_OK) return fail(why);
+    if (sL && sL->upper && sL->symmetry != BT_SYM_ANTIHERMITIAN) return fail("sigL off-diagonal blocks must be anti-Hermitian");
+    if (sG && sG->upper && sG->symmetry != BT_SYM_ANTIHERMITIAN) return fail("sigG off-diagonal blocks must be anti-Hermitian");
+  } else {
+    if (S) return fail("S must be NULL for the W system");
+    if (H->per_energy) return fail("V must be shared across energies");
+    if (H->symmetry != BT_SYM_HERMITIAN) return fail("V must be Hermitian");
+    if ((s = validate_operand(sR, true, false, "P^R", &why)) != BT_OK) return fail(why);
+    if (c->d.nb > 1 && (!sR->upper || (sR->symmetry == BT_SYM_GENERAL && !sR->lower))) return fail("P^R off-diagonal blocks are required");
+    if ((s = validate_operand(sL, false, false, "P^<", &why)) != BT_OK) return fail(why);
+    if ((s = validate_operand(sG, false, false, "P^>", &why)) != BT_OK) return fail(why);
+    if ((oL && (oL->diag || oL->upper) && !sL) || (oG && (oG->diag || oG->upper) && !sG))
+      return fail("W^<> outputs need P^<>");
+    if (c->d.nb > 1 && ((sL && (!sL->upper || sL->symmetry != BT_SYM_ANTIHERMITIAN)) ||
+                        (sG && (!sG->upper || sG->symmetry != BT_SYM_ANTIHERMITIAN))))
+      return fail("P^<> need anti-Hermitian off-diagonal blocks");
+  }
+  (void)oR;
+  (void)s;
+  return BT_OK;
+}
+
+}  // namespace
+
+extern "C" bt_status bt_selinv_solve(bt_ctx* c, const bt_bt* H, const bt_bt* S, const bt_bt* sigR, const bt_bt* sigL,
+                                     const bt_bt* sigG, const double* energies_host, int n_energies,
+                                     const bt_bt_out* outR, const bt_bt_out* outL, const bt_bt_out* outG,
+                                     int* status_device) {
+  if (!c) return BT_ERR_INVALID_ARG;
+  c->err.clear();
+  BT_TRY(check_solve_args(c, H, S, sigR, sigL, sigG, energies_host, n_energies, outR, outL, outG, status_device));
+  if (n_energies == 0) return BT_OK;
+  c->flops = 0.0;
+  const long long launches0 = bt::launches_total();
+  struct LaunchTally {  // attributes this call's launches to the context on every return path
+    bt_ctx* c;
+    long long l0;
+    ~LaunchTally() { c->stats.kernel_launches += bt::launches_total() - l0; }
+  } tally{c, launches0};
+  if (cudaMemsetAsync(status_device, 0, sizeof(int) * (size_t)n_energies, c->st) != cudaSuccess)
+    return set_err(c, BT_ERR_CUDA, "cudaMemsetAsync(status) failed");
+  const int Emax = c->d.max_energies;
+  for (long long e0 = 0; e0 < n_energies; e0 += Emax) {
+    const int Ec = (int)std::min<long long>(Emax, n_energies - e0);
+    // stage this chunk's energies (the previous chunk's copy may still be in flight)
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return set_err(c, BT_ERR_CUDA, "stream error");
+    std::memcpy(c->h_E, energies_host + e0, sizeof(double) * Ec);
+    if (cudaMemcpyAsync(c->Edev, c->h_E, sizeof(double) * Ec, cudaMemcpyHostToDevice, c->st) != cudaSuccess)
+      return set_err(c, BT_ERR_CUDA, "energy upload failed");
+    bt_status s;
+    if (c->d.system == BT_SYS_G)
+      s = solve_chunk_g(c, H, S, sigR, sigL, sigG, e0, Ec, outR, outL, outG, status_device + e0);
+    else
+      s = solve_chunk_w(c, H, sigR, sigL, sigG, e0, Ec, outR, outL, outG, status_device + e0);
+    if (s != BT_OK) {
+      if (c->err.empty()) c->err = "a kernel launch failed";
+      return s;
+    }
+  }
+  c->stats.solves += 1;
+  c->stats.energies += n_energies;
+  c->stats.flops_model = c->flops;
+  return BT_OK;
+}
+
+// ======================================================================================
+// Host-buffer entry point: stages inputs chunk by chunk, runs the device path, copies back.
+// ======================================================================================
+namespace {
+
+struct StagedOperand {
+  bt_bt dev{};
+  const bt_bt* host = nullptr;
+  long long dext = 0, oext = 0;  // per-energy element extents (or whole operand when shared)
+  zd *d = nullptr, *u = nullptr, *l = nullptr;
+};
+
+}  // namespace
+
+extern "C" bt_status bt_selinv_solve_host(bt_ctx* c, const bt_bt* H, const bt_bt* S, const bt_bt* sigR,
+                                          const bt_bt* sigL, const bt_bt* sigG, const double* energies_host,
+                                          int n_energies, const bt_bt_out* outR, const bt_bt_out* outL,
+                                          const bt_bt_out* outG, int* status_host) {
+  if (!c) return BT_ERR_INVALID_ARG;
+  c->err.clear();
+  BT_TRY(check_solve_args(c, H, S, sigR, sigL, sigG, energies_host, n_energies, outR, outL, outG, status_host));
+  if (n_energies == 0) return BT_OK;
+  const int N = c->d.nb, bs = c->d.bs, Emax = c->d.max_energies;
+  const long long B2 = (long long)bs * bs, NB2 = N * B2, N1B2 = (long long)(N > 1 ? N - 1 : 0) * B2;
+  const bt_bt* ins[5] = {H, S, sigR, sigL, sigG};
+  StagedOperand so[5];
+  // bytes: shared operands whole, per-energy operands for one chunk
+  size_t need = 0;
+  auto elems_d = [&](const bt_bt* b) { return diag_extent(*b, N, bs); };
+  for (int k = 0; k < 5; ++k) {
+    if (!ins[k]) continue;
+    so[k].host = ins[k];
+    so[k].dext = elems_d(ins[k]);
+    so[k].oext = N1B2;
+    const long long mult = ins[k]->per_energy ? Emax : 1;
+    if (ins[k]->diag) need += al(sizeof(zd) * so[k].dext * mult);
+    if (ins[k]->upper) need += al(sizeof(zd) * so[k].oext * mult);
+    if (ins[k]->lower) need += al(sizeof(zd) * so[k].oext * mult);
+  }
+  const bt_bt_out* outs[3] = {outR, outL, outG};
+  for (int k = 0; k < 3; ++k) {
+    if (!outs[k]) continue;
+    if (outs[k]->diag) need += al(sizeof(zd) * NB2 * Emax);
+    if (outs[k]->upper) need += al(sizeof(zd) * N1B2 * Emax);
+    if (outs[k]->lower) need += al(sizeof(zd) * N1B2 * Emax);
+  }
+  need += al(sizeof(int) * Emax);
+  if (c->stage_bytes < need) {
+    if (c->stage) cudaFree(c->stage);
+    c->stage = nullptr;
+    c->stage_bytes = 0;
+    if (cudaMalloc(&c->stage, need) != cudaSuccess) { cudaGetLastError(); return set_err(c, BT_ERR_OOM, "staging allocation failed"); }
+    c->stage_bytes = need;
+  }
+  Carver cv(c->stage);
+  for (int k = 0; k < 5; ++k) {
+    if (!ins[k]) continue;
+    const long long mult = ins[k]->per_energy ? Emax : 1;
+    so[k].dev = *ins[k];
+    if (ins[k]->diag) { so[k].d = cv.take<zd>(so[k].dext * mult); so[k].dev.diag = so[k].d; }
+    if (ins[k]->upper) { so[k].u = cv.take<zd>(so[k].oext * mult); so[k].dev.upper = so[k].u; }
+    if (ins[k]->lower) { so[k].l = cv.take<zd>(so[k].oext * mult); so[k].dev.lower = so[k].l; }
+  }
+  bt_bt_out dout[3] = {};
+  for (int k = 0; k < 3; ++k) {
+    if (!outs[k]) continue;
+    if (outs[k]->diag) dout[k].diag = cv.take<zd>(NB2 * Emax);
+    if (outs[k]->upper) dout[k].upper = cv.take<zd>(N1B2 * Emax);
+    if (outs[k]->lower) dout[k].lower = cv.take<zd>(N1B2 * Emax);
+  }
+  int* dstatus = cv.take<int>(Emax);
+  cudaStream_t st = c->st;
+  auto h2d = [&](void* dst, const void* src, size_t bytes) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) == cudaSuccess;
+  };
+  auto d2h = [&](void* dst, const void* src, size_t bytes) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+  };
+  // shared operands once
+  for (int k = 0; k < 5; ++k) {
+    if (!ins[k] || ins[k]->per_energy) continue;
+    if (so[k].d && !h2d(so[k].d, ins[k]->diag, sizeof(zd) * so[k].dext)) return set_err(c, BT_ERR_CUDA, "H2D failed");
+    if (so[k].u && !h2d(so[k].u, ins[k]->upper, sizeof(zd) * so[k].oext)) return set_err(c, BT_ERR_CUDA, "H2D failed");
+    if (so[k].l && !h2d(so[k].l, ins[k]->lower, sizeof(zd) * so[k].oext)) return set_err(c, BT_ERR_CUDA, "H2D failed");
+  }
+  for (long long e0 = 0; e0 < n_energies; e0 += Emax) {
+    const int Ec = (int)std::min<long long>(Emax, n_energies - e0);
+    for (int k = 0; k < 5; ++k) {
+      if (!ins[k] || !ins[k]->per_energy) continue;
+      const zd* hd = static_cast<const zd*>(ins[k]->diag);
+      const zd* hu = static_cast<const zd*>(ins[k]->upper);
+      const zd* hl = static_cast<const zd*>(ins[k]->lower);
+      if (so[k].d && !h2d(so[k].d, hd + so[k].dext * e0, sizeof(zd) * so[k].dext * Ec)) return set_err(c, BT_ERR_CUDA, "H2D failed");
+      if (so[k].u && !h2d(so[k].u, hu + so[k].oext * e0, sizeof(zd) * so[k].oext * Ec)) return set_err(c, BT_ERR_CUDA, "H2D failed");
+      if (so[k].l && !h2d(so[k].l, hl + so[k].oext * e0, sizeof(zd) * so[k].oext * Ec)) return set_err(c, BT_ERR_CUDA, "H2D failed");
+    }
+    bt_status s = bt_selinv_solve(c, H ? &so[0].dev : nullptr, S ? &so[1].dev : nullptr, sigR ? &so[2].dev : nullptr,
+                                  sigL ? &so[3].dev : nullptr, sigG ? &so[4].dev : nullptr, energies_host + e0, Ec,
+                                  outR ? &dout[0] : nullptr, outL ? &dout[1] : nullptr, outG ? &dout[2] : nullptr,
+                                  dstatus);
+    if (s != BT_OK) return s;
+    for (int k = 0; k < 3; ++k) {
+      if (!outs[k]) continue;
+      if (outs[k]->diag && !d2h(static_cast<zd*>(outs[k]->diag) + NB2 * e0, dout[k].diag, sizeof(zd) * NB2 * Ec)) return set_err(c, BT_ERR_CUDA, "D2H failed");
+      if (outs[k]->upper && !d2h(static_cast<zd*>(outs[k]->upper) + N1B2 * e0, dout[k].upper, sizeof(zd) * N1B2 * Ec)) return set_err(c, BT_ERR_CUDA, "D2H failed");
+      if (outs[k]->lower && !d2h(static_cast<zd*>(outs[k]->lower) + N1B2 * e0, dout[k].lower, sizeof(zd) * N1B2 * Ec)) return set_err(c, BT_ERR_CUDA, "D2H failed");
+    }
+    if (!d2h(status_host + e0, dstatus, sizeof(int) * Ec)) return set_err(c, BT_ERR_CUDA, "D2H failed");
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) return set_err(c, BT_ERR_CUDA, "stream error");
+  return BT_OK;
+}

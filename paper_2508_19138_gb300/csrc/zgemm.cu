@@ -1,0 +1,176 @@
+// Batched complex128 GEMM on the FP64 pipe (DFMA): the dense block products of the RGF
+// forward / backward passes (Sec. 3.2.2, Eq. 8-11) and of the decimation (Eq. 4).
+//
+// GB300 note: the FP64 pipe of this part issues about 2 DFMA per clock per SM (measured
+// ~1.2 TFLOP/s for the whole GPU; the FP64 mma.sync path measured ~1.05 TFLOP/s), so this
+// kernel is bound by FP64 issue, not by memory.  What matters is keeping every SM busy with
+// whole tiles: 32 x 32 output tiles divide the workload block sizes (32, 416 = 13 x 32,
+// 1024) without ragged waste, and the batch (energies x blocks) gives >= 152 CTAs.
+// Tiles are staged through shared memory with a register prefetch of the next k-slab.
+#include <atomic>
+
+#include "bt_common.cuh"
+
+namespace bt {
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
+
+namespace {
+
+constexpr int BM = 32, BN = 32, BK = 16;
+constexpr int NT = 256;  // 16 x 16 threads, 2 x 2 outputs each
+
+template <int OPA, int OPB>
+__global__ void __launch_bounds__(NT) zgemm_kernel(int m, int n, int k, zd alpha, const zd* __restrict__ A,
+                                                   int lda, long long sA, const zd* __restrict__ B, int ldb,
+                                                   long long sB, zd beta, zd* __restrict__ C, int ldc,
+                                                   long long sC, const int* __restrict__ active) {
+  const int bz = blockIdx.z;
+  if (active && active[bz] == 0) return;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  A += sA * bz;
+  B += sB * bz;
+  C += sC * bz;
+  __shared__ zd As[BK][BM + 1];
+  __shared__ zd Bs[BK][BN + 1];
+  const int t = threadIdx.x;
+  const int tx = t & 15, ty = t >> 4;
+
+  zd acc[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) acc[i][j] = zmake(0.0, 0.0);
+
+  zd ra[2], rb[2];  // prefetch registers: 2 elements of A and of B per thread per k-slab
+  auto load_a = [&](int k0) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      int e = t + NT * s;
+      int r, c;
+      if (OPA == BT_OP_N) { r = e >> 4; c = e & 15; } else { c = e >> 5; r = e & 31; }
+      int gr = m0 + r, gc = k0 + c;
+      zd v = zmake(0.0, 0.0);
+      if (gr < m && gc < k) {
+        if (OPA == BT_OP_N) v = A[(long long)gr * lda + gc];
+        else v = zconj(A[(long long)gc * lda + gr]);
+      }
+      ra[s] = v;
+    }
+  };
+  auto load_b = [&](int k0) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      int e = t + NT * s;
+      int r, c;
+      if (OPB == BT_OP_N) { r = e >> 5; c = e & 31; } else { c = e >> 4; r = e & 15; }
+      int gr = k0 + r, gc = n0 + c;
+      zd v = zmake(0.0, 0.0);
+      if (gr < k && gc < n) {
+        if (OPB == BT_OP_N) v = B[(long long)gr * ldb + gc];
+        else v = zconj(B[(long long)gc * ldb + gr]);
+      }
+      rb[s] = v;
+    }
+  };
+  auto store_tiles = [&]() {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      int e = t + NT * s;
+      int r, c;
+      if (OPA == BT_OP_N) { r = e >> 4; c = e & 15; } else { c = e >> 5; r = e & 31; }
+      As[c][r] = ra[s];
+      if (OPB == BT_OP_N) { r = e >> 5; c = e & 31; } else { c = e >> 4; r = e & 15; }
+      Bs[r][c] = rb[s];
+    }
+  };
+
+  load_a(0);
+  load_b(0);
+  for (int k0 = 0; k0 < k; k0 += BK) {
+    __syncthreads();
+    store_tiles();
+    __syncthreads();
+    if (k0 + BK < k) {
+      load_a(k0 + BK);
+      load_b(k0 + BK);
+    }
+#pragma unroll 4
+    for (int kk = 0; kk < BK; ++kk) {
+      zd a0 = As[kk][ty], a1 = As[kk][ty + 16];
+      zd b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
+      zfma(acc[0][0], a0, b0);
+      zfma(acc[0][1], a0, b1);
+      zfma(acc[1][0], a1, b0);
+      zfma(acc[1][1], a1, b1);
+    }
+  }
+  const bool beta_zero = (beta.x == 0.0 && beta.y == 0.0);
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    int gr = m0 + ty + 16 * i;
+    if (gr >= m) continue;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      int gc = n0 + tx + 16 * j;
+      if (gc >= n) continue;
+      zd* cp = C + (long long)gr * ldc + gc;
+      zd v = zmul(alpha, acc[i][j]);
+      if (!beta_zero) v = zadd(v, zmul(beta, *cp));
+      *cp = v;
+    }
+  }
+}
+
+}  // namespace
+
+bt_status zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A, Operand B, zd beta, zd* C,
+                int ldc, long long strideC, int batch, const int* active) {
+  if (m < 0 || n < 0 || k < 0 || batch < 0) return BT_ERR_INVALID_ARG;
+  if (m == 0 || n == 0 || batch == 0) return BT_OK;
+  if (batch > 65535) {
+    // split very large batches into several launches (grid z limit)
+    for (int b0 = 0; b0 < batch; b0 += 65535) {
+      int nbatch = batch - b0 < 65535 ? batch - b0 : 65535;
+      Operand a = A, b = B;
+      a.p += A.stride * b0;
+      b.p += B.stride * b0;
+      BT_TRY(zgemm(st, m, n, k, alpha, a, b, beta, C + strideC * b0, ldc, strideC, nbatch,
+                   active ? active + b0 : nullptr));
+    }
+    return BT_OK;
+  }
+  dim3 grid((n + BN - 1) / BN, (m + BM - 1) / BM, batch);
+  if (A.op == BT_OP_N && B.op == BT_OP_N)
+    zgemm_kernel<BT_OP_N, BT_OP_N><<<grid, NT, 0, st>>>(m, n, k, alpha, A.p, A.ld, A.stride, B.p, B.ld, B.stride, beta, C, ldc, strideC, active);
+  else if (A.op == BT_OP_N && B.op == BT_OP_C)
+    zgemm_kernel<BT_OP_N, BT_OP_C><<<grid, NT, 0, st>>>(m, n, k, alpha, A.p, A.ld, A.stride, B.p, B.ld, B.stride, beta, C, ldc, strideC, active);
+  else if (A.op == BT_OP_C && B.op == BT_OP_N)
+    zgemm_kernel<BT_OP_C, BT_OP_N><<<grid, NT, 0, st>>>(m, n, k, alpha, A.p, A.ld, A.stride, B.p, B.ld, B.stride, beta, C, ldc, strideC, active);
+  else
+    zgemm_kernel<BT_OP_C, BT_OP_C><<<grid, NT, 0, st>>>(m, n, k, alpha, A.p, A.ld, A.stride, B.p, B.ld, B.stride, beta, C, ldc, strideC, active);
+  count_launch();
+  BT_CUDA_TRY(cudaGetLastError());
+  return BT_OK;
+}
+
+}  // namespace bt
+
+extern "C" bt_status bt_zgemm_batched(int m, int n, int k, double alpha_re, double alpha_im, const void* A, int lda,
+                                      long long strideA, int opA, const void* B, int ldb, long long strideB, int opB,
+                                      double beta_re, double beta_im, void* C, int ldc, long long strideC, int batch,
+                                      void* stream) {
+  if ((opA != BT_OP_N && opA != BT_OP_C) || (opB != BT_OP_N && opB != BT_OP_C)) return BT_ERR_INVALID_ARG;
+  if (m < 0 || n < 0 || k < 0 || batch < 0) return BT_ERR_INVALID_ARG;
+  if (m > 0 && n > 0 && batch > 0 && (!C || (k > 0 && (!A || !B)))) return BT_ERR_INVALID_ARG;
+  int rowsA = opA == BT_OP_N ? k : m;  // minimal leading dimensions
+  int rowsB = opB == BT_OP_N ? n : k;
+  if (lda < (rowsA > 1 ? rowsA : 1) || ldb < (rowsB > 1 ? rowsB : 1) || ldc < (n > 1 ? n : 1))
+    return BT_ERR_INVALID_ARG;
+  bt::Operand a{static_cast<const zd*>(A), lda, strideA, opA};
+  bt::Operand b{static_cast<const zd*>(B), ldb, strideB, opB};
+  return bt::zgemm(static_cast<cudaStream_t>(stream), m, n, k, zmake(alpha_re, alpha_im), a, b,
+                   zmake(beta_re, beta_im), static_cast<zd*>(C), ldc, strideC, batch, nullptr);
+}
