@@ -105,7 +105,7 @@ def test_decimation_matches_oracle(pkg, bs):
     import torch
     rng = np.random.default_rng(bs)
     batch = 3
-    ms, ns, nps, refs, its = [], [], [], [], []
+    ms, ns, nps, refs, its, disc = [], [], [], [], [], []
     for b in range(batch):
         h00 = cplx(rng, (bs, bs))
         h00 = (h00 + h00.conj().T) / 2 / np.sqrt(bs)
@@ -114,6 +114,9 @@ def test_decimation_matches_oracle(pkg, bs):
         m, n, n_ = z * np.eye(bs) - h00, -h01, -h01.conj().T
         x, it, ok = oracle.sancho_rubio(m, n, n_)
         assert ok
+        # FP64 sensitivity of the surface function at this z: the two oracle routes' disagreement
+        x_eig = oracle.surface_gf_eig(m, n, n_)
+        disc.append(np.linalg.norm(x - x_eig) / np.linalg.norm(x))
         ms.append(m); ns.append(n); nps.append(n_); refs.append(x); its.append(it)
     dm, dn, dnp = (torch.from_numpy(np.ascontiguousarray(np.stack(a))).cuda() for a in (ms, ns, nps))
     x = torch.empty_like(dm)
@@ -125,10 +128,11 @@ def test_decimation_matches_oracle(pkg, bs):
     got = x.cpu().numpy()
     gi = iters.cpu().numpy()
     for b in range(batch):
-        assert np.linalg.norm(got[b] - refs[b]) / np.linalg.norm(refs[b]) < 1e-10
+        tol = max(1e-10, 10 * disc[b])
+        assert np.linalg.norm(got[b] - refs[b]) / np.linalg.norm(refs[b]) < tol
         assert abs(int(gi[b]) - its[b]) <= 1
         sref = ns[b] @ refs[b] @ nps[b]
-        assert np.linalg.norm(sig.cpu().numpy()[b] - sref) / np.linalg.norm(sref) < 1e-10
+        assert np.linalg.norm(sig.cpu().numpy()[b] - sref) / np.linalg.norm(sref) < tol
 
 
 def test_decimation_iteration_cap_reports_not_converged(pkg):

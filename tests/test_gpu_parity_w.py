@@ -1,0 +1,72 @@
+"""Parity of the W (screened interaction) path with the dense oracle: M~ = I - V P^R and
+B^<> = V P^<> V^H assembled as block-tridiagonal products on the GPU, RGF sweep, W^R = X^R V
+on the selected blocks (needs X^R_{i,i+-2}), W^<> = X^<>."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+from gpu_util import TOL_FP64, TOL_SPLIT, block_errors
+
+pytestmark = pytest.mark.gpu
+
+
+def run_w(ws, idx, precision=0, max_energies=None, symmetrize=True):
+    import torch
+    import paper_2508_19138_gb300 as pkg
+    from paper_2508_19138_gb300 import BT, BTOut
+    nb, bs = ws.nb, ws.bs
+    E = len(idx)
+    parts = [ws.P_blocks(e) for e in idx]
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    PRd = t(np.stack([p[0] for p in parts]))
+    PRu = t(np.stack([p[1] for p in parts]))
+    PRl = t(np.stack([p[2] for p in parts]))
+    PLd = t(np.stack([p[3] for p in parts]))
+    PLu = t(np.stack([p[4] for p in parts]))
+    PGd = t(np.stack([p[5] for p in parts]))
+    PGu = t(np.stack([p[6] for p in parts]))
+    desc = pkg.make_desc(nb, bs, max_energies or E, system=pkg.BT_SYS_W, precision=precision,
+                         symmetrize=symmetrize, obc=False, eta=0.0)
+    ctx = pkg.bt_selinv_create(desc)
+    V = BT(t(ws.V_diag), t(ws.V_upper), None, pkg.BT_LAYOUT_BLOCKS, pkg.BT_SYM_HERMITIAN, False)
+    PR = BT(PRd, PRu, PRl, pkg.BT_LAYOUT_BLOCKS, pkg.BT_SYM_GENERAL, True)
+    PL = BT(PLd, PLu, None, pkg.BT_LAYOUT_BLOCKS, pkg.BT_SYM_ANTIHERMITIAN, True)
+    PG = BT(PGd, PGu, None, pkg.BT_LAYOUT_BLOCKS, pkg.BT_SYM_ANTIHERMITIAN, True)
+    mk = lambda *sh: torch.empty(sh, dtype=torch.complex128, device="cuda")
+    oR = BTOut(mk(E, nb, bs, bs), mk(E, nb - 1, bs, bs), mk(E, nb - 1, bs, bs))
+    oL = BTOut(mk(E, nb, bs, bs), mk(E, nb - 1, bs, bs), None)
+    oG = BTOut(mk(E, nb, bs, bs), mk(E, nb - 1, bs, bs), None)
+    status = torch.zeros(E, dtype=torch.int32, device="cuda")
+    pkg.bt_selinv_solve(ctx, V, None, PR, PL, PG, ws.energies[idx], oR, oL, oG, status)
+    torch.cuda.synchronize()
+    ctx.close()
+    out = {"R_diag": oR.diag, "R_upper": oR.upper, "R_lower": oR.lower, "L_diag": oL.diag, "L_upper": oL.upper,
+           "G_diag": oG.diag, "G_upper": oG.upper}
+    return {k: v.cpu().numpy() for k, v in out.items()}, status.cpu().numpy()
+
+
+@pytest.mark.parametrize("geom", [dict(nb=4, ny=2, nz=2, nx=8, r_cut=5.0),
+                                  dict(nb=5, ny=3, nz=2, nx=6, r_cut=4.0)])
+@pytest.mark.parametrize("precision,tol", [(0, TOL_FP64), (1, TOL_SPLIT)])
+def test_w_system_matches_dense(geom, precision, tol):
+    ws = synthetic.w_system(spacing=2.2, n_energies=5, **geom)
+    idx = np.arange(5)
+    res, status = run_w(ws, idx, precision=precision, max_energies=3)
+    assert (status == 0).all()
+    for j, e in enumerate(idx):
+        ref = oracle.solve_w(ws, e)
+        for k in ("R_diag", "R_upper", "R_lower", "L_diag", "L_upper", "G_diag", "G_upper"):
+            errs = block_errors(res[k][j], ref[k])
+            assert errs.max() < tol, (k, e, errs.max())
+
+
+def test_w_identity_on_gpu_output():
+    """W^> - W^< = W^R - W^A (exact for P^> - P^< = P^R - P^A, V Hermitian) on the diagonal."""
+    ws = synthetic.w_system(nb=4, ny=2, nz=2, nx=8, spacing=2.2, r_cut=5.0, n_energies=2)
+    res, status = run_w(ws, np.arange(2))
+    for j in range(2):
+        for i in range(ws.nb):
+            R = res["R_diag"][j, i]
+            lhs = res["G_diag"][j, i] - res["L_diag"][j, i]
+            assert np.abs(lhs - (R - R.conj().T)).max() <= 1e-11 * np.abs(R).max()
