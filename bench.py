@@ -41,10 +41,17 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["nanoribbon", "random8x32"], default="nanoribbon")
+    p.add_argument("--workload", choices=["nanoribbon", "random8x32", "w16x1024", "serving"], default="nanoribbon")
+    p.add_argument("--requests", type=int, default=24, help="serving: prefix of the request stream")
+    p.add_argument("--serving-max-energies", type=int, default=32, help="serving: cap per request (flagged)")
+    p.add_argument("--serving-budget-gb", type=float, default=150.0)
+    p.add_argument("--serving-active", type=int, default=4)
     p.add_argument("--energies-per-step", type=int, default=16)
     p.add_argument("--precision", choices=["fp64", "split"], default="fp64")
     p.add_argument("--slices", type=int, default=0)
+    p.add_argument("--split-scope", type=int, default=0,
+                   help="split: 0 = sweep products only, 1 = also inversion updates and decimation")
+    p.add_argument("--memo", action="store_true", help="contact memoization across steps of the same energies")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-blocks", type=int, default=10)
@@ -177,6 +184,7 @@ def run_ours(args):
     import torch
 
     import paper_2508_19138_gb300 as pkg
+    from paper_2508_19138_gb300 import replicas
     from paper_2508_19138_gb300.highlevel import GSolver
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -205,7 +213,8 @@ def run_ours(args):
     precision = pkg.BT_SPLIT if args.precision == "split" else pkg.BT_FP64
     stream = torch.cuda.Stream()
     solver = GSolver(sysg.nb, sysg.bs, eps, sysg.eta, sysg.kT, sysg.mu_left, sysg.mu_right, obc=True,
-                     precision=precision, split_slices=args.slices, stream=stream)
+                     precision=precision, split_slices=args.slices, stream=stream, split_scope=args.split_scope,
+                     obc_memo=args.memo, memo_capacity=nE if args.memo else 0)
     with torch.cuda.stream(stream):
         solver.set_inputs(sysg.H_diag, sysg.H_upper, sysg.sigR_diag, sysg.sigL_diag, sysg.sigG_diag)
         outs, status = solver.allocate_outputs(eps)
@@ -213,7 +222,7 @@ def run_ours(args):
     n_batches = max(1, nE // eps)
 
     def batch_range(step):
-        j = (rank * 7919 + step) % n_batches
+        j = replicas.batch_index(rank, step, n_batches)
         return j * eps, j * eps + eps
 
     def one_step(step):
@@ -240,10 +249,7 @@ def run_ours(args):
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
     bad = int((status.cpu().numpy() != 0).sum())
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms_max = float(t.item())
+    total_ms_max = replicas.max_over_ranks(total_ms, dist, device="cuda")
     value = eps * args.steps * world / (total_ms_max / 1e3)
     flops_step = st1["flops_model"]
     launches = int(st1["kernel_launches"] - st0["kernel_launches"])
@@ -286,6 +292,8 @@ def run_ours(args):
                 "data": "synthetic",
                 "config": {"workload": wl, "nb": sysg.nb, "bs": sysg.bs, "grid_energies": nE,
                            "energies_per_step": eps, "precision": args.precision,
+                           "split_scope": args.split_scope if args.precision == "split" else None,
+                           "contact_memo": bool(args.memo),
                            "l2": "per-step working set > 10 GB exceeds L2; no flush",
                            "parallelism": f"energy replicas x{world} (no collective)"},
                 "fp64_eq_tflops": flops_step / (statistics.median(step_ms) / 1e3) / 1e12,
@@ -330,8 +338,10 @@ def run_e2e(args, pkg, sysg, solver, eps, rank, world, barrier, dist):
     nE = len(sysg.energies)
     n_batches = max(1, nE // eps)
 
+    from paper_2508_19138_gb300 import replicas
+
     def step(s):
-        j = (rank * 7919 + s + 3) % n_batches
+        j = replicas.batch_index(rank, s + 3, n_batches)
         e0, e1 = j * eps, j * eps + eps
         bt_selinv_solve_host(solver.ctx, H, None, BT(sR[e0:e1], None, None, BT_LAYOUT_DIAGVEC, BT_SYM_GENERAL, True),
                              BT(sL[e0:e1], None, None, BT_LAYOUT_DIAGVEC, BT_SYM_ANTIHERMITIAN, True),
@@ -344,11 +354,7 @@ def run_e2e(args, pkg, sysg, solver, eps, rank, world, barrier, dist):
     for s in range(args.steps):
         step(1 + s)
     barrier()
-    dt = time.perf_counter() - t0
-    t = torch.tensor([dt], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    dt = float(t.item())
+    dt = replicas.max_over_ranks(time.perf_counter() - t0, dist, device="cuda")
     c16 = 16
     h2d = (Hd.numel() + Hu.numel()) * c16 + 3 * eps * nb * bs * c16 + 8 * eps
     d2h = (oR.diag.numel() + oR.upper.numel() + oR.lower.numel() + 2 * (oL.diag.numel() + oL.upper.numel())) * c16 \
@@ -357,10 +363,170 @@ def run_e2e(args, pkg, sysg, solver, eps, rank, world, barrier, dist):
             "d2h_bytes_per_step": int(d2h), "entry_point": "bt_selinv_solve_host (pinned host buffers)"}
 
 
+def run_w(args):
+    """W system (16 cells of 1024 atoms, 256 energies): P^R, P^<> per energy built on the device
+    from the seeded bases before the timed region; one step = one solve over a batch."""
+    import numpy as np
+    import torch
+
+    import paper_2508_19138_gb300 as pkg
+    import synthetic
+    from paper_2508_19138_gb300 import BT, BTOut
+
+    ws = synthetic.w_system_16x1024()
+    nb, bs, nE = ws.nb, ws.bs, len(ws.energies)
+    eps = min(args.energies_per_step, nE)
+    precision = pkg.BT_SPLIT if args.precision == "split" else pkg.BT_FP64
+    stream = torch.cuda.Stream()
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    with torch.cuda.stream(stream):
+        R0d, R0u, R1d, R1u, Gd, Gu = (t(x) for x in (ws.R0_diag, ws.R0_upper, ws.R1_diag, ws.R1_upper, ws.Gam_diag,
+                                                       ws.Gam_upper))
+        R0l, R1l, Gl = (x.transpose(1, 2).conj().contiguous() for x in (R0u, R1u, Gu))
+        n_batches = max(1, nE // eps)
+        batches = []
+        for j in range(min(n_batches, args.warmup + args.steps)):
+            idx = j + n_batches * np.arange(eps)
+            idx = idx[idx < nE]
+            r1 = torch.tensor(ws.r1[idx], device="cuda").view(-1, 1, 1, 1)
+            s1 = torch.tensor(1.0 + ws.g1[idx], device="cuda").view(-1, 1, 1, 1)
+            a = torch.tensor(ws.a[idx], device="cuda").view(-1, 1, 1, 1)
+            PRd = (R0d + r1 * R1d - 0.5j * s1 * Gd).contiguous()
+            PRu = (R0u + r1 * R1u - 0.5j * s1 * Gu).contiguous()
+            PRl = (R0l + r1 * R1l - 0.5j * s1 * Gl).contiguous()
+            PLd, PLu = (-1j * a * s1 * Gd).contiguous(), (-1j * a * s1 * Gu).contiguous()
+            PGd, PGu = (-1j * (1 + a) * s1 * Gd).contiguous(), (-1j * (1 + a) * s1 * Gu).contiguous()
+            batches.append((idx, BT(PRd, PRu, PRl, pkg.BT_LAYOUT_BLOCKS, pkg.BT_SYM_GENERAL, True),
+                            BT(PLd, PLu, None, pkg.BT_LAYOUT_BLOCKS, pkg.BT_SYM_ANTIHERMITIAN, True),
+                            BT(PGd, PGu, None, pkg.BT_LAYOUT_BLOCKS, pkg.BT_SYM_ANTIHERMITIAN, True)))
+        V = BT(t(ws.V_diag), t(ws.V_upper), None, pkg.BT_LAYOUT_BLOCKS, pkg.BT_SYM_HERMITIAN, False)
+        mk = lambda *sh: torch.empty(sh, dtype=torch.complex128, device="cuda")
+        oR = BTOut(mk(eps, nb, bs, bs), mk(eps, nb - 1, bs, bs), mk(eps, nb - 1, bs, bs))
+        oL = BTOut(mk(eps, nb, bs, bs), mk(eps, nb - 1, bs, bs))
+        oG = BTOut(mk(eps, nb, bs, bs), mk(eps, nb - 1, bs, bs))
+        status = torch.zeros(eps, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    ctx = pkg.bt_selinv_create(pkg.make_desc(nb, bs, eps, system=pkg.BT_SYS_W, precision=precision,
+                                             split_slices=args.slices, obc=False, eta=0.0), stream)
+
+    def step(j):
+        idx, PR, PL, PG = batches[j % len(batches)]
+        pkg.bt_selinv_solve(ctx, V, None, PR, PL, PG, ws.energies[idx], oR, oL, oG, status)
+
+    for w in range(args.warmup):
+        step(w)
+    torch.cuda.synchronize()
+    st0 = pkg.bt_selinv_get_stats(ctx)
+    clocks = ClockSampler(0)
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    for s in range(args.steps):
+        step(args.warmup + s)
+        ev[s + 1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    st1 = pkg.bt_selinv_get_stats(ctx)
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total = ev[0].elapsed_time(ev[-1])
+    line = {"metric": METRIC, "value": eps * args.steps / (total / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == pkg.BT_FP64 else "f64+bf16-sliced",
+            "data": "synthetic",
+            "config": {"workload": f"W system 16x1024 (2.2 A grid, r_cut 7.5 A), {nE} energies, {eps} per step",
+                       "precision": args.precision},
+            "fp64_eq_tflops": st1["flops_model"] / (statistics.median(step_ms) / 1e3) / 1e12,
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+            "nonzero_status": int((status.cpu().numpy() != 0).sum()), "clocks": clk,
+            "gpu_launches": int(st1["kernel_launches"] - st0["kernel_launches"])}
+    ctx.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serving(args):
+    """Serving stream prefix: Poisson arrivals submitted at their arrival times to bt_server;
+    reports p50 / p99 latency (submit -> done) and aggregate energy points/s."""
+    import numpy as np
+    import torch
+
+    import paper_2508_19138_gb300 as pkg
+    import synthetic
+    from paper_2508_19138_gb300 import BT, BTOut
+
+    precision = pkg.BT_SPLIT if args.precision == "split" else pkg.BT_FP64
+    stream = synthetic.serving_stream(n_requests=args.requests, rate_per_s=1.0)
+    reqs = []
+    for rq in stream:
+        nE = min(rq.n_energies, args.serving_max_energies)
+        s = synthetic.random_device(rq.seed, rq.nb, rq.bs, nE)
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        H = BT(t(s.H_diag), t(s.H_upper), None, pkg.BT_LAYOUT_BLOCKS, pkg.BT_SYM_HERMITIAN, False)
+        mk = lambda: torch.empty((nE, s.nb, s.bs), dtype=torch.complex128, device="cuda")
+        outs = [BTOut(mk(), layout=pkg.BT_LAYOUT_DIAGVEC) for _ in range(3)]
+        status = torch.full((nE,), -1, dtype=torch.int32, device="cuda")
+        reqs.append((rq, s, H, outs, status))
+    torch.cuda.synchronize()
+    budget = int(args.serving_budget_gb * (1 << 30))
+    srv = pkg.bt_server_create(budget, max_active=args.serving_active, max_energies_per_chunk=args.energies_per_step,
+                               precision=precision, split_slices=args.slices)
+
+    def submit(item):
+        rq, s, H, outs, status = item
+        return pkg.bt_server_submit(srv, s.nb, s.bs, H, s.energies, status, outs[0], outs[1], outs[2], eta=s.eta,
+                                    kT=s.kT, mu_left=s.mu_left, mu_right=s.mu_right)
+
+    # capacity calibration on the first request alone -> arrival rate 0.8 x capacity
+    t0 = time.perf_counter()
+    pkg.bt_server_wait(srv, submit(reqs[0]), 3600.0)
+    t_first = time.perf_counter() - t0
+    work = lambda it: it[1].nb * it[1].bs ** 3 * len(it[1].energies)
+    rate = 0.8 / (t_first * (np.mean([work(it) for it in reqs]) / work(reqs[0])))
+    rng = np.random.default_rng(synthetic.BASE_SEED + 4)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs) - 1))
+    pkg.bt_server_destroy(srv)
+    srv = pkg.bt_server_create(budget, max_active=args.serving_active, max_energies_per_chunk=args.energies_per_step,
+                               precision=precision, split_slices=args.slices)
+    clocks = ClockSampler(0)
+    clocks.start()
+    start = time.perf_counter()
+    tickets = []
+    for item, ta in zip(reqs[1:], arrivals):
+        now = time.perf_counter() - start
+        if ta > now:
+            time.sleep(ta - now)
+        tickets.append(submit(item))
+    for tk in tickets:
+        pkg.bt_server_wait(srv, tk, 7200.0)
+    wall = time.perf_counter() - start
+    clk = clocks.stop()
+    st = pkg.bt_server_get_stats(srv)
+    pkg.bt_server_destroy(srv)
+    bad = sum(int((it[4].cpu().numpy() != 0).sum()) for it in reqs[1:])
+    n_en = sum(len(it[1].energies) for it in reqs[1:])
+    line = {"metric": METRIC, "value": n_en / wall, "unit": UNIT, "n_gpus": 1, "steps": len(tickets), "warmup": 1,
+            "ms_per_step": wall / len(tickets) * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if precision == pkg.BT_FP64 else "f64+bf16-sliced", "data": "synthetic",
+            "config": {"workload": (f"serving stream prefix: requests 1..{len(reqs) - 1} of the 2000-request stream "
+                                    f"(b in 64..832, N_B 8..64), energies per request capped at "
+                                    f"{args.serving_max_energies} (flagged), Poisson arrivals at 0.8x capacity"),
+                       "arrival_rate_per_s": rate, "budget_gb": args.serving_budget_gb,
+                       "max_active": args.serving_active, "chunk": args.energies_per_step,
+                       "precision": args.precision},
+            "latency_s": {"p50": st["p50_latency_s"], "p99": st["p99_latency_s"], "mean": st["mean_latency_s"]},
+            "server": st, "nonzero_status": bad, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "w16x1024":
+        return run_w(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_ours(args)
 
 

@@ -82,11 +82,14 @@ typedef struct {
 } bt_bt;
 
 /* An output operand: [n_energies][nb][bs][bs] diagonal blocks, [n_energies][nb-1][bs][bs]
- * upper (i,i+1) and lower (i+1,i) blocks.  A NULL pointer means "do not write". */
+ * upper (i,i+1) and lower (i+1,i) blocks.  A NULL pointer means "do not write".
+ * layout BT_LAYOUT_DIAGVEC writes only the diagonal entries of the diagonal blocks,
+ * [n_energies][nb][bs] (densities / local DOS), and requires upper = lower = NULL. */
 typedef struct {
   void* diag;
   void* upper;
   void* lower;
+  int layout;
 } bt_bt_out;
 
 typedef struct {
@@ -108,6 +111,17 @@ typedef struct {
   double decim_tol;    /* decimation stops when max|a|,max|b| <= decim_tol * max|n| (<=0: 1e-14) */
   int decim_maxit;     /* decimation iteration cap (<= 0: 100)                                 */
   size_t hbm_budget_bytes; /* 0 = unlimited; otherwise the workspace must fit                  */
+  /* Contact memoization (Sec. 4.3): the surface functions of every solved energy are kept in
+   * the workspace (memo_capacity energies, oldest evicted first).  A later solve of the same
+   * energy starts the fixed-point iteration x <- (m - n x n')^{-1} (Eq. 5) from the kept value
+   * and runs at most memo_nfpi iterations; leads that do not converge within them (judged from
+   * the update ratio) fall back to decimation.  0 = off.                                        */
+  int obc_memo;
+  int memo_nfpi;           /* <= 0: 20                                                          */
+  int memo_capacity;       /* energies kept; <= 0: 4 * max_energies                             */
+  int split_scope;         /* BT_SPLIT only.  0: sliced products in the sweeps (the default
+                              split); 1: also the products inside the block inversions (the
+                              rank-kb updates), the decimation and the memoized fixed point    */
 } bt_selinv_desc;
 
 typedef struct bt_ctx bt_ctx;
@@ -120,6 +134,9 @@ typedef struct {
                                   product or inversion, actual decimation iterations)         */
   size_t workspace_bytes;
   long long kernel_launches;   /* kernels this context launched (all solves)                  */
+  long long lead_iterations;   /* decimation iterations summed over leads (all solves)        */
+  long long fpi_iterations;    /* memoized fixed-point iterations summed over leads           */
+  long long memo_hits;         /* energies whose contacts started from a kept surface function*/
 } bt_stats;
 
 /* Sizes of the workspace bt_selinv_create would allocate for `desc`. */
@@ -158,6 +175,59 @@ BT_API bt_status bt_selinv_get_stats(const bt_ctx* ctx, bt_stats* out);
 BT_API bt_status bt_selinv_destroy(bt_ctx* ctx);
 /* Text of the last error recorded on ctx (or of the last failed create when ctx is NULL). */
 BT_API const char* bt_selinv_last_error(const bt_ctx* ctx);
+
+/* ---------------------------------------------------------------------------------------
+ * Serving: solves of different device sizes arriving over time (G system).
+ *   - bt_server_create allocates ONE device arena of hbm_budget_bytes; each admitted request
+ *     borrows its workspace (as bt_selinv_workspace_bytes for a chunk of
+ *     max_energies_per_chunk energies) from it; requests are admitted in arrival order as soon
+ *     as their workspace fits, so memory freed by a finished request admits the next one;
+ *   - max_active worker threads, each with its own stream, run admitted requests concurrently
+ *     (continuous batching: new requests start while earlier ones are still on the GPU);
+ *   - a request's inputs / outputs are the caller's device buffers and must stay valid until
+ *     the request is done; results equal those of bt_selinv_solve with the same chunking.
+ * ------------------------------------------------------------------------------------- */
+typedef struct bt_server bt_server;
+
+typedef struct {
+  size_t hbm_budget_bytes;    /* arena size (device memory reserved at create)             */
+  int max_active;             /* concurrent requests, 1..64                                */
+  int max_energies_per_chunk; /* energies per batched launch of one request                */
+  int precision;              /* bt_precision                                              */
+  int split_slices;           /* BT_SPLIT slices (0 = default)                             */
+  int device;                 /* CUDA device ordinal                                       */
+} bt_server_desc;
+
+typedef struct {
+  int nb, bs, n_energies;
+  bt_bt H;                    /* shared across energies (device)                           */
+  bt_bt S, sigR, sigL, sigG;  /* optional: diag == NULL means absent                       */
+  const double* energies_host;/* [n_energies], copied by bt_server_submit                  */
+  double eta, kT, mu_left, mu_right;
+  int obc;                    /* Sancho-Rubio contacts from the edge blocks (nb >= 2)      */
+  bt_bt_out outR, outL, outG; /* device outputs (NULL pointers = not written)              */
+  int* status_device;         /* [n_energies]                                              */
+} bt_request;
+
+typedef struct {
+  long long submitted, completed, failed, rejected, energies_done, queued;
+  int active, peak_active;
+  double p50_latency_s, p99_latency_s, mean_latency_s; /* submit -> completion, completed  */
+  double busy_seconds;        /* first admission to last completion                        */
+  double energies_per_s;      /* energies_done / busy_seconds                              */
+  size_t peak_bytes;          /* largest arena occupancy                                   */
+} bt_server_stats;
+
+BT_API bt_status bt_server_create(const bt_server_desc* desc, bt_server** out);
+/* Queue a request; returns a ticket.  BT_ERR_BUDGET if its workspace can never fit. */
+BT_API bt_status bt_server_submit(bt_server* srv, const bt_request* req, long long* ticket);
+/* state: 0 queued, 1 running, 2 done, 3 failed (the return code is then the failure). */
+BT_API bt_status bt_server_poll(bt_server* srv, long long ticket, int* state);
+/* Block until the request is done or failed, or timeout_s passed (BT_ERR_TIMEOUT). */
+BT_API bt_status bt_server_wait(bt_server* srv, long long ticket, double timeout_s, int* state);
+BT_API bt_status bt_server_get_stats(bt_server* srv, bt_server_stats* out);
+/* Cancels queued requests, waits for running ones, frees the arena. */
+BT_API bt_status bt_server_destroy(bt_server* srv);
 
 /* ---------------------------------------------------------------------------------------
  * Building blocks, exported for callers that assemble their own sweeps (and for tests).

@@ -26,19 +26,21 @@ class bt_bt(C.Structure):
 
 
 class bt_bt_out(C.Structure):
-    _fields_ = [("diag", C.c_void_p), ("upper", C.c_void_p), ("lower", C.c_void_p)]
+    _fields_ = [("diag", C.c_void_p), ("upper", C.c_void_p), ("lower", C.c_void_p), ("layout", C.c_int)]
 
 
 class bt_selinv_desc(C.Structure):
     _fields_ = [("nb", C.c_int), ("bs", C.c_int), ("max_energies", C.c_int), ("system", C.c_int),
                 ("precision", C.c_int), ("split_slices", C.c_int), ("symmetrize", C.c_int), ("obc", C.c_int),
                 ("eta", C.c_double), ("kT", C.c_double), ("mu_left", C.c_double), ("mu_right", C.c_double),
-                ("decim_tol", C.c_double), ("decim_maxit", C.c_int), ("hbm_budget_bytes", C.c_size_t)]
+                ("decim_tol", C.c_double), ("decim_maxit", C.c_int), ("hbm_budget_bytes", C.c_size_t),
+                ("obc_memo", C.c_int), ("memo_nfpi", C.c_int), ("memo_capacity", C.c_int), ("split_scope", C.c_int)]
 
 
 class bt_stats(C.Structure):
     _fields_ = [("solves", C.c_longlong), ("energies", C.c_longlong), ("decim_iterations", C.c_longlong),
-                ("flops_model", C.c_double), ("workspace_bytes", C.c_size_t), ("kernel_launches", C.c_longlong)]
+                ("flops_model", C.c_double), ("workspace_bytes", C.c_size_t), ("kernel_launches", C.c_longlong),
+                ("lead_iterations", C.c_longlong), ("fpi_iterations", C.c_longlong), ("memo_hits", C.c_longlong)]
 
 
 # exported names and their ctypes signatures (restype is bt_status unless noted)
@@ -96,3 +98,35 @@ def load(build_if_missing: bool = False) -> C.CDLL:
         fn.restype = RESTYPES.get(name, C.c_int)
     _lib = lib
     return lib
+
+
+# ---- serving ----
+class bt_server_desc(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_active", C.c_int), ("max_energies_per_chunk", C.c_int),
+                ("precision", C.c_int), ("split_slices", C.c_int), ("device", C.c_int)]
+
+
+class bt_request(C.Structure):
+    _fields_ = [("nb", C.c_int), ("bs", C.c_int), ("n_energies", C.c_int), ("H", bt_bt), ("S", bt_bt),
+                ("sigR", bt_bt), ("sigL", bt_bt), ("sigG", bt_bt), ("energies_host", C.POINTER(C.c_double)),
+                ("eta", C.c_double), ("kT", C.c_double), ("mu_left", C.c_double), ("mu_right", C.c_double),
+                ("obc", C.c_int), ("outR", bt_bt_out), ("outL", bt_bt_out), ("outG", bt_bt_out),
+                ("status_device", C.c_void_p)]
+
+
+class bt_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_longlong), ("completed", C.c_longlong), ("failed", C.c_longlong),
+                ("rejected", C.c_longlong), ("energies_done", C.c_longlong), ("queued", C.c_longlong),
+                ("active", C.c_int), ("peak_active", C.c_int), ("p50_latency_s", C.c_double),
+                ("p99_latency_s", C.c_double), ("mean_latency_s", C.c_double), ("busy_seconds", C.c_double),
+                ("energies_per_s", C.c_double), ("peak_bytes", C.c_size_t)]
+
+
+SIGNATURES.update({
+    "bt_server_create": [C.POINTER(bt_server_desc), C.POINTER(_P)],
+    "bt_server_submit": [_P, C.POINTER(bt_request), C.POINTER(C.c_longlong)],
+    "bt_server_poll": [_P, C.c_longlong, C.POINTER(C.c_int)],
+    "bt_server_wait": [_P, C.c_longlong, C.c_double, C.POINTER(C.c_int)],
+    "bt_server_get_stats": [_P, C.POINTER(bt_server_stats)],
+    "bt_server_destroy": [_P],
+})

@@ -84,23 +84,26 @@ class BT:
 
 
 class BTOut:
-    """Output operand: [E][nb][bs][bs] diag, [E][nb-1][bs][bs] upper / lower (None = not written)."""
+    """Output operand: [E][nb][bs][bs] diag, [E][nb-1][bs][bs] upper / lower (None = not written);
+    layout BT_LAYOUT_DIAGVEC: diag is [E][nb][bs] (diagonal entries of the diagonal blocks)."""
 
-    def __init__(self, diag=None, upper=None, lower=None):
-        self.diag, self.upper, self.lower = diag, upper, lower
+    def __init__(self, diag=None, upper=None, lower=None, layout: int = N.BT_LAYOUT_BLOCKS):
+        self.diag, self.upper, self.lower, self.layout = diag, upper, lower, layout
 
     def struct(self, device="cuda") -> N.bt_bt_out:
         torch = _torch()
         return N.bt_bt_out(_ptr(self.diag, torch.complex128, device), _ptr(self.upper, torch.complex128, device),
-                           _ptr(self.lower, torch.complex128, device))
+                           _ptr(self.lower, torch.complex128, device), self.layout)
 
 
 def make_desc(nb: int, bs: int, max_energies: int, system: int = N.BT_SYS_G, precision: int = N.BT_FP64,
               split_slices: int = 0, symmetrize: bool = True, obc: bool = True, eta: float = 1e-6,
               kT: float = 0.025, mu_left: float = 0.0, mu_right: float = 0.0, decim_tol: float = 1e-14,
-              decim_maxit: int = 100, hbm_budget_bytes: int = 0) -> N.bt_selinv_desc:
+              decim_maxit: int = 100, hbm_budget_bytes: int = 0, obc_memo: bool = False, memo_nfpi: int = 0,
+              memo_capacity: int = 0, split_scope: int = 0) -> N.bt_selinv_desc:
     return N.bt_selinv_desc(nb, bs, max_energies, system, precision, split_slices, 1 if symmetrize else 0,
-                            1 if obc else 0, eta, kT, mu_left, mu_right, decim_tol, decim_maxit, hbm_budget_bytes)
+                            1 if obc else 0, eta, kT, mu_left, mu_right, decim_tol, decim_maxit, hbm_budget_bytes,
+                            1 if obc_memo else 0, memo_nfpi, memo_capacity, split_scope)
 
 
 class Context:

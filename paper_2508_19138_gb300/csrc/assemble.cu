@@ -128,6 +128,19 @@ __global__ void write_blocks_kernel(int bs, int nblk, const zd* __restrict__ src
   }
 }
 
+// Diagonal entries of nblk diagonal blocks per batch entry -> [nblk][bs] vectors; mode 1 keeps
+// the anti-Hermitian part of the block, whose diagonal is i Im(x).
+__global__ void write_diagvec_kernel(int bs, int nblk, const zd* __restrict__ src, long long s_blk, long long s_e,
+                                     zd* __restrict__ dst, long long d_blk, long long d_e, int mode) {
+  const int e = blockIdx.z, blk = blockIdx.y;
+  const zd* s = src + s_e * e + s_blk * blk;
+  zd* d = dst + d_e * e + d_blk * blk;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < bs; r += gridDim.x * blockDim.x) {
+    const zd v = s[(long long)r * bs + r];
+    d[r] = mode == 0 ? v : zmake(0.0, v.y);
+  }
+}
+
 __global__ void merge_status_kernel(int E, const int* __restrict__ info, int n_sources, long long src_stride,
                                     int* __restrict__ status) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -224,6 +237,17 @@ bt_status write_blocks(cudaStream_t st, int bs, int nblk, int batch, const zd* s
 bt_status shift_diag(cudaStream_t st, int bs, int batch, zd* X, long long sX, double v) {
   if (batch <= 0) return BT_OK;
   shift_diag_kernel<<<dim3((bs + 127) / 128, batch), 128, 0, st>>>(bs, X, sX, v); count_launch();
+  BT_CUDA_TRY(cudaGetLastError());
+  return BT_OK;
+}
+
+bt_status write_diagvec(cudaStream_t st, int bs, int nblk, int batch, const zd* src, long long s_blk, long long s_e,
+                        zd* dst, long long d_blk, long long d_e, int mode) {
+  if (batch <= 0 || nblk <= 0) return BT_OK;
+  if (nblk > 65535 || batch > 65535) return BT_ERR_INVALID_ARG;
+  dim3 g((bs + 255) / 256, nblk, batch);
+  write_diagvec_kernel<<<g, 256, 0, st>>>(bs, nblk, src, s_blk, s_e, dst, d_blk, d_e, mode);
+  count_launch();
   BT_CUDA_TRY(cudaGetLastError());
   return BT_OK;
 }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstdio>
+#include <string>
 #include "../../include/bt_selinv.h"
 
 typedef double2 zd;  // complex128: x = re, y = im
@@ -69,21 +70,46 @@ struct Operand {
 bt_status zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A, Operand B, zd beta,
                 zd* C, int ldc, long long strideC, int batch, const int* active);
 
+// Which kernel runs a complex product: FP64 DFMA (slices == 0) or the sliced bf16 tensor-core
+// product with `slices` slices per operand and its workspace.
+struct Engine {
+  int slices = 0;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+};
+
 // Split-precision (sliced bf16 tensor-core) variant of zgemm; see split_gemm.cu.
 size_t split_workspace_bytes(int m, int n, int k, int slices, int batch);
 bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A, Operand B, zd beta,
                       zd* C, int ldc, long long strideC, int batch, int slices, void* ws,
                       size_t ws_bytes, const int* active);
 
-// In-place batched inverse (Gauss-Jordan, partial pivoting).  info[b] |= error code.
+// C = alpha op(A) op(B) + beta C on the engine's kernel.
+bt_status gemm(const Engine& eng, cudaStream_t st, int m, int n, int k, zd alpha, Operand A, Operand B, zd beta,
+               zd* C, int ldc, long long strideC, int batch, const int* active);
+
+// In-place batched inverse (Gauss-Jordan, partial pivoting).  info[b] |= error code.  The
+// rank-kb updates of the blocked variant run on `eng` (FP64 unless given).
 size_t zinv_workspace_bytes(int n, int batch);
 bt_status zinv(cudaStream_t st, int n, zd* A, long long strideA, int batch, int* info, void* ws,
-               size_t ws_bytes, const int* active);
+               size_t ws_bytes, const int* active, const Engine* eng = nullptr);
 
 // Sancho-Rubio decimation for `batch` leads.
 size_t decimate_workspace_bytes(int bs, int batch);
 bt_status decimate(cudaStream_t st, int bs, int batch, const zd* m, const zd* n, const zd* np,
                    double tol, int maxit, zd* x, zd* sigma, int* iters, int* info, void* ws,
-                   size_t ws_bytes, int* iters_host_max, int* h_pinned);
+                   size_t ws_bytes, int* iters_host_max, int* h_pinned, const int* mask = nullptr,
+                   long long* lead_iterations = nullptr, const Engine* eng = nullptr);
+bt_status invert_mask(cudaStream_t st, int batch, const int* a, int* out);  // out = !a
+// Fixed-point iteration x <- (m - n x n')^{-1} (Eq. 5) from the given x for leads with run[l];
+// conv[l] = 1 where it converged to tol within nfpi iterations.
+bt_status fixed_point(cudaStream_t st, int bs, int batch, const zd* m, const zd* n, const zd* np, zd* x,
+                      const int* run, int* conv, int nfpi, double tol, int* info, void* ws, size_t ws_bytes,
+                      int* h_pinned, long long* lead_iterations, const Engine* eng = nullptr);
+
+// Context creation with an optional lent workspace (serving arena); see selinv.cu.
+bt_status ctx_create(const bt_selinv_desc* desc, void* cuda_stream, void* ext_ws, size_t ext_bytes, bt_ctx** out,
+                     std::string* err);
+size_t ctx_workspace_bytes(const bt_selinv_desc& d);
 
 }  // namespace bt

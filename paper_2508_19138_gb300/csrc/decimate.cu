@@ -11,6 +11,8 @@
 // reduction; converged leads drop out of every later launch through an `active` mask, and
 // the host stops as soon as the device-side count of active leads reaches zero.  The loop is
 // bounded by maxit; leads still active then get BT_ERR_NOT_CONVERGED (never a hang).
+#include <vector>
+
 #include "bt_common.cuh"
 
 namespace bt {
@@ -95,14 +97,68 @@ __global__ void sub2_kernel(long long bs2, int batch, const zd* __restrict__ t, 
   }
 }
 
-__global__ void init_kernel(int batch, int* active, int* iters, int* info) {
+// active[l] = mask[l] (all leads without a mask); state of masked-out leads is left alone
+__global__ void init_kernel(int batch, const int* __restrict__ mask, int* active, int* iters, int* info) {
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
-  if (l < batch) { active[l] = 1; iters[l] = 0; info[l] = 0; }
+  if (l >= batch) return;
+  const int on = mask ? (mask[l] != 0) : 1;
+  active[l] = on;
+  if (on) { iters[l] = 0; info[l] = 0; }
 }
 
 __global__ void finish_kernel(int batch, const int* active, int* info) {
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l < batch && active[l] != 0 && info[l] == 0) info[l] = BT_ERR_NOT_CONVERGED;
+}
+
+// dst[l] = src[l] for leads with mask[l] != 0 (all leads without a mask)
+__global__ void masked_copy_kernel(long long bs2, const zd* __restrict__ src, zd* __restrict__ dst,
+                                   const int* __restrict__ mask) {
+  const int l = blockIdx.y;
+  if (mask && mask[l] == 0) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < bs2; i += (long long)gridDim.x * blockDim.x)
+    dst[(long long)l * bs2 + i] = src[(long long)l * bs2 + i];
+}
+
+// Fixed-point convergence test: lead l converged when max|x_new - x| <= tol * max|x_new|.  A
+// lead whose geometric extrapolation (rate = this update / previous update) cannot reach the
+// tolerance within the remaining iterations is given up (left for decimation).
+__global__ void __launch_bounds__(NT) fpi_check_kernel(int bs2, const zd* __restrict__ xn, const zd* __restrict__ x,
+                                                       double tol, int it, int nfpi, int* __restrict__ active,
+                                                       int* __restrict__ conv, double* __restrict__ prev,
+                                                       int* __restrict__ n_active) {
+  __shared__ double sh[32];
+  const int l = blockIdx.x;
+  if (active[l] == 0) return;
+  double d = 0.0, r = 0.0;
+  for (int e = threadIdx.x; e < bs2; e += blockDim.x) {
+    const zd a = xn[(long long)l * bs2 + e], b = x[(long long)l * bs2 + e];
+    d = fmax(d, zmod(zsub(a, b)));
+    r = fmax(r, zmod(a));
+  }
+  d = block_max(d, sh);
+  r = block_max(r, sh);
+  if (threadIdx.x == 0) {
+    // linear convergence with rate rho = d_k / d_{k-1}: the distance to the fixed point is
+    // about d rho / (1 - rho).  The first update has no rate: accept it only 10x below tol.
+    const double rate = it > 1 && prev[l] > 0.0 ? d / prev[l] : 0.0;
+    const double err = it > 1 ? (rate < 1.0 ? d * rate / (1.0 - rate) : INFINITY) : 10.0 * d;
+    if (d <= tol * r && err <= tol * r) {
+      active[l] = 0;
+      conv[l] = 1;
+    } else {
+      const bool hopeless =
+          isnan(d) || (it > 1 && (rate >= 1.0 || d * pow(rate, (double)(nfpi - it)) > tol * r * (1.0 - rate)));
+      if (hopeless || it >= nfpi) { active[l] = 0; conv[l] = 0; }
+      else atomicAdd(n_active, 1);
+      prev[l] = d;
+    }
+  }
+}
+
+__global__ void not_kernel(int batch, const int* __restrict__ a, int* __restrict__ out) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l < batch) out[l] = a[l] ? 0 : 1;
 }
 
 struct DecimWs {
@@ -140,7 +196,10 @@ size_t decimate_workspace_bytes(int bs, int batch) {
 
 bt_status decimate(cudaStream_t st, int bs, int batch, const zd* m, const zd* n, const zd* np, double tol,
                    int maxit, zd* x, zd* sigma, int* iters, int* info, void* ws, size_t ws_bytes,
-                   int* iters_host_max, int* h_pinned) {
+                   int* iters_host_max, int* h_pinned, const int* mask, long long* lead_iterations,
+                   const Engine* eng) {
+  const Engine fp64;
+  const Engine& E = eng ? *eng : fp64;
   if (bs <= 0 || batch <= 0 || maxit <= 0 || batch > 65535) return BT_ERR_INVALID_ARG;
   if (!ws || ws_bytes < decimate_workspace_bytes(bs, batch)) return BT_ERR_INVALID_ARG;
   DecimWs w;
@@ -151,7 +210,7 @@ bt_status decimate(cudaStream_t st, int bs, int batch, const zd* m, const zd* n,
   BT_CUDA_TRY(cudaMemcpyAsync(w.b, np, mat_bytes, cudaMemcpyDeviceToDevice, st));
   BT_CUDA_TRY(cudaMemcpyAsync(w.e, m, mat_bytes, cudaMemcpyDeviceToDevice, st));
   BT_CUDA_TRY(cudaMemcpyAsync(w.es, m, mat_bytes, cudaMemcpyDeviceToDevice, st));
-  init_kernel<<<(batch + 255) / 256, 256, 0, st>>>(batch, w.active, iters, info); count_launch();
+  init_kernel<<<(batch + 255) / 256, 256, 0, st>>>(batch, mask, w.active, iters, info); count_launch();
   ref_kernel<<<batch, NT, 0, st>>>((int)bs2, n, np, w.ref); count_launch();
   BT_CUDA_TRY(cudaGetLastError());
 
@@ -160,24 +219,37 @@ bt_status decimate(cudaStream_t st, int bs, int batch, const zd* m, const zd* n,
   const zd one = zmake(1.0, 0.0), mone = zmake(-1.0, 0.0), zero = zmake(0.0, 0.0);
   const long long S = bs2;
   int it = 0;
+  long long lead_its = 0;
+  int running = batch;  // leads entering the next iteration (upper bound before the first test)
+  if (mask) {
+    // count the masked-in leads so a fully memoized chunk runs no iteration at all
+    if (cudaMemsetAsync(w.n_active, 0, sizeof(int), st) != cudaSuccess) return BT_ERR_CUDA;
+    std::vector<int> hm(batch);
+    if (cudaMemcpyAsync(hm.data(), mask, sizeof(int) * batch, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return BT_ERR_CUDA;
+    running = 0;
+    for (int v : hm) running += v != 0;
+  }
   bt_status rc = BT_OK;
-  for (it = 1; it <= maxit; ++it) {
+  for (it = 1; it <= maxit && running > 0; ++it) {
+    lead_its += running;
     if (cudaMemcpyAsync(w.g, w.e, mat_bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) { rc = BT_ERR_CUDA; break; }
-    if ((rc = zinv(st, bs, w.g, S, batch, info, w.inv_ws, w.inv_bytes, w.active)) != BT_OK) break;
+    if ((rc = zinv(st, bs, w.g, S, batch, info, w.inv_ws, w.inv_bytes, w.active, &E)) != BT_OK) break;
     // ag = a g, bg = b g
-    if ((rc = zgemm(st, bs, bs, bs, one, Operand{w.a, bs, S, BT_OP_N}, Operand{w.g, bs, S, BT_OP_N}, zero, w.ag, bs, S, batch, w.active)) != BT_OK) break;
-    if ((rc = zgemm(st, bs, bs, bs, one, Operand{w.b, bs, S, BT_OP_N}, Operand{w.g, bs, S, BT_OP_N}, zero, w.bg, bs, S, batch, w.active)) != BT_OK) break;
+    if ((rc = gemm(E, st, bs, bs, bs, one, Operand{w.a, bs, S, BT_OP_N}, Operand{w.g, bs, S, BT_OP_N}, zero, w.ag, bs, S, batch, w.active)) != BT_OK) break;
+    if ((rc = gemm(E, st, bs, bs, bs, one, Operand{w.b, bs, S, BT_OP_N}, Operand{w.g, bs, S, BT_OP_N}, zero, w.bg, bs, S, batch, w.active)) != BT_OK) break;
     // t = a g b; es -= t; e -= t
-    if ((rc = zgemm(st, bs, bs, bs, one, Operand{w.ag, bs, S, BT_OP_N}, Operand{w.b, bs, S, BT_OP_N}, zero, w.t, bs, S, batch, w.active)) != BT_OK) break;
+    if ((rc = gemm(E, st, bs, bs, bs, one, Operand{w.ag, bs, S, BT_OP_N}, Operand{w.b, bs, S, BT_OP_N}, zero, w.t, bs, S, batch, w.active)) != BT_OK) break;
     {
       dim3 g((unsigned)((bs2 + 255) / 256 < 64 ? (bs2 + 255) / 256 : 64), batch);
       sub2_kernel<<<g, 256, 0, st>>>(bs2, batch, w.t, w.es, w.e, w.active); count_launch();
     }
     // e -= b g a
-    if ((rc = zgemm(st, bs, bs, bs, mone, Operand{w.bg, bs, S, BT_OP_N}, Operand{w.a, bs, S, BT_OP_N}, one, w.e, bs, S, batch, w.active)) != BT_OK) break;
+    if ((rc = gemm(E, st, bs, bs, bs, mone, Operand{w.bg, bs, S, BT_OP_N}, Operand{w.a, bs, S, BT_OP_N}, one, w.e, bs, S, batch, w.active)) != BT_OK) break;
     // a2 = -a g a, b2 = -b g b
-    if ((rc = zgemm(st, bs, bs, bs, mone, Operand{w.ag, bs, S, BT_OP_N}, Operand{w.a, bs, S, BT_OP_N}, zero, w.a2, bs, S, batch, w.active)) != BT_OK) break;
-    if ((rc = zgemm(st, bs, bs, bs, mone, Operand{w.bg, bs, S, BT_OP_N}, Operand{w.b, bs, S, BT_OP_N}, zero, w.b2, bs, S, batch, w.active)) != BT_OK) break;
+    if ((rc = gemm(E, st, bs, bs, bs, mone, Operand{w.ag, bs, S, BT_OP_N}, Operand{w.a, bs, S, BT_OP_N}, zero, w.a2, bs, S, batch, w.active)) != BT_OK) break;
+    if ((rc = gemm(E, st, bs, bs, bs, mone, Operand{w.bg, bs, S, BT_OP_N}, Operand{w.b, bs, S, BT_OP_N}, zero, w.b2, bs, S, batch, w.active)) != BT_OK) break;
     std::swap(w.a, w.a2);
     std::swap(w.b, w.b2);
     if (cudaMemsetAsync(w.n_active, 0, sizeof(int), st) != cudaSuccess) { rc = BT_ERR_CUDA; break; }
@@ -185,20 +257,78 @@ bt_status decimate(cudaStream_t st, int bs, int batch, const zd* m, const zd* n,
     if (cudaGetLastError() != cudaSuccess) { rc = BT_ERR_CUDA; break; }
     if (cudaMemcpyAsync(h_active, w.n_active, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) { rc = BT_ERR_CUDA; break; }
     if (cudaStreamSynchronize(st) != cudaSuccess) { rc = BT_ERR_CUDA; break; }
-    if (*h_active == 0) break;
+    running = *h_active;
+    if (running == 0) break;
   }
   if (!h_pinned) cudaFreeHost(h_active);
   if (rc != BT_OK) return rc;
-  if (iters_host_max) *iters_host_max = it > maxit ? maxit : it;
+  if (iters_host_max) *iters_host_max = it > maxit ? maxit : (it > 0 ? it : 0);
+  if (lead_iterations) *lead_iterations = lead_its;
   finish_kernel<<<(batch + 255) / 256, 256, 0, st>>>(batch, w.active, info); count_launch();
   BT_CUDA_TRY(cudaGetLastError());
-  // x = e_s^{-1};  sigma = n x n'
-  BT_CUDA_TRY(cudaMemcpyAsync(x, w.es, mat_bytes, cudaMemcpyDeviceToDevice, st));
-  BT_TRY(zinv(st, bs, x, S, batch, info, w.inv_ws, w.inv_bytes, nullptr));
-  if (sigma) {
-    BT_TRY(zgemm(st, bs, bs, bs, one, Operand{n, bs, S, BT_OP_N}, Operand{x, bs, S, BT_OP_N}, zero, w.t, bs, S, batch, nullptr));
-    BT_TRY(zgemm(st, bs, bs, bs, one, Operand{w.t, bs, S, BT_OP_N}, Operand{np, bs, S, BT_OP_N}, zero, sigma, bs, S, batch, nullptr));
+  // x = e_s^{-1} (decimated leads);  sigma = n x n'
+  {
+    dim3 g((unsigned)((bs2 + 255) / 256 < 64 ? (bs2 + 255) / 256 : 64), batch);
+    masked_copy_kernel<<<g, 256, 0, st>>>(bs2, w.es, x, mask); count_launch();
+    BT_CUDA_TRY(cudaGetLastError());
   }
+  BT_TRY(zinv(st, bs, x, S, batch, info, w.inv_ws, w.inv_bytes, mask, &E));
+  if (sigma) {
+    BT_TRY(gemm(E, st, bs, bs, bs, one, Operand{n, bs, S, BT_OP_N}, Operand{x, bs, S, BT_OP_N}, zero, w.t, bs, S, batch, nullptr));
+    BT_TRY(gemm(E, st, bs, bs, bs, one, Operand{w.t, bs, S, BT_OP_N}, Operand{np, bs, S, BT_OP_N}, zero, sigma, bs, S, batch, nullptr));
+  }
+  return BT_OK;
+}
+
+bt_status invert_mask(cudaStream_t st, int batch, const int* a, int* out) {
+  not_kernel<<<(batch + 255) / 256, 256, 0, st>>>(batch, a, out);
+  count_launch();
+  BT_CUDA_TRY(cudaGetLastError());
+  return BT_OK;
+}
+
+bt_status fixed_point(cudaStream_t st, int bs, int batch, const zd* m, const zd* n, const zd* np, zd* x,
+                      const int* run, int* conv, int nfpi, double tol, int* info, void* ws, size_t ws_bytes,
+                      int* h_pinned, long long* lead_iterations, const Engine* eng) {
+  const Engine fp64;
+  const Engine& E = eng ? *eng : fp64;
+  if (bs <= 0 || batch <= 0 || batch > 65535) return BT_ERR_INVALID_ARG;
+  if (!ws || ws_bytes < decimate_workspace_bytes(bs, batch)) return BT_ERR_INVALID_ARG;
+  DecimWs w;
+  carve(ws, bs, batch, &w);
+  const long long bs2 = (long long)bs * bs;
+  const size_t mat_bytes = (size_t)batch * bs2 * sizeof(zd);
+  const long long S = bs2;
+  const zd one = zmake(1.0, 0.0), mone = zmake(-1.0, 0.0), zero = zmake(0.0, 0.0);
+  BT_CUDA_TRY(cudaMemsetAsync(conv, 0, sizeof(int) * batch, st));
+  BT_CUDA_TRY(cudaMemcpyAsync(w.active, run, sizeof(int) * batch, cudaMemcpyDeviceToDevice, st));
+  BT_CUDA_TRY(cudaMemsetAsync(w.ref, 0, sizeof(double) * batch, st));  // previous update sizes
+  std::vector<int> hm(batch);
+  if (cudaMemcpyAsync(hm.data(), run, sizeof(int) * batch, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return BT_ERR_CUDA;
+  int running = 0;
+  for (int v : hm) running += v != 0;
+  long long lead_its = 0;
+  dim3 gcopy((unsigned)((bs2 + 255) / 256 < 64 ? (bs2 + 255) / 256 : 64), batch);
+  for (int it = 1; it <= nfpi && running > 0; ++it) {
+    lead_its += running;
+    // x_new = (m - n x n')^{-1}   (Eq. 5)
+    BT_TRY(gemm(E, st, bs, bs, bs, one, Operand{n, bs, S, BT_OP_N}, Operand{x, bs, S, BT_OP_N}, zero, w.t, bs, S, batch, w.active));
+    BT_CUDA_TRY(cudaMemcpyAsync(w.g, m, mat_bytes, cudaMemcpyDeviceToDevice, st));
+    BT_TRY(gemm(E, st, bs, bs, bs, mone, Operand{w.t, bs, S, BT_OP_N}, Operand{np, bs, S, BT_OP_N}, one, w.g, bs, S, batch, w.active));
+    BT_TRY(zinv(st, bs, w.g, S, batch, info, w.inv_ws, w.inv_bytes, w.active, &E));
+    // the test reads the current mask; copy x_new -> x for the leads still iterating first
+    masked_copy_kernel<<<gcopy, 256, 0, st>>>(bs2, x, w.e, w.active); count_launch();  // keep x_k
+    masked_copy_kernel<<<gcopy, 256, 0, st>>>(bs2, w.g, x, w.active); count_launch();
+    BT_CUDA_TRY(cudaMemsetAsync(w.n_active, 0, sizeof(int), st));
+    fpi_check_kernel<<<batch, NT, 0, st>>>((int)bs2, x, w.e, tol, it, nfpi, w.active, conv, w.ref, w.n_active); count_launch();
+    BT_CUDA_TRY(cudaGetLastError());
+    BT_CUDA_TRY(cudaMemcpyAsync(h_pinned, w.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BT_CUDA_TRY(cudaStreamSynchronize(st));
+    running = *h_pinned;
+  }
+  if (lead_iterations) *lead_iterations = lead_its;
   return BT_OK;
 }
 
@@ -218,5 +348,6 @@ extern "C" bt_status bt_decimate_batched(int bs, int batch, const void* m, const
   if (maxit <= 0) maxit = 100;
   return bt::decimate(static_cast<cudaStream_t>(stream), bs, batch, static_cast<const zd*>(m),
                       static_cast<const zd*>(n), static_cast<const zd*>(n_prime), tol, maxit, static_cast<zd*>(x),
-                      static_cast<zd*>(sigma), iters_device, info_device, workspace, workspace_bytes, nullptr, nullptr);
+                      static_cast<zd*>(sigma), iters_device, info_device, workspace, workspace_bytes, nullptr, nullptr,
+                      nullptr, nullptr);
 }

@@ -56,6 +56,8 @@ bt_status axpby(cudaStream_t st, long long n, int batch, double alpha, const zd*
                 long long so);
 bt_status write_blocks(cudaStream_t st, int bs, int nblk, int batch, const zd* src, long long s_blk, long long s_e,
                        zd* dst, long long d_blk, long long d_e, int mode);
+bt_status write_diagvec(cudaStream_t st, int bs, int nblk, int batch, const zd* src, long long s_blk, long long s_e,
+                        zd* dst, long long d_blk, long long d_e, int mode);  // diagonal entries only
 bt_status shift_diag(cudaStream_t st, int bs, int batch, zd* X, long long sX, double v);  // X += v I
 bt_status merge_status(cudaStream_t st, int E, const int* info, int n_sources, long long src_stride, int* status);
 bt_status check_nonfinite(cudaStream_t st, long long n, int batch, const zd* x, long long sx, int* status);

@@ -18,6 +18,7 @@
 #include <cstring>
 #include <functional>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "elementwise.cuh"
@@ -39,6 +40,13 @@ struct bt_ctx {
   zd *lead_m = nullptr, *lead_n = nullptr, *lead_np = nullptr, *lead_x = nullptr, *lead_sig = nullptr;
   zd *obcL = nullptr, *obcG = nullptr;                // [2E][B2]
   int *lead_iters = nullptr, *lead_info = nullptr;    // [2E]
+  // contact memoization: surface functions of solved energies [cap][2][B2] + lead masks [2E]
+  zd* memo_x = nullptr;
+  int *lead_run = nullptr, *lead_conv = nullptr, *lead_dec = nullptr;
+  std::unordered_map<uint64_t, int> memo_slot;        // energy bits -> slot
+  std::vector<uint64_t> memo_key;                     // slot -> energy bits (0 = empty)
+  std::vector<char> memo_used;
+  int memo_next = 0;
   zd* z = nullptr;
   double *fL = nullptr, *fR = nullptr, *Edev = nullptr;
   void* inv_ws = nullptr;
@@ -47,8 +55,11 @@ struct bt_ctx {
   size_t dec_bytes = 0;
   void* split_ws = nullptr;
   size_t split_bytes = 0;
+  bt::Engine eng_kept;  // products of the inversions and the decimation (FP64 unless split_scope = 1)
   int* h_pinned = nullptr;
   double* h_E = nullptr;
+  bool pinned = true;   // host buffers from cudaMallocHost (else new[])
+  bool owns_ws = true;  // workspace from cudaMalloc (else lent by a serving arena)
   // host-buffer entry point staging (allocated on first use)
   char* stage = nullptr;
   size_t stage_bytes = 0;
@@ -118,6 +129,13 @@ size_t layout(bt_ctx* c, const bt_selinv_desc& d, char* base) {
     x->lead_info = cv.take<int>(2 * E);
     x->dec_bytes = bt::decimate_workspace_bytes(d.bs, (int)(2 * E));
     x->dec_ws = cv.take<char>(x->dec_bytes);
+    if (d.obc_memo) {
+      const size_t cap = (size_t)(d.memo_capacity > 0 ? d.memo_capacity : 4 * d.max_energies);
+      x->memo_x = cv.take<zd>(cap * 2 * B2);
+      x->lead_run = cv.take<int>(2 * E);
+      x->lead_conv = cv.take<int>(2 * E);
+      x->lead_dec = cv.take<int>(2 * E);
+    }
   }
   x->z = cv.take<zd>(E);
   x->fL = cv.take<double>(E);
@@ -126,7 +144,9 @@ size_t layout(bt_ctx* c, const bt_selinv_desc& d, char* base) {
   x->inv_bytes = bt::zinv_workspace_bytes(d.bs, (int)E);
   x->inv_ws = cv.take<char>(x->inv_bytes);
   if (is_split(d)) {
-    x->split_bytes = bt::split_workspace_bytes(d.bs, d.bs, d.bs, slices_of(d), (int)E);
+    // sweep products batch E; with split_scope = 1 also the decimation's 2E leads
+    const int sb = (d.split_scope == 1 && d.obc) ? (int)(2 * E) : (int)E;
+    x->split_bytes = bt::split_workspace_bytes(d.bs, d.bs, d.bs, slices_of(d), sb);
     x->split_ws = cv.take<char>(x->split_bytes);
   }
   return cv.off;
@@ -145,6 +165,9 @@ bt_status validate_desc(const bt_selinv_desc* d, std::string* why) {
   if (d->obc && d->system != BT_SYS_G) return fail("Sancho-Rubio contacts are defined for the G system only");
   if (d->obc && d->nb < 2) return fail("contacts from the edge blocks need nb >= 2");
   if (d->obc && !(d->kT > 0.0)) return fail("kT must be > 0 with contacts");
+  if (d->obc_memo && !d->obc) return fail("contact memoization needs obc = 1");
+  if (d->split_scope != 0 && d->split_scope != 1) return fail("split_scope must be 0 or 1");
+  if (d->obc_memo && d->memo_capacity > 1000000) return fail("memo_capacity too large");
   if (!(d->eta >= 0.0)) return fail("eta must be >= 0");
   if ((double)d->bs * d->bs * d->nb > 4.0e12) return fail("problem too large");
   return BT_OK;
@@ -200,7 +223,7 @@ bt_status prod(bt_ctx* c, int Ec, double alpha, const Blk& A, const Blk& B, doub
 bt_status inv(bt_ctx* c, int Ec, zd* A, long long sA, int* info) {
   const int bs = c->d.bs;
   c->flops += 8.0 * bs * (double)bs * bs * Ec;
-  return bt::zinv(c->st, bs, A, sA, Ec, info, c->inv_ws, c->inv_bytes, nullptr);
+  return bt::zinv(c->st, bs, A, sA, Ec, info, c->inv_ws, c->inv_bytes, nullptr, &c->eng_kept);
 }
 
 // Forward (Eq. 8-9) and backward (Eq. 10-11) passes for one chunk.  x^R, x^<> live in
@@ -323,50 +346,88 @@ extern "C" bt_status bt_selinv_workspace_bytes(const bt_selinv_desc* desc, size_
   return BT_OK;
 }
 
-extern "C" bt_status bt_selinv_create(const bt_selinv_desc* desc, void* cuda_stream, bt_ctx** out) {
-  g_create_error.clear();
-  if (!out) { g_create_error = "out is NULL"; return BT_ERR_INVALID_ARG; }
+namespace bt {
+
+// Creates a context.  With ext_ws == nullptr the workspace is allocated here (cudaMalloc) and
+// host staging buffers are pinned; otherwise the caller lends ext_bytes of device memory at
+// ext_ws (a serving arena) and host buffers are pageable, so creation allocates no device or
+// pinned memory.
+bt_status ctx_create(const bt_selinv_desc* desc, void* cuda_stream, void* ext_ws, size_t ext_bytes, bt_ctx** out,
+                     std::string* err) {
+  if (!out) { *err = "out is NULL"; return BT_ERR_INVALID_ARG; }
   *out = nullptr;
-  std::string why;
-  bt_status s = validate_desc(desc, &why);
-  if (s != BT_OK) { g_create_error = why; return s; }
+  bt_status s = validate_desc(desc, err);
+  if (s != BT_OK) return s;
   bt_selinv_desc d = *desc;
   if (!(d.decim_tol > 0.0)) d.decim_tol = 1e-14;
   if (d.decim_maxit <= 0) d.decim_maxit = 100;
+  if (d.memo_nfpi <= 0) d.memo_nfpi = 20;
+  if (d.memo_capacity <= 0) d.memo_capacity = 4 * d.max_energies;
   const size_t need = layout(nullptr, d, nullptr);
   if (d.hbm_budget_bytes && need > d.hbm_budget_bytes) {
-    g_create_error = "workspace exceeds hbm_budget_bytes";
+    *err = "workspace exceeds hbm_budget_bytes";
     return BT_ERR_BUDGET;
   }
+  if (ext_ws && ext_bytes < need) {
+    *err = "lent workspace is too small";
+    return BT_ERR_INVALID_ARG;
+  }
   bt_ctx* c = new (std::nothrow) bt_ctx();
-  if (!c) { g_create_error = "host allocation failed"; return BT_ERR_OOM; }
+  if (!c) { *err = "host allocation failed"; return BT_ERR_OOM; }
   c->d = d;
   c->st = static_cast<cudaStream_t>(cuda_stream);
-  if (cudaMalloc(&c->ws, need) != cudaSuccess) {
+  if (ext_ws) {
+    c->ws = static_cast<char*>(ext_ws);
+    c->owns_ws = false;
+  } else if (cudaMalloc(&c->ws, need) != cudaSuccess) {
     cudaGetLastError();
     delete c;
-    g_create_error = "cudaMalloc of the workspace failed";
+    *err = "cudaMalloc of the workspace failed";
     return BT_ERR_OOM;
   }
   c->ws_bytes = need;
   layout(c, d, c->ws);
-  if (cudaMallocHost(&c->h_pinned, 64) != cudaSuccess || cudaMallocHost(&c->h_E, sizeof(double) * d.max_energies) != cudaSuccess) {
+  if (ext_ws) {
+    c->h_pinned = new int[16];
+    c->h_E = new double[d.max_energies];
+    c->pinned = false;
+  } else if (cudaMallocHost(&c->h_pinned, 64) != cudaSuccess ||
+             cudaMallocHost(&c->h_E, sizeof(double) * d.max_energies) != cudaSuccess) {
     cudaGetLastError();
     bt_selinv_destroy(c);
-    g_create_error = "pinned host allocation failed";
+    *err = "pinned host allocation failed";
     return BT_ERR_OOM;
   }
   c->stats.workspace_bytes = need;
+  if (is_split(d) && d.split_scope == 1) c->eng_kept = bt::Engine{slices_of(d), c->split_ws, c->split_bytes};
+  if (d.obc_memo) {
+    c->memo_key.assign(d.memo_capacity, 0);
+    c->memo_used.assign(d.memo_capacity, 0);
+  }
   *out = c;
   return BT_OK;
 }
 
+size_t ctx_workspace_bytes(const bt_selinv_desc& d) { return layout(nullptr, d, nullptr); }
+
+}  // namespace bt
+
+extern "C" bt_status bt_selinv_create(const bt_selinv_desc* desc, void* cuda_stream, bt_ctx** out) {
+  g_create_error.clear();
+  return bt::ctx_create(desc, cuda_stream, nullptr, 0, out, &g_create_error);
+}
+
 extern "C" bt_status bt_selinv_destroy(bt_ctx* c) {
   if (!c) return BT_OK;
-  if (c->ws) cudaFree(c->ws);
+  if (c->ws && c->owns_ws) cudaFree(c->ws);
   if (c->stage) cudaFree(c->stage);
-  if (c->h_pinned) cudaFreeHost(c->h_pinned);
-  if (c->h_E) cudaFreeHost(c->h_E);
+  if (c->pinned) {
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    if (c->h_E) cudaFreeHost(c->h_E);
+  } else {
+    delete[] c->h_pinned;
+    delete[] c->h_E;
+  }
   delete c;
   return BT_OK;
 }
@@ -409,6 +470,18 @@ const zd* at_energy(const void* p, int per_energy, long long extent, long long e
   if (!p) return nullptr;
   const zd* q = static_cast<const zd*>(p);
   return per_energy ? q + extent * e0 : q;
+}
+
+// a5: diagonal blocks of the chunk from the workspace [Ec][N][b][b] to the caller's output,
+// as full blocks or as the diagonal-vector layout; mode 1 applies (X - X^H)/2.
+bt_status write_diag_out(bt_ctx* c, int Ec, const zd* src, const bt_bt_out* o, long long e0, int mode) {
+  if (!o || !o->diag) return BT_OK;
+  const int N = c->d.nb, bs = c->d.bs;
+  const long long B2 = (long long)bs * bs, NB2 = N * B2;
+  if (o->layout == BT_LAYOUT_DIAGVEC)
+    return bt::write_diagvec(c->st, bs, N, Ec, src, B2, NB2, static_cast<zd*>(o->diag) + e0 * N * bs, bs,
+                             (long long)N * bs, mode);
+  return bt::write_blocks(c->st, bs, N, Ec, src, B2, NB2, static_cast<zd*>(o->diag) + e0 * NB2, B2, NB2, mode);
 }
 
 bt_status solve_chunk_g(bt_ctx* c, const bt_bt* H, const bt_bt* S, const bt_bt* sR, const bt_bt* sL, const bt_bt* sG,
@@ -515,12 +588,69 @@ bt_status solve_chunk_g(bt_ctx* c, const bt_bt* H, const bt_bt* S, const bt_bt* 
     BT_TRY(bt::assemble_m(st, bs, Ec, off_args(N - 2, true, c->lead_n + Ec * B2, B2)));
     BT_TRY(bt::assemble_m(st, bs, Ec, off_args(N - 2, false, c->lead_np + Ec * B2, B2)));
     int it_max = 0;
+    long long lead_its = 0, fpi_its = 0;
+    const double U = 8.0 * bs * (double)bs * bs;
+    const int* dec_mask = nullptr;
+    std::vector<int> slots;
+    if (d.obc_memo) {
+      // Sec. 4.3: energies solved before start the fixed point (Eq. 5) from their kept surface
+      // functions; leads that do not converge within memo_nfpi iterations are decimated.
+      std::vector<int> run(2 * Ec, 0);
+      slots.assign(Ec, -1);
+      for (int e = 0; e < Ec; ++e) {
+        uint64_t key;
+        std::memcpy(&key, &c->h_E[e], sizeof(key));
+        auto it = c->memo_slot.find(key);
+        if (it == c->memo_slot.end()) continue;
+        slots[e] = it->second;
+        run[e] = run[Ec + e] = 1;
+        for (int side = 0; side < 2; ++side)
+          BT_CUDA_TRY(cudaMemcpyAsync(c->lead_x + (long long)(side * Ec + e) * B2,
+                                      c->memo_x + ((long long)it->second * 2 + side) * B2, sizeof(zd) * B2,
+                                      cudaMemcpyDeviceToDevice, st));
+      }
+      c->stats.memo_hits += (long long)std::count_if(slots.begin(), slots.end(), [](int v) { return v >= 0; });
+      BT_CUDA_TRY(cudaMemcpyAsync(c->lead_run, run.data(), sizeof(int) * 2 * Ec, cudaMemcpyHostToDevice, st));
+      BT_CUDA_TRY(cudaMemsetAsync(c->lead_info, 0, sizeof(int) * 2 * Ec, st));
+      BT_TRY(bt::fixed_point(st, bs, 2 * Ec, c->lead_m, c->lead_n, c->lead_np, c->lead_x, c->lead_run, c->lead_conv,
+                             // fixed-point target: 1e-12 of |x| (FP64 rounding already moves the
+                             // surface function of an in-band lead by ~1e-13 at eta = 1e-6)
+                             d.memo_nfpi, d.decim_tol > 1e-12 ? d.decim_tol : 1e-12, c->lead_info, c->dec_ws,
+                             c->dec_bytes, c->h_pinned, &fpi_its,
+                             &c->eng_kept));
+      BT_TRY(bt::invert_mask(st, 2 * Ec, c->lead_conv, c->lead_dec));
+      dec_mask = c->lead_dec;
+      c->flops += 3.0 * U * (double)fpi_its;
+    }
     bt_status s = bt::decimate(st, bs, 2 * Ec, c->lead_m, c->lead_n, c->lead_np, d.decim_tol, d.decim_maxit, c->lead_x,
                                c->lead_sig, c->lead_iters, c->lead_info, c->dec_ws, c->dec_bytes, &it_max,
-                               c->h_pinned);
+                               c->h_pinned, dec_mask, &lead_its, &c->eng_kept);
     if (s != BT_OK) return set_err(c, s, "decimation failed to launch");
     c->stats.decim_iterations += it_max;
-    c->flops += 2.0 * Ec * (7.0 * it_max + 3.0) * 8.0 * bs * (double)bs * bs;
+    c->stats.lead_iterations += lead_its;
+    c->stats.fpi_iterations += fpi_its;
+    // 7 products per lead-iteration, then x = e_s^{-1} and n x n' for every lead
+    c->flops += 7.0 * U * (double)lead_its + 3.0 * U * 2.0 * Ec;
+    if (d.obc_memo) {
+      // keep this chunk's surface functions (oldest entries evicted first)
+      for (int e = 0; e < Ec; ++e) {
+        uint64_t key;
+        std::memcpy(&key, &c->h_E[e], sizeof(key));
+        int slot = slots[e];
+        if (slot < 0) {
+          slot = c->memo_next;
+          c->memo_next = (c->memo_next + 1) % d.memo_capacity;
+          if (c->memo_used[slot]) c->memo_slot.erase(c->memo_key[slot]);
+          c->memo_used[slot] = 1;
+          c->memo_key[slot] = key;
+          c->memo_slot[key] = slot;
+        }
+        for (int side = 0; side < 2; ++side)
+          BT_CUDA_TRY(cudaMemcpyAsync(c->memo_x + ((long long)slot * 2 + side) * B2,
+                                      c->lead_x + (long long)(side * Ec + e) * B2, sizeof(zd) * B2,
+                                      cudaMemcpyDeviceToDevice, st));
+      }
+    }
     BT_TRY(bt::merge_status(st, Ec, c->lead_info, 2, Ec, status));
     BT_TRY(bt::obc_lesser_greater(st, bs, Ec, c->lead_sig, c->fL, c->fR, c->obcL, c->obcG));
   }
@@ -581,12 +711,9 @@ bt_status solve_chunk_g(bt_ctx* c, const bt_bt* H, const bt_bt* S, const bt_bt* 
   BT_TRY(run_sweep(sw, status));
 
   // ---------------- a5: write-out ----------------
-  if (oR && oR->diag)
-    BT_TRY(bt::write_blocks(st, bs, N, Ec, c->xR, B2, NB2, static_cast<zd*>(oR->diag) + e0 * NB2, B2, NB2, 0));
-  if (oL && oL->diag)
-    BT_TRY(bt::write_blocks(st, bs, N, Ec, c->xL, B2, NB2, static_cast<zd*>(oL->diag) + e0 * NB2, B2, NB2, d.symmetrize ? 1 : 0));
-  if (oG && oG->diag)
-    BT_TRY(bt::write_blocks(st, bs, N, Ec, c->xG, B2, NB2, static_cast<zd*>(oG->diag) + e0 * NB2, B2, NB2, d.symmetrize ? 1 : 0));
+  BT_TRY(write_diag_out(c, Ec, c->xR, oR, e0, 0));
+  BT_TRY(write_diag_out(c, Ec, c->xL, oL, e0, d.symmetrize ? 1 : 0));
+  BT_TRY(write_diag_out(c, Ec, c->xG, oG, e0, d.symmetrize ? 1 : 0));
   return BT_OK;
 }
 
@@ -722,12 +849,18 @@ bt_status solve_chunk_w(bt_ctx* c, const bt_bt* V, const bt_bt* PR, const bt_bt*
     auto XRl = [&](int i) { return W(c->XRl + i * B2, N1B2); };
     auto X2u = [&](int i) { return W(c->X2u + i * B2, N2B2); };
     auto X2l = [&](int i) { return W(c->X2l + i * B2, N2B2); };
+    const bool rvec = oR->layout == BT_LAYOUT_DIAGVEC;
     for (int i = 0; i < N; ++i) {
       if (oR->diag) {
-        zd* o = static_cast<zd*>(oR->diag) + (e0 * N + i) * B2;
-        BT_TRY(prod(c, Ec, 1.0, XRd(i), Vb(i, i), 0.0, o, NB2));
-        if (i > 0) BT_TRY(prod(c, Ec, 1.0, XRl(i - 1), Vb(i - 1, i), 1.0, o, NB2));
-        if (i + 1 < N) BT_TRY(prod(c, Ec, 1.0, XRu(i), Vb(i + 1, i), 1.0, o, NB2));
+        // diagonal-vector output: form the block in a temporary, keep its diagonal
+        zd* o = rvec ? c->t[0] : static_cast<zd*>(oR->diag) + (e0 * N + i) * B2;
+        const long long es = rvec ? B2 : NB2;
+        BT_TRY(prod(c, Ec, 1.0, XRd(i), Vb(i, i), 0.0, o, es));
+        if (i > 0) BT_TRY(prod(c, Ec, 1.0, XRl(i - 1), Vb(i - 1, i), 1.0, o, es));
+        if (i + 1 < N) BT_TRY(prod(c, Ec, 1.0, XRu(i), Vb(i + 1, i), 1.0, o, es));
+        if (rvec)
+          BT_TRY(bt::write_diagvec(st, bs, 1, Ec, o, 0, B2, static_cast<zd*>(oR->diag) + (e0 * N + i) * bs, 0,
+                                   (long long)N * bs, 0));
       }
       if (i + 1 < N && oR->upper) {
         zd* o = static_cast<zd*>(oR->upper) + (e0 * (N - 1) + i) * B2;
@@ -744,10 +877,8 @@ bt_status solve_chunk_w(bt_ctx* c, const bt_bt* V, const bt_bt* PR, const bt_bt*
     }
   }
   // ---- a5 ----
-  if (oL && oL->diag)
-    BT_TRY(bt::write_blocks(st, bs, N, Ec, c->xL, B2, NB2, static_cast<zd*>(oL->diag) + e0 * NB2, B2, NB2, d.symmetrize ? 1 : 0));
-  if (oG && oG->diag)
-    BT_TRY(bt::write_blocks(st, bs, N, Ec, c->xG, B2, NB2, static_cast<zd*>(oG->diag) + e0 * NB2, B2, NB2, d.symmetrize ? 1 : 0));
+  BT_TRY(write_diag_out(c, Ec, c->xL, oL, e0, d.symmetrize ? 1 : 0));
+  BT_TRY(write_diag_out(c, Ec, c->xG, oG, e0, d.symmetrize ? 1 : 0));
   (void)status;
   return BT_OK;
 }
@@ -784,7 +915,13 @@ bt_status check_solve_args(bt_ctx* c, const bt_bt* H, const bt_bt* S, const bt_b
                         (sG && (!sG->upper || sG->symmetry != BT_SYM_ANTIHERMITIAN))))
       return fail("P^<> need anti-Hermitian off-diagonal blocks");
   }
-  (void)oR;
+  const bt_bt_out* outs[3] = {oR, oL, oG};
+  for (const bt_bt_out* o : outs) {
+    if (!o) continue;
+    if (o->layout != BT_LAYOUT_BLOCKS && o->layout != BT_LAYOUT_DIAGVEC) return fail("bad output layout");
+    if (o->layout == BT_LAYOUT_DIAGVEC && (o->upper || o->lower))
+      return fail("diagonal-vector outputs have no off-diagonal blocks");
+  }
   (void)s;
   return BT_OK;
 }
@@ -837,6 +974,10 @@ extern "C" bt_status bt_selinv_solve(bt_ctx* c, const bt_bt* H, const bt_bt* S, 
 // ======================================================================================
 namespace {
 
+long long diag_out_extent(const bt_bt_out* o, int nb, int bs) {
+  return o->layout == BT_LAYOUT_DIAGVEC ? (long long)nb * bs : (long long)nb * bs * bs;
+}
+
 struct StagedOperand {
   bt_bt dev{};
   const bt_bt* host = nullptr;
@@ -874,7 +1015,7 @@ extern "C" bt_status bt_selinv_solve_host(bt_ctx* c, const bt_bt* H, const bt_bt
   const bt_bt_out* outs[3] = {outR, outL, outG};
   for (int k = 0; k < 3; ++k) {
     if (!outs[k]) continue;
-    if (outs[k]->diag) need += al(sizeof(zd) * NB2 * Emax);
+    if (outs[k]->diag) need += al(sizeof(zd) * diag_out_extent(outs[k], N, bs) * Emax);
     if (outs[k]->upper) need += al(sizeof(zd) * N1B2 * Emax);
     if (outs[k]->lower) need += al(sizeof(zd) * N1B2 * Emax);
   }
@@ -898,7 +1039,8 @@ extern "C" bt_status bt_selinv_solve_host(bt_ctx* c, const bt_bt* H, const bt_bt
   bt_bt_out dout[3] = {};
   for (int k = 0; k < 3; ++k) {
     if (!outs[k]) continue;
-    if (outs[k]->diag) dout[k].diag = cv.take<zd>(NB2 * Emax);
+    dout[k].layout = outs[k]->layout;
+    if (outs[k]->diag) dout[k].diag = cv.take<zd>(diag_out_extent(outs[k], N, bs) * Emax);
     if (outs[k]->upper) dout[k].upper = cv.take<zd>(N1B2 * Emax);
     if (outs[k]->lower) dout[k].lower = cv.take<zd>(N1B2 * Emax);
   }
@@ -935,7 +1077,8 @@ extern "C" bt_status bt_selinv_solve_host(bt_ctx* c, const bt_bt* H, const bt_bt
     if (s != BT_OK) return s;
     for (int k = 0; k < 3; ++k) {
       if (!outs[k]) continue;
-      if (outs[k]->diag && !d2h(static_cast<zd*>(outs[k]->diag) + NB2 * e0, dout[k].diag, sizeof(zd) * NB2 * Ec)) return set_err(c, BT_ERR_CUDA, "D2H failed");
+      const long long dx = diag_out_extent(outs[k], N, bs);
+      if (outs[k]->diag && !d2h(static_cast<zd*>(outs[k]->diag) + dx * e0, dout[k].diag, sizeof(zd) * dx * Ec)) return set_err(c, BT_ERR_CUDA, "D2H failed");
       if (outs[k]->upper && !d2h(static_cast<zd*>(outs[k]->upper) + N1B2 * e0, dout[k].upper, sizeof(zd) * N1B2 * Ec)) return set_err(c, BT_ERR_CUDA, "D2H failed");
       if (outs[k]->lower && !d2h(static_cast<zd*>(outs[k]->lower) + N1B2 * e0, dout[k].lower, sizeof(zd) * N1B2 * Ec)) return set_err(c, BT_ERR_CUDA, "D2H failed");
     }

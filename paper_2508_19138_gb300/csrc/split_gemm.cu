@@ -73,11 +73,28 @@ struct MmaParams {
   int beta_zero;
   int complex_coef;  // alpha or beta has an imaginary part
   int* err;          // per batch entry error slot (may be null)
+  const int* active; // batch entries with active[b] == 0 are skipped (may be null)
   Schedule sched;
 };
 
 __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
   return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
+}
+
+// fp32 value -> int64 fixed point with kFixShift fraction bits, from the IEEE fields with
+// integer instructions only (a float -> int64 conversion would run on GB300's slow FP64 pipe).
+// Exact for the single-pair groups (integers times 2^-7(s+t-2), s+t <= 7); the shared group
+// is truncated below 2^-36 of a leading digit product.
+__device__ __forceinline__ long long f32_to_fix(float v) {
+  const uint32_t bits = __float_as_uint(v);
+  const int e = (int)((bits >> 23) & 0xFFu);
+  if (e == 0) return 0;  // zero (denormals are far below the fixed-point resolution)
+  const long long m = (long long)((bits & 0x7FFFFFu) | 0x800000u);
+  const int sh = e - 150 + kFixShift;  // value = m * 2^(e - 150)
+  long long r;
+  if (sh >= 0) r = sh < 40 ? (m << sh) : 0x7FFFFFFFFFFFFFFFll;  // |v| >= 2^27 cannot occur
+  else r = sh > -32 ? (m >> -sh) : 0;
+  return (bits >> 31) ? -r : r;
 }
 
 // int64 fixed-point value * 2^e -> double, integer arithmetic only (round to nearest even).
@@ -114,6 +131,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   static_assert(2 * NT <= 256, "two accumulators must fit in 256 TMEM columns");
   constexpr uint32_t kIdesc = ptx::idesc_bf16_f32(kTileM, NT);
 
+  if (p.active && p.active[blockIdx.z] == 0) return;  // before any barrier or TMEM use
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
   uint8_t* sA = smem;
@@ -236,7 +254,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     long long acc[kHalf];
 #pragma unroll
     for (int c = 0; c < kHalf; ++c) acc[c] = 0;
-    const float fix_scale = 68719476736.0f;  // 2^36
     bool ok = true;
     for (int g = 0; g < sc.n_groups; ++g) {
       const int ab = g & 1;
@@ -253,7 +270,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         ptx::tmem_ld_x8(base + c * 8, v);
         ptx::tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[c * 8 + j] += __float2ll_rn(__uint_as_float(v[j]) * fix_scale);
+        for (int j = 0; j < 8; ++j) acc[c * 8 + j] += f32_to_fix(__uint_as_float(v[j]));
       }
       ptx::tc_fence_before();
       __syncwarp();
@@ -331,9 +348,11 @@ __device__ __forceinline__ zd load_op(const zd* X, int ld, int op, int r, int c)
 // Row maxima (rows != null) and column maxima (cols != null) of the biased exponents of L
 // (R x Kc), tiles of 32 x 32 loaded coalesced for either orientation.
 __global__ void exp_max_kernel(int R, int Kc, const zd* __restrict__ X, int ld, long long sX, int op,
-                               int* __restrict__ rows, long long sRows, int* __restrict__ cols, long long sCols) {
+                               int* __restrict__ rows, long long sRows, int* __restrict__ cols, long long sCols,
+                               const int* __restrict__ active) {
   __shared__ int E[32][33];
   const int b = blockIdx.z;
+  if (active && active[b] == 0) return;
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
   const zd* Xb = X + sX * b;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
@@ -396,9 +415,11 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 
 // At slices: out[b][s][r][2p + c] for L = op(A) (R x Kc), row exponents erow[b][r].
 __global__ void slice_rows_kernel(int R, int Rpad, int Kc, int Kp, const zd* __restrict__ X, int ld, long long sX,
-                                  int op, const int* __restrict__ erow, int S, uint32_t* __restrict__ out) {
+                                  int op, const int* __restrict__ erow, int S, uint32_t* __restrict__ out,
+                                  const int* __restrict__ active) {
   __shared__ zd T[32][33];
   const int b = blockIdx.z;
+  if (active && active[b] == 0) return;
   const int r0 = blockIdx.y * 32, p0 = blockIdx.x * 32;
   const zd* Xb = X + sX * b;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -432,9 +453,10 @@ __global__ void slice_rows_kernel(int R, int Rpad, int Kc, int Kp, const zd* __r
 // column exponents ecol[b][j].
 __global__ void slice_cols_kernel(int Kc, int Ncol, int NcolPad, int Kp, const zd* __restrict__ X, int ld,
                                   long long sX, int op, const int* __restrict__ ecol, int S,
-                                  uint32_t* __restrict__ out) {
+                                  uint32_t* __restrict__ out, const int* __restrict__ active) {
   __shared__ zd T[32][33];  // T[j][p]
   const int b = blockIdx.z;
+  if (active && active[b] == 0) return;
   const int j0 = blockIdx.y * 32, p0 = blockIdx.x * 32;
   const zd* Xb = X + sX * b;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -500,7 +522,10 @@ bool encode_slices_map(CUtensorMap* map, void* base, int Kp, int rows, int depth
 Schedule make_schedule(int S) {
   Schedule sc{};
   int np = 0, ng = 0;
-  for (int d = 2; d <= kExactD && d <= S + 1; ++d)
+  // exact single-pair groups up to s + t = dx; the shared group's fp32 rounding (~2^-24 of
+  // terms scaled by 2^-7(dx-1)) then stays below the slicing error for every S
+  const int dx = S - 1 > kExactD ? S - 1 : kExactD;
+  for (int d = 2; d <= dx && d <= S + 1; ++d)
     for (int s = 1; s <= S; ++s) {
       const int t = d - s;
       if (t < 1 || t > S) continue;
@@ -510,7 +535,7 @@ Schedule make_schedule(int S) {
       sc.group_end[ng++] = (unsigned char)np;
     }
   const int np0 = np;
-  for (int d = kExactD + 1; d <= S + 1; ++d)
+  for (int d = dx + 1; d <= S + 1; ++d)
     for (int s = 1; s <= S; ++s) {
       const int t = d - s;
       if (t < 1 || t > S) continue;
@@ -525,11 +550,17 @@ Schedule make_schedule(int S) {
 }
 
 int pick_nt(int m) {
-  // the widest N tile (<= 128, multiple of 16) among those with the least padding
-  int best = 16, best_pad = 1 << 30;
+  // Cost of one K=16 step of a 128 x NT tile: the MMA needs NT/2 clocks of tensor work and
+  // reads (128 + NT) x 32 bytes of shared memory at ~128 B/clock, so the step costs
+  // max(NT/2, 32 + NT/4) clocks.  Pick the N tile (multiple of 16, <= 128) that minimises
+  // tiles x step cost for the m columns (e.g. m = 416 -> 112: 4 tiles, 7 % padding).
+  int best = 16;
+  double best_cost = 1e30;
   for (int nt = 128; nt >= 16; nt -= 16) {
-    const int pad = ((m + nt - 1) / nt) * nt - m;
-    if (pad < best_pad) { best_pad = pad; best = nt; }
+    const int tiles = (m + nt - 1) / nt;
+    const double step = nt / 2.0 > 32.0 + nt / 4.0 ? nt / 2.0 : 32.0 + nt / 4.0;
+    const double cost = tiles * step;
+    if (cost < best_cost - 1e-9) { best_cost = cost; best = nt; }
   }
   return best;
 }
@@ -560,12 +591,19 @@ size_t carve_ws(char* base, int m, int n, int kc, int S, int batch, SplitWs* w) 
 template <int NT>
 bt_status launch_mma(cudaStream_t st, const CUtensorMap& mA, const CUtensorMap& mB, const MmaParams& p, int batch) {
   const size_t smem = 1024 + (size_t)kStages * (kTileM * 128 + NT * 128) + 256;
-  static bool attr_set = false;
-  if (!attr_set) {
-    if (cudaFuncSetAttribute(split_mma_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return BT_ERR_CUDA;
-    attr_set = true;
+  // per-function device state: set once per device (the value never changes for one NT)
+  static std::mutex mu;
+  static bool attr_set[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return BT_ERR_CUDA;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!attr_set[dev]) {
+      if (cudaFuncSetAttribute(split_mma_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess)
+        return BT_ERR_CUDA;
+      attr_set[dev] = true;
+    }
   }
   dim3 grid((p.n2 + kTileM - 1) / kTileM, (p.m + NT - 1) / NT, batch);
   split_mma_kernel<NT><<<grid, kThreads, smem, st>>>(mA, mB, p);
@@ -603,7 +641,6 @@ size_t split_workspace_bytes(int m, int n, int k, int slices, int batch) {
 
 bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A, Operand B, zd beta, zd* C, int ldc,
                       long long strideC, int batch, int slices, void* ws, size_t ws_bytes, const int* active) {
-  (void)active;
   const int S = slices > 0 ? slices : 6;
   if (S < 2 || S > kMaxSlices) return BT_ERR_INVALID_ARG;
   if (m < 0 || n < 0 || k < 0 || batch < 0) return BT_ERR_INVALID_ARG;
@@ -615,7 +652,7 @@ bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A,
         BT_CUDA_TRY(cudaMemset2DAsync(C + strideC * b, sizeof(zd) * ldc, 0, sizeof(zd) * n, m, st));
       return BT_OK;
     }
-    return zgemm(st, m, n, 0, alpha, A, B, beta, C, ldc, strideC, batch, nullptr);  // C = beta C
+    return zgemm(st, m, n, 0, alpha, A, B, beta, C, ldc, strideC, batch, active);  // C = beta C
   }
   if (!ws || ws_bytes < split_workspace_bytes(m, n, k, S, batch)) return BT_ERR_INVALID_ARG;
   if (!get_encode()) return BT_ERR_UNSUPPORTED;
@@ -634,19 +671,20 @@ bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A,
     BT_CUDA_TRY(cudaMemsetAsync(w.eB, 0, sizeof(int) * (size_t)batch * n, st));
     {
       dim3 g((kc + 31) / 32, (m + 31) / 32, batch);
-      exp_max_kernel<<<g, 256, 0, st>>>(m, kc, a.p, a.ld, a.stride, a.op, w.eA, m, nullptr, 0);
+      exp_max_kernel<<<g, 256, 0, st>>>(m, kc, a.p, a.ld, a.stride, a.op, w.eA, m, nullptr, 0, active);
       count_launch();
       dim3 g2((n + 31) / 32, (kc + 31) / 32, batch);
-      exp_max_kernel<<<g2, 256, 0, st>>>(kc, n, bop.p, bop.ld, bop.stride, bop.op, nullptr, 0, w.eB, n);
+      exp_max_kernel<<<g2, 256, 0, st>>>(kc, n, bop.p, bop.ld, bop.stride, bop.op, nullptr, 0, w.eB, n, active);
       count_launch();
       BT_CUDA_TRY(cudaGetLastError());
     }
     {
       dim3 g((Kp / 2 + 31) / 32, (mp + 31) / 32, batch);
-      slice_rows_kernel<<<g, 256, 0, st>>>(m, mp, kc, Kp, a.p, a.ld, a.stride, a.op, w.eA, S, w.At);
+      slice_rows_kernel<<<g, 256, 0, st>>>(m, mp, kc, Kp, a.p, a.ld, a.stride, a.op, w.eA, S, w.At, active);
       count_launch();
       dim3 g2((Kp / 2 + 31) / 32, (n2p / 2 + 31) / 32, batch);
-      slice_cols_kernel<<<g2, 256, 0, st>>>(kc, n, n2p / 2, Kp, bop.p, bop.ld, bop.stride, bop.op, w.eB, S, w.Bt);
+      slice_cols_kernel<<<g2, 256, 0, st>>>(kc, n, n2p / 2, Kp, bop.p, bop.ld, bop.stride, bop.op, w.eB, S, w.Bt,
+                                            active);
       count_launch();
       BT_CUDA_TRY(cudaGetLastError());
     }
@@ -668,6 +706,7 @@ bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A,
     p.beta_zero = (p.beta.x == 0.0 && p.beta.y == 0.0) ? 1 : 0;
     p.complex_coef = (p.alpha.y != 0.0 || p.beta.y != 0.0) ? 1 : 0;
     p.err = nullptr;
+    p.active = active;
     p.sched = make_schedule(S);
     BT_TRY(launch_mma_nt(nt, st, mA, mB, p, batch));
   }

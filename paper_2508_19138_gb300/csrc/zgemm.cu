@@ -3,9 +3,15 @@
 //
 // GB300 note: the FP64 pipe of this part issues about 2 DFMA per clock per SM (measured
 // ~1.2 TFLOP/s for the whole GPU; the FP64 mma.sync path measured ~1.05 TFLOP/s), so this
-// kernel is bound by FP64 issue, not by memory.  What matters is keeping every SM busy with
-// whole tiles: 32 x 32 output tiles divide the workload block sizes (32, 416 = 13 x 32,
-// 1024) without ragged waste, and the batch (energies x blocks) gives >= 152 CTAs.
+// kernel is bound by FP64 issue, not by memory.  Two consequences:
+//  * the complex product uses three real products instead of four (Gauss's trick, the "3M"
+//    method): t1 = Re a Re b, t2 = Im a Im b, t3 = (Re a + Im a)(Re b + Im b), Re c = t1 - t2,
+//    Im c = t3 - t1 - t2.  The sums Re + Im are formed once per element when a tile is staged
+//    in shared memory, so the inner loop issues 3 DFMA per complex multiply-add instead of 4
+//    (error bound u |a||b| per term with |.| the 1-norm of re/im, Higham 2002, Sec. 23.2.4);
+//  * what matters otherwise is keeping every SM busy with whole tiles: 32 x 32 output tiles
+//    divide the workload block sizes (32, 416 = 13 x 32, 1024) without ragged waste, and the
+//    batch (energies x blocks) gives >= 152 CTAs.
 // Tiles are staged through shared memory with a register prefetch of the next k-slab.
 #include <atomic>
 
@@ -33,16 +39,17 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(int m, int n, int k, zd alpha
   A += sA * bz;
   B += sB * bz;
   C += sC * bz;
-  __shared__ zd As[BK][BM + 1];
-  __shared__ zd Bs[BK][BN + 1];
+  // real, imaginary and re + im planes of the staged tiles
+  __shared__ double Ar[BK][BM + 1], Ai[BK][BM + 1], Ap[BK][BM + 1];
+  __shared__ double Br[BK][BN + 1], Bi[BK][BN + 1], Bp[BK][BN + 1];
   const int t = threadIdx.x;
   const int tx = t & 15, ty = t >> 4;
 
-  zd acc[2][2];
+  double t1[2][2], t2[2][2], t3[2][2];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 2; ++j) acc[i][j] = zmake(0.0, 0.0);
+    for (int j = 0; j < 2; ++j) t1[i][j] = t2[i][j] = t3[i][j] = 0.0;
 
   zd ra[2], rb[2];  // prefetch registers: 2 elements of A and of B per thread per k-slab
   auto load_a = [&](int k0) {
@@ -81,9 +88,13 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(int m, int n, int k, zd alpha
       int e = t + NT * s;
       int r, c;
       if (OPA == BT_OP_N) { r = e >> 4; c = e & 15; } else { c = e >> 5; r = e & 31; }
-      As[c][r] = ra[s];
+      Ar[c][r] = ra[s].x;
+      Ai[c][r] = ra[s].y;
+      Ap[c][r] = ra[s].x + ra[s].y;
       if (OPB == BT_OP_N) { r = e >> 5; c = e & 31; } else { c = e >> 4; r = e & 15; }
-      Bs[r][c] = rb[s];
+      Br[r][c] = rb[s].x;
+      Bi[r][c] = rb[s].y;
+      Bp[r][c] = rb[s].x + rb[s].y;
     }
   };
 
@@ -99,14 +110,31 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(int m, int n, int k, zd alpha
     }
 #pragma unroll 4
     for (int kk = 0; kk < BK; ++kk) {
-      zd a0 = As[kk][ty], a1 = As[kk][ty + 16];
-      zd b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
-      zfma(acc[0][0], a0, b0);
-      zfma(acc[0][1], a0, b1);
-      zfma(acc[1][0], a1, b0);
-      zfma(acc[1][1], a1, b1);
+      double ar[2], ai[2], ap[2], br[2], bi[2], bp[2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        ar[i] = Ar[kk][ty + 16 * i];
+        ai[i] = Ai[kk][ty + 16 * i];
+        ap[i] = Ap[kk][ty + 16 * i];
+        br[i] = Br[kk][tx + 16 * i];
+        bi[i] = Bi[kk][tx + 16 * i];
+        bp[i] = Bp[kk][tx + 16 * i];
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          t1[i][j] = fma(ar[i], br[j], t1[i][j]);
+          t2[i][j] = fma(ai[i], bi[j], t2[i][j]);
+          t3[i][j] = fma(ap[i], bp[j], t3[i][j]);
+        }
     }
   }
+  zd acc[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) acc[i][j] = zmake(t1[i][j] - t2[i][j], t3[i][j] - t1[i][j] - t2[i][j]);
   const bool beta_zero = (beta.x == 0.0 && beta.y == 0.0);
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
@@ -154,6 +182,14 @@ bt_status zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A, Opera
   count_launch();
   BT_CUDA_TRY(cudaGetLastError());
   return BT_OK;
+}
+
+bt_status gemm(const Engine& eng, cudaStream_t st, int m, int n, int k, zd alpha, Operand A, Operand B, zd beta,
+               zd* C, int ldc, long long strideC, int batch, const int* active) {
+  if (eng.slices > 0)
+    return split_zgemm(st, m, n, k, alpha, A, B, beta, C, ldc, strideC, batch, eng.slices, eng.ws, eng.ws_bytes,
+                       active);
+  return zgemm(st, m, n, k, alpha, A, B, beta, C, ldc, strideC, batch, active);
 }
 
 }  // namespace bt

@@ -13,6 +13,8 @@
 //    then receive the panel's row exchanges and the rank-kb update
 //        A[:, C] += P[:, K] * A_old[K, C]   (rows K of C zeroed first)
 //    as one batched FP64 GEMM, so the O(n^3) part runs on the GEMM kernel.
+#include <mutex>
+
 #include "bt_common.cuh"
 
 namespace bt {
@@ -226,7 +228,10 @@ __global__ void gj_unscramble_kernel(int n, zd* __restrict__ A, long long sA, co
 }
 
 int panel_width(int n) {
-  for (int kb = 32; kb >= 4; kb >>= 1) {
+  // The panel elimination costs ~n kb^2 complex FMAs per panel on ONE SM per matrix (4 n^2 kb
+  // DFMA per inverse), the rank-kb updates n^3 on all SMs; kb = 16 balances the two on GB300's
+  // slow FP64 pipe (kb = 32 made the panels ~27 % of a split-precision step).
+  for (int kb = 16; kb >= 4; kb >>= 1) {
     size_t need = (size_t)n * (kb + 1) * sizeof(zd) + (size_t)(n + kb) * sizeof(zd) + 1024;
     if (need <= kSmemLimit) return kb;
   }
@@ -235,6 +240,25 @@ int panel_width(int n) {
 
 size_t small_smem(int n) { return (size_t)n * (n + 1) * sizeof(zd) + 2 * (size_t)n * sizeof(zd) + n * sizeof(int) + 16; }
 size_t panel_smem(int n, int kb) { return (size_t)n * (kb + 1) * sizeof(zd) + (size_t)(n + kb) * sizeof(zd) + 16; }
+
+// The dynamic shared-memory limits are per-function device state: set them once per device to
+// the largest size any launch uses (setting them per launch races between host threads that
+// invert different block sizes concurrently, e.g. the serving workers).
+bt_status set_smem_limits() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return BT_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return BT_OK;
+  const int small_max = (int)small_smem(kSmallN);
+  const int panel_max = (int)(kSmemLimit - 1024);  // leaves room for the kernels' static shared memory
+  if (cudaFuncSetAttribute(zinv_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, small_max) != cudaSuccess ||
+      cudaFuncSetAttribute(gj_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, panel_max) != cudaSuccess)
+    return BT_ERR_CUDA;
+  done[dev] = true;
+  return BT_OK;
+}
 
 }  // namespace
 
@@ -248,13 +272,15 @@ size_t zinv_workspace_bytes(int n, int batch) {
 }
 
 bt_status zinv(cudaStream_t st, int n, zd* A, long long sA, int batch, int* info, void* ws, size_t ws_bytes,
-               const int* active) {
+               const int* active, const Engine* eng) {
+  const Engine fp64;
+  const Engine& E = eng ? *eng : fp64;
   if (n < 0 || batch < 0) return BT_ERR_INVALID_ARG;
   if (n == 0 || batch == 0) return BT_OK;
   if (batch > 2147483647 / 2) return BT_ERR_INVALID_ARG;
+  BT_TRY(set_smem_limits());
   if (n <= kSmallN) {
     size_t sm = small_smem(n);
-    BT_CUDA_TRY(cudaFuncSetAttribute(zinv_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     zinv_small_kernel<<<batch, NT, sm, st>>>(n, A, sA, info, active); count_launch();
     BT_CUDA_TRY(cudaGetLastError());
     return BT_OK;
@@ -267,8 +293,6 @@ bt_status zinv(cudaStream_t st, int n, zd* A, long long sA, int batch, int* info
   size_t perm_bytes = ((size_t)batch * n * sizeof(int) + 255) / 256 * 256;
   zd* T = reinterpret_cast<zd*>(static_cast<char*>(ws) + perm_bytes);
   const long long sT = (long long)kb * n;
-  size_t sm = panel_smem(n, kb);
-  BT_CUDA_TRY(cudaFuncSetAttribute(gj_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   for (int k0 = 0; k0 < n; k0 += kb) {
     const int w = (n - k0) < kb ? (n - k0) : kb;
     gj_panel_kernel<<<batch, NT, panel_smem(n, w), st>>>(n, k0, w, A, sA, perm, info, active); count_launch();
@@ -280,12 +304,12 @@ bt_status zinv(cudaStream_t st, int n, zd* A, long long sA, int batch, int* info
     Operand P{A + k0, n, sA, BT_OP_N};
     if (k0 > 0) {
       Operand Tl{T, n, sT, BT_OP_N};
-      BT_TRY(zgemm(st, n, k0, w, zmake(1.0, 0.0), P, Tl, zmake(1.0, 0.0), A, n, sA, batch, active));
+      BT_TRY(gemm(E, st, n, k0, w, zmake(1.0, 0.0), P, Tl, zmake(1.0, 0.0), A, n, sA, batch, active));
     }
     const int c1 = k0 + w;
     if (c1 < n) {
       Operand Tr{T + c1, n, sT, BT_OP_N};
-      BT_TRY(zgemm(st, n, n - c1, w, zmake(1.0, 0.0), P, Tr, zmake(1.0, 0.0), A + c1, n, sA, batch, active));
+      BT_TRY(gemm(E, st, n, n - c1, w, zmake(1.0, 0.0), P, Tr, zmake(1.0, 0.0), A + c1, n, sA, batch, active));
     }
   }
   dim3 g((n + 255) / 256, batch);

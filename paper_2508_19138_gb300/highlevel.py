@@ -29,11 +29,13 @@ class GSolver:
     def __init__(self, nb: int, bs: int, max_energies: int, eta: float, kT: float = 0.025, mu_left: float = 0.0,
                  mu_right: float = 0.0, obc: bool = True, precision: int = N.BT_FP64, split_slices: int = 0,
                  symmetrize: bool = True, decim_tol: float = 1e-14, decim_maxit: int = 100, stream=None,
-                 hbm_budget_bytes: int = 0, device: str = "cuda"):
+                 hbm_budget_bytes: int = 0, device: str = "cuda", obc_memo: bool = False, memo_nfpi: int = 0,
+                 memo_capacity: int = 0, split_scope: int = 0):
         self.nb, self.bs, self.max_energies = nb, bs, max_energies
         self.device = device
         self.desc = make_desc(nb, bs, max_energies, N.BT_SYS_G, precision, split_slices, symmetrize, obc, eta, kT,
-                              mu_left, mu_right, decim_tol, decim_maxit, hbm_budget_bytes)
+                              mu_left, mu_right, decim_tol, decim_maxit, hbm_budget_bytes, obc_memo, memo_nfpi,
+                              memo_capacity, split_scope)
         self.ctx = bt_selinv_create(self.desc, stream)
         self.H = self.S = self.sigR = self.sigL = self.sigG = None
 

@@ -1,0 +1,66 @@
+"""Runs one building-block kernel of the library at a given launch shape, for profiling:
+
+    python -m paper_2508_19138_gb300.kernel_driver --kernel zgemm --bs 416 --batch 32 --reps 3
+    python -m paper_2508_19138_gb300.kernel_driver --kernel split --bs 416 --batch 32 --slices 6
+    python -m paper_2508_19138_gb300.kernel_driver --kernel zinv --bs 416 --batch 32
+
+Inputs are random complex128 blocks already on the device; each kernel is launched `--reps`
+times on the current stream and its mean time is printed (CUDA events)."""
+from __future__ import annotations
+
+import argparse
+import json
+
+
+def main():
+    import torch
+
+    import paper_2508_19138_gb300 as pkg
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--kernel", choices=["zgemm", "split", "zinv"], required=True)
+    ap.add_argument("--bs", type=int, default=416)
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--slices", type=int, default=6)
+    a = ap.parse_args()
+    pkg.library()
+    b, n = a.batch, a.bs
+    g = torch.Generator(device="cuda").manual_seed(1)
+    A = torch.randn(b, n, n, dtype=torch.complex128, device="cuda", generator=g)
+    B = torch.randn(b, n, n, dtype=torch.complex128, device="cuda", generator=g)
+    C = torch.empty_like(A)
+    ws = None
+    if a.kernel == "split":
+        ws = torch.empty(pkg.bt_split_zgemm_workspace_bytes(n, n, n, a.slices, b), dtype=torch.uint8, device="cuda")
+    info = torch.zeros(b, dtype=torch.int32, device="cuda")
+    if a.kernel == "zinv":
+        A += 4.0 * torch.eye(n, dtype=torch.complex128, device="cuda")
+        ws = torch.empty(max(1, pkg.bt_zinv_workspace_bytes(n, b)), dtype=torch.uint8, device="cuda")
+    Ainv = A.clone()
+
+    def run():
+        if a.kernel == "zgemm":
+            pkg.bt_zgemm_batched(n, n, n, 1.0, A, n, n * n, 0, B, n, n * n, 0, 0.0, C, n, n * n, b)
+        elif a.kernel == "split":
+            pkg.bt_split_zgemm_batched(n, n, n, 1.0, A, n, n * n, 0, B, n, n * n, 0, 0.0, C, n, n * n, b, a.slices,
+                                       workspace=ws)
+        else:
+            Ainv.copy_(A)
+            pkg.bt_zinv_batched(n, Ainv, n * n, b, info, workspace=ws)
+
+    run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.reps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.reps
+    flops = 8.0 * n ** 3 * b
+    print(json.dumps({"kernel": a.kernel, "bs": n, "batch": b, "ms": ms, "fp64_eq_tflops": flops / ms / 1e9,
+                      "slices": a.slices if a.kernel == "split" else None}))
+
+
+if __name__ == "__main__":
+    main()

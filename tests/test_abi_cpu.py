@@ -53,7 +53,7 @@ def test_workspace_sizes_host_logic(lib):
     assert pkg.bt_selinv_workspace_bytes(d2) > n1 > 0
     # blocked inverse needs pivots + panel copy, small inverse none
     assert pkg.bt_zinv_workspace_bytes(32, 10) == 0
-    assert pkg.bt_zinv_workspace_bytes(416, 10) >= 10 * 416 * 4 + 10 * 32 * 416 * 16
+    assert pkg.bt_zinv_workspace_bytes(416, 10) >= 10 * 416 * 4 + 10 * 16 * 416 * 16
     assert pkg.bt_decimate_workspace_bytes(32, 4) >= 10 * 4 * 32 * 32 * 16
 
 

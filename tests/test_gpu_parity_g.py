@@ -212,3 +212,26 @@ def test_split_precision_path(maker):
     for e in range(len(s.energies)):
         _, bad = compare_g_derived(res, s, e, e, tol=TOL_SPLIT)
         assert not bad, f"e={e}: {bad}"
+
+
+def test_split_scope_all_products():
+    """split_scope = 1: also the block-inversion updates and the decimation products run as
+    sliced tensor-core products (the default keeps them FP64)."""
+    import torch
+    from paper_2508_19138_gb300.highlevel import GSolver
+    s = synthetic.nanoribbon(nb=5, n_puc=4, puc=26, n_energies=6)  # bs = 104 > 96: blocked inverse
+    solver = GSolver(s.nb, s.bs, 3, s.eta, s.kT, s.mu_left, s.mu_right, precision=1, split_scope=1)
+    solver.set_inputs(s.H_diag, s.H_upper, s.sigR_diag, s.sigL_diag, s.sigG_diag)
+    outs, status = solver.solve(s.energies)
+    torch.cuda.synchronize()
+    res = {"status": status.cpu().numpy()}
+    for w, o in outs.items():
+        res[w + "_diag"] = o.diag.cpu().numpy()
+        res[w + "_upper"] = o.upper.cpu().numpy()
+        if o.lower is not None:
+            res[w + "_lower"] = o.lower.cpu().numpy()
+    solver.close()
+    assert (res["status"] == 0).all()
+    for e in range(len(s.energies)):
+        _, bad = compare_g_derived(res, s, e, e, tol=TOL_SPLIT)
+        assert not bad, f"e={e}: {bad}"

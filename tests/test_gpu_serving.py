@@ -1,0 +1,105 @@
+"""Serving (bt_server_*): requests of different device sizes submitted while others run; each
+result equals the same request solved alone (same kernels, same chunking), admission respects
+the arena budget, and latency statistics are reported."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+from gpu_util import block_errors
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(4, 24, 5), (3, 40, 3), (6, 16, 8), (5, 64, 4), (3, 24, 6), (4, 40, 2)]  # (nb, bs, energies)
+CHUNK = 4
+
+
+def _request_inputs(k, nb, bs, nE):
+    s = synthetic.random_device(1000 + k, nb, bs, nE)
+    return s
+
+
+def _tensors(s):
+    import torch
+    from paper_2508_19138_gb300 import BT, BTOut, BT_LAYOUT_BLOCKS, BT_SYM_HERMITIAN
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    H = BT(t(s.H_diag), t(s.H_upper), None, BT_LAYOUT_BLOCKS, BT_SYM_HERMITIAN, False)
+    nE, nb, bs = len(s.energies), s.nb, s.bs
+    mk = lambda *sh: torch.full(sh, float("nan"), dtype=torch.complex128, device="cuda")
+    outs = {"R": BTOut(mk(nE, nb, bs, bs), mk(nE, nb - 1, bs, bs), mk(nE, nb - 1, bs, bs)),
+            "L": BTOut(mk(nE, nb, bs, bs), mk(nE, nb - 1, bs, bs)),
+            "G": BTOut(mk(nE, nb, bs, bs), mk(nE, nb - 1, bs, bs))}
+    status = torch.full((nE,), -1, dtype=torch.int32, device="cuda")
+    return H, outs, status
+
+
+def _alone(s):
+    """The same request through a plain context with the server's chunking."""
+    import torch
+    from paper_2508_19138_gb300.highlevel import GSolver
+    solver = GSolver(s.nb, s.bs, min(CHUNK, len(s.energies)), s.eta, s.kT, s.mu_left, s.mu_right)
+    solver.set_inputs(s.H_diag, s.H_upper)
+    outs, status = solver.solve(s.energies)
+    torch.cuda.synchronize()
+    res = {w: (o.diag.cpu().numpy(), o.upper.cpu().numpy()) for w, o in outs.items()}
+    solver.close()
+    return res
+
+
+def test_mixed_stream_equals_alone():
+    import torch
+    import paper_2508_19138_gb300 as pkg
+    systems = [_request_inputs(k, *sh) for k, sh in enumerate(SHAPES)]
+    srv = pkg.bt_server_create(hbm_budget_bytes=2 << 30, max_active=3, max_energies_per_chunk=CHUNK)
+    tickets, held = [], []
+    for s in systems:
+        H, outs, status = _tensors(s)
+        held.append((outs, status))
+        tickets.append(pkg.bt_server_submit(srv, s.nb, s.bs, H, s.energies, status, outs["R"], outs["L"], outs["G"],
+                                            eta=s.eta, kT=s.kT, mu_left=s.mu_left, mu_right=s.mu_right))
+    for t in tickets:
+        assert pkg.bt_server_wait(srv, t, 300.0) == 2
+    stats = pkg.bt_server_get_stats(srv)
+    assert stats["completed"] == len(SHAPES) and stats["failed"] == 0
+    assert 0 < stats["p50_latency_s"] <= stats["p99_latency_s"]
+    assert stats["peak_active"] >= 2  # requests overlapped
+    assert stats["peak_bytes"] <= 2 << 30
+    pkg.bt_server_destroy(srv)
+    torch.cuda.synchronize()
+    for s, (outs, status) in zip(systems, held):
+        assert (status.cpu().numpy() == 0).all()
+        alone = _alone(s)
+        for w in "RLG":
+            assert np.array_equal(outs[w].diag.cpu().numpy(), alone[w][0])
+            assert np.array_equal(outs[w].upper.cpu().numpy(), alone[w][1])
+    # and one request against the oracle
+    s, (outs, _) = systems[0], held[0]
+    ref = oracle.solve_g(s, 2)
+    assert block_errors(outs["R"].diag.cpu().numpy()[2], ref["R_diag"]).max() < 1e-9
+
+
+def test_budget_admission_and_rejection():
+    import paper_2508_19138_gb300 as pkg
+    s_big = _request_inputs(50, 6, 64, 4)
+    s_small = _request_inputs(51, 3, 16, 4)
+    need = pkg.bt_selinv_workspace_bytes(pkg.make_desc(s_big.nb, s_big.bs, CHUNK))
+    # an arena that holds exactly one large request at a time
+    srv = pkg.bt_server_create(hbm_budget_bytes=need + 4096, max_active=4, max_energies_per_chunk=CHUNK)
+    H, outs, status = _tensors(s_big)
+    tickets = [pkg.bt_server_submit(srv, s_big.nb, s_big.bs, H, s_big.energies, status, outs["R"], None, None,
+                                    eta=s_big.eta, kT=s_big.kT)]
+    H2, outs2, status2 = _tensors(s_big)
+    tickets.append(pkg.bt_server_submit(srv, s_big.nb, s_big.bs, H2, s_big.energies, status2, outs2["R"], None,
+                                        None, eta=s_big.eta, kT=s_big.kT))
+    for t in tickets:
+        assert pkg.bt_server_wait(srv, t, 300.0) == 2
+    st = pkg.bt_server_get_stats(srv)
+    assert st["peak_active"] == 1 and st["peak_bytes"] <= need + 4096
+    # a request that can never fit is rejected at submit
+    s_huge = _request_inputs(52, 8, 200, 64)
+    H3, outs3, status3 = _tensors(s_small)
+    with pytest.raises(pkg.BTError) as ei:
+        pkg.bt_server_submit(srv, s_huge.nb, s_huge.bs, H3, s_huge.energies, status3, None, None, None)
+    assert ei.value.status == pkg.BT_ERR_BUDGET
+    assert pkg.bt_server_get_stats(srv)["rejected"] == 1
+    pkg.bt_server_destroy(srv)
