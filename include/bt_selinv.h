@@ -269,6 +269,23 @@ BT_API bt_status bt_zinv_workspace_bytes(int n, int batch, size_t* bytes);
 BT_API bt_status bt_zinv_batched(int n, void* A, long long strideA, int batch, int* info_device,
                           void* workspace, size_t workspace_bytes, void* stream);
 
+/* Allocation-free bt_zinv_batched (the paper has no counterpart: this is a service for callers
+ * that cannot allocate device memory when they invert, e.g. code running inside its own pool
+ * allocator or with all free memory already handed to an arena).  Same inputs, outputs and
+ * numerics as bt_zinv_batched, but the scratch is a fixed array of
+ * BT_ZINV_NOALLOC_SCRATCH_BYTES bytes inside the library (present on every GPU that loads the
+ * library until the process exits); the call itself never allocates.
+ *   - needs bt_zinv_workspace_bytes(n, batch) <= BT_ZINV_NOALLOC_SCRATCH_BYTES, else returns
+ *     BT_ERR_BUDGET and launches nothing (n <= 96 needs no scratch at all);
+ *   - the first call on a device, with that device current, looks up the array's device
+ *     address; make that first call before any stream capture;
+ *   - every call shares the array: calls that overlap on the GPU (other streams or threads)
+ *     race; calls on one stream are ordered.  The array keeps the last call's contents and
+ *     needs no clearing (every word is written before it is read). */
+#define BT_ZINV_NOALLOC_SCRATCH_BYTES (16u << 20)
+BT_API bt_status bt_zinv_batched_noalloc(int n, void* A, long long strideA, int batch, int* info_device,
+                                         void* stream);
+
 /* Surface Green's function of semi-infinite leads, x = (m - n x n')^{-1} (Eq. 4), by
  * Sancho-Rubio decimation for `batch` independent leads (m, n, n' each [batch][bs][bs]).
  * Writes x [batch][bs][bs] and the boundary block sigma = n x n' [batch][bs][bs];

@@ -67,6 +67,7 @@ SIGNATURES = {
                                _P, _SZ, _P],
     "bt_zinv_workspace_bytes": [_I, _I, C.POINTER(C.c_size_t)],
     "bt_zinv_batched": [_I, _P, _LL, _I, _P, _P, _SZ, _P],
+    "bt_zinv_batched_noalloc": [_I, _P, _LL, _I, _P, _P],
     "bt_decimate_workspace_bytes": [_I, _I, C.POINTER(C.c_size_t)],
     "bt_decimate_batched": [_I, _I, _P, _P, _P, _D, _I, _P, _P, _P, _P, _P, _SZ, _P],
 }

@@ -16,7 +16,7 @@ __all__ = [
     "BTError", "BT", "BTOut", "Context", "make_desc", "bt_selinv_workspace_bytes", "bt_selinv_create",
     "bt_selinv_solve", "bt_selinv_solve_host", "bt_selinv_destroy", "bt_selinv_last_error", "bt_selinv_get_stats",
     "bt_zgemm_batched", "bt_split_zgemm_workspace_bytes", "bt_split_zgemm_batched", "bt_zinv_workspace_bytes",
-    "bt_zinv_batched", "bt_decimate_workspace_bytes", "bt_decimate_batched", "library",
+    "bt_zinv_batched", "bt_zinv_batched_noalloc", "bt_decimate_workspace_bytes", "bt_decimate_batched", "library",
 ]
 
 
@@ -243,6 +243,16 @@ def bt_zinv_batched(n, A, strideA, batch, info, workspace=None, stream=None) -> 
     rc = N.load().bt_zinv_batched(n, _ptr(A, torch.complex128), strideA, batch, _ptr(info, torch.int32),
                                   _ptr(workspace), nbytes if workspace is not None else 0, _stream(stream))
     _check(rc, None, "zinv")
+
+
+def bt_zinv_batched_noalloc(n, A, strideA, batch, info, stream=None) -> None:
+    """In-place batched inverse whose scratch is a fixed array inside the library (for callers
+    that must not allocate device memory at this point); raises BTError(BT_ERR_BUDGET) when the
+    request needs more than BT_ZINV_NOALLOC_SCRATCH_BYTES of scratch."""
+    torch = _torch()
+    rc = N.load().bt_zinv_batched_noalloc(n, _ptr(A, torch.complex128), strideA, batch, _ptr(info, torch.int32),
+                                          _stream(stream))
+    _check(rc, None, "zinv_noalloc")
 
 
 def bt_decimate_workspace_bytes(bs, batch) -> int:
