@@ -30,6 +30,14 @@ UNIT = "energy points/s"
 # FP64 roofline denominator: nominal GB300 FP64 rate (1.25 TFLOP/s, profiling recipe table); the
 # FP64 FMA pipe measured 1.20 TFLOP/s on this machine.
 FP64_PEAK_TFLOPS = 1.25
+# bf16 dense tensor peak measured on this machine (MEASURED_PEAKS.json, burst), used for the
+# split-precision kernel's roofline; read from the file when present.
+BF16_PEAK_TFLOPS = 1903.6
+try:
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as _f:
+        BF16_PEAK_TFLOPS = float(json.load(_f).get("bf16_tflops", BF16_PEAK_TFLOPS))
+except (OSError, ValueError):
+    pass
 # dram bytes (read + write) per launch of the dominant kernel from the committed ncu capture of
 # the same launch shape (profiles/); None until captured for the current kernel.
 ZGEMM_TRAFFIC_BYTES = None
@@ -52,6 +60,7 @@ def parse():
     p.add_argument("--split-scope", type=int, default=0,
                    help="split: 0 = sweep products only, 1 = also inversion updates and decimation")
     p.add_argument("--memo", action="store_true", help="contact memoization across steps of the same energies")
+    p.add_argument("--no-split-line", action="store_true", help="skip the split-precision measurements")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-blocks", type=int, default=10)
@@ -284,6 +293,66 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = run_e2e(args, pkg, sysg, solver, eps, rank, world, barrier, dist)
 
+    # ---- the same workload on the split-precision paths (config 3) ----
+    split_lines = None
+    if precision == pkg.BT_FP64 and not args.no_split_line:
+        split_lines = {}
+        for scope in (0, 1):
+            sp = GSolver(sysg.nb, sysg.bs, eps, sysg.eta, sysg.kT, sysg.mu_left, sysg.mu_right, obc=True,
+                         precision=pkg.BT_SPLIT, split_slices=args.slices, stream=stream, split_scope=scope)
+            with torch.cuda.stream(stream):
+                sp.set_inputs(sysg.H_diag, sysg.H_upper, sysg.sigR_diag, sysg.sigL_diag, sysg.sigG_diag)
+            torch.cuda.synchronize()
+
+            def sp_step(step):
+                e0, e1 = batch_range(step)
+                sp.solve(sysg.energies[e0:e1], outs, status, sig_range=(e0, e1))
+
+            for w in range(args.warmup):
+                sp_step(w)
+            barrier()
+            q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            q0.record(stream)
+            for s in range(args.steps):
+                sp_step(args.warmup + s)
+            q1.record(stream)
+            barrier()
+            ms = replicas.max_over_ranks(q0.elapsed_time(q1), dist, device="cuda")
+            flops_sp = sp.stats()["flops_model"]
+            split_lines[f"scope{scope}"] = {
+                "value": eps * args.steps * world / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
+                "fp64_eq_tflops": flops_sp / (ms / args.steps / 1e3) / 1e12,
+                "nonzero_status": int((status.cpu().numpy() != 0).sum()),
+                "what": ("sweep products sliced (bf16 tcgen05, 6 slices); inversions and decimation FP64"
+                         if scope == 0 else "every block product sliced; inversion panels and pivots FP64")}
+            sp.close()
+        # tensor-core kernel at the sweep's launch shape (slicing kernels included in the time)
+        A = torch.randn(eps, bs, bs, dtype=torch.complex128, device="cuda")
+        B = torch.randn(eps, bs, bs, dtype=torch.complex128, device="cuda")
+        Cm = torch.empty_like(A)
+        S = args.slices or 6
+        ws = torch.empty(pkg.bt_split_zgemm_workspace_bytes(bs, bs, bs, S, eps), dtype=torch.uint8, device="cuda")
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                pkg.bt_split_zgemm_batched(bs, bs, bs, 1.0, A, bs, bs * bs, 0, B, bs, bs * bs, 0, 0.0, Cm, bs, bs * bs,
+                                           eps, S, workspace=ws, stream=stream)
+            k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            k0.record(stream)
+            for _ in range(reps):
+                pkg.bt_split_zgemm_batched(bs, bs, bs, 1.0, A, bs, bs * bs, 0, B, bs, bs * bs, 0, 0.0, Cm, bs, bs * bs,
+                                           eps, S, workspace=ws, stream=stream)
+            k1.record(stream)
+        torch.cuda.synchronize()
+        sms = k0.elapsed_time(k1) / reps
+        pairs = S * (S + 1) // 2
+        bf16 = pairs * 2.0 * (2 * bs) * bs * (2 * bs) * eps / (sms / 1e3) / 1e12
+        split_lines["roofline"] = {"bound": "tensor", "achieved": bf16, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                   "frac": bf16 / BF16_PEAK_TFLOPS, "traffic": None,
+                                   "kernel": f"bt_split_zgemm_batched {bs}^3 x {eps}, {S} slices ({pairs} bf16 products)",
+                                   "fp64_eq_tflops": 8.0 * bs ** 3 * eps / (sms / 1e3) / 1e12, "launch_ms": sms,
+                                   "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)"}
+        del A, B, Cm, ws
+
     line = None
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -301,7 +370,7 @@ def run_ours(args):
                 "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
                 "decim_iterations_per_step": (st1["decim_iterations"] - st0["decim_iterations"]) / args.steps,
                 "nonzero_status": bad, "roofline": roofline, "clocks": clk, "gpu_launches": launches,
-                "e2e": e2e}
+                "e2e": e2e, "split": split_lines}
         if not args.no_cpu_baseline and world == 1:
             dt, scale, k = cpu_oracle_sample(sysg, args.cpu_sample_blocks, 101 % nE)
             line["cpu_baseline"] = {
@@ -329,7 +398,8 @@ def run_e2e(args, pkg, sysg, solver, eps, rank, world, barrier, dist):
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     Hd, Hu = pin(sysg.H_diag), pin(sysg.H_upper)
     H = BT(Hd, Hu, None, BT_LAYOUT_BLOCKS, BT_SYM_HERMITIAN, False)
-    sR, sL, sG = pin(sysg.sigR_diag), pin(sysg.sigL_diag), pin(sysg.sigG_diag)
+    pin_opt = lambda a: None if a is None else pin(a)
+    sR, sL, sG = pin_opt(sysg.sigR_diag), pin_opt(sysg.sigL_diag), pin_opt(sysg.sigG_diag)
     mk = lambda shape: torch.empty(shape, dtype=torch.complex128).pin_memory()
     oR = BTOut(mk((eps, nb, bs, bs)), mk((eps, nb - 1, bs, bs)), mk((eps, nb - 1, bs, bs)))
     oL = BTOut(mk((eps, nb, bs, bs)), mk((eps, nb - 1, bs, bs)), None)
@@ -340,13 +410,14 @@ def run_e2e(args, pkg, sysg, solver, eps, rank, world, barrier, dist):
 
     from paper_2508_19138_gb300 import replicas
 
+    def sig(x, e0, e1, sym):
+        return None if x is None else BT(x[e0:e1], None, None, BT_LAYOUT_DIAGVEC, sym, True)
+
     def step(s):
         j = replicas.batch_index(rank, s + 3, n_batches)
         e0, e1 = j * eps, j * eps + eps
-        bt_selinv_solve_host(solver.ctx, H, None, BT(sR[e0:e1], None, None, BT_LAYOUT_DIAGVEC, BT_SYM_GENERAL, True),
-                             BT(sL[e0:e1], None, None, BT_LAYOUT_DIAGVEC, BT_SYM_ANTIHERMITIAN, True),
-                             BT(sG[e0:e1], None, None, BT_LAYOUT_DIAGVEC, BT_SYM_ANTIHERMITIAN, True),
-                             sysg.energies[e0:e1], oR, oL, oG, status)
+        bt_selinv_solve_host(solver.ctx, H, None, sig(sR, e0, e1, BT_SYM_GENERAL), sig(sL, e0, e1, BT_SYM_ANTIHERMITIAN),
+                             sig(sG, e0, e1, BT_SYM_ANTIHERMITIAN), sysg.energies[e0:e1], oR, oL, oG, status)
 
     step(0)  # warm (staging allocation)
     barrier()
@@ -356,7 +427,8 @@ def run_e2e(args, pkg, sysg, solver, eps, rank, world, barrier, dist):
     barrier()
     dt = replicas.max_over_ranks(time.perf_counter() - t0, dist, device="cuda")
     c16 = 16
-    h2d = (Hd.numel() + Hu.numel()) * c16 + 3 * eps * nb * bs * c16 + 8 * eps
+    n_sig = sum(x is not None for x in (sR, sL, sG))
+    h2d = (Hd.numel() + Hu.numel()) * c16 + n_sig * eps * nb * bs * c16 + 8 * eps
     d2h = (oR.diag.numel() + oR.upper.numel() + oR.lower.numel() + 2 * (oL.diag.numel() + oL.upper.numel())) * c16 \
         + 4 * eps
     return {"value": eps * args.steps * world / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),

@@ -45,7 +45,7 @@ constexpr int kExactD = 5;       // pairs with s + t <= kExactD get their own ac
 constexpr int kFixShift = 36;    // int64 fixed point: units of 2^-36 of a leading digit product
 constexpr int kTileM = 128;
 constexpr int kKBlock = 64;      // bf16 per 128-byte swizzle row
-constexpr int kStages = 4;
+constexpr int kStages = 7;       // 7 x (16 + 16) KB covers the TMA latency at 224 clocks per stage
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kMaxKp = 1040;     // K' bound for exact fp32 accumulation of one slice pair
@@ -74,6 +74,8 @@ struct MmaParams {
   int complex_coef;  // alpha or beta has an imaginary part
   int* err;          // per batch entry error slot (may be null)
   const int* active; // batch entries with active[b] == 0 are skipped (may be null)
+  int a_shared;      // op(A) / op(B) shared by every batch entry: sliced once (batch index 0)
+  int b_shared;
   Schedule sched;
 };
 
@@ -191,8 +193,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int pi = it / KB, kb = it - pi * KB;
         if (!ptx::mbar_wait_bounded(&empty[stage], phase ^ 1u, abort_flag, kWaitLimitNs)) { fail(); break; }
         ptx::mbar_arrive_expect_tx(&full[stage], kABytes + kBBytes);
-        ptx::tma_load_3d(sA + stage * kABytes, &tmA, &full[stage], kb * kKBlock, m0, b * p.S + (sc.t[pi] - 1));
-        ptx::tma_load_3d(sB + stage * kBBytes, &tmB, &full[stage], kb * kKBlock, n0, b * p.S + (sc.s[pi] - 1));
+        ptx::tma_load_3d(sA + stage * kABytes, &tmA, &full[stage], kb * kKBlock, m0,
+                         (p.b_shared ? 0 : b) * p.S + (sc.t[pi] - 1));
+        ptx::tma_load_3d(sB + stage * kBBytes, &tmB, &full[stage], kb * kKBlock, n0,
+                         (p.a_shared ? 0 : b) * p.S + (sc.s[pi] - 1));
         ++issued;
         if (++stage == kStages) { stage = 0; phase ^= 1u; }
       }
@@ -282,7 +286,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool row_ok = jp < p.n2;
       const int j = jp >> 1, part = jp & 1;
       const int n = p.n2 >> 1;
-      const int EB = row_ok ? p.eB[(long long)b * n + j] : 1;
+      const int EB = row_ok ? p.eB[(long long)(p.b_shared ? 0 : b) * n + j] : 1;
       zd* Cb = p.C + p.sC * b;
       const double ar = p.alpha.x, ai = p.alpha.y, br = p.beta.x, bi = p.beta.y;
 #pragma unroll
@@ -292,7 +296,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         double v = 0.0;
         int EA = 1;
         if (ok_el) {
-          EA = p.eA[(long long)b * p.m + i];
+          EA = p.eA[(long long)(p.a_shared ? 0 : b) * p.m + i];
           // value = acc * 2^-36 * 2^(eA + eB - 14), eA = EA - 1022, eB = EB - 1022
           v = fix_to_double(acc[c], EA + EB - 2044 - 14 - kFixShift);
           if (EA >= 2047 || EB >= 2047) v = __longlong_as_double(0x7ff8000000000000ll);
@@ -667,24 +671,29 @@ bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A,
     Operand a = A, bop = B;
     a.p = A.op == BT_OP_N ? A.p + k0 : A.p + (long long)k0 * A.ld;
     bop.p = B.op == BT_OP_N ? B.p + (long long)k0 * B.ld : B.p + k0;
-    BT_CUDA_TRY(cudaMemsetAsync(w.eA, 0, sizeof(int) * (size_t)batch * m, st));
-    BT_CUDA_TRY(cudaMemsetAsync(w.eB, 0, sizeof(int) * (size_t)batch * n, st));
+    // an operand shared by every batch entry (stride 0, e.g. a Hamiltonian block) is sliced once
+    const bool a_shared = A.stride == 0 && batch > 1, b_shared = B.stride == 0 && batch > 1;
+    const int ba = a_shared ? 1 : batch, bb = b_shared ? 1 : batch;
+    const int* act_a = a_shared ? nullptr : active;
+    const int* act_b = b_shared ? nullptr : active;
+    BT_CUDA_TRY(cudaMemsetAsync(w.eA, 0, sizeof(int) * (size_t)ba * m, st));
+    BT_CUDA_TRY(cudaMemsetAsync(w.eB, 0, sizeof(int) * (size_t)bb * n, st));
     {
-      dim3 g((kc + 31) / 32, (m + 31) / 32, batch);
-      exp_max_kernel<<<g, 256, 0, st>>>(m, kc, a.p, a.ld, a.stride, a.op, w.eA, m, nullptr, 0, active);
+      dim3 g((kc + 31) / 32, (m + 31) / 32, ba);
+      exp_max_kernel<<<g, 256, 0, st>>>(m, kc, a.p, a.ld, a.stride, a.op, w.eA, m, nullptr, 0, act_a);
       count_launch();
-      dim3 g2((n + 31) / 32, (kc + 31) / 32, batch);
-      exp_max_kernel<<<g2, 256, 0, st>>>(kc, n, bop.p, bop.ld, bop.stride, bop.op, nullptr, 0, w.eB, n, active);
+      dim3 g2((n + 31) / 32, (kc + 31) / 32, bb);
+      exp_max_kernel<<<g2, 256, 0, st>>>(kc, n, bop.p, bop.ld, bop.stride, bop.op, nullptr, 0, w.eB, n, act_b);
       count_launch();
       BT_CUDA_TRY(cudaGetLastError());
     }
     {
-      dim3 g((Kp / 2 + 31) / 32, (mp + 31) / 32, batch);
-      slice_rows_kernel<<<g, 256, 0, st>>>(m, mp, kc, Kp, a.p, a.ld, a.stride, a.op, w.eA, S, w.At, active);
+      dim3 g((Kp / 2 + 31) / 32, (mp + 31) / 32, ba);
+      slice_rows_kernel<<<g, 256, 0, st>>>(m, mp, kc, Kp, a.p, a.ld, a.stride, a.op, w.eA, S, w.At, act_a);
       count_launch();
-      dim3 g2((Kp / 2 + 31) / 32, (n2p / 2 + 31) / 32, batch);
+      dim3 g2((Kp / 2 + 31) / 32, (n2p / 2 + 31) / 32, bb);
       slice_cols_kernel<<<g2, 256, 0, st>>>(kc, n, n2p / 2, Kp, bop.p, bop.ld, bop.stride, bop.op, w.eB, S, w.Bt,
-                                            active);
+                                            act_b);
       count_launch();
       BT_CUDA_TRY(cudaGetLastError());
     }
@@ -707,6 +716,8 @@ bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A,
     p.complex_coef = (p.alpha.y != 0.0 || p.beta.y != 0.0) ? 1 : 0;
     p.err = nullptr;
     p.active = active;
+    p.a_shared = a_shared ? 1 : 0;
+    p.b_shared = b_shared ? 1 : 0;
     p.sched = make_schedule(S);
     BT_TRY(launch_mma_nt(nt, st, mA, mB, p, batch));
   }

@@ -13,6 +13,8 @@
 //    then receive the panel's row exchanges and the rank-kb update
 //        A[:, C] += P[:, K] * A_old[K, C]   (rows K of C zeroed first)
 //    as one batched FP64 GEMM, so the O(n^3) part runs on the GEMM kernel.
+#include <cooperative_groups.h>
+
 #include <mutex>
 
 #include "bt_common.cuh"
@@ -148,6 +150,132 @@ __global__ void __launch_bounds__(NT) zinv_small_kernel(int n, zd* __restrict__ 
   __syncthreads();
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) Ag[e] = P[(e / n) * ld + (e % n)];
   if (threadIdx.x == 0 && code && info && info[b] == 0) info[b] = code;
+}
+
+// Panel of kb columns eliminated by a cluster of CL CTAs: CTA r of the cluster holds rows
+// [r R, r R + R) of the panel in its shared memory (R = ceil(n / CL)), so the panel's FP64
+// updates use CL SMs instead of one.  Per column: each CTA proposes its best pivot candidate,
+// all CTAs read every candidate through distributed shared memory and agree on the same pivot
+// (max |re| + |im|, first index on ties), read the pivot row and exchange rows j and p through
+// DSMEM, then update their own rows.  Two cluster barriers per column; no spin-waits.
+template <int CL>
+__global__ void __launch_bounds__(NT) gj_panel_cluster_kernel(int n, int k0, int kb, zd* __restrict__ A,
+                                                              long long sA, int* __restrict__ perm_all, int* info,
+                                                              const int* __restrict__ active) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int b = blockIdx.x / CL;
+  if (active && active[b] == 0) return;  // uniform over the cluster
+  const int R = (n + CL - 1) / CL;
+  const int r0 = rank * R;
+  const int rows = max(0, min(R, n - r0));
+  const int ld = kb + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  zd* P = reinterpret_cast<zd*>(smem_raw);  // [R][ld]
+  zd* colj = P + (size_t)R * ld;            // [R]
+  zd* rowj = colj + R;                      // [kb]
+  zd* pivrow = rowj + kb;                   // [kb]
+  zd* swapbuf = pivrow + kb;                // [kb]
+  __shared__ double cand_v;
+  __shared__ int cand_i;
+  __shared__ double sv[32];
+  __shared__ int si[32];
+  __shared__ int code;
+  __shared__ int gp;
+  zd* Ag = A + sA * b;
+  int* perm = perm_all + (long long)n * b;
+  if (threadIdx.x == 0) code = 0;
+  for (int e = threadIdx.x; e < rows * kb; e += blockDim.x) {
+    const int r = e / kb, c = e - r * kb;
+    P[r * ld + c] = Ag[(long long)(r0 + r) * n + k0 + c];
+  }
+  __syncthreads();
+  for (int jj = 0; jj < kb; ++jj) {
+    const int j = k0 + jj;
+    // local pivot candidate among rows >= j
+    double best = -1.0;
+    int bi = 0x7fffffff;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+      if (r0 + r < j) continue;
+      double v = zabs1(P[r * ld + jj]);
+      if (!(v <= 1.0e308)) v = 1.0e308;
+      if (v > best) { best = v; bi = r0 + r; }
+    }
+    block_argmax(best, bi, sv, si);
+    if (threadIdx.x == 0) { cand_v = best; cand_i = bi; }
+    cluster.sync();  // candidates visible
+    if (threadIdx.x < 32) {  // lane q reads CTA q's candidate (all remote loads in parallel)
+      const int q = threadIdx.x;
+      double v = q < CL ? *cluster.map_shared_rank(&cand_v, q) : -1.0;
+      int p = q < CL ? *cluster.map_shared_rank(&cand_i, q) : 0x7fffffff;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, v, off);
+        const int oi = __shfl_down_sync(0xffffffffu, p, off);
+        if (ov > v || (ov == v && oi < p)) { v = ov; p = oi; }
+      }
+      if (q == 0) gp = p;
+    }
+    __syncthreads();
+    const int p = gp;
+    const int own_p = p / R, own_j = j / R;
+    {
+      const zd* rp = cluster.map_shared_rank(P, own_p) + (size_t)(p - own_p * R) * ld;
+      for (int c = threadIdx.x; c < kb; c += blockDim.x) pivrow[c] = rp[c];
+      if (rank == own_p && p != j) {
+        const zd* rj = cluster.map_shared_rank(P, own_j) + (size_t)(j - own_j * R) * ld;
+        for (int c = threadIdx.x; c < kb; c += blockDim.x) swapbuf[c] = rj[c];
+      }
+    }
+    cluster.sync();  // every read of rows p and j and of the candidates is done
+    if (p != j) {
+      if (rank == own_j)
+        for (int c = threadIdx.x; c < kb; c += blockDim.x) P[(j - r0) * ld + c] = pivrow[c];
+      if (rank == own_p)
+        for (int c = threadIdx.x; c < kb; c += blockDim.x) P[(p - r0) * ld + c] = swapbuf[c];
+    }
+    const zd piv = pivrow[jj];
+    const int pc = pivot_code(piv);
+    if (pc && threadIdx.x == 0 && code == 0) code = pc;
+    const zd ip = pc ? zmake(0.0, 0.0) : zinv(piv);
+    if (rank == 0 && threadIdx.x == 0) perm[j] = p;
+    for (int c = threadIdx.x; c < kb; c += blockDim.x) rowj[c] = zmul(pivrow[c], ip);
+    __syncthreads();
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) colj[r] = P[r * ld + jj];
+    __syncthreads();
+    for (int e = threadIdx.x; e < rows * kb; e += blockDim.x) {
+      const int r = e / kb, c = e - r * kb;
+      zd* pe = P + r * ld + c;
+      if (r0 + r == j) {
+        *pe = (c == jj) ? ip : rowj[c];
+      } else if (c == jj) {
+        *pe = zmul(zmake(-colj[r].x, -colj[r].y), ip);
+      } else {
+        zd a = *pe;
+        const zd f = colj[r], g = rowj[c];
+        a.x = fma(-f.x, g.x, a.x);
+        a.x = fma(f.y, g.y, a.x);
+        a.y = fma(-f.x, g.y, a.y);
+        a.y = fma(-f.y, g.x, a.y);
+        *pe = a;
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < rows * kb; e += blockDim.x) {
+    const int r = e / kb, c = e - r * kb;
+    Ag[(long long)(r0 + r) * n + k0 + c] = P[r * ld + c];
+  }
+  if (rank == 0 && threadIdx.x == 0 && code && info && info[b] == 0) info[b] = code;
+  cluster.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+constexpr int kPanelCluster = 8;
+constexpr int kClusterMinN = 192;  // below this a single CTA holds the panel comfortably
+size_t cluster_panel_smem(int n, int kb) {
+  const int R = (n + kPanelCluster - 1) / kPanelCluster;
+  return (size_t)R * (kb + 1) * sizeof(zd) + (size_t)(R + 3 * kb) * sizeof(zd) + 16;
 }
 
 // Panel of kb columns starting at k0: eliminated in shared memory, written back in place.
@@ -293,9 +421,29 @@ bt_status zinv(cudaStream_t st, int n, zd* A, long long sA, int batch, int* info
   size_t perm_bytes = ((size_t)batch * n * sizeof(int) + 255) / 256 * 256;
   zd* T = reinterpret_cast<zd*>(static_cast<char*>(ws) + perm_bytes);
   const long long sT = (long long)kb * n;
+  const bool clustered = n >= kClusterMinN;
   for (int k0 = 0; k0 < n; k0 += kb) {
     const int w = (n - k0) < kb ? (n - k0) : kb;
-    gj_panel_kernel<<<batch, NT, panel_smem(n, w), st>>>(n, k0, w, A, sA, perm, info, active); count_launch();
+    if (clustered) {
+      // one cluster of kPanelCluster CTAs per matrix (rows of the panel split across SMs)
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)(batch * kPanelCluster));
+      cfg.blockDim = dim3(NT);
+      cfg.dynamicSmemBytes = cluster_panel_smem(n, w);
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = kPanelCluster;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      BT_CUDA_TRY(cudaLaunchKernelEx(&cfg, gj_panel_cluster_kernel<kPanelCluster>, n, k0, w, A, sA, perm, info,
+                                     active));
+      count_launch();
+    } else {
+      gj_panel_kernel<<<batch, NT, panel_smem(n, w), st>>>(n, k0, w, A, sA, perm, info, active); count_launch();
+    }
     BT_CUDA_TRY(cudaGetLastError());
     dim3 g((n + 255) / 256, batch);
     gj_swap_copy_kernel<<<g, 256, 0, st>>>(n, k0, w, A, sA, perm, T, sT, active); count_launch();

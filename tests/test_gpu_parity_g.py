@@ -53,6 +53,17 @@ def test_single_block_no_contacts():
         assert np.linalg.norm(res["R_diag"][e, 0] - np.linalg.inv(M)) / np.linalg.norm(np.linalg.inv(M)) < 1e-12
 
 
+def test_nanoribbon_wide_blocks_cluster_panels():
+    """b = 200 >= 192: the inversions use the cluster-parallel panels; FP64 and split."""
+    s = synthetic.nanoribbon(nb=3, n_puc=2, puc=100, n_energies=3)
+    for precision, tol in ((0, TOL_FP64), (1, TOL_SPLIT)):
+        res = run_g(s, precision=precision)
+        assert (res["status"] == 0).all()
+        for e in range(3):
+            _, bad = compare_g_derived(res, s, e, e, tol=tol)
+            assert not bad, f"precision={precision} e={e}: {bad}"
+
+
 def test_nanoribbon_diagonal_sigma():
     """Nanoribbon structure (sparse-in-dense H, periodic, diagonal scattering self-energies)."""
     s = synthetic.nanoribbon(nb=6, n_puc=2, puc=26, n_energies=6)

@@ -78,6 +78,32 @@ def test_mixed_stream_equals_alone():
     assert block_errors(outs["R"].diag.cpu().numpy()[2], ref["R_diag"]).max() < 1e-9
 
 
+def test_failed_request_is_reported_and_others_complete():
+    """A request that fails inside the server (here: its Hamiltonian lacks the off-diagonal
+    blocks, which the solve rejects after admission) ends in state 3 with its error code;
+    requests around it complete."""
+    import paper_2508_19138_gb300 as pkg
+    good = [_request_inputs(60 + k, 3, 16, 3) for k in range(2)]
+    bad = _request_inputs(70, 3, 16, 3)
+    srv = pkg.bt_server_create(hbm_budget_bytes=1 << 30, max_active=2, max_energies_per_chunk=CHUNK)
+    held, tickets = [], []
+    for k, s in enumerate([good[0], bad, good[1]]):
+        H, outs, status = _tensors(s)
+        if s is bad:
+            H.upper = None  # injected fault: missing coupling blocks
+        held.append((H, status))
+        tickets.append(pkg.bt_server_submit(srv, s.nb, s.bs, H, s.energies, status, outs["R"], None, None,
+                                            eta=s.eta, kT=s.kT))
+    assert pkg.bt_server_wait(srv, tickets[0], 300.0) == 2
+    assert pkg.bt_server_wait(srv, tickets[2], 300.0) == 2
+    with pytest.raises(pkg.BTError) as ei:
+        pkg.bt_server_wait(srv, tickets[1], 300.0)
+    assert ei.value.status == pkg.BT_ERR_INVALID_ARG
+    st = pkg.bt_server_get_stats(srv)
+    assert st["completed"] == 2 and st["failed"] == 1
+    pkg.bt_server_destroy(srv)
+
+
 def test_budget_admission_and_rejection():
     import paper_2508_19138_gb300 as pkg
     s_big = _request_inputs(50, 6, 64, 4)
