@@ -39,8 +39,10 @@ try:
 except (OSError, ValueError):
     pass
 # dram bytes (read + write) per launch of the dominant kernel from the committed ncu capture of
-# the same launch shape (profiles/); None until captured for the current kernel.
-ZGEMM_TRAFFIC_BYTES = None
+# the same launch shape (profiles/zgemm_fp64_416x16.md: 88.7 MB read + 22.3 MB written, batch 16);
+# valid only for that shape and the kernel version captured.
+ZGEMM_TRAFFIC_BYTES = 111_007_232
+ZGEMM_TRAFFIC_SHAPE = (416, 16)
 
 
 def parse():
@@ -283,7 +285,8 @@ def run_ours(args):
     kms = k0.elapsed_time(k1) / reps
     achieved = 8.0 * bs ** 3 * eps / (kms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": ZGEMM_TRAFFIC_BYTES,
+                "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": ZGEMM_TRAFFIC_BYTES if (bs, eps) == ZGEMM_TRAFFIC_SHAPE else None,
                 "kernel": f"zgemm_kernel (FP64 DFMA) {bs}^3 x {eps}", "launch_ms": kms,
                 "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe); measured FP64 FMA probe 1.20"}
     del A, B, Cm

@@ -9,24 +9,32 @@
 // gives (Bt At^T)[2j][i] = Re C[i][j], [2j+1][i] = Im C[i][j]: one real GEMM, M = 2n rows
 // (MMA "A" operand Bt), N = m columns (MMA "B" operand At), K = 2k, both operands K-major.
 //
-// Slicing.  Each row i of op(A) is scaled by 2^-eA_i (eA_i = max exponent of the row) and cut
-// into S digits of 7 bits by integer arithmetic on the IEEE fields (truncated fixed point with
-// 7S fraction bits); digit s is stored as bf16(sign * d_s * 2^(-7(s-1))), exact.  Columns of
-// op(B) likewise with eB_j.  A slice product of digits is an integer < K' * 127^2 < 2^24 for
-// K' <= 1040, so the tensor core's fp32 accumulation of a single slice pair is exact.
+// Slicing.  Each row i of op(A) is scaled by R_i = 2^(eA_i - 1022) (eA_i = largest biased
+// exponent in the row, so every component is below R_i), rounded to a fixed-point integer
+// X = round(|v| / R_i * 2^(7S-1)) by integer arithmetic on the IEEE fields, and written as S
+// balanced base-128 digits d_1..d_S in [-64, 64] (X = sum_s d_s 128^(S-s)); digit s is stored as
+// the bf16 integer sign * d_s.  Columns of op(B) likewise with eB_j.  Then
+//     v ~= R * 2^-6 * sum_s d_s 2^(-7(s-1)),
+// and a product of digits is an integer of magnitude <= 2^12.
 //
-// Accumulation.  Pairs (s, t) with s + t <= S + 1 are used.  Pairs with s + t <= 5 are
-// accumulated one per TMEM accumulator (exact); all remaining pairs share one accumulator
-// (their fp32 rounding is below 2^-45 of the leading term).  Every accumulator is drained into
-// per-thread int64 fixed-point sums (2^-36 units of the leading digit product), so the final
-// value is assembled without floating-point cancellation; the FP64 pipe is touched only for
-// the alpha / beta update of C.
+// Accumulation.  Pairs (s, t) with s + t <= S + 1 are used.  Each pair, over one K segment of at
+// most 960 real terms, is accumulated alone in a TMEM fp32 accumulator: its value is an integer
+// below 960 * 2^12 < 2^22, so the tensor core's fp32 sum is exact.  The drain adds 1.5 * 2^23 to
+// it (one FFMA, which also applies the 2^-p pre-scale of the low-order pairs); the bits of that
+// float are then 0x4B400000 + the integer, and one 32 x 32 -> 64-bit multiply-add accumulates
+// them with the pair's weight 2^(30 - 7(s+t-2) + p) into a per-thread uint64 fixed-point sum
+// (units of 2^-30 of a leading digit product, arithmetic mod 2^64).  The known sum of the
+// 0x4B400000 biases is subtracted once at the end, giving the exact (to 2^-30) two's-complement
+// value.  The FP64 pipe is touched only by the alpha / beta update of C, and not at all for
+// alpha = +-1, beta = 0.
 //
-// Kernel shape: one CTA per 128 x NT output tile of C^T and batch entry; warp 0 issues TMA
-// loads (3-D tensor maps over [batch*S][rows][K'], 128-byte swizzle), warp 1 issues the
-// tcgen05.mma instructions (M = 128, N = NT, K = 16) into a double-buffered TMEM accumulator,
-// warps 2..9 drain the accumulators and write C.  All waits are bounded in time; on a timeout
-// the CTA records BT_ERR_TIMEOUT, drains what it issued and frees its TMEM.
+// Kernel shape: a persistent grid of one CTA per SM walks the 128 x NT output tiles of C^T
+// (all batch entries); warp 0 issues TMA loads (3-D tensor maps over [batch*S][rows][K'],
+// 128-byte swizzle) through a ring of shared-memory stages, warp 1 issues tcgen05.mma (M = 128,
+// N = NT, K = 16) into a double-buffered TMEM accumulator, warps 2..17 drain the accumulators and
+// write C.  The ring and the accumulators run on across tiles, so the write of one tile overlaps
+// the MMAs of the next.  All waits are bounded in time; on a timeout the CTA records
+// BT_ERR_TIMEOUT, drains what it issued and frees its TMEM.
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
@@ -40,38 +48,54 @@ namespace {
 
 constexpr int kDigitBits = 7;
 constexpr int kMaxSlices = 8;
-constexpr int kMaxPairs = kMaxSlices * (kMaxSlices + 1) / 2;
-constexpr int kExactD = 5;       // pairs with s + t <= kExactD get their own accumulator
-constexpr int kFixShift = 36;    // int64 fixed point: units of 2^-36 of a leading digit product
+constexpr int kMaxGroups = 128;    // (pair, K segment) accumulations per tile
+constexpr int kSegBlocks = 15;     // K blocks per segment: 15 * 64 = 960 real terms, 960 * 2^12 < 2^22
+constexpr float kMagic = 12582912.0f;       // 1.5 * 2^23
+constexpr uint32_t kMagicBits = 0x4B400000u;
 constexpr int kTileM = 128;
 constexpr int kKBlock = 64;      // bf16 per 128-byte swizzle row
-constexpr int kStages = 7;       // 7 x (16 + 16) KB covers the TMA latency at 224 clocks per stage
-constexpr int kEpiWarps = 8;
+constexpr int kStages = 7;       // 7 x (16 + 14) KB of operand stages
+constexpr int kEpiWarps = 16;   // 4 lane quarters x 4 column quarters of the accumulator
 constexpr int kThreads = 64 + 32 * kEpiWarps;
-constexpr int kMaxKp = 1040;     // K' bound for exact fp32 accumulation of one slice pair
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
 
+// One accumulation group = one slice pair (s, t) over K blocks [kb0, kb1).
 struct Schedule {
-  int n_pairs;
   int n_groups;
-  unsigned char s[kMaxPairs];          // slice of op(A) (1-based)
-  unsigned char t[kMaxPairs];          // slice of op(B) (1-based)
-  unsigned char group_end[kMaxPairs];  // pairs [group_end[g-1], group_end[g]) form group g
+  unsigned char s[kMaxGroups];    // slice of op(A) (1-based)
+  unsigned char t[kMaxGroups];    // slice of op(B) (1-based)
+  unsigned char kb0[kMaxGroups];
+  unsigned char kb1[kMaxGroups];
+  unsigned char lsh[kMaxGroups];  // weight 2^(F - 7w) > 2^31: shift instead of multiply
+  uint32_t mult[kMaxGroups];      // weight 2^(F - 7w) <= 2^31 (after the pre-scale)
+  float fscale[kMaxGroups];       // 2^-p: pre-scale of pairs with F - 7w < 0
+};
+
+enum CoefMode : int {
+  kCoefUnit = 0,       // alpha = +-1, beta = 0
+  kCoefUnitAcc = 1,    // alpha = +-1, beta = 1
+  kCoefReal = 2,       // real alpha, real beta
+  kCoefComplex = 3,    // alpha or beta complex
 };
 
 struct MmaParams {
   int m;          // rows of C (N side of the MMA)
   int n2;         // 2 * columns of C (M side)
-  int Kp;         // padded K' (multiple of 8)
+  int Kp;         // padded K' (multiple of 64)
   int S;
+  int tiles_x;    // tiles along the 2n rows of C^T
+  int tiles_y;    // tiles along the m rows of C
+  int n_tiles;    // tiles_x * tiles_y * batch
   const int* eA;  // [batch][m] biased exponents of op(A) rows
   const int* eB;  // [batch][n] biased exponents of op(B) columns
   zd* C;
   int ldc;
   long long sC;
   zd alpha, beta;
-  int beta_zero;
-  int complex_coef;  // alpha or beta has an imaginary part
+  int coef_mode;
+  int negate;                 // alpha = -1 (kCoefUnit / kCoefUnitAcc)
+  unsigned long long bias;    // sum over groups of kMagicBits * weight (mod 2^64)
+  int fix_bits;               // F: fixed-point units of 2^-F of a leading digit product
   int* err;          // per batch entry error slot (may be null)
   const int* active; // batch entries with active[b] == 0 are skipped (may be null)
   int a_shared;      // op(A) / op(B) shared by every batch entry: sliced once (batch index 0)
@@ -81,22 +105,6 @@ struct MmaParams {
 
 __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
   return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
-}
-
-// fp32 value -> int64 fixed point with kFixShift fraction bits, from the IEEE fields with
-// integer instructions only (a float -> int64 conversion would run on GB300's slow FP64 pipe).
-// Exact for the single-pair groups (integers times 2^-7(s+t-2), s+t <= 7); the shared group
-// is truncated below 2^-36 of a leading digit product.
-__device__ __forceinline__ long long f32_to_fix(float v) {
-  const uint32_t bits = __float_as_uint(v);
-  const int e = (int)((bits >> 23) & 0xFFu);
-  if (e == 0) return 0;  // zero (denormals are far below the fixed-point resolution)
-  const long long m = (long long)((bits & 0x7FFFFFu) | 0x800000u);
-  const int sh = e - 150 + kFixShift;  // value = m * 2^(e - 150)
-  long long r;
-  if (sh >= 0) r = sh < 40 ? (m << sh) : 0x7FFFFFFFFFFFFFFFll;  // |v| >= 2^27 cannot occur
-  else r = sh > -32 ? (m >> -sh) : 0;
-  return (bits >> 31) ? -r : r;
 }
 
 // int64 fixed-point value * 2^e -> double, integer arithmetic only (round to nearest even).
@@ -127,13 +135,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                      const MmaParams p) {
   constexpr int kABytes = kTileM * 128;
   constexpr int kBBytes = NT * 128;
-  constexpr int kHalf = NT / 2;
-  constexpr int kChunks = kHalf / 8;
+  constexpr int kCols = NT / 4;   // accumulator columns per epilogue thread
+  constexpr int kBatch = kCols % 8 == 0 ? 8 : 4;  // columns per tcgen05.ld wait
   static_assert(NT % 16 == 0 && NT >= 16 && NT <= 256, "UMMA N");
   static_assert(2 * NT <= 256, "two accumulators must fit in 256 TMEM columns");
   constexpr uint32_t kIdesc = ptx::idesc_bf16_f32(kTileM, NT);
 
-  if (p.active && p.active[blockIdx.z] == 0) return;  // before any barrier or TMEM use
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
   uint8_t* sA = smem;
@@ -147,9 +154,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * kTileM;  // rows of C^T
-  const int n0 = blockIdx.y * NT;      // rows of C
-  const int b = blockIdx.z;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -173,9 +177,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   ptx::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  const int KB = (p.Kp + kKBlock - 1) / kKBlock;
   const Schedule& sc = p.sched;
-  auto fail = [&]() {
+  const int per_b = p.tiles_x * p.tiles_y;
+  // every role walks the same tiles in the same order and skips the same inactive entries
+  auto tile_of = [&](int tile, int& m0, int& n0, int& b) {
+    b = tile / per_b;
+    const int r = tile - b * per_b;
+    const int ty = r / p.tiles_x;
+    m0 = (r - ty * p.tiles_x) * kTileM;  // rows of C^T
+    n0 = ty * NT;                        // rows of C
+    return !p.active || p.active[b] != 0;
+  };
+  auto fail = [&](int b) {
     *abort_flag = 1;
     if (p.err) atomicCAS(&p.err[b], 0, (int)BT_ERR_TIMEOUT);
   };
@@ -188,17 +201,25 @@ __global__ void __launch_bounds__(kThreads, 1)
       int stage = 0;
       uint32_t phase = 0;
       int issued = 0;
-      const int n_items = sc.n_pairs * KB;
-      for (int it = 0; it < n_items; ++it) {
-        const int pi = it / KB, kb = it - pi * KB;
-        if (!ptx::mbar_wait_bounded(&empty[stage], phase ^ 1u, abort_flag, kWaitLimitNs)) { fail(); break; }
-        ptx::mbar_arrive_expect_tx(&full[stage], kABytes + kBBytes);
-        ptx::tma_load_3d(sA + stage * kABytes, &tmA, &full[stage], kb * kKBlock, m0,
-                         (p.b_shared ? 0 : b) * p.S + (sc.t[pi] - 1));
-        ptx::tma_load_3d(sB + stage * kBBytes, &tmB, &full[stage], kb * kKBlock, n0,
-                         (p.a_shared ? 0 : b) * p.S + (sc.s[pi] - 1));
-        ++issued;
-        if (++stage == kStages) { stage = 0; phase ^= 1u; }
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
+        int m0, n0, b;
+        if (!tile_of(tile, m0, n0, b)) continue;
+        const int zA = (p.b_shared ? 0 : b) * p.S - 1, zB = (p.a_shared ? 0 : b) * p.S - 1;
+        for (int g = 0; g < sc.n_groups && ok; ++g) {
+          for (int kb = sc.kb0[g]; kb < sc.kb1[g]; ++kb) {
+            if (!ptx::mbar_wait_bounded(&empty[stage], phase ^ 1u, abort_flag, kWaitLimitNs)) {
+              fail(b);
+              ok = false;
+              break;
+            }
+            ptx::mbar_arrive_expect_tx(&full[stage], kABytes + kBBytes);
+            ptx::tma_load_3d(sA + stage * kABytes, &tmA, &full[stage], kb * kKBlock, m0, zA + sc.t[g]);
+            ptx::tma_load_3d(sB + stage * kBBytes, &tmB, &full[stage], kb * kKBlock, n0, zB + sc.s[g]);
+            ++issued;
+            if (++stage == kStages) { stage = 0; phase ^= 1u; }
+          }
+        }
       }
       if (*abort_flag) {
         // let the loads already in flight land before the CTA exits (bounded)
@@ -212,38 +233,41 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
+      uint32_t gc = 0;  // accumulation groups issued so far (all tiles)
       bool ok = true;
-      for (int g = 0; g < sc.n_groups && ok; ++g) {
-        const int ab = g & 1;
-        if (g >= 2) {
-          if (!ptx::mbar_wait_bounded(&tempty[ab], (uint32_t)(((g >> 1) - 1) & 1), abort_flag, kWaitLimitNs)) {
-            fail();
+      for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
+        int m0, n0, b;
+        if (!tile_of(tile, m0, n0, b)) continue;
+        for (int g = 0; g < sc.n_groups && ok; ++g, ++gc) {
+          const uint32_t ab = gc & 1u;
+          if (gc >= 2 && !ptx::mbar_wait_bounded(&tempty[ab], ((gc >> 1) - 1u) & 1u, abort_flag, kWaitLimitNs)) {
+            fail(b);
             ok = false;
             break;
           }
-        }
-        ptx::tc_fence_after();
-        const uint32_t dcol = tmem + (uint32_t)(ab * NT);
-        const int pb = g == 0 ? 0 : sc.group_end[g - 1], pe = sc.group_end[g];
-        bool first = true;
-        for (int pi = pb; pi < pe && ok; ++pi) {
-          for (int kb = 0; kb < KB; ++kb) {
-            if (!ptx::mbar_wait_bounded(&full[stage], phase, abort_flag, kWaitLimitNs)) { fail(); ok = false; break; }
+          ptx::tc_fence_after();
+          const uint32_t dcol = tmem + ab * (uint32_t)NT;
+          for (int kb = sc.kb0[g]; kb < sc.kb1[g]; ++kb) {
+            if (!ptx::mbar_wait_bounded(&full[stage], phase, abort_flag, kWaitLimitNs)) {
+              fail(b);
+              ok = false;
+              break;
+            }
             ptx::tc_fence_after();
             const uint32_t a_addr = ptx::smem_u32(sA + stage * kABytes);
             const uint32_t b_addr = ptx::smem_u32(sB + stage * kBBytes);
+            const uint32_t acc0 = kb == sc.kb0[g] ? 0u : 1u;
 #pragma unroll
             for (int k = 0; k < kKBlock / 16; ++k) {
               const uint64_t ad = ptx::sdesc_kmajor_sw128(a_addr + k * 32);
               const uint64_t bd = ptx::sdesc_kmajor_sw128(b_addr + k * 32);
-              ptx::umma_f16(dcol, ad, bd, kIdesc, (first && k == 0) ? 0u : 1u);
+              ptx::umma_f16(dcol, ad, bd, kIdesc, k == 0 ? acc0 : 1u);
             }
-            first = false;
             ptx::umma_commit(&empty[stage]);
             if (++stage == kStages) { stage = 0; phase ^= 1u; }
           }
+          if (ok) ptx::umma_commit(&tfull[ab]);
         }
-        if (ok) ptx::umma_commit(&tfull[ab]);
       }
       // every MMA this thread issued has completed once `drain` fires
       ptx::umma_commit(drain);
@@ -251,76 +275,102 @@ __global__ void __launch_bounds__(kThreads, 1)
       ptx::mbar_wait_bounded(drain, 0, &never, kWaitLimitNs);
     }
   } else {
-    // ---------------- epilogue: TMEM -> int64 fixed point -> C ----------------
+    // ---------------- epilogue: TMEM -> uint64 fixed point -> C ----------------
     const int ew = warp - 2;
     const int q = warp & 3;  // TMEM lanes [32q, 32q+32) are accessible to this warp
-    const int half = ew >> 2;
-    long long acc[kHalf];
-#pragma unroll
-    for (int c = 0; c < kHalf; ++c) acc[c] = 0;
+    const int cq = ew >> 2;  // column quarter
+    const int r = q * 32 + lane;
+    uint32_t gc = 0;
     bool ok = true;
-    for (int g = 0; g < sc.n_groups; ++g) {
-      const int ab = g & 1;
-      if (!ptx::mbar_wait_bounded(&tfull[ab], (uint32_t)((g >> 1) & 1), abort_flag, kWaitLimitNs)) {
-        fail();
-        ok = false;
-        break;
-      }
-      ptx::tc_fence_after();
-      const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * NT + half * kHalf);
+    for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
+      int m0, n0, b;
+      if (!tile_of(tile, m0, n0, b)) continue;
+      unsigned long long acc[kCols];
 #pragma unroll
-      for (int c = 0; c < kChunks; ++c) {
-        uint32_t v[8];
-        ptx::tmem_ld_x8(base + c * 8, v);
-        ptx::tmem_wait_ld();
+      for (int c = 0; c < kCols; ++c) acc[c] = 0ull;
+      for (int g = 0; g < sc.n_groups; ++g, ++gc) {
+        const uint32_t ab = gc & 1u;
+        const bool got = ptx::mbar_wait_bounded(&tfull[ab], (gc >> 1) & 1u, abort_flag, kWaitLimitNs);
+        // the warp-collective tcgen05.ld below needs every lane: one lane's timeout stops the warp
+        if (!__all_sync(0xffffffffu, got)) {
+          if (!got) fail(b);
+          ok = false;
+          break;
+        }
+        ptx::tc_fence_after();
+        const float fs = sc.fscale[g];
+        const uint32_t mu = sc.mult[g];
+        const int lsh = sc.lsh[g];
+        const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + ab * (uint32_t)NT + (uint32_t)(cq * kCols);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[c * 8 + j] += f32_to_fix(__uint_as_float(v[j]));
+        for (int c0 = 0; c0 < kCols; c0 += kBatch) {
+          uint32_t v[kBatch];
+#pragma unroll
+          for (int c = 0; c < kBatch; c += 4) ptx::tmem_ld_x4(base + c0 + c, v + c);
+          ptx::tmem_wait_ld();
+          if (lsh == 0) {
+#pragma unroll
+            for (int c = 0; c < kBatch; ++c) {
+              const float t = fmaf(__uint_as_float(v[c]), fs, kMagic);
+              acc[c0 + c] += (unsigned long long)__float_as_uint(t) * (unsigned long long)mu;
+            }
+          } else {
+#pragma unroll
+            for (int c = 0; c < kBatch; ++c)
+              acc[c0 + c] += (unsigned long long)__float_as_uint(__uint_as_float(v[c]) + kMagic) << lsh;
+          }
+        }
+        ptx::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&tempty[ab]);
       }
-      ptx::tc_fence_before();
-      __syncwarp();
-      if (lane == 0) ptx::mbar_arrive(&tempty[ab]);
-    }
-    if (ok) {
-      const int r = q * 32 + lane;
+      if (!ok) break;
+      // write this tile of C (overlaps the MMAs of the next tile)
       const int jp = m0 + r;  // row of C^T
       const bool row_ok = jp < p.n2;
       const int j = jp >> 1, part = jp & 1;
       const int n = p.n2 >> 1;
       const int EB = row_ok ? p.eB[(long long)(p.b_shared ? 0 : b) * n + j] : 1;
       zd* Cb = p.C + p.sC * b;
-      const double ar = p.alpha.x, ai = p.alpha.y, br = p.beta.x, bi = p.beta.y;
+      const int* eAb = p.eA + (long long)(p.a_shared ? 0 : b) * p.m;
 #pragma unroll
-      for (int c = 0; c < kHalf; ++c) {
-        const int i = n0 + half * kHalf + c;
+      for (int c = 0; c < kCols; ++c) {
+        const int i = n0 + cq * kCols + c;
         const bool ok_el = row_ok && i < p.m;
         double v = 0.0;
-        int EA = 1;
         if (ok_el) {
-          EA = p.eA[(long long)(p.a_shared ? 0 : b) * p.m + i];
-          // value = acc * 2^-36 * 2^(eA + eB - 14), eA = EA - 1022, eB = EB - 1022
-          v = fix_to_double(acc[c], EA + EB - 2044 - 14 - kFixShift);
+          const int EA = eAb[i];
+          long long a = (long long)(acc[c] - p.bias);
+          if (p.negate) a = -a;
+          // value = a * 2^-F * R_A * R_B * 2^-12, R = 2^(E - 1022)
+          v = fix_to_double(a, EA + EB - 2044 - 12 - p.fix_bits);
           if (EA >= 2047 || EB >= 2047) v = __longlong_as_double(0x7ff8000000000000ll);
         }
         double* cp = reinterpret_cast<double*>(Cb + (long long)(ok_el ? i : 0) * p.ldc + (ok_el ? j : 0)) + part;
-        if (!p.complex_coef) {
+        if (p.coef_mode == kCoefUnit) {
+          if (ok_el) *cp = v;
+        } else if (p.coef_mode == kCoefUnitAcc) {
+          if (ok_el) *cp += v;
+        } else if (p.coef_mode == kCoefReal) {
           if (ok_el) {
-            double out = ar == 1.0 ? v : (ar == -1.0 ? -v : ar * v);
-            if (!p.beta_zero) out = fma(br, *cp, out);
-            *cp = out;
+            const double out = p.alpha.x * v;
+            *cp = p.beta.x == 0.0 ? out : fma(p.beta.x, *cp, out);
           }
         } else {
           // complex alpha / beta: the partner lane (2j vs 2j+1) holds the other component
           const double vo = __shfl_xor_sync(0xffffffffu, v, 1);
           const double re = part ? vo : v, im = part ? v : vo;
+          const double ar = p.alpha.x, ai = p.alpha.y, br = p.beta.x, bi = p.beta.y;
+          const bool bz = br == 0.0 && bi == 0.0;
           double cre = 0.0, cim = 0.0;
-          if (ok_el && !p.beta_zero) {
+          if (ok_el && !bz) {
             const zd old = Cb[(long long)i * p.ldc + j];
             cre = old.x;
             cim = old.y;
           }
           if (ok_el) {
-            const double outr = ar * re - ai * im + (p.beta_zero ? 0.0 : br * cre - bi * cim);
-            const double outi = ar * im + ai * re + (p.beta_zero ? 0.0 : br * cim + bi * cre);
+            const double outr = ar * re - ai * im + (bz ? 0.0 : br * cre - bi * cim);
+            const double outi = ar * im + ai * re + (bz ? 0.0 : br * cim + bi * cre);
             *cp = part ? outi : outr;
           }
         }
@@ -344,72 +394,32 @@ __device__ __forceinline__ int biased_exp(double v) {
   return e == 0 ? 1 : e;
 }
 
-// element (r, c) of L = op(X): op N -> X[r][c], op C -> conj(X[c][r])
-__device__ __forceinline__ zd load_op(const zd* X, int ld, int op, int r, int c) {
-  return op == BT_OP_N ? X[(long long)r * ld + c] : zconj(X[(long long)c * ld + r]);
-}
-
-// Row maxima (rows != null) and column maxima (cols != null) of the biased exponents of L
-// (R x Kc), tiles of 32 x 32 loaded coalesced for either orientation.
-__global__ void exp_max_kernel(int R, int Kc, const zd* __restrict__ X, int ld, long long sX, int op,
-                               int* __restrict__ rows, long long sRows, int* __restrict__ cols, long long sCols,
-                               const int* __restrict__ active) {
-  __shared__ int E[32][33];
-  const int b = blockIdx.z;
-  if (active && active[b] == 0) return;
-  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
-  const zd* Xb = X + sX * b;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
-  for (int yy = ty; yy < 32; yy += 8) {
-    // coalesced along the stored row: op N reads X[r][c] with c fastest; op C reads X[c][r] with r fastest
-    int r, c;
-    if (op == BT_OP_N) { r = r0 + yy; c = c0 + tx; } else { r = r0 + tx; c = c0 + yy; }
-    int e = 0;
-    if (r < R && c < Kc) {
-      const zd v = load_op(Xb, ld, op, r, c);
-      e = max(biased_exp(v.x), biased_exp(v.y));
-    }
-    if (op == BT_OP_N) E[yy][tx] = e; else E[tx][yy] = e;
-  }
-  __syncthreads();
-  if (ty == 0) {
-    int m = 0;
-    if (rows && r0 + tx < R) {
-      for (int c = 0; c < 32; ++c) m = max(m, E[tx][c]);
-      atomicMax(&rows[sRows * b + r0 + tx], m);
-    }
-  } else if (ty == 1) {
-    int m = 0;
-    if (cols && c0 + tx < Kc) {
-      for (int r = 0; r < 32; ++r) m = max(m, E[r][tx]);
-      atomicMax(&cols[sCols * b + c0 + tx], m);
-    }
-  }
-}
-
-// Digits of |v| * 2^(-eRow) as a fixed-point number with 7S fraction bits (truncated);
-// q[s] = sign * d_s * 2^(-7s) (pre-scaled by the slice position).
+// Balanced base-128 digits of v / R, R = 2^(Erow - 1022):  X = round(|v| / R * 2^(7S-1)) <=
+// 2^(7S-1) (integer arithmetic on the IEEE fields), X = sum_s d_s 128^(S-s) with the lower digits
+// in [-64, 63] and the leading digit in [0, 64];  q[s-1] = sign * d_s (integers, exact in bf16).
 __device__ __forceinline__ void slice_value(double v, int Erow, int S, float* q) {
   const long long bits = __double_as_longlong(v);
   int E = (int)((bits >> 52) & 0x7FF);
   unsigned long long M = (unsigned long long)bits & ((1ull << 52) - 1);
   if (E == 0) E = 1; else M |= (1ull << 52);
-  const int F = kDigitBits * S;
-  const int sh = E - Erow + F - 53;
-  unsigned long long X;
-  if (sh >= 0) X = M << sh;
-  else if (-sh >= 64) X = 0;
-  else X = M >> (-sh);
+  // X2 = trunc(|v| / R * 2^(7S)) = M * 2^(E - Erow + 7S - 53); one bit beyond X for rounding
+  const int sh = E - Erow + kDigitBits * S - 53;
+  unsigned long long X2;
+  if (sh >= 0) X2 = M << sh;
+  else if (-sh >= 64) X2 = 0;
+  else X2 = M >> (-sh);
+  unsigned long long X = (X2 + 1ull) >> 1;
   const float sign = bits < 0 ? -1.0f : 1.0f;
-  float scale = sign;
 #pragma unroll
-  for (int s = 1; s <= kMaxSlices; ++s) {
+  for (int s = kMaxSlices; s >= 2; --s) {
     if (s <= S) {
-      const unsigned d = (unsigned)((X >> (F - kDigitBits * s)) & 127ull);
-      q[s - 1] = scale * (float)d;
-      scale *= 0.0078125f;  // 2^-7
+      int d = (int)(X & 127ull);
+      if (d >= 64) d -= 128;
+      q[s - 1] = sign * (float)d;
+      X = (X - (unsigned long long)(long long)d) >> kDigitBits;  // X + 128 - d' when d < 0: stays >= 0
     }
   }
+  q[0] = sign * (float)X;  // leading digit, <= 64
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
@@ -417,82 +427,134 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
-// At slices: out[b][s][r][2p + c] for L = op(A) (R x Kc), row exponents erow[b][r].
-__global__ void slice_rows_kernel(int R, int Rpad, int Kc, int Kp, const zd* __restrict__ X, int ld, long long sX,
-                                  int op, const int* __restrict__ erow, int S, uint32_t* __restrict__ out,
-                                  const int* __restrict__ active) {
-  __shared__ zd T[32][33];
-  const int b = blockIdx.z;
-  if (active && active[b] == 0) return;
-  const int r0 = blockIdx.y * 32, p0 = blockIdx.x * 32;
-  const zd* Xb = X + sX * b;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int yy = ty; yy < 32; yy += 8) {
-    int r, c;
-    if (op == BT_OP_N) { r = r0 + yy; c = p0 + tx; } else { r = r0 + tx; c = p0 + yy; }
-    zd v = zmake(0.0, 0.0);
-    if (r < R && c < Kc) v = load_op(Xb, ld, op, r, c);
-    if (op == BT_OP_N) T[yy][tx] = v; else T[tx][yy] = v;
-  }
-  __syncthreads();
-  const int Kw = Kp >> 1;  // 32-bit words per output row
-  const long long slice_words = (long long)Rpad * Kw;
-  for (int yy = ty; yy < 32; yy += 8) {
-    const int r = r0 + yy, p = p0 + tx;
-    if (r >= Rpad || p >= Kw) continue;
-    float qr[kMaxSlices], qi[kMaxSlices];
-    const zd v = T[yy][tx];
-    const bool in = r < R && p < Kc;  // padding rows / columns are written as zeros
-    if (in) {
-      const int Er = erow[(long long)b * R + r];
-      slice_value(v.x, Er, S, qr);
-      slice_value(v.y, Er, S, qi);
+// Slicing works on "lines": the rows of op(A) (At operand) and the columns of op(B) (Bt
+// operand), each of Kc complex elements, one exponent per line.  A line is contiguous in memory
+// for op(A) = A and op(B) = B^H, strided (a memory column) otherwise.  Output rows hold Kw = Kp/2
+// 32-bit words (bf16 pairs) per slice:
+//   At: out[b][s][l][p]               = (Re, Im) digits of op(A)[l][p]
+//   Bt: out[b][s][2l][p], [2l+1][p]   = (Re, -Im), (Im, Re) digits of op(B)[p][l]
+// Lines l in [L, Lpad) and words p in [Kc, Kw) are written as zeros.  The line exponents go to
+// e[b][l]; every kernel reads its input line twice (max exponent, then digits), the second time
+// mostly from L2.
+template <bool kBt>
+__device__ __forceinline__ void write_slices(uint32_t* __restrict__ out, long long slice_words, int Kw, int l, int p,
+                                             int S, bool in, const float* qr, const float* qi) {
+  uint32_t* o0 = out + (long long)(kBt ? 2 * l : l) * Kw + p;
+#pragma unroll
+  for (int s = 0; s < kMaxSlices; ++s) {
+    if (s < S) {
+      if (kBt) {
+        o0[s * slice_words] = in ? pack_bf16x2(qr[s], -qi[s]) : 0u;
+        o0[s * slice_words + Kw] = in ? pack_bf16x2(qi[s], qr[s]) : 0u;
+      } else {
+        o0[s * slice_words] = in ? pack_bf16x2(qr[s], qi[s]) : 0u;
+      }
     }
-    uint32_t* o = out + ((long long)b * S) * slice_words + (long long)r * Kw + p;
-    for (int s = 0; s < S; ++s) o[s * slice_words] = in ? pack_bf16x2(qr[s], qi[s]) : 0u;
   }
 }
 
-// Bt slices: rows 2j (re) and 2j+1 (im) of out[b][s][2 Ncol][Kp] for L = op(B) (Kc x Ncol),
-// column exponents ecol[b][j].
-__global__ void slice_cols_kernel(int Kc, int Ncol, int NcolPad, int Kp, const zd* __restrict__ X, int ld,
-                                  long long sX, int op, const int* __restrict__ ecol, int S,
-                                  uint32_t* __restrict__ out, const int* __restrict__ active) {
-  __shared__ zd T[32][33];  // T[j][p]
-  const int b = blockIdx.z;
+// Contiguous lines: one warp per line, grid (ceil(Lpad / 8), batch), 256 threads.
+template <bool kBt>
+__global__ void slice_lines_contig_kernel(int L, int Lpad, int Kc, int Kw, const zd* __restrict__ X, int ld,
+                                          long long sX, int conj, int S, int* __restrict__ e,
+                                          uint32_t* __restrict__ out, const int* __restrict__ active) {
+  const int b = blockIdx.y;
   if (active && active[b] == 0) return;
-  const int j0 = blockIdx.y * 32, p0 = blockIdx.x * 32;
-  const zd* Xb = X + sX * b;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int l = blockIdx.x * 8 + warp;
+  if (l >= Lpad) return;
+  const bool line_ok = l < L;
+  const zd* line = X + sX * b + (long long)(line_ok ? l : 0) * ld;
+  int E = 1;
+  if (line_ok)
+    for (int p = lane; p < Kc; p += 32) {
+      const zd v = line[p];
+      E = max(E, max(biased_exp(v.x), biased_exp(v.y)));
+    }
+  E = __reduce_max_sync(0xffffffffu, E);
+  if (line_ok && lane == 0) e[(long long)b * L + l] = E;
+  const long long slice_words = (long long)(kBt ? 2 : 1) * Lpad * Kw;
+  uint32_t* ob = out + (long long)b * S * slice_words;
+  for (int p = lane; p < Kw; p += 32) {
+    const bool in = line_ok && p < Kc;
+    float qr[kMaxSlices], qi[kMaxSlices];
+    if (in) {
+      const zd v = line[p];
+      slice_value(v.x, E, S, qr);
+      slice_value(conj ? -v.y : v.y, E, S, qi);
+    }
+    write_slices<kBt>(ob, slice_words, Kw, l, p, S, in, qr, qi);
+  }
+}
+
+// Strided lines (memory columns): 32 lines per CTA, grid (ceil(Lpad / 32), batch), 256 threads.
+template <bool kBt>
+__global__ void slice_lines_strided_kernel(int L, int Lpad, int Kc, int Kw, const zd* __restrict__ X, int ld,
+                                           long long sX, int conj, int S, int* __restrict__ e,
+                                           uint32_t* __restrict__ out, const int* __restrict__ active) {
+  __shared__ zd T[32][33];  // T[p][l]
+  __shared__ int red[8][32];
+  const int b = blockIdx.y;
+  if (active && active[b] == 0) return;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int yy = ty; yy < 32; yy += 8) {
-    // op N: L[p][j] = X[p][j] (coalesced along j);  op C: L[p][j] = conj(X[j][p]) (along p)
-    int p, j;
-    if (op == BT_OP_N) { p = p0 + yy; j = j0 + tx; } else { p = p0 + tx; j = j0 + yy; }
-    zd v = zmake(0.0, 0.0);
-    if (p < Kc && j < Ncol) v = load_op(Xb, ld, op, p, j);
-    if (op == BT_OP_N) T[tx][yy] = v; else T[yy][tx] = v;
+  const int l0 = blockIdx.x * 32;
+  const zd* Xb = X + sX * b;
+  {
+    const int l = l0 + tx;
+    int E = 1;
+    if (l < L)
+      for (int p = ty; p < Kc; p += 8) {
+        const zd v = Xb[(long long)p * ld + l];
+        E = max(E, max(biased_exp(v.x), biased_exp(v.y)));
+      }
+    red[ty][tx] = E;
   }
   __syncthreads();
-  const int Kw = Kp >> 1;
-  const long long slice_words = (long long)2 * NcolPad * Kw;
-  for (int yy = ty; yy < 32; yy += 8) {
-    const int j = j0 + yy, p = p0 + tx;
-    if (j >= NcolPad || p >= Kw) continue;
-    float qr[kMaxSlices], qi[kMaxSlices];
-    const zd v = T[yy][tx];
-    const bool in = j < Ncol && p < Kc;  // padding rows / columns are written as zeros
-    if (in) {
-      const int Ec = ecol[(long long)b * Ncol + j];
-      slice_value(v.x, Ec, S, qr);
-      slice_value(v.y, Ec, S, qi);
+  __shared__ int Eline[32];
+  if (ty == 0) {
+    int E = red[0][tx];
+#pragma unroll
+    for (int y = 1; y < 8; ++y) E = max(E, red[y][tx]);
+    Eline[tx] = E;
+    if (l0 + tx < L) e[(long long)b * L + l0 + tx] = E;
+  }
+  const long long slice_words = (long long)(kBt ? 2 : 1) * Lpad * Kw;
+  uint32_t* ob = out + (long long)b * S * slice_words;
+  for (int p0 = 0; p0 < Kw; p0 += 32) {
+    __syncthreads();  // Eline ready; previous tile consumed
+    for (int yy = ty; yy < 32; yy += 8) {
+      const int p = p0 + yy, l = l0 + tx;
+      T[yy][tx] = (p < Kc && l < L) ? Xb[(long long)p * ld + l] : zmake(0.0, 0.0);
     }
-    uint32_t* o0 = out + ((long long)b * S) * slice_words + (long long)(2 * j) * Kw + p;
-    uint32_t* o1 = o0 + Kw;
-    for (int s = 0; s < S; ++s) {
-      o0[s * slice_words] = in ? pack_bf16x2(qr[s], -qi[s]) : 0u;
-      o1[s * slice_words] = in ? pack_bf16x2(qi[s], qr[s]) : 0u;
+    __syncthreads();
+    for (int yy = ty; yy < 32; yy += 8) {
+      const int l = l0 + yy, p = p0 + tx;
+      if (l >= Lpad || p >= Kw) continue;
+      const bool in = l < L && p < Kc;
+      float qr[kMaxSlices], qi[kMaxSlices];
+      if (in) {
+        const zd v = T[tx][yy];
+        slice_value(v.x, Eline[yy], S, qr);
+        slice_value(conj ? -v.y : v.y, Eline[yy], S, qi);
+      }
+      write_slices<kBt>(ob, slice_words, Kw, l, p, S, in, qr, qi);
     }
   }
+}
+
+template <bool kBt>
+bt_status slice_lines(cudaStream_t st, bool contiguous, int L, int Lpad, int Kc, int Kw, const zd* X, int ld,
+                      long long sX, int conj, int S, int* e, uint32_t* out, int batch, const int* active) {
+  if (contiguous) {
+    dim3 g((Lpad + 7) / 8, batch);
+    slice_lines_contig_kernel<kBt><<<g, 256, 0, st>>>(L, Lpad, Kc, Kw, X, ld, sX, conj, S, e, out, active);
+  } else {
+    dim3 g((Lpad + 31) / 32, batch);
+    slice_lines_strided_kernel<kBt><<<g, 256, 0, st>>>(L, Lpad, Kc, Kw, X, ld, sX, conj, S, e, out, active);
+  }
+  count_launch();
+  BT_CUDA_TRY(cudaGetLastError());
+  return BT_OK;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -523,34 +585,43 @@ bool encode_slices_map(CUtensorMap* map, void* base, int Kp, int rows, int depth
   return r == CUDA_SUCCESS;
 }
 
-Schedule make_schedule(int S) {
-  Schedule sc{};
-  int np = 0, ng = 0;
-  // exact single-pair groups up to s + t = dx; the shared group's fp32 rounding (~2^-24 of
-  // terms scaled by 2^-7(dx-1)) then stays below the slicing error for every S
-  const int dx = S - 1 > kExactD ? S - 1 : kExactD;
-  for (int d = 2; d <= dx && d <= S + 1; ++d)
+// Groups: every slice pair (s, t) with s + t <= S + 1, in order of weight, times the K
+// segments of at most kSegBlocks blocks (balanced).  With pair weight w = s + t - 2 the group
+// enters the fixed-point sum with factor 2^(F - 7w): a shift for factors above 2^31, a 32-bit
+// multiplier down to 2^0, and below that a pre-scale 2^(F - 7w) in the drain's FFMA (rounding
+// below 2^-F of a leading digit product).  F = min(7S - 9, 50 - log2(K')): resolution below the
+// slicing error, and |sum| <= K' * 2^12 * 2^F * (1 + 2^-6) < 2^63.
+bool make_schedule(int S, int KB, Schedule* sc, unsigned long long* bias, int* fix_bits) {
+  *sc = Schedule{};
+  int lg = 0;
+  while ((1 << lg) < KB * kKBlock) ++lg;
+  int F = kDigitBits * S - 9;
+  if (F > 50 - lg) F = 50 - lg;
+  const int nseg = (KB + kSegBlocks - 1) / kSegBlocks;
+  unsigned long long bs = 0;
+  int ng = 0;
+  for (int d = 2; d <= S + 1; ++d)
     for (int s = 1; s <= S; ++s) {
       const int t = d - s;
       if (t < 1 || t > S) continue;
-      sc.s[np] = (unsigned char)s;
-      sc.t[np] = (unsigned char)t;
-      ++np;
-      sc.group_end[ng++] = (unsigned char)np;
+      const int e = F - kDigitBits * (d - 2);
+      for (int seg = 0; seg < nseg; ++seg) {
+        if (ng >= kMaxGroups) return false;
+        sc->s[ng] = (unsigned char)s;
+        sc->t[ng] = (unsigned char)t;
+        sc->kb0[ng] = (unsigned char)((long long)KB * seg / nseg);
+        sc->kb1[ng] = (unsigned char)((long long)KB * (seg + 1) / nseg);
+        sc->lsh[ng] = (unsigned char)(e > 31 ? e : 0);
+        sc->mult[ng] = e > 31 ? 1u : (e >= 0 ? (1u << e) : 1u);
+        sc->fscale[ng] = e >= 0 ? 1.0f : ldexpf(1.0f, e);
+        bs += (unsigned long long)kMagicBits * ((unsigned long long)sc->mult[ng] << sc->lsh[ng]);
+        ++ng;
+      }
     }
-  const int np0 = np;
-  for (int d = dx + 1; d <= S + 1; ++d)
-    for (int s = 1; s <= S; ++s) {
-      const int t = d - s;
-      if (t < 1 || t > S) continue;
-      sc.s[np] = (unsigned char)s;
-      sc.t[np] = (unsigned char)t;
-      ++np;
-    }
-  if (np > np0) sc.group_end[ng++] = (unsigned char)np;
-  sc.n_pairs = np;
-  sc.n_groups = ng;
-  return sc;
+  sc->n_groups = ng;
+  *bias = bs;
+  *fix_bits = F;
+  return true;
 }
 
 int pick_nt(int m) {
@@ -592,8 +663,19 @@ size_t carve_ws(char* base, int m, int n, int kc, int S, int batch, SplitWs* w) 
   return off;
 }
 
+int num_sms() {
+  static std::mutex mu;
+  static int sms[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  std::lock_guard<std::mutex> lock(mu);
+  if (sms[dev] == 0 && cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms[dev] = 0;
+  return sms[dev];
+}
+
 template <int NT>
-bt_status launch_mma(cudaStream_t st, const CUtensorMap& mA, const CUtensorMap& mB, const MmaParams& p, int batch) {
+bt_status launch_mma(cudaStream_t st, const CUtensorMap& mA, const CUtensorMap& mB, const MmaParams& p) {
   const size_t smem = 1024 + (size_t)kStages * (kTileM * 128 + NT * 128) + 256;
   // per-function device state: set once per device (the value never changes for one NT)
   static std::mutex mu;
@@ -609,29 +691,31 @@ bt_status launch_mma(cudaStream_t st, const CUtensorMap& mA, const CUtensorMap& 
       attr_set[dev] = true;
     }
   }
-  dim3 grid((p.n2 + kTileM - 1) / kTileM, (p.m + NT - 1) / NT, batch);
+  const int sms = num_sms();
+  if (sms <= 0) return BT_ERR_CUDA;
+  // persistent: one CTA per SM (1 CTA fits per SM by shared memory), tiles walked in order
+  const int grid = p.n_tiles < sms ? p.n_tiles : sms;
   split_mma_kernel<NT><<<grid, kThreads, smem, st>>>(mA, mB, p);
   count_launch();
   BT_CUDA_TRY(cudaGetLastError());
   return BT_OK;
 }
 
-bt_status launch_mma_nt(int nt, cudaStream_t st, const CUtensorMap& mA, const CUtensorMap& mB, const MmaParams& p,
-                        int batch) {
+bt_status launch_mma_nt(int nt, cudaStream_t st, const CUtensorMap& mA, const CUtensorMap& mB, const MmaParams& p) {
   switch (nt) {
-    case 16: return launch_mma<16>(st, mA, mB, p, batch);
-    case 32: return launch_mma<32>(st, mA, mB, p, batch);
-    case 48: return launch_mma<48>(st, mA, mB, p, batch);
-    case 64: return launch_mma<64>(st, mA, mB, p, batch);
-    case 80: return launch_mma<80>(st, mA, mB, p, batch);
-    case 96: return launch_mma<96>(st, mA, mB, p, batch);
-    case 112: return launch_mma<112>(st, mA, mB, p, batch);
-    case 128: return launch_mma<128>(st, mA, mB, p, batch);
+    case 16: return launch_mma<16>(st, mA, mB, p);
+    case 32: return launch_mma<32>(st, mA, mB, p);
+    case 48: return launch_mma<48>(st, mA, mB, p);
+    case 64: return launch_mma<64>(st, mA, mB, p);
+    case 80: return launch_mma<80>(st, mA, mB, p);
+    case 96: return launch_mma<96>(st, mA, mB, p);
+    case 112: return launch_mma<112>(st, mA, mB, p);
+    case 128: return launch_mma<128>(st, mA, mB, p);
     default: return BT_ERR_UNSUPPORTED;
   }
 }
 
-constexpr int kMaxKc = 512;  // complex k per launch: K' = 2k <= 1024 <= 1040 (exact slice products)
+constexpr int kMaxKc = 1024;  // complex k per launch (slice workspace); K' = 2k <= 2048 = 32 K blocks
 
 }  // namespace
 
@@ -676,27 +760,11 @@ bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A,
     const int ba = a_shared ? 1 : batch, bb = b_shared ? 1 : batch;
     const int* act_a = a_shared ? nullptr : active;
     const int* act_b = b_shared ? nullptr : active;
-    BT_CUDA_TRY(cudaMemsetAsync(w.eA, 0, sizeof(int) * (size_t)ba * m, st));
-    BT_CUDA_TRY(cudaMemsetAsync(w.eB, 0, sizeof(int) * (size_t)bb * n, st));
-    {
-      dim3 g((kc + 31) / 32, (m + 31) / 32, ba);
-      exp_max_kernel<<<g, 256, 0, st>>>(m, kc, a.p, a.ld, a.stride, a.op, w.eA, m, nullptr, 0, act_a);
-      count_launch();
-      dim3 g2((n + 31) / 32, (kc + 31) / 32, bb);
-      exp_max_kernel<<<g2, 256, 0, st>>>(kc, n, bop.p, bop.ld, bop.stride, bop.op, nullptr, 0, w.eB, n, act_b);
-      count_launch();
-      BT_CUDA_TRY(cudaGetLastError());
-    }
-    {
-      dim3 g((Kp / 2 + 31) / 32, (mp + 31) / 32, ba);
-      slice_rows_kernel<<<g, 256, 0, st>>>(m, mp, kc, Kp, a.p, a.ld, a.stride, a.op, w.eA, S, w.At, act_a);
-      count_launch();
-      dim3 g2((Kp / 2 + 31) / 32, (n2p / 2 + 31) / 32, bb);
-      slice_cols_kernel<<<g2, 256, 0, st>>>(kc, n, n2p / 2, Kp, bop.p, bop.ld, bop.stride, bop.op, w.eB, S, w.Bt,
-                                            act_b);
-      count_launch();
-      BT_CUDA_TRY(cudaGetLastError());
-    }
+    // At from the rows of op(A): contiguous for op N;  Bt from the columns of op(B): contiguous for op C
+    BT_TRY(slice_lines<false>(st, a.op == BT_OP_N, m, mp, kc, Kp / 2, a.p, a.ld, a.stride, a.op == BT_OP_C, S, w.eA,
+                              w.At, ba, act_a));
+    BT_TRY(slice_lines<true>(st, bop.op == BT_OP_C, n, n2p / 2, kc, Kp / 2, bop.p, bop.ld, bop.stride,
+                             bop.op == BT_OP_C, S, w.eB, w.Bt, bb, act_b));
     CUtensorMap mA, mB;
     if (!encode_slices_map(&mA, w.Bt, Kp, n2p, batch * S, kTileM)) return BT_ERR_CUDA;
     if (!encode_slices_map(&mB, w.At, Kp, mp, batch * S, nt)) return BT_ERR_CUDA;
@@ -705,6 +773,9 @@ bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A,
     p.n2 = 2 * n;
     p.Kp = Kp;
     p.S = S;
+    p.tiles_x = n2p / kTileM;
+    p.tiles_y = mp / nt;
+    p.n_tiles = p.tiles_x * p.tiles_y * batch;
     p.eA = w.eA;
     p.eB = w.eB;
     p.C = C;
@@ -712,14 +783,18 @@ bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A,
     p.sC = strideC;
     p.alpha = alpha;
     p.beta = k0 == 0 ? beta : zmake(1.0, 0.0);
-    p.beta_zero = (p.beta.x == 0.0 && p.beta.y == 0.0) ? 1 : 0;
-    p.complex_coef = (p.alpha.y != 0.0 || p.beta.y != 0.0) ? 1 : 0;
+    const bool unit = alpha.y == 0.0 && (alpha.x == 1.0 || alpha.x == -1.0);
+    if (p.alpha.y != 0.0 || p.beta.y != 0.0) p.coef_mode = kCoefComplex;
+    else if (unit && p.beta.x == 0.0) p.coef_mode = kCoefUnit;
+    else if (unit && p.beta.x == 1.0) p.coef_mode = kCoefUnitAcc;
+    else p.coef_mode = kCoefReal;
+    p.negate = (unit && alpha.x == -1.0) ? 1 : 0;
     p.err = nullptr;
     p.active = active;
     p.a_shared = a_shared ? 1 : 0;
     p.b_shared = b_shared ? 1 : 0;
-    p.sched = make_schedule(S);
-    BT_TRY(launch_mma_nt(nt, st, mA, mB, p, batch));
+    if (!make_schedule(S, Kp / kKBlock, &p.sched, &p.bias, &p.fix_bits)) return BT_ERR_UNSUPPORTED;
+    BT_TRY(launch_mma_nt(nt, st, mA, mB, p));
   }
   return BT_OK;
 }
