@@ -156,8 +156,12 @@ __global__ void nonfinite_kernel(long long n, const zd* __restrict__ x, long lon
   const int e = blockIdx.y;
   int bad = 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    // exponent field all ones = Inf / NaN (integer test: no FP64 instruction)
     const zd v = x[sx * e + i];
-    if (!isfinite(v.x) || !isfinite(v.y)) bad = 1;
+    const unsigned long long a = (unsigned long long)__double_as_longlong(v.x),
+                             b = (unsigned long long)__double_as_longlong(v.y);
+    if ((a & 0x7FF0000000000000ull) == 0x7FF0000000000000ull || (b & 0x7FF0000000000000ull) == 0x7FF0000000000000ull)
+      bad = 1;
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0 && status[e] == 0) atomicCAS(&status[e], 0, (int)BT_ERR_NONFINITE);
 }

@@ -90,12 +90,13 @@ bt_status gemm(const Engine& eng, cudaStream_t st, int m, int n, int k, zd alpha
 
 // In-place batched inverse (Gauss-Jordan, partial pivoting).  info[b] |= error code.  The
 // rank-kb updates of the blocked variant run on `eng` (FP64 unless given).
-size_t zinv_workspace_bytes(int n, int batch);
+// `wide`: workspace for the wider panels used when the updates run sliced (Engine::slices > 0).
+size_t zinv_workspace_bytes(int n, int batch, bool wide = false);
 bt_status zinv(cudaStream_t st, int n, zd* A, long long strideA, int batch, int* info, void* ws,
                size_t ws_bytes, const int* active, const Engine* eng = nullptr);
 
 // Sancho-Rubio decimation for `batch` leads.
-size_t decimate_workspace_bytes(int bs, int batch);
+size_t decimate_workspace_bytes(int bs, int batch, bool wide = false);
 bt_status decimate(cudaStream_t st, int bs, int batch, const zd* m, const zd* n, const zd* np,
                    double tol, int maxit, zd* x, zd* sigma, int* iters, int* info, void* ws,
                    size_t ws_bytes, int* iters_host_max, int* h_pinned, const int* mask = nullptr,

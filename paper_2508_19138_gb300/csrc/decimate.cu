@@ -7,8 +7,9 @@
 // from a = n, b = n', e = e_s = m, until max|a|, max|b| <= tol * max(|n|, |n'|); then
 // x = e_s^{-1} and the boundary block sigma = n x n'.
 //
-// The per-lead convergence test is a warp-shuffle max-|.| reduction followed by a block
-// reduction; converged leads drop out of every later launch through an `active` mask, and
+// The per-lead convergence test is a max-|.|^2 reduction (integer keys, warp shuffles, one
+// atomicMax per CTA over many CTAs per lead); converged leads drop out of every later launch
+// through an `active` mask, and
 // the host stops as soon as the device-side count of active leads reaches zero.  The loop is
 // bounded by maxit; leads still active then get BT_ERR_NOT_CONVERGED (never a hang).
 #include <vector>
@@ -20,68 +21,103 @@ namespace {
 
 constexpr int NT = 256;
 
-__device__ __forceinline__ double warp_max(double v) {
+// Per-lead maxima of squared moduli over bs^2 elements, spread over (chunks x leads) CTAs.  The
+// maxima are kept as the bit patterns of non-negative doubles, which order like the doubles:
+// integer max reductions and one atomicMax per CTA, so the only FP64 work is |z|^2 (two
+// instructions per element on GB300's narrow FP64 pipe).  A component with an all-ones exponent
+// (Inf / NaN) sets the lead's non-finite flag.
+//   kind 0: keys[2l] = max |X|^2, keys[2l+1] = max |Y|^2
+//   kind 1: keys[2l] = max |X - Y|^2, keys[2l+1] = max |X|^2
+__device__ __forceinline__ unsigned long long sq_key(zd a) {
+  return (unsigned long long)__double_as_longlong(fma(a.x, a.x, a.y * a.y));
+}
+__device__ __forceinline__ int nonfinite_bits(zd a) {
+  const unsigned long long x = (unsigned long long)__double_as_longlong(a.x),
+                           y = (unsigned long long)__double_as_longlong(a.y);
+  return ((x & 0x7FF0000000000000ull) == 0x7FF0000000000000ull) ||
+         ((y & 0x7FF0000000000000ull) == 0x7FF0000000000000ull);
+}
+__device__ __forceinline__ unsigned long long warp_umax(unsigned long long v) {
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, off);
+    v = o > v ? o : v;
+  }
   return v;
 }
 
-// block-wide max of v (NaN-propagating: any NaN makes the result NaN)
-__device__ double block_max(double v, double* sh) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int nan = isnan(v);
-  nan = __syncthreads_or(nan);
-  v = warp_max(v);
-  if (lane == 0) sh[w] = v;
-  __syncthreads();
-  double r = 0.0;
-  if (w == 0) {
-    r = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
-    r = warp_max(r);
-    if (lane == 0) sh[0] = r;
+template <int KIND>
+__global__ void __launch_bounds__(NT) lead_max_kernel(long long bs2, const zd* __restrict__ X,
+                                                      const zd* __restrict__ Y, const int* __restrict__ active,
+                                                      unsigned long long* __restrict__ keys, int* __restrict__ flags) {
+  __shared__ unsigned long long sh0[NT / 32], sh1[NT / 32];
+  const int l = blockIdx.y;
+  if (active && active[l] == 0) return;
+  unsigned long long k0 = 0, k1 = 0;
+  int bad = 0;
+  const zd* x = X + (long long)l * bs2;
+  const zd* y = Y + (long long)l * bs2;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < bs2; i += (long long)gridDim.x * blockDim.x) {
+    const zd u = x[i], v = y[i];
+    bad |= nonfinite_bits(u) | nonfinite_bits(v);
+    unsigned long long a, b;
+    if (KIND == 0) { a = sq_key(u); b = sq_key(v); }
+    else { a = sq_key(zsub(u, v)); b = sq_key(u); }
+    k0 = a > k0 ? a : k0;
+    k1 = b > k1 ? b : k1;
   }
+  bad = __syncthreads_or(bad);
+  k0 = warp_umax(k0);
+  k1 = warp_umax(k1);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) { sh0[w] = k0; sh1[w] = k1; }
   __syncthreads();
-  r = sh[0];
-  __syncthreads();
-  return nan ? __longlong_as_double(0x7ff8000000000000ULL) : r;
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < NT / 32; ++i) { k0 = sh0[i] > k0 ? sh0[i] : k0; k1 = sh1[i] > k1 ? sh1[i] : k1; }
+    atomicMax(&keys[2 * l], k0);
+    atomicMax(&keys[2 * l + 1], k1);
+    if (bad) atomicOr(&flags[l], 1);
+  }
 }
 
-__device__ __forceinline__ double zmod(zd a) { return sqrt(a.x * a.x + a.y * a.y); }
+__device__ __forceinline__ double key_sqrt(unsigned long long k) { return sqrt(__longlong_as_double((long long)k)); }
+
+bt_status lead_max(cudaStream_t st, int kind, long long bs2, int batch, const zd* X, const zd* Y, const int* active,
+                   unsigned long long* keys, int* flags) {
+  BT_CUDA_TRY(cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * 2 * batch, st));
+  BT_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * batch, st));
+  long long chunks = (bs2 + NT * 8 - 1) / (NT * 8);
+  if (chunks > 64) chunks = 64;
+  dim3 g((unsigned)chunks, (unsigned)batch);
+  if (kind == 0) lead_max_kernel<0><<<g, NT, 0, st>>>(bs2, X, Y, active, keys, flags);
+  else lead_max_kernel<1><<<g, NT, 0, st>>>(bs2, X, Y, active, keys, flags);
+  count_launch();
+  BT_CUDA_TRY(cudaGetLastError());
+  return BT_OK;
+}
 
 // ref[l] = max(max|n|, max|n'|)
-__global__ void __launch_bounds__(NT) ref_kernel(int bs2, const zd* __restrict__ n, const zd* __restrict__ np,
-                                                 double* __restrict__ ref) {
-  __shared__ double sh[32];
-  const int l = blockIdx.x;
-  double v = 0.0;
-  for (int e = threadIdx.x; e < bs2; e += blockDim.x)
-    v = fmax(v, fmax(zmod(n[(long long)l * bs2 + e]), zmod(np[(long long)l * bs2 + e])));
-  v = block_max(v, sh);
-  if (threadIdx.x == 0) ref[l] = v;
+__global__ void ref_kernel(int batch, const unsigned long long* __restrict__ keys, double* __restrict__ ref) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= batch) return;
+  ref[l] = key_sqrt(keys[2 * l] > keys[2 * l + 1] ? keys[2 * l] : keys[2 * l + 1]);
 }
 
 // convergence test of one iteration: lead l leaves the active set once max|a|,|b| <= tol*ref
-__global__ void __launch_bounds__(NT) check_kernel(int bs2, const zd* __restrict__ a, const zd* __restrict__ b,
-                                                   const double* __restrict__ ref, double tol, int it,
-                                                   int* __restrict__ active, int* __restrict__ iters,
-                                                   int* __restrict__ info, int* __restrict__ n_active) {
-  __shared__ double sh[32];
-  const int l = blockIdx.x;
-  if (active[l] == 0) return;
-  double v = 0.0;
-  for (int e = threadIdx.x; e < bs2; e += blockDim.x)
-    v = fmax(v, fmax(zmod(a[(long long)l * bs2 + e]), zmod(b[(long long)l * bs2 + e])));
-  v = block_max(v, sh);
-  if (threadIdx.x == 0) {
-    iters[l] = it;
-    if (isnan(v) || info[l] != 0) {
-      if (info[l] == 0) info[l] = BT_ERR_NONFINITE;
-      active[l] = 0;
-    } else if (v <= tol * ref[l]) {
-      active[l] = 0;
-    } else {
-      atomicAdd(n_active, 1);
-    }
+__global__ void check_kernel(int batch, const unsigned long long* __restrict__ keys, const int* __restrict__ flags,
+                             const double* __restrict__ ref, double tol, int it, int* __restrict__ active,
+                             int* __restrict__ iters, int* __restrict__ info, int* __restrict__ n_active) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= batch || active[l] == 0) return;
+  const double v = key_sqrt(keys[2 * l] > keys[2 * l + 1] ? keys[2 * l] : keys[2 * l + 1]);
+  iters[l] = it;
+  if (flags[l] || info[l] != 0) {
+    if (info[l] == 0) info[l] = BT_ERR_NONFINITE;
+    active[l] = 0;
+  } else if (v <= tol * ref[l]) {
+    active[l] = 0;
+  } else {
+    atomicAdd(n_active, 1);
   }
 }
 
@@ -123,36 +159,27 @@ __global__ void masked_copy_kernel(long long bs2, const zd* __restrict__ src, zd
 // Fixed-point convergence test: lead l converged when max|x_new - x| <= tol * max|x_new|.  A
 // lead whose geometric extrapolation (rate = this update / previous update) cannot reach the
 // tolerance within the remaining iterations is given up (left for decimation).
-__global__ void __launch_bounds__(NT) fpi_check_kernel(int bs2, const zd* __restrict__ xn, const zd* __restrict__ x,
-                                                       double tol, int it, int nfpi, int* __restrict__ active,
-                                                       int* __restrict__ conv, double* __restrict__ prev,
-                                                       int* __restrict__ n_active) {
-  __shared__ double sh[32];
-  const int l = blockIdx.x;
-  if (active[l] == 0) return;
-  double d = 0.0, r = 0.0;
-  for (int e = threadIdx.x; e < bs2; e += blockDim.x) {
-    const zd a = xn[(long long)l * bs2 + e], b = x[(long long)l * bs2 + e];
-    d = fmax(d, zmod(zsub(a, b)));
-    r = fmax(r, zmod(a));
-  }
-  d = block_max(d, sh);
-  r = block_max(r, sh);
-  if (threadIdx.x == 0) {
-    // linear convergence with rate rho = d_k / d_{k-1}: the distance to the fixed point is
-    // about d rho / (1 - rho).  The first update has no rate: accept it only 10x below tol.
-    const double rate = it > 1 && prev[l] > 0.0 ? d / prev[l] : 0.0;
-    const double err = it > 1 ? (rate < 1.0 ? d * rate / (1.0 - rate) : INFINITY) : 10.0 * d;
-    if (d <= tol * r && err <= tol * r) {
-      active[l] = 0;
-      conv[l] = 1;
-    } else {
-      const bool hopeless =
-          isnan(d) || (it > 1 && (rate >= 1.0 || d * pow(rate, (double)(nfpi - it)) > tol * r * (1.0 - rate)));
-      if (hopeless || it >= nfpi) { active[l] = 0; conv[l] = 0; }
-      else atomicAdd(n_active, 1);
-      prev[l] = d;
-    }
+__global__ void fpi_check_kernel(int batch, const unsigned long long* __restrict__ keys,
+                                 const int* __restrict__ flags, double tol, int it, int nfpi,
+                                 int* __restrict__ active, int* __restrict__ conv, double* __restrict__ prev,
+                                 int* __restrict__ n_active) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= batch || active[l] == 0) return;
+  const double d = flags[l] ? __longlong_as_double(0x7ff8000000000000ll) : key_sqrt(keys[2 * l]);
+  const double r = key_sqrt(keys[2 * l + 1]);
+  // linear convergence with rate rho = d_k / d_{k-1}: the distance to the fixed point is
+  // about d rho / (1 - rho).  The first update has no rate: accept it only 10x below tol.
+  const double rate = it > 1 && prev[l] > 0.0 ? d / prev[l] : 0.0;
+  const double err = it > 1 ? (rate < 1.0 ? d * rate / (1.0 - rate) : INFINITY) : 10.0 * d;
+  if (d <= tol * r && err <= tol * r) {
+    active[l] = 0;
+    conv[l] = 1;
+  } else {
+    const bool hopeless =
+        isnan(d) || (it > 1 && (rate >= 1.0 || d * pow(rate, (double)(nfpi - it)) > tol * r * (1.0 - rate)));
+    if (hopeless || it >= nfpi) { active[l] = 0; conv[l] = 0; }
+    else atomicAdd(n_active, 1);
+    prev[l] = d;
   }
 }
 
@@ -164,6 +191,8 @@ __global__ void not_kernel(int batch, const int* __restrict__ a, int* __restrict
 struct DecimWs {
   zd *a, *b, *a2, *b2, *e, *es, *g, *ag, *bg, *t;
   double* ref;
+  unsigned long long* keys;
+  int* flags;
   int* active;
   int* n_active;
   void* inv_ws;
@@ -172,7 +201,7 @@ struct DecimWs {
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
-size_t carve(void* base, int bs, int batch, DecimWs* w) {
+size_t carve(void* base, int bs, int batch, bool wide, DecimWs* w) {
   const size_t mat = align256((size_t)batch * bs * bs * sizeof(zd));
   char* p = static_cast<char*>(base);
   size_t off = 0;
@@ -180,18 +209,20 @@ size_t carve(void* base, int bs, int batch, DecimWs* w) {
   zd** mats[] = {&w->a, &w->b, &w->a2, &w->b2, &w->e, &w->es, &w->g, &w->ag, &w->bg, &w->t};
   for (zd** m : mats) *m = reinterpret_cast<zd*>(take(mat));
   w->ref = reinterpret_cast<double*>(take(sizeof(double) * batch));
+  w->keys = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * 2 * batch));
+  w->flags = reinterpret_cast<int*>(take(sizeof(int) * batch));
   w->active = reinterpret_cast<int*>(take(sizeof(int) * batch));
   w->n_active = reinterpret_cast<int*>(take(sizeof(int)));
-  w->inv_bytes = zinv_workspace_bytes(bs, batch);
+  w->inv_bytes = zinv_workspace_bytes(bs, batch, wide);
   w->inv_ws = take(w->inv_bytes);
   return off;
 }
 
 }  // namespace
 
-size_t decimate_workspace_bytes(int bs, int batch) {
+size_t decimate_workspace_bytes(int bs, int batch, bool wide) {
   DecimWs w;
-  return carve(nullptr, bs, batch, &w);
+  return carve(nullptr, bs, batch, wide, &w);
 }
 
 bt_status decimate(cudaStream_t st, int bs, int batch, const zd* m, const zd* n, const zd* np, double tol,
@@ -201,9 +232,11 @@ bt_status decimate(cudaStream_t st, int bs, int batch, const zd* m, const zd* n,
   const Engine fp64;
   const Engine& E = eng ? *eng : fp64;
   if (bs <= 0 || batch <= 0 || maxit <= 0 || batch > 65535) return BT_ERR_INVALID_ARG;
-  if (!ws || ws_bytes < decimate_workspace_bytes(bs, batch)) return BT_ERR_INVALID_ARG;
+  // wide inversion panels when the products run sliced and the workspace was sized for them
+  const bool wide = E.slices > 0 && ws_bytes >= decimate_workspace_bytes(bs, batch, true);
+  if (!ws || ws_bytes < decimate_workspace_bytes(bs, batch, wide)) return BT_ERR_INVALID_ARG;
   DecimWs w;
-  carve(ws, bs, batch, &w);
+  carve(ws, bs, batch, wide, &w);
   const long long bs2 = (long long)bs * bs;
   const size_t mat_bytes = (size_t)batch * bs2 * sizeof(zd);
   BT_CUDA_TRY(cudaMemcpyAsync(w.a, n, mat_bytes, cudaMemcpyDeviceToDevice, st));
@@ -211,7 +244,9 @@ bt_status decimate(cudaStream_t st, int bs, int batch, const zd* m, const zd* n,
   BT_CUDA_TRY(cudaMemcpyAsync(w.e, m, mat_bytes, cudaMemcpyDeviceToDevice, st));
   BT_CUDA_TRY(cudaMemcpyAsync(w.es, m, mat_bytes, cudaMemcpyDeviceToDevice, st));
   init_kernel<<<(batch + 255) / 256, 256, 0, st>>>(batch, mask, w.active, iters, info); count_launch();
-  ref_kernel<<<batch, NT, 0, st>>>((int)bs2, n, np, w.ref); count_launch();
+  BT_CUDA_TRY(cudaGetLastError());
+  BT_TRY(lead_max(st, 0, bs2, batch, n, np, nullptr, w.keys, w.flags));
+  ref_kernel<<<(batch + 255) / 256, 256, 0, st>>>(batch, w.keys, w.ref); count_launch();
   BT_CUDA_TRY(cudaGetLastError());
 
   int* h_active = h_pinned;
@@ -253,7 +288,9 @@ bt_status decimate(cudaStream_t st, int bs, int batch, const zd* m, const zd* n,
     std::swap(w.a, w.a2);
     std::swap(w.b, w.b2);
     if (cudaMemsetAsync(w.n_active, 0, sizeof(int), st) != cudaSuccess) { rc = BT_ERR_CUDA; break; }
-    check_kernel<<<batch, NT, 0, st>>>((int)bs2, w.a, w.b, w.ref, tol, it, w.active, iters, info, w.n_active); count_launch();
+    if ((rc = lead_max(st, 0, bs2, batch, w.a, w.b, w.active, w.keys, w.flags)) != BT_OK) break;
+    check_kernel<<<(batch + 255) / 256, 256, 0, st>>>(batch, w.keys, w.flags, w.ref, tol, it, w.active, iters, info,
+                                                      w.n_active); count_launch();
     if (cudaGetLastError() != cudaSuccess) { rc = BT_ERR_CUDA; break; }
     if (cudaMemcpyAsync(h_active, w.n_active, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) { rc = BT_ERR_CUDA; break; }
     if (cudaStreamSynchronize(st) != cudaSuccess) { rc = BT_ERR_CUDA; break; }
@@ -293,9 +330,11 @@ bt_status fixed_point(cudaStream_t st, int bs, int batch, const zd* m, const zd*
   const Engine fp64;
   const Engine& E = eng ? *eng : fp64;
   if (bs <= 0 || batch <= 0 || batch > 65535) return BT_ERR_INVALID_ARG;
-  if (!ws || ws_bytes < decimate_workspace_bytes(bs, batch)) return BT_ERR_INVALID_ARG;
+  // wide inversion panels when the products run sliced and the workspace was sized for them
+  const bool wide = E.slices > 0 && ws_bytes >= decimate_workspace_bytes(bs, batch, true);
+  if (!ws || ws_bytes < decimate_workspace_bytes(bs, batch, wide)) return BT_ERR_INVALID_ARG;
   DecimWs w;
-  carve(ws, bs, batch, &w);
+  carve(ws, bs, batch, wide, &w);
   const long long bs2 = (long long)bs * bs;
   const size_t mat_bytes = (size_t)batch * bs2 * sizeof(zd);
   const long long S = bs2;
@@ -322,7 +361,9 @@ bt_status fixed_point(cudaStream_t st, int bs, int batch, const zd* m, const zd*
     masked_copy_kernel<<<gcopy, 256, 0, st>>>(bs2, x, w.e, w.active); count_launch();  // keep x_k
     masked_copy_kernel<<<gcopy, 256, 0, st>>>(bs2, w.g, x, w.active); count_launch();
     BT_CUDA_TRY(cudaMemsetAsync(w.n_active, 0, sizeof(int), st));
-    fpi_check_kernel<<<batch, NT, 0, st>>>((int)bs2, x, w.e, tol, it, nfpi, w.active, conv, w.ref, w.n_active); count_launch();
+    BT_TRY(lead_max(st, 1, bs2, batch, x, w.e, w.active, w.keys, w.flags));
+    fpi_check_kernel<<<(batch + 255) / 256, 256, 0, st>>>(batch, w.keys, w.flags, tol, it, nfpi, w.active, conv, w.ref,
+                                                          w.n_active); count_launch();
     BT_CUDA_TRY(cudaGetLastError());
     BT_CUDA_TRY(cudaMemcpyAsync(h_pinned, w.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
     BT_CUDA_TRY(cudaStreamSynchronize(st));
@@ -336,7 +377,7 @@ bt_status fixed_point(cudaStream_t st, int bs, int batch, const zd* m, const zd*
 
 extern "C" bt_status bt_decimate_workspace_bytes(int bs, int batch, size_t* bytes) {
   if (!bytes || bs <= 0 || batch <= 0) return BT_ERR_INVALID_ARG;
-  *bytes = bt::decimate_workspace_bytes(bs, batch);
+  *bytes = bt::decimate_workspace_bytes(bs, batch, false);
   return BT_OK;
 }
 

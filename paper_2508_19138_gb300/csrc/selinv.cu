@@ -127,7 +127,7 @@ size_t layout(bt_ctx* c, const bt_selinv_desc& d, char* base) {
     x->obcG = cv.take<zd>(2 * E * B2);
     x->lead_iters = cv.take<int>(2 * E);
     x->lead_info = cv.take<int>(2 * E);
-    x->dec_bytes = bt::decimate_workspace_bytes(d.bs, (int)(2 * E));
+    x->dec_bytes = bt::decimate_workspace_bytes(d.bs, (int)(2 * E), is_split(d) && d.split_scope == 1);
     x->dec_ws = cv.take<char>(x->dec_bytes);
     if (d.obc_memo) {
       const size_t cap = (size_t)(d.memo_capacity > 0 ? d.memo_capacity : 4 * d.max_energies);
@@ -141,7 +141,7 @@ size_t layout(bt_ctx* c, const bt_selinv_desc& d, char* base) {
   x->fL = cv.take<double>(E);
   x->fR = cv.take<double>(E);
   x->Edev = cv.take<double>(E);
-  x->inv_bytes = bt::zinv_workspace_bytes(d.bs, (int)E);
+  x->inv_bytes = bt::zinv_workspace_bytes(d.bs, (int)E, is_split(d) && d.split_scope == 1);
   x->inv_ws = cv.take<char>(x->inv_bytes);
   if (is_split(d)) {
     // sweep products batch E; with split_scope = 1 also the decimation's 2E leads

@@ -48,7 +48,8 @@ namespace {
 
 constexpr int kDigitBits = 7;
 constexpr int kMaxSlices = 8;
-constexpr int kMaxGroups = 128;    // (pair, K segment) accumulations per tile
+constexpr int kMaxItems = 128;     // (slice pair, K segment) products per tile
+constexpr int kMaxGroups = 128;    // accumulations (drains) per tile
 constexpr int kSegBlocks = 15;     // K blocks per segment: 15 * 64 = 960 real terms, 960 * 2^12 < 2^22
 constexpr float kMagic = 12582912.0f;       // 1.5 * 2^23
 constexpr uint32_t kMagicBits = 0x4B400000u;
@@ -59,11 +60,14 @@ constexpr int kEpiWarps = 16;   // 4 lane quarters x 4 column quarters of the ac
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
 
-// One accumulation group = one slice pair (s, t) over K blocks [kb0, kb1).
+// One accumulation group = slice pairs (s, t) of equal weight, items [ib, ie), over K blocks
+// [kb0, kb1), summed in one TMEM accumulator.
 struct Schedule {
   int n_groups;
-  unsigned char s[kMaxGroups];    // slice of op(A) (1-based)
-  unsigned char t[kMaxGroups];    // slice of op(B) (1-based)
+  unsigned char s[kMaxItems];     // slice of op(A) (1-based)
+  unsigned char t[kMaxItems];     // slice of op(B) (1-based)
+  unsigned char ib[kMaxGroups];
+  unsigned char ie[kMaxGroups];
   unsigned char kb0[kMaxGroups];
   unsigned char kb1[kMaxGroups];
   unsigned char lsh[kMaxGroups];  // weight 2^(F - 7w) > 2^31: shift instead of multiply
@@ -207,17 +211,19 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!tile_of(tile, m0, n0, b)) continue;
         const int zA = (p.b_shared ? 0 : b) * p.S - 1, zB = (p.a_shared ? 0 : b) * p.S - 1;
         for (int g = 0; g < sc.n_groups && ok; ++g) {
-          for (int kb = sc.kb0[g]; kb < sc.kb1[g]; ++kb) {
-            if (!ptx::mbar_wait_bounded(&empty[stage], phase ^ 1u, abort_flag, kWaitLimitNs)) {
-              fail(b);
-              ok = false;
-              break;
+          for (int it = sc.ib[g]; it < sc.ie[g] && ok; ++it) {
+            for (int kb = sc.kb0[g]; kb < sc.kb1[g]; ++kb) {
+              if (!ptx::mbar_wait_bounded(&empty[stage], phase ^ 1u, abort_flag, kWaitLimitNs)) {
+                fail(b);
+                ok = false;
+                break;
+              }
+              ptx::mbar_arrive_expect_tx(&full[stage], kABytes + kBBytes);
+              ptx::tma_load_3d(sA + stage * kABytes, &tmA, &full[stage], kb * kKBlock, m0, zA + sc.t[it]);
+              ptx::tma_load_3d(sB + stage * kBBytes, &tmB, &full[stage], kb * kKBlock, n0, zB + sc.s[it]);
+              ++issued;
+              if (++stage == kStages) { stage = 0; phase ^= 1u; }
             }
-            ptx::mbar_arrive_expect_tx(&full[stage], kABytes + kBBytes);
-            ptx::tma_load_3d(sA + stage * kABytes, &tmA, &full[stage], kb * kKBlock, m0, zA + sc.t[g]);
-            ptx::tma_load_3d(sB + stage * kBBytes, &tmB, &full[stage], kb * kKBlock, n0, zB + sc.s[g]);
-            ++issued;
-            if (++stage == kStages) { stage = 0; phase ^= 1u; }
           }
         }
       }
@@ -247,24 +253,27 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           ptx::tc_fence_after();
           const uint32_t dcol = tmem + ab * (uint32_t)NT;
-          for (int kb = sc.kb0[g]; kb < sc.kb1[g]; ++kb) {
-            if (!ptx::mbar_wait_bounded(&full[stage], phase, abort_flag, kWaitLimitNs)) {
-              fail(b);
-              ok = false;
-              break;
-            }
-            ptx::tc_fence_after();
-            const uint32_t a_addr = ptx::smem_u32(sA + stage * kABytes);
-            const uint32_t b_addr = ptx::smem_u32(sB + stage * kBBytes);
-            const uint32_t acc0 = kb == sc.kb0[g] ? 0u : 1u;
+          uint32_t acc0 = 0u;  // the group's first MMA overwrites the accumulator
+          for (int it = sc.ib[g]; it < sc.ie[g] && ok; ++it) {
+            for (int kb = sc.kb0[g]; kb < sc.kb1[g]; ++kb) {
+              if (!ptx::mbar_wait_bounded(&full[stage], phase, abort_flag, kWaitLimitNs)) {
+                fail(b);
+                ok = false;
+                break;
+              }
+              ptx::tc_fence_after();
+              const uint32_t a_addr = ptx::smem_u32(sA + stage * kABytes);
+              const uint32_t b_addr = ptx::smem_u32(sB + stage * kBBytes);
 #pragma unroll
-            for (int k = 0; k < kKBlock / 16; ++k) {
-              const uint64_t ad = ptx::sdesc_kmajor_sw128(a_addr + k * 32);
-              const uint64_t bd = ptx::sdesc_kmajor_sw128(b_addr + k * 32);
-              ptx::umma_f16(dcol, ad, bd, kIdesc, k == 0 ? acc0 : 1u);
+              for (int k = 0; k < kKBlock / 16; ++k) {
+                const uint64_t ad = ptx::sdesc_kmajor_sw128(a_addr + k * 32);
+                const uint64_t bd = ptx::sdesc_kmajor_sw128(b_addr + k * 32);
+                ptx::umma_f16(dcol, ad, bd, kIdesc, k == 0 ? acc0 : 1u);
+              }
+              acc0 = 1u;
+              ptx::umma_commit(&empty[stage]);
+              if (++stage == kStages) { stage = 0; phase ^= 1u; }
             }
-            ptx::umma_commit(&empty[stage]);
-            if (++stage == kStages) { stage = 0; phase ^= 1u; }
           }
           if (ok) ptx::umma_commit(&tfull[ab]);
         }
@@ -585,12 +594,15 @@ bool encode_slices_map(CUtensorMap* map, void* base, int Kp, int rows, int depth
   return r == CUDA_SUCCESS;
 }
 
-// Groups: every slice pair (s, t) with s + t <= S + 1, in order of weight, times the K
-// segments of at most kSegBlocks blocks (balanced).  With pair weight w = s + t - 2 the group
-// enters the fixed-point sum with factor 2^(F - 7w): a shift for factors above 2^31, a 32-bit
-// multiplier down to 2^0, and below that a pre-scale 2^(F - 7w) in the drain's FFMA (rounding
-// below 2^-F of a leading digit product).  F = min(7S - 9, 50 - log2(K')): resolution below the
-// slicing error, and |sum| <= K' * 2^12 * 2^F * (1 + 2^-6) < 2^63.
+// Items: every slice pair (s, t) with s + t <= S + 1 times the K segments of at most kSegBlocks
+// blocks (balanced).  A group sums items of one segment and one pair weight w = s + t - 2 in one
+// accumulator while it stays an exact fp32 integer below 2^22: n pairs over L blocks of 64 real
+// terms reach at most n * L * 64 * 2^12, so n * L < 16 (one pair for long segments, up to 15 for
+// a single K block).  The group enters the fixed-point sum with factor 2^(F - 7w): a shift for
+// factors above 2^31, a 32-bit multiplier down to 2^0, and below that a pre-scale 2^(F - 7w) in
+// the drain's FFMA (rounding below 2^-F of a leading digit product).
+// F = min(7S - 9, 50 - log2(K')): resolution below the slicing error, and
+// |sum| <= K' * 2^12 * 2^F * (1 + 2^-6) < 2^63.
 bool make_schedule(int S, int KB, Schedule* sc, unsigned long long* bias, int* fix_bits) {
   *sc = Schedule{};
   int lg = 0;
@@ -599,25 +611,36 @@ bool make_schedule(int S, int KB, Schedule* sc, unsigned long long* bias, int* f
   if (F > 50 - lg) F = 50 - lg;
   const int nseg = (KB + kSegBlocks - 1) / kSegBlocks;
   unsigned long long bs = 0;
-  int ng = 0;
-  for (int d = 2; d <= S + 1; ++d)
-    for (int s = 1; s <= S; ++s) {
-      const int t = d - s;
-      if (t < 1 || t > S) continue;
+  int ni = 0, ng = 0;
+  for (int seg = 0; seg < nseg; ++seg) {
+    const int kb0 = (int)((long long)KB * seg / nseg), kb1 = (int)((long long)KB * (seg + 1) / nseg);
+    const int per_group = 15 / (kb1 - kb0);  // n * L < 16
+    for (int d = 2; d <= S + 1; ++d) {
       const int e = F - kDigitBits * (d - 2);
-      for (int seg = 0; seg < nseg; ++seg) {
-        if (ng >= kMaxGroups) return false;
-        sc->s[ng] = (unsigned char)s;
-        sc->t[ng] = (unsigned char)t;
-        sc->kb0[ng] = (unsigned char)((long long)KB * seg / nseg);
-        sc->kb1[ng] = (unsigned char)((long long)KB * (seg + 1) / nseg);
-        sc->lsh[ng] = (unsigned char)(e > 31 ? e : 0);
-        sc->mult[ng] = e > 31 ? 1u : (e >= 0 ? (1u << e) : 1u);
-        sc->fscale[ng] = e >= 0 ? 1.0f : ldexpf(1.0f, e);
-        bs += (unsigned long long)kMagicBits * ((unsigned long long)sc->mult[ng] << sc->lsh[ng]);
-        ++ng;
+      int in_group = 0;
+      for (int s = 1; s <= S; ++s) {
+        const int t = d - s;
+        if (t < 1 || t > S) continue;
+        if (ni >= kMaxItems) return false;
+        if (in_group == 0) {
+          if (ng >= kMaxGroups) return false;
+          sc->ib[ng] = (unsigned char)ni;
+          sc->kb0[ng] = (unsigned char)kb0;
+          sc->kb1[ng] = (unsigned char)kb1;
+          sc->lsh[ng] = (unsigned char)(e > 31 ? e : 0);
+          sc->mult[ng] = e > 31 ? 1u : (e >= 0 ? (1u << e) : 1u);
+          sc->fscale[ng] = e >= 0 ? 1.0f : ldexpf(1.0f, e);
+          bs += (unsigned long long)kMagicBits * ((unsigned long long)sc->mult[ng] << sc->lsh[ng]);
+          ++ng;
+        }
+        sc->s[ni] = (unsigned char)s;
+        sc->t[ni] = (unsigned char)t;
+        ++ni;
+        sc->ie[ng - 1] = (unsigned char)ni;
+        if (++in_group == per_group) in_group = 0;
       }
     }
+  }
   sc->n_groups = ng;
   *bias = bs;
   *fix_bits = F;

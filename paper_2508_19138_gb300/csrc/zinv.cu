@@ -23,36 +23,50 @@ namespace bt {
 namespace {
 
 constexpr int kSmallN = 96;
+constexpr int kClusterMinN = 192;  // below this a single CTA holds the panel comfortably
 constexpr int NT = 256;
 constexpr size_t kSmemLimit = 227 * 1024;
 
-// block-wide argmax of v over threads (ties -> smaller index); result broadcast
-__device__ __forceinline__ void block_argmax(double& v, int& idx, double* sv, int* si) {
+// block-wide argmax of the key k over threads (ties -> smaller index); result broadcast.
+// Keys are compared as integers (see pivot_key).
+__device__ __forceinline__ void block_argmax(unsigned long long& k, int& idx, unsigned long long* sk, int* si) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
-    double ov = __shfl_down_sync(0xffffffffu, v, off);
-    int oi = __shfl_down_sync(0xffffffffu, idx, off);
-    if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+    const unsigned long long ok = __shfl_down_sync(0xffffffffu, k, off);
+    const int oi = __shfl_down_sync(0xffffffffu, idx, off);
+    if (ok > k || (ok == k && oi < idx)) { k = ok; idx = oi; }
   }
-  if (lane == 0) { sv[w] = v; si[w] = idx; }
+  if (lane == 0) { sk[w] = k; si[w] = idx; }
   __syncthreads();
   if (w == 0) {
     const int nw = blockDim.x >> 5;
-    v = lane < nw ? sv[lane] : -1.0;
+    k = lane < nw ? sk[lane] : 0ull;
     idx = lane < nw ? si[lane] : 0x7fffffff;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-      double ov = __shfl_down_sync(0xffffffffu, v, off);
-      int oi = __shfl_down_sync(0xffffffffu, idx, off);
-      if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+      const unsigned long long ok = __shfl_down_sync(0xffffffffu, k, off);
+      const int oi = __shfl_down_sync(0xffffffffu, idx, off);
+      if (ok > k || (ok == k && oi < idx)) { k = ok; idx = oi; }
     }
-    if (lane == 0) { sv[0] = v; si[0] = idx; }
+    if (lane == 0) { sk[0] = k; si[0] = idx; }
   }
   __syncthreads();
-  v = sv[0];
+  k = sk[0];
   idx = si[0];
   __syncthreads();
+}
+
+// Pivot key of a candidate entry: the bits of |re| + |im| (non-negative doubles order like their
+// bit patterns), Inf / NaN clamped to the largest finite value so that they are still chosen and
+// then flagged.  Integer compares keep the pivot search off GB300's narrow FP64 pipe.
+__device__ __forceinline__ unsigned long long pivot_key(zd a) {
+  const unsigned long long k = (unsigned long long)__double_as_longlong(zabs1(a));
+  return k >= 0x7FF0000000000000ull ? 0x7FEFFFFFFFFFFFFFull : k;
+}
+// (key, pos) ordering of pivot candidates: larger key, then smaller position
+__device__ __forceinline__ bool cand_better(unsigned long long k1, int p1, unsigned long long k2, int p2) {
+  return k1 > k2 || (k1 == k2 && p1 < p2);
 }
 
 __device__ __forceinline__ int pivot_code(zd piv) {
@@ -63,18 +77,18 @@ __device__ __forceinline__ int pivot_code(zd piv) {
 
 // One Gauss-Jordan step on a row-major panel P (rows 0..n-1, columns 0..kb-1, leading
 // dimension ld) in shared memory, pivot column jj, pivot row searched in rows >= j.
-// Returns the pivot row; *code gets a failure code (thread 0 view).
-__device__ int gj_step(zd* P, int n, int kb, int ld, int j, int jj, zd* colj, zd* rowj, double* sv, int* si,
-                       int* code) {
-  // pivot search
-  double best = -1.0;
+// Returns the pivot row; *code gets a failure code (thread 0 view).  The pivot's reciprocal is
+// formed once (thread 0) and broadcast.
+__device__ int gj_step(zd* P, int n, int kb, int ld, int j, int jj, zd* colj, zd* rowj, unsigned long long* sk,
+                       int* si, zd* s_ip, int* code) {
+  // pivot search (rows scanned in increasing order: strict > keeps the first on ties)
+  unsigned long long best = 0;
   int bi = 0x7fffffff;
   for (int r = j + threadIdx.x; r < n; r += blockDim.x) {
-    double v = zabs1(P[r * ld + jj]);
-    if (!(v <= 1.0e308)) v = 1.0e308;  // NaN / Inf: still a candidate, flagged below
-    if (v > best) { best = v; bi = r; }
+    const unsigned long long k = pivot_key(P[r * ld + jj]);
+    if (bi == 0x7fffffff || k > best) { best = k; bi = r; }
   }
-  block_argmax(best, bi, sv, si);
+  block_argmax(best, bi, sk, si);
   const int p = bi;
   if (p != j) {
     for (int c = threadIdx.x; c < kb; c += blockDim.x) {
@@ -84,10 +98,14 @@ __device__ int gj_step(zd* P, int n, int kb, int ld, int j, int jj, zd* colj, zd
     }
   }
   __syncthreads();
-  const zd piv = P[j * ld + jj];
-  const int pc = pivot_code(piv);
-  if (pc && threadIdx.x == 0 && *code == 0) *code = pc;
-  const zd ip = pc ? zmake(0.0, 0.0) : zinv(piv);
+  if (threadIdx.x == 0) {
+    const zd piv = P[j * ld + jj];
+    const int pc = pivot_code(piv);
+    if (pc && *code == 0) *code = pc;
+    *s_ip = pc ? zmake(0.0, 0.0) : zinv(piv);
+  }
+  __syncthreads();
+  const zd ip = *s_ip;
   for (int r = threadIdx.x; r < n; r += blockDim.x) colj[r] = P[r * ld + jj];
   for (int c = threadIdx.x; c < kb; c += blockDim.x) rowj[c] = zmul(P[j * ld + c], ip);
   __syncthreads();
@@ -124,15 +142,16 @@ __global__ void __launch_bounds__(NT) zinv_small_kernel(int n, zd* __restrict__ 
   zd* colj = P + n * ld;
   zd* rowj = colj + n;
   int* perm = reinterpret_cast<int*>(rowj + n);
-  __shared__ double sv[32];
+  __shared__ unsigned long long sk[32];
   __shared__ int si[32];
   __shared__ int code;
+  __shared__ zd s_ip;
   zd* Ag = A + sA * b;
   if (threadIdx.x == 0) code = 0;
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) P[(e / n) * ld + (e % n)] = Ag[e];
   __syncthreads();
   for (int j = 0; j < n; ++j) {
-    int p = gj_step(P, n, n, ld, j, j, colj, rowj, sv, si, &code);
+    int p = gj_step(P, n, n, ld, j, j, colj, rowj, sk, si, &s_ip, &code);
     if (threadIdx.x == 0) perm[j] = p;
   }
   __syncthreads();
@@ -154,10 +173,17 @@ __global__ void __launch_bounds__(NT) zinv_small_kernel(int n, zd* __restrict__ 
 
 // Panel of kb columns eliminated by a cluster of CL CTAs: CTA r of the cluster holds rows
 // [r R, r R + R) of the panel in its shared memory (R = ceil(n / CL)), so the panel's FP64
-// updates use CL SMs instead of one.  Per column: each CTA proposes its best pivot candidate,
-// all CTAs read every candidate through distributed shared memory and agree on the same pivot
-// (max |re| + |im|, first index on ties), read the pivot row and exchange rows j and p through
-// DSMEM, then update their own rows.  Two cluster barriers per column; no spin-waits.
+// updates use CL SMs instead of one.  Rows are not exchanged while the panel is eliminated:
+// every CTA keeps the same position map of the row exchanges (row_at / pos_of), and the pivot
+// search of column j runs over the rows whose current position is >= j, ties going to the
+// smaller position, which selects the pivot sequence of elimination with physical exchanges.
+// Per column: warp 0 of each CTA publishes its best candidate (key, position, row and the row's
+// kb entries) in a buffer of parity j & 1, one cluster barrier, then every CTA reads all
+// candidates and the winning row through distributed shared memory and updates its own rows.
+// A buffer of parity j & 1 is rewritten two columns later, after the barrier of column j + 1,
+// which no CTA passes before every CTA has finished reading it.  At the end each CTA writes its
+// rows to their final positions.  perm[] records the exchanges as the LAPACK-style sequence
+// (row j swapped with row perm[j], in order), as the rest of the blocked inverse expects.
 template <int CL>
 __global__ void __launch_bounds__(NT) gj_panel_cluster_kernel(int n, int k0, int kb, zd* __restrict__ A,
                                                               long long sA, int* __restrict__ perm_all, int* info,
@@ -173,109 +199,134 @@ __global__ void __launch_bounds__(NT) gj_panel_cluster_kernel(int n, int k0, int
   const int ld = kb + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   zd* P = reinterpret_cast<zd*>(smem_raw);  // [R][ld]
-  zd* colj = P + (size_t)R * ld;            // [R]
-  zd* rowj = colj + R;                      // [kb]
-  zd* pivrow = rowj + kb;                   // [kb]
-  zd* swapbuf = pivrow + kb;                // [kb]
-  __shared__ double cand_v;
-  __shared__ int cand_i;
-  __shared__ double sv[32];
-  __shared__ int si[32];
-  __shared__ int code;
-  __shared__ int gp;
+  zd* pub = P + (size_t)R * ld;             // [2][kb]  published candidate rows
+  zd* rowj = pub + 2 * kb;                  // [kb]     scaled pivot row
+  int* pos_of = reinterpret_cast<int*>(rowj + kb);  // [n] current position of each row
+  int* row_at = pos_of + n;                          // [n] row at each position
+  __shared__ unsigned long long cand_key[2];
+  __shared__ int cand_pos[2], cand_row[2];
+  __shared__ zd s_ip;
+  __shared__ int s_q, s_code;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   zd* Ag = A + sA * b;
   int* perm = perm_all + (long long)n * b;
-  if (threadIdx.x == 0) code = 0;
-  for (int e = threadIdx.x; e < rows * kb; e += blockDim.x) {
+  if (tid == 0) s_code = 0;
+  for (int r = tid; r < n; r += blockDim.x) { pos_of[r] = r; row_at[r] = r; }
+  for (int e = tid; e < rows * kb; e += blockDim.x) {
     const int r = e / kb, c = e - r * kb;
     P[r * ld + c] = Ag[(long long)(r0 + r) * n + k0 + c];
   }
   __syncthreads();
+  // row update layout: 4 threads per row, columns c = sub, sub + 4, ...
+  const int sub = tid & 3;
+  const int rows_per_pass = blockDim.x >> 2;
   for (int jj = 0; jj < kb; ++jj) {
-    const int j = k0 + jj;
-    // local pivot candidate among rows >= j
-    double best = -1.0;
-    int bi = 0x7fffffff;
-    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
-      if (r0 + r < j) continue;
-      double v = zabs1(P[r * ld + jj]);
-      if (!(v <= 1.0e308)) v = 1.0e308;
-      if (v > best) { best = v; bi = r0 + r; }
-    }
-    block_argmax(best, bi, sv, si);
-    if (threadIdx.x == 0) { cand_v = best; cand_i = bi; }
-    cluster.sync();  // candidates visible
-    if (threadIdx.x < 32) {  // lane q reads CTA q's candidate (all remote loads in parallel)
-      const int q = threadIdx.x;
-      double v = q < CL ? *cluster.map_shared_rank(&cand_v, q) : -1.0;
-      int p = q < CL ? *cluster.map_shared_rank(&cand_i, q) : 0x7fffffff;
+    const int j = k0 + jj, par = jj & 1;
+    if (warp == 0) {
+      // best local candidate among rows at positions >= j
+      unsigned long long bk = 0;
+      int bp = 0x7fffffff, br = -1;
+      for (int r = lane; r < rows; r += 32) {
+        const int pos = pos_of[r0 + r];
+        if (pos < j) continue;
+        const unsigned long long k = pivot_key(P[r * ld + jj]);
+        if (br < 0 || cand_better(k, pos, bk, bp)) { bk = k; bp = pos; br = r0 + r; }
+      }
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
-        const double ov = __shfl_down_sync(0xffffffffu, v, off);
-        const int oi = __shfl_down_sync(0xffffffffu, p, off);
-        if (ov > v || (ov == v && oi < p)) { v = ov; p = oi; }
+        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, off);
+        const int op = __shfl_xor_sync(0xffffffffu, bp, off);
+        const int orr = __shfl_xor_sync(0xffffffffu, br, off);
+        if (orr >= 0 && (br < 0 || cand_better(ok, op, bk, bp))) { bk = ok; bp = op; br = orr; }
       }
-      if (q == 0) gp = p;
+      if (lane == 0) { cand_key[par] = bk; cand_pos[par] = br < 0 ? 0x7fffffff : bp; cand_row[par] = br; }
+      if (br >= 0)
+        for (int c = lane; c < kb; c += 32) pub[par * kb + c] = P[(br - r0) * ld + c];
     }
-    __syncthreads();
-    const int p = gp;
-    const int own_p = p / R, own_j = j / R;
-    {
-      const zd* rp = cluster.map_shared_rank(P, own_p) + (size_t)(p - own_p * R) * ld;
-      for (int c = threadIdx.x; c < kb; c += blockDim.x) pivrow[c] = rp[c];
-      if (rank == own_p && p != j) {
-        const zd* rj = cluster.map_shared_rank(P, own_j) + (size_t)(j - own_j * R) * ld;
-        for (int c = threadIdx.x; c < kb; c += blockDim.x) swapbuf[c] = rj[c];
+    cluster.sync();  // candidates of column j visible cluster-wide
+    if (warp == 0) {
+      unsigned long long bk = 0;
+      int bp = 0x7fffffff, br = -1, bq = 0;
+      if (lane < CL) {
+        bk = *cluster.map_shared_rank(&cand_key[par], lane);
+        bp = *cluster.map_shared_rank(&cand_pos[par], lane);
+        br = *cluster.map_shared_rank(&cand_row[par], lane);
+        bq = lane;
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, off);
+        const int op = __shfl_xor_sync(0xffffffffu, bp, off);
+        const int orr = __shfl_xor_sync(0xffffffffu, br, off);
+        const int oq = __shfl_xor_sync(0xffffffffu, bq, off);
+        if (orr >= 0 && (br < 0 || cand_better(ok, op, bk, bp))) { bk = ok; bp = op; br = orr; bq = oq; }
+      }
+      // every lane now holds the winner (row br >= 0 always: position j itself is a candidate);
+      // one remote read of the winning row (kb <= 32 lanes), pivot broadcast from lane jj
+      const zd* wrow = cluster.map_shared_rank(pub, bq) + par * kb;
+      const zd wv = lane < kb ? wrow[lane] : zmake(0.0, 0.0);
+      const zd piv = zmake(__shfl_sync(0xffffffffu, wv.x, jj), __shfl_sync(0xffffffffu, wv.y, jj));
+      const int pc = pivot_code(piv);
+      zd ip = zmake(0.0, 0.0);
+      if (lane == 0 && !pc) ip = zinv(piv);  // one lane: GB300's FP64 pipe is narrow
+      ip = zmake(__shfl_sync(0xffffffffu, ip.x, 0), __shfl_sync(0xffffffffu, ip.y, 0));
+      if (lane < kb) rowj[lane] = lane == jj ? ip : zmul(wv, ip);
+      if (lane == 0) {
+        s_ip = ip;
+        s_q = br;
+        if (pc && s_code == 0) s_code = pc;
+        // exchange positions j and pos_of[br]
+        const int cur = pos_of[br], rj = row_at[j];
+        if (rank == 0) perm[j] = cur;
+        row_at[cur] = rj;
+        pos_of[rj] = cur;
+        row_at[j] = br;
+        pos_of[br] = j;
       }
     }
-    cluster.sync();  // every read of rows p and j and of the candidates is done
-    if (p != j) {
-      if (rank == own_j)
-        for (int c = threadIdx.x; c < kb; c += blockDim.x) P[(j - r0) * ld + c] = pivrow[c];
-      if (rank == own_p)
-        for (int c = threadIdx.x; c < kb; c += blockDim.x) P[(p - r0) * ld + c] = swapbuf[c];
-    }
-    const zd piv = pivrow[jj];
-    const int pc = pivot_code(piv);
-    if (pc && threadIdx.x == 0 && code == 0) code = pc;
-    const zd ip = pc ? zmake(0.0, 0.0) : zinv(piv);
-    if (rank == 0 && threadIdx.x == 0) perm[j] = p;
-    for (int c = threadIdx.x; c < kb; c += blockDim.x) rowj[c] = zmul(pivrow[c], ip);
     __syncthreads();
-    for (int r = threadIdx.x; r < rows; r += blockDim.x) colj[r] = P[r * ld + jj];
-    __syncthreads();
-    for (int e = threadIdx.x; e < rows * kb; e += blockDim.x) {
-      const int r = e / kb, c = e - r * kb;
-      zd* pe = P + r * ld + c;
-      if (r0 + r == j) {
-        *pe = (c == jj) ? ip : rowj[c];
-      } else if (c == jj) {
-        *pe = zmul(zmake(-colj[r].x, -colj[r].y), ip);
-      } else {
-        zd a = *pe;
-        const zd f = colj[r], g = rowj[c];
-        a.x = fma(-f.x, g.x, a.x);
-        a.x = fma(f.y, g.y, a.x);
-        a.y = fma(-f.x, g.y, a.y);
-        a.y = fma(-f.y, g.x, a.y);
-        *pe = a;
+    const zd ip = s_ip;
+    const int q = s_q;
+    for (int rb = 0; rb < rows; rb += rows_per_pass) {  // uniform trip count (the __syncwarp below)
+      const int r = rb + (tid >> 2);
+      const bool act = r < rows;
+      const zd f = act ? P[r * ld + jj] : zmake(0.0, 0.0);
+      __syncwarp();
+      if (act) {
+        if (r0 + r == q) {
+          for (int c = sub; c < kb; c += 4) P[r * ld + c] = rowj[c];
+        } else {
+          for (int c = sub; c < kb; c += 4) {
+            if (c == jj) {
+              P[r * ld + c] = zmul(zmake(-f.x, -f.y), ip);
+            } else {
+              zd a = P[r * ld + c];
+              const zd g = rowj[c];
+              a.x = fma(-f.x, g.x, a.x);
+              a.x = fma(f.y, g.y, a.x);
+              a.y = fma(-f.x, g.y, a.y);
+              a.y = fma(-f.y, g.x, a.y);
+              P[r * ld + c] = a;
+            }
+          }
+        }
       }
     }
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < rows * kb; e += blockDim.x) {
+  // rows to their final positions (pos_of is a permutation: disjoint destinations)
+  for (int e = tid; e < rows * kb; e += blockDim.x) {
     const int r = e / kb, c = e - r * kb;
-    Ag[(long long)(r0 + r) * n + k0 + c] = P[r * ld + c];
+    Ag[(long long)pos_of[r0 + r] * n + k0 + c] = P[r * ld + c];
   }
-  if (rank == 0 && threadIdx.x == 0 && code && info && info[b] == 0) info[b] = code;
+  if (rank == 0 && tid == 0 && s_code && info && info[b] == 0) info[b] = s_code;
   cluster.sync();  // no CTA leaves while another may still read its shared memory
 }
 
-constexpr int kPanelCluster = 8;
-constexpr int kClusterMinN = 192;  // below this a single CTA holds the panel comfortably
-size_t cluster_panel_smem(int n, int kb) {
-  const int R = (n + kPanelCluster - 1) / kPanelCluster;
-  return (size_t)R * (kb + 1) * sizeof(zd) + (size_t)(R + 3 * kb) * sizeof(zd) + 16;
+constexpr int kPanelCluster = 8;  // largest cluster (portable size)
+size_t cluster_panel_smem(int n, int kb, int cl) {
+  const int R = (n + cl - 1) / cl;
+  return (size_t)R * (kb + 1) * sizeof(zd) + (size_t)(3 * kb) * sizeof(zd) + 2 * (size_t)n * sizeof(int) + 16;
 }
 
 // Panel of kb columns starting at k0: eliminated in shared memory, written back in place.
@@ -289,9 +340,10 @@ __global__ void __launch_bounds__(NT) gj_panel_kernel(int n, int k0, int kb, zd*
   zd* P = reinterpret_cast<zd*>(smem_raw);
   zd* colj = P + n * ld;
   zd* rowj = colj + n;
-  __shared__ double sv[32];
+  __shared__ unsigned long long sk[32];
   __shared__ int si[32];
   __shared__ int code;
+  __shared__ zd s_ip;
   zd* Ag = A + sA * b;
   int* perm = perm_all + (long long)n * b;
   if (threadIdx.x == 0) code = 0;
@@ -301,7 +353,7 @@ __global__ void __launch_bounds__(NT) gj_panel_kernel(int n, int k0, int kb, zd*
   }
   __syncthreads();
   for (int jj = 0; jj < kb; ++jj) {
-    int p = gj_step(P, n, kb, ld, k0 + jj, jj, colj, rowj, sv, si, &code);
+    int p = gj_step(P, n, kb, ld, k0 + jj, jj, colj, rowj, sk, si, &s_ip, &code);
     if (threadIdx.x == 0) perm[k0 + jj] = p;
   }
   for (int e = threadIdx.x; e < n * kb; e += blockDim.x) {
@@ -311,61 +363,117 @@ __global__ void __launch_bounds__(NT) gj_panel_kernel(int n, int k0, int kb, zd*
   if (threadIdx.x == 0 && code && info && info[b] == 0) info[b] = code;
 }
 
-// Row exchanges of the panel applied to the columns outside it; rows K copied to T and zeroed.
-__global__ void gj_swap_copy_kernel(int n, int k0, int kb, zd* __restrict__ A, long long sA,
-                                    const int* __restrict__ perm_all, zd* __restrict__ T, long long sT,
-                                    const int* __restrict__ active) {
+// Row exchanges of the panel (the LAPACK-style sequence perm[k0..k0+kb)) applied to the columns
+// outside it as one permutation of the touched rows (at most 2 kb): all touched entries of a
+// column are read first (independent loads, 8 rows in flight per column), then written to their
+// new rows.  Rows K of those columns are copied to T and zeroed; T's panel columns are zeroed,
+// so that one rank-kb GEMM over all n columns leaves the panel columns unchanged.
+// Block = 32 columns x 8 row slots of one matrix.
+constexpr int kSwapCols = 32;
+constexpr int kSwapRows = 8;
+constexpr int kMaxTouched = 64;  // 2 * the largest panel width
+__global__ void __launch_bounds__(kSwapCols * kSwapRows) gj_swap_copy_kernel(int n, int k0, int kb,
+                                                                             zd* __restrict__ A, long long sA,
+                                                                             const int* __restrict__ perm_all,
+                                                                             zd* __restrict__ T, long long sT,
+                                                                             const int* __restrict__ active) {
+  __shared__ int pos[kMaxTouched], src[kMaxTouched];
+  __shared__ int cnt;
+  __shared__ zd stage[kMaxTouched][kSwapCols + 1];
   const int b = blockIdx.y;
   if (active && active[b] == 0) return;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n || (c >= k0 && c < k0 + kb)) return;
-  zd* Ag = A + sA * b;
   const int* perm = perm_all + (long long)n * b;
-  for (int jj = 0; jj < kb; ++jj) {
-    const int j = k0 + jj, p = perm[j];
-    if (p != j) {
-      zd t = Ag[(long long)j * n + c];
-      Ag[(long long)j * n + c] = Ag[(long long)p * n + c];
-      Ag[(long long)p * n + c] = t;
+  const int tx = threadIdx.x % kSwapCols, ty = threadIdx.x / kSwapCols;
+  if (threadIdx.x == 0) {
+    // pos[i] <- the row src[i] after the exchanges, for every touched row
+    int m = 0;
+    for (int jj = 0; jj < kb; ++jj) {
+      const int j = k0 + jj, p = perm[j];
+      int ij = -1, ip = -1;
+      for (int i = 0; i < m; ++i) {
+        if (pos[i] == j) ij = i;
+        if (pos[i] == p) ip = i;
+      }
+      if (ij < 0) { pos[m] = j; src[m] = j; ij = m++; }
+      if (ip < 0) { pos[m] = p; src[m] = p; ip = m++; }
+      const int t = src[ij];
+      src[ij] = src[ip];
+      src[ip] = t;
     }
+    cnt = m;
   }
+  __syncthreads();
+  const int c = blockIdx.x * kSwapCols + tx;
+  const bool col_ok = c < n;
+  const bool panel = c >= k0 && c < k0 + kb;
+  zd* Ag = A + sA * b;
   zd* Tb = T + sT * b;
-  for (int jj = 0; jj < kb; ++jj) {
-    Tb[(long long)jj * n + c] = Ag[(long long)(k0 + jj) * n + c];
-    Ag[(long long)(k0 + jj) * n + c] = zmake(0.0, 0.0);
+  const int m = cnt;
+  if (col_ok && !panel)
+    for (int i = ty; i < m; i += kSwapRows) stage[i][tx] = Ag[(long long)src[i] * n + c];
+  __syncthreads();  // every touched entry of these columns read before any is written
+  if (!col_ok) return;
+  if (panel) {
+    for (int jj = ty; jj < kb; jj += kSwapRows) Tb[(long long)jj * n + c] = zmake(0.0, 0.0);
+    return;
+  }
+  for (int i = ty; i < m; i += kSwapRows) {
+    const int q = pos[i];
+    if (q >= k0 && q < k0 + kb) {
+      Tb[(long long)(q - k0) * n + c] = stage[i][tx];
+      Ag[(long long)q * n + c] = zmake(0.0, 0.0);
+    } else {
+      Ag[(long long)q * n + c] = stage[i][tx];
+    }
   }
 }
 
-// Row exchanges undone as column exchanges in reverse order; one thread per row.
-__global__ void gj_unscramble_kernel(int n, zd* __restrict__ A, long long sA, const int* __restrict__ perm_all,
-                                     const int* __restrict__ active) {
+// Row exchanges undone as column exchanges in reverse order, composed into one column
+// permutation: out[r][c] = row_r[src[c]].  One row per warp (blockDim / 32 rows per block), each
+// staged in shared memory (coalesced read, gather from shared memory, coalesced write).
+constexpr int kUnscrRows = 4;
+__global__ void __launch_bounds__(32 * kUnscrRows) gj_unscramble_kernel(int n, zd* __restrict__ A, long long sA,
+                                                                        const int* __restrict__ perm_all,
+                                                                        const int* __restrict__ active) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nrows = blockDim.x >> 5;
+  zd* rows = reinterpret_cast<zd*>(smem_raw);                  // [nrows][n]
+  int* src = reinterpret_cast<int*>(rows + (size_t)nrows * n);  // [n]
   const int b = blockIdx.y;
   if (active && active[b] == 0) return;
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int* perm = perm_all + (long long)n * b;
+  for (int c = threadIdx.x; c < n; c += blockDim.x) src[c] = c;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int j = n - 1; j >= 0; --j) {
+      const int p = perm[j];
+      if (p != j) { const int t = src[j]; src[j] = src[p]; src[p] = t; }
+    }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = blockIdx.x * nrows + warp;
   if (r >= n) return;
   zd* row = A + sA * b + (long long)r * n;
-  const int* perm = perm_all + (long long)n * b;
-  for (int j = n - 1; j >= 0; --j) {
-    const int p = perm[j];
-    if (p != j) {
-      zd t = row[j];
-      row[j] = row[p];
-      row[p] = t;
-    }
-  }
+  zd* buf = rows + (size_t)warp * n;
+  for (int c = lane; c < n; c += 32) buf[c] = row[c];
+  __syncwarp();
+  for (int c = lane; c < n; c += 32) row[c] = buf[src[c]];
 }
 
-int panel_width(int n) {
-  // The panel elimination costs ~n kb^2 complex FMAs per panel on ONE SM per matrix (4 n^2 kb
-  // DFMA per inverse), the rank-kb updates n^3 on all SMs; kb = 16 balances the two on GB300's
-  // slow FP64 pipe (kb = 32 made the panels ~27 % of a split-precision step).
-  for (int kb = 16; kb >= 4; kb >>= 1) {
+int panel_width(int n, bool wide) {
+  // The panel elimination costs ~n kb^2 complex FMAs per panel on the SMs of one matrix's
+  // cluster (4 n^2 kb DFMA per inverse), the rank-kb updates n^3 on all SMs.  On GB300's slow
+  // FP64 pipe kb = 16 balances the two when the updates are FP64 GEMMs; when they run sliced on
+  // the tensor cores (wide), kb = 32 fills one 64-deep K block of the split GEMM (K' = 2 kb)
+  // and halves the number of update launches.
+  for (int kb = wide ? 32 : 16; kb >= 4; kb >>= 1) {
     size_t need = (size_t)n * (kb + 1) * sizeof(zd) + (size_t)(n + kb) * sizeof(zd) + 1024;
-    if (need <= kSmemLimit) return kb;
+    if (need <= kSmemLimit || n >= kClusterMinN) return kb;
   }
   return 0;
 }
 
+size_t unscramble_smem(int n, int rows) { return (size_t)rows * n * sizeof(zd) + (size_t)n * sizeof(int); }
 size_t small_smem(int n) { return (size_t)n * (n + 1) * sizeof(zd) + 2 * (size_t)n * sizeof(zd) + n * sizeof(int) + 16; }
 size_t panel_smem(int n, int kb) { return (size_t)n * (kb + 1) * sizeof(zd) + (size_t)(n + kb) * sizeof(zd) + 16; }
 
@@ -382,7 +490,14 @@ bt_status set_smem_limits() {
   const int small_max = (int)small_smem(kSmallN);
   const int panel_max = (int)(kSmemLimit - 1024);  // leaves room for the kernels' static shared memory
   if (cudaFuncSetAttribute(zinv_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, small_max) != cudaSuccess ||
-      cudaFuncSetAttribute(gj_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, panel_max) != cudaSuccess)
+      cudaFuncSetAttribute(gj_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, panel_max) != cudaSuccess ||
+      cudaFuncSetAttribute(gj_panel_cluster_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, panel_max) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(gj_panel_cluster_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, panel_max) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(gj_panel_cluster_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, panel_max) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(gj_unscramble_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, panel_max) != cudaSuccess)
     return BT_ERR_CUDA;
   done[dev] = true;
   return BT_OK;
@@ -390,9 +505,9 @@ bt_status set_smem_limits() {
 
 }  // namespace
 
-size_t zinv_workspace_bytes(int n, int batch) {
+size_t zinv_workspace_bytes(int n, int batch, bool wide) {
   if (n <= kSmallN) return 0;
-  int kb = panel_width(n);
+  int kb = panel_width(n, wide);
   if (kb == 0) return 0;
   // perm [batch][n] ints (rounded to 256 B) + T [batch][kb][n] complex
   size_t perm = ((size_t)batch * n * sizeof(int) + 255) / 256 * 256;
@@ -413,55 +528,67 @@ bt_status zinv(cudaStream_t st, int n, zd* A, long long sA, int batch, int* info
     BT_CUDA_TRY(cudaGetLastError());
     return BT_OK;
   }
-  const int kb = panel_width(n);
+  // wide panels when the updates run sliced and the workspace was sized for them
+  const bool wide = E.slices > 0 && ws_bytes >= zinv_workspace_bytes(n, batch, true);
+  const int kb = panel_width(n, wide);
   if (kb == 0) return BT_ERR_UNSUPPORTED;
-  if (ws_bytes < zinv_workspace_bytes(n, batch) || ws == nullptr) return BT_ERR_INVALID_ARG;
+  if (ws_bytes < zinv_workspace_bytes(n, batch, wide) || ws == nullptr) return BT_ERR_INVALID_ARG;
   if (batch > 65535) return BT_ERR_INVALID_ARG;
   int* perm = static_cast<int*>(ws);
   size_t perm_bytes = ((size_t)batch * n * sizeof(int) + 255) / 256 * 256;
   zd* T = reinterpret_cast<zd*>(static_cast<char*>(ws) + perm_bytes);
   const long long sT = (long long)kb * n;
   const bool clustered = n >= kClusterMinN;
+  int cl = kPanelCluster;
+  if (clustered) {
+    int sms = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return BT_ERR_CUDA;
+    while (cl > 2 && (long long)batch * cl > sms) cl >>= 1;
+    if (cluster_panel_smem(n, kb, cl) > kSmemLimit - 1024) return BT_ERR_UNSUPPORTED;
+  }
   for (int k0 = 0; k0 < n; k0 += kb) {
     const int w = (n - k0) < kb ? (n - k0) : kb;
     if (clustered) {
-      // one cluster of kPanelCluster CTAs per matrix (rows of the panel split across SMs)
+      // one cluster of cl CTAs per matrix (rows of the panel split across SMs): the largest
+      // cluster for which every matrix of the batch gets its own SMs at once
       cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3((unsigned)(batch * kPanelCluster));
+      cfg.gridDim = dim3((unsigned)(batch * cl));
       cfg.blockDim = dim3(NT);
-      cfg.dynamicSmemBytes = cluster_panel_smem(n, w);
+      cfg.dynamicSmemBytes = cluster_panel_smem(n, w, cl);
       cfg.stream = st;
       cudaLaunchAttribute attr[1];
       attr[0].id = cudaLaunchAttributeClusterDimension;
-      attr[0].val.clusterDim.x = kPanelCluster;
+      attr[0].val.clusterDim.x = cl;
       attr[0].val.clusterDim.y = 1;
       attr[0].val.clusterDim.z = 1;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
-      BT_CUDA_TRY(cudaLaunchKernelEx(&cfg, gj_panel_cluster_kernel<kPanelCluster>, n, k0, w, A, sA, perm, info,
-                                     active));
+      if (cl == 8) {
+        BT_CUDA_TRY(cudaLaunchKernelEx(&cfg, gj_panel_cluster_kernel<8>, n, k0, w, A, sA, perm, info, active));
+      } else if (cl == 4) {
+        BT_CUDA_TRY(cudaLaunchKernelEx(&cfg, gj_panel_cluster_kernel<4>, n, k0, w, A, sA, perm, info, active));
+      } else {
+        BT_CUDA_TRY(cudaLaunchKernelEx(&cfg, gj_panel_cluster_kernel<2>, n, k0, w, A, sA, perm, info, active));
+      }
       count_launch();
     } else {
       gj_panel_kernel<<<batch, NT, panel_smem(n, w), st>>>(n, k0, w, A, sA, perm, info, active); count_launch();
     }
     BT_CUDA_TRY(cudaGetLastError());
-    dim3 g((n + 255) / 256, batch);
-    gj_swap_copy_kernel<<<g, 256, 0, st>>>(n, k0, w, A, sA, perm, T, sT, active); count_launch();
+    dim3 g((n + kSwapCols - 1) / kSwapCols, batch);
+    gj_swap_copy_kernel<<<g, kSwapCols * kSwapRows, 0, st>>>(n, k0, w, A, sA, perm, T, sT, active); count_launch();
     BT_CUDA_TRY(cudaGetLastError());
-    // A[:, C] += A[:, K] * T[:, C] for the column ranges left and right of the panel
+    // A[:, all] += A[:, K] * T: T's panel columns are zero, so the panel columns keep their values
     Operand P{A + k0, n, sA, BT_OP_N};
-    if (k0 > 0) {
-      Operand Tl{T, n, sT, BT_OP_N};
-      BT_TRY(gemm(E, st, n, k0, w, zmake(1.0, 0.0), P, Tl, zmake(1.0, 0.0), A, n, sA, batch, active));
-    }
-    const int c1 = k0 + w;
-    if (c1 < n) {
-      Operand Tr{T + c1, n, sT, BT_OP_N};
-      BT_TRY(gemm(E, st, n, n - c1, w, zmake(1.0, 0.0), P, Tr, zmake(1.0, 0.0), A + c1, n, sA, batch, active));
-    }
+    Operand Tall{T, n, sT, BT_OP_N};
+    BT_TRY(gemm(E, st, n, n, w, zmake(1.0, 0.0), P, Tall, zmake(1.0, 0.0), A, n, sA, batch, active));
   }
-  dim3 g((n + 255) / 256, batch);
-  gj_unscramble_kernel<<<g, 256, 0, st>>>(n, A, sA, perm, active); count_launch();
+  int urows = kUnscrRows;
+  while (urows > 1 && unscramble_smem(n, urows) > kSmemLimit - 1024) --urows;
+  if (unscramble_smem(n, urows) > kSmemLimit - 1024) return BT_ERR_UNSUPPORTED;
+  dim3 g((n + urows - 1) / urows, batch);
+  gj_unscramble_kernel<<<g, 32 * urows, unscramble_smem(n, urows), st>>>(n, A, sA, perm, active); count_launch();
   BT_CUDA_TRY(cudaGetLastError());
   return BT_OK;
 }
@@ -470,7 +597,7 @@ bt_status zinv(cudaStream_t st, int n, zd* A, long long sA, int batch, int* info
 
 extern "C" bt_status bt_zinv_workspace_bytes(int n, int batch, size_t* bytes) {
   if (!bytes || n < 0 || batch < 0) return BT_ERR_INVALID_ARG;
-  *bytes = bt::zinv_workspace_bytes(n, batch);
+  *bytes = bt::zinv_workspace_bytes(n, batch, false);
   return BT_OK;
 }
 

@@ -84,7 +84,30 @@ def test_zinv_pivoting_needed(pkg):
     assert np.abs(dA.cpu().numpy()[0] - np.linalg.inv(A)).max() < 1e-14
 
 
-@pytest.mark.parametrize("n", [4, 130])
+@pytest.mark.parametrize("n", [200, 416])
+def test_zinv_far_pivots(pkg, n):
+    """Pivots in rows owned by other CTAs of the panel cluster: a matrix dominated by its
+    anti-diagonal (every pivot comes from the far end), plus ties of equal magnitude."""
+    import torch
+    rng = np.random.default_rng(n + 5)
+    A = np.zeros((3, n, n), dtype=np.complex128)
+    J = np.fliplr(np.eye(n))
+    A[0] = 4.0 * J + 0.1 * cplx(rng, (n, n))
+    A[1] = J * (1.0 + 1.0j) + 0.05 * cplx(rng, (n, n))
+    A[2] = np.where(rng.random((n, n)) < 0.5, 1.0, -1.0) + 0.0j  # many exact ties in |re| + |im|
+    A[2] += 0.01 * n * np.eye(n)
+    ref = np.linalg.inv(A)
+    dA = torch.from_numpy(A).cuda()
+    info = torch.zeros(3, dtype=torch.int32, device="cuda")
+    pkg.bt_zinv_batched(n, dA, n * n, 3, info)
+    assert info.cpu().numpy().tolist() == [0, 0, 0]
+    got = dA.cpu().numpy()
+    for b in range(3):
+        cond = np.linalg.cond(A[b])
+        assert np.linalg.norm(got[b] - ref[b]) / np.linalg.norm(ref[b]) < 1e-15 * cond * n
+
+
+@pytest.mark.parametrize("n", [4, 130, 416])
 def test_zinv_reports_singular_and_nonfinite(pkg, n):
     import torch
     rng = np.random.default_rng(1)
