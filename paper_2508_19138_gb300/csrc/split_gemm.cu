@@ -48,31 +48,34 @@ namespace {
 
 constexpr int kDigitBits = 7;
 constexpr int kMaxSlices = 8;
-constexpr int kMaxItems = 128;     // (slice pair, K segment) products per tile
-constexpr int kMaxGroups = 128;    // accumulations (drains) per tile
+constexpr int kMaxItems = 128;     // slice pairs (or pair couples) per tile
+constexpr int kMaxJobs = 96;       // accumulations rounds (one or two drains each) per tile
 constexpr int kSegBlocks = 15;     // K blocks per segment: 15 * 64 = 960 real terms, 960 * 2^12 < 2^22
 constexpr float kMagic = 12582912.0f;       // 1.5 * 2^23
 constexpr uint32_t kMagicBits = 0x4B400000u;
 constexpr int kTileM = 128;
 constexpr int kKBlock = 64;      // bf16 per 128-byte swizzle row
-constexpr int kStages = 7;       // 7 x (16 + 14) KB of operand stages
 constexpr int kEpiWarps = 16;   // 4 lane quarters x 4 column quarters of the accumulator
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
 
-// One accumulation group = slice pairs (s, t) of equal weight, items [ib, ie), over K blocks
-// [kb0, kb1), summed in one TMEM accumulator.
+// One job = one accumulation round over K blocks [kb0, kb1), drained once:
+//  * dual job: two TMEM accumulators (lanes) fed by one item (t, s, s2): the pairs (s, t) and
+//    (s2, t) share op(B)'s slice t, so each K block loads the Bt tile once for eight MMAs;
+//  * single job: one accumulator summing the pairs of items [ib, ie) (equal weights).
 struct Schedule {
-  int n_groups;
-  unsigned char s[kMaxItems];     // slice of op(A) (1-based)
-  unsigned char t[kMaxItems];     // slice of op(B) (1-based)
-  unsigned char ib[kMaxGroups];
-  unsigned char ie[kMaxGroups];
-  unsigned char kb0[kMaxGroups];
-  unsigned char kb1[kMaxGroups];
-  unsigned char lsh[kMaxGroups];  // weight 2^(F - 7w) > 2^31: shift instead of multiply
-  uint32_t mult[kMaxGroups];      // weight 2^(F - 7w) <= 2^31 (after the pre-scale)
-  float fscale[kMaxGroups];       // 2^-p: pre-scale of pairs with F - 7w < 0
+  int n_jobs;
+  unsigned char dual[kMaxJobs];
+  unsigned char ib[kMaxJobs];
+  unsigned char ie[kMaxJobs];
+  unsigned char kb0[kMaxJobs];
+  unsigned char kb1[kMaxJobs];
+  unsigned char lsh[kMaxJobs][2];  // weight 2^(F - 7w) > 2^31: shift instead of multiply
+  uint32_t mult[kMaxJobs][2];      // weight 2^(F - 7w) <= 2^31 (after the pre-scale)
+  float fscale[kMaxJobs][2];       // 2^-p: pre-scale of pairs with F - 7w < 0
+  unsigned char s[kMaxItems];      // slice of op(A) (1-based), lane 0
+  unsigned char s2[kMaxItems];     // slice of op(A), lane 1 of a dual job
+  unsigned char t[kMaxItems];      // slice of op(B) (1-based)
 };
 
 enum CoefMode : int {
@@ -133,23 +136,48 @@ __device__ __forceinline__ double fix_to_double(long long v, int e) {
   return __longlong_as_double((long long)bits);
 }
 
+// Pipeline depth for an N tile: as many stages (Bt tile + two At tiles) as fit in 227 KB of shared
+// memory next to the 1 KB alignment pad and the barriers, at most 8.
+__host__ __device__ constexpr int stages_for(int nt) {
+  return (227 * 1024 - 1024 - 256) / (kTileM * 128 + 2 * nt * 128) < 8
+             ? (227 * 1024 - 1024 - 256) / (kTileM * 128 + 2 * nt * 128)
+             : 8;
+}
+__host__ __device__ constexpr size_t smem_for(int nt) {
+  return 1024 + (size_t)stages_for(nt) * (kTileM * 128 + 2 * nt * 128) + 256;
+}
+
+// Tile t of a batched launch -> (rows of C^T, rows of C, batch entry); false for inactive entries.
+__device__ __forceinline__ bool tile_coords(const MmaParams& p, int nt, int tile, int& m0, int& n0, int& b) {
+  const int per_b = p.tiles_x * p.tiles_y;
+  b = tile / per_b;
+  const int r = tile - b * per_b;
+  const int ty = r / p.tiles_x;
+  m0 = (r - ty * p.tiles_x) * kTileM;
+  n0 = ty * nt;
+  return !p.active || p.active[b] != 0;
+}
+
 template <int NT>
 __global__ void __launch_bounds__(kThreads, 1)
     split_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      const MmaParams p) {
   constexpr int kABytes = kTileM * 128;
   constexpr int kBBytes = NT * 128;
+  constexpr int kStages = stages_for(NT);
   constexpr int kCols = NT / 4;   // accumulator columns per epilogue thread
   constexpr int kBatch = kCols % 8 == 0 ? 8 : 4;  // columns per tcgen05.ld wait
+  constexpr int kWB = 4;  // outputs per write chunk (kCols is a multiple of 4)
   static_assert(NT % 16 == 0 && NT >= 16 && NT <= 256, "UMMA N");
-  static_assert(2 * NT <= 256, "two accumulators must fit in 256 TMEM columns");
+  static_assert(4 * NT <= 512, "two double-buffered accumulator pairs must fit in TMEM");
   constexpr uint32_t kIdesc = ptx::idesc_bf16_f32(kTileM, NT);
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
-  uint8_t* sA = smem;
-  uint8_t* sB = smem + kStages * kABytes;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sB + kStages * kBBytes);
+  // stage: Bt tile (A operand) + two At tiles (B operands of the two lanes of a dual job)
+  constexpr int kStageBytes = kABytes + 2 * kBBytes;
+  uint8_t* stages = smem;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
   uint64_t* empty = full + kStages;
   uint64_t* tfull = empty + kStages;
   uint64_t* tempty = tfull + 2;
@@ -173,7 +201,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     ptx::fence_barrier_init();
   }
   if (warp == 1) {
-    ptx::tmem_alloc(tmem_slot, 256);
+    ptx::tmem_alloc(tmem_slot, 512);
     ptx::tmem_relinquish();
   }
   ptx::tc_fence_before();
@@ -182,16 +210,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = *tmem_slot;
 
   const Schedule& sc = p.sched;
-  const int per_b = p.tiles_x * p.tiles_y;
   // every role walks the same tiles in the same order and skips the same inactive entries
-  auto tile_of = [&](int tile, int& m0, int& n0, int& b) {
-    b = tile / per_b;
-    const int r = tile - b * per_b;
-    const int ty = r / p.tiles_x;
-    m0 = (r - ty * p.tiles_x) * kTileM;  // rows of C^T
-    n0 = ty * NT;                        // rows of C
-    return !p.active || p.active[b] != 0;
-  };
   auto fail = [&](int b) {
     *abort_flag = 1;
     if (p.err) atomicCAS(&p.err[b], 0, (int)BT_ERR_TIMEOUT);
@@ -208,19 +227,25 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
         int m0, n0, b;
-        if (!tile_of(tile, m0, n0, b)) continue;
+        if (!tile_coords(p, NT, tile, m0, n0, b)) continue;
         const int zA = (p.b_shared ? 0 : b) * p.S - 1, zB = (p.a_shared ? 0 : b) * p.S - 1;
-        for (int g = 0; g < sc.n_groups && ok; ++g) {
-          for (int it = sc.ib[g]; it < sc.ie[g] && ok; ++it) {
-            for (int kb = sc.kb0[g]; kb < sc.kb1[g]; ++kb) {
+        for (int g = 0; g < sc.n_jobs && ok; ++g) {
+          const bool dual = sc.dual[g] != 0;
+          const uint32_t bytes = (uint32_t)(kABytes + (dual ? 2 : 1) * kBBytes);
+          const int ie = sc.ie[g], kb0 = sc.kb0[g], kb1 = sc.kb1[g];
+          for (int it = sc.ib[g]; it < ie && ok; ++it) {
+            const int ct = zA + sc.t[it], cs = zB + sc.s[it], cs2 = zB + sc.s2[it];
+            for (int kb = kb0; kb < kb1; ++kb) {
               if (!ptx::mbar_wait_bounded(&empty[stage], phase ^ 1u, abort_flag, kWaitLimitNs)) {
                 fail(b);
                 ok = false;
                 break;
               }
-              ptx::mbar_arrive_expect_tx(&full[stage], kABytes + kBBytes);
-              ptx::tma_load_3d(sA + stage * kABytes, &tmA, &full[stage], kb * kKBlock, m0, zA + sc.t[it]);
-              ptx::tma_load_3d(sB + stage * kBBytes, &tmB, &full[stage], kb * kKBlock, n0, zB + sc.s[it]);
+              uint8_t* st = stages + stage * kStageBytes;
+              ptx::mbar_arrive_expect_tx(&full[stage], bytes);
+              ptx::tma_load_3d(st, &tmA, &full[stage], kb * kKBlock, m0, ct);
+              ptx::tma_load_3d(st + kABytes, &tmB, &full[stage], kb * kKBlock, n0, cs);
+              if (dual) ptx::tma_load_3d(st + kABytes + kBBytes, &tmB, &full[stage], kb * kKBlock, n0, cs2);
               ++issued;
               if (++stage == kStages) { stage = 0; phase ^= 1u; }
             }
@@ -239,12 +264,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
-      uint32_t gc = 0;  // accumulation groups issued so far (all tiles)
+      uint32_t gc = 0;  // jobs started so far (all tiles)
       bool ok = true;
       for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
         int m0, n0, b;
-        if (!tile_of(tile, m0, n0, b)) continue;
-        for (int g = 0; g < sc.n_groups && ok; ++g, ++gc) {
+        if (!tile_coords(p, NT, tile, m0, n0, b)) continue;
+        for (int g = 0; g < sc.n_jobs && ok; ++g, ++gc) {
           const uint32_t ab = gc & 1u;
           if (gc >= 2 && !ptx::mbar_wait_bounded(&tempty[ab], ((gc >> 1) - 1u) & 1u, abort_flag, kWaitLimitNs)) {
             fail(b);
@@ -252,23 +277,29 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           ptx::tc_fence_after();
-          const uint32_t dcol = tmem + ab * (uint32_t)NT;
-          uint32_t acc0 = 0u;  // the group's first MMA overwrites the accumulator
-          for (int it = sc.ib[g]; it < sc.ie[g] && ok; ++it) {
-            for (int kb = sc.kb0[g]; kb < sc.kb1[g]; ++kb) {
+          const uint32_t dcol0 = tmem + (2u * ab) * (uint32_t)NT, dcol1 = dcol0 + (uint32_t)NT;
+          const bool dual = sc.dual[g] != 0;
+          const int ie = sc.ie[g], kb0 = sc.kb0[g], kb1 = sc.kb1[g];
+          uint32_t acc0 = 0u;  // the job's first MMA overwrites the accumulators
+          for (int it = sc.ib[g]; it < ie && ok; ++it) {
+            for (int kb = kb0; kb < kb1; ++kb) {
               if (!ptx::mbar_wait_bounded(&full[stage], phase, abort_flag, kWaitLimitNs)) {
                 fail(b);
                 ok = false;
                 break;
               }
               ptx::tc_fence_after();
-              const uint32_t a_addr = ptx::smem_u32(sA + stage * kABytes);
-              const uint32_t b_addr = ptx::smem_u32(sB + stage * kBBytes);
+              const uint32_t a_addr = ptx::smem_u32(stages + stage * kStageBytes);
+              const uint32_t b_addr = a_addr + kABytes;
 #pragma unroll
-              for (int k = 0; k < kKBlock / 16; ++k) {
-                const uint64_t ad = ptx::sdesc_kmajor_sw128(a_addr + k * 32);
-                const uint64_t bd = ptx::sdesc_kmajor_sw128(b_addr + k * 32);
-                ptx::umma_f16(dcol, ad, bd, kIdesc, k == 0 ? acc0 : 1u);
+              for (int k = 0; k < kKBlock / 16; ++k)
+                ptx::umma_f16(dcol0, ptx::sdesc_kmajor_sw128(a_addr + k * 32),
+                              ptx::sdesc_kmajor_sw128(b_addr + k * 32), kIdesc, k == 0 ? acc0 : 1u);
+              if (dual) {
+#pragma unroll
+                for (int k = 0; k < kKBlock / 16; ++k)
+                  ptx::umma_f16(dcol1, ptx::sdesc_kmajor_sw128(a_addr + k * 32),
+                                ptx::sdesc_kmajor_sw128(b_addr + kBBytes + k * 32), kIdesc, k == 0 ? acc0 : 1u);
               }
               acc0 = 1u;
               ptx::umma_commit(&empty[stage]);
@@ -293,11 +324,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool ok = true;
     for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
       int m0, n0, b;
-      if (!tile_of(tile, m0, n0, b)) continue;
+      if (!tile_coords(p, NT, tile, m0, n0, b)) continue;
       unsigned long long acc[kCols];
 #pragma unroll
       for (int c = 0; c < kCols; ++c) acc[c] = 0ull;
-      for (int g = 0; g < sc.n_groups; ++g, ++gc) {
+      for (int g = 0; g < sc.n_jobs; ++g, ++gc) {
         const uint32_t ab = gc & 1u;
         const bool got = ptx::mbar_wait_bounded(&tfull[ab], (gc >> 1) & 1u, abort_flag, kWaitLimitNs);
         // the warp-collective tcgen05.ld below needs every lane: one lane's timeout stops the warp
@@ -307,26 +338,30 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         ptx::tc_fence_after();
-        const float fs = sc.fscale[g];
-        const uint32_t mu = sc.mult[g];
-        const int lsh = sc.lsh[g];
-        const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + ab * (uint32_t)NT + (uint32_t)(cq * kCols);
+        const int lanes = sc.dual[g] ? 2 : 1;
+        for (int l = 0; l < lanes; ++l) {
+          const float fs = sc.fscale[g][l];
+          const uint32_t mu = sc.mult[g][l];
+          const int lsh = sc.lsh[g][l];
+          const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (2u * ab + (uint32_t)l) * (uint32_t)NT +
+                                (uint32_t)(cq * kCols);
 #pragma unroll
-        for (int c0 = 0; c0 < kCols; c0 += kBatch) {
-          uint32_t v[kBatch];
+          for (int c0 = 0; c0 < kCols; c0 += kBatch) {
+            uint32_t v[kBatch];
 #pragma unroll
-          for (int c = 0; c < kBatch; c += 4) ptx::tmem_ld_x4(base + c0 + c, v + c);
-          ptx::tmem_wait_ld();
-          if (lsh == 0) {
+            for (int c = 0; c < kBatch; c += 4) ptx::tmem_ld_x4(base + c0 + c, v + c);
+            ptx::tmem_wait_ld();
+            if (lsh == 0) {
 #pragma unroll
-            for (int c = 0; c < kBatch; ++c) {
-              const float t = fmaf(__uint_as_float(v[c]), fs, kMagic);
-              acc[c0 + c] += (unsigned long long)__float_as_uint(t) * (unsigned long long)mu;
+              for (int c = 0; c < kBatch; ++c) {
+                const float t = fmaf(__uint_as_float(v[c]), fs, kMagic);
+                acc[c0 + c] += (unsigned long long)__float_as_uint(t) * (unsigned long long)mu;
+              }
+            } else {
+#pragma unroll
+              for (int c = 0; c < kBatch; ++c)
+                acc[c0 + c] += (unsigned long long)__float_as_uint(__uint_as_float(v[c]) + kMagic) << lsh;
             }
-          } else {
-#pragma unroll
-            for (int c = 0; c < kBatch; ++c)
-              acc[c0 + c] += (unsigned long long)__float_as_uint(__uint_as_float(v[c]) + kMagic) << lsh;
           }
         }
         ptx::tc_fence_before();
@@ -342,45 +377,61 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int EB = row_ok ? p.eB[(long long)(p.b_shared ? 0 : b) * n + j] : 1;
       zd* Cb = p.C + p.sC * b;
       const int* eAb = p.eA + (long long)(p.a_shared ? 0 : b) * p.m;
+      const bool need_old = p.coef_mode == kCoefUnitAcc || (p.coef_mode == kCoefReal && p.beta.x != 0.0);
+      // chunks of kWB outputs: every load of a chunk (exponents, old C) is issued before its
+      // stores, so the loads overlap instead of waiting one by one behind possibly aliasing stores
 #pragma unroll
-      for (int c = 0; c < kCols; ++c) {
-        const int i = n0 + cq * kCols + c;
-        const bool ok_el = row_ok && i < p.m;
-        double v = 0.0;
-        if (ok_el) {
-          const int EA = eAb[i];
-          long long a = (long long)(acc[c] - p.bias);
-          if (p.negate) a = -a;
-          // value = a * 2^-F * R_A * R_B * 2^-12, R = 2^(E - 1022)
-          v = fix_to_double(a, EA + EB - 2044 - 12 - p.fix_bits);
-          if (EA >= 2047 || EB >= 2047) v = __longlong_as_double(0x7ff8000000000000ll);
+      for (int c0 = 0; c0 < kCols; c0 += kWB) {
+        int ea[kWB];
+        double old[kWB];
+#pragma unroll
+        for (int u = 0; u < kWB; ++u) {
+          const int i = n0 + cq * kCols + c0 + u;
+          const bool ok_el = row_ok && i < p.m;
+          ea[u] = ok_el ? eAb[i] : 1;
+          old[u] = (need_old && ok_el) ? reinterpret_cast<const double*>(Cb + (long long)i * p.ldc + j)[part] : 0.0;
         }
-        double* cp = reinterpret_cast<double*>(Cb + (long long)(ok_el ? i : 0) * p.ldc + (ok_el ? j : 0)) + part;
-        if (p.coef_mode == kCoefUnit) {
-          if (ok_el) *cp = v;
-        } else if (p.coef_mode == kCoefUnitAcc) {
-          if (ok_el) *cp += v;
-        } else if (p.coef_mode == kCoefReal) {
+#pragma unroll
+        for (int u = 0; u < kWB; ++u) {
+          const int c = c0 + u;
+          const int i = n0 + cq * kCols + c;
+          const bool ok_el = row_ok && i < p.m;
+          double v = 0.0;
           if (ok_el) {
-            const double out = p.alpha.x * v;
-            *cp = p.beta.x == 0.0 ? out : fma(p.beta.x, *cp, out);
+            const int EA = ea[u];
+            long long a = (long long)(acc[c] - p.bias);
+            if (p.negate) a = -a;
+            // value = a * 2^-F * R_A * R_B * 2^-12, R = 2^(E - 1022)
+            v = fix_to_double(a, EA + EB - 2044 - 12 - p.fix_bits);
+            if (EA >= 2047 || EB >= 2047) v = __longlong_as_double(0x7ff8000000000000ll);
           }
-        } else {
-          // complex alpha / beta: the partner lane (2j vs 2j+1) holds the other component
-          const double vo = __shfl_xor_sync(0xffffffffu, v, 1);
-          const double re = part ? vo : v, im = part ? v : vo;
-          const double ar = p.alpha.x, ai = p.alpha.y, br = p.beta.x, bi = p.beta.y;
-          const bool bz = br == 0.0 && bi == 0.0;
-          double cre = 0.0, cim = 0.0;
-          if (ok_el && !bz) {
-            const zd old = Cb[(long long)i * p.ldc + j];
-            cre = old.x;
-            cim = old.y;
-          }
-          if (ok_el) {
-            const double outr = ar * re - ai * im + (bz ? 0.0 : br * cre - bi * cim);
-            const double outi = ar * im + ai * re + (bz ? 0.0 : br * cim + bi * cre);
-            *cp = part ? outi : outr;
+          double* cp = reinterpret_cast<double*>(Cb + (long long)(ok_el ? i : 0) * p.ldc + (ok_el ? j : 0)) + part;
+          if (p.coef_mode == kCoefUnit) {
+            if (ok_el) *cp = v;
+          } else if (p.coef_mode == kCoefUnitAcc) {
+            if (ok_el) *cp = old[u] + v;
+          } else if (p.coef_mode == kCoefReal) {
+            if (ok_el) {
+              const double out = p.alpha.x * v;
+              *cp = p.beta.x == 0.0 ? out : fma(p.beta.x, old[u], out);
+            }
+          } else {
+            // complex alpha / beta: the partner lane (2j vs 2j+1) holds the other component
+            const double vo = __shfl_xor_sync(0xffffffffu, v, 1);
+            const double re = part ? vo : v, im = part ? v : vo;
+            const double ar = p.alpha.x, ai = p.alpha.y, br = p.beta.x, bi = p.beta.y;
+            const bool bz = br == 0.0 && bi == 0.0;
+            double cre = 0.0, cim = 0.0;
+            if (ok_el && !bz) {
+              const zd o = Cb[(long long)i * p.ldc + j];
+              cre = o.x;
+              cim = o.y;
+            }
+            if (ok_el) {
+              const double outr = ar * re - ai * im + (bz ? 0.0 : br * cre - bi * cim);
+              const double outi = ar * im + ai * re + (bz ? 0.0 : br * cim + bi * cre);
+              *cp = part ? outi : outr;
+            }
           }
         }
       }
@@ -391,7 +442,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   if (warp == 1) {
     ptx::tc_fence_after();
-    ptx::tmem_dealloc(tmem, 256);
+    ptx::tmem_dealloc(tmem, 512);
   }
 }
 
@@ -405,7 +456,10 @@ __device__ __forceinline__ int biased_exp(double v) {
 
 // Balanced base-128 digits of v / R, R = 2^(Erow - 1022):  X = round(|v| / R * 2^(7S-1)) <=
 // 2^(7S-1) (integer arithmetic on the IEEE fields), X = sum_s d_s 128^(S-s) with the lower digits
-// in [-64, 63] and the leading digit in [0, 64];  q[s-1] = sign * d_s (integers, exact in bf16).
+// in [-64, 63] and the leading digit in [0, 64];  q[s-1] = sign * d_s as an exact float, formed
+// as (bits 0x4B400000 + d) - 1.5 * 2^23: one integer add and one FADD, no conversion instruction
+// (conversions run on GB300's narrow FP64 / conversion pipe).
+__device__ __forceinline__ float digit_float(int d) { return __int_as_float(0x4B400000 + d) - 12582912.0f; }
 __device__ __forceinline__ void slice_value(double v, int Erow, int S, float* q) {
   const long long bits = __double_as_longlong(v);
   int E = (int)((bits >> 52) & 0x7FF);
@@ -418,22 +472,22 @@ __device__ __forceinline__ void slice_value(double v, int Erow, int S, float* q)
   else if (-sh >= 64) X2 = 0;
   else X2 = M >> (-sh);
   unsigned long long X = (X2 + 1ull) >> 1;
-  const float sign = bits < 0 ? -1.0f : 1.0f;
+  const int sg = bits < 0 ? -1 : 1;
 #pragma unroll
   for (int s = kMaxSlices; s >= 2; --s) {
     if (s <= S) {
       int d = (int)(X & 127ull);
-      if (d >= 64) d -= 128;
-      q[s - 1] = sign * (float)d;
-      X = (X - (unsigned long long)(long long)d) >> kDigitBits;  // X + 128 - d' when d < 0: stays >= 0
+      X >>= kDigitBits;
+      if (d >= 64) { d -= 128; X += 1ull; }  // borrow from the next digit
+      q[s - 1] = digit_float(sg * d);
     }
   }
-  q[0] = sign * (float)X;  // leading digit, <= 64
+  q[0] = digit_float(sg * (int)X);  // leading digit, <= 64
 }
 
+// Two exact small floats -> packed bf16 pair: their upper halves (the low 16 bits are zero).
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
-  const __nv_bfloat16 a = __float2bfloat16_rn(lo), b = __float2bfloat16_rn(hi);
-  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
 }
 
 // Slicing works on "lines": the rows of op(A) (At operand) and the columns of op(B) (Bt
@@ -443,8 +497,7 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 //   At: out[b][s][l][p]               = (Re, Im) digits of op(A)[l][p]
 //   Bt: out[b][s][2l][p], [2l+1][p]   = (Re, -Im), (Im, Re) digits of op(B)[p][l]
 // Lines l in [L, Lpad) and words p in [Kc, Kw) are written as zeros.  The line exponents go to
-// e[b][l]; every kernel reads its input line twice (max exponent, then digits), the second time
-// mostly from L2.
+// e[b][l].
 template <bool kBt>
 __device__ __forceinline__ void write_slices(uint32_t* __restrict__ out, long long slice_words, int Kw, int l, int p,
                                              int S, bool in, const float* qr, const float* qi) {
@@ -496,58 +549,66 @@ __global__ void slice_lines_contig_kernel(int L, int Lpad, int Kc, int Kw, const
   }
 }
 
-// Strided lines (memory columns): 32 lines per CTA, grid (ceil(Lpad / 32), batch), 256 threads.
-template <bool kBt>
-__global__ void slice_lines_strided_kernel(int L, int Lpad, int Kc, int Kw, const zd* __restrict__ X, int ld,
-                                           long long sX, int conj, int S, int* __restrict__ e,
-                                           uint32_t* __restrict__ out, const int* __restrict__ active) {
-  __shared__ zd T[32][33];  // T[p][l]
+// Strided lines (memory columns), pass 1: e[b][l] = max biased exponent of line l, as atomicMax
+// over CTAs of 32 lines x kExpRows rows (e zeroed before).  Grid (ceil(L / 32), ceil(Kc / kExpRows),
+// batch), 256 threads.
+constexpr int kExpRows = 64;
+__global__ void line_exp_strided_kernel(int L, int Kc, const zd* __restrict__ X, int ld, long long sX,
+                                        int* __restrict__ e, const int* __restrict__ active) {
   __shared__ int red[8][32];
-  const int b = blockIdx.y;
+  const int b = blockIdx.z;
   if (active && active[b] == 0) return;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int l0 = blockIdx.x * 32;
+  const int l = blockIdx.x * 32 + tx, p0 = blockIdx.y * kExpRows;
   const zd* Xb = X + sX * b;
-  {
-    const int l = l0 + tx;
-    int E = 1;
-    if (l < L)
-      for (int p = ty; p < Kc; p += 8) {
-        const zd v = Xb[(long long)p * ld + l];
-        E = max(E, max(biased_exp(v.x), biased_exp(v.y)));
-      }
-    red[ty][tx] = E;
-  }
+  int E = 1;
+  if (l < L)
+    for (int p = p0 + ty; p < Kc && p < p0 + kExpRows; p += 8) {
+      const zd v = Xb[(long long)p * ld + l];
+      E = max(E, max(biased_exp(v.x), biased_exp(v.y)));
+    }
+  red[ty][tx] = E;
   __syncthreads();
-  __shared__ int Eline[32];
-  if (ty == 0) {
-    int E = red[0][tx];
+  if (ty == 0 && l < L) {
 #pragma unroll
     for (int y = 1; y < 8; ++y) E = max(E, red[y][tx]);
-    Eline[tx] = E;
-    if (l0 + tx < L) e[(long long)b * L + l0 + tx] = E;
+    atomicMax(&e[(long long)b * L + l], E);
   }
+}
+
+// Strided lines, pass 2: one 32-line x 32-word tile per CTA (grid (ceil(Lpad / 32), Kw / 32,
+// batch), 256 threads): coalesced loads along the memory rows, shared-memory transpose, digits
+// written along the output rows.
+template <bool kBt>
+__global__ void slice_lines_strided_kernel(int L, int Lpad, int Kc, int Kw, const zd* __restrict__ X, int ld,
+                                           long long sX, int conj, int S, const int* __restrict__ e,
+                                           uint32_t* __restrict__ out, const int* __restrict__ active) {
+  __shared__ zd T[32][33];  // T[p][l]
+  __shared__ int Eline[32];
+  const int b = blockIdx.z;
+  if (active && active[b] == 0) return;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int l0 = blockIdx.x * 32, p0 = blockIdx.y * 32;
+  const zd* Xb = X + sX * b;
+  if (ty == 0) Eline[tx] = l0 + tx < L ? e[(long long)b * L + l0 + tx] : 1;
+  for (int yy = ty; yy < 32; yy += 8) {
+    const int p = p0 + yy, l = l0 + tx;
+    T[yy][tx] = (p < Kc && l < L) ? Xb[(long long)p * ld + l] : zmake(0.0, 0.0);
+  }
+  __syncthreads();
   const long long slice_words = (long long)(kBt ? 2 : 1) * Lpad * Kw;
   uint32_t* ob = out + (long long)b * S * slice_words;
-  for (int p0 = 0; p0 < Kw; p0 += 32) {
-    __syncthreads();  // Eline ready; previous tile consumed
-    for (int yy = ty; yy < 32; yy += 8) {
-      const int p = p0 + yy, l = l0 + tx;
-      T[yy][tx] = (p < Kc && l < L) ? Xb[(long long)p * ld + l] : zmake(0.0, 0.0);
+  for (int yy = ty; yy < 32; yy += 8) {
+    const int l = l0 + yy, p = p0 + tx;
+    if (l >= Lpad || p >= Kw) continue;
+    const bool in = l < L && p < Kc;
+    float qr[kMaxSlices], qi[kMaxSlices];
+    if (in) {
+      const zd v = T[tx][yy];
+      slice_value(v.x, Eline[yy], S, qr);
+      slice_value(conj ? -v.y : v.y, Eline[yy], S, qi);
     }
-    __syncthreads();
-    for (int yy = ty; yy < 32; yy += 8) {
-      const int l = l0 + yy, p = p0 + tx;
-      if (l >= Lpad || p >= Kw) continue;
-      const bool in = l < L && p < Kc;
-      float qr[kMaxSlices], qi[kMaxSlices];
-      if (in) {
-        const zd v = T[tx][yy];
-        slice_value(v.x, Eline[yy], S, qr);
-        slice_value(conj ? -v.y : v.y, Eline[yy], S, qi);
-      }
-      write_slices<kBt>(ob, slice_words, Kw, l, p, S, in, qr, qi);
-    }
+    write_slices<kBt>(ob, slice_words, Kw, l, p, S, in, qr, qi);
   }
 }
 
@@ -558,7 +619,11 @@ bt_status slice_lines(cudaStream_t st, bool contiguous, int L, int Lpad, int Kc,
     dim3 g((Lpad + 7) / 8, batch);
     slice_lines_contig_kernel<kBt><<<g, 256, 0, st>>>(L, Lpad, Kc, Kw, X, ld, sX, conj, S, e, out, active);
   } else {
-    dim3 g((Lpad + 31) / 32, batch);
+    BT_CUDA_TRY(cudaMemsetAsync(e, 0, sizeof(int) * (size_t)batch * L, st));
+    dim3 ge((L + 31) / 32, (Kc + kExpRows - 1) / kExpRows, batch);
+    line_exp_strided_kernel<<<ge, 256, 0, st>>>(L, Kc, X, ld, sX, e, active);
+    count_launch();
+    dim3 g((Lpad + 31) / 32, Kw / 32, batch);
     slice_lines_strided_kernel<kBt><<<g, 256, 0, st>>>(L, Lpad, Kc, Kw, X, ld, sX, conj, S, e, out, active);
   }
   count_launch();
@@ -594,11 +659,13 @@ bool encode_slices_map(CUtensorMap* map, void* base, int Kp, int rows, int depth
   return r == CUDA_SUCCESS;
 }
 
-// Items: every slice pair (s, t) with s + t <= S + 1 times the K segments of at most kSegBlocks
-// blocks (balanced).  A group sums items of one segment and one pair weight w = s + t - 2 in one
-// accumulator while it stays an exact fp32 integer below 2^22: n pairs over L blocks of 64 real
-// terms reach at most n * L * 64 * 2^12, so n * L < 16 (one pair for long segments, up to 15 for
-// a single K block).  The group enters the fixed-point sum with factor 2^(F - 7w): a shift for
+// Jobs for every slice pair (s, t) with s + t <= S + 1 over each K segment of at most kSegBlocks
+// blocks (balanced).  An accumulator stays an exact fp32 integer below 2^22 while n pairs over L
+// blocks of 64 real terms satisfy n * L < 16 (each term is at most 2^12).
+//  * Long segments (L >= 8, one pair per accumulator): pairs of equal t and consecutive s go two
+//    by two into dual jobs (one Bt tile per K block for both), a leftover pair into a single job.
+//  * Short segments: single jobs summing up to 15 / L pairs of equal weight.
+// A pair of weight w = s + t - 2 enters the fixed-point sum with factor 2^(F - 7w): a shift for
 // factors above 2^31, a 32-bit multiplier down to 2^0, and below that a pre-scale 2^(F - 7w) in
 // the drain's FFMA (rounding below 2^-F of a leading digit product).
 // F = min(7S - 9, 50 - log2(K')): resolution below the slicing error, and
@@ -609,39 +676,63 @@ bool make_schedule(int S, int KB, Schedule* sc, unsigned long long* bias, int* f
   while ((1 << lg) < KB * kKBlock) ++lg;
   int F = kDigitBits * S - 9;
   if (F > 50 - lg) F = 50 - lg;
-  const int nseg = (KB + kSegBlocks - 1) / kSegBlocks;
   unsigned long long bs = 0;
-  int ni = 0, ng = 0;
+  int ni = 0, nj = 0;
+  auto set_lane = [&](int j, int l, int d) {
+    const int e = F - kDigitBits * (d - 2);
+    sc->lsh[j][l] = (unsigned char)(e > 31 ? e : 0);
+    sc->mult[j][l] = e > 31 ? 1u : (e >= 0 ? (1u << e) : 1u);
+    sc->fscale[j][l] = e >= 0 ? 1.0f : ldexpf(1.0f, e);
+    bs += (unsigned long long)kMagicBits * ((unsigned long long)sc->mult[j][l] << sc->lsh[j][l]);
+  };
+  auto new_job = [&](int kb0, int kb1, bool dual) {
+    if (nj >= kMaxJobs) return -1;
+    sc->dual[nj] = dual ? 1 : 0;
+    sc->ib[nj] = (unsigned char)ni;
+    sc->ie[nj] = (unsigned char)ni;
+    sc->kb0[nj] = (unsigned char)kb0;
+    sc->kb1[nj] = (unsigned char)kb1;
+    return nj++;
+  };
+  const int nseg = (KB + kSegBlocks - 1) / kSegBlocks;
   for (int seg = 0; seg < nseg; ++seg) {
     const int kb0 = (int)((long long)KB * seg / nseg), kb1 = (int)((long long)KB * (seg + 1) / nseg);
-    const int per_group = 15 / (kb1 - kb0);  // n * L < 16
-    for (int d = 2; d <= S + 1; ++d) {
-      const int e = F - kDigitBits * (d - 2);
-      int in_group = 0;
-      for (int s = 1; s <= S; ++s) {
-        const int t = d - s;
-        if (t < 1 || t > S) continue;
-        if (ni >= kMaxItems) return false;
-        if (in_group == 0) {
-          if (ng >= kMaxGroups) return false;
-          sc->ib[ng] = (unsigned char)ni;
-          sc->kb0[ng] = (unsigned char)kb0;
-          sc->kb1[ng] = (unsigned char)kb1;
-          sc->lsh[ng] = (unsigned char)(e > 31 ? e : 0);
-          sc->mult[ng] = e > 31 ? 1u : (e >= 0 ? (1u << e) : 1u);
-          sc->fscale[ng] = e >= 0 ? 1.0f : ldexpf(1.0f, e);
-          bs += (unsigned long long)kMagicBits * ((unsigned long long)sc->mult[ng] << sc->lsh[ng]);
-          ++ng;
+    const int per_group = 15 / (kb1 - kb0);
+    if (per_group == 1) {
+      for (int t = 1; t <= S; ++t)
+        for (int s = 1; s + t <= S + 1; s += 2) {
+          const bool two = s + 1 + t <= S + 1;
+          const int j = new_job(kb0, kb1, two);
+          if (j < 0 || ni >= kMaxItems) return false;
+          sc->s[ni] = (unsigned char)s;
+          sc->s2[ni] = (unsigned char)(two ? s + 1 : s);
+          sc->t[ni] = (unsigned char)t;
+          sc->ie[j] = (unsigned char)++ni;
+          set_lane(j, 0, s + t);
+          if (two) set_lane(j, 1, s + 1 + t);
         }
-        sc->s[ni] = (unsigned char)s;
-        sc->t[ni] = (unsigned char)t;
-        ++ni;
-        sc->ie[ng - 1] = (unsigned char)ni;
-        if (++in_group == per_group) in_group = 0;
+    } else {
+      for (int d = 2; d <= S + 1; ++d) {
+        int j = -1, in_job = 0;
+        for (int s = 1; s <= S; ++s) {
+          const int t = d - s;
+          if (t < 1 || t > S) continue;
+          if (in_job == 0) {
+            j = new_job(kb0, kb1, false);
+            if (j < 0) return false;
+            set_lane(j, 0, d);
+          }
+          if (ni >= kMaxItems) return false;
+          sc->s[ni] = (unsigned char)s;
+          sc->s2[ni] = (unsigned char)s;
+          sc->t[ni] = (unsigned char)t;
+          sc->ie[j] = (unsigned char)++ni;
+          if (++in_job == per_group) in_job = 0;
+        }
       }
     }
   }
-  sc->n_groups = ng;
+  sc->n_jobs = nj;
   *bias = bs;
   *fix_bits = F;
   return true;
@@ -699,7 +790,7 @@ int num_sms() {
 
 template <int NT>
 bt_status launch_mma(cudaStream_t st, const CUtensorMap& mA, const CUtensorMap& mB, const MmaParams& p) {
-  const size_t smem = 1024 + (size_t)kStages * (kTileM * 128 + NT * 128) + 256;
+  const size_t smem = smem_for(NT);
   // per-function device state: set once per device (the value never changes for one NT)
   static std::mutex mu;
   static bool attr_set[64] = {};

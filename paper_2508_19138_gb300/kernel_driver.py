@@ -22,16 +22,18 @@ def main():
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--slices", type=int, default=6)
+    ap.add_argument("--k", type=int, default=0, help="inner dimension of the products (default: --bs)")
     a = ap.parse_args()
     pkg.library()
     b, n = a.batch, a.bs
+    kk = a.k if a.k > 0 and a.kernel != "zinv" else n
     g = torch.Generator(device="cuda").manual_seed(1)
-    A = torch.randn(b, n, n, dtype=torch.complex128, device="cuda", generator=g)
-    B = torch.randn(b, n, n, dtype=torch.complex128, device="cuda", generator=g)
-    C = torch.empty_like(A)
+    A = torch.randn(b, n, kk, dtype=torch.complex128, device="cuda", generator=g)
+    B = torch.randn(b, kk, n, dtype=torch.complex128, device="cuda", generator=g)
+    C = torch.empty(b, n, n, dtype=torch.complex128, device="cuda")
     ws = None
     if a.kernel == "split":
-        ws = torch.empty(pkg.bt_split_zgemm_workspace_bytes(n, n, n, a.slices, b), dtype=torch.uint8, device="cuda")
+        ws = torch.empty(pkg.bt_split_zgemm_workspace_bytes(n, n, kk, a.slices, b), dtype=torch.uint8, device="cuda")
     info = torch.zeros(b, dtype=torch.int32, device="cuda")
     if a.kernel == "zinv":
         A += 4.0 * torch.eye(n, dtype=torch.complex128, device="cuda")
@@ -40,10 +42,10 @@ def main():
 
     def run():
         if a.kernel == "zgemm":
-            pkg.bt_zgemm_batched(n, n, n, 1.0, A, n, n * n, 0, B, n, n * n, 0, 0.0, C, n, n * n, b)
+            pkg.bt_zgemm_batched(n, n, kk, 1.0, A, kk, n * kk, 0, B, n, kk * n, 0, 0.0, C, n, n * n, b)
         elif a.kernel == "split":
-            pkg.bt_split_zgemm_batched(n, n, n, 1.0, A, n, n * n, 0, B, n, n * n, 0, 0.0, C, n, n * n, b, a.slices,
-                                       workspace=ws)
+            pkg.bt_split_zgemm_batched(n, n, kk, 1.0, A, kk, n * kk, 0, B, n, kk * n, 0, 0.0, C, n, n * n, b,
+                                       a.slices, workspace=ws)
         else:
             Ainv.copy_(A)
             pkg.bt_zinv_batched(n, Ainv, n * n, b, info, workspace=ws)
@@ -57,8 +59,8 @@ def main():
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / a.reps
-    flops = 8.0 * n ** 3 * b
-    print(json.dumps({"kernel": a.kernel, "bs": n, "batch": b, "ms": ms, "fp64_eq_tflops": flops / ms / 1e9,
+    flops = 8.0 * n * n * kk * b
+    print(json.dumps({"kernel": a.kernel, "bs": n, "k": kk, "batch": b, "ms": ms, "fp64_eq_tflops": flops / ms / 1e9,
                       "slices": a.slices if a.kernel == "split" else None}))
 
 
