@@ -18,21 +18,24 @@
 // and a product of digits is an integer of magnitude <= 2^12.
 //
 // Accumulation.  Pairs (s, t) with s + t <= S + 1 are used.  Each pair, over one K segment of at
-// most 960 real terms, is accumulated alone in a TMEM fp32 accumulator: its value is an integer
-// below 960 * 2^12 < 2^22, so the tensor core's fp32 sum is exact.  The drain adds 1.5 * 2^23 to
-// it (one FFMA, which also applies the 2^-p pre-scale of the low-order pairs); the bits of that
-// float are then 0x4B400000 + the integer, and one 32 x 32 -> 64-bit multiply-add accumulates
-// them with the pair's weight 2^(30 - 7(s+t-2) + p) into a per-thread uint64 fixed-point sum
-// (units of 2^-30 of a leading digit product, arithmetic mod 2^64).  The known sum of the
-// 0x4B400000 biases is subtracted once at the end, giving the exact (to 2^-30) two's-complement
-// value.  The FP64 pipe is touched only by the alpha / beta update of C, and not at all for
-// alpha = +-1, beta = 0.
+// most 960 real terms, is accumulated in a TMEM fp32 accumulator (short segments sum several
+// pairs of equal weight in one): its value is an integer below 2^22, so the tensor core's fp32
+// sum is exact.  The drain adds 1.5 * 2^23 to it (one FFMA, which also applies the 2^-p
+// pre-scale of the low-order pairs); the bits of that float are then 0x4B400000 + the integer,
+// and one 32 x 32 -> 64-bit multiply-add accumulates them with the pair's weight 2^(F - 7w + p)
+// into a per-thread uint64 fixed-point sum (units of 2^-F of a leading digit product,
+// arithmetic mod 2^64).  The known sum of the 0x4B400000 biases is subtracted once at the end,
+// giving the exact (to 2^-F) two's-complement value, converted to double once per output.
+//
+// Pairs (s, t), (s + 1, t) of a long segment form a dual job: their At tiles are adjacent in a
+// pipeline stage and their accumulators adjacent in TMEM, so one M = 128, N = 2 NT MMA per K
+// step serves both and reads the Bt tile once.
 //
 // Kernel shape: a persistent grid of one CTA per SM walks the 128 x NT output tiles of C^T
 // (all batch entries); warp 0 issues TMA loads (3-D tensor maps over [batch*S][rows][K'],
 // 128-byte swizzle) through a ring of shared-memory stages, warp 1 issues tcgen05.mma (M = 128,
-// N = NT, K = 16) into a double-buffered TMEM accumulator, warps 2..17 drain the accumulators and
-// write C.  The ring and the accumulators run on across tiles, so the write of one tile overlaps
+// N = NT or 2 NT, K = 16) into double-buffered TMEM accumulators, warps 2..17 drain the
+// accumulators and write C.  The ring and the accumulators run on across tiles, so the write of one tile overlaps
 // the MMAs of the next.  All waits are bounded in time; on a timeout the CTA records
 // BT_ERR_TIMEOUT, drains what it issued and frees its TMEM.
 #include <cuda_bf16.h>
@@ -114,26 +117,18 @@ __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
   return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
 }
 
-// int64 fixed-point value * 2^e -> double, integer arithmetic only (round to nearest even).
+// int64 fixed-point value v * 2^e -> double: one hardware conversion (rounded to nearest even),
+// then the power of two added to the exponent field (ldexp only when the result would leave the
+// normal range).  About a tenth of the integer instructions of a software normalisation, which
+// matters where the write of C dominates (short K).
 __device__ __forceinline__ double fix_to_double(long long v, int e) {
-  if (v == 0) return 0.0;
-  unsigned long long sign = v < 0 ? (1ull << 63) : 0ull;
-  unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
-  const int lz = __clzll(a);
-  a <<= lz;                                   // leading one at bit 63
-  unsigned long long mant = a >> 11;          // 53 bits incl. the leading one
-  const unsigned long long rem = a & 0x7FFull;
-  int expo = 1023 + (63 - lz) + e;            // value = mant * 2^(63-lz-52) * 2^e
-  if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) {
-    ++mant;
-    if (mant >> 53) { mant >>= 1; ++expo; }
-  }
-  if (expo <= 0 || expo >= 2047) {            // outside the normal range: slow path
-    const double r = ldexp((double)mant, expo - 1023 - 52);
-    return sign ? -r : r;
-  }
-  const unsigned long long bits = sign | ((unsigned long long)expo << 52) | (mant & ((1ull << 52) - 1));
-  return __longlong_as_double((long long)bits);
+  const double d = __ll2double_rn(v);
+  const long long bits = __double_as_longlong(d);
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  if (ex == 0) return d;  // v == 0
+  const int ne = ex + e;
+  if (ne <= 0 || ne >= 2047) return ldexp(d, e);
+  return __longlong_as_double(bits + ((long long)e << 52));
 }
 
 // Pipeline depth for an N tile: as many stages (Bt tile + two At tiles) as fit in 227 KB of shared
@@ -171,6 +166,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   static_assert(NT % 16 == 0 && NT >= 16 && NT <= 256, "UMMA N");
   static_assert(4 * NT <= 512, "two double-buffered accumulator pairs must fit in TMEM");
   constexpr uint32_t kIdesc = ptx::idesc_bf16_f32(kTileM, NT);
+  constexpr uint32_t kIdesc2 = ptx::idesc_bf16_f32(kTileM, 2 * NT);
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
@@ -277,7 +273,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           ptx::tc_fence_after();
-          const uint32_t dcol0 = tmem + (2u * ab) * (uint32_t)NT, dcol1 = dcol0 + (uint32_t)NT;
+          const uint32_t dcol0 = tmem + (2u * ab) * (uint32_t)NT;
           const bool dual = sc.dual[g] != 0;
           const int ie = sc.ie[g], kb0 = sc.kb0[g], kb1 = sc.kb1[g];
           uint32_t acc0 = 0u;  // the job's first MMA overwrites the accumulators
@@ -291,16 +287,15 @@ __global__ void __launch_bounds__(kThreads, 1)
               ptx::tc_fence_after();
               const uint32_t a_addr = ptx::smem_u32(stages + stage * kStageBytes);
               const uint32_t b_addr = a_addr + kABytes;
+              // a dual job's two At tiles are contiguous (rows of one 2NT-row operand) and its two
+              // accumulators adjacent in TMEM: one M = 128, N = 2 NT MMA per K step reads the Bt
+              // tile once for both lanes
+              const uint32_t idesc = dual ? kIdesc2 : kIdesc;
 #pragma unroll
               for (int k = 0; k < kKBlock / 16; ++k)
                 ptx::umma_f16(dcol0, ptx::sdesc_kmajor_sw128(a_addr + k * 32),
-                              ptx::sdesc_kmajor_sw128(b_addr + k * 32), kIdesc, k == 0 ? acc0 : 1u);
-              if (dual) {
-#pragma unroll
-                for (int k = 0; k < kKBlock / 16; ++k)
-                  ptx::umma_f16(dcol1, ptx::sdesc_kmajor_sw128(a_addr + k * 32),
-                                ptx::sdesc_kmajor_sw128(b_addr + kBBytes + k * 32), kIdesc, k == 0 ? acc0 : 1u);
-              }
+                              ptx::sdesc_kmajor_sw128(b_addr + k * 32), idesc, k == 0 ? acc0 : 1u);
+
               acc0 = 1u;
               ptx::umma_commit(&empty[stage]);
               if (++stage == kStages) { stage = 0; phase ^= 1u; }

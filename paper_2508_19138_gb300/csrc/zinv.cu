@@ -69,6 +69,22 @@ __device__ __forceinline__ bool cand_better(unsigned long long k1, int p1, unsig
   return k1 > k2 || (k1 == k2 && p1 < p2);
 }
 
+// 1 / a for a finite, non-zero a with one real reciprocal: a is scaled by an exact power of two
+// 2^-e so that s = |a 2^-e|^2 lies in [1, 8), then 1/a = conj(a 2^-e) 2^-e / s.  A handful of dependent
+// FP64 operations instead of the three divisions of Smith's method (used when the exponent is at
+// the ends of the range, where the scaling itself could leave the normal numbers).
+__device__ __forceinline__ zd zrecip_fast(zd a) {
+  const unsigned long long bx = (unsigned long long)__double_as_longlong(a.x) & 0x7FFFFFFFFFFFFFFFull;
+  const unsigned long long by = (unsigned long long)__double_as_longlong(a.y) & 0x7FFFFFFFFFFFFFFFull;
+  const int e = (int)(((bx > by ? bx : by) >> 52) & 0x7FF);  // biased exponent of max(|re|, |im|)
+  if (e < 64 || e > 2046 - 64) return zinv(a);
+  const double sc = __longlong_as_double((long long)(2046 - e) << 52);  // 2^(1023 - e)
+  const double xr = a.x * sc, xi = a.y * sc;                              // exact, max in [1, 2)
+  const double s = fma(xr, xr, xi * xi);
+  const double t = __drcp_rn(s) * sc;
+  return zmake(xr * t, -xi * t);
+}
+
 __device__ __forceinline__ int pivot_code(zd piv) {
   if (!isfinite(piv.x) || !isfinite(piv.y)) return BT_ERR_NONFINITE;
   if (piv.x == 0.0 && piv.y == 0.0) return BT_ERR_SINGULAR;
@@ -245,6 +261,8 @@ __global__ void __launch_bounds__(NT) gj_panel_cluster_kernel(int n, int k0, int
     }
     cluster.sync();  // candidates of column j visible cluster-wide
     if (warp == 0) {
+      // one round of remote reads: every candidate's key and every candidate's row (lane c
+      // holds entry c of all CL rows); the winner's row is then selected locally
       unsigned long long bk = 0;
       int bp = 0x7fffffff, br = -1, bq = 0;
       if (lane < CL) {
@@ -253,6 +271,10 @@ __global__ void __launch_bounds__(NT) gj_panel_cluster_kernel(int n, int k0, int
         br = *cluster.map_shared_rank(&cand_row[par], lane);
         bq = lane;
       }
+      zd cv[CL];
+#pragma unroll
+      for (int q = 0; q < CL; ++q)
+        cv[q] = lane < kb ? cluster.map_shared_rank(pub, q)[par * kb + lane] : zmake(0.0, 0.0);
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
         const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, off);
@@ -261,14 +283,15 @@ __global__ void __launch_bounds__(NT) gj_panel_cluster_kernel(int n, int k0, int
         const int oq = __shfl_xor_sync(0xffffffffu, bq, off);
         if (orr >= 0 && (br < 0 || cand_better(ok, op, bk, bp))) { bk = ok; bp = op; br = orr; bq = oq; }
       }
-      // every lane now holds the winner (row br >= 0 always: position j itself is a candidate);
-      // one remote read of the winning row (kb <= 32 lanes), pivot broadcast from lane jj
-      const zd* wrow = cluster.map_shared_rank(pub, bq) + par * kb;
-      const zd wv = lane < kb ? wrow[lane] : zmake(0.0, 0.0);
+      // every lane now holds the winner (row br >= 0 always: position j itself is a candidate)
+      zd wv = cv[0];
+#pragma unroll
+      for (int q = 1; q < CL; ++q)
+        if (bq == q) wv = cv[q];
       const zd piv = zmake(__shfl_sync(0xffffffffu, wv.x, jj), __shfl_sync(0xffffffffu, wv.y, jj));
       const int pc = pivot_code(piv);
       zd ip = zmake(0.0, 0.0);
-      if (lane == 0 && !pc) ip = zinv(piv);  // one lane: GB300's FP64 pipe is narrow
+      if (lane == 0 && !pc) ip = zrecip_fast(piv);  // one lane: GB300's FP64 pipe is narrow
       ip = zmake(__shfl_sync(0xffffffffu, ip.x, 0), __shfl_sync(0xffffffffu, ip.y, 0));
       if (lane < kb) rowj[lane] = lane == jj ? ip : zmul(wv, ip);
       if (lane == 0) {
