@@ -56,7 +56,10 @@ def parse():
     p.add_argument("--serving-max-energies", type=int, default=32, help="serving: cap per request (flagged)")
     p.add_argument("--serving-budget-gb", type=float, default=150.0)
     p.add_argument("--serving-active", type=int, default=4)
-    p.add_argument("--energies-per-step", type=int, default=16)
+    p.add_argument("--energies-per-step", type=int, default=0,
+                   help="energies per solve (0: 16 for the nanoribbon, the whole 64-energy grid for random8x32)")
+    p.add_argument("--graph", choices=["auto", "on", "off"], default="auto",
+                   help="graph mode (captured chunk replayed; decimation loop on the device); auto: on for random8x32")
     p.add_argument("--precision", choices=["fp64", "split"], default="fp64")
     p.add_argument("--slices", type=int, default=0)
     p.add_argument("--split-scope", type=int, default=0,
@@ -215,7 +218,8 @@ def run_ours(args):
     pkg.library()
     sysg, wl = make_workload(args.workload)
     nE = len(sysg.energies)
-    eps = min(args.energies_per_step, nE)
+    eps = min(args.energies_per_step or (16 if args.workload == "nanoribbon" else nE), nE)
+    graph = args.graph == "on" or (args.graph == "auto" and args.workload == "random8x32")
     # interleave the grid so that every batch of eps energies spans the whole energy window
     nbat = max(1, nE // eps)
     perm = (np.arange(nbat)[:, None] + nbat * np.arange(eps)[None, :]).ravel()
@@ -225,12 +229,15 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     solver = GSolver(sysg.nb, sysg.bs, eps, sysg.eta, sysg.kT, sysg.mu_left, sysg.mu_right, obc=True,
                      precision=precision, split_slices=args.slices, stream=stream, split_scope=args.split_scope,
-                     obc_memo=args.memo, memo_capacity=nE if args.memo else 0)
+                     obc_memo=args.memo, memo_capacity=nE if args.memo else 0, graph=graph and not args.memo)
     with torch.cuda.stream(stream):
         solver.set_inputs(sysg.H_diag, sysg.H_upper, sysg.sigR_diag, sysg.sigL_diag, sysg.sigG_diag)
         outs, status = solver.allocate_outputs(eps)
     torch.cuda.synchronize()
     n_batches = max(1, nE // eps)
+    # bytes the step touches: x^R, x^<, x^> and the outputs, 16 B per complex element
+    step_bytes = 7 * eps * sysg.nb * sysg.bs * sysg.bs * 16
+    l2_small = step_bytes < 4 * 129e6
 
     def batch_range(step):
         j = replicas.batch_index(rank, step, n_batches)
@@ -248,17 +255,32 @@ def run_ours(args):
     barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    barrier()
-    ev[0].record(stream)
-    for s in range(args.steps):
-        one_step(args.warmup + s)
-        ev[s + 1].record(stream)
-    barrier()
+    # a working set below ~L2 size is flushed before every timed step (512 MB write, outside the
+    # step's events); the nanoribbon's per-step working set (> 10 GB) needs none
+    flush = None
+    if l2_small:
+        flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def timed_steps(step_fn):
+        """Times args.steps steps, each bracketed by its own CUDA events on the solve stream (the
+        L2 flush, when needed, sits between a step's end and the next step's start event)."""
+        ev_a = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        barrier()
+        for s in range(args.steps):
+            if flush is not None:
+                with torch.cuda.stream(stream):
+                    flush.fill_(s & 0xFF)
+            ev_a[s].record(stream)
+            step_fn(args.warmup + s)
+            ev_b[s].record(stream)
+        barrier()
+        return [ev_a[i].elapsed_time(ev_b[i]) for i in range(args.steps)]
+
+    step_ms = timed_steps(one_step)
     clk = clocks.stop()
     st1 = solver.stats()
-    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[-1])
+    total_ms = sum(step_ms)
     bad = int((status.cpu().numpy() != 0).sum())
     total_ms_max = replicas.max_over_ranks(total_ms, dist, device="cuda")
     value = eps * args.steps * world / (total_ms_max / 1e3)
@@ -302,7 +324,8 @@ def run_ours(args):
         split_lines = {}
         for scope in (0, 1):
             sp = GSolver(sysg.nb, sysg.bs, eps, sysg.eta, sysg.kT, sysg.mu_left, sysg.mu_right, obc=True,
-                         precision=pkg.BT_SPLIT, split_slices=args.slices, stream=stream, split_scope=scope)
+                         precision=pkg.BT_SPLIT, split_slices=args.slices, stream=stream, split_scope=scope,
+                         graph=graph and not args.memo)
             with torch.cuda.stream(stream):
                 sp.set_inputs(sysg.H_diag, sysg.H_upper, sysg.sigR_diag, sysg.sigL_diag, sysg.sigG_diag)
             torch.cuda.synchronize()
@@ -313,14 +336,7 @@ def run_ours(args):
 
             for w in range(args.warmup):
                 sp_step(w)
-            barrier()
-            q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            q0.record(stream)
-            for s in range(args.steps):
-                sp_step(args.warmup + s)
-            q1.record(stream)
-            barrier()
-            ms = replicas.max_over_ranks(q0.elapsed_time(q1), dist, device="cuda")
+            ms = replicas.max_over_ranks(sum(timed_steps(sp_step)), dist, device="cuda")
             flops_sp = sp.stats()["flops_model"]
             split_lines[f"scope{scope}"] = {
                 "value": eps * args.steps * world / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
@@ -365,8 +381,9 @@ def run_ours(args):
                 "config": {"workload": wl, "nb": sysg.nb, "bs": sysg.bs, "grid_energies": nE,
                            "energies_per_step": eps, "precision": args.precision,
                            "split_scope": args.split_scope if args.precision == "split" else None,
-                           "contact_memo": bool(args.memo),
-                           "l2": "per-step working set > 10 GB exceeds L2; no flush",
+                           "contact_memo": bool(args.memo), "graph": bool(graph and not args.memo),
+                           "l2": ("512 MB write flushes L2 before each timed step (outside its events)" if l2_small
+                                  else f"per-step working set ~{step_bytes / 1e9:.0f} GB exceeds L2; no flush"),
                            "parallelism": f"energy replicas x{world} (no collective)"},
                 "fp64_eq_tflops": flops_step / (statistics.median(step_ms) / 1e3) / 1e12,
                 "fp64_eq_frac_of_peak": flops_step / (statistics.median(step_ms) / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
@@ -450,7 +467,7 @@ def run_w(args):
 
     ws = synthetic.w_system_16x1024()
     nb, bs, nE = ws.nb, ws.bs, len(ws.energies)
-    eps = min(args.energies_per_step, nE)
+    eps = min(args.energies_per_step or 16, nE)
     precision = pkg.BT_SPLIT if args.precision == "split" else pkg.BT_FP64
     stream = torch.cuda.Stream()
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
@@ -543,7 +560,7 @@ def run_serving(args):
         reqs.append((rq, s, H, outs, status))
     torch.cuda.synchronize()
     budget = int(args.serving_budget_gb * (1 << 30))
-    srv = pkg.bt_server_create(budget, max_active=args.serving_active, max_energies_per_chunk=args.energies_per_step,
+    srv = pkg.bt_server_create(budget, max_active=args.serving_active, max_energies_per_chunk=args.energies_per_step or 16,
                                precision=precision, split_slices=args.slices)
 
     def submit(item):
@@ -560,7 +577,7 @@ def run_serving(args):
     rng = np.random.default_rng(synthetic.BASE_SEED + 4)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs) - 1))
     pkg.bt_server_destroy(srv)
-    srv = pkg.bt_server_create(budget, max_active=args.serving_active, max_energies_per_chunk=args.energies_per_step,
+    srv = pkg.bt_server_create(budget, max_active=args.serving_active, max_energies_per_chunk=args.energies_per_step or 16,
                                precision=precision, split_slices=args.slices)
     clocks = ClockSampler(0)
     clocks.start()
@@ -586,7 +603,7 @@ def run_serving(args):
                                     f"(b in 64..832, N_B 8..64), energies per request capped at "
                                     f"{args.serving_max_energies} (flagged), Poisson arrivals at 0.8x capacity"),
                        "arrival_rate_per_s": rate, "budget_gb": args.serving_budget_gb,
-                       "max_active": args.serving_active, "chunk": args.energies_per_step,
+                       "max_active": args.serving_active, "chunk": args.energies_per_step or 16,
                        "precision": args.precision},
             "latency_s": {"p50": st["p50_latency_s"], "p99": st["p99_latency_s"], "mean": st["mean_latency_s"]},
             "server": st, "nonzero_status": bad, "clocks": clk}

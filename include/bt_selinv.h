@@ -122,6 +122,15 @@ typedef struct {
   int split_scope;         /* BT_SPLIT only.  0: sliced products in the sweeps (the default
                               split); 1: also the products inside the block inversions (the
                               rank-kb updates), the decimation and the memoized fixed point    */
+  /* Graph mode (the batching pattern: one launch per chunk).  1: the first solve of a chunk
+   * with a given set of operand pointers captures all of its launches into a CUDA graph, with
+   * the decimation loop as a device-side conditional while node (the iteration stops when the
+   * device count of unconverged leads reaches zero or at decim_maxit), and later solves with the
+   * same pointers replay it as one graph launch (the 8 most recent chunks are kept).  Needs a
+   * non-default stream; exclusive with obc_memo.  The decimation statistics of a replay are
+   * read back asynchronously and folded in at the next solve or bt_selinv_get_stats (which then
+   * synchronises the stream).  0: direct launches.                                              */
+  int graph;
 } bt_selinv_desc;
 
 typedef struct bt_ctx bt_ctx;

@@ -100,10 +100,10 @@ def make_desc(nb: int, bs: int, max_energies: int, system: int = N.BT_SYS_G, pre
               split_slices: int = 0, symmetrize: bool = True, obc: bool = True, eta: float = 1e-6,
               kT: float = 0.025, mu_left: float = 0.0, mu_right: float = 0.0, decim_tol: float = 1e-14,
               decim_maxit: int = 100, hbm_budget_bytes: int = 0, obc_memo: bool = False, memo_nfpi: int = 0,
-              memo_capacity: int = 0, split_scope: int = 0) -> N.bt_selinv_desc:
+              memo_capacity: int = 0, split_scope: int = 0, graph: bool = False) -> N.bt_selinv_desc:
     return N.bt_selinv_desc(nb, bs, max_energies, system, precision, split_slices, 1 if symmetrize else 0,
                             1 if obc else 0, eta, kT, mu_left, mu_right, decim_tol, decim_maxit, hbm_budget_bytes,
-                            1 if obc_memo else 0, memo_nfpi, memo_capacity, split_scope)
+                            1 if obc_memo else 0, memo_nfpi, memo_capacity, split_scope, 1 if graph else 0)
 
 
 class Context:

@@ -95,12 +95,23 @@ size_t zinv_workspace_bytes(int n, int batch, bool wide = false);
 bt_status zinv(cudaStream_t st, int n, zd* A, long long strideA, int batch, int* info, void* ws,
                size_t ws_bytes, const int* active, const Engine* eng = nullptr);
 
-// Sancho-Rubio decimation for `batch` leads.
+// Graph mode of the decimation: `st` is being captured into a CUDA graph, and the iteration
+// loop is captured as a conditional while node whose body (one iteration and the convergence
+// test) is recorded on `body_stream`; the device decides when to stop.  body_launches returns
+// the kernels of one pass of the body.
+struct LoopCapture {
+  cudaStream_t body_stream = nullptr;
+  long long body_launches = 0;
+};
+
+// Sancho-Rubio decimation for `batch` leads.  With `loop` (graph capture), iters_host_max and
+// lead_iterations are not written: the per-lead counts are in `iters` on the device.
 size_t decimate_workspace_bytes(int bs, int batch, bool wide = false);
 bt_status decimate(cudaStream_t st, int bs, int batch, const zd* m, const zd* n, const zd* np,
                    double tol, int maxit, zd* x, zd* sigma, int* iters, int* info, void* ws,
                    size_t ws_bytes, int* iters_host_max, int* h_pinned, const int* mask = nullptr,
-                   long long* lead_iterations = nullptr, const Engine* eng = nullptr);
+                   long long* lead_iterations = nullptr, const Engine* eng = nullptr,
+                   LoopCapture* loop = nullptr);
 bt_status invert_mask(cudaStream_t st, int batch, const int* a, int* out);  // out = !a
 // Fixed-point iteration x <- (m - n x n')^{-1} (Eq. 5) from the given x for leads with run[l];
 // conv[l] = 1 where it converged to tol within nfpi iterations.

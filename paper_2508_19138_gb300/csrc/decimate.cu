@@ -12,6 +12,11 @@
 // through an `active` mask, and
 // the host stops as soon as the device-side count of active leads reaches zero.  The loop is
 // bounded by maxit; leads still active then get BT_ERR_NOT_CONVERGED (never a hang).
+// In graph mode the same loop is a conditional while node of the captured graph: a one-thread
+// kernel at the end of each iteration sets the loop condition from that count and the device
+// iteration counter, so a whole solve runs without returning to the host.
+#include <cstring>
+#include <utility>
 #include <vector>
 
 #include "bt_common.cuh"
@@ -183,6 +188,35 @@ __global__ void fpi_check_kernel(int batch, const unsigned long long* __restrict
   }
 }
 
+// Graph mode: the convergence test reads the iteration number from the device counter.
+__global__ void check_dev_kernel(int batch, const unsigned long long* __restrict__ keys, const int* __restrict__ flags,
+                                 const double* __restrict__ ref, double tol, const int* __restrict__ itc,
+                                 int* __restrict__ active, int* __restrict__ iters, int* __restrict__ info,
+                                 int* __restrict__ n_active) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= batch || active[l] == 0) return;
+  const double v = key_sqrt(keys[2 * l] > keys[2 * l + 1] ? keys[2 * l] : keys[2 * l + 1]);
+  iters[l] = *itc;
+  if (flags[l] || info[l] != 0) {
+    if (info[l] == 0) info[l] = BT_ERR_NONFINITE;
+    active[l] = 0;
+  } else if (v <= tol * ref[l]) {
+    active[l] = 0;
+  } else {
+    atomicAdd(n_active, 1);
+  }
+}
+
+// Graph mode: iteration counter and loop condition (continue while leads are active and the
+// iteration cap is not reached).  One thread.
+__global__ void loop_ctl_kernel(cudaGraphConditionalHandle h, const int* __restrict__ n_active, int* itc, int maxit) {
+  const int it = *itc;
+  *itc = it + 1;
+  cudaGraphSetConditional(h, (*n_active > 0 && it < maxit) ? 1u : 0u);
+}
+
+__global__ void set_int_kernel(int* p, int v) { *p = v; }
+
 __global__ void not_kernel(int batch, const int* __restrict__ a, int* __restrict__ out) {
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l < batch) out[l] = a[l] ? 0 : 1;
@@ -195,6 +229,7 @@ struct DecimWs {
   int* flags;
   int* active;
   int* n_active;
+  int* itc;  // graph mode: iteration counter
   void* inv_ws;
   size_t inv_bytes;
 };
@@ -213,9 +248,126 @@ size_t carve(void* base, int bs, int batch, bool wide, DecimWs* w) {
   w->flags = reinterpret_cast<int*>(take(sizeof(int) * batch));
   w->active = reinterpret_cast<int*>(take(sizeof(int) * batch));
   w->n_active = reinterpret_cast<int*>(take(sizeof(int)));
+  w->itc = reinterpret_cast<int*>(take(sizeof(int)));
   w->inv_bytes = zinv_workspace_bytes(bs, batch, wide);
   w->inv_ws = take(w->inv_bytes);
   return off;
+}
+
+// One decimation iteration on the active leads.  With `fixed` the new a, b are copied back into
+// w.a, w.b (the buffers stay where a captured graph expects them); otherwise the buffers swap.
+bt_status decimate_step(cudaStream_t st, int bs, int batch, DecimWs& w, int* info, const Engine& E, bool fixed) {
+  const long long bs2 = (long long)bs * bs, S = bs2;
+  const size_t mat_bytes = (size_t)batch * bs2 * sizeof(zd);
+  const zd one = zmake(1.0, 0.0), mone = zmake(-1.0, 0.0), zero = zmake(0.0, 0.0);
+  BT_CUDA_TRY(cudaMemcpyAsync(w.g, w.e, mat_bytes, cudaMemcpyDeviceToDevice, st));
+  BT_TRY(zinv(st, bs, w.g, S, batch, info, w.inv_ws, w.inv_bytes, w.active, &E));
+  // ag = a g, bg = b g
+  BT_TRY(gemm(E, st, bs, bs, bs, one, Operand{w.a, bs, S, BT_OP_N}, Operand{w.g, bs, S, BT_OP_N}, zero, w.ag, bs, S, batch, w.active));
+  BT_TRY(gemm(E, st, bs, bs, bs, one, Operand{w.b, bs, S, BT_OP_N}, Operand{w.g, bs, S, BT_OP_N}, zero, w.bg, bs, S, batch, w.active));
+  // t = a g b; es -= t; e -= t
+  BT_TRY(gemm(E, st, bs, bs, bs, one, Operand{w.ag, bs, S, BT_OP_N}, Operand{w.b, bs, S, BT_OP_N}, zero, w.t, bs, S, batch, w.active));
+  {
+    dim3 g((unsigned)((bs2 + 255) / 256 < 64 ? (bs2 + 255) / 256 : 64), batch);
+    sub2_kernel<<<g, 256, 0, st>>>(bs2, batch, w.t, w.es, w.e, w.active); count_launch();
+    BT_CUDA_TRY(cudaGetLastError());
+  }
+  // e -= b g a
+  BT_TRY(gemm(E, st, bs, bs, bs, mone, Operand{w.bg, bs, S, BT_OP_N}, Operand{w.a, bs, S, BT_OP_N}, one, w.e, bs, S, batch, w.active));
+  // a2 = -a g a, b2 = -b g b
+  BT_TRY(gemm(E, st, bs, bs, bs, mone, Operand{w.ag, bs, S, BT_OP_N}, Operand{w.a, bs, S, BT_OP_N}, zero, w.a2, bs, S, batch, w.active));
+  BT_TRY(gemm(E, st, bs, bs, bs, mone, Operand{w.bg, bs, S, BT_OP_N}, Operand{w.b, bs, S, BT_OP_N}, zero, w.b2, bs, S, batch, w.active));
+  if (fixed) {
+    BT_CUDA_TRY(cudaMemcpyAsync(w.a, w.a2, mat_bytes, cudaMemcpyDeviceToDevice, st));
+    BT_CUDA_TRY(cudaMemcpyAsync(w.b, w.b2, mat_bytes, cudaMemcpyDeviceToDevice, st));
+  } else {
+    std::swap(w.a, w.a2);
+    std::swap(w.b, w.b2);
+  }
+  BT_CUDA_TRY(cudaMemsetAsync(w.n_active, 0, sizeof(int), st));
+  BT_TRY(lead_max(st, 0, bs2, batch, w.a, w.b, w.active, w.keys, w.flags));
+  return BT_OK;
+}
+
+// Graph mode: the iteration loop as a conditional while node of the graph being captured on st.
+bt_status decimate_loop_graph(cudaStream_t st, LoopCapture& loop, int bs, int batch, double tol, int maxit,
+                              DecimWs& w, int* iters, int* info, const Engine& E) {
+  set_int_kernel<<<1, 1, 0, st>>>(w.itc, 1); count_launch();
+  BT_CUDA_TRY(cudaGetLastError());
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  BT_CUDA_TRY(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &ndeps));
+  if (cs != cudaStreamCaptureStatusActive || !g) return BT_ERR_INVALID_ARG;
+  cudaGraphConditionalHandle h;
+  BT_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault));
+  // the parameter union has no default constructor: zeroed storage, fields set by name
+  alignas(cudaGraphNodeParams) unsigned char pbuf[sizeof(cudaGraphNodeParams)];
+  std::memset(pbuf, 0, sizeof(pbuf));
+  cudaGraphNodeParams& p = *reinterpret_cast<cudaGraphNodeParams*>(pbuf);
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  BT_CUDA_TRY(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &p));
+  BT_CUDA_TRY(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  cudaGraph_t body = p.conditional.phGraph_out[0];
+  cudaStream_t bst = loop.body_stream;
+  BT_CUDA_TRY(cudaStreamBeginCaptureToGraph(bst, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  const long long l0 = launches_total();
+  bt_status rc = decimate_step(bst, bs, batch, w, info, E, true);
+  if (rc == BT_OK) {
+    check_dev_kernel<<<(batch + 255) / 256, 256, 0, bst>>>(batch, w.keys, w.flags, w.ref, tol, w.itc, w.active, iters,
+                                                           info, w.n_active); count_launch();
+    loop_ctl_kernel<<<1, 1, 0, bst>>>(h, w.n_active, w.itc, maxit); count_launch();
+    if (cudaGetLastError() != cudaSuccess) rc = BT_ERR_CUDA;
+  }
+  loop.body_launches = launches_total() - l0;
+  cudaGraph_t got = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(bst, &got);
+  if (rc != BT_OK) return rc;
+  return ce == cudaSuccess ? BT_OK : BT_ERR_CUDA;
+}
+
+
+// Direct mode: host-driven loop, one convergence read-back per iteration.
+bt_status decimate_loop_host(cudaStream_t st, int bs, int batch, double tol, int maxit, DecimWs& w, int* iters,
+                             int* info, const Engine& E, const int* mask, int* h_pinned, int* iters_host_max,
+                             long long* lead_iterations) {
+  int* h_active = h_pinned;
+  if (!h_active) BT_CUDA_TRY(cudaMallocHost(&h_active, sizeof(int)));
+  int it = 0;
+  long long lead_its = 0;
+  int running = batch;  // leads entering the next iteration (upper bound before the first test)
+  bt_status rc = BT_OK;
+  if (mask) {
+    // count the masked-in leads so a fully memoized chunk runs no iteration at all
+    std::vector<int> hm(batch);
+    if (cudaMemsetAsync(w.n_active, 0, sizeof(int), st) != cudaSuccess ||
+        cudaMemcpyAsync(hm.data(), mask, sizeof(int) * batch, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      rc = BT_ERR_CUDA;
+    running = 0;
+    for (int v : hm) running += v != 0;
+  }
+  for (it = 1; rc == BT_OK && it <= maxit && running > 0; ++it) {
+    lead_its += running;
+    if ((rc = decimate_step(st, bs, batch, w, info, E, false)) != BT_OK) break;
+    check_kernel<<<(batch + 255) / 256, 256, 0, st>>>(batch, w.keys, w.flags, w.ref, tol, it, w.active, iters, info,
+                                                      w.n_active); count_launch();
+    if (cudaGetLastError() != cudaSuccess) { rc = BT_ERR_CUDA; break; }
+    if (cudaMemcpyAsync(h_active, w.n_active, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) { rc = BT_ERR_CUDA; break; }
+    if (cudaStreamSynchronize(st) != cudaSuccess) { rc = BT_ERR_CUDA; break; }
+    running = *h_active;
+    if (running == 0) break;
+  }
+  if (!h_pinned) cudaFreeHost(h_active);
+  if (rc != BT_OK) return rc;
+  if (iters_host_max) *iters_host_max = it > maxit ? maxit : (it > 0 ? it : 0);
+  if (lead_iterations) *lead_iterations = lead_its;
+  return BT_OK;
 }
 
 }  // namespace
@@ -228,10 +380,11 @@ size_t decimate_workspace_bytes(int bs, int batch, bool wide) {
 bt_status decimate(cudaStream_t st, int bs, int batch, const zd* m, const zd* n, const zd* np, double tol,
                    int maxit, zd* x, zd* sigma, int* iters, int* info, void* ws, size_t ws_bytes,
                    int* iters_host_max, int* h_pinned, const int* mask, long long* lead_iterations,
-                   const Engine* eng) {
+                   const Engine* eng, LoopCapture* loop) {
   const Engine fp64;
   const Engine& E = eng ? *eng : fp64;
   if (bs <= 0 || batch <= 0 || maxit <= 0 || batch > 65535) return BT_ERR_INVALID_ARG;
+  if (loop && (mask || !loop->body_stream)) return BT_ERR_INVALID_ARG;
   // wide inversion panels when the products run sliced and the workspace was sized for them
   const bool wide = E.slices > 0 && ws_bytes >= decimate_workspace_bytes(bs, batch, true);
   if (!ws || ws_bytes < decimate_workspace_bytes(bs, batch, wide)) return BT_ERR_INVALID_ARG;
@@ -249,58 +402,12 @@ bt_status decimate(cudaStream_t st, int bs, int batch, const zd* m, const zd* n,
   ref_kernel<<<(batch + 255) / 256, 256, 0, st>>>(batch, w.keys, w.ref); count_launch();
   BT_CUDA_TRY(cudaGetLastError());
 
-  int* h_active = h_pinned;
-  if (!h_active) BT_CUDA_TRY(cudaMallocHost(&h_active, sizeof(int)));
-  const zd one = zmake(1.0, 0.0), mone = zmake(-1.0, 0.0), zero = zmake(0.0, 0.0);
-  const long long S = bs2;
-  int it = 0;
-  long long lead_its = 0;
-  int running = batch;  // leads entering the next iteration (upper bound before the first test)
-  if (mask) {
-    // count the masked-in leads so a fully memoized chunk runs no iteration at all
-    if (cudaMemsetAsync(w.n_active, 0, sizeof(int), st) != cudaSuccess) return BT_ERR_CUDA;
-    std::vector<int> hm(batch);
-    if (cudaMemcpyAsync(hm.data(), mask, sizeof(int) * batch, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
-      return BT_ERR_CUDA;
-    running = 0;
-    for (int v : hm) running += v != 0;
+  if (loop) {
+    BT_TRY(decimate_loop_graph(st, *loop, bs, batch, tol, maxit, w, iters, info, E));
+  } else {
+    BT_TRY(decimate_loop_host(st, bs, batch, tol, maxit, w, iters, info, E, mask, h_pinned, iters_host_max,
+                              lead_iterations));
   }
-  bt_status rc = BT_OK;
-  for (it = 1; it <= maxit && running > 0; ++it) {
-    lead_its += running;
-    if (cudaMemcpyAsync(w.g, w.e, mat_bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) { rc = BT_ERR_CUDA; break; }
-    if ((rc = zinv(st, bs, w.g, S, batch, info, w.inv_ws, w.inv_bytes, w.active, &E)) != BT_OK) break;
-    // ag = a g, bg = b g
-    if ((rc = gemm(E, st, bs, bs, bs, one, Operand{w.a, bs, S, BT_OP_N}, Operand{w.g, bs, S, BT_OP_N}, zero, w.ag, bs, S, batch, w.active)) != BT_OK) break;
-    if ((rc = gemm(E, st, bs, bs, bs, one, Operand{w.b, bs, S, BT_OP_N}, Operand{w.g, bs, S, BT_OP_N}, zero, w.bg, bs, S, batch, w.active)) != BT_OK) break;
-    // t = a g b; es -= t; e -= t
-    if ((rc = gemm(E, st, bs, bs, bs, one, Operand{w.ag, bs, S, BT_OP_N}, Operand{w.b, bs, S, BT_OP_N}, zero, w.t, bs, S, batch, w.active)) != BT_OK) break;
-    {
-      dim3 g((unsigned)((bs2 + 255) / 256 < 64 ? (bs2 + 255) / 256 : 64), batch);
-      sub2_kernel<<<g, 256, 0, st>>>(bs2, batch, w.t, w.es, w.e, w.active); count_launch();
-    }
-    // e -= b g a
-    if ((rc = gemm(E, st, bs, bs, bs, mone, Operand{w.bg, bs, S, BT_OP_N}, Operand{w.a, bs, S, BT_OP_N}, one, w.e, bs, S, batch, w.active)) != BT_OK) break;
-    // a2 = -a g a, b2 = -b g b
-    if ((rc = gemm(E, st, bs, bs, bs, mone, Operand{w.ag, bs, S, BT_OP_N}, Operand{w.a, bs, S, BT_OP_N}, zero, w.a2, bs, S, batch, w.active)) != BT_OK) break;
-    if ((rc = gemm(E, st, bs, bs, bs, mone, Operand{w.bg, bs, S, BT_OP_N}, Operand{w.b, bs, S, BT_OP_N}, zero, w.b2, bs, S, batch, w.active)) != BT_OK) break;
-    std::swap(w.a, w.a2);
-    std::swap(w.b, w.b2);
-    if (cudaMemsetAsync(w.n_active, 0, sizeof(int), st) != cudaSuccess) { rc = BT_ERR_CUDA; break; }
-    if ((rc = lead_max(st, 0, bs2, batch, w.a, w.b, w.active, w.keys, w.flags)) != BT_OK) break;
-    check_kernel<<<(batch + 255) / 256, 256, 0, st>>>(batch, w.keys, w.flags, w.ref, tol, it, w.active, iters, info,
-                                                      w.n_active); count_launch();
-    if (cudaGetLastError() != cudaSuccess) { rc = BT_ERR_CUDA; break; }
-    if (cudaMemcpyAsync(h_active, w.n_active, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) { rc = BT_ERR_CUDA; break; }
-    if (cudaStreamSynchronize(st) != cudaSuccess) { rc = BT_ERR_CUDA; break; }
-    running = *h_active;
-    if (running == 0) break;
-  }
-  if (!h_pinned) cudaFreeHost(h_active);
-  if (rc != BT_OK) return rc;
-  if (iters_host_max) *iters_host_max = it > maxit ? maxit : (it > 0 ? it : 0);
-  if (lead_iterations) *lead_iterations = lead_its;
   finish_kernel<<<(batch + 255) / 256, 256, 0, st>>>(batch, w.active, info); count_launch();
   BT_CUDA_TRY(cudaGetLastError());
   // x = e_s^{-1} (decimated leads);  sigma = n x n'
@@ -309,6 +416,8 @@ bt_status decimate(cudaStream_t st, int bs, int batch, const zd* m, const zd* n,
     masked_copy_kernel<<<g, 256, 0, st>>>(bs2, w.es, x, mask); count_launch();
     BT_CUDA_TRY(cudaGetLastError());
   }
+  const long long S = bs2;
+  const zd one = zmake(1.0, 0.0), zero = zmake(0.0, 0.0);
   BT_TRY(zinv(st, bs, x, S, batch, info, w.inv_ws, w.inv_bytes, mask, &E));
   if (sigma) {
     BT_TRY(gemm(E, st, bs, bs, bs, one, Operand{n, bs, S, BT_OP_N}, Operand{x, bs, S, BT_OP_N}, zero, w.t, bs, S, batch, nullptr));
@@ -316,6 +425,7 @@ bt_status decimate(cudaStream_t st, int bs, int batch, const zd* m, const zd* n,
   }
   return BT_OK;
 }
+
 
 bt_status invert_mask(cudaStream_t st, int batch, const int* a, int* out) {
   not_kernel<<<(batch + 255) / 256, 256, 0, st>>>(batch, a, out);

@@ -66,6 +66,26 @@ struct bt_ctx {
   std::string err;
   bt_stats stats{};
   double flops = 0.0;
+  // graph mode: captured chunks (least recently used first), the stream the decimation loop body
+  // is captured on, and the per-lead iteration counts of the last replayed chunk (read back
+  // asynchronously, folded into the statistics at the next synchronisation)
+  struct Captured {
+    std::vector<char> key;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    double flops = 0.0;             // model flops without the decimation iterations
+    long long launches = 0;         // kernels outside the decimation loop
+    long long body_launches = 0;    // kernels per decimation iteration
+    bool decim = false;
+  };
+  std::vector<Captured> graphs;
+  cudaStream_t body_st = nullptr;
+  bt::LoopCapture* loop = nullptr;  // non-null while a chunk is being captured
+  int* h_iters = nullptr;           // [2E] pinned
+  bool pending = false;
+  int pending_Ec = 0;
+  long long pending_body = 0;
+  long long uncounted = 0;          // launches recorded during capture (not executed)
 };
 
 namespace {
@@ -166,6 +186,8 @@ bt_status validate_desc(const bt_selinv_desc* d, std::string* why) {
   if (d->obc && d->nb < 2) return fail("contacts from the edge blocks need nb >= 2");
   if (d->obc && !(d->kT > 0.0)) return fail("kT must be > 0 with contacts");
   if (d->obc_memo && !d->obc) return fail("contact memoization needs obc = 1");
+  if (d->graph != 0 && d->graph != 1) return fail("graph must be 0 or 1");
+  if (d->graph && d->obc_memo) return fail("graph mode and contact memoization are exclusive");
   if (d->split_scope != 0 && d->split_scope != 1) return fail("split_scope must be 0 or 1");
   if (d->obc_memo && d->memo_capacity > 1000000) return fail("memo_capacity too large");
   if (!(d->eta >= 0.0)) return fail("eta must be >= 0");
@@ -398,6 +420,21 @@ bt_status ctx_create(const bt_selinv_desc* desc, void* cuda_stream, void* ext_ws
     *err = "pinned host allocation failed";
     return BT_ERR_OOM;
   }
+  if (d.graph) {
+    if (!c->st) {
+      bt_selinv_destroy(c);
+      *err = "graph mode needs a non-default stream (stream capture)";
+      return BT_ERR_INVALID_ARG;
+    }
+    if (cudaStreamCreateWithFlags(&c->body_st, cudaStreamNonBlocking) != cudaSuccess ||
+        (c->pinned ? cudaMallocHost(&c->h_iters, sizeof(int) * 2 * d.max_energies) != cudaSuccess
+                   : (c->h_iters = new int[2 * d.max_energies]) == nullptr)) {
+      cudaGetLastError();
+      bt_selinv_destroy(c);
+      *err = "graph mode set-up failed";
+      return BT_ERR_CUDA;
+    }
+  }
   c->stats.workspace_bytes = need;
   if (is_split(d) && d.split_scope == 1) c->eng_kept = bt::Engine{slices_of(d), c->split_ws, c->split_bytes};
   if (d.obc_memo) {
@@ -419,6 +456,16 @@ extern "C" bt_status bt_selinv_create(const bt_selinv_desc* desc, void* cuda_str
 
 extern "C" bt_status bt_selinv_destroy(bt_ctx* c) {
   if (!c) return BT_OK;
+  if (c->st) cudaStreamSynchronize(c->st);
+  for (auto& g : c->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+  }
+  if (c->body_st) cudaStreamDestroy(c->body_st);
+  if (c->h_iters) {
+    if (c->pinned) cudaFreeHost(c->h_iters);
+    else delete[] c->h_iters;
+  }
   if (c->ws && c->owns_ws) cudaFree(c->ws);
   if (c->stage) cudaFree(c->stage);
   if (c->pinned) {
@@ -437,8 +484,36 @@ extern "C" const char* bt_selinv_last_error(const bt_ctx* c) {
   return c->err.c_str();
 }
 
+namespace {
+
+// Graph mode: folds the device-side decimation counts of the last replayed chunk into the
+// statistics.  The caller has synchronised the stream.
+void fold_pending(bt_ctx* c) {
+  if (!c->pending) return;
+  c->pending = false;
+  long long it_max = 0, lead_its = 0;
+  for (int l = 0; l < 2 * c->pending_Ec; ++l) {
+    const long long v = c->h_iters[l] > 0 ? c->h_iters[l] : 0;
+    it_max = v > it_max ? v : it_max;
+    lead_its += v;
+  }
+  const double U = 8.0 * c->d.bs * (double)c->d.bs * c->d.bs;
+  c->stats.decim_iterations += it_max;
+  c->stats.lead_iterations += lead_its;
+  c->stats.kernel_launches += c->pending_body * it_max;
+  c->flops += 7.0 * U * (double)lead_its;
+  c->stats.flops_model = c->flops;
+}
+
+}  // namespace
+
 extern "C" bt_status bt_selinv_get_stats(const bt_ctx* c, bt_stats* out) {
   if (!c || !out) return BT_ERR_INVALID_ARG;
+  if (c->pending) {
+    bt_ctx* m = const_cast<bt_ctx*>(c);  // a handle is single-threaded; the read-back is folded here
+    if (cudaStreamSynchronize(m->st) != cudaSuccess) return BT_ERR_CUDA;
+    fold_pending(m);
+  }
   *out = c->stats;
   return BT_OK;
 }
@@ -624,7 +699,7 @@ bt_status solve_chunk_g(bt_ctx* c, const bt_bt* H, const bt_bt* S, const bt_bt* 
     }
     bt_status s = bt::decimate(st, bs, 2 * Ec, c->lead_m, c->lead_n, c->lead_np, d.decim_tol, d.decim_maxit, c->lead_x,
                                c->lead_sig, c->lead_iters, c->lead_info, c->dec_ws, c->dec_bytes, &it_max,
-                               c->h_pinned, dec_mask, &lead_its, &c->eng_kept);
+                               c->h_pinned, dec_mask, &lead_its, &c->eng_kept, c->loop);
     if (s != BT_OK) return set_err(c, s, "decimation failed to launch");
     c->stats.decim_iterations += it_max;
     c->stats.lead_iterations += lead_its;
@@ -928,6 +1003,117 @@ bt_status check_solve_args(bt_ctx* c, const bt_bt* H, const bt_bt* S, const bt_b
 
 }  // namespace
 
+namespace {
+
+// Key of a captured chunk: every pointer and layout field the captured launches depend on (the
+// energies themselves are uploaded outside the graph).
+std::vector<char> chunk_key(long long e0, int Ec, const bt_bt* const* ins, int n_in, const bt_bt_out* const* outs,
+                            int n_out, const int* status) {
+  std::vector<char> k;
+  auto put = [&](const void* p, size_t n) {
+    const char* b = static_cast<const char*>(p);
+    k.insert(k.end(), b, b + n);
+  };
+  put(&e0, sizeof(e0));
+  put(&Ec, sizeof(Ec));
+  for (int i = 0; i < n_in; ++i) {
+    const char present = ins[i] != nullptr;
+    put(&present, 1);
+    if (present) {
+      put(&ins[i]->diag, sizeof(void*));
+      put(&ins[i]->upper, sizeof(void*));
+      put(&ins[i]->lower, sizeof(void*));
+      put(&ins[i]->layout, sizeof(int));
+      put(&ins[i]->symmetry, sizeof(int));
+      put(&ins[i]->per_energy, sizeof(int));
+    }
+  }
+  for (int i = 0; i < n_out; ++i) {
+    const char present = outs[i] != nullptr;
+    put(&present, 1);
+    if (present) {
+      put(&outs[i]->diag, sizeof(void*));
+      put(&outs[i]->upper, sizeof(void*));
+      put(&outs[i]->lower, sizeof(void*));
+      put(&outs[i]->layout, sizeof(int));
+    }
+  }
+  put(&status, sizeof(status));
+  return k;
+}
+
+constexpr size_t kMaxCaptured = 8;
+
+// Graph mode: replays the chunk's captured graph, capturing it first when this combination of
+// operands has not been seen (kMaxCaptured most recent kept).  The decimation loop is a
+// conditional while node, so a replay needs no host round trip.
+template <class Direct>
+bt_status run_chunk_graph(bt_ctx* c, const bt_bt* H, const bt_bt* S, const bt_bt* sR, const bt_bt* sL,
+                          const bt_bt* sG, long long e0, int Ec, const bt_bt_out* oR, const bt_bt_out* oL,
+                          const bt_bt_out* oG, int* status, Direct direct) {
+  const bt_bt* ins[5] = {H, S, sR, sL, sG};
+  const bt_bt_out* outs[3] = {oR, oL, oG};
+  std::vector<char> key = chunk_key(e0, Ec, ins, 5, outs, 3, status);
+  size_t idx = c->graphs.size();
+  for (size_t i = 0; i < c->graphs.size(); ++i)
+    if (c->graphs[i].key == key) { idx = i; break; }
+  if (idx == c->graphs.size()) {
+    bt_ctx::Captured g;
+    g.key = std::move(key);
+    bt::LoopCapture loop;
+    loop.body_stream = c->body_st;
+    const double f0 = c->flops;
+    const long long l0 = bt::launches_total();
+    if (cudaStreamBeginCapture(c->st, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+      return set_err(c, BT_ERR_CUDA, "stream capture could not start");
+    c->loop = c->d.obc ? &loop : nullptr;
+    bt_status s = direct();
+    c->loop = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(c->st, &g.graph);
+    const long long recorded = bt::launches_total() - l0;
+    c->uncounted += recorded;
+    if (s != BT_OK || ce != cudaSuccess) {
+      if (g.graph) cudaGraphDestroy(g.graph);
+      cudaGetLastError();
+      return s != BT_OK ? s : set_err(c, BT_ERR_CUDA, "stream capture failed");
+    }
+    if (cudaGraphInstantiate(&g.exec, g.graph, 0) != cudaSuccess) {
+      cudaGetLastError();
+      cudaGraphDestroy(g.graph);
+      return set_err(c, BT_ERR_CUDA, "graph instantiation failed");
+    }
+    g.flops = c->flops - f0;
+    c->flops = f0;  // counted again below, as for every replay
+    g.body_launches = loop.body_launches;
+    g.launches = recorded - loop.body_launches;
+    g.decim = c->d.obc != 0;
+    if (c->graphs.size() >= kMaxCaptured) {
+      cudaGraphExecDestroy(c->graphs.front().exec);
+      cudaGraphDestroy(c->graphs.front().graph);
+      c->graphs.erase(c->graphs.begin());
+    }
+    c->graphs.push_back(std::move(g));
+    idx = c->graphs.size() - 1;
+  } else if (idx + 1 != c->graphs.size()) {
+    std::rotate(c->graphs.begin() + idx, c->graphs.begin() + idx + 1, c->graphs.end());
+    idx = c->graphs.size() - 1;
+  }
+  const bt_ctx::Captured& g = c->graphs[idx];
+  if (cudaGraphLaunch(g.exec, c->st) != cudaSuccess) return set_err(c, BT_ERR_CUDA, "graph launch failed");
+  c->flops += g.flops;
+  c->stats.kernel_launches += g.launches;
+  if (g.decim) {
+    if (cudaMemcpyAsync(c->h_iters, c->lead_iters, sizeof(int) * 2 * Ec, cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
+      return set_err(c, BT_ERR_CUDA, "iteration read-back failed");
+    c->pending = true;
+    c->pending_Ec = Ec;
+    c->pending_body = g.body_launches;
+  }
+  return BT_OK;
+}
+
+}  // namespace
+
 extern "C" bt_status bt_selinv_solve(bt_ctx* c, const bt_bt* H, const bt_bt* S, const bt_bt* sigR, const bt_bt* sigL,
                                      const bt_bt* sigG, const double* energies_host, int n_energies,
                                      const bt_bt_out* outR, const bt_bt_out* outL, const bt_bt_out* outG,
@@ -936,12 +1122,17 @@ extern "C" bt_status bt_selinv_solve(bt_ctx* c, const bt_bt* H, const bt_bt* S, 
   c->err.clear();
   BT_TRY(check_solve_args(c, H, S, sigR, sigL, sigG, energies_host, n_energies, outR, outL, outG, status_device));
   if (n_energies == 0) return BT_OK;
+  if (c->pending) {  // the previous solve's last replayed chunk: complete its statistics first
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return set_err(c, BT_ERR_CUDA, "stream error");
+    fold_pending(c);
+  }
   c->flops = 0.0;
   const long long launches0 = bt::launches_total();
+  c->uncounted = 0;
   struct LaunchTally {  // attributes this call's launches to the context on every return path
     bt_ctx* c;
     long long l0;
-    ~LaunchTally() { c->stats.kernel_launches += bt::launches_total() - l0; }
+    ~LaunchTally() { c->stats.kernel_launches += bt::launches_total() - l0 - c->uncounted; }
   } tally{c, launches0};
   if (cudaMemsetAsync(status_device, 0, sizeof(int) * (size_t)n_energies, c->st) != cudaSuccess)
     return set_err(c, BT_ERR_CUDA, "cudaMemsetAsync(status) failed");
@@ -953,11 +1144,16 @@ extern "C" bt_status bt_selinv_solve(bt_ctx* c, const bt_bt* H, const bt_bt* S, 
     std::memcpy(c->h_E, energies_host + e0, sizeof(double) * Ec);
     if (cudaMemcpyAsync(c->Edev, c->h_E, sizeof(double) * Ec, cudaMemcpyHostToDevice, c->st) != cudaSuccess)
       return set_err(c, BT_ERR_CUDA, "energy upload failed");
+    fold_pending(c);  // the stream is idle here
     bt_status s;
-    if (c->d.system == BT_SYS_G)
-      s = solve_chunk_g(c, H, S, sigR, sigL, sigG, e0, Ec, outR, outL, outG, status_device + e0);
+    auto direct = [&]() {
+      return c->d.system == BT_SYS_G ? solve_chunk_g(c, H, S, sigR, sigL, sigG, e0, Ec, outR, outL, outG, status_device + e0)
+                                     : solve_chunk_w(c, H, sigR, sigL, sigG, e0, Ec, outR, outL, outG, status_device + e0);
+    };
+    if (c->d.graph)
+      s = run_chunk_graph(c, H, S, sigR, sigL, sigG, e0, Ec, outR, outL, outG, status_device + e0, direct);
     else
-      s = solve_chunk_w(c, H, sigR, sigL, sigG, e0, Ec, outR, outL, outG, status_device + e0);
+      s = direct();
     if (s != BT_OK) {
       if (c->err.empty()) c->err = "a kernel launch failed";
       return s;

@@ -30,12 +30,18 @@ class GSolver:
                  mu_right: float = 0.0, obc: bool = True, precision: int = N.BT_FP64, split_slices: int = 0,
                  symmetrize: bool = True, decim_tol: float = 1e-14, decim_maxit: int = 100, stream=None,
                  hbm_budget_bytes: int = 0, device: str = "cuda", obc_memo: bool = False, memo_nfpi: int = 0,
-                 memo_capacity: int = 0, split_scope: int = 0):
+                 memo_capacity: int = 0, split_scope: int = 0, graph: bool = False):
         self.nb, self.bs, self.max_energies = nb, bs, max_energies
         self.device = device
         self.desc = make_desc(nb, bs, max_energies, N.BT_SYS_G, precision, split_slices, symmetrize, obc, eta, kT,
                               mu_left, mu_right, decim_tol, decim_maxit, hbm_budget_bytes, obc_memo, memo_nfpi,
-                              memo_capacity, split_scope)
+                              memo_capacity, split_scope, graph)
+        self._own_stream = None
+        if graph and stream is None:
+            import torch
+            stream = torch.cuda.Stream()  # stream capture needs a non-default stream
+            self._own_stream = stream
+        self.stream = stream
         self.ctx = bt_selinv_create(self.desc, stream)
         self.H = self.S = self.sigR = self.sigL = self.sigG = None
 
@@ -85,8 +91,14 @@ class GSolver:
         if outs is None:
             outs, status = self.allocate_outputs(len(energies))
         sR, sL, sG = (self.sigR, self.sigL, self.sigG) if sig_range is None else self.energy_slice(*sig_range)
+        if self._own_stream is not None:
+            # the private stream of graph mode is ordered after, and before, the caller's stream
+            import torch
+            self._own_stream.wait_stream(torch.cuda.current_stream())
         bt_selinv_solve(self.ctx, self.H, self.S, sR, sL, sG, energies, outs.get("R"), outs.get("L"),
                         outs.get("G"), status)
+        if self._own_stream is not None:
+            torch.cuda.current_stream().wait_stream(self._own_stream)
         return outs, status
 
     def stats(self):

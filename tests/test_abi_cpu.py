@@ -74,6 +74,19 @@ def test_create_rejects_bad_descriptors_on_host(lib, kw, needle):
     assert needle in str(ei.value)
 
 
+def test_graph_mode_validation_on_host(lib):
+    import paper_2508_19138_gb300 as pkg
+    d = pkg.make_desc(4, 8, 4, obc=True, obc_memo=True, graph=True)
+    with pytest.raises(pkg.BTError) as ei:
+        pkg.bt_selinv_create(d, stream=0)
+    assert ei.value.status == pkg.BT_ERR_INVALID_ARG and "exclusive" in str(ei.value)
+    d = pkg.make_desc(4, 8, 4)
+    d.graph = 2
+    with pytest.raises(pkg.BTError) as ei:
+        pkg.bt_selinv_create(d, stream=0)
+    assert "graph" in str(ei.value)
+
+
 def test_budget_rejection_on_host(lib):
     import paper_2508_19138_gb300 as pkg
     d = pkg.make_desc(40, 416, 64, hbm_budget_bytes=1 << 20)
