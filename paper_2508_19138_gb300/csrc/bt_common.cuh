@@ -70,6 +70,12 @@ struct Operand {
 bt_status zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A, Operand B, zd beta,
                 zd* C, int ldc, long long strideC, int batch, const int* active);
 
+// C = alpha op(A) op(B) + beta C for a square n x n C whose exact value is anti-Hermitian
+// (alpha real, beta C anti-Hermitian, op(A) op(B) anti-Hermitian): the tiles on and above the
+// diagonal are computed, the others written as -(upper)^H.  Complex alpha: plain zgemm.
+bt_status zgemm_antiherm(cudaStream_t st, int n, int k, zd alpha, Operand A, Operand B, zd beta, zd* C, int ldc,
+                         long long strideC, int batch, const int* active);
+
 // Which kernel runs a complex product: FP64 DFMA (slices == 0) or the sliced bf16 tensor-core
 // product with `slices` slices per operand and its workspace.
 struct Engine {
@@ -87,6 +93,9 @@ bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A,
 // C = alpha op(A) op(B) + beta C on the engine's kernel.
 bt_status gemm(const Engine& eng, cudaStream_t st, int m, int n, int k, zd alpha, Operand A, Operand B, zd beta,
                zd* C, int ldc, long long strideC, int batch, const int* active);
+// The anti-Hermitian variant (zgemm_antiherm on the FP64 engine; the sliced engine computes all of C).
+bt_status gemm_antiherm(const Engine& eng, cudaStream_t st, int n, int k, zd alpha, Operand A, Operand B, zd beta,
+                        zd* C, int ldc, long long strideC, int batch, const int* active);
 
 // In-place batched inverse (Gauss-Jordan, partial pivoting).  info[b] |= error code.  The
 // rank-kb updates of the blocked variant run on `eng` (FP64 unless given).

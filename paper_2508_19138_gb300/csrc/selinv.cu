@@ -229,15 +229,21 @@ bt_status set_err(bt_ctx* c, bt_status s, const char* what) {
   return s;
 }
 
-// C = alpha op(A) op(B) + beta C for the chunk (bs x bs blocks)
+// C = alpha op(A) op(B) + beta C for the chunk (bs x bs blocks).  antiherm: the exact result is
+// anti-Hermitian (a lesser / greater sandwich x B x^H with B = -B^H, plus an anti-Hermitian C):
+// with symmetrised outputs (Sec. 4.2) the FP64 engine computes only the blocks' upper half and
+// mirrors it, about half of the product's FP64 work.
 bt_status prod(bt_ctx* c, int Ec, double alpha, const Blk& A, const Blk& B, double beta, zd* C, long long sC,
-               bool allow_split = true) {
+               bool antiherm = false) {
   const int bs = c->d.bs;
   const double a = alpha * A.f * B.f;
   c->flops += 8.0 * bs * (double)bs * bs * Ec;
-  if (allow_split && is_split(c->d))
+  if (is_split(c->d))
     return bt::split_zgemm(c->st, bs, bs, bs, zmake(a, 0.0), opnd(A, bs), opnd(B, bs), zmake(beta, 0.0), C, bs, sC,
                            Ec, slices_of(c->d), c->split_ws, c->split_bytes, nullptr);
+  if (antiherm && c->d.symmetrize)
+    return bt::zgemm_antiherm(c->st, bs, bs, zmake(a, 0.0), opnd(A, bs), opnd(B, bs), zmake(beta, 0.0), C, bs, sC, Ec,
+                              nullptr);
   return bt::zgemm(c->st, bs, bs, bs, zmake(a, 0.0), opnd(A, bs), opnd(B, bs), zmake(beta, 0.0), C, bs, sC, Ec,
                    nullptr);
 }
@@ -273,7 +279,7 @@ bt_status run_sweep(Sweep& s, int* status) {
       BT_TRY(s.asmB(i, w, Bt, B2));
       if (i > 0) {
         BT_TRY(prod(c, Ec, 1.0, s.Ml(i - 1), X(xLG(w, i - 1), NB2), 0.0, Tq, B2));        // M~_{i,i-1} x^<>_{i-1}
-        BT_TRY(prod(c, Ec, 1.0, X(Tq, B2), flip(s.Ml(i - 1)), 1.0, Bt, B2));              // ... M~_{i,i-1}^H
+        BT_TRY(prod(c, Ec, 1.0, X(Tq, B2), flip(s.Ml(i - 1)), 1.0, Bt, B2, true));        // ... M~_{i,i-1}^H
         if (s.has_boff) {
           Blk bu = s.Bu(i - 1, w);
           if (bu.valid()) {
@@ -283,7 +289,7 @@ bt_status run_sweep(Sweep& s, int* status) {
         }
       }
       BT_TRY(prod(c, Ec, 1.0, X(xR(i), NB2), X(Bt, B2), 0.0, Tq, B2));
-      BT_TRY(prod(c, Ec, 1.0, X(Tq, B2), flip(X(xR(i), NB2)), 0.0, xLG(w, i), NB2));     // x^R (...) x^R^H
+      BT_TRY(prod(c, Ec, 1.0, X(Tq, B2), flip(X(xR(i), NB2)), 0.0, xLG(w, i), NB2, true));  // x^R (...) x^R^H
     }
   }
   // ---------------- backward pass ----------------
@@ -342,7 +348,7 @@ bt_status run_sweep(Sweep& s, int* status) {
       }
       BT_TRY(prod(c, Ec, 1.0, s.Ml(i), X(xLi, NB2), 0.0, Zt, B2));                  // M~_{i+1,i} x^<>_i
       BT_TRY(prod(c, Ec, -1.0, X(XRu, esu), X(Zt, B2), 0.0, Z, B2));                // Z_i
-      BT_TRY(prod(c, Ec, 1.0, X(P, B2), flip(X(U1, B2)), 1.0, xLi, NB2));           // + x M X M^H x^H
+      BT_TRY(prod(c, Ec, 1.0, X(P, B2), flip(X(U1, B2)), 1.0, xLi, NB2, true));     // + x M X M^H x^H
       BT_TRY(bt::add_antiherm(c->st, bs, Ec, xLi, NB2, Z, B2, 1.0));                // + (Z - Z^H)
       if (bu_valid) {
         BT_TRY(prod(c, Ec, -1.0, X(XB[w], B2), flip(X(XRu, esu)), 0.0, Yb, B2));    // Y_i

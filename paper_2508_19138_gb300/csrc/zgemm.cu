@@ -13,6 +13,8 @@
 //    divide the workload block sizes (32, 416 = 13 x 32, 1024) without ragged waste, and the
 //    batch (energies x blocks) gives >= 152 CTAs.
 // Tiles are staged through shared memory with a register prefetch of the next k-slab.
+// zgemm_antiherm: the same kernel over the upper tiles only, for products whose exact result is
+// anti-Hermitian (the lesser / greater sandwiches), the lower tiles written as mirror images.
 #include <atomic>
 
 #include "bt_common.cuh"
@@ -28,14 +30,30 @@ namespace {
 constexpr int BM = 32, BN = 32, BK = 16;
 constexpr int NT = 256;  // 16 x 16 threads, 2 x 2 outputs each
 
-template <int OPA, int OPB>
+// TRI: C (square, n x n) is known to be anti-Hermitian (C_ji = -conj(C_ij)) in exact arithmetic,
+// e.g. the sandwiches x^R B^<> x^R^H of Eq. 9 and 11: only the tiles on and above the diagonal
+// are computed (blockIdx.x runs over them row by row), every tile above the diagonal also
+// writes its mirror image -(tile)^H below it (staged through shared memory so that the
+// transposed store stays coalesced), and the diagonal tiles are made exactly anti-Hermitian.
+// About half of the FP64 work of the product.
+template <int OPA, int OPB, bool TRI>
 __global__ void __launch_bounds__(NT) zgemm_kernel(int m, int n, int k, zd alpha, const zd* __restrict__ A,
                                                    int lda, long long sA, const zd* __restrict__ B, int ldb,
                                                    long long sB, zd beta, zd* __restrict__ C, int ldc,
                                                    long long sC, const int* __restrict__ active) {
   const int bz = blockIdx.z;
   if (active && active[bz] == 0) return;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  int m0, n0;
+  if (TRI) {
+    const int T = (n + BN - 1) / BN;
+    int idx = blockIdx.x, tr = 0;
+    while (idx >= T - tr) { idx -= T - tr; ++tr; }
+    m0 = tr * BM;
+    n0 = (tr + idx) * BN;
+  } else {
+    m0 = blockIdx.y * BM;
+    n0 = blockIdx.x * BN;
+  }
   A += sA * bz;
   B += sB * bz;
   C += sC * bz;
@@ -136,10 +154,11 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(int m, int n, int k, zd alpha
 #pragma unroll
     for (int j = 0; j < 2; ++j) acc[i][j] = zmake(t1[i][j] - t2[i][j], t3[i][j] - t1[i][j] - t2[i][j]);
   const bool beta_zero = (beta.x == 0.0 && beta.y == 0.0);
+  const bool diag_tile = TRI && m0 == n0;  // written below, element by element
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
     int gr = m0 + ty + 16 * i;
-    if (gr >= m) continue;
+    if (gr >= m || diag_tile) continue;
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       int gc = n0 + tx + 16 * j;
@@ -150,6 +169,60 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(int m, int n, int k, zd alpha
       *cp = v;
     }
   }
+  if (TRI) {
+    // Tile above the diagonal: its mirror image C[n0 + c][m0 + r] = -conj(alpha acc[r][c]) +
+    // beta C[n0 + c][m0 + r] (alpha, beta real).  Diagonal tile: its upper triangle as computed,
+    // the strict lower triangle mirrored from it and the diagonal made imaginary, so that the
+    // whole of C comes out exactly anti-Hermitian.  (Mirroring only whole tiles would turn the
+    // Hermitian rounding noise that the operands carry into anti-Hermitian error; with every
+    // output exactly anti-Hermitian no such noise builds up along the sweep.)
+    __shared__ double Mr[TRI ? BN : 1][TRI ? BM + 1 : 1], Mi[TRI ? BN : 1][TRI ? BM + 1 : 1];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const zd v = zmul(alpha, acc[i][j]);
+        if (diag_tile) {
+          Mr[ty + 16 * i][tx + 16 * j] = v.x;
+          Mi[ty + 16 * i][tx + 16 * j] = v.y;
+        } else {
+          Mr[tx + 16 * j][ty + 16 * i] = -v.x;
+          Mi[tx + 16 * j][ty + 16 * i] = v.y;
+        }
+      }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < (BM * BN) / NT; ++s) {
+      const int r = (t >> 5) + (NT / 32) * s, c = t & 31;
+      const int gr = (diag_tile ? m0 : n0) + r, gc = (diag_tile ? n0 : m0) + c;
+      if (gr < m && gc < n) {
+        zd* cp = C + (long long)gr * ldc + gc;
+        zd v;
+        if (!diag_tile || r < c) v = zmake(Mr[r][c], Mi[r][c]);
+        else if (r > c) v = zmake(-Mr[c][r], Mi[c][r]);
+        else v = zmake(0.0, Mi[r][r]);
+        if (!beta_zero) v = zadd(v, zmul(beta, *cp));
+        if (diag_tile && r == c) v.x = 0.0;
+        *cp = v;
+      }
+    }
+  }
+}
+
+template <bool TRI>
+bt_status launch_zgemm(cudaStream_t st, dim3 grid, int m, int n, int k, zd alpha, const Operand& A, const Operand& B,
+                       zd beta, zd* C, int ldc, long long strideC, const int* active) {
+  if (A.op == BT_OP_N && B.op == BT_OP_N)
+    zgemm_kernel<BT_OP_N, BT_OP_N, TRI><<<grid, NT, 0, st>>>(m, n, k, alpha, A.p, A.ld, A.stride, B.p, B.ld, B.stride, beta, C, ldc, strideC, active);
+  else if (A.op == BT_OP_N && B.op == BT_OP_C)
+    zgemm_kernel<BT_OP_N, BT_OP_C, TRI><<<grid, NT, 0, st>>>(m, n, k, alpha, A.p, A.ld, A.stride, B.p, B.ld, B.stride, beta, C, ldc, strideC, active);
+  else if (A.op == BT_OP_C && B.op == BT_OP_N)
+    zgemm_kernel<BT_OP_C, BT_OP_N, TRI><<<grid, NT, 0, st>>>(m, n, k, alpha, A.p, A.ld, A.stride, B.p, B.ld, B.stride, beta, C, ldc, strideC, active);
+  else
+    zgemm_kernel<BT_OP_C, BT_OP_C, TRI><<<grid, NT, 0, st>>>(m, n, k, alpha, A.p, A.ld, A.stride, B.p, B.ld, B.stride, beta, C, ldc, strideC, active);
+  count_launch();
+  BT_CUDA_TRY(cudaGetLastError());
+  return BT_OK;
 }
 
 }  // namespace
@@ -171,17 +244,25 @@ bt_status zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A, Opera
     return BT_OK;
   }
   dim3 grid((n + BN - 1) / BN, (m + BM - 1) / BM, batch);
-  if (A.op == BT_OP_N && B.op == BT_OP_N)
-    zgemm_kernel<BT_OP_N, BT_OP_N><<<grid, NT, 0, st>>>(m, n, k, alpha, A.p, A.ld, A.stride, B.p, B.ld, B.stride, beta, C, ldc, strideC, active);
-  else if (A.op == BT_OP_N && B.op == BT_OP_C)
-    zgemm_kernel<BT_OP_N, BT_OP_C><<<grid, NT, 0, st>>>(m, n, k, alpha, A.p, A.ld, A.stride, B.p, B.ld, B.stride, beta, C, ldc, strideC, active);
-  else if (A.op == BT_OP_C && B.op == BT_OP_N)
-    zgemm_kernel<BT_OP_C, BT_OP_N><<<grid, NT, 0, st>>>(m, n, k, alpha, A.p, A.ld, A.stride, B.p, B.ld, B.stride, beta, C, ldc, strideC, active);
-  else
-    zgemm_kernel<BT_OP_C, BT_OP_C><<<grid, NT, 0, st>>>(m, n, k, alpha, A.p, A.ld, A.stride, B.p, B.ld, B.stride, beta, C, ldc, strideC, active);
-  count_launch();
-  BT_CUDA_TRY(cudaGetLastError());
-  return BT_OK;
+  return launch_zgemm<false>(st, grid, m, n, k, alpha, A, B, beta, C, ldc, strideC, active);
+}
+
+bt_status zgemm_antiherm(cudaStream_t st, int n, int k, zd alpha, Operand A, Operand B, zd beta, zd* C, int ldc,
+                         long long strideC, int batch, const int* active) {
+  if (n < 0 || k < 0 || batch < 0) return BT_ERR_INVALID_ARG;
+  if (n == 0 || batch == 0) return BT_OK;
+  if (alpha.y != 0.0 || batch > 65535) return zgemm(st, n, n, k, alpha, A, B, beta, C, ldc, strideC, batch, active);
+  const int T = (n + BN - 1) / BN;
+  dim3 grid((unsigned)(T * (T + 1) / 2), 1, batch);
+  return launch_zgemm<true>(st, grid, n, n, k, alpha, A, B, beta, C, ldc, strideC, active);
+}
+
+bt_status gemm_antiherm(const Engine& eng, cudaStream_t st, int n, int k, zd alpha, Operand A, Operand B, zd beta,
+                       zd* C, int ldc, long long strideC, int batch, const int* active) {
+  if (eng.slices > 0)
+    return split_zgemm(st, n, n, k, alpha, A, B, beta, C, ldc, strideC, batch, eng.slices, eng.ws, eng.ws_bytes,
+                       active);
+  return zgemm_antiherm(st, n, k, alpha, A, B, beta, C, ldc, strideC, batch, active);
 }
 
 bt_status gemm(const Engine& eng, cudaStream_t st, int m, int n, int k, zd alpha, Operand A, Operand B, zd beta,
