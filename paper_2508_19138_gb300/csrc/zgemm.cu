@@ -27,8 +27,14 @@ long long launches_total() { return g_launches.load(std::memory_order_relaxed); 
 
 namespace {
 
-constexpr int BM = 32, BN = 32, BK = 16;
-constexpr int NT = 256;  // 16 x 16 threads, 2 x 2 outputs each
+constexpr int BK = 16;
+// TILE x TILE output tiles, (TILE/2)^2 threads with 2 x 2 outputs each: 32 (256 threads) for the
+// large blocks, 16 (64 threads) when the 32-tiles would leave SMs idle (small blocks, few energies).
+template <int TILE>
+struct Shape {
+  static constexpr int BM = TILE, BN = TILE, NT = TILE * TILE / 4, H = TILE / 2;
+  static constexpr int EA = BM * BK / NT, EB = BN * BK / NT;  // staged elements per thread
+};
 
 // TRI: C (square, n x n) is known to be anti-Hermitian (C_ji = -conj(C_ij)) in exact arithmetic,
 // e.g. the sandwiches x^R B^<> x^R^H of Eq. 9 and 11: only the tiles on and above the diagonal
@@ -36,11 +42,13 @@ constexpr int NT = 256;  // 16 x 16 threads, 2 x 2 outputs each
 // writes its mirror image -(tile)^H below it (staged through shared memory so that the
 // transposed store stays coalesced), and the diagonal tiles are made exactly anti-Hermitian.
 // About half of the FP64 work of the product.
-template <int OPA, int OPB, bool TRI>
-__global__ void __launch_bounds__(NT) zgemm_kernel(int m, int n, int k, zd alpha, const zd* __restrict__ A,
+template <int OPA, int OPB, bool TRI, int TILE>
+__global__ void __launch_bounds__(Shape<TILE>::NT) zgemm_kernel(int m, int n, int k, zd alpha, const zd* __restrict__ A,
                                                    int lda, long long sA, const zd* __restrict__ B, int ldb,
                                                    long long sB, zd beta, zd* __restrict__ C, int ldc,
                                                    long long sC, const int* __restrict__ active) {
+  constexpr int BM = Shape<TILE>::BM, BN = Shape<TILE>::BN, NT = Shape<TILE>::NT, H = Shape<TILE>::H;
+  constexpr int EA = Shape<TILE>::EA, EB = Shape<TILE>::EB;
   const int bz = blockIdx.z;
   if (active && active[bz] == 0) return;
   int m0, n0;
@@ -61,7 +69,7 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(int m, int n, int k, zd alpha
   __shared__ double Ar[BK][BM + 1], Ai[BK][BM + 1], Ap[BK][BM + 1];
   __shared__ double Br[BK][BN + 1], Bi[BK][BN + 1], Bp[BK][BN + 1];
   const int t = threadIdx.x;
-  const int tx = t & 15, ty = t >> 4;
+  const int tx = t % H, ty = t / H;
 
   double t1[2][2], t2[2][2], t3[2][2];
 #pragma unroll
@@ -69,13 +77,13 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(int m, int n, int k, zd alpha
 #pragma unroll
     for (int j = 0; j < 2; ++j) t1[i][j] = t2[i][j] = t3[i][j] = 0.0;
 
-  zd ra[2], rb[2];  // prefetch registers: 2 elements of A and of B per thread per k-slab
+  zd ra[EA], rb[EB];  // prefetch registers: the thread's elements of A and of B per k-slab
   auto load_a = [&](int k0) {
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < EA; ++s) {
       int e = t + NT * s;
       int r, c;
-      if (OPA == BT_OP_N) { r = e >> 4; c = e & 15; } else { c = e >> 5; r = e & 31; }
+      if (OPA == BT_OP_N) { r = e / BK; c = e % BK; } else { c = e / BM; r = e % BM; }
       int gr = m0 + r, gc = k0 + c;
       zd v = zmake(0.0, 0.0);
       if (gr < m && gc < k) {
@@ -87,10 +95,10 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(int m, int n, int k, zd alpha
   };
   auto load_b = [&](int k0) {
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < EB; ++s) {
       int e = t + NT * s;
       int r, c;
-      if (OPB == BT_OP_N) { r = e >> 5; c = e & 31; } else { c = e >> 4; r = e & 15; }
+      if (OPB == BT_OP_N) { r = e / BN; c = e % BN; } else { c = e / BK; r = e % BK; }
       int gr = k0 + r, gc = n0 + c;
       zd v = zmake(0.0, 0.0);
       if (gr < k && gc < n) {
@@ -102,14 +110,19 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(int m, int n, int k, zd alpha
   };
   auto store_tiles = [&]() {
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < EA; ++s) {
       int e = t + NT * s;
       int r, c;
-      if (OPA == BT_OP_N) { r = e >> 4; c = e & 15; } else { c = e >> 5; r = e & 31; }
+      if (OPA == BT_OP_N) { r = e / BK; c = e % BK; } else { c = e / BM; r = e % BM; }
       Ar[c][r] = ra[s].x;
       Ai[c][r] = ra[s].y;
       Ap[c][r] = ra[s].x + ra[s].y;
-      if (OPB == BT_OP_N) { r = e >> 5; c = e & 31; } else { c = e >> 4; r = e & 15; }
+    }
+#pragma unroll
+    for (int s = 0; s < EB; ++s) {
+      int e = t + NT * s;
+      int r, c;
+      if (OPB == BT_OP_N) { r = e / BN; c = e % BN; } else { c = e / BK; r = e % BK; }
       Br[r][c] = rb[s].x;
       Bi[r][c] = rb[s].y;
       Bp[r][c] = rb[s].x + rb[s].y;
@@ -131,12 +144,12 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(int m, int n, int k, zd alpha
       double ar[2], ai[2], ap[2], br[2], bi[2], bp[2];
 #pragma unroll
       for (int i = 0; i < 2; ++i) {
-        ar[i] = Ar[kk][ty + 16 * i];
-        ai[i] = Ai[kk][ty + 16 * i];
-        ap[i] = Ap[kk][ty + 16 * i];
-        br[i] = Br[kk][tx + 16 * i];
-        bi[i] = Bi[kk][tx + 16 * i];
-        bp[i] = Bp[kk][tx + 16 * i];
+        ar[i] = Ar[kk][ty + H * i];
+        ai[i] = Ai[kk][ty + H * i];
+        ap[i] = Ap[kk][ty + H * i];
+        br[i] = Br[kk][tx + H * i];
+        bi[i] = Bi[kk][tx + H * i];
+        bp[i] = Bp[kk][tx + H * i];
       }
 #pragma unroll
       for (int i = 0; i < 2; ++i)
@@ -157,11 +170,11 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(int m, int n, int k, zd alpha
   const bool diag_tile = TRI && m0 == n0;  // written below, element by element
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
-    int gr = m0 + ty + 16 * i;
+    int gr = m0 + ty + H * i;
     if (gr >= m || diag_tile) continue;
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-      int gc = n0 + tx + 16 * j;
+      int gc = n0 + tx + H * j;
       if (gc >= n) continue;
       zd* cp = C + (long long)gr * ldc + gc;
       zd v = zmul(alpha, acc[i][j]);
@@ -183,17 +196,17 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(int m, int n, int k, zd alpha
       for (int j = 0; j < 2; ++j) {
         const zd v = zmul(alpha, acc[i][j]);
         if (diag_tile) {
-          Mr[ty + 16 * i][tx + 16 * j] = v.x;
-          Mi[ty + 16 * i][tx + 16 * j] = v.y;
+          Mr[ty + H * i][tx + H * j] = v.x;
+          Mi[ty + H * i][tx + H * j] = v.y;
         } else {
-          Mr[tx + 16 * j][ty + 16 * i] = -v.x;
-          Mi[tx + 16 * j][ty + 16 * i] = v.y;
+          Mr[tx + H * j][ty + H * i] = -v.x;
+          Mi[tx + H * j][ty + H * i] = v.y;
         }
       }
     __syncthreads();
 #pragma unroll
     for (int s = 0; s < (BM * BN) / NT; ++s) {
-      const int r = (t >> 5) + (NT / 32) * s, c = t & 31;
+      const int r = t / BN + (NT / BN) * s, c = t % BN;
       const int gr = (diag_tile ? m0 : n0) + r, gc = (diag_tile ? n0 : m0) + c;
       if (gr < m && gc < n) {
         zd* cp = C + (long long)gr * ldc + gc;
@@ -209,20 +222,50 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(int m, int n, int k, zd alpha
   }
 }
 
-template <bool TRI>
-bt_status launch_zgemm(cudaStream_t st, dim3 grid, int m, int n, int k, zd alpha, const Operand& A, const Operand& B,
-                       zd beta, zd* C, int ldc, long long strideC, const int* active) {
+template <bool TRI, int TILE>
+bt_status launch_tile(cudaStream_t st, dim3 grid, int m, int n, int k, zd alpha, const Operand& A, const Operand& B,
+                      zd beta, zd* C, int ldc, long long strideC, const int* active) {
+  constexpr int NT = Shape<TILE>::NT;
   if (A.op == BT_OP_N && B.op == BT_OP_N)
-    zgemm_kernel<BT_OP_N, BT_OP_N, TRI><<<grid, NT, 0, st>>>(m, n, k, alpha, A.p, A.ld, A.stride, B.p, B.ld, B.stride, beta, C, ldc, strideC, active);
+    zgemm_kernel<BT_OP_N, BT_OP_N, TRI, TILE><<<grid, NT, 0, st>>>(m, n, k, alpha, A.p, A.ld, A.stride, B.p, B.ld, B.stride, beta, C, ldc, strideC, active);
   else if (A.op == BT_OP_N && B.op == BT_OP_C)
-    zgemm_kernel<BT_OP_N, BT_OP_C, TRI><<<grid, NT, 0, st>>>(m, n, k, alpha, A.p, A.ld, A.stride, B.p, B.ld, B.stride, beta, C, ldc, strideC, active);
+    zgemm_kernel<BT_OP_N, BT_OP_C, TRI, TILE><<<grid, NT, 0, st>>>(m, n, k, alpha, A.p, A.ld, A.stride, B.p, B.ld, B.stride, beta, C, ldc, strideC, active);
   else if (A.op == BT_OP_C && B.op == BT_OP_N)
-    zgemm_kernel<BT_OP_C, BT_OP_N, TRI><<<grid, NT, 0, st>>>(m, n, k, alpha, A.p, A.ld, A.stride, B.p, B.ld, B.stride, beta, C, ldc, strideC, active);
+    zgemm_kernel<BT_OP_C, BT_OP_N, TRI, TILE><<<grid, NT, 0, st>>>(m, n, k, alpha, A.p, A.ld, A.stride, B.p, B.ld, B.stride, beta, C, ldc, strideC, active);
   else
-    zgemm_kernel<BT_OP_C, BT_OP_C, TRI><<<grid, NT, 0, st>>>(m, n, k, alpha, A.p, A.ld, A.stride, B.p, B.ld, B.stride, beta, C, ldc, strideC, active);
+    zgemm_kernel<BT_OP_C, BT_OP_C, TRI, TILE><<<grid, NT, 0, st>>>(m, n, k, alpha, A.p, A.ld, A.stride, B.p, B.ld, B.stride, beta, C, ldc, strideC, active);
   count_launch();
   BT_CUDA_TRY(cudaGetLastError());
   return BT_OK;
+}
+
+int sm_count() {
+  static std::atomic<int> cached{0};
+  int v = cached.load(std::memory_order_relaxed);
+  if (v == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      v = 152;
+    cached.store(v, std::memory_order_relaxed);
+  }
+  return v;
+}
+
+// Tiles of 32 unless they would leave SMs idle (fewer than two tiles per SM), then 16.
+template <bool TRI>
+bt_status launch_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, const Operand& A, const Operand& B, zd beta,
+                       zd* C, int ldc, long long strideC, int batch, const int* active) {
+  auto tiles = [&](int tl) {
+    const long long tm = (m + tl - 1) / tl, tn = (n + tl - 1) / tl;
+    return TRI ? tn * (tn + 1) / 2 : tm * tn;
+  };
+  if (tiles(32) * batch < 2LL * sm_count()) {
+    const long long t16 = tiles(16);
+    dim3 grid = TRI ? dim3((unsigned)t16, 1, batch) : dim3((n + 15) / 16, (m + 15) / 16, batch);
+    return launch_tile<TRI, 16>(st, grid, m, n, k, alpha, A, B, beta, C, ldc, strideC, active);
+  }
+  dim3 grid = TRI ? dim3((unsigned)tiles(32), 1, batch) : dim3((n + 31) / 32, (m + 31) / 32, batch);
+  return launch_tile<TRI, 32>(st, grid, m, n, k, alpha, A, B, beta, C, ldc, strideC, active);
 }
 
 }  // namespace
@@ -243,8 +286,7 @@ bt_status zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A, Opera
     }
     return BT_OK;
   }
-  dim3 grid((n + BN - 1) / BN, (m + BM - 1) / BM, batch);
-  return launch_zgemm<false>(st, grid, m, n, k, alpha, A, B, beta, C, ldc, strideC, active);
+  return launch_zgemm<false>(st, m, n, k, alpha, A, B, beta, C, ldc, strideC, batch, active);
 }
 
 bt_status zgemm_antiherm(cudaStream_t st, int n, int k, zd alpha, Operand A, Operand B, zd beta, zd* C, int ldc,
@@ -252,9 +294,7 @@ bt_status zgemm_antiherm(cudaStream_t st, int n, int k, zd alpha, Operand A, Ope
   if (n < 0 || k < 0 || batch < 0) return BT_ERR_INVALID_ARG;
   if (n == 0 || batch == 0) return BT_OK;
   if (alpha.y != 0.0 || batch > 65535) return zgemm(st, n, n, k, alpha, A, B, beta, C, ldc, strideC, batch, active);
-  const int T = (n + BN - 1) / BN;
-  dim3 grid((unsigned)(T * (T + 1) / 2), 1, batch);
-  return launch_zgemm<true>(st, grid, n, n, k, alpha, A, B, beta, C, ldc, strideC, active);
+  return launch_zgemm<true>(st, n, n, k, alpha, A, B, beta, C, ldc, strideC, batch, active);
 }
 
 bt_status gemm_antiherm(const Engine& eng, cudaStream_t st, int n, int k, zd alpha, Operand A, Operand B, zd beta,

@@ -194,19 +194,12 @@ __global__ void __launch_bounds__(NT) zinv_small_kernel(int n, zd* __restrict__ 
 // search of column j runs over the rows whose current position is >= j, ties going to the
 // smaller position, which selects the pivot sequence of elimination with physical exchanges.
 // Per column: warp 0 of each CTA publishes its best candidate (key, position, row and the row's
-// kb entries) in a buffer of parity j & 1; after the cluster barrier every CTA reads all
+// kb entries) in a buffer of parity j & 1, one cluster barrier, then every CTA reads all
 // candidates and the winning row through distributed shared memory and updates its own rows.
-// The barrier is split (arrive / wait) and overlapped with the FP64 work by one column of
-// look-ahead: once the pivot row of column j is known, column j + 1 of the local rows is updated
-// first, warp 0 publishes the candidate of column j + 1 (its row updated in registers) and
-// arrives, and the rank-1 update of the other columns runs while the other CTAs catch up.
 // A buffer of parity j & 1 is rewritten two columns later, after the barrier of column j + 1,
 // which no CTA passes before every CTA has finished reading it.  At the end each CTA writes its
 // rows to their final positions.  perm[] records the exchanges as the LAPACK-style sequence
 // (row j swapped with row perm[j], in order), as the rest of the blocked inverse expects.
-__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
-__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
-
 template <int CL>
 __global__ void __launch_bounds__(NT) gj_panel_cluster_kernel(int n, int k0, int kb, zd* __restrict__ A,
                                                               long long sA, int* __restrict__ perm_all, int* info,
@@ -240,45 +233,33 @@ __global__ void __launch_bounds__(NT) gj_panel_cluster_kernel(int n, int k0, int
     P[r * ld + c] = Ag[(long long)(r0 + r) * n + k0 + c];
   }
   __syncthreads();
-
-  // warp 0: best local candidate of column jj among rows at positions >= k0 + jj (its row index,
-  // -1 if none), published as key / position / row in slot par
-  auto search = [&](int jj, int par) {
-    const int j = k0 + jj;
-    unsigned long long bk = 0;
-    int bp = 0x7fffffff, br = -1;
-    for (int r = lane; r < rows; r += 32) {
-      const int pos = pos_of[r0 + r];
-      if (pos < j) continue;
-      const unsigned long long k = pivot_key(P[r * ld + jj]);
-      if (br < 0 || cand_better(k, pos, bk, bp)) { bk = k; bp = pos; br = r0 + r; }
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, off);
-      const int op = __shfl_xor_sync(0xffffffffu, bp, off);
-      const int orr = __shfl_xor_sync(0xffffffffu, br, off);
-      if (orr >= 0 && (br < 0 || cand_better(ok, op, bk, bp))) { bk = ok; bp = op; br = orr; }
-    }
-    if (lane == 0) { cand_key[par] = bk; cand_pos[par] = br < 0 ? 0x7fffffff : bp; cand_row[par] = br; }
-    return br;
-  };
-
-  // prologue: candidates of column 0 straight from the loaded panel
-  if (warp == 0) {
-    const int br = search(0, 0);
-    if (br >= 0)
-      for (int c = lane; c < kb; c += 32) pub[c] = P[(br - r0) * ld + c];
-  }
-  cluster_arrive();
-
   // row update layout: 4 threads per row, columns c = sub, sub + 4, ...
   const int sub = tid & 3;
   const int rows_per_pass = blockDim.x >> 2;
   for (int jj = 0; jj < kb; ++jj) {
     const int j = k0 + jj, par = jj & 1;
-    const bool ahead = jj + 1 < kb;
-    cluster_wait();  // candidates of column j visible cluster-wide
+    if (warp == 0) {
+      // best local candidate among rows at positions >= j
+      unsigned long long bk = 0;
+      int bp = 0x7fffffff, br = -1;
+      for (int r = lane; r < rows; r += 32) {
+        const int pos = pos_of[r0 + r];
+        if (pos < j) continue;
+        const unsigned long long k = pivot_key(P[r * ld + jj]);
+        if (br < 0 || cand_better(k, pos, bk, bp)) { bk = k; bp = pos; br = r0 + r; }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, off);
+        const int op = __shfl_xor_sync(0xffffffffu, bp, off);
+        const int orr = __shfl_xor_sync(0xffffffffu, br, off);
+        if (orr >= 0 && (br < 0 || cand_better(ok, op, bk, bp))) { bk = ok; bp = op; br = orr; }
+      }
+      if (lane == 0) { cand_key[par] = bk; cand_pos[par] = br < 0 ? 0x7fffffff : bp; cand_row[par] = br; }
+      if (br >= 0)
+        for (int c = lane; c < kb; c += 32) pub[par * kb + c] = P[(br - r0) * ld + c];
+    }
+    cluster.sync();  // candidates of column j visible cluster-wide
     if (warp == 0) {
       // one round of remote reads: every candidate's key and every candidate's row (lane c
       // holds entry c of all CL rows); the winner's row is then selected locally
@@ -329,56 +310,6 @@ __global__ void __launch_bounds__(NT) gj_panel_cluster_kernel(int n, int k0, int
     __syncthreads();
     const zd ip = s_ip;
     const int q = s_q;
-    zd cand_v = zmake(0.0, 0.0), cand_f = zmake(0.0, 0.0);
-    int cand_r = -1;
-    if (ahead) {
-      // look-ahead: column jj + 1 of the local rows (the next pivot search needs only it)
-      const zd g = rowj[jj + 1];
-      for (int r = tid; r < rows; r += blockDim.x) {
-        if (r0 + r == q) {
-          P[r * ld + jj + 1] = g;
-        } else {
-          const zd f = P[r * ld + jj];
-          zd a = P[r * ld + jj + 1];
-          a.x = fma(-f.x, g.x, a.x);
-          a.x = fma(f.y, g.y, a.x);
-          a.y = fma(-f.x, g.y, a.y);
-          a.y = fma(-f.y, g.x, a.y);
-          P[r * ld + jj + 1] = a;
-        }
-      }
-      __syncthreads();
-      if (warp == 0) {
-        // candidate of column jj + 1; its row is read here, before the rank-1 update below
-        cand_r = search(jj + 1, par ^ 1);
-        if (cand_r >= 0 && lane < kb) {
-          cand_v = P[(cand_r - r0) * ld + lane];
-          cand_f = P[(cand_r - r0) * ld + jj];
-        }
-      }
-    }
-    __syncthreads();
-    if (ahead) {
-      if (warp == 0 && cand_r >= 0 && lane < kb) {
-        // the candidate row after the update of column jj (never the pivot row: that one now
-        // sits at position j < j + 1)
-        const int c = lane;
-        zd v = cand_v;
-        if (c == jj) {
-          v = zmul(zmake(-cand_f.x, -cand_f.y), ip);
-        } else if (c != jj + 1) {
-          const zd g = rowj[c];
-          v.x = fma(-cand_f.x, g.x, v.x);
-          v.x = fma(cand_f.y, g.y, v.x);
-          v.y = fma(-cand_f.x, g.y, v.y);
-          v.y = fma(-cand_f.y, g.x, v.y);
-        }
-        pub[(par ^ 1) * kb + c] = v;
-      }
-      __syncwarp();
-      cluster_arrive();  // publishes the candidate of column jj + 1 (release)
-    }
-    // rank-1 update of column jj on the local rows (column jj + 1 was done above)
     for (int rb = 0; rb < rows; rb += rows_per_pass) {  // uniform trip count (the __syncwarp below)
       const int r = rb + (tid >> 2);
       const bool act = r < rows;
@@ -386,13 +317,12 @@ __global__ void __launch_bounds__(NT) gj_panel_cluster_kernel(int n, int k0, int
       __syncwarp();
       if (act) {
         if (r0 + r == q) {
-          for (int c = sub; c < kb; c += 4)
-            if (!ahead || c != jj + 1) P[r * ld + c] = rowj[c];
+          for (int c = sub; c < kb; c += 4) P[r * ld + c] = rowj[c];
         } else {
           for (int c = sub; c < kb; c += 4) {
             if (c == jj) {
               P[r * ld + c] = zmul(zmake(-f.x, -f.y), ip);
-            } else if (!ahead || c != jj + 1) {
+            } else {
               zd a = P[r * ld + c];
               const zd g = rowj[c];
               a.x = fma(-f.x, g.x, a.x);
@@ -405,7 +335,6 @@ __global__ void __launch_bounds__(NT) gj_panel_cluster_kernel(int n, int k0, int
         }
       }
     }
-    if (!ahead) cluster_arrive();  // last column: the arrival that the final wait completes
     __syncthreads();
   }
   // rows to their final positions (pos_of is a permutation: disjoint destinations)
@@ -414,7 +343,7 @@ __global__ void __launch_bounds__(NT) gj_panel_cluster_kernel(int n, int k0, int
     Ag[(long long)pos_of[r0 + r] * n + k0 + c] = P[r * ld + c];
   }
   if (rank == 0 && tid == 0 && s_code && info && info[b] == 0) info[b] = s_code;
-  cluster_wait();  // no CTA leaves while another may still read its shared memory
+  cluster.sync();  // no CTA leaves while another may still read its shared memory
 }
 
 constexpr int kPanelCluster = 8;  // largest cluster (portable size)

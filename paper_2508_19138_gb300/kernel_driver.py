@@ -3,6 +3,7 @@
     python -m paper_2508_19138_gb300.kernel_driver --kernel zgemm --bs 416 --batch 32 --reps 3
     python -m paper_2508_19138_gb300.kernel_driver --kernel split --bs 416 --batch 32 --slices 6
     python -m paper_2508_19138_gb300.kernel_driver --kernel zinv --bs 416 --batch 32
+    python -m paper_2508_19138_gb300.kernel_driver --kernel cublas --bs 416 --batch 16   # library reference
 
 Inputs are random complex128 blocks already on the device; each kernel is launched `--reps`
 times on the current stream and its mean time is printed (CUDA events)."""
@@ -17,13 +18,15 @@ def main():
 
     import paper_2508_19138_gb300 as pkg
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kernel", choices=["zgemm", "split", "zinv"], required=True)
+    ap.add_argument("--kernel", choices=["zgemm", "split", "zinv", "cublas"], required=True)
     ap.add_argument("--bs", type=int, default=416)
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--slices", type=int, default=6)
     ap.add_argument("--k", type=int, default=0, help="inner dimension of the products (default: --bs)")
     a = ap.parse_args()
+    if a.kernel == "cublas":
+        return cublas_reference(a)
     pkg.library()
     b, n = a.batch, a.bs
     kk = a.k if a.k > 0 and a.kernel != "zinv" else n
@@ -62,6 +65,29 @@ def main():
     flops = 8.0 * n * n * kk * b
     print(json.dumps({"kernel": a.kernel, "bs": n, "k": kk, "batch": b, "ms": ms, "fp64_eq_tflops": flops / ms / 1e9,
                       "slices": a.slices if a.kernel == "split" else None}))
+
+
+def cublas_reference(a):
+    """Library FP64 rates for comparison (not this library's kernels): cuBLAS DGEMM and ZGEMM
+    through torch.matmul, batched over --batch matrices of --bs, mean of --reps after a warm-up."""
+    import torch
+    n, b = a.bs, a.batch
+    out = {"kernel": "cublas", "bs": n, "batch": b}
+    for name, dt, flop in (("dgemm", torch.float64, 2.0), ("zgemm", torch.complex128, 8.0)):
+        x = torch.randn(b, n, n, dtype=dt, device="cuda")
+        y = torch.randn(b, n, n, dtype=dt, device="cuda")
+        torch.matmul(x, y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(a.reps):
+            torch.matmul(x, y)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / a.reps
+        out[name + "_ms"] = ms
+        out[name + "_tflops"] = flop * n ** 3 * b / ms / 1e9
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":
