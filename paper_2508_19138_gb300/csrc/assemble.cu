@@ -100,6 +100,26 @@ __global__ void add_antiherm_kernel(int bs, zd* __restrict__ X, long long sX, co
   }
 }
 
+// X <- (X - X^H) / 2 in place: each pair (r, c), (c, r) with r <= c handled by one thread, so the
+// result is exactly anti-Hermitian (diagonal purely imaginary).
+__global__ void antiherm_project_kernel(int bs, zd* __restrict__ X, long long sX) {
+  const int e = blockIdx.y;
+  const long long bs2 = (long long)bs * bs;
+  zd* x = X + sX * e;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < bs2; i += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(i / bs), c = (int)(i - (long long)r * bs);
+    if (r > c) continue;
+    if (r == c) {
+      x[i].x = 0.0;
+      continue;
+    }
+    const long long j = (long long)c * bs + r;
+    const zd u = zscale(zsub(x[i], zconj(x[j])), 0.5);
+    x[i] = u;
+    x[j] = zmake(-u.x, u.y);
+  }
+}
+
 // out = alpha * x  (+ beta * out unless beta == 0)
 __global__ void axpby_kernel(long long n, double alpha, const zd* __restrict__ x, long long sx, double beta,
                              zd* __restrict__ out, long long so) {
@@ -208,6 +228,12 @@ bt_status obc_lesser_greater(cudaStream_t st, int bs, int E, const zd* sig, cons
                              zd* outL, zd* outG) {
   if (E <= 0) return BT_OK;
   obc_lg_kernel<<<grid_for((long long)bs * bs, 2 * E), 256, 0, st>>>(bs, E, sig, fL, fR, outL, outG); count_launch();
+  BT_CUDA_TRY(cudaGetLastError());
+  return BT_OK;
+}
+
+bt_status antiherm_project(cudaStream_t st, int bs, int batch, zd* X, long long sX) {
+  antiherm_project_kernel<<<grid_for((long long)bs * bs, batch), 256, 0, st>>>(bs, X, sX); count_launch();
   BT_CUDA_TRY(cudaGetLastError());
   return BT_OK;
 }

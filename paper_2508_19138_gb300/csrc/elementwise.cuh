@@ -52,6 +52,8 @@ bt_status assemble_b(cudaStream_t st, int bs, int batch, const BBlockArgs& a);
 bt_status obc_lesser_greater(cudaStream_t st, int bs, int E, const zd* sig, const double* fL, const double* fR,
                              zd* outL, zd* outG);
 bt_status add_antiherm(cudaStream_t st, int bs, int batch, zd* X, long long sX, const zd* Y, long long sY, double sgn);
+// X <- (X - X^H) / 2 per bs x bs block (exactly anti-Hermitian result)
+bt_status antiherm_project(cudaStream_t st, int bs, int batch, zd* X, long long sX);
 bt_status axpby(cudaStream_t st, long long n, int batch, double alpha, const zd* x, long long sx, double beta, zd* out,
                 long long so);
 bt_status write_blocks(cudaStream_t st, int bs, int nblk, int batch, const zd* src, long long s_blk, long long s_e,

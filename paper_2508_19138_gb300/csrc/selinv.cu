@@ -231,16 +231,24 @@ bt_status set_err(bt_ctx* c, bt_status s, const char* what) {
 
 // C = alpha op(A) op(B) + beta C for the chunk (bs x bs blocks).  antiherm: the exact result is
 // anti-Hermitian (a lesser / greater sandwich x B x^H with B = -B^H, plus an anti-Hermitian C):
-// with symmetrised outputs (Sec. 4.2) the FP64 engine computes only the blocks' upper half and
-// mirrors it, about half of the product's FP64 work.
+// with symmetrised outputs (Sec. 4.2) the result is made exactly anti-Hermitian — the FP64 engine
+// computes only the blocks' upper half and mirrors it (about half of the product's FP64 work),
+// the sliced engine projects its full result.
+// `units`: block products of the paper's formulation that this product stands for (the model
+// flop count is 8 b^3 per such product, however the kernels compute it).
 bt_status prod(bt_ctx* c, int Ec, double alpha, const Blk& A, const Blk& B, double beta, zd* C, long long sC,
-               bool antiherm = false) {
+               bool antiherm = false, double units = 1.0) {
   const int bs = c->d.bs;
   const double a = alpha * A.f * B.f;
-  c->flops += 8.0 * bs * (double)bs * bs * Ec;
-  if (is_split(c->d))
-    return bt::split_zgemm(c->st, bs, bs, bs, zmake(a, 0.0), opnd(A, bs), opnd(B, bs), zmake(beta, 0.0), C, bs, sC,
-                           Ec, slices_of(c->d), c->split_ws, c->split_bytes, nullptr);
+  c->flops += units * 8.0 * bs * (double)bs * bs * Ec;
+  if (is_split(c->d)) {
+    BT_TRY(bt::split_zgemm(c->st, bs, bs, bs, zmake(a, 0.0), opnd(A, bs), opnd(B, bs), zmake(beta, 0.0), C, bs, sC,
+                           Ec, slices_of(c->d), c->split_ws, c->split_bytes, nullptr));
+    // the sliced product computes every entry; its result is projected onto the anti-Hermitian
+    // matrices so that, as on the FP64 engine, the sandwiches come out exactly anti-Hermitian
+    if (antiherm && c->d.symmetrize) return bt::antiherm_project(c->st, bs, Ec, C, sC);
+    return BT_OK;
+  }
   if (antiherm && c->d.symmetrize)
     return bt::zgemm_antiherm(c->st, bs, bs, zmake(a, 0.0), opnd(A, bs), opnd(B, bs), zmake(beta, 0.0), C, bs, sC, Ec,
                               nullptr);
@@ -339,15 +347,26 @@ bt_status run_sweep(Sweep& s, int* status) {
       zd* oU = w == 0 ? s.oLu : s.oGu;
       const bool bu_valid = s.has_boff && s.Bu(i, w).valid();
       BT_TRY(prod(c, Ec, 1.0, X(U1, B2), X(XLn, NB2), 0.0, P, B2));                 // x^R M X^<>_{i+1}
+      // With exactly anti-Hermitian x^<>_i (symmetrised outputs: the sandwiches above are computed
+      // so), Z_i = -X^R_{i,i+1} M~_{i+1,i} x^<>_i = U1 V1 x^<>_i = U1 D^H with
+      // D = -x^<>_i V1^H, the first term of X^<>_{i,i+1}: one product instead of two.
+      const bool z_from_d = c->d.symmetrize != 0;
+      zd* d = oU ? oU + i * B2 : Zt;
+      const long long des = oU ? s.oes_u : B2;
+      if (oU || z_from_d) {
+        BT_TRY(prod(c, Ec, -1.0, X(xLi, NB2), flip(X(V1, B2)), 0.0, d, des, false,    // D = - x^<> (X^R M)^H
+                    oU ? 1.0 : 0.0));
+        if (z_from_d) BT_TRY(prod(c, Ec, 1.0, X(U1, B2), flip(X(d, des)), 0.0, Z, B2, false, 2.0));  // Z_i
+      }
       if (oU) {
-        zd* d = oU + i * B2;
-        BT_TRY(prod(c, Ec, -1.0, X(xLi, NB2), flip(X(V1, B2)), 0.0, d, s.oes_u));  // - x^<> (X^R M)^H
         BT_TRY(bt::axpby(c->st, B2, Ec, -1.0, P, B2, 1.0, d, s.oes_u));             // - x^R M X^<>
         if (bu_valid)
           BT_TRY(prod(c, Ec, 1.0, X(XB[w], B2), flip(X(XRn, NB2)), 1.0, d, s.oes_u));  // + x^R B X^R^H
       }
-      BT_TRY(prod(c, Ec, 1.0, s.Ml(i), X(xLi, NB2), 0.0, Zt, B2));                  // M~_{i+1,i} x^<>_i
-      BT_TRY(prod(c, Ec, -1.0, X(XRu, esu), X(Zt, B2), 0.0, Z, B2));                // Z_i
+      if (!z_from_d) {
+        BT_TRY(prod(c, Ec, 1.0, s.Ml(i), X(xLi, NB2), 0.0, Zt, B2));                // M~_{i+1,i} x^<>_i
+        BT_TRY(prod(c, Ec, -1.0, X(XRu, esu), X(Zt, B2), 0.0, Z, B2));              // Z_i
+      }
       BT_TRY(prod(c, Ec, 1.0, X(P, B2), flip(X(U1, B2)), 1.0, xLi, NB2, true));     // + x M X M^H x^H
       BT_TRY(bt::add_antiherm(c->st, bs, Ec, xLi, NB2, Z, B2, 1.0));                // + (Z - Z^H)
       if (bu_valid) {
@@ -888,6 +907,9 @@ bt_status solve_chunk_w(bt_ctx* c, const bt_bt* V, const bt_bt* PR, const bt_bt*
       BT_TRY(prod(c, Ec, 1.0, W(c->Td + i * B2, NB2), Vh(i, i), 0.0, bd, NB2));
       if (i > 0) BT_TRY(prod(c, Ec, 1.0, W(c->Tl + (i - 1) * B2, N1B2), Vh(i, i - 1), 1.0, bd, NB2));
       if (i + 1 < N) BT_TRY(prod(c, Ec, 1.0, W(c->Tu + i * B2, N1B2), Vh(i, i + 1), 1.0, bd, NB2));
+      // B^<>_ii is anti-Hermitian as a sum of three products: made exactly so (Sec. 4.2) before the
+      // sweep's anti-Hermitian products take it as an operand
+      if (c->d.symmetrize) BT_TRY(bt::antiherm_project(c->st, bs, Ec, bd, NB2));
       if (i + 1 < N) {
         zd* bu = Bu[w] + i * B2;
         BT_TRY(prod(c, Ec, 1.0, W(c->Td + i * B2, NB2), Vh(i + 1, i), 0.0, bu, N1B2));

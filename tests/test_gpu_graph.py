@@ -136,3 +136,36 @@ def test_graph_w_system():
     for a, b in zip(got[False], got[True]):
         for x, y in zip(a, b):
             assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("precision,scope", [(0, 0), (1, 1)])
+def test_graph_wide_blocks_staged_sigma(precision, scope):
+    """b = 200: cluster-parallel inversion panels inside the captured decimation loop; scattering
+    self-energies given per energy and passed as energy slices, which graph mode stages into
+    fixed buffers so that every batch replays the same graph.  Bitwise equal to direct launches."""
+    import torch
+    from paper_2508_19138_gb300.highlevel import GSolver
+    s = synthetic.nanoribbon(nb=3, n_puc=2, puc=100, n_energies=6)
+    got = {}
+    for graph in (False, True):
+        stream = torch.cuda.Stream()
+        solver = GSolver(s.nb, s.bs, 3, s.eta, s.kT, s.mu_left, s.mu_right, obc=True, precision=precision,
+                         split_scope=scope, stream=stream, graph=graph)
+        with torch.cuda.stream(stream):
+            solver.set_inputs(s.H_diag, s.H_upper, s.sigR_diag, s.sigL_diag, s.sigG_diag)
+            outs, status = solver.allocate_outputs(3)
+        torch.cuda.synchronize()
+        runs = []
+        for e0 in (0, 3, 0):
+            with torch.cuda.stream(stream):
+                solver.solve(s.energies[e0:e0 + 3], outs, status, sig_range=(e0, e0 + 3))
+            torch.cuda.synchronize()
+            runs.append([o.cpu().numpy() for w in ("R", "L", "G") for o in (outs[w].diag, outs[w].upper)
+                         if o is not None] + [status.cpu().numpy()])
+        st = solver.stats()
+        solver.close()
+        got[graph] = (runs, st)
+    for a, b in zip(got[False][0], got[True][0]):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    assert got[False][1]["decim_iterations"] == got[True][1]["decim_iterations"]
