@@ -193,9 +193,10 @@ __global__ void __launch_bounds__(NT) zinv_small_kernel(int n, zd* __restrict__ 
 // every CTA keeps the same position map of the row exchanges (row_at / pos_of), and the pivot
 // search of column j runs over the rows whose current position is >= j, ties going to the
 // smaller position, which selects the pivot sequence of elimination with physical exchanges.
-// Per column: warp 0 of each CTA publishes its best candidate (key, position, row and the row's
-// kb entries) in a buffer of parity j & 1, one cluster barrier, then every CTA reads all
-// candidates and the winning row through distributed shared memory and updates its own rows.
+// Per column: warp 0 of each CTA publishes its best candidate (key, position and the row's kb
+// entries) in a buffer of parity j & 1, one cluster barrier, then every CTA reads all candidates
+// and their rows through distributed shared memory in one round of independent loads, picks the
+// winner (its row index from the replicated position map) and updates its own rows.
 // A buffer of parity j & 1 is rewritten two columns later, after the barrier of column j + 1,
 // which no CTA passes before every CTA has finished reading it.  At the end each CTA writes its
 // rows to their final positions.  perm[] records the exchanges as the LAPACK-style sequence
@@ -220,7 +221,7 @@ __global__ void __launch_bounds__(NT) gj_panel_cluster_kernel(int n, int k0, int
   int* pos_of = reinterpret_cast<int*>(rowj + kb);  // [n] current position of each row
   int* row_at = pos_of + n;                          // [n] row at each position
   __shared__ unsigned long long cand_key[2];
-  __shared__ int cand_pos[2], cand_row[2];
+  __shared__ int cand_pos[2];
   __shared__ zd s_ip;
   __shared__ int s_q, s_code;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -239,51 +240,50 @@ __global__ void __launch_bounds__(NT) gj_panel_cluster_kernel(int n, int k0, int
   for (int jj = 0; jj < kb; ++jj) {
     const int j = k0 + jj, par = jj & 1;
     if (warp == 0) {
-      // best local candidate among rows at positions >= j
+      // best local candidate among rows at positions >= j: (key, position) reduced over the warp;
+      // its row is row_at[position] (the position maps are the same in every CTA)
       unsigned long long bk = 0;
-      int bp = 0x7fffffff, br = -1;
+      int bp = 0x7fffffff;
       for (int r = lane; r < rows; r += 32) {
         const int pos = pos_of[r0 + r];
         if (pos < j) continue;
         const unsigned long long k = pivot_key(P[r * ld + jj]);
-        if (br < 0 || cand_better(k, pos, bk, bp)) { bk = k; bp = pos; br = r0 + r; }
+        if (bp == 0x7fffffff || cand_better(k, pos, bk, bp)) { bk = k; bp = pos; }
       }
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
         const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, off);
         const int op = __shfl_xor_sync(0xffffffffu, bp, off);
-        const int orr = __shfl_xor_sync(0xffffffffu, br, off);
-        if (orr >= 0 && (br < 0 || cand_better(ok, op, bk, bp))) { bk = ok; bp = op; br = orr; }
+        if (op != 0x7fffffff && (bp == 0x7fffffff || cand_better(ok, op, bk, bp))) { bk = ok; bp = op; }
       }
-      if (lane == 0) { cand_key[par] = bk; cand_pos[par] = br < 0 ? 0x7fffffff : bp; cand_row[par] = br; }
-      if (br >= 0)
+      if (lane == 0) { cand_key[par] = bk; cand_pos[par] = bp; }
+      if (bp != 0x7fffffff) {
+        const int br = row_at[bp];
         for (int c = lane; c < kb; c += 32) pub[par * kb + c] = P[(br - r0) * ld + c];
+      }
     }
     cluster.sync();  // candidates of column j visible cluster-wide
     if (warp == 0) {
-      // one round of remote reads: every candidate's key and every candidate's row (lane c
-      // holds entry c of all CL rows); the winner's row is then selected locally
-      unsigned long long bk = 0;
-      int bp = 0x7fffffff, br = -1, bq = 0;
-      if (lane < CL) {
-        bk = *cluster.map_shared_rank(&cand_key[par], lane);
-        bp = *cluster.map_shared_rank(&cand_pos[par], lane);
-        br = *cluster.map_shared_rank(&cand_row[par], lane);
-        bq = lane;
-      }
+      // one round of remote reads, all issued before any is used: lane l reads the candidate of
+      // CTA l % CL, and entry l of every CTA's candidate row; the winner's row is then selected
+      // locally (lanes >= kb read a valid entry they do not use)
+      const int qr = lane & (CL - 1);
+      const int cl = lane < kb ? lane : kb - 1;
+      unsigned long long bk = *cluster.map_shared_rank(&cand_key[par], qr);
+      int bp = *cluster.map_shared_rank(&cand_pos[par], qr);
+      int bq = qr;
       zd cv[CL];
 #pragma unroll
-      for (int q = 0; q < CL; ++q)
-        cv[q] = lane < kb ? cluster.map_shared_rank(pub, q)[par * kb + lane] : zmake(0.0, 0.0);
+      for (int q = 0; q < CL; ++q) cv[q] = cluster.map_shared_rank(pub, q)[par * kb + cl];
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
+      for (int off = CL / 2; off > 0; off >>= 1) {
         const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, off);
         const int op = __shfl_xor_sync(0xffffffffu, bp, off);
-        const int orr = __shfl_xor_sync(0xffffffffu, br, off);
         const int oq = __shfl_xor_sync(0xffffffffu, bq, off);
-        if (orr >= 0 && (br < 0 || cand_better(ok, op, bk, bp))) { bk = ok; bp = op; br = orr; bq = oq; }
+        if (op != 0x7fffffff && (bp == 0x7fffffff || cand_better(ok, op, bk, bp))) { bk = ok; bp = op; bq = oq; }
       }
-      // every lane now holds the winner (row br >= 0 always: position j itself is a candidate)
+      // every lane now holds the winner (position j itself is always a candidate)
+      const int br = row_at[bp];
       zd wv = cv[0];
 #pragma unroll
       for (int q = 1; q < CL; ++q)
@@ -298,8 +298,8 @@ __global__ void __launch_bounds__(NT) gj_panel_cluster_kernel(int n, int k0, int
         s_ip = ip;
         s_q = br;
         if (pc && s_code == 0) s_code = pc;
-        // exchange positions j and pos_of[br]
-        const int cur = pos_of[br], rj = row_at[j];
+        // exchange positions j and bp
+        const int cur = bp, rj = row_at[j];
         if (rank == 0) perm[j] = cur;
         row_at[cur] = rj;
         pos_of[rj] = cur;
