@@ -58,7 +58,7 @@ typedef enum {
 
 typedef enum { BT_SYS_G = 0, BT_SYS_W = 1 } bt_system;           /* Table 2 columns      */
 typedef enum { BT_FP64 = 0, BT_SPLIT = 1 } bt_precision;         /* see bt_selinv_desc   */
-typedef enum { BT_LAYOUT_BLOCKS = 0, BT_LAYOUT_DIAGVEC = 1 } bt_layout;
+typedef enum { BT_LAYOUT_BLOCKS = 0, BT_LAYOUT_DIAGVEC = 1, BT_LAYOUT_PACKED_UPPER = 2 } bt_layout;
 typedef enum { BT_SYM_GENERAL = 0, BT_SYM_HERMITIAN = 1, BT_SYM_ANTIHERMITIAN = 2 } bt_symmetry;
 
 /* A block-tridiagonal input operand.
@@ -84,7 +84,12 @@ typedef struct {
 /* An output operand: [n_energies][nb][bs][bs] diagonal blocks, [n_energies][nb-1][bs][bs]
  * upper (i,i+1) and lower (i+1,i) blocks.  A NULL pointer means "do not write".
  * layout BT_LAYOUT_DIAGVEC writes only the diagonal entries of the diagonal blocks,
- * [n_energies][nb][bs] (densities / local DOS), and requires upper = lower = NULL. */
+ * [n_energies][nb][bs] (densities / local DOS), and requires upper = lower = NULL.
+ * layout BT_LAYOUT_PACKED_UPPER (lesser / greater outputs with symmetrize = 1 only; Sec. 4.2:
+ * anti-Hermitian quantities stored by their upper triangle) writes each diagonal block
+ * X_ii = -X_ii^H as its upper triangle, row by row: [n_energies][nb][bs (bs + 1) / 2], entry
+ * (r, c >= r) at r bs - r (r - 1) / 2 + (c - r), the lower triangle being -conj of it; upper
+ * (i,i+1) blocks are written in full as with BT_LAYOUT_BLOCKS; lower must be NULL. */
 typedef struct {
   void* diag;
   void* upper;

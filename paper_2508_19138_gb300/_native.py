@@ -15,7 +15,7 @@ STATUS_NAMES = {0: "BT_OK", 1: "BT_ERR_INVALID_ARG", 2: "BT_ERR_OOM", 3: "BT_ERR
                 9: "BT_ERR_UNSUPPORTED"}
 BT_SYS_G, BT_SYS_W = 0, 1
 BT_FP64, BT_SPLIT = 0, 1
-BT_LAYOUT_BLOCKS, BT_LAYOUT_DIAGVEC = 0, 1
+BT_LAYOUT_BLOCKS, BT_LAYOUT_DIAGVEC, BT_LAYOUT_PACKED_UPPER = 0, 1, 2
 BT_SYM_GENERAL, BT_SYM_HERMITIAN, BT_SYM_ANTIHERMITIAN = 0, 1, 2
 BT_OP_N, BT_OP_C = 0, 1
 

@@ -131,6 +131,23 @@ __global__ void axpby_kernel(long long n, double alpha, const zd* __restrict__ x
   }
 }
 
+// Packed upper triangle of (X - X^H)/2 per block (Sec. 4.2: the anti-Hermitian lesser / greater
+// blocks stored by their upper triangle): row r holds columns r..bs-1, starting at
+// r bs - r (r - 1) / 2; bs (bs + 1) / 2 entries per block.
+__global__ void write_packed_kernel(int bs, int nblk, const zd* __restrict__ src, long long s_blk, long long s_e,
+                                    zd* __restrict__ dst, long long d_e) {
+  const int e = blockIdx.z, blk = blockIdx.y;
+  const long long bs2 = (long long)bs * bs, pk = (long long)bs * (bs + 1) / 2;
+  const zd* s = src + s_e * e + s_blk * blk;
+  zd* d = dst + d_e * e + pk * blk;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < bs2; i += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(i / bs), c = (int)(i - (long long)r * bs);
+    if (c < r) continue;
+    const long long o = (long long)r * bs - (long long)r * (r - 1) / 2 + (c - r);
+    d[o] = zscale(zsub(s[i], zconj(s[(long long)c * bs + r])), 0.5);
+  }
+}
+
 // Write nblk blocks per batch entry: mode 0 copy, mode 1 (X - X^H)/2.
 __global__ void write_blocks_kernel(int bs, int nblk, const zd* __restrict__ src, long long s_blk, long long s_e,
                                     zd* __restrict__ dst, long long d_blk, long long d_e, int mode) {
@@ -260,6 +277,17 @@ bt_status write_blocks(cudaStream_t st, int bs, int nblk, int batch, const zd* s
   dim3 g = grid_for((long long)bs * bs, nblk, batch);
   if (g.x > 64) g.x = 64;
   write_blocks_kernel<<<g, 256, 0, st>>>(bs, nblk, src, s_blk, s_e, dst, d_blk, d_e, mode); count_launch();
+  BT_CUDA_TRY(cudaGetLastError());
+  return BT_OK;
+}
+
+bt_status write_packed(cudaStream_t st, int bs, int nblk, int batch, const zd* src, long long s_blk, long long s_e,
+                       zd* dst, long long d_e) {
+  if (batch <= 0 || nblk <= 0) return BT_OK;
+  if (nblk > 65535 || batch > 65535) return BT_ERR_INVALID_ARG;
+  dim3 g = grid_for((long long)bs * bs, nblk, batch);
+  if (g.x > 64) g.x = 64;
+  write_packed_kernel<<<g, 256, 0, st>>>(bs, nblk, src, s_blk, s_e, dst, d_e); count_launch();
   BT_CUDA_TRY(cudaGetLastError());
   return BT_OK;
 }

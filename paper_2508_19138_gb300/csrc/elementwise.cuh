@@ -60,6 +60,9 @@ bt_status write_blocks(cudaStream_t st, int bs, int nblk, int batch, const zd* s
                        zd* dst, long long d_blk, long long d_e, int mode);
 bt_status write_diagvec(cudaStream_t st, int bs, int nblk, int batch, const zd* src, long long s_blk, long long s_e,
                         zd* dst, long long d_blk, long long d_e, int mode);  // diagonal entries only
+// packed upper triangle of (X - X^H)/2, bs (bs + 1) / 2 entries per block
+bt_status write_packed(cudaStream_t st, int bs, int nblk, int batch, const zd* src, long long s_blk, long long s_e,
+                       zd* dst, long long d_e);
 bt_status shift_diag(cudaStream_t st, int bs, int batch, zd* X, long long sX, double v);  // X += v I
 bt_status merge_status(cudaStream_t st, int E, const int* info, int n_sources, long long src_stride, int* status);
 bt_status check_nonfinite(cudaStream_t st, long long n, int batch, const zd* x, long long sx, int* status);

@@ -581,6 +581,10 @@ bt_status write_diag_out(bt_ctx* c, int Ec, const zd* src, const bt_bt_out* o, l
   if (o->layout == BT_LAYOUT_DIAGVEC)
     return bt::write_diagvec(c->st, bs, N, Ec, src, B2, NB2, static_cast<zd*>(o->diag) + e0 * N * bs, bs,
                              (long long)N * bs, mode);
+  if (o->layout == BT_LAYOUT_PACKED_UPPER) {
+    const long long pk = (long long)N * bs * (bs + 1) / 2;
+    return bt::write_packed(c->st, bs, N, Ec, src, B2, NB2, static_cast<zd*>(o->diag) + e0 * pk, pk);
+  }
   return bt::write_blocks(c->st, bs, N, Ec, src, B2, NB2, static_cast<zd*>(o->diag) + e0 * NB2, B2, NB2, mode);
 }
 
@@ -1019,11 +1023,15 @@ bt_status check_solve_args(bt_ctx* c, const bt_bt* H, const bt_bt* S, const bt_b
       return fail("P^<> need anti-Hermitian off-diagonal blocks");
   }
   const bt_bt_out* outs[3] = {oR, oL, oG};
-  for (const bt_bt_out* o : outs) {
+  for (int k = 0; k < 3; ++k) {
+    const bt_bt_out* o = outs[k];
     if (!o) continue;
-    if (o->layout != BT_LAYOUT_BLOCKS && o->layout != BT_LAYOUT_DIAGVEC) return fail("bad output layout");
+    if (o->layout != BT_LAYOUT_BLOCKS && o->layout != BT_LAYOUT_DIAGVEC && o->layout != BT_LAYOUT_PACKED_UPPER)
+      return fail("bad output layout");
     if (o->layout == BT_LAYOUT_DIAGVEC && (o->upper || o->lower))
       return fail("diagonal-vector outputs have no off-diagonal blocks");
+    if (o->layout == BT_LAYOUT_PACKED_UPPER && (k == 0 || !c->d.symmetrize || o->lower))
+      return fail("packed upper-triangle storage is for symmetrised lesser/greater diagonal blocks (lower = NULL)");
   }
   (void)s;
   return BT_OK;
@@ -1199,7 +1207,9 @@ extern "C" bt_status bt_selinv_solve(bt_ctx* c, const bt_bt* H, const bt_bt* S, 
 namespace {
 
 long long diag_out_extent(const bt_bt_out* o, int nb, int bs) {
-  return o->layout == BT_LAYOUT_DIAGVEC ? (long long)nb * bs : (long long)nb * bs * bs;
+  if (o->layout == BT_LAYOUT_DIAGVEC) return (long long)nb * bs;
+  if (o->layout == BT_LAYOUT_PACKED_UPPER) return (long long)nb * bs * (bs + 1) / 2;
+  return (long long)nb * bs * bs;
 }
 
 struct StagedOperand {

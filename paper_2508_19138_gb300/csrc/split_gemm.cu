@@ -491,8 +491,8 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 // 32-bit words (bf16 pairs) per slice:
 //   At: out[b][s][l][p]               = (Re, Im) digits of op(A)[l][p]
 //   Bt: out[b][s][2l][p], [2l+1][p]   = (Re, -Im), (Im, Re) digits of op(B)[p][l]
-// Lines l in [L, Lpad) and words p in [Kc, Kw) are written as zeros.  The line exponents go to
-// e[b][l].
+// Words p in [Kc, Kw) are written as zeros; lines in [L, Lpad) are not written (the tensor maps
+// end at line L, so TMA fills them with zeros).  The line exponents go to e[b][l].
 template <bool kBt>
 __device__ __forceinline__ void write_slices(uint32_t* __restrict__ out, long long slice_words, int Kw, int l, int p,
                                              int S, bool in, const float* qr, const float* qi) {
@@ -519,8 +519,8 @@ __global__ void slice_lines_contig_kernel(int L, int Lpad, int Kc, int Kw, const
   if (active && active[b] == 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int l = blockIdx.x * 8 + warp;
-  if (l >= Lpad) return;
-  const bool line_ok = l < L;
+  if (l >= L) return;  // lines in [L, Lpad) are read by TMA as out of range (zeros)
+  const bool line_ok = true;
   const zd* line = X + sX * b + (long long)(line_ok ? l : 0) * ld;
   int E = 1;
   if (line_ok)
@@ -595,7 +595,7 @@ __global__ void slice_lines_strided_kernel(int L, int Lpad, int Kc, int Kw, cons
   uint32_t* ob = out + (long long)b * S * slice_words;
   for (int yy = ty; yy < 32; yy += 8) {
     const int l = l0 + yy, p = p0 + tx;
-    if (l >= Lpad || p >= Kw) continue;
+    if (l >= L || p >= Kw) continue;  // lines in [L, Lpad): out of range for TMA, never written
     const bool in = l < L && p < Kc;
     float qr[kMaxSlices], qi[kMaxSlices];
     if (in) {
@@ -611,14 +611,14 @@ template <bool kBt>
 bt_status slice_lines(cudaStream_t st, bool contiguous, int L, int Lpad, int Kc, int Kw, const zd* X, int ld,
                       long long sX, int conj, int S, int* e, uint32_t* out, int batch, const int* active) {
   if (contiguous) {
-    dim3 g((Lpad + 7) / 8, batch);
+    dim3 g((L + 7) / 8, batch);
     slice_lines_contig_kernel<kBt><<<g, 256, 0, st>>>(L, Lpad, Kc, Kw, X, ld, sX, conj, S, e, out, active);
   } else {
     BT_CUDA_TRY(cudaMemsetAsync(e, 0, sizeof(int) * (size_t)batch * L, st));
     dim3 ge((L + 31) / 32, (Kc + kExpRows - 1) / kExpRows, batch);
     line_exp_strided_kernel<<<ge, 256, 0, st>>>(L, Kc, X, ld, sX, e, active);
     count_launch();
-    dim3 g((Lpad + 31) / 32, Kw / 32, batch);
+    dim3 g((L + 31) / 32, Kw / 32, batch);
     slice_lines_strided_kernel<kBt><<<g, 256, 0, st>>>(L, Lpad, Kc, Kw, X, ld, sX, conj, S, e, out, active);
   }
   count_launch();
@@ -643,9 +643,11 @@ bool get_encode() {
   return g_encode != nullptr;
 }
 
-bool encode_slices_map(CUtensorMap* map, void* base, int Kp, int rows, int depth, int box_rows) {
+// rows: the rows that hold data; rows_alloc: the rows allocated per slice (a multiple of the
+// tile).  Rows in [rows, rows_alloc) are never written: TMA reads them as zeros (out of range).
+bool encode_slices_map(CUtensorMap* map, void* base, int Kp, int rows, int rows_alloc, int depth, int box_rows) {
   cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)depth};
-  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)Kp * 2 * rows};
+  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)Kp * 2 * rows_alloc};
   cuuint32_t box[3] = {(cuuint32_t)kKBlock, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr,
@@ -875,8 +877,8 @@ bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A,
     BT_TRY(slice_lines<true>(st, bop.op == BT_OP_C, n, n2p / 2, kc, Kp / 2, bop.p, bop.ld, bop.stride,
                              bop.op == BT_OP_C, S, w.eB, w.Bt, bb, act_b));
     CUtensorMap mA, mB;
-    if (!encode_slices_map(&mA, w.Bt, Kp, n2p, batch * S, kTileM)) return BT_ERR_CUDA;
-    if (!encode_slices_map(&mB, w.At, Kp, mp, batch * S, nt)) return BT_ERR_CUDA;
+    if (!encode_slices_map(&mA, w.Bt, Kp, 2 * n, n2p, batch * S, kTileM)) return BT_ERR_CUDA;
+    if (!encode_slices_map(&mB, w.At, Kp, m, mp, batch * S, nt)) return BT_ERR_CUDA;
     MmaParams p{};
     p.m = m;
     p.n2 = 2 * n;

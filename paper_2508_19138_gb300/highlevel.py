@@ -81,17 +81,22 @@ class GSolver:
             out.append(None if s is None else BT(s.diag[e0:e1], None, None, s.layout, s.symmetry, True))
         return out
 
-    def allocate_outputs(self, n_energies: int, which=("R", "L", "G"), lower_R: bool = True):
+    def allocate_outputs(self, n_energies: int, which=("R", "L", "G"), lower_R: bool = True, packed_lg: bool = False):
+        """Device output tensors; packed_lg: lesser/greater diagonal blocks in packed upper-triangle
+        storage ([E][nb][bs (bs + 1) / 2], BT_LAYOUT_PACKED_UPPER)."""
         import torch
         nb, bs, dev = self.nb, self.bs, self.device
         shape_d = (n_energies, nb, bs, bs)
+        shape_p = (n_energies, nb, bs * (bs + 1) // 2)
         shape_o = (n_energies, max(nb - 1, 0), bs, bs)
         outs = {}
         for w in which:
-            outs[w] = BTOut(torch.empty(shape_d, dtype=torch.complex128, device=dev),
+            packed = packed_lg and w in ("L", "G")
+            outs[w] = BTOut(torch.empty(shape_p if packed else shape_d, dtype=torch.complex128, device=dev),
                             torch.empty(shape_o, dtype=torch.complex128, device=dev) if nb > 1 else None,
                             torch.empty(shape_o, dtype=torch.complex128, device=dev)
-                            if (w == "R" and lower_R and nb > 1) else None)
+                            if (w == "R" and lower_R and nb > 1) else None,
+                            N.BT_LAYOUT_PACKED_UPPER if packed else N.BT_LAYOUT_BLOCKS)
         status = torch.empty(n_energies, dtype=torch.int32, device=dev)
         return outs, status
 

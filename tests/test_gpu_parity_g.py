@@ -273,3 +273,28 @@ def test_split_scope_all_products():
     for e in range(len(s.energies)):
         _, bad = compare_g_derived(res, s, e, e, tol=TOL_SPLIT)
         assert not bad, f"e={e}: {bad}"
+
+
+def test_packed_upper_storage_of_lesser_greater():
+    """Sec. 4.2 storage: lesser/greater diagonal blocks written as packed upper triangles equal the
+    full symmetrised blocks exactly; the packed layout is refused for G^R and unsymmetrised runs."""
+    import torch
+    import paper_2508_19138_gb300 as pkg
+    from paper_2508_19138_gb300.highlevel import GSolver
+    s = synthetic.random_device(61, 4, 70, 3)
+    solver = GSolver(s.nb, s.bs, 3, s.eta, s.kT, s.mu_left, s.mu_right, obc=True)
+    solver.set_inputs(s.H_diag, s.H_upper)
+    full, st1 = solver.allocate_outputs(3)
+    packed, st2 = solver.allocate_outputs(3, packed_lg=True)
+    solver.solve(s.energies, full, st1)
+    solver.solve(s.energies, packed, st2)
+    torch.cuda.synchronize()
+    assert packed["L"].diag.shape == (3, s.nb, s.bs * (s.bs + 1) // 2)
+    for w in ("L", "G"):
+        got = pkg.unpack_upper(packed[w].diag.cpu().numpy(), s.bs)
+        assert np.array_equal(got, full[w].diag.cpu().numpy())
+        assert np.array_equal(packed[w].upper.cpu().numpy(), full[w].upper.cpu().numpy())
+    bad = {"R": pkg.BTOut(packed["L"].diag, None, None, pkg.BT_LAYOUT_PACKED_UPPER)}
+    with pytest.raises(pkg.BTError):
+        solver.solve(s.energies, bad, st1)
+    solver.close()
