@@ -179,7 +179,9 @@ BT_API bt_status bt_selinv_solve(bt_ctx* ctx, const bt_bt* H, const bt_bt* S, co
 
 /* Same as bt_selinv_solve, but every data pointer (inputs, outputs, status) is HOST memory.
  * Inputs are copied to the device chunk by chunk, outputs copied back; the call returns
- * after the last copy completed (synchronous).  Pinned host memory gives full copy speed. */
+ * after the last copy completed (synchronous).  Pinned host memory gives full copy speed.
+ * With more than one chunk the device staging of the outputs is double-buffered and the copies
+ * of chunk k back to the host run on a second stream while chunk k + 1 computes. */
 BT_API bt_status bt_selinv_solve_host(bt_ctx* ctx, const bt_bt* H, const bt_bt* S, const bt_bt* sigR,
                                const bt_bt* sigL, const bt_bt* sigG, const double* energies_host,
                                int n_energies, const bt_bt_out* outR, const bt_bt_out* outL,

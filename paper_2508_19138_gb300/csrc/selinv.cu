@@ -60,9 +60,13 @@ struct bt_ctx {
   double* h_E = nullptr;
   bool pinned = true;   // host buffers from cudaMallocHost (else new[])
   bool owns_ws = true;  // workspace from cudaMalloc (else lent by a serving arena)
-  // host-buffer entry point staging (allocated on first use)
+  // host-buffer entry point staging (allocated on first use), and the stream and events that
+  // overlap the copies of one chunk's outputs with the next chunk's compute
   char* stage = nullptr;
   size_t stage_bytes = 0;
+  cudaStream_t copy_st = nullptr;
+  cudaEvent_t ev_done[2] = {nullptr, nullptr};
+  cudaEvent_t ev_ready = nullptr;
   std::string err;
   bt_stats stats{};
   double flops = 0.0;
@@ -491,8 +495,12 @@ extern "C" bt_status bt_selinv_destroy(bt_ctx* c) {
     if (c->pinned) cudaFreeHost(c->h_iters);
     else delete[] c->h_iters;
   }
+  if (c->copy_st) cudaStreamSynchronize(c->copy_st);
   if (c->ws && c->owns_ws) cudaFree(c->ws);
   if (c->stage) cudaFree(c->stage);
+  for (cudaEvent_t ev : {c->ev_done[0], c->ev_done[1], c->ev_ready})
+    if (ev) cudaEventDestroy(ev);
+  if (c->copy_st) cudaStreamDestroy(c->copy_st);
   if (c->pinned) {
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     if (c->h_E) cudaFreeHost(c->h_E);
@@ -1230,10 +1238,15 @@ extern "C" bt_status bt_selinv_solve_host(bt_ctx* c, const bt_bt* H, const bt_bt
   BT_TRY(check_solve_args(c, H, S, sigR, sigL, sigG, energies_host, n_energies, outR, outL, outG, status_host));
   if (n_energies == 0) return BT_OK;
   const int N = c->d.nb, bs = c->d.bs, Emax = c->d.max_energies;
-  const long long B2 = (long long)bs * bs, NB2 = N * B2, N1B2 = (long long)(N > 1 ? N - 1 : 0) * B2;
+  const long long B2 = (long long)bs * bs, N1B2 = (long long)(N > 1 ? N - 1 : 0) * B2;
   const bt_bt* ins[5] = {H, S, sigR, sigL, sigG};
   StagedOperand so[5];
-  // bytes: shared operands whole, per-energy operands for one chunk
+  const bt_bt_out* outs[3] = {outR, outL, outG};
+  // Output staging is double-buffered when there is more than one chunk: the copies of chunk k
+  // back to the host run on a second stream while chunk k + 1 computes.
+  const int n_chunks = (int)((n_energies + Emax - 1) / Emax);
+  const int nbuf = n_chunks > 1 ? 2 : 1;
+  // bytes: shared operands whole, per-energy operands for one chunk, outputs for nbuf chunks
   size_t need = 0;
   auto elems_d = [&](const bt_bt* b) { return diag_extent(*b, N, bs); };
   for (int k = 0; k < 5; ++k) {
@@ -1246,20 +1259,30 @@ extern "C" bt_status bt_selinv_solve_host(bt_ctx* c, const bt_bt* H, const bt_bt
     if (ins[k]->upper) need += al(sizeof(zd) * so[k].oext * mult);
     if (ins[k]->lower) need += al(sizeof(zd) * so[k].oext * mult);
   }
-  const bt_bt_out* outs[3] = {outR, outL, outG};
-  for (int k = 0; k < 3; ++k) {
-    if (!outs[k]) continue;
-    if (outs[k]->diag) need += al(sizeof(zd) * diag_out_extent(outs[k], N, bs) * Emax);
-    if (outs[k]->upper) need += al(sizeof(zd) * N1B2 * Emax);
-    if (outs[k]->lower) need += al(sizeof(zd) * N1B2 * Emax);
+  for (int q = 0; q < nbuf; ++q) {
+    for (int k = 0; k < 3; ++k) {
+      if (!outs[k]) continue;
+      if (outs[k]->diag) need += al(sizeof(zd) * diag_out_extent(outs[k], N, bs) * Emax);
+      if (outs[k]->upper) need += al(sizeof(zd) * N1B2 * Emax);
+      if (outs[k]->lower) need += al(sizeof(zd) * N1B2 * Emax);
+    }
+    need += al(sizeof(int) * Emax);
   }
-  need += al(sizeof(int) * Emax);
   if (c->stage_bytes < need) {
     if (c->stage) cudaFree(c->stage);
     c->stage = nullptr;
     c->stage_bytes = 0;
     if (cudaMalloc(&c->stage, need) != cudaSuccess) { cudaGetLastError(); return set_err(c, BT_ERR_OOM, "staging allocation failed"); }
     c->stage_bytes = need;
+  }
+  if (nbuf > 1 && !c->copy_st) {
+    if (cudaStreamCreateWithFlags(&c->copy_st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_done[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_done[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_ready, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(c, BT_ERR_CUDA, "copy stream set-up failed");
+    }
   }
   Carver cv(c->stage);
   for (int k = 0; k < 5; ++k) {
@@ -1270,21 +1293,25 @@ extern "C" bt_status bt_selinv_solve_host(bt_ctx* c, const bt_bt* H, const bt_bt
     if (ins[k]->upper) { so[k].u = cv.take<zd>(so[k].oext * mult); so[k].dev.upper = so[k].u; }
     if (ins[k]->lower) { so[k].l = cv.take<zd>(so[k].oext * mult); so[k].dev.lower = so[k].l; }
   }
-  bt_bt_out dout[3] = {};
-  for (int k = 0; k < 3; ++k) {
-    if (!outs[k]) continue;
-    dout[k].layout = outs[k]->layout;
-    if (outs[k]->diag) dout[k].diag = cv.take<zd>(diag_out_extent(outs[k], N, bs) * Emax);
-    if (outs[k]->upper) dout[k].upper = cv.take<zd>(N1B2 * Emax);
-    if (outs[k]->lower) dout[k].lower = cv.take<zd>(N1B2 * Emax);
+  bt_bt_out dout[2][3] = {};
+  int* dstatus[2] = {nullptr, nullptr};
+  for (int q = 0; q < nbuf; ++q) {
+    for (int k = 0; k < 3; ++k) {
+      if (!outs[k]) continue;
+      dout[q][k].layout = outs[k]->layout;
+      if (outs[k]->diag) dout[q][k].diag = cv.take<zd>(diag_out_extent(outs[k], N, bs) * Emax);
+      if (outs[k]->upper) dout[q][k].upper = cv.take<zd>(N1B2 * Emax);
+      if (outs[k]->lower) dout[q][k].lower = cv.take<zd>(N1B2 * Emax);
+    }
+    dstatus[q] = cv.take<int>(Emax);
   }
-  int* dstatus = cv.take<int>(Emax);
   cudaStream_t st = c->st;
+  cudaStream_t cs = nbuf > 1 ? c->copy_st : st;  // stream of the copies back to the host
   auto h2d = [&](void* dst, const void* src, size_t bytes) {
     return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) == cudaSuccess;
   };
   auto d2h = [&](void* dst, const void* src, size_t bytes) {
-    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, cs) == cudaSuccess;
   };
   // shared operands once
   for (int k = 0; k < 5; ++k) {
@@ -1293,8 +1320,13 @@ extern "C" bt_status bt_selinv_solve_host(bt_ctx* c, const bt_bt* H, const bt_bt
     if (so[k].u && !h2d(so[k].u, ins[k]->upper, sizeof(zd) * so[k].oext)) return set_err(c, BT_ERR_CUDA, "H2D failed");
     if (so[k].l && !h2d(so[k].l, ins[k]->lower, sizeof(zd) * so[k].oext)) return set_err(c, BT_ERR_CUDA, "H2D failed");
   }
-  for (long long e0 = 0; e0 < n_energies; e0 += Emax) {
+  int chunk = 0;
+  for (long long e0 = 0; e0 < n_energies; e0 += Emax, ++chunk) {
     const int Ec = (int)std::min<long long>(Emax, n_energies - e0);
+    const int q = chunk % nbuf;
+    // the copies out of this output set (two chunks ago) must be done before it is overwritten
+    if (nbuf > 1 && chunk >= 2 && cudaStreamWaitEvent(st, c->ev_done[q], 0) != cudaSuccess)
+      return set_err(c, BT_ERR_CUDA, "stream wait failed");
     for (int k = 0; k < 5; ++k) {
       if (!ins[k] || !ins[k]->per_energy) continue;
       const zd* hd = static_cast<const zd*>(ins[k]->diag);
@@ -1306,18 +1338,24 @@ extern "C" bt_status bt_selinv_solve_host(bt_ctx* c, const bt_bt* H, const bt_bt
     }
     bt_status s = bt_selinv_solve(c, H ? &so[0].dev : nullptr, S ? &so[1].dev : nullptr, sigR ? &so[2].dev : nullptr,
                                   sigL ? &so[3].dev : nullptr, sigG ? &so[4].dev : nullptr, energies_host + e0, Ec,
-                                  outR ? &dout[0] : nullptr, outL ? &dout[1] : nullptr, outG ? &dout[2] : nullptr,
-                                  dstatus);
+                                  outR ? &dout[q][0] : nullptr, outL ? &dout[q][1] : nullptr,
+                                  outG ? &dout[q][2] : nullptr, dstatus[q]);
     if (s != BT_OK) return s;
+    if (nbuf > 1) {
+      if (cudaEventRecord(c->ev_ready, st) != cudaSuccess || cudaStreamWaitEvent(cs, c->ev_ready, 0) != cudaSuccess)
+        return set_err(c, BT_ERR_CUDA, "event record failed");
+    }
     for (int k = 0; k < 3; ++k) {
       if (!outs[k]) continue;
       const long long dx = diag_out_extent(outs[k], N, bs);
-      if (outs[k]->diag && !d2h(static_cast<zd*>(outs[k]->diag) + dx * e0, dout[k].diag, sizeof(zd) * dx * Ec)) return set_err(c, BT_ERR_CUDA, "D2H failed");
-      if (outs[k]->upper && !d2h(static_cast<zd*>(outs[k]->upper) + N1B2 * e0, dout[k].upper, sizeof(zd) * N1B2 * Ec)) return set_err(c, BT_ERR_CUDA, "D2H failed");
-      if (outs[k]->lower && !d2h(static_cast<zd*>(outs[k]->lower) + N1B2 * e0, dout[k].lower, sizeof(zd) * N1B2 * Ec)) return set_err(c, BT_ERR_CUDA, "D2H failed");
+      if (outs[k]->diag && !d2h(static_cast<zd*>(outs[k]->diag) + dx * e0, dout[q][k].diag, sizeof(zd) * dx * Ec)) return set_err(c, BT_ERR_CUDA, "D2H failed");
+      if (outs[k]->upper && !d2h(static_cast<zd*>(outs[k]->upper) + N1B2 * e0, dout[q][k].upper, sizeof(zd) * N1B2 * Ec)) return set_err(c, BT_ERR_CUDA, "D2H failed");
+      if (outs[k]->lower && !d2h(static_cast<zd*>(outs[k]->lower) + N1B2 * e0, dout[q][k].lower, sizeof(zd) * N1B2 * Ec)) return set_err(c, BT_ERR_CUDA, "D2H failed");
     }
-    if (!d2h(status_host + e0, dstatus, sizeof(int) * Ec)) return set_err(c, BT_ERR_CUDA, "D2H failed");
+    if (!d2h(status_host + e0, dstatus[q], sizeof(int) * Ec)) return set_err(c, BT_ERR_CUDA, "D2H failed");
+    if (nbuf > 1 && cudaEventRecord(c->ev_done[q], cs) != cudaSuccess) return set_err(c, BT_ERR_CUDA, "event record failed");
   }
-  if (cudaStreamSynchronize(st) != cudaSuccess) return set_err(c, BT_ERR_CUDA, "stream error");
+  if (cudaStreamSynchronize(st) != cudaSuccess || cudaStreamSynchronize(cs) != cudaSuccess)
+    return set_err(c, BT_ERR_CUDA, "stream error");
   return BT_OK;
 }

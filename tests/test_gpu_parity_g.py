@@ -223,18 +223,23 @@ def test_status_decimation_not_converged():
     assert (res["status"] == pkg.BT_ERR_NOT_CONVERGED).all()
 
 
-def test_host_entry_point_matches_device():
-    import torch
+@pytest.mark.parametrize("graph", [False, True])
+def test_host_entry_point_matches_device(graph):
+    """Host buffers, 5 energies in chunks of 2: the output copies of one chunk overlap the next
+    chunk (double-buffered staging, second stream); twice in a row (graph mode: capture, then
+    replays).  Bitwise equal to the device entry point."""
     from paper_2508_19138_gb300 import highlevel
     s = synthetic.nanoribbon(nb=4, n_puc=2, puc=10, n_energies=5)
     dev = run_g(s, max_energies=2)
-    solver = highlevel.GSolver(s.nb, s.bs, 2, s.eta, s.kT, s.mu_left, s.mu_right)
-    outs, status = highlevel.g_solve_host(solver.ctx, s.H_diag, s.H_upper, s.energies, s.sigR_diag, s.sigL_diag,
-                                          s.sigG_diag)
-    assert (status.numpy() == 0).all()
-    for w in "RLG":
-        assert np.array_equal(outs[w].diag.numpy(), dev[w + "_diag"])
-        assert np.array_equal(outs[w].upper.numpy(), dev[w + "_upper"])
+    solver = highlevel.GSolver(s.nb, s.bs, 2, s.eta, s.kT, s.mu_left, s.mu_right, graph=graph)
+    for _ in range(2):
+        outs, status = highlevel.g_solve_host(solver.ctx, s.H_diag, s.H_upper, s.energies, s.sigR_diag,
+                                              s.sigL_diag, s.sigG_diag)
+        assert (status.numpy() == 0).all()
+        for w in "RLG":
+            assert np.array_equal(outs[w].diag.numpy(), dev[w + "_diag"])
+            assert np.array_equal(outs[w].upper.numpy(), dev[w + "_upper"])
+    solver.close()
 
 
 @pytest.mark.parametrize("maker", ["random8x32", "ribbon"])
