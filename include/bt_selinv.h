@@ -126,7 +126,8 @@ typedef struct {
   int memo_capacity;       /* energies kept; <= 0: 4 * max_energies                             */
   int split_scope;         /* BT_SPLIT only.  0: sliced products in the sweeps (the default
                               split); 1: also the products inside the block inversions (the
-                              rank-kb updates), the decimation and the memoized fixed point    */
+                              rank-kb updates), the decimation and the memoized fixed point,
+                              those with one slice more (split_slices + 1, at most 8)         */
   /* Graph mode (the batching pattern: one launch per chunk).  1: the first solve of a chunk
    * with a given set of operand pointers captures all of its launches into a CUDA graph, with
    * the decimation loop as a device-side conditional while node (the iteration stops when the

@@ -112,6 +112,10 @@ struct Carver {
 
 bool is_split(const bt_selinv_desc& d) { return d.precision == BT_SPLIT; }
 int slices_of(const bt_selinv_desc& d) { return d.split_slices > 0 ? d.split_slices : 6; }
+// split_scope = 1: the products inside the inversions and the decimation carry one slice more
+// than the sweep products; their errors are amplified by the condition of the inverted blocks
+// (at S = 6 the 40 x 416 nanoribbon's retarded blocks came out 2e-8 off the oracle).
+int kept_slices_of(const bt_selinv_desc& d) { return slices_of(d) < 8 ? slices_of(d) + 1 : 8; }
 
 // Lays out the workspace; with base == nullptr only measures it.
 size_t layout(bt_ctx* c, const bt_selinv_desc& d, char* base) {
@@ -170,7 +174,7 @@ size_t layout(bt_ctx* c, const bt_selinv_desc& d, char* base) {
   if (is_split(d)) {
     // sweep products batch E; with split_scope = 1 also the decimation's 2E leads
     const int sb = (d.split_scope == 1 && d.obc) ? (int)(2 * E) : (int)E;
-    x->split_bytes = bt::split_workspace_bytes(d.bs, d.bs, d.bs, slices_of(d), sb);
+    x->split_bytes = bt::split_workspace_bytes(d.bs, d.bs, d.bs, d.split_scope == 1 ? kept_slices_of(d) : slices_of(d), sb);
     x->split_ws = cv.take<char>(x->split_bytes);
   }
   return cv.off;
@@ -465,7 +469,7 @@ bt_status ctx_create(const bt_selinv_desc* desc, void* cuda_stream, void* ext_ws
     }
   }
   c->stats.workspace_bytes = need;
-  if (is_split(d) && d.split_scope == 1) c->eng_kept = bt::Engine{slices_of(d), c->split_ws, c->split_bytes};
+  if (is_split(d) && d.split_scope == 1) c->eng_kept = bt::Engine{kept_slices_of(d), c->split_ws, c->split_bytes};
   if (d.obc_memo) {
     c->memo_key.assign(d.memo_capacity, 0);
     c->memo_used.assign(d.memo_capacity, 0);
