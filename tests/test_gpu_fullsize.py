@@ -59,3 +59,49 @@ def test_fullsize_nanoribbon_sampled(reference, precision, scope, tol):
     bad = {k: v for k, v in worst.items() if not v <= tol}
     assert not bad, bad
     solver.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-9), (1, 1e-7)])
+def test_fullsize_w_identity(precision, tol):
+    """W system at full size (16 cells of 1024 atoms, the bench's W workload), two energies: the
+    identity W^> - W^< = W^R - W^A, exact when P^> - P^< = P^R - P^A and V = V^H (Table 2), on every
+    diagonal and upper block, relative to the largest W^R block."""
+    import torch
+    import paper_2508_19138_gb300 as pkg
+    from paper_2508_19138_gb300 import BT, BTOut
+    ws = synthetic.w_system_16x1024()
+    nb, bs = ws.nb, ws.bs
+    idx = np.array([40, 200])
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    R0d, R0u, R1d, R1u, Gd, Gu = (t(x) for x in (ws.R0_diag, ws.R0_upper, ws.R1_diag, ws.R1_upper, ws.Gam_diag,
+                                                   ws.Gam_upper))
+    R0l, R1l, Gl = (x.transpose(1, 2).conj().contiguous() for x in (R0u, R1u, Gu))
+    r1 = torch.tensor(ws.r1[idx], device="cuda").view(-1, 1, 1, 1)
+    s1 = torch.tensor(1.0 + ws.g1[idx], device="cuda").view(-1, 1, 1, 1)
+    a = torch.tensor(ws.a[idx], device="cuda").view(-1, 1, 1, 1)
+    PR = BT((R0d + r1 * R1d - 0.5j * s1 * Gd).contiguous(), (R0u + r1 * R1u - 0.5j * s1 * Gu).contiguous(),
+            (R0l + r1 * R1l - 0.5j * s1 * Gl).contiguous(), pkg.BT_LAYOUT_BLOCKS, pkg.BT_SYM_GENERAL, True)
+    PL = BT((-1j * a * s1 * Gd).contiguous(), (-1j * a * s1 * Gu).contiguous(), None, pkg.BT_LAYOUT_BLOCKS,
+            pkg.BT_SYM_ANTIHERMITIAN, True)
+    PG = BT((-1j * (1 + a) * s1 * Gd).contiguous(), (-1j * (1 + a) * s1 * Gu).contiguous(), None,
+            pkg.BT_LAYOUT_BLOCKS, pkg.BT_SYM_ANTIHERMITIAN, True)
+    V = BT(t(ws.V_diag), t(ws.V_upper), None, pkg.BT_LAYOUT_BLOCKS, pkg.BT_SYM_HERMITIAN, False)
+    E = len(idx)
+    mk = lambda *sh: torch.empty(sh, dtype=torch.complex128, device="cuda")
+    oR = BTOut(mk(E, nb, bs, bs), mk(E, nb - 1, bs, bs), mk(E, nb - 1, bs, bs))
+    oL = BTOut(mk(E, nb, bs, bs), mk(E, nb - 1, bs, bs))
+    oG = BTOut(mk(E, nb, bs, bs), mk(E, nb - 1, bs, bs))
+    status = torch.zeros(E, dtype=torch.int32, device="cuda")
+    ctx = pkg.bt_selinv_create(pkg.make_desc(nb, bs, E, system=pkg.BT_SYS_W, precision=precision, obc=False,
+                                             eta=0.0))
+    pkg.bt_selinv_solve(ctx, V, None, PR, PL, PG, ws.energies[idx], oR, oL, oG, status)
+    torch.cuda.synchronize()
+    ctx.close()
+    assert (status.cpu().numpy() == 0).all()
+    scale = torch.linalg.matrix_norm(oR.diag).max().item()
+    lhs_d = oG.diag - oL.diag
+    rhs_d = oR.diag - oR.diag.transpose(-1, -2).conj()
+    lhs_u = oG.upper - oL.upper
+    rhs_u = oR.upper - oR.lower.transpose(-1, -2).conj()
+    err = max(torch.linalg.matrix_norm(lhs_d - rhs_d).max().item(), torch.linalg.matrix_norm(lhs_u - rhs_u).max().item())
+    assert err <= tol * scale, (err / scale, tol)
