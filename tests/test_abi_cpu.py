@@ -101,3 +101,19 @@ def test_primitive_argument_checks_on_host(lib):
     assert lib.bt_zgemm_batched(4, 4, 4, 1.0, 0.0, C.c_void_p(16), 2, 0, 0, C.c_void_p(16), 4, 0, 0, 0.0, 0.0,
                                 C.c_void_p(16), 4, 0, 1, None) == 1
     assert lib.bt_zinv_batched(-1, None, 0, 1, None, None, 0, None) == 1
+
+
+def test_packed_upper_layout_formula():
+    """BT_LAYOUT_PACKED_UPPER as the header states it: entry (r, c >= r) at r bs - r (r - 1) / 2 + (c - r);
+    unpack_upper rebuilds the anti-Hermitian block from it."""
+    import numpy as np
+    import paper_2508_19138_gb300 as pkg
+    bs = 7
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((bs, bs)) + 1j * rng.standard_normal((bs, bs))
+    A = 0.5 * (X - X.conj().T)
+    packed = np.zeros(bs * (bs + 1) // 2, dtype=np.complex128)
+    for r in range(bs):
+        for c in range(r, bs):
+            packed[r * bs - r * (r - 1) // 2 + (c - r)] = A[r, c]
+    assert np.array_equal(pkg.unpack_upper(packed, bs), A)
