@@ -11,9 +11,14 @@
 //         X^<>_{i,i+1} = -x^R_i M~_{i,i+1} X^<>_{i+1} - x^<>_i (X^R_{i+1} M~_{i+1,i})^H
 //                        + x^R_i B^<>_{i,i+1} (X^R_{i+1})^H
 //       W system: W^R = X^R V on the selected blocks (needs X^R_{i,i+-2})
-//   a5  symmetrised write-out of the diagonal lesser/greater blocks (Sec. 4.2)
-// All products go through prod(), which runs the FP64 DFMA kernel or, with BT_SPLIT, the
-// sliced bf16 tensor-core product.  Inversions and decimation are always FP64.
+//   a5  symmetrised write-out of the diagonal lesser/greater blocks (Sec. 4.2), as full blocks
+//       or packed upper triangles
+// All sweep products go through prod(), which runs the FP64 DFMA kernel or, with BT_SPLIT, the
+// sliced bf16 tensor-core product; with symmetrised outputs the lesser/greater sandwiches come
+// out exactly anti-Hermitian (Sec. 4.2 symmetry kept inside the sweep) and Z_i of Eq. 11 is
+// formed from the first term of X^<>_{i,i+1}.  The inversions and the decimation run on the
+// FP64 engine, or on a sliced one with split_scope = 1.  In graph mode a chunk's launches are
+// captured once into a CUDA graph and replayed (run_chunk_graph).
 #include <algorithm>
 #include <cstring>
 #include <functional>
