@@ -8,11 +8,13 @@
 // end as column exchanges in reverse order.
 //
 //  * n <= kSmallN: one CTA per matrix, the whole matrix resident in shared memory.
-//  * larger n: blocked.  For each panel of kb columns one CTA per matrix eliminates the n x kb
-//    panel in shared memory (all rows, pivots searched in rows >= j); the remaining columns
-//    then receive the panel's row exchanges and the rank-kb update
+//  * larger n: blocked.  For each panel of kb columns the n x kb panel is eliminated in shared
+//    memory (all rows, pivots searched in rows >= j) — by one CTA per matrix, or for
+//    n >= kClusterMinN by a thread-block cluster per matrix with the rows split across its
+//    SMs; the remaining columns then receive the panel's row exchanges and the rank-kb update
 //        A[:, C] += P[:, K] * A_old[K, C]   (rows K of C zeroed first)
-//    as one batched FP64 GEMM, so the O(n^3) part runs on the GEMM kernel.
+//    as one batched GEMM (FP64, or sliced on the tensor cores), so the O(n^3) part runs on
+//    the GEMM kernels.
 #include <cooperative_groups.h>
 
 #include <mutex>
