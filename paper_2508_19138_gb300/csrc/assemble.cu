@@ -1,6 +1,8 @@
 // Element-wise kernels of the sweep: assembly of M~ and B^<> blocks (Sec. 3.2.1, Table 2),
 // the lesser/greater boundary blocks by fluctuation-dissipation (Sec. 3.1), the anti-Hermitian
-// corrections (y - y^H), (Z - Z^H) of Eq. 9 and 11, and the symmetrised write-out of Sec. 4.2.
+// corrections (y - y^H), (Z - Z^H) of Eq. 9 and 11, the projection onto anti-Hermitian blocks
+// and the symmetrised write-out of Sec. 4.2 (full blocks, diagonal entries or packed upper
+// triangles).
 // All are memory-bound grid-stride loops over (element, batch entry) with coalesced accesses
 // along the row-major block; transposed reads (X^H) go through the L1/L2 of the same block.
 #include "elementwise.cuh"

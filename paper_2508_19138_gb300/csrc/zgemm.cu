@@ -11,7 +11,8 @@
 //    (error bound u |a||b| per term with |.| the 1-norm of re/im, Higham 2002, Sec. 23.2.4);
 //  * what matters otherwise is keeping every SM busy with whole tiles: 32 x 32 output tiles
 //    divide the workload block sizes (32, 416 = 13 x 32, 1024) without ragged waste, and the
-//    batch (energies x blocks) gives >= 152 CTAs.
+//    batch (energies x blocks) gives >= 152 CTAs; where it would not (small blocks, few
+//    energies), 16 x 16 tiles of 64 threads are used instead.
 // Tiles are staged through shared memory with a register prefetch of the next k-slab.
 // zgemm_antiherm: the same kernel over the upper tiles only, for products whose exact result is
 // anti-Hermitian (the lesser / greater sandwiches), the lower tiles written as mirror images.
