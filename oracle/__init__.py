@@ -13,7 +13,9 @@ What it computes (the plain definitions the recursive Green's function method re
     independently by the direct eigen-decomposition route (Eq. 6, polynomial eigenproblem).
   * Sec. 3.1 (lesser/greater OBC): fluctuation-dissipation from the retarded boundary block.
   * Sec. 4.2: the symmetrisation X_ij <- (X_ij - X_ji^*)/2.
-  * Table 2, right column: the W system M = I, B^R = V P^R, B^<> = V P^<> V^H, W^R = X^R V.
+  * Table 2, right column: the W system M = I, B^R = V P^R, B^<> = V P^<> V^H, W^R = X^R V;
+    with contacts (Sec. 3.1, Eq. 4 and 7), the leads folded into the edge cells by the retarded
+    recursion and a Stein (discrete Lyapunov) equation for the lesser / greater boundary.
 
 Pins (tests/test_oracle_pins.py) tie every function to something other than itself: closed
 forms of the 1D chain, integer transmission, the eigen-route surface function, algebraic

@@ -12,7 +12,8 @@ import scipy.linalg as sla
 __all__ = [
     "fermi", "bt_dense", "sancho_rubio", "surface_gf_eig", "lead_blocks", "obc_self_energies",
     "assemble_g", "selected_blocks", "symmetrize_lesser", "solve_g", "assemble_w", "solve_w",
-    "transmission", "bond_currents", "block_rows_banded", "solve_g_sampled",
+    "transmission", "bond_currents", "block_rows_banded", "solve_g_sampled", "w_extended_chain",
+    "w_lead_fold", "solve_w_contacts", "solve_w_long_leads",
 ]
 
 
@@ -351,3 +352,139 @@ def solve_g_sampled(sysg, e, blocks, symmetrize=True, tol=1e-14, maxit=100):
             r["L_upper"], r["G_upper"] = Lu, Gu
         out[i] = r
     return out
+
+
+# ----------------------------------------------------------------------------------------------
+# W system with contacts (Sec. 3.1: retarded OBC by Eq. 4, lesser/greater OBC by the discrete
+# Lyapunov equation of Eq. 7).  Groundwork for the W contacts: the CUDA path does not solve W
+# with contacts.
+#
+# Reading.  Each lead is the periodic continuation of the device's edge cell (its diagonal
+# blocks and its coupling to the next cell inward), for V and for P.  M = I - V P^R and
+# B^<> = V P^<> V^H are then block-tridiagonal over the whole chain (cells longer than 3 r_cut).
+# A lead with bulk blocks m, n (coupling from a cell to the next one away from the device),
+# n', and right-hand-side blocks b, c (c = B_{far, near}) folds into the device's edge cell as
+#     x^R = (m - n x^R n')^{-1}                         (Eq. 4)
+#     y = n x^R c,   a = x^R n,   q = x^R (b - y + y^H) x^R^H
+#     w^<> = q + a w^<> a^H                              (Eq. 7; a Stein equation)
+#     B^R_OBC = n x^R n',   B^<>_OBC = n w^<> n^H - (y - y^H)
+# — the fixed point of the forward recursion of Eq. 8-9 run along the lead from infinity.  The
+# edge cells' own blocks of M and B include the products with the first lead cell.
+# ----------------------------------------------------------------------------------------------
+
+def w_extended_chain(wsys, e, n_lead):
+    """BT blocks of V, P^R, P^<, P^> over n_lead lead cells, the device, n_lead lead cells: each
+    lead repeats the device's edge cell and its coupling to the next cell inward.  Returns
+    (V_d, V_u, PR_d, PR_u, PR_l, PL_d, PL_u, PG_d, PG_u) for the whole chain."""
+    nb = wsys.nb
+    PRd, PRu, PRl, PLd, PLu, PGd, PGu = wsys.P_blocks(e)
+    ops_d = [wsys.V_diag, PRd, PLd, PGd]
+    ops_u = [wsys.V_upper, PRu, PLu, PGu]
+
+    def extend_d(d):
+        return np.concatenate([np.repeat(d[:1], n_lead, 0), d, np.repeat(d[-1:], n_lead, 0)])
+
+    def extend_u(u):
+        return np.concatenate([np.repeat(u[:1], n_lead, 0), u, np.repeat(u[-1:], n_lead, 0)])
+
+    Vd, PRd_x, PLd_x, PGd_x = (extend_d(d) for d in ops_d)
+    Vu, PRu_x, PLu_x, PGu_x = (extend_u(u) for u in ops_u)
+    PRl_x = extend_u(PRl)
+    return Vd, Vu, PRd_x, PRu_x, PRl_x, PLd_x, PLu_x, PGd_x, PGu_x
+
+
+def _w_chain_dense(wsys, e, n_lead):
+    Vd, Vu, PRd, PRu, PRl, PLd, PLu, PGd, PGu = w_extended_chain(wsys, e, n_lead)
+    V = bt_dense(Vd, Vu)
+    PR = bt_dense(PRd, PRu, PRl)
+    PL = bt_dense(PLd, PLu, lower_sign=-1.0)
+    PG = bt_dense(PGd, PGu, lower_sign=-1.0)
+    n = V.shape[0]
+    return np.eye(n) - V @ PR, V @ PL @ V.conj().T, V @ PG @ V.conj().T, V
+
+
+def w_lead_fold(m, n, n_prime, b, c, tol=1e-14, maxit=200):
+    """Retarded and lesser/greater boundary blocks of one lead (see the reading above).
+    Returns (B^R_OBC, B^<>_OBC, x^R, w^<>)."""
+    x, _, ok = sancho_rubio(m, n, n_prime, tol, maxit)
+    if not ok:
+        raise ValueError("decimation did not converge")
+    y = n @ x @ c
+    a = x @ n
+    q = x @ (b - y + y.conj().T) @ x.conj().T
+    w = sla.solve_discrete_lyapunov(a, q)   # w = a w a^H + q
+    return n @ x @ n_prime, n @ w @ n.conj().T - (y - y.conj().T), x, w
+
+
+def solve_w_contacts(wsys, e, symmetrize=True):
+    """Selected blocks of W^R = X^R V and W^<> = X^<> for the W system with both leads attached
+    (the reading above), by folding the leads into the edge cells and a dense solve of the
+    device.  W^R's edge blocks include V's coupling to the first lead cells through
+    X^R_{0,-1} = -X^R_{00} M_{0,-1} x^R_L (and the mirror on the right)."""
+    nb, bs = wsys.nb, wsys.bs
+    K = 4   # lead cells in the assembly window: cell 1 and cell (K + nb + 2) are bulk lead cells
+    M, BL, BG, V = _w_chain_dense(wsys, e, K)
+    blk = lambda A, i, j: A[i * bs:(i + 1) * bs, j * bs:(j + 1) * bs]
+    d0, d1 = K, K + nb          # device cells [d0, d1)
+    sl = slice(d0 * bs, d1 * bs)
+    Md = M[sl, sl].copy()
+    Bs = {"L": BL[sl, sl].copy(), "G": BG[sl, sl].copy()}
+    # left lead: bulk cell 1, away = toward cell 0
+    kL = 1
+    mL, nL, npL = blk(M, kL, kL), blk(M, kL, kL - 1), blk(M, kL - 1, kL)
+    # right lead: bulk cell d1 + 2, away = toward d1 + 3
+    kR = d1 + 2
+    mR, nR, npR = blk(M, kR, kR), blk(M, kR, kR + 1), blk(M, kR + 1, kR)
+    outs = {}
+    xs = {}
+    for w, B in (("L", BL), ("G", BG)):
+        bLb, cL = blk(B, kL, kL), blk(B, kL - 1, kL)
+        bRb, cR = blk(B, kR, kR), blk(B, kR + 1, kR)
+        rL, lgL, xL, _ = w_lead_fold(mL, nL, npL, bLb, cL)
+        rR, lgR, xR, _ = w_lead_fold(mR, nR, npR, bRb, cR)
+        Bs[w][:bs, :bs] += lgL
+        Bs[w][-bs:, -bs:] += lgR
+        xs = {"L": xL, "R": xR, "RL": rL, "RR": rR}
+    Md[:bs, :bs] -= xs["RL"]
+    Md[-bs:, -bs:] -= xs["RR"]
+    XR = np.linalg.inv(Md)
+    # W^R = X^R V over the whole chain restricted to device rows: device columns from the
+    # device X^R, plus the first lead cell on each side
+    Vx = V
+    XRfull = np.zeros((nb * bs, (nb + 2) * bs), dtype=np.complex128)   # columns: lead cell, device, lead cell
+    XRfull[:, bs:-bs] = XR
+    XRfull[:, :bs] = -XR[:, :bs] @ blk(M, d0, d0 - 1) @ xs["L"]        # X^R_{i,-1}
+    XRfull[:, -bs:] = -XR[:, -bs:] @ blk(M, d1 - 1, d1) @ xs["R"]      # X^R_{i,N}
+    Vrows = Vx[(d0 - 1) * bs:(d1 + 1) * bs, sl]                           # V_{k, device} for k in [d0-1, d1]
+    WR = XRfull @ Vrows
+    res = {}
+    for w in ("L", "G"):
+        X = XR @ Bs[w] @ XR.conj().T
+        if symmetrize:
+            X = symmetrize_lesser(X)
+        d, u, _ = selected_blocks(X, nb, bs)
+        res[w + "_diag"], res[w + "_upper"] = d, u
+    d, u, l = selected_blocks(WR, nb, bs)
+    res.update(R_diag=d, R_upper=u, R_lower=l, WR=WR, XR=XR, M=Md, BL=Bs["L"], BG=Bs["G"])
+    return res
+
+
+def solve_w_long_leads(wsys, e, n_lead, symmetrize=True):
+    """The same selected blocks from a finite chain with n_lead lead cells on each side, solved
+    densely without any boundary condition: converges to solve_w_contacts as n_lead grows (the
+    absorbing part of P^R damps the leads).  The pin of the folding."""
+    nb, bs = wsys.nb, wsys.bs
+    M, BL, BG, V = _w_chain_dense(wsys, e, n_lead)
+    XR = np.linalg.inv(M)
+    sl = slice(n_lead * bs, (n_lead + nb) * bs)
+    res = {}
+    for w, B in (("L", BL), ("G", BG)):
+        X = (XR @ B @ XR.conj().T)[sl, sl]
+        if symmetrize:
+            X = symmetrize_lesser(X)
+        d, u, _ = selected_blocks(X, nb, bs)
+        res[w + "_diag"], res[w + "_upper"] = d, u
+    WR = (XR @ V)[sl, sl]
+    d, u, l = selected_blocks(WR, nb, bs)
+    res.update(R_diag=d, R_upper=u, R_lower=l)
+    return res
