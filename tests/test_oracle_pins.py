@@ -371,3 +371,40 @@ def test_mutation_wrong_fluctuation_dissipation_sign_is_caught(dev):
             assert w.min() < 0
             return
     pytest.fail("no block had a nonzero lesser function")
+
+
+def test_mutation_w_product_order_is_caught(wsmall, monkeypatch):
+    """M = I - P^R V instead of I - V P^R: the solution no longer satisfies (I - V P^R) W^R = V."""
+    orig = oracle.negf.assemble_w
+
+    def swapped(wsys, e):
+        M, BL, BG, V = orig(wsys, e)
+        PRd, PRu, PRl, *_ = wsys.P_blocks(e)
+        PR = oracle.bt_dense(PRd, PRu, PRl)
+        return np.eye(M.shape[0]) - PR @ V, BL, BG, V
+
+    monkeypatch.setattr(oracle.negf, "assemble_w", swapped)
+    r = oracle.solve_w(wsmall, 1, symmetrize=False)
+    V = oracle.bt_dense(wsmall.V_diag, wsmall.V_upper)
+    PRd, PRu, PRl, *_ = wsmall.P_blocks(1)
+    PR = oracle.bt_dense(PRd, PRu, PRl)
+    resid = np.abs((np.eye(V.shape[0]) - V @ PR) @ r["WR"] - V).max()
+    assert resid > 1e-6 * np.abs(V).max()
+
+
+def test_mutation_hermitian_instead_of_antihermitian_symmetrisation_is_caught(dev, monkeypatch):
+    """(X + X^H)/2 in place of (X - X^H)/2 (Sec. 4.2) keeps only the rounding noise of the lesser
+    and greater functions: the G^> - G^< identity of Table 2, which the symmetrised blocks satisfy,
+    no longer holds."""
+    bs = dev.bs
+
+    def identity_error():
+        r = oracle.solve_g(dev, 3)
+        XR = r["XR"]
+        lhs = r["G_diag"][0] - r["L_diag"][0]
+        rhs = (XR - XR.conj().T + 2j * dev.eta * XR @ XR.conj().T)[:bs, :bs]
+        return np.abs(lhs - rhs).max() / np.abs(rhs).max()
+
+    assert identity_error() < 1e-12
+    monkeypatch.setattr(oracle.negf, "symmetrize_lesser", lambda X: 0.5 * (X + X.conj().T))
+    assert identity_error() > 1e-3
