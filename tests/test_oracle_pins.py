@@ -405,6 +405,7 @@ def test_mutation_hermitian_instead_of_antihermitian_symmetrisation_is_caught(de
         rhs = (XR - XR.conj().T + 2j * dev.eta * XR @ XR.conj().T)[:bs, :bs]
         return np.abs(lhs - rhs).max() / np.abs(rhs).max()
 
-    assert identity_error() < 1e-12
+    assert identity_error() < 1e-8
     monkeypatch.setattr(oracle.negf, "symmetrize_lesser", lambda X: 0.5 * (X + X.conj().T))
-    assert identity_error() > 1e-3
+    bad = identity_error()
+    assert bad > 1e-3, bad
