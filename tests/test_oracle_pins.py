@@ -133,6 +133,28 @@ def test_bond_current_conserved_and_equals_transmission():
         assert np.allclose(I, T, rtol=1e-6, atol=1e-8)
 
 
+def test_contact_currents_meir_wingreen():
+    """Coherent transport (no scattering, eta -> 0) with f_L = 1, f_R = 0 on a random, non-periodic
+    device: the current into the device at each contact, Tr[B^<_c G^>_cc - B^>_c G^<_cc] over that
+    contact's edge block, is +T(E) at the left and -T(E) at the right, and the bond current inside
+    the device is T(E) at every interface.  T comes from retarded quantities only, so this pins the
+    lesser/greater edge blocks and the contacts' Fermi weights and orientation."""
+    s = synthetic.random_device(12, 5, 6, 8, e_lo=-1.0, e_hi=1.0, coupling=1.5, eta=1e-10, mu_left=50.0,
+                                mu_right=-50.0)
+    open_channels = 0
+    for e in range(s.energies.size):
+        r = oracle.solve_g(s, e)
+        o = oracle.obc_self_energies(s, e)
+        I_left = np.trace(o["L_L"] @ r["G_diag"][0] - o["G_L"] @ r["L_diag"][0])
+        I_right = np.trace(o["L_R"] @ r["G_diag"][-1] - o["G_R"] @ r["L_diag"][-1])
+        T = oracle.transmission(s, e)
+        tol = 1e-6 * max(1.0, T)
+        assert abs(I_left - T) <= tol and abs(I_right + T) <= tol, (e, I_left, I_right, T)
+        assert np.allclose(oracle.bond_currents(s.H_upper, r["L_upper"]), T, rtol=1e-6, atol=1e-8)
+        open_channels += T > 0.5
+    assert open_channels >= 2
+
+
 def test_two_block_inverse_closed_form():
     """N = 2, no contacts: blocks of the 2x2 block inverse via the Schur complement."""
     rng = np.random.default_rng(2)
