@@ -73,7 +73,7 @@ def tune_g_chunk(nb: int, bs: int, H_diag, H_upper, energies, sigR=None, sigL=No
     def measure(c):
         solver = GSolver(nb, bs, c, eta, kT, mu_left, mu_right, precision=precision, split_scope=split_scope)
         solver.set_inputs(H_diag, H_upper, sigR, sigL, sigG)
-        n = min(len(energies), max(c, 2 * c))
+        n = min(len(energies), 2 * c)
         outs, status = solver.allocate_outputs(n)
         solver.solve(energies[:n], outs, status, sig_range=(0, n) if sigR is not None else None)  # warm-up
         torch.cuda.synchronize()
