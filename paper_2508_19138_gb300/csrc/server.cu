@@ -23,6 +23,7 @@
 #include <thread>
 #include <vector>
 
+#include "arena.h"
 #include "bt_common.cuh"
 
 namespace {
@@ -32,50 +33,6 @@ using Clock = std::chrono::steady_clock;
 double seconds_since(Clock::time_point t0) {
   return std::chrono::duration<double>(Clock::now() - t0).count();
 }
-
-// First-fit arena over one device allocation.
-class Arena {
- public:
-  void reset(char* base, size_t bytes) {
-    base_ = base;
-    free_.clear();
-    free_[0] = bytes;
-  }
-  // returns offset or SIZE_MAX
-  size_t alloc(size_t bytes) {
-    bytes = (bytes + 255) / 256 * 256;
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second >= bytes) {
-        const size_t off = it->first, len = it->second;
-        free_.erase(it);
-        if (len > bytes) free_[off + bytes] = len - bytes;
-        return off;
-      }
-    }
-    return SIZE_MAX;
-  }
-  void release(size_t off, size_t bytes) {
-    bytes = (bytes + 255) / 256 * 256;
-    auto it = free_.emplace(off, bytes).first;
-    auto nx = std::next(it);
-    if (nx != free_.end() && it->first + it->second == nx->first) {
-      it->second += nx->second;
-      free_.erase(nx);
-    }
-    if (it != free_.begin()) {
-      auto pv = std::prev(it);
-      if (pv->first + pv->second == it->first) {
-        pv->second += it->second;
-        free_.erase(it);
-      }
-    }
-  }
-  char* base() const { return base_; }
-
- private:
-  char* base_ = nullptr;
-  std::map<size_t, size_t> free_;  // offset -> length
-};
 
 struct Request {
   bt_request r;
@@ -94,7 +51,7 @@ struct bt_server {
   bt_server_desc d{};
   char* arena_mem = nullptr;
   size_t arena_bytes = 0;
-  Arena arena;
+  bt::Arena arena;
   std::mutex mu;
   std::condition_variable cv;
   std::deque<Request*> queue;
