@@ -106,6 +106,12 @@ class GSolver:
         if outs is None:
             outs, status = self.allocate_outputs(len(energies))
         sR, sL, sG = (self.sigR, self.sigL, self.sigG) if sig_range is None else self.energy_slice(*sig_range)
+        if self._own_stream is not None:
+            # the private stream of graph mode runs after what the caller queued on its stream (the
+            # staging copies below and the solve read inputs the caller may just have produced), and
+            # the caller's stream waits for the solve at the end
+            import torch
+            self._own_stream.wait_stream(torch.cuda.current_stream())
         if self.graph and sig_range is not None:
             # graph mode replays a captured chunk only while the operand pointers stay the same:
             # the energy slices are copied (on the solve stream) into buffers that stay put
@@ -119,12 +125,10 @@ class GSolver:
                 for a, buf in zip(ins, self._stage):
                     if a is not None:
                         buf.copy_(a.diag, non_blocking=True)
+                        if isinstance(st, torch.cuda.Stream):
+                            buf.record_stream(st)  # allocated on the caller's stream, read on st
             sR, sL, sG = [None if a is None else BT(buf, None, None, a.layout, a.symmetry, True)
                           for a, buf in zip(ins, self._stage)]
-        if self._own_stream is not None:
-            # the private stream of graph mode is ordered after, and before, the caller's stream
-            import torch
-            self._own_stream.wait_stream(torch.cuda.current_stream())
         bt_selinv_solve(self.ctx, self.H, self.S, sR, sL, sG, energies, outs.get("R"), outs.get("L"),
                         outs.get("G"), status)
         if self._own_stream is not None:
