@@ -73,6 +73,8 @@ def bt_server_submit(srv: Server, nb: int, bs: int, H: BT, energies, status, out
 def bt_server_poll(srv: Server, ticket: int) -> int:
     st = C.c_int(0)
     rc = N.load().bt_server_poll(srv.handle, ticket, C.byref(st))
+    if st.value >= 2:  # done or failed: the server no longer touches the request's tensors
+        srv.keep.pop(ticket, None)
     if rc != N.BT_OK:
         raise BTError(rc, "bt_server_poll")
     return st.value
@@ -81,9 +83,10 @@ def bt_server_poll(srv: Server, ticket: int) -> int:
 def bt_server_wait(srv: Server, ticket: int, timeout_s: float = 600.0) -> int:
     st = C.c_int(0)
     rc = N.load().bt_server_wait(srv.handle, ticket, timeout_s, C.byref(st))
+    if st.value >= 2:
+        srv.keep.pop(ticket, None)
     if rc != N.BT_OK:
         raise BTError(rc, f"bt_server_wait (state {st.value})")
-    srv.keep.pop(ticket, None)
     return st.value
 
 
