@@ -5,7 +5,8 @@ Workload (default): the nanoribbon-shaped G system, 40 blocks of 416 (sparse-in-
 scattering self-energies), 512 energies on [-4, 4].  One step = one bt_selinv_solve over a batch
 of `--energies-per-step` consecutive grid energies (all hot-path stages: assembly, decimation,
 forward and backward sweeps, symmetrised write-out).  Inputs are resident in HBM before the timed
-region; the per-step working set (>10 GB) exceeds L2, so no flush is needed.
+region; the per-step working set (>10 GB) exceeds L2, so no flush is needed (smaller workloads
+write a 512 MB buffer before every timed step, outside its events).
 
 Prints ONE JSON line (rank 0).  Multi-GPU (torchrun): every rank solves its own energies (weak
 scaling, no data-path collective); time = max over ranks.
@@ -119,24 +120,30 @@ class ClockSampler:
             os.remove(self.path)
         except OSError:
             pass
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in lines:
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 8:
-                continue
-            try:
-                sm.append(float(parts[0]))
-                smax.append(float(parts[1]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[4:8]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return summarize_clocks(lines)
+
+
+def summarize_clocks(lines):
+    """nvidia-smi samples (ClockSampler.FIELDS, csv, noheader, nounits) -> median SM clock under
+    load, the maximum SM clock, and the throttle reasons seen Active in any sample."""
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in lines:
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 8:
+            continue
+        try:
+            sm.append(float(parts[0]))
+            smax.append(float(parts[1]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, parts[4:8]):
+            if v.lower().startswith("active"):
+                reasons.add(nm)
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+            "samples": len(sm)}
 
 
 # ------------------------------------------------------------------------------------------
