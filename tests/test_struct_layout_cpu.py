@@ -71,3 +71,25 @@ def _header_fields(struct):
 @pytest.mark.parametrize("struct", STRUCTS)
 def test_binding_names_every_header_field_in_order(struct):
     assert [name for name, _ in getattr(N, struct)._fields_] == _header_fields(struct)
+
+
+def test_binding_constants_match_header(tmp_path):
+    """Every BT_* enumerator of the header has the binding's value, and the binding defines them all."""
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    names = []
+    for body in re.findall(r"enum\s*\{([^{}]*)\}", text):
+        names += re.findall(r"\b(BT_[A-Z0-9_]+)\s*=", body)
+    assert len(names) >= 20
+    src = tmp_path / "consts.c"
+    src.write_text('#include <stdio.h>\n#include "bt_selinv.h"\nint main(void) {\n' +
+                   "".join(f'  printf("{n} %d\\n", (int){n});\n' for n in names) + "  return 0;\n}\n")
+    exe = str(tmp_path / "consts")
+    subprocess.run([cc, "-std=c99", "-I", os.path.dirname(HEADER), str(src), "-o", exe], check=True,
+                   capture_output=True, text=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    for ln in out.splitlines():
+        n, v = ln.split()
+        assert getattr(N, n) == int(v), n
