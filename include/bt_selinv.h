@@ -51,7 +51,10 @@ typedef enum {
   BT_ERR_CUDA = 4,          /* a CUDA runtime call or kernel launch failed                   */
   BT_ERR_SINGULAR = 5,      /* per energy: a zero pivot in a block inversion                 */
   BT_ERR_NOT_CONVERGED = 6, /* per energy: decimation reached decim_maxit                    */
-  BT_ERR_NONFINITE = 7,     /* per energy: NaN / Inf in an input or a pivot                  */
+  BT_ERR_NONFINITE = 7,     /* per energy: NaN / Inf reached a pivot of a block inversion or */
+                            /* the decimation's convergence test (non-finite H, S, Sigma^R,  */
+                            /* P^R or V); non-finite lesser/greater inputs are not scanned:  */
+                            /* they reach the lesser/greater outputs with status BT_OK       */
   BT_ERR_TIMEOUT = 8,       /* a bounded device wait expired                                 */
   BT_ERR_UNSUPPORTED = 9    /* valid request this build does not implement                   */
 } bt_status;

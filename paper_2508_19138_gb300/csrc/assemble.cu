@@ -190,21 +190,6 @@ __global__ void merge_status_kernel(int E, const int* __restrict__ info, int n_s
   }
 }
 
-// scan of a batch of blocks for NaN / Inf; flags status[e]
-__global__ void nonfinite_kernel(long long n, const zd* __restrict__ x, long long sx, int* __restrict__ status) {
-  const int e = blockIdx.y;
-  int bad = 0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    // exponent field all ones = Inf / NaN (integer test: no FP64 instruction)
-    const zd v = x[sx * e + i];
-    const unsigned long long a = (unsigned long long)__double_as_longlong(v.x),
-                             b = (unsigned long long)__double_as_longlong(v.y);
-    if ((a & 0x7FF0000000000000ull) == 0x7FF0000000000000ull || (b & 0x7FF0000000000000ull) == 0x7FF0000000000000ull)
-      bad = 1;
-  }
-  if (__syncthreads_or(bad) && threadIdx.x == 0 && status[e] == 0) atomicCAS(&status[e], 0, (int)BT_ERR_NONFINITE);
-}
-
 __global__ void shift_diag_kernel(int bs, zd* __restrict__ X, long long sX, double v) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= bs) return;
@@ -315,13 +300,6 @@ bt_status write_diagvec(cudaStream_t st, int bs, int nblk, int batch, const zd* 
 bt_status merge_status(cudaStream_t st, int E, const int* info, int n_sources, long long src_stride, int* status) {
   if (E <= 0) return BT_OK;
   merge_status_kernel<<<(E + 127) / 128, 128, 0, st>>>(E, info, n_sources, src_stride, status); count_launch();
-  BT_CUDA_TRY(cudaGetLastError());
-  return BT_OK;
-}
-
-bt_status check_nonfinite(cudaStream_t st, long long n, int batch, const zd* x, long long sx, int* status) {
-  if (batch <= 0 || n <= 0) return BT_OK;
-  nonfinite_kernel<<<grid_for(n, batch), 256, 0, st>>>(n, x, sx, status); count_launch();
   BT_CUDA_TRY(cudaGetLastError());
   return BT_OK;
 }

@@ -65,6 +65,5 @@ bt_status write_packed(cudaStream_t st, int bs, int nblk, int batch, const zd* s
                        zd* dst, long long d_e);
 bt_status shift_diag(cudaStream_t st, int bs, int batch, zd* X, long long sX, double v);  // X += v I
 bt_status merge_status(cudaStream_t st, int E, const int* info, int n_sources, long long src_stride, int* status);
-bt_status check_nonfinite(cudaStream_t st, long long n, int batch, const zd* x, long long sx, int* status);
 
 }  // namespace bt
