@@ -18,14 +18,16 @@ __all__ = [
 
 
 def fermi(E, mu, kT):
-    """Fermi-Dirac occupation 1 / (1 + exp((E - mu)/kT)), evaluated without overflow."""
+    """Fermi-Dirac occupation 1 / (1 + exp((E - mu)/kT)) of a contact (Sec. 3.1: the lesser/greater
+    boundary blocks carry the contacts' occupations), evaluated without overflow."""
     x = (np.asarray(E, dtype=np.float64) - mu) / kT
     ex = np.exp(-np.abs(x))
     return np.where(x > 0, ex / (1.0 + ex), 1.0 / (1.0 + ex))
 
 
 def bt_dense(diag, upper, lower=None, lower_sign=1.0):
-    """Dense n x n matrix from BT blocks.  lower=None means block (i+1,i) = lower_sign * upper[i]^H
+    """Dense n x n matrix from BT blocks (the block-tridiagonal operands of Eq. 1 and Table 2).
+    lower=None means block (i+1,i) = lower_sign * upper[i]^H
     (lower_sign = +1 Hermitian pattern, -1 anti-Hermitian pattern)."""
     nb, bs = diag.shape[0], diag.shape[1]
     A = np.zeros((nb * bs, nb * bs), dtype=np.complex128)
@@ -91,7 +93,8 @@ def surface_gf_eig(m, n, n_prime):
 
 
 def _M_blocks(sysg, e):
-    """Blocks of M - B^R_scatt at energy index e: (diag [N,b,b], upper, lower)."""
+    """Blocks of M - B^R_scatt at energy index e (Table 2, left column: M = E S - H):
+    (diag [N,b,b], upper, lower)."""
     z = sysg.energies[e] + 1j * sysg.eta
     nb, bs = sysg.nb, sysg.bs
     I = np.eye(bs)
@@ -104,7 +107,7 @@ def _M_blocks(sysg, e):
 
 
 def lead_blocks(sysg, e):
-    """(m, n, n') of the left and right leads: the edge cells of M - B^R_scatt repeated
+    """(m, n, n') of Eq. 4 for the left and right leads (Sec. 3.1): the edge cells of M - B^R_scatt repeated
     periodically.  Left lead: m = M_11, n = M_21, n' = M_12.  Right: m = M_NN,
     n = M_{N-1,N}, n' = M_{N,N-1}."""
     d, u, l = _M_blocks(sysg, e)
@@ -161,7 +164,8 @@ def assemble_g(sysg, e, tol=1e-14, maxit=100):
 
 
 def selected_blocks(X, nb, bs):
-    """Diagonal, upper (i,i+1) and lower (i+1,i) blocks of a dense matrix."""
+    """Diagonal, upper (i,i+1) and lower (i+1,i) blocks of a dense matrix: the selected blocks of
+    X that Sec. 2 asks for."""
     diag = np.stack([X[i * bs:(i + 1) * bs, i * bs:(i + 1) * bs] for i in range(nb)])
     if nb > 1:
         upper = np.stack([X[i * bs:(i + 1) * bs, (i + 1) * bs:(i + 2) * bs] for i in range(nb - 1)])
@@ -216,7 +220,8 @@ def assemble_w(wsys, e):
 
 
 def solve_w(wsys, e, symmetrize=True):
-    """W^R = (I - V P^R)^{-1} V and W^<> = X^R (V P^<> V^H) X^R^H, selected blocks."""
+    """W^R = (I - V P^R)^{-1} V and W^<> = X^R (V P^<> V^H) X^R^H, selected blocks (Table 2, right
+    column; no contacts)."""
     M, BL, BG, V = assemble_w(wsys, e)
     XR = np.linalg.inv(M)
     WR = XR @ V
@@ -239,7 +244,9 @@ def solve_w(wsys, e, symmetrize=True):
 # ----------------------------------------------------------------------------------------------
 
 def transmission(sysg, e):
-    """Landauer transmission T = Tr[Gam_L G^R_1N Gam_R G^A_N1] with Gam_c = i(B^R_c - B^R_c^H)."""
+    """Landauer transmission T = Tr[Gam_L G^R_1N Gam_R G^A_N1] with Gam_c = i(B^R_c - B^R_c^H).
+    Not a step of the method: a physical observable of the G system (Table 2) that the pins
+    compare with closed forms and with the currents."""
     M, _, _, o = assemble_g(sysg, e)
     bs = sysg.bs
     XR = np.linalg.inv(M)
@@ -251,7 +258,8 @@ def transmission(sysg, e):
 
 def bond_currents(H_upper, L_upper):
     """Bond current between cells i and i+1: I_i = 2 Re Tr[H_{i,i+1} G^<_{i+1,i}] with
-    G^<_{i+1,i} = -(G^<_{i,i+1})^H (anti-Hermiticity)."""
+    G^<_{i+1,i} = -(G^<_{i,i+1})^H (anti-Hermiticity, Sec. 4.2).  Not a step of the method: an
+    observable the pins use to check the off-diagonal lesser blocks."""
     out = []
     for i in range(H_upper.shape[0]):
         Glow = -np.conj(L_upper[i].T)
@@ -264,7 +272,8 @@ def bond_currents(H_upper, L_upper):
 # ----------------------------------------------------------------------------------------------
 
 def _band_storage(A_diag, A_upper, A_lower, transpose):
-    """LAPACK band storage of a BT matrix (or its transpose) with l = u = 2 bs - 1."""
+    """LAPACK band storage of a BT matrix (or its transpose) with l = u = 2 bs - 1 (the BT
+    structure of Eq. 1 as a band matrix)."""
     nb, bs = A_diag.shape[0], A_diag.shape[1]
     n = nb * bs
     kl = ku = 2 * bs - 1
@@ -286,7 +295,7 @@ def _band_storage(A_diag, A_upper, A_lower, transpose):
 
 
 def block_rows_banded(A_diag, A_upper, A_lower, rows):
-    """Full block rows `rows` of A^{-1} for a BT matrix A, by banded LU of A^T (LAPACK gbsv):
+    """Full block rows `rows` of A^{-1} for a BT matrix A (Eq. 1), by banded LU of A^T (LAPACK gbsv):
     row block i of A^{-1} is (A^{-T} E_i)^T.  Returns {i: [bs, n] array}."""
     nb, bs = A_diag.shape[0], A_diag.shape[1]
     n = nb * bs
@@ -299,7 +308,8 @@ def block_rows_banded(A_diag, A_upper, A_lower, rows):
 
 
 def solve_g_sampled(sysg, e, blocks, symmetrize=True, tol=1e-14, maxit=100):
-    """Selected blocks at energy index e for block indices `blocks` without a dense inverse:
+    """Selected blocks (Sec. 2, Eq. 1 and Table 2) at energy index e for block indices `blocks`
+    without a dense inverse:
     rows i and i+1 of X^R by banded LU, then X^<>_{ij} = X^R[i,:] B^<> X^R[j,:]^H with the
     (block-diagonal) B^<> of the G system.  Returns {i: dict(R_diag, R_upper, R_lower, L_diag,
     L_upper, G_diag, G_upper)} (upper/lower entries only when i+1 < N)."""
@@ -373,7 +383,8 @@ def solve_g_sampled(sysg, e, blocks, symmetrize=True, tol=1e-14, maxit=100):
 # ----------------------------------------------------------------------------------------------
 
 def w_extended_chain(wsys, e, n_lead):
-    """BT blocks of V, P^R, P^<, P^> over n_lead lead cells, the device, n_lead lead cells: each
+    """BT blocks of V, P^R, P^<, P^> (Table 2, right column) over n_lead lead cells, the device,
+    n_lead lead cells (Sec. 3.1: periodic leads): each
     lead repeats the device's edge cell and its coupling to the next cell inward.  Returns
     (V_d, V_u, PR_d, PR_u, PR_l, PL_d, PL_u, PG_d, PG_u) for the whole chain."""
     nb = wsys.nb
@@ -394,6 +405,8 @@ def w_extended_chain(wsys, e, n_lead):
 
 
 def _w_chain_dense(wsys, e, n_lead):
+    """Dense M = I - V P^R, B^<> = V P^<> V^H and V (Table 2, right column) of the chain of
+    w_extended_chain."""
     Vd, Vu, PRd, PRu, PRl, PLd, PLu, PGd, PGu = w_extended_chain(wsys, e, n_lead)
     V = bt_dense(Vd, Vu)
     PR = bt_dense(PRd, PRu, PRl)
@@ -404,7 +417,8 @@ def _w_chain_dense(wsys, e, n_lead):
 
 
 def w_lead_fold(m, n, n_prime, b, c, tol=1e-14, maxit=200):
-    """Retarded and lesser/greater boundary blocks of one lead (see the reading above).
+    """Retarded and lesser/greater boundary blocks of one lead (Sec. 3.1: Eq. 4 for x^R, the Stein
+    equation of Eq. 7 for w^<>; see the reading above).
     Returns (B^R_OBC, B^<>_OBC, x^R, w^<>)."""
     x, _, ok = sancho_rubio(m, n, n_prime, tol, maxit)
     if not ok:
@@ -417,9 +431,9 @@ def w_lead_fold(m, n, n_prime, b, c, tol=1e-14, maxit=200):
 
 
 def solve_w_contacts(wsys, e, symmetrize=True):
-    """Selected blocks of W^R = X^R V and W^<> = X^<> for the W system with both leads attached
-    (the reading above), by folding the leads into the edge cells and a dense solve of the
-    device.  W^R's edge blocks include V's coupling to the first lead cells through
+    """Selected blocks of W^R = X^R V and W^<> = X^<> (Table 2, right column) for the W system with
+    both leads attached (Sec. 3.1, Eq. 4 and 7; the reading above), by folding the leads into the
+    edge cells and a dense solve of the device.  W^R's edge blocks include V's coupling to the first lead cells through
     X^R_{0,-1} = -X^R_{00} M_{0,-1} x^R_L (and the mirror on the right)."""
     nb, bs = wsys.nb, wsys.bs
     K = 4   # lead cells in the assembly window: cell 1 and cell (K + nb + 2) are bulk lead cells
@@ -472,7 +486,8 @@ def solve_w_contacts(wsys, e, symmetrize=True):
 def solve_w_long_leads(wsys, e, n_lead, symmetrize=True):
     """The same selected blocks from a finite chain with n_lead lead cells on each side, solved
     densely without any boundary condition: converges to solve_w_contacts as n_lead grows (the
-    absorbing part of P^R damps the leads).  The pin of the folding."""
+    absorbing part of P^R damps the leads).  The pin of the folding (Sec. 3.1: the boundary
+    blocks stand for semi-infinite leads)."""
     nb, bs = wsys.nb, wsys.bs
     M, BL, BG, V = _w_chain_dense(wsys, e, n_lead)
     XR = np.linalg.inv(M)
