@@ -2,17 +2,17 @@
  * bt_selinv.h -- C ABI of the GB300 (sm_103a) block-tridiagonal selected-inversion library.
  *
  * The library computes, for a batch of energies, the selected blocks of the solution of the
- * quadratic system of Sec. 2, Eq. 1 of "QuaTrEx: ... NEGF+scGW" (arXiv 2508.19138):
+ * quadratic system of Sec. 3, Eq. 1 of "QuaTrEx: ... NEGF+scGW" (arXiv 2508.19138):
  *
  *     (M - B^R) X^<> (M - B^R)^H = B^<>,      X^R = (M - B^R)^{-1} = M~^{-1},
  *
  * with the quantities of Table 2:
  *   electrons (BT_SYS_G):          M = E S - H,  B^R = Sigma^R,   B^<> = Sigma^<>
  *   screened Coulomb (BT_SYS_W):   M = I,        B^R = V P^R,     B^<> = V P^<> V^H
- * plus the open-boundary blocks B_OBC of Sec. 3.1 (Eq. 4, Sancho-Rubio decimation; lesser /
+ * plus the open-boundary blocks B_OBC of Sec. 4.2 (Eq. 4, Sancho-Rubio decimation; lesser /
  * greater by fluctuation-dissipation).  The solver is the recursive Green's function method
- * of Sec. 3.2.2 (forward pass Eq. 8-9, backward pass Eq. 10-11), with the symmetrisation of
- * Sec. 4.2.  Outputs are the diagonal and first off-diagonal blocks.
+ * of Sec. 4.3.2 (forward pass Eq. 9-10, backward pass Eq. 11-12), with the symmetrisation of
+ * Sec. 5.2.  Outputs are the diagonal and first off-diagonal blocks.
  *
  * Conventions shared by every entry point:
  *   - complex numbers are complex128: two doubles (re, im), the layout of cuDoubleComplex,
@@ -88,7 +88,7 @@ typedef struct {
  * upper (i,i+1) and lower (i+1,i) blocks.  A NULL pointer means "do not write".
  * layout BT_LAYOUT_DIAGVEC writes only the diagonal entries of the diagonal blocks,
  * [n_energies][nb][bs] (densities / local DOS), and requires upper = lower = NULL.
- * layout BT_LAYOUT_PACKED_UPPER (lesser / greater outputs with symmetrize = 1 only; Sec. 4.2:
+ * layout BT_LAYOUT_PACKED_UPPER (lesser / greater outputs with symmetrize = 1 only; Sec. 5.2:
  * anti-Hermitian quantities stored by their upper triangle) writes each diagonal block
  * X_ii = -X_ii^H as its upper triangle, row by row: [n_energies][nb][bs (bs + 1) / 2], entry
  * (r, c >= r) at r bs - r (r - 1) / 2 + (c - r), the lower triangle being -conj of it; upper
@@ -110,7 +110,7 @@ typedef struct {
                           cores with exact fp32 accumulation; inversions, decimation and
                           symmetrisation stay FP64                                              */
   int split_slices;    /* BT_SPLIT: slices per operand (0 = default 6, range 2..8)            */
-  int symmetrize;      /* 1: lesser/greater diagonal blocks returned as (X - X^H)/2 (Sec. 4.2) */
+  int symmetrize;      /* 1: lesser/greater diagonal blocks returned as (X - X^H)/2 (Sec. 5.2) */
   int obc;             /* 1: Sancho-Rubio contacts on both ends (G only, nb >= 2)             */
   double eta;          /* G: z = E + i eta                                                     */
   double kT;           /* contact temperature (energy units of H)                              */
@@ -119,7 +119,7 @@ typedef struct {
   double decim_tol;    /* decimation stops when max|a|,max|b| <= decim_tol * max|n| (<=0: 1e-14) */
   int decim_maxit;     /* decimation iteration cap (<= 0: 100)                                 */
   size_t hbm_budget_bytes; /* 0 = unlimited; otherwise the workspace must fit                  */
-  /* Contact memoization (Sec. 4.3): the surface functions of every solved energy are kept in
+  /* Contact memoization (Sec. 5.3): the surface functions of every solved energy are kept in
    * the workspace (memo_capacity energies, oldest evicted first).  A later solve of the same
    * energy starts the fixed-point iteration x <- (m - n x n')^{-1} (Eq. 5) from the kept value
    * and runs at most memo_nfpi iterations; leads that do not converge within them (judged from
@@ -164,7 +164,9 @@ BT_API bt_status bt_selinv_workspace_bytes(const bt_selinv_desc* desc, size_t* b
  * (a cudaStream_t; NULL = default stream).  On success *out owns the workspace. */
 BT_API bt_status bt_selinv_create(const bt_selinv_desc* desc, void* cuda_stream, bt_ctx** out);
 
-/* Selected inversion for n_energies energies (processed in chunks of max_energies).
+/* Selected inversion for n_energies energies (processed in chunks of max_energies): the
+ * selected blocks of X^R, X^<, X^> of Sec. 3, Eq. 1 with the quantities of Table 2, by the RGF
+ * passes of Sec. 4.3.2 (Eq. 9-12) and, with desc->obc, the contacts of Sec. 4.2 (Eq. 4).
  *   H       G: Hamiltonian H (BLOCKS, Hermitian or general, shared or per energy)
  *           W: bare Coulomb V (BLOCKS, Hermitian, shared)
  *   S       G: overlap (NULL = identity); W: must be NULL
@@ -191,13 +193,18 @@ BT_API bt_status bt_selinv_solve_host(bt_ctx* ctx, const bt_bt* H, const bt_bt* 
                                int n_energies, const bt_bt_out* outR, const bt_bt_out* outL,
                                const bt_bt_out* outG, int* status_host);
 
+/* Counters of ctx (host struct *out).  In graph mode it first synchronises ctx's stream to
+ * fold in the device-side iteration counts.  BT_ERR_INVALID_ARG for NULL arguments. */
 BT_API bt_status bt_selinv_get_stats(const bt_ctx* ctx, bt_stats* out);
+/* Waits for ctx's work, frees its workspace and graphs; NULL is a no-op. */
 BT_API bt_status bt_selinv_destroy(bt_ctx* ctx);
 /* Text of the last error recorded on ctx (or of the last failed create when ctx is NULL). */
 BT_API const char* bt_selinv_last_error(const bt_ctx* ctx);
 
 /* ---------------------------------------------------------------------------------------
- * Serving: solves of different device sizes arriving over time (G system).
+ * Serving: solves of different device sizes arriving over time (G system).  The paper has no
+ * counterpart (its energies are distributed over ranks, Sec. 4.4); each request is the solve
+ * of bt_selinv_solve (Sec. 3, Eq. 1; Sec. 4.3.2).
  *   - bt_server_create allocates ONE device arena of hbm_budget_bytes; each admitted request
  *     borrows its workspace (as bt_selinv_workspace_bytes for a chunk of
  *     max_energies_per_chunk energies) from it; requests are admitted in arrival order as soon
@@ -256,7 +263,7 @@ BT_API bt_status bt_server_destroy(bt_server* srv);
 enum { BT_OP_N = 0, BT_OP_C = 1 };  /* op(X) = X or X^H (conjugate transpose) */
 
 /* C[b] = alpha * op(A[b]) * op(B[b]) + beta * C[b] for b < batch, complex128, FP64 arithmetic
- * (the dense products of Eq. 8-11).  op(A) is m x k, op(B) is k x n, C is m x n, all row-major
+ * (the dense products of Eq. 9-12).  op(A) is m x k, op(B) is k x n, C is m x n, all row-major
  * with leading dimensions lda/ldb/ldc (elements); strideX is the element distance between
  * batch entries (0 = the same matrix for every batch entry).  beta = 0 does not read C.
  * C must not alias A or B. */
@@ -281,7 +288,7 @@ BT_API bt_status bt_split_zgemm_batched(int m, int n, int k, double alpha_re, do
                                  void* stream);
 
 /* In-place inverse of `batch` n x n complex128 matrices (A + b*strideA), Gauss-Jordan
- * elimination with partial (row) pivoting -- the block LU of the forward pass (Eq. 8) carried
+ * elimination with partial (row) pivoting -- the block LU of the forward pass (Eq. 9) carried
  * to the full inverse; pivots chosen by max |re| + |im|, first index on ties.
  * info_device[b] = 0, or BT_ERR_SINGULAR / BT_ERR_NONFINITE (matrix b is then undefined).
  * `workspace` must hold bt_zinv_workspace_bytes(n, batch) bytes (may be 0 for small n). */
@@ -309,7 +316,8 @@ BT_API bt_status bt_zinv_batched_noalloc(int n, void* A, long long strideA, int 
 /* Surface Green's function of semi-infinite leads, x = (m - n x n')^{-1} (Eq. 4), by
  * Sancho-Rubio decimation for `batch` independent leads (m, n, n' each [batch][bs][bs]).
  * Writes x [batch][bs][bs] and the boundary block sigma = n x n' [batch][bs][bs];
- * iters_device[b] = iterations used, info_device[b] = 0 / BT_ERR_NOT_CONVERGED / _SINGULAR.
+ * iters_device[b] = iterations used, info_device[b] = 0 / BT_ERR_NOT_CONVERGED / _SINGULAR /
+ * _NONFINITE (x and sigma of lead b are then undefined).
  * `workspace` must hold bt_decimate_workspace_bytes(bs, batch) bytes. */
 BT_API bt_status bt_decimate_workspace_bytes(int bs, int batch, size_t* bytes);
 BT_API bt_status bt_decimate_batched(int bs, int batch, const void* m, const void* n, const void* n_prime,

@@ -18,7 +18,7 @@ __all__ = [
 
 
 def fermi(E, mu, kT):
-    """Fermi-Dirac occupation 1 / (1 + exp((E - mu)/kT)) of a contact (Sec. 3.1: the lesser/greater
+    """Fermi-Dirac occupation 1 / (1 + exp((E - mu)/kT)) of a contact (Sec. 4.2: the lesser/greater
     boundary blocks carry the contacts' occupations), evaluated without overflow."""
     x = (np.asarray(E, dtype=np.float64) - mu) / kT
     ex = np.exp(-np.abs(x))
@@ -107,7 +107,7 @@ def _M_blocks(sysg, e):
 
 
 def lead_blocks(sysg, e):
-    """(m, n, n') of Eq. 4 for the left and right leads (Sec. 3.1): the edge cells of M - B^R_scatt repeated
+    """(m, n, n') of Eq. 4 for the left and right leads (Sec. 4.2): the edge cells of M - B^R_scatt repeated
     periodically.  Left lead: m = M_11, n = M_21, n' = M_12.  Right: m = M_NN,
     n = M_{N-1,N}, n' = M_{N,N-1}."""
     d, u, l = _M_blocks(sysg, e)
@@ -139,7 +139,7 @@ def obc_self_energies(sysg, e, tol=1e-14, maxit=100):
 
 def assemble_g(sysg, e, tol=1e-14, maxit=100):
     """Dense M~ = E S - H - Sigma^R_scatt - Sigma^R_OBC and B^<> = Sigma^<>_scatt + Sigma^<>_OBC
-    (Table 2; the element-wise G assembly of Sec. 3.2.1)."""
+    (Table 2; the element-wise G assembly of Sec. 4.3.1)."""
     d, u, l = _M_blocks(sysg, e)
     nb, bs = sysg.nb, sysg.bs
     M = bt_dense(d, u, l)
@@ -165,7 +165,7 @@ def assemble_g(sysg, e, tol=1e-14, maxit=100):
 
 def selected_blocks(X, nb, bs):
     """Diagonal, upper (i,i+1) and lower (i+1,i) blocks of a dense matrix: the selected blocks of
-    X that Sec. 2 asks for."""
+    X that Sec. 3 asks for."""
     diag = np.stack([X[i * bs:(i + 1) * bs, i * bs:(i + 1) * bs] for i in range(nb)])
     if nb > 1:
         upper = np.stack([X[i * bs:(i + 1) * bs, (i + 1) * bs:(i + 2) * bs] for i in range(nb - 1)])
@@ -177,7 +177,7 @@ def selected_blocks(X, nb, bs):
 
 
 def symmetrize_lesser(X):
-    """Sec. 4.2: X_ij <- (X_ij - X_ji^*)/2 on the whole matrix."""
+    """Sec. 5.2: X_ij <- (X_ij - X_ji^*)/2 on the whole matrix."""
     return 0.5 * (X - X.conj().T)
 
 
@@ -205,7 +205,7 @@ def solve_g(sysg, e, symmetrize=True, tol=1e-14, maxit=100):
 # ----------------------------------------------------------------------------------------------
 
 def assemble_w(wsys, e):
-    """Dense M~ = I - V P^R and B^<> = V P^<> V^H (Sec. 3.2.1, W assembly)."""
+    """Dense M~ = I - V P^R and B^<> = V P^<> V^H (Sec. 4.3.1, W assembly)."""
     nb, bs = wsys.nb, wsys.bs
     V = bt_dense(wsys.V_diag, wsys.V_upper)
     PRd, PRu, PRl, PLd, PLu, PGd, PGu = wsys.P_blocks(e)
@@ -240,7 +240,7 @@ def solve_w(wsys, e, symmetrize=True):
 
 
 # ----------------------------------------------------------------------------------------------
-# Observables (Sec. 3.4) used as invariants
+# Observables (Sec. 4.5) used as invariants
 # ----------------------------------------------------------------------------------------------
 
 def transmission(sysg, e):
@@ -258,7 +258,7 @@ def transmission(sysg, e):
 
 def bond_currents(H_upper, L_upper):
     """Bond current between cells i and i+1: I_i = 2 Re Tr[H_{i,i+1} G^<_{i+1,i}] with
-    G^<_{i+1,i} = -(G^<_{i,i+1})^H (anti-Hermiticity, Sec. 4.2).  Not a step of the method: an
+    G^<_{i+1,i} = -(G^<_{i,i+1})^H (anti-Hermiticity, Sec. 5.2).  Not a step of the method: an
     observable the pins use to check the off-diagonal lesser blocks."""
     out = []
     for i in range(H_upper.shape[0]):
@@ -308,7 +308,7 @@ def block_rows_banded(A_diag, A_upper, A_lower, rows):
 
 
 def solve_g_sampled(sysg, e, blocks, symmetrize=True, tol=1e-14, maxit=100):
-    """Selected blocks (Sec. 2, Eq. 1 and Table 2) at energy index e for block indices `blocks`
+    """Selected blocks (Sec. 3, Eq. 1 and Table 2) at energy index e for block indices `blocks`
     without a dense inverse:
     rows i and i+1 of X^R by banded LU, then X^<>_{ij} = X^R[i,:] B^<> X^R[j,:]^H with the
     (block-diagonal) B^<> of the G system.  Returns {i: dict(R_diag, R_upper, R_lower, L_diag,
@@ -365,7 +365,7 @@ def solve_g_sampled(sysg, e, blocks, symmetrize=True, tol=1e-14, maxit=100):
 
 
 # ----------------------------------------------------------------------------------------------
-# W system with contacts (Sec. 3.1: retarded OBC by Eq. 4, lesser/greater OBC by the discrete
+# W system with contacts (Sec. 4.2: retarded OBC by Eq. 4, lesser/greater OBC by the discrete
 # Lyapunov equation of Eq. 7).  Groundwork for the W contacts: the CUDA path does not solve W
 # with contacts.
 #
@@ -378,13 +378,13 @@ def solve_g_sampled(sysg, e, blocks, symmetrize=True, tol=1e-14, maxit=100):
 #     y = n x^R c,   a = x^R n,   q = x^R (b - y + y^H) x^R^H
 #     w^<> = q + a w^<> a^H                              (Eq. 7; a Stein equation)
 #     B^R_OBC = n x^R n',   B^<>_OBC = n w^<> n^H - (y - y^H)
-# — the fixed point of the forward recursion of Eq. 8-9 run along the lead from infinity.  The
+# — the fixed point of the forward recursion of Eq. 9-10 run along the lead from infinity.  The
 # edge cells' own blocks of M and B include the products with the first lead cell.
 # ----------------------------------------------------------------------------------------------
 
 def w_extended_chain(wsys, e, n_lead):
     """BT blocks of V, P^R, P^<, P^> (Table 2, right column) over n_lead lead cells, the device,
-    n_lead lead cells (Sec. 3.1: periodic leads): each
+    n_lead lead cells (Sec. 4.2: periodic leads): each
     lead repeats the device's edge cell and its coupling to the next cell inward.  Returns
     (V_d, V_u, PR_d, PR_u, PR_l, PL_d, PL_u, PG_d, PG_u) for the whole chain."""
     nb = wsys.nb
@@ -417,7 +417,7 @@ def _w_chain_dense(wsys, e, n_lead):
 
 
 def w_lead_fold(m, n, n_prime, b, c, tol=1e-14, maxit=200):
-    """Retarded and lesser/greater boundary blocks of one lead (Sec. 3.1: Eq. 4 for x^R, the Stein
+    """Retarded and lesser/greater boundary blocks of one lead (Sec. 4.2: Eq. 4 for x^R, the Stein
     equation of Eq. 7 for w^<>; see the reading above).
     Returns (B^R_OBC, B^<>_OBC, x^R, w^<>)."""
     x, _, ok = sancho_rubio(m, n, n_prime, tol, maxit)
@@ -432,7 +432,7 @@ def w_lead_fold(m, n, n_prime, b, c, tol=1e-14, maxit=200):
 
 def solve_w_contacts(wsys, e, symmetrize=True):
     """Selected blocks of W^R = X^R V and W^<> = X^<> (Table 2, right column) for the W system with
-    both leads attached (Sec. 3.1, Eq. 4 and 7; the reading above), by folding the leads into the
+    both leads attached (Sec. 4.2, Eq. 4 and 7; the reading above), by folding the leads into the
     edge cells and a dense solve of the device.  W^R's edge blocks include V's coupling to the first lead cells through
     X^R_{0,-1} = -X^R_{00} M_{0,-1} x^R_L (and the mirror on the right)."""
     nb, bs = wsys.nb, wsys.bs
@@ -486,7 +486,7 @@ def solve_w_contacts(wsys, e, symmetrize=True):
 def solve_w_long_leads(wsys, e, n_lead, symmetrize=True):
     """The same selected blocks from a finite chain with n_lead lead cells on each side, solved
     densely without any boundary condition: converges to solve_w_contacts as n_lead grows (the
-    absorbing part of P^R damps the leads).  The pin of the folding (Sec. 3.1: the boundary
+    absorbing part of P^R damps the leads).  The pin of the folding (Sec. 4.2: the boundary
     blocks stand for semi-infinite leads)."""
     nb, bs = wsys.nb, wsys.bs
     M, BL, BG, V = _w_chain_dense(wsys, e, n_lead)

@@ -1,7 +1,7 @@
-// Element-wise kernels of the sweep: assembly of M~ and B^<> blocks (Sec. 3.2.1, Table 2),
-// the lesser/greater boundary blocks by fluctuation-dissipation (Sec. 3.1), the anti-Hermitian
-// corrections (y - y^H), (Z - Z^H) of Eq. 9 and 11, the projection onto anti-Hermitian blocks
-// and the symmetrised write-out of Sec. 4.2 (full blocks, diagonal entries or packed upper
+// Element-wise kernels of the sweep: assembly of M~ and B^<> blocks (Sec. 4.3.1, Table 2),
+// the lesser/greater boundary blocks by fluctuation-dissipation (Sec. 4.2), the anti-Hermitian
+// corrections (y - y^H), (Z - Z^H) of Eq. 10 and 12, the projection onto anti-Hermitian blocks
+// and the symmetrised write-out of Sec. 5.2 (full blocks, diagonal entries or packed upper
 // triangles).
 // All are memory-bound grid-stride loops over (element, batch entry) with coalesced accesses
 // along the row-major block; transposed reads (X^H) go through the L1/L2 of the same block.
@@ -133,7 +133,7 @@ __global__ void axpby_kernel(long long n, double alpha, const zd* __restrict__ x
   }
 }
 
-// Packed upper triangle of (X - X^H)/2 per block (Sec. 4.2: the anti-Hermitian lesser / greater
+// Packed upper triangle of (X - X^H)/2 per block (Sec. 5.2: the anti-Hermitian lesser / greater
 // blocks stored by their upper triangle): row r holds columns r..bs-1, starting at
 // r bs - r (r - 1) / 2; bs (bs + 1) / 2 entries per block.
 __global__ void write_packed_kernel(int bs, int nblk, const zd* __restrict__ src, long long s_blk, long long s_e,

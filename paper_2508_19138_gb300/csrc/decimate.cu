@@ -1,4 +1,4 @@
-// Sancho-Rubio decimation for the retarded open-boundary condition (Sec. 3.1, Eq. 4):
+// Sancho-Rubio decimation for the retarded open-boundary condition (Sec. 4.2, Eq. 4):
 //     x = (m - n x n')^{-1}
 // for a batch of independent semi-infinite leads (cells with diagonal block m, coupling n from a
 // cell to the next one away from the device and n' back).  Every iteration removes every second

@@ -1,21 +1,21 @@
-// Context, workspace and the recursive Green's function sweeps (Sec. 3.2.2) behind the C ABI.
+// Context, workspace and the recursive Green's function sweeps (Sec. 4.3.2) behind the C ABI.
 //
 // For a chunk of Ec energies every step below is ONE batched launch over the chunk (the
-// energies are the data-parallel axis, Sec. 3.3 / 4.4):
-//   a1  assembly of M~ = M - B^R_scatt - B^R_OBC and B^<> (Table 2, Sec. 3.2.1);
+// energies are the data-parallel axis, Sec. 4.4 / 5.4):
+//   a1  assembly of M~ = M - B^R_scatt - B^R_OBC and B^<> (Table 2, Sec. 4.3.1);
 //       W system: V P^R and V P^<> V^H as block-tridiagonal products
 //   a2  contact decimation (Eq. 4) for the 2 Ec leads, fluctuation-dissipation for B^<>_OBC
-//   a3  forward pass, Eq. 8 (x^R_i) and Eq. 9 (x^<>_i, with y_i = M~_{i,i-1} x^R_{i-1} B_{i-1,i})
-//   a4  backward pass, Eq. 10 (X^R_i), Eq. 11 (X^<>_i with Y_i, Z_i); first off-diagonal blocks
+//   a3  forward pass, Eq. 9 (x^R_i) and Eq. 10 (x^<>_i, with y_i = M~_{i,i-1} x^R_{i-1} B_{i-1,i})
+//   a4  backward pass, Eq. 11 (X^R_i), Eq. 12 (X^<>_i with Y_i, Z_i); first off-diagonal blocks
 //         X^R_{i,i+1} = -x^R_i M~_{i,i+1} X^R_{i+1},   X^R_{i+1,i} = -X^R_{i+1} M~_{i+1,i} x^R_i
 //         X^<>_{i,i+1} = -x^R_i M~_{i,i+1} X^<>_{i+1} - x^<>_i (X^R_{i+1} M~_{i+1,i})^H
 //                        + x^R_i B^<>_{i,i+1} (X^R_{i+1})^H
 //       W system: W^R = X^R V on the selected blocks (needs X^R_{i,i+-2})
-//   a5  symmetrised write-out of the diagonal lesser/greater blocks (Sec. 4.2), as full blocks
+//   a5  symmetrised write-out of the diagonal lesser/greater blocks (Sec. 5.2), as full blocks
 //       or packed upper triangles
 // All sweep products go through prod(), which runs the FP64 DFMA kernel or, with BT_SPLIT, the
 // sliced bf16 tensor-core product; with symmetrised outputs the lesser/greater sandwiches come
-// out exactly anti-Hermitian (Sec. 4.2 symmetry kept inside the sweep) and Z_i of Eq. 11 is
+// out exactly anti-Hermitian (Sec. 5.2 symmetry kept inside the sweep) and Z_i of Eq. 12 is
 // formed from the first term of X^<>_{i,i+1}.  The inversions and the decimation run on the
 // FP64 engine, or on a sliced one with split_scope = 1.  In graph mode a chunk's launches are
 // captured once into a CUDA graph and replayed (run_chunk_graph).
@@ -244,7 +244,7 @@ bt_status set_err(bt_ctx* c, bt_status s, const char* what) {
 
 // C = alpha op(A) op(B) + beta C for the chunk (bs x bs blocks).  antiherm: the exact result is
 // anti-Hermitian (a lesser / greater sandwich x B x^H with B = -B^H, plus an anti-Hermitian C):
-// with symmetrised outputs (Sec. 4.2) the result is made exactly anti-Hermitian — the FP64 engine
+// with symmetrised outputs (Sec. 5.2) the result is made exactly anti-Hermitian — the FP64 engine
 // computes only the blocks' upper half and mirrors it (about half of the product's FP64 work),
 // the sliced engine projects its full result.
 // `units`: block products of the paper's formulation that this product stands for (the model
@@ -275,7 +275,7 @@ bt_status inv(bt_ctx* c, int Ec, zd* A, long long sA, int* info) {
   return bt::zinv(c->st, bs, A, sA, Ec, info, c->inv_ws, c->inv_bytes, nullptr, &c->eng_kept);
 }
 
-// Forward (Eq. 8-9) and backward (Eq. 10-11) passes for one chunk.  x^R, x^<> live in
+// Forward (Eq. 9-10) and backward (Eq. 11-12) passes for one chunk.  x^R, x^<> live in
 // c->xR/xL/xG and are overwritten by X^R, X^<> in the backward pass.
 bt_status run_sweep(Sweep& s, int* status) {
   bt_ctx* c = s.c;
@@ -352,7 +352,7 @@ bt_status run_sweep(Sweep& s, int* status) {
         if (bu.valid()) BT_TRY(prod(c, Ec, 1.0, X(xR(i), NB2), bu, 0.0, XB[w], B2)); // x^R_i B_{i,i+1}
       }
     }
-    BT_TRY(prod(c, Ec, -1.0, X(XRu, esu), X(W1, B2), 1.0, xR(i), NB2));            // X^R_i (Eq. 10)
+    BT_TRY(prod(c, Ec, -1.0, X(XRu, esu), X(W1, B2), 1.0, xR(i), NB2));            // X^R_i (Eq. 11)
     for (int w = 0; w < 2; ++w) {
       if (!need[w]) continue;
       zd* xLi = xLG(w, i);
@@ -714,7 +714,7 @@ bt_status solve_chunk_g(bt_ctx* c, const bt_bt* H, const bt_bt* S, const bt_bt* 
     const int* dec_mask = nullptr;
     std::vector<int> slots;
     if (d.obc_memo) {
-      // Sec. 4.3: energies solved before start the fixed point (Eq. 5) from their kept surface
+      // Sec. 5.3: energies solved before start the fixed point (Eq. 5) from their kept surface
       // functions; leads that do not converge within memo_nfpi iterations are decimated.
       std::vector<int> run(2 * Ec, 0);
       slots.assign(Ec, -1);
@@ -840,7 +840,7 @@ bt_status solve_chunk_g(bt_ctx* c, const bt_bt* H, const bt_bt* S, const bt_bt* 
 
 
 // W system (Table 2, right column): M~ = I - V P^R, B^<> = V P^<> V^H as block-tridiagonal
-// products (Sec. 3.2.1; exact when the cell is longer than 3 r_cut), the RGF sweep on them, and
+// products (Sec. 4.3.1; exact when the cell is longer than 3 r_cut), the RGF sweep on them, and
 // W^R = X^R V on the selected blocks (X^R_{i,i+-2} from the backward pass).  W^<> = X^<>.
 bt_status solve_chunk_w(bt_ctx* c, const bt_bt* V, const bt_bt* PR, const bt_bt* PL, const bt_bt* PG, long long e0,
                         int Ec, const bt_bt_out* oR, const bt_bt_out* oL, const bt_bt_out* oG, int* status) {
@@ -928,7 +928,7 @@ bt_status solve_chunk_w(bt_ctx* c, const bt_bt* V, const bt_bt* PR, const bt_bt*
       BT_TRY(prod(c, Ec, 1.0, W(c->Td + i * B2, NB2), Vh(i, i), 0.0, bd, NB2));
       if (i > 0) BT_TRY(prod(c, Ec, 1.0, W(c->Tl + (i - 1) * B2, N1B2), Vh(i, i - 1), 1.0, bd, NB2));
       if (i + 1 < N) BT_TRY(prod(c, Ec, 1.0, W(c->Tu + i * B2, N1B2), Vh(i, i + 1), 1.0, bd, NB2));
-      // B^<>_ii is anti-Hermitian as a sum of three products: made exactly so (Sec. 4.2) before the
+      // B^<>_ii is anti-Hermitian as a sum of three products: made exactly so (Sec. 5.2) before the
       // sweep's anti-Hermitian products take it as an operand
       if (c->d.symmetrize) BT_TRY(bt::antiherm_project(c->st, bs, Ec, bd, NB2));
       if (i + 1 < N) {

@@ -1,5 +1,5 @@
 // Batched complex128 GEMM on the FP64 pipe (DFMA): the dense block products of the RGF
-// forward / backward passes (Sec. 3.2.2, Eq. 8-11) and of the decimation (Eq. 4).
+// forward / backward passes (Sec. 4.3.2, Eq. 9-12) and of the decimation (Eq. 4).
 //
 // GB300 note: the FP64 pipe of this part issues about 2 DFMA per clock per SM (measured
 // ~1.2 TFLOP/s for the whole GPU; the FP64 mma.sync path measured ~1.05 TFLOP/s), so this
@@ -38,7 +38,7 @@ struct Shape {
 };
 
 // TRI: C (square, n x n) is known to be anti-Hermitian (C_ji = -conj(C_ij)) in exact arithmetic,
-// e.g. the sandwiches x^R B^<> x^R^H of Eq. 9 and 11: only the tiles on and above the diagonal
+// e.g. the sandwiches x^R B^<> x^R^H of Eq. 10 and 12: only the tiles on and above the diagonal
 // are computed (blockIdx.x runs over them row by row), every tile above the diagonal also
 // writes its mirror image -(tile)^H below it (staged through shared memory so that the
 // transposed store stays coalesced), and the diagonal tiles are made exactly anti-Hermitian.

@@ -1,5 +1,5 @@
 // Batched in-place inversion of complex128 blocks: the x^R_i = (Schur complement)^{-1} of the
-// RGF forward pass (Sec. 3.2.2, Eq. 8) and the g = e^{-1} of the decimation (Eq. 4).
+// RGF forward pass (Sec. 4.3.2, Eq. 9) and the g = e^{-1} of the decimation (Eq. 4).
 //
 // Algorithm: Gauss-Jordan elimination with partial (row) pivoting, i.e. the block LU of the
 // pivot column carried to the full inverse in one sweep.  Pivot = max |re| + |im| over the

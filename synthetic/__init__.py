@@ -3,7 +3,7 @@
 This module builds *inputs only*: Hamiltonian / Coulomb blocks, scattering
 self-energies and energy grids shaped after the devices of the paper's Table 3
 (silicon nanowire / nanoribbon transport cells, N_BS = 416 = 4 primitive cells
-x 104 orbitals) and after the problem statement of Sec. 2 (Eqs. 1-3, Table 2).
+x 104 orbitals) and after the problem statement of Sec. 3 (Eqs. 1-3, Table 2).
 It contains none of the method's arithmetic (no assembly, no decimation, no
 inversion). Both the CPU oracle and the GPU path consume these arrays, so a
 mismatch between them can never come from a shared helper.
@@ -31,7 +31,7 @@ class GSystem:
     """Inputs of the electron (G) system of Table 2.
 
     H_diag [N,b,b], H_upper [N-1,b,b]; H is Hermitian so block (i+1,i) is
-    H_upper[i]^H.  S is the identity (orthogonal MLWF basis, Sec. 3).
+    H_upper[i]^H.  S is the identity (orthogonal MLWF basis, Sec. 4.1).
     Scattering self-energies are either None or diagonal vectors
     sig*_diag [E,N,b] (retarded / lesser / greater).
     """
@@ -85,7 +85,7 @@ def random_device_8x32(seed: int = BASE_SEED) -> GSystem:
 
 
 def _fermi_occupation(E: np.ndarray, mu: np.ndarray, kT: float) -> np.ndarray:
-    # occupation used only to *build* scattering self-energy inputs (Sec. 2: Sigma^<> consistent
+    # occupation used only to *build* scattering self-energy inputs (Sec. 3: Sigma^<> consistent
     # with Fermi occupations); overflow-safe logistic
     x = (E - mu) / kT
     out = np.empty(np.broadcast(E, mu).shape)
@@ -103,7 +103,7 @@ def nanoribbon(seed: int = BASE_SEED + 1, nb: int = 40, n_puc: int = 4, puc: int
     `puc` orbitals; defaults give N_B = 40, N_BS = 416, 512 energies on [-4, 4]).
 
     * H is periodic along transport (every H_ii equal, every H_{i,i+1} equal), as the paper's
-      devices built by repeating one primitive cell (Sec. 3).
+      devices built by repeating one primitive cell (Sec. 4.1).
     * H_ii: sparse Hermitian, ~h_density nonzero, values CN(0,1)/sqrt(h_density*bs).
     * H_{i,i+1}: fixed ~c_density nonzero pattern inside the primitive-cell blocks (p, q) with
       q <= p (a cell couples to the next n_puc cells along +x), values
@@ -242,7 +242,7 @@ def w_system(seed: int = BASE_SEED + 2, nb: int = 16, ny: int = 8, nz: int = 8, 
              target_norm: float = 0.5) -> WSystem:
     """W-type system: nb cells of ny x nz x nx atoms on a `spacing` grid (defaults: 16 cells of
     8x8x16 = 1024 atoms, 2.2 A grid, block length 35.2 A), one orbital per atom.
-    V_ij = 1/(1 + r_ij) for r_ij <= r_cut (the r_cut truncation of Sec. 3), P banded with the
+    V_ij = 1/(1 + r_ij) for r_ij <= r_cut (the r_cut truncation of Sec. 4.1), P banded with the
     same r_cut.  With nx*spacing > 3*r_cut, V, P, V P^R and V P^<> V^H are exactly
     block-tridiagonal."""
     assert nx * spacing > 3.0 * r_cut, "cell too short: V P V^H would not be block-tridiagonal"

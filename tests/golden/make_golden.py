@@ -1,8 +1,8 @@
 """Writes the stored expected values under tests/golden/ from the CPU oracle only.
 
-random_3x4.json: selected blocks of G^R, G^<, G^> (Sec. 2, Eq. 1 and Table 2: dense inverse of
-M~ = E + i eta - H - B^R_OBC and X^<> = X^R B^<> X^R^H, symmetrised as in Sec. 4.2) for a seeded
-3-block device of block size 4 with Sancho-Rubio contacts (Sec. 3.1, Eq. 4), at three energies
+random_3x4.json: selected blocks of G^R, G^<, G^> (Sec. 3, Eq. 1 and Table 2: dense inverse of
+M~ = E + i eta - H - B^R_OBC and X^<> = X^R B^<> X^R^H, symmetrised as in Sec. 5.2) for a seeded
+3-block device of block size 4 with Sancho-Rubio contacts (Sec. 4.2, Eq. 4), at three energies
 inside the lead bands.  Regenerate with `python tests/golden/make_golden.py`; a change of the
 stored numbers must name, in its commit message, the passage of the paper that justifies it.
 """
@@ -38,7 +38,7 @@ def main():
     sys.path.insert(0, os.path.dirname(HERE))
     from gpu_util import TOL_FP64, lesser_floor, route_discrepancy  # oracle-only helpers of the tests
     s = system()
-    out = {"case": CASE, "source": "oracle.solve_g (dense inverse, Sec. 2 Eq. 1, Table 2; symmetrised, Sec. 4.2)",
+    out = {"case": CASE, "source": "oracle.solve_g (dense inverse, Sec. 3 Eq. 1, Table 2; symmetrised, Sec. 5.2)",
            "energies": s.energies.tolist(), "blocks": {k: [] for k in KEYS},
            # per energy: absolute floor of the lesser/greater comparisons and per-output tolerance,
            # both from the oracle (FP64 rounding of the boundary broadening; 10x the disagreement

@@ -38,7 +38,7 @@ def test_golden_oracle_reproduces_stored_values():
 
 def test_golden_fixture_invariants():
     """The stored blocks themselves satisfy what the definitions fix: lesser/greater diagonal
-    blocks anti-Hermitian (Sec. 4.2 symmetrisation), -i G^< and i G^> positive semidefinite,
+    blocks anti-Hermitian (Sec. 5.2 symmetrisation), -i G^< and i G^> positive semidefinite,
     spectral function i (G^R - G^A) positive semidefinite on the diagonal."""
     _, _, blocks = load()
     for e in range(blocks["R_diag"].shape[0]):

@@ -1,4 +1,4 @@
-"""Contact memoization (Sec. 4.3): a second solve of the same energies starts the fixed-point
+"""Contact memoization (Sec. 5.3): a second solve of the same energies starts the fixed-point
 iteration of Eq. 5 from the kept surface functions instead of decimating; the results agree
 with a fresh solve, and far fewer decimation iterations run."""
 import numpy as np

@@ -76,7 +76,7 @@ def test_nanoribbon_diagonal_sigma():
 
 def test_block_sigma_with_off_diagonals():
     """Full per-energy Sigma blocks with off-diagonal blocks: exercises the assembled M~ off-diagonal
-    blocks and the y, Y terms of Eq. 9 / 11 (B^<> with off-diagonal blocks)."""
+    blocks and the y, Y terms of Eq. 10 / 11 (B^<> with off-diagonal blocks)."""
     rng = np.random.default_rng(17)
     s = synthetic.random_device(17, 5, 12, 4)
     nb, bs, E = s.nb, s.bs, 4
@@ -281,7 +281,7 @@ def test_split_scope_all_products():
 
 
 def test_packed_upper_storage_of_lesser_greater():
-    """Sec. 4.2 storage: lesser/greater diagonal blocks written as packed upper triangles equal the
+    """Sec. 5.2 storage: lesser/greater diagonal blocks written as packed upper triangles equal the
     full symmetrised blocks exactly; the packed layout is refused for G^R and unsymmetrised runs."""
     import torch
     import paper_2508_19138_gb300 as pkg

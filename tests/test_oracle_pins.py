@@ -415,7 +415,7 @@ def test_mutation_w_product_order_is_caught(wsmall, monkeypatch):
 
 
 def test_mutation_hermitian_instead_of_antihermitian_symmetrisation_is_caught(dev, monkeypatch):
-    """(X + X^H)/2 in place of (X - X^H)/2 (Sec. 4.2) keeps only the rounding noise of the lesser
+    """(X + X^H)/2 in place of (X - X^H)/2 (Sec. 5.2) keeps only the rounding noise of the lesser
     and greater functions: the G^> - G^< identity of Table 2, which the symmetrised blocks satisfy,
     no longer holds."""
     bs = dev.bs

@@ -1,4 +1,4 @@
-"""Pins of the W-contact route of the oracle (groundwork for the W contacts, Sec. 3.1: Eq. 4 for
+"""Pins of the W-contact route of the oracle (groundwork for the W contacts, Sec. 4.2: Eq. 4 for
 the retarded boundary, the Lyapunov / Stein equation of Eq. 7 for the lesser / greater one).
 
 * w_lead_fold on a generic lead whose transfer a = x^R n is far from zero: x^R and w^<> equal the

@@ -1,12 +1,12 @@
 """The readings of the paper that the CUDA sweep relies on, checked on the CPU: a plain numpy
-RGF (Sec. 3.2.2, Eq. 8-11, written here from the equations with the readings applied) against the
+RGF (Sec. 4.3.2, Eq. 9-12, written here from the equations with the readings applied) against the
 dense oracle, and each reading against its alternative.
 
-* R1: y_i of Eq. 9 with x^R_{i-1} (the printed x^<>_{i-1} disagrees with the dense inverse);
+* R1: y_i of Eq. 10 with x^R_{i-1} (the printed x^<>_{i-1} disagrees with the dense inverse);
 * R3: the off-diagonal lesser block X^<>_{i,i+1};
-* R15: Z_i of Eq. 11 equals U1 D^H with D the first term of X^<>_{i,i+1}, when x^<>_i is
+* R15: Z_i of Eq. 12 equals U1 D^H with D the first term of X^<>_{i,i+1}, when x^<>_i is
   exactly anti-Hermitian;
-* Sec. 4.2 symmetry enforced inside the sweep: every sandwich made exactly anti-Hermitian,
+* Sec. 5.2 symmetry enforced inside the sweep: every sandwich made exactly anti-Hermitian,
   element by element, matches the dense result; mirroring whole 32-wide tiles does not."""
 import numpy as np
 import pytest
@@ -37,7 +37,7 @@ def antiherm_tiles(C, tile=32):
 
 
 def rgf(M, B, nb, bs, y_with_lesser=False, z_from_d=False, sandwich=None):
-    """Selected blocks of X^R and X^< by the forward (Eq. 8-9) and backward (Eq. 10-11) passes;
+    """Selected blocks of X^R and X^< by the forward (Eq. 9-10) and backward (Eq. 11-12) passes;
     B may have off-diagonal blocks.  sandwich(C) post-processes every x B x^H product."""
     S = sandwich or (lambda C: C)
     blk = lambda A, i, j: _blocks(A, i, j, bs)
