@@ -46,7 +46,7 @@ def first_fit(live, size, capacity):
 def test_arena_matches_first_fit_model(driver, seed):
     rng = random.Random(seed)
     capacity = rng.choice([1 << 20, 3 * (1 << 20) + 512, 10_000_000])
-    # one scripted session: the driver's answers are compared afterwards, so the script must not
+    # one scripted session: arena_driver's answers are compared afterwards, so the script must not
     # depend on them -- the model decides which blocks are live
     cmds = [f"reset {capacity}"]
     expected = []
