@@ -2,7 +2,7 @@
 //
 // Some callers cannot allocate device memory at the point where they need an inverse: code
 // running under a memory pool or allocator that must not be re-entered, code that has already
-// handed all free memory to its own arena, or a host thread that must not take the driver's
+// handed all free memory to its own arena, or a host thread that must not take the CUDA driver's
 // allocation lock in a latency-critical loop.  For them this entry point runs the same blocked
 // Gauss-Jordan inversion as bt_zinv_batched, but its scratch (pivot rows and the panel copy)
 // lives in one fixed array compiled into the library instead of a caller-provided workspace.
