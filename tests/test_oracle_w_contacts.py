@@ -4,6 +4,7 @@ the retarded boundary, the Lyapunov / Stein equation of Eq. 7 for the lesser / g
 * w_lead_fold on a generic lead whose transfer a = x^R n is far from zero: x^R and w^<> equal the
   surface blocks of X^R and X^R B X^R^H of a long finite lead (dense inverse), the Stein term
   and the y term of a block-tridiagonal right-hand side included; dropping either fails.
+* Eq. 7 as printed (w = q - a w a^H) misses the long-lead surface block; w = q + a w a^H matches.
 * solve_w_contacts on a small W system equals a dense solve of the device with long explicit
   leads; dropping the lesser boundary fails."""
 import numpy as np
@@ -60,6 +61,25 @@ def test_lead_fold_matches_long_finite_lead(seed):
     import scipy.linalg as sla
     w0 = sla.solve_discrete_lyapunov(a, q0)
     assert block_errors(w0[None], ws[None]).max() > 1e-3                     # without the y term
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_stein_sign_as_printed_fails(seed):
+    """Eq. 7 is printed as w = q - a w a^H.  No scalar factor in a changes the sign of a w a^H
+    (c a w (c a)^H = |c|^2 a w a^H), and the printed sign, solved exactly, misses the surface block
+    of a long explicit lead by far; w = q + a w a^H matches it (the reading of the oracle)."""
+    m, n, n_prime, b, c = _lead(seed, 4, 0.05)
+    _, ws = _chain_surface(m, n, n_prime, b, c, 400)
+    _, _, x, w = oracle.w_lead_fold(m, n, n_prime, b, c)
+    y = n @ x @ c
+    a = x @ n
+    q = x @ (b - y + y.conj().T) @ x.conj().T
+    k = q.shape[0]
+    # w = q - a w a^H  <=>  (I + conj(a) (x) a) vec(w) = vec(q), vec stacking columns
+    w_printed = np.linalg.solve(np.eye(k * k) + np.kron(a.conj(), a), q.reshape(-1, order="F")).reshape(k, k, order="F")
+    assert np.abs(w_printed - (q - a @ w_printed @ a.conj().T)).max() < 1e-12
+    assert block_errors(w_printed[None], ws[None]).max() > 0.1
+    assert block_errors(w[None], ws[None]).max() < 1e-10
 
 
 def test_w_contacts_match_long_explicit_leads():
