@@ -379,7 +379,9 @@ def solve_g_sampled(sysg, e, blocks, symmetrize=True, tol=1e-14, maxit=100):
 #     w^<> = q + a w^<> a^H                              (Eq. 7; a Stein equation)
 #     B^R_OBC = n x^R n',   B^<>_OBC = n w^<> n^H - (y - y^H)
 # — the fixed point of the forward recursion of Eq. 9-10 run along the lead from infinity.  The
-# edge cells' own blocks of M and B include the products with the first lead cell.
+# edge cells' own blocks of M and B include the products with the first lead cell.  Eq. 7 is
+# printed with a minus sign before a w a^H; the fixed point has a plus sign (a scalar factor in a
+# cannot change that sign), and the long-lead pin decides between the two.
 # ----------------------------------------------------------------------------------------------
 
 def w_extended_chain(wsys, e, n_lead):
