@@ -435,8 +435,8 @@ def w_lead_fold(m, n, n_prime, b, c, tol=1e-14, maxit=200):
 def solve_w_contacts(wsys, e, symmetrize=True):
     """Selected blocks of W^R = X^R V and W^<> = X^<> (Table 2, right column) for the W system with
     both leads attached (Sec. 4.2, Eq. 4 and 7; the reading above), by folding the leads into the
-    edge cells and a dense solve of the device.  W^R's edge blocks include V's coupling to the first lead cells through
-    X^R_{0,-1} = -X^R_{00} M_{0,-1} x^R_L (and the mirror on the right)."""
+    edge cells and a dense solve of the device.  W^R's edge blocks include V's coupling to the
+    first lead cells through X^R_{0,-1} = -X^R_{00} M_{0,-1} x^R_L (and the mirror on the right)."""
     nb, bs = wsys.nb, wsys.bs
     K = 4   # lead cells in the assembly window: cell 1 and cell (K + nb + 2) are bulk lead cells
     M, BL, BG, V = _w_chain_dense(wsys, e, K)
