@@ -140,6 +140,12 @@ typedef struct {
    * read back asynchronously and folded in at the next solve or bt_selinv_get_stats (which then
    * synchronises the stream).  0: direct launches.                                              */
   int graph;
+  /* Newton step on the decimated surface functions (Sec. 4.2, Eq. 4).  FP64 decimation loses
+   * accuracy where a lead mode decays slowly (energies near a band edge at small eta; up to
+   * ~1e-8 relative after 25 iterations).  Leads whose decimation took more than this many
+   * iterations get one Newton step on x^{-1} (a Stein equation solved by doubling), which brings
+   * the surface function back to FP64 accuracy.  0: 14; negative: never.                        */
+  int decim_newton_after;
 } bt_selinv_desc;
 
 typedef struct bt_ctx bt_ctx;
@@ -155,6 +161,8 @@ typedef struct {
   long long lead_iterations;   /* decimation iterations summed over leads (all solves)        */
   long long fpi_iterations;    /* memoized fixed-point iterations summed over leads           */
   long long memo_hits;         /* energies whose contacts started from a kept surface function*/
+  long long newton_leads;      /* leads that took the Newton step after decimation            */
+  long long newton_iterations; /* doubling iterations of those steps, summed over leads       */
 } bt_stats;
 
 /* Sizes of the workspace bt_selinv_create would allocate for `desc`. */
@@ -305,7 +313,11 @@ BT_API bt_status bt_zinv_batched(int n, void* A, long long strideA, int batch, i
  *   - needs bt_zinv_workspace_bytes(n, batch) <= BT_ZINV_NOALLOC_SCRATCH_BYTES, else returns
  *     BT_ERR_BUDGET and launches nothing (n <= 96 needs no scratch at all);
  *   - the first call on a device, with that device current, looks up the array's device
- *     address; make that first call before any stream capture;
+ *     address; under CUDA's default lazy module loading that lookup also loads the library's
+ *     device code for the array and so reserves its memory on that device (an allocation made
+ *     by the CUDA driver, which can fail when the device is full).  Make that first call before
+ *     the caller's pool or arena takes the device's free memory, and before any stream
+ *     capture; later calls on that device allocate nothing;
  *   - every call shares the array: calls that overlap on the GPU (other streams or threads)
  *     race; calls on one stream are ordered.  The array keeps the last call's contents and
  *     needs no clearing (every word is written before it is read). */

@@ -10,9 +10,11 @@ import numpy as np
 import scipy.linalg as sla
 
 __all__ = [
-    "fermi", "bt_dense", "sancho_rubio", "surface_gf_eig", "lead_blocks", "obc_self_energies",
+    "fermi", "bt_dense", "sancho_rubio", "sancho_rubio_mp", "surface_gf_eig", "surface_function",
+    "lead_blocks", "obc_self_energies",
     "assemble_g", "selected_blocks", "symmetrize_lesser", "solve_g", "assemble_w", "solve_w",
-    "transmission", "bond_currents", "block_rows_banded", "solve_g_sampled", "w_extended_chain",
+    "transmission", "bond_currents", "block_rows_banded", "solve_g_sampled", "w_bt_blocks", "solve_w_sampled",
+    "w_extended_chain",
     "w_lead_fold", "solve_w_contacts", "solve_w_long_leads",
 ]
 
@@ -92,6 +94,64 @@ def surface_gf_eig(m, n, n_prime):
     return np.linalg.inv(m + n @ T)
 
 
+def sancho_rubio_mp(m, n, n_prime, dps=40, tol=1e-30, maxit=400):
+    """The decimation of sancho_rubio (Sec. 4.2, Eq. 4) carried out in mpmath arithmetic with `dps`
+    significant decimal digits, for small blocks.  The inputs are exact binary numbers, so the
+    result, rounded to complex128, is the surface function of the given FP64 blocks to full
+    FP64 accuracy wherever the decimation converges.  It decides which FP64 route is right where
+    the two disagree (near band edges, at small eta).  Returns (x as complex128, iterations,
+    converged)."""
+    import mpmath as mp
+
+    def to_mp(A):
+        A = np.asarray(A, dtype=np.complex128)
+        M = mp.matrix(A.shape[0], A.shape[1])
+        for i in range(A.shape[0]):
+            for j in range(A.shape[1]):
+                M[i, j] = mp.mpc(float(A[i, j].real), float(A[i, j].imag))
+        return M
+
+    def maxabs(M):
+        return max(abs(M[i, j]) for i in range(M.rows) for j in range(M.cols))
+
+    with mp.workdps(dps):
+        a, b, e = to_mp(n), to_mp(n_prime), to_mp(m)
+        es = e.copy()
+        ref = max(maxabs(a), maxabs(b))
+        it, converged = 0, ref == 0
+        while not converged and it < maxit:
+            it += 1
+            g = e ** -1
+            agb = a * g * b
+            bga = b * g * a
+            es = es - agb
+            e = e - agb - bga
+            a = -(a * g * a)
+            b = -(b * g * b)
+            converged = max(maxabs(a), maxabs(b)) <= tol * ref
+        x = es ** -1
+        out = np.array([[complex(x[i, j]) for j in range(x.cols)] for i in range(x.rows)], dtype=np.complex128)
+    return out, it, converged
+
+
+def surface_function(m, n, n_prime, route="decimation", tol=1e-14, maxit=100):
+    """Surface function x = (m - n x n')^{-1} of Eq. 4 by one of three routes:
+      "decimation"  Sancho-Rubio in FP64 (sancho_rubio), the solver the paper cites;
+      "eig"         the direct route through the decaying modes of the lead (Eq. 6,
+                    surface_gf_eig): the definition of the retarded surface function written out;
+      "exact"       Sancho-Rubio in extended precision (sancho_rubio_mp), small blocks only.
+    FP64 decimation loses accuracy where a lead mode decays slowly (energies near a band edge at
+    small eta: up to ~1e-8 relative); the eigen route keeps FP64 accuracy there (the tests check
+    both against the extended-precision route).  Returns (x, iterations, converged)."""
+    if route == "decimation":
+        return sancho_rubio(m, n, n_prime, tol, maxit)
+    if route == "eig":
+        return surface_gf_eig(m, n, n_prime), 0, True
+    if route == "exact":
+        return sancho_rubio_mp(m, n, n_prime)
+    raise ValueError(f"unknown surface-function route {route!r}")
+
+
 def _M_blocks(sysg, e):
     """Blocks of M - B^R_scatt at energy index e (Table 2, left column: M = E S - H):
     (diag [N,b,b], upper, lower)."""
@@ -116,16 +176,16 @@ def lead_blocks(sysg, e):
     return left, right
 
 
-def obc_self_energies(sysg, e, tol=1e-14, maxit=100):
-    """Boundary blocks B_OBC at energy index e.  Retarded: n x n' with x from Eq. 4 (Sancho-
-    Rubio).  Lesser/greater by fluctuation-dissipation:
+def obc_self_energies(sysg, e, tol=1e-14, maxit=100, surface="decimation"):
+    """Boundary blocks B_OBC at energy index e.  Retarded: n x n' with x from Eq. 4 (by the route
+    `surface` of surface_function).  Lesser/greater by fluctuation-dissipation:
         B^<_c = -f_c (B^R_c - B^R_c^H),  B^>_c = (1 - f_c)(B^R_c - B^R_c^H).
     Returns dict with keys R_L, R_R, L_L, L_R, G_L, G_R, it_L, it_R, ok."""
     if sysg.nb < 2:
         raise ValueError("contacts from the edge blocks need at least two blocks")
     (mL, nL, npL), (mR, nR, npR) = lead_blocks(sysg, e)
-    xL, itL, okL = sancho_rubio(mL, nL, npL, tol, maxit)
-    xR, itR, okR = sancho_rubio(mR, nR, npR, tol, maxit)
+    xL, itL, okL = surface_function(mL, nL, npL, surface, tol, maxit)
+    xR, itR, okR = surface_function(mR, nR, npR, surface, tol, maxit)
     SL = nL @ xL @ npL
     SR = nR @ xR @ npR
     E = sysg.energies[e]
@@ -137,9 +197,10 @@ def obc_self_energies(sysg, e, tol=1e-14, maxit=100):
                 it_L=itL, it_R=itR, ok=okL and okR)
 
 
-def assemble_g(sysg, e, tol=1e-14, maxit=100):
+def assemble_g(sysg, e, tol=1e-14, maxit=100, surface="decimation"):
     """Dense M~ = E S - H - Sigma^R_scatt - Sigma^R_OBC and B^<> = Sigma^<>_scatt + Sigma^<>_OBC
-    (Table 2; the element-wise G assembly of Sec. 4.3.1)."""
+    (Table 2; the element-wise G assembly of Sec. 4.3.1); `surface` picks the route of the lead
+    surface functions (surface_function)."""
     d, u, l = _M_blocks(sysg, e)
     nb, bs = sysg.nb, sysg.bs
     M = bt_dense(d, u, l)
@@ -152,7 +213,7 @@ def assemble_g(sysg, e, tol=1e-14, maxit=100):
         BG += np.diag(sysg.sigG_diag[e].reshape(-1))
     info = {}
     if sysg.obc:
-        o = obc_self_energies(sysg, e, tol, maxit)
+        o = obc_self_energies(sysg, e, tol, maxit, surface)
         M[:bs, :bs] -= o["R_L"]
         M[-bs:, -bs:] -= o["R_R"]
         BL[:bs, :bs] += o["L_L"]
@@ -181,11 +242,12 @@ def symmetrize_lesser(X):
     return 0.5 * (X - X.conj().T)
 
 
-def solve_g(sysg, e, symmetrize=True, tol=1e-14, maxit=100):
+def solve_g(sysg, e, symmetrize=True, tol=1e-14, maxit=100, surface="decimation"):
     """Selected blocks of X^R = M~^{-1} and X^<> = X^R B^<> X^R^H at energy index e, by dense
-    inversion (Eq. 1).  Returns dict: R_diag, R_upper, R_lower, L_diag, L_upper, G_diag,
+    inversion (Eq. 1), with the lead surface functions by the route `surface`.  Returns dict:
+    R_diag, R_upper, R_lower, L_diag, L_upper, G_diag,
     G_upper (lesser/greater lower blocks are -upper^H), plus 'info' from the OBC."""
-    M, BL, BG, info = assemble_g(sysg, e, tol, maxit)
+    M, BL, BG, info = assemble_g(sysg, e, tol, maxit, surface)
     XR = np.linalg.inv(M)
     XL = XR @ BL @ XR.conj().T
     XG = XR @ BG @ XR.conj().T
@@ -307,7 +369,7 @@ def block_rows_banded(A_diag, A_upper, A_lower, rows):
     return {i: Z[:, k * bs:(k + 1) * bs].T.copy() for k, i in enumerate(rows)}
 
 
-def solve_g_sampled(sysg, e, blocks, symmetrize=True, tol=1e-14, maxit=100):
+def solve_g_sampled(sysg, e, blocks, symmetrize=True, tol=1e-14, maxit=100, surface="decimation"):
     """Selected blocks (Sec. 3, Eq. 1 and Table 2) at energy index e for block indices `blocks`
     without a dense inverse:
     rows i and i+1 of X^R by banded LU, then X^<>_{ij} = X^R[i,:] B^<> X^R[j,:]^H with the
@@ -324,7 +386,7 @@ def solve_g_sampled(sysg, e, blocks, symmetrize=True, tol=1e-14, maxit=100):
         if sysg.sigG_diag is not None:
             bg[i] += np.diag(sysg.sigG_diag[e, i])
     if sysg.obc:
-        o = obc_self_energies(sysg, e, tol, maxit)
+        o = obc_self_energies(sysg, e, tol, maxit, surface)
         d[0] -= o["R_L"]
         d[-1] -= o["R_R"]
         bl[0] += o["L_L"]
@@ -359,6 +421,99 @@ def solve_g_sampled(sysg, e, blocks, symmetrize=True, tol=1e-14, maxit=100):
             if symmetrize:
                 Lu = 0.5 * (Lu - quad(rj, ri, bl).conj().T)
                 Gu = 0.5 * (Gu - quad(rj, ri, bg).conj().T)
+            r["L_upper"], r["G_upper"] = Lu, Gu
+        out[i] = r
+    return out
+
+
+def w_bt_blocks(wsys, e):
+    """Block-tridiagonal blocks of M = I - V P^R and B^<> = V P^<> V^H (Table 2, right column) at
+    energy index e, each block summed from the products of the V and P blocks it contains:
+    M_ij = delta_ij I - sum_k V_ik P_kj and B_ij = sum_{k,l} V_ik P_kl (V_jl)^H for |i - j| <= 1.
+    Exact when the cells are longer than three cut-off radii (the blocks two or more cells apart
+    then vanish).  Returns (M_d, M_u, M_l, BL_d, BL_u, BG_d, BG_u, V block accessor)."""
+    nb, bs = wsys.nb, wsys.bs
+    PRd, PRu, PRl, PLd, PLu, PGd, PGu = wsys.P_blocks(e)
+
+    def Vb(i, j):
+        if i == j:
+            return wsys.V_diag[i]
+        return wsys.V_upper[i] if j == i + 1 else wsys.V_upper[j].conj().T
+
+    def Pb(d, u, l, i, j):
+        if i == j:
+            return d[i]
+        if j == i + 1:
+            return u[i]
+        return l[j] if l is not None else -u[j].conj().T
+
+    near = lambda i: [k for k in (i - 1, i, i + 1) if 0 <= k < nb]
+    I = np.eye(bs)
+    Md = np.stack([I - sum(Vb(i, k) @ Pb(PRd, PRu, PRl, k, i) for k in near(i)) for i in range(nb)])
+    Mu = np.stack([-sum(Vb(i, k) @ Pb(PRd, PRu, PRl, k, i + 1) for k in near(i) if abs(k - i - 1) <= 1)
+                   for i in range(nb - 1)]) if nb > 1 else np.zeros((0, bs, bs), np.complex128)
+    Ml = np.stack([-sum(Vb(i + 1, k) @ Pb(PRd, PRu, PRl, k, i) for k in near(i + 1) if abs(k - i) <= 1)
+                   for i in range(nb - 1)]) if nb > 1 else np.zeros((0, bs, bs), np.complex128)
+
+    def B(d, u, i, j):
+        acc = np.zeros((bs, bs), np.complex128)
+        for k in near(i):
+            for l_ in near(j):
+                if abs(k - l_) <= 1:
+                    acc += Vb(i, k) @ Pb(d, u, None, k, l_) @ Vb(j, l_).conj().T
+        return acc
+
+    BLd = np.stack([B(PLd, PLu, i, i) for i in range(nb)])
+    BGd = np.stack([B(PGd, PGu, i, i) for i in range(nb)])
+    BLu = np.stack([B(PLd, PLu, i, i + 1) for i in range(nb - 1)]) if nb > 1 else np.zeros((0, bs, bs), np.complex128)
+    BGu = np.stack([B(PGd, PGu, i, i + 1) for i in range(nb - 1)]) if nb > 1 else np.zeros((0, bs, bs), np.complex128)
+    return Md, Mu, Ml, BLd, BLu, BGd, BGu, Vb
+
+
+def solve_w_sampled(wsys, e, blocks, symmetrize=True):
+    """Selected blocks of W^R = X^R V and W^<> = X^R B^<> X^R^H (Table 2, right column; no
+    contacts) for block indices `blocks` without a dense inverse: rows of X^R = M^{-1} by banded LU
+    (block_rows_banded), then the products with the block-tridiagonal V and B^<> of w_bt_blocks.
+    Returns {i: dict(R_diag, R_upper, R_lower, L_diag, L_upper, G_diag, G_upper)} (upper / lower
+    entries only when i + 1 < N)."""
+    nb, bs = wsys.nb, wsys.bs
+    Md, Mu, Ml, BLd, BLu, BGd, BGu, Vb = w_bt_blocks(wsys, e)
+    need = sorted(set(list(blocks) + [i + 1 for i in blocks if i + 1 < nb]))
+    rows = block_rows_banded(Md, Mu, Ml, need)
+    cols = lambda r, k: r[:, k * bs:(k + 1) * bs]
+
+    def wr(r, j):  # (X^R V)_{., j} from a block row of X^R
+        return sum(cols(r, k) @ Vb(k, j) for k in (j - 1, j, j + 1) if 0 <= k < nb)
+
+    def Bb(d, u, k, l_):
+        if k == l_:
+            return d[k]
+        return u[k] if l_ == k + 1 else -u[l_].conj().T
+
+    def row_times_b(ri, d, u):  # the block row X^R[i, :] B^<> (B block-tridiagonal)
+        return [sum(cols(ri, k) @ Bb(d, u, k, l_) for k in (l_ - 1, l_, l_ + 1) if 0 <= k < nb) for l_ in range(nb)]
+
+    def quad(tb, rj):  # (X^R[i, :] B^<>) X^R[j, :]^H
+        return sum(tb[l_] @ cols(rj, l_).conj().T for l_ in range(nb))
+
+    tbs = {}
+    for j in need:
+        tbs[j] = (row_times_b(rows[j], BLd, BLu), row_times_b(rows[j], BGd, BGu))
+    out = {}
+    for i in blocks:
+        ri = rows[i]
+        r = dict(R_diag=wr(ri, i))
+        Ld, Gd = quad(tbs[i][0], ri), quad(tbs[i][1], ri)
+        if symmetrize:
+            Ld, Gd = 0.5 * (Ld - Ld.conj().T), 0.5 * (Gd - Gd.conj().T)
+        r["L_diag"], r["G_diag"] = Ld, Gd
+        if i + 1 < nb:
+            rj = rows[i + 1]
+            r["R_upper"], r["R_lower"] = wr(ri, i + 1), wr(rj, i)
+            Lu, Gu = quad(tbs[i][0], rj), quad(tbs[i][1], rj)
+            if symmetrize:
+                Lu = 0.5 * (Lu - quad(tbs[i + 1][0], ri).conj().T)
+                Gu = 0.5 * (Gu - quad(tbs[i + 1][1], ri).conj().T)
             r["L_upper"], r["G_upper"] = Lu, Gu
         out[i] = r
     return out

@@ -35,13 +35,14 @@ class bt_selinv_desc(C.Structure):
                 ("eta", C.c_double), ("kT", C.c_double), ("mu_left", C.c_double), ("mu_right", C.c_double),
                 ("decim_tol", C.c_double), ("decim_maxit", C.c_int), ("hbm_budget_bytes", C.c_size_t),
                 ("obc_memo", C.c_int), ("memo_nfpi", C.c_int), ("memo_capacity", C.c_int), ("split_scope", C.c_int),
-                ("graph", C.c_int)]
+                ("graph", C.c_int), ("decim_newton_after", C.c_int)]
 
 
 class bt_stats(C.Structure):
     _fields_ = [("solves", C.c_longlong), ("energies", C.c_longlong), ("decim_iterations", C.c_longlong),
                 ("flops_model", C.c_double), ("workspace_bytes", C.c_size_t), ("kernel_launches", C.c_longlong),
-                ("lead_iterations", C.c_longlong), ("fpi_iterations", C.c_longlong), ("memo_hits", C.c_longlong)]
+                ("lead_iterations", C.c_longlong), ("fpi_iterations", C.c_longlong), ("memo_hits", C.c_longlong),
+                ("newton_leads", C.c_longlong), ("newton_iterations", C.c_longlong)]
 
 
 # exported names and their ctypes signatures (restype is bt_status unless noted)

@@ -13,7 +13,7 @@ import numpy as np
 from . import _native as N
 
 __all__ = [
-    "BTError", "BT", "BTOut", "unpack_upper", "Context", "make_desc", "bt_selinv_workspace_bytes", "bt_selinv_create",
+    "BTError", "BT", "BTOut", "Context", "make_desc", "bt_selinv_workspace_bytes", "bt_selinv_create",
     "bt_selinv_solve", "bt_selinv_solve_host", "bt_selinv_destroy", "bt_selinv_last_error", "bt_selinv_get_stats",
     "bt_zgemm_batched", "bt_split_zgemm_workspace_bytes", "bt_split_zgemm_batched", "bt_zinv_workspace_bytes",
     "bt_zinv_batched", "bt_zinv_batched_noalloc", "bt_decimate_workspace_bytes", "bt_decimate_batched", "library",
@@ -83,25 +83,11 @@ class BT:
                        1 if self.per_energy else 0)
 
 
-def unpack_upper(packed, bs):
-    """Full anti-Hermitian blocks from BT_LAYOUT_PACKED_UPPER storage (host-side convenience):
-    packed [..., bs (bs + 1) / 2] -> [..., bs, bs] with X_cr = -conj(X_rc)."""
-    import numpy as np
-    packed = np.asarray(packed)
-    iu = np.triu_indices(bs)
-    out = np.zeros(packed.shape[:-1] + (bs, bs), dtype=np.complex128)
-    out[..., iu[0], iu[1]] = packed
-    low = -np.conj(np.swapaxes(out, -1, -2))
-    il = np.tril_indices(bs, -1)
-    out[..., il[0], il[1]] = low[..., il[0], il[1]]
-    return out
-
-
 class BTOut:
     """Output operand: [E][nb][bs][bs] diag, [E][nb-1][bs][bs] upper / lower (None = not written);
     layout BT_LAYOUT_DIAGVEC: diag is [E][nb][bs] (diagonal entries of the diagonal blocks);
     BT_LAYOUT_PACKED_UPPER (lesser/greater, symmetrised): diag is [E][nb][bs (bs + 1) / 2], the upper
-    triangle of each anti-Hermitian block row by row (see unpack_upper)."""
+    triangle of each anti-Hermitian block row by row (entry (r, c >= r) at r bs - r (r - 1) / 2 + (c - r))."""
 
     def __init__(self, diag=None, upper=None, lower=None, layout: int = N.BT_LAYOUT_BLOCKS):
         self.diag, self.upper, self.lower, self.layout = diag, upper, lower, layout
@@ -116,10 +102,12 @@ def make_desc(nb: int, bs: int, max_energies: int, system: int = N.BT_SYS_G, pre
               split_slices: int = 0, symmetrize: bool = True, obc: bool = True, eta: float = 1e-6,
               kT: float = 0.025, mu_left: float = 0.0, mu_right: float = 0.0, decim_tol: float = 1e-14,
               decim_maxit: int = 100, hbm_budget_bytes: int = 0, obc_memo: bool = False, memo_nfpi: int = 0,
-              memo_capacity: int = 0, split_scope: int = 0, graph: bool = False) -> N.bt_selinv_desc:
+              memo_capacity: int = 0, split_scope: int = 0, graph: bool = False,
+              decim_newton_after: int = 0) -> N.bt_selinv_desc:
     return N.bt_selinv_desc(nb, bs, max_energies, system, precision, split_slices, 1 if symmetrize else 0,
                             1 if obc else 0, eta, kT, mu_left, mu_right, decim_tol, decim_maxit, hbm_budget_bytes,
-                            1 if obc_memo else 0, memo_nfpi, memo_capacity, split_scope, 1 if graph else 0)
+                            1 if obc_memo else 0, memo_nfpi, memo_capacity, split_scope, 1 if graph else 0,
+                            decim_newton_after)
 
 
 class Context:

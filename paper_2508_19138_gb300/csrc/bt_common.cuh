@@ -113,6 +113,17 @@ struct LoopCapture {
   long long body_launches = 0;
 };
 
+// One Newton step on decimated surface functions (see decimate.cu): for the leads whose
+// decimation took more than `after` iterations, e_s <- e_s + d with d solving the linearised
+// equation d - (n x) d (x n') = m - n x n' - e_s (a Stein equation, solved by doubling).
+struct Polish {
+  int after = -1;                 // < 0: no lead is polished
+  int* iters = nullptr;           // [batch] device: doubling iterations per lead (0 = not polished)
+  long long lead_iterations = 0;  // direct mode: doubling iterations summed over the leads
+  int selected = 0;               // direct mode: leads that took the step
+  long long body_launches = 0;    // graph mode: kernels of one pass of the doubling loop
+};
+
 // Sancho-Rubio decimation for `batch` leads.  With `loop` (graph capture), iters_host_max and
 // lead_iterations are not written: the per-lead counts are in `iters` on the device.
 size_t decimate_workspace_bytes(int bs, int batch, bool wide = false);
@@ -120,7 +131,18 @@ bt_status decimate(cudaStream_t st, int bs, int batch, const zd* m, const zd* n,
                    double tol, int maxit, zd* x, zd* sigma, int* iters, int* info, void* ws,
                    size_t ws_bytes, int* iters_host_max, int* h_pinned, const int* mask = nullptr,
                    long long* lead_iterations = nullptr, const Engine* eng = nullptr,
-                   LoopCapture* loop = nullptr);
+                   LoopCapture* loop = nullptr, Polish* polish = nullptr);
+
+// X = R + A X B for `batch` independent bs x bs problems (B = A^H when B is null), by doubling:
+// X <- X + A X B, A <- A A, B <- B B until bs^2 max|A| max|B| <= tol.  X holds R on entry; A and B
+// are overwritten.  mask[l] == 0 leaves problem l alone (mask may be null); ok[l] = 1 where the
+// doubling converged within maxit, else 0 (X is then a partial sum); iters[l] = doublings.
+// With `loop` (graph capture) the doubling loop is a conditional while node and the counts are
+// left on the device; otherwise *lead_iterations = doublings summed over the problems.
+size_t stein_workspace_bytes(int bs, int batch);
+bt_status stein(cudaStream_t st, int bs, int batch, zd* A, zd* B, zd* X, double tol, int maxit, const int* mask,
+                int* ok, int* iters, void* ws, size_t ws_bytes, int* h_pinned, long long* lead_iterations,
+                const Engine* eng = nullptr, LoopCapture* loop = nullptr);
 bt_status invert_mask(cudaStream_t st, int batch, const int* a, int* out);  // out = !a
 // Fixed-point iteration x <- (m - n x n')^{-1} (Eq. 5) from the given x for leads with run[l];
 // conv[l] = 1 where it converged to tol within nfpi iterations.

@@ -15,6 +15,17 @@
 // In graph mode the same loop is a conditional while node of the captured graph: a one-thread
 // kernel at the end of each iteration sets the loop condition from that count and the device
 // iteration counter, so a whole solve runs without returning to the host.
+//
+// Newton polish.  Decimation in FP64 loses accuracy where a lead mode decays slowly (energies
+// near a band edge at small eta): a rounding error made early is carried through the 2^k
+// decimated cells, and the surface function comes out up to ~1e-8 off (checked against an
+// extended-precision decimation).  For leads whose decimation took more than `after` iterations
+// one Newton step on e_s restores FP64 accuracy: with x = e_s^{-1} the residual of
+// e_s = m - n e_s^{-1} n' is r = m - n x n' - e_s, and the correction d solves the linearised
+// equation d - (n x) d (x n') = r, a Stein equation X = R + A X B solved by doubling
+// (X <- X + A X B, A <- A A, B <- B B: after k steps X sums the first 2^k terms).  Then
+// e_s <- e_s + d and x = e_s^{-1}.  The same doubling solves the Stein equation of the W
+// contacts (Eq. 7).
 #include <cstring>
 #include <utility>
 #include <vector>
@@ -222,6 +233,91 @@ __global__ void not_kernel(int batch, const int* __restrict__ a, int* __restrict
   if (l < batch) out[l] = a[l] ? 0 : 1;
 }
 
+// ---- Stein doubling and the Newton polish ----
+
+// problems selected by the mask (all without one) start active, not converged, no iterations
+__global__ void stein_init_kernel(int batch, const int* __restrict__ mask, int* active, int* ok, int* iters) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= batch) return;
+  const int on = mask ? (mask[l] != 0) : 1;
+  active[l] = on;
+  ok[l] = 0;
+  if (iters) iters[l] = 0;
+}
+
+// convergence test after one doubling step: the next increment A X B is bounded by
+// bs^2 max|A| max|X| max|B|, so problem l is done once bs^2 max|A| max|B| <= tol
+__device__ __forceinline__ void stein_test(int l, const unsigned long long* keys, const int* flags, double bs2,
+                                           double tol, int it, int* active, int* ok, int* iters, int* n_active) {
+  if (iters) iters[l] = it;
+  if (flags[l]) {
+    active[l] = 0;  // non-finite: no correction
+  } else if (key_sqrt(keys[2 * l]) * key_sqrt(keys[2 * l + 1]) * bs2 <= tol) {
+    active[l] = 0;
+    ok[l] = 1;
+  } else {
+    atomicAdd(n_active, 1);
+  }
+}
+
+__global__ void stein_check_kernel(int batch, const unsigned long long* __restrict__ keys, const int* __restrict__ flags,
+                                   double bs2, double tol, int it, int* __restrict__ active, int* __restrict__ ok,
+                                   int* __restrict__ iters, int* __restrict__ n_active) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= batch || active[l] == 0) return;
+  stein_test(l, keys, flags, bs2, tol, it, active, ok, iters, n_active);
+}
+
+// graph mode: the iteration number comes from the device counter
+__global__ void stein_check_dev_kernel(int batch, const unsigned long long* __restrict__ keys,
+                                       const int* __restrict__ flags, double bs2, double tol,
+                                       const int* __restrict__ itc, int* __restrict__ active, int* __restrict__ ok,
+                                       int* __restrict__ iters, int* __restrict__ n_active) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= batch || active[l] == 0) return;
+  stein_test(l, keys, flags, bs2, tol, *itc, active, ok, iters, n_active);
+}
+
+// leads to polish: selected by the decimation mask, decimated without error, and with more than
+// `after` iterations
+__global__ void polish_mask_kernel(int batch, const int* __restrict__ mask, const int* __restrict__ iters,
+                                   const int* __restrict__ info, int after, int* __restrict__ pm) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= batch) return;
+  pm[l] = (mask ? mask[l] != 0 : 1) && info[l] == 0 && iters[l] > after;
+}
+
+// X = m - es - t (the residual r of the Newton step, t = n x n') for selected leads
+__global__ void residual_kernel(long long bs2, const zd* __restrict__ m, const zd* __restrict__ es,
+                                const zd* __restrict__ t, zd* __restrict__ X, const int* __restrict__ sel) {
+  const int l = blockIdx.y;
+  if (sel[l] == 0) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < bs2; i += (long long)gridDim.x * blockDim.x) {
+    const long long o = (long long)l * bs2 + i;
+    X[o] = zsub(zsub(m[o], es[o]), t[o]);
+  }
+}
+
+// es += X for leads whose doubling converged
+__global__ void add_masked_kernel(long long bs2, zd* __restrict__ es, const zd* __restrict__ X,
+                                  const int* __restrict__ sel) {
+  const int l = blockIdx.y;
+  if (sel[l] == 0) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < bs2; i += (long long)gridDim.x * blockDim.x) {
+    const long long o = (long long)l * bs2 + i;
+    es[o] = zadd(es[o], X[o]);
+  }
+}
+
+struct SteinWs {
+  zd *T, *A2, *B2;
+  unsigned long long* keys;
+  int* flags;
+  int* active;
+  int* n_active;
+  int* itc;
+};
+
 struct DecimWs {
   zd *a, *b, *a2, *b2, *e, *es, *g, *ag, *bg, *t;
   double* ref;
@@ -230,6 +326,9 @@ struct DecimWs {
   int* active;
   int* n_active;
   int* itc;  // graph mode: iteration counter
+  int* pm;   // Newton polish: leads selected
+  int* ok;   // Newton polish: leads whose doubling converged
+  int* itc2; // graph mode: iteration counter of the polish loop
   void* inv_ws;
   size_t inv_bytes;
 };
@@ -249,6 +348,9 @@ size_t carve(void* base, int bs, int batch, bool wide, DecimWs* w) {
   w->active = reinterpret_cast<int*>(take(sizeof(int) * batch));
   w->n_active = reinterpret_cast<int*>(take(sizeof(int)));
   w->itc = reinterpret_cast<int*>(take(sizeof(int)));
+  w->pm = reinterpret_cast<int*>(take(sizeof(int) * batch));
+  w->ok = reinterpret_cast<int*>(take(sizeof(int) * batch));
+  w->itc2 = reinterpret_cast<int*>(take(sizeof(int)));
   w->inv_bytes = zinv_workspace_bytes(bs, batch, wide);
   w->inv_ws = take(w->inv_bytes);
   return off;
@@ -289,11 +391,11 @@ bt_status decimate_step(cudaStream_t st, int bs, int batch, DecimWs& w, int* inf
   return BT_OK;
 }
 
-// Graph mode: the iteration loop as a conditional while node of the graph being captured on st.
-bt_status decimate_loop_graph(cudaStream_t st, LoopCapture& loop, int bs, int batch, double tol, int maxit,
-                              DecimWs& w, int* iters, int* info, const Engine& E) {
-  set_int_kernel<<<1, 1, 0, st>>>(w.itc, 1); count_launch();
-  BT_CUDA_TRY(cudaGetLastError());
+// Graph mode: a loop as a conditional while node of the graph being captured on st.  The body
+// (one iteration, ending with a kernel that sets the loop condition through the handle) is
+// recorded by body(bst, handle) on the loop's body stream; the body runs at least once.
+template <class Body>
+bt_status while_node(cudaStream_t st, LoopCapture& loop, long long* body_launches, Body body) {
   cudaStreamCaptureStatus cs;
   cudaGraph_t g = nullptr;
   const cudaGraphNode_t* deps = nullptr;
@@ -313,24 +415,135 @@ bt_status decimate_loop_graph(cudaStream_t st, LoopCapture& loop, int bs, int ba
   cudaGraphNode_t node;
   BT_CUDA_TRY(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &p));
   BT_CUDA_TRY(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
-  cudaGraph_t body = p.conditional.phGraph_out[0];
+  cudaGraph_t bodyg = p.conditional.phGraph_out[0];
   cudaStream_t bst = loop.body_stream;
-  BT_CUDA_TRY(cudaStreamBeginCaptureToGraph(bst, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  BT_CUDA_TRY(cudaStreamBeginCaptureToGraph(bst, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   const long long l0 = launches_total();
-  bt_status rc = decimate_step(bst, bs, batch, w, info, E, true);
-  if (rc == BT_OK) {
-    check_dev_kernel<<<(batch + 255) / 256, 256, 0, bst>>>(batch, w.keys, w.flags, w.ref, tol, w.itc, w.active, iters,
-                                                           info, w.n_active); count_launch();
-    loop_ctl_kernel<<<1, 1, 0, bst>>>(h, w.n_active, w.itc, maxit); count_launch();
-    if (cudaGetLastError() != cudaSuccess) rc = BT_ERR_CUDA;
-  }
-  loop.body_launches = launches_total() - l0;
+  bt_status rc = body(bst, h);
+  if (rc == BT_OK && cudaGetLastError() != cudaSuccess) rc = BT_ERR_CUDA;
+  if (body_launches) *body_launches = launches_total() - l0;
   cudaGraph_t got = nullptr;
   const cudaError_t ce = cudaStreamEndCapture(bst, &got);
   if (rc != BT_OK) return rc;
   return ce == cudaSuccess ? BT_OK : BT_ERR_CUDA;
 }
 
+// Graph mode: the decimation loop as a conditional while node.
+bt_status decimate_loop_graph(cudaStream_t st, LoopCapture& loop, int bs, int batch, double tol, int maxit,
+                              DecimWs& w, int* iters, int* info, const Engine& E) {
+  set_int_kernel<<<1, 1, 0, st>>>(w.itc, 1); count_launch();
+  BT_CUDA_TRY(cudaGetLastError());
+  return while_node(st, loop, &loop.body_launches, [&](cudaStream_t bst, cudaGraphConditionalHandle h) {
+    BT_TRY(decimate_step(bst, bs, batch, w, info, E, true));
+    check_dev_kernel<<<(batch + 255) / 256, 256, 0, bst>>>(batch, w.keys, w.flags, w.ref, tol, w.itc, w.active, iters,
+                                                           info, w.n_active); count_launch();
+    loop_ctl_kernel<<<1, 1, 0, bst>>>(h, w.n_active, w.itc, maxit); count_launch();
+    return BT_OK;
+  });
+}
+
+// One doubling step of X = R + A X B on the active problems: X += (A X) B, then A <- A A and
+// B <- B B (B = A^H when herm).  With `fixed` the squares are copied back into A, B (the buffers
+// stay where a captured graph expects them); otherwise the pointers swap.  Ends with the
+// max-|.| reduction of the new A, B.
+bt_status stein_step(cudaStream_t st, int bs, int batch, zd*& A, zd*& B, bool herm, zd* X, SteinWs& w,
+                     const Engine& E, bool fixed) {
+  const long long bs2 = (long long)bs * bs, S = bs2;
+  const size_t mat_bytes = (size_t)batch * bs2 * sizeof(zd);
+  const zd one = zmake(1.0, 0.0), zero = zmake(0.0, 0.0);
+  BT_TRY(gemm(E, st, bs, bs, bs, one, Operand{A, bs, S, BT_OP_N}, Operand{X, bs, S, BT_OP_N}, zero, w.T, bs, S, batch, w.active));
+  const Operand opB = herm ? Operand{A, bs, S, BT_OP_C} : Operand{B, bs, S, BT_OP_N};
+  BT_TRY(gemm(E, st, bs, bs, bs, one, Operand{w.T, bs, S, BT_OP_N}, opB, one, X, bs, S, batch, w.active));
+  BT_TRY(gemm(E, st, bs, bs, bs, one, Operand{A, bs, S, BT_OP_N}, Operand{A, bs, S, BT_OP_N}, zero, w.A2, bs, S, batch, w.active));
+  if (!herm)
+    BT_TRY(gemm(E, st, bs, bs, bs, one, Operand{B, bs, S, BT_OP_N}, Operand{B, bs, S, BT_OP_N}, zero, w.B2, bs, S, batch, w.active));
+  if (fixed) {
+    BT_CUDA_TRY(cudaMemcpyAsync(A, w.A2, mat_bytes, cudaMemcpyDeviceToDevice, st));
+    if (!herm) BT_CUDA_TRY(cudaMemcpyAsync(B, w.B2, mat_bytes, cudaMemcpyDeviceToDevice, st));
+  } else {
+    std::swap(A, w.A2);
+    if (!herm) std::swap(B, w.B2);
+  }
+  BT_CUDA_TRY(cudaMemsetAsync(w.n_active, 0, sizeof(int), st));
+  return lead_max(st, 0, bs2, batch, A, herm ? A : B, w.active, w.keys, w.flags);
+}
+
+// The doubling loop: direct (one read-back of the active count per step) or, with `loop`, a
+// conditional while node.  ok[l] = 1 where problem l converged.  The swapped buffers of the
+// direct loop leave A, B pointing at either copy: their contents are scratch afterwards.
+bt_status stein_loop(cudaStream_t st, int bs, int batch, zd* A, zd* B, bool herm, zd* X, double tol, int maxit,
+                     const int* mask, int* ok, int* iters, SteinWs& w, int* h_pinned, long long* lead_iterations,
+                     const Engine& E, LoopCapture* loop, long long* body_launches, int* n_selected = nullptr) {
+  const double bs2 = (double)bs * bs;
+  stein_init_kernel<<<(batch + 255) / 256, 256, 0, st>>>(batch, mask, w.active, ok, iters); count_launch();
+  BT_CUDA_TRY(cudaGetLastError());
+  if (loop) {
+    set_int_kernel<<<1, 1, 0, st>>>(w.itc, 1); count_launch();
+    BT_CUDA_TRY(cudaGetLastError());
+    return while_node(st, *loop, body_launches, [&](cudaStream_t bst, cudaGraphConditionalHandle h) {
+      zd *a = A, *b = B;
+      BT_TRY(stein_step(bst, bs, batch, a, b, herm, X, w, E, true));
+      stein_check_dev_kernel<<<(batch + 255) / 256, 256, 0, bst>>>(batch, w.keys, w.flags, bs2, tol, w.itc, w.active,
+                                                                   ok, iters, w.n_active); count_launch();
+      loop_ctl_kernel<<<1, 1, 0, bst>>>(h, w.n_active, w.itc, maxit); count_launch();
+      return BT_OK;
+    });
+  }
+  int running = batch;
+  if (mask) {
+    std::vector<int> hm(batch);
+    if (cudaMemcpyAsync(hm.data(), mask, sizeof(int) * batch, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return BT_ERR_CUDA;
+    running = 0;
+    for (int v : hm) running += v != 0;
+  }
+  if (n_selected) *n_selected = running;
+  long long its = 0;
+  zd *a = A, *b = B;
+  SteinWs ws = w;  // the direct loop swaps buffers; the caller's struct keeps its pointers
+  for (int it = 1; it <= maxit && running > 0; ++it) {
+    its += running;
+    BT_TRY(stein_step(st, bs, batch, a, b, herm, X, ws, E, false));
+    stein_check_kernel<<<(batch + 255) / 256, 256, 0, st>>>(batch, ws.keys, ws.flags, bs2, tol, it, ws.active, ok,
+                                                            iters, ws.n_active); count_launch();
+    BT_CUDA_TRY(cudaGetLastError());
+    BT_CUDA_TRY(cudaMemcpyAsync(h_pinned, ws.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BT_CUDA_TRY(cudaStreamSynchronize(st));
+    running = *h_pinned;
+  }
+  if (lead_iterations) *lead_iterations = its;
+  return BT_OK;
+}
+
+// Newton step on the decimated leads with more than pol.after iterations (see the file header).
+// On entry x = e_s^{-1} for every decimated lead; on return x and e_s are corrected where the
+// doubling converged.
+constexpr double kPolishTol = 1e-12;  // relative size of the neglected doubling terms
+constexpr int kPolishMaxit = 64;
+bt_status polish_step(cudaStream_t st, int bs, int batch, const zd* m, const zd* n, const zd* np, zd* x,
+                      const int* mask, const int* iters, int* info, DecimWs& w, int* h_pinned, const Engine& E,
+                      LoopCapture* loop, Polish& pol) {
+  const long long bs2 = (long long)bs * bs, S = bs2;
+  const zd one = zmake(1.0, 0.0), zero = zmake(0.0, 0.0);
+  polish_mask_kernel<<<(batch + 255) / 256, 256, 0, st>>>(batch, mask, iters, info, pol.after, w.pm); count_launch();
+  BT_CUDA_TRY(cudaGetLastError());
+  // A = n x, B = x n', t = A n' = n x n', residual X = m - e_s - t
+  BT_TRY(gemm(E, st, bs, bs, bs, one, Operand{n, bs, S, BT_OP_N}, Operand{x, bs, S, BT_OP_N}, zero, w.a, bs, S, batch, w.pm));
+  BT_TRY(gemm(E, st, bs, bs, bs, one, Operand{x, bs, S, BT_OP_N}, Operand{np, bs, S, BT_OP_N}, zero, w.b, bs, S, batch, w.pm));
+  BT_TRY(gemm(E, st, bs, bs, bs, one, Operand{w.a, bs, S, BT_OP_N}, Operand{np, bs, S, BT_OP_N}, zero, w.t, bs, S, batch, w.pm));
+  dim3 g((unsigned)((bs2 + 255) / 256 < 64 ? (bs2 + 255) / 256 : 64), batch);
+  residual_kernel<<<g, 256, 0, st>>>(bs2, m, w.es, w.t, w.g, w.pm); count_launch();
+  BT_CUDA_TRY(cudaGetLastError());
+  SteinWs sw{w.ag, w.a2, w.b2, w.keys, w.flags, w.active, w.n_active, w.itc2};
+  BT_TRY(stein_loop(st, bs, batch, w.a, w.b, false, w.g, kPolishTol, kPolishMaxit, w.pm, w.ok, pol.iters, sw, h_pinned,
+                    &pol.lead_iterations, E, loop, &pol.body_launches, &pol.selected));
+  // e_s += d, x = e_s^{-1} where the doubling converged
+  add_masked_kernel<<<g, 256, 0, st>>>(bs2, w.es, w.g, w.ok); count_launch();
+  masked_copy_kernel<<<g, 256, 0, st>>>(bs2, w.es, x, w.ok); count_launch();
+  BT_CUDA_TRY(cudaGetLastError());
+  return zinv(st, bs, x, S, batch, info, w.inv_ws, w.inv_bytes, w.ok, &E);
+}
 
 // Direct mode: host-driven loop, one convergence read-back per iteration.
 bt_status decimate_loop_host(cudaStream_t st, int bs, int batch, double tol, int maxit, DecimWs& w, int* iters,
@@ -380,7 +593,7 @@ size_t decimate_workspace_bytes(int bs, int batch, bool wide) {
 bt_status decimate(cudaStream_t st, int bs, int batch, const zd* m, const zd* n, const zd* np, double tol,
                    int maxit, zd* x, zd* sigma, int* iters, int* info, void* ws, size_t ws_bytes,
                    int* iters_host_max, int* h_pinned, const int* mask, long long* lead_iterations,
-                   const Engine* eng, LoopCapture* loop) {
+                   const Engine* eng, LoopCapture* loop, Polish* polish) {
   const Engine fp64;
   const Engine& E = eng ? *eng : fp64;
   if (bs <= 0 || batch <= 0 || maxit <= 0 || batch > 65535) return BT_ERR_INVALID_ARG;
@@ -419,6 +632,10 @@ bt_status decimate(cudaStream_t st, int bs, int batch, const zd* m, const zd* n,
   const long long S = bs2;
   const zd one = zmake(1.0, 0.0), zero = zmake(0.0, 0.0);
   BT_TRY(zinv(st, bs, x, S, batch, info, w.inv_ws, w.inv_bytes, mask, &E));
+  if (polish && polish->after >= 0) {
+    if (!loop && !h_pinned) return BT_ERR_INVALID_ARG;
+    BT_TRY(polish_step(st, bs, batch, m, n, np, x, mask, iters, info, w, h_pinned, E, loop, *polish));
+  }
   if (sigma) {
     BT_TRY(gemm(E, st, bs, bs, bs, one, Operand{n, bs, S, BT_OP_N}, Operand{x, bs, S, BT_OP_N}, zero, w.t, bs, S, batch, nullptr));
     BT_TRY(gemm(E, st, bs, bs, bs, one, Operand{w.t, bs, S, BT_OP_N}, Operand{np, bs, S, BT_OP_N}, zero, sigma, bs, S, batch, nullptr));
@@ -426,6 +643,38 @@ bt_status decimate(cudaStream_t st, int bs, int batch, const zd* m, const zd* n,
   return BT_OK;
 }
 
+
+size_t stein_workspace_bytes(int bs, int batch) {
+  const size_t mat = align256((size_t)batch * bs * bs * sizeof(zd));
+  return 3 * mat + align256(sizeof(unsigned long long) * 2 * batch) + 2 * align256(sizeof(int) * batch) +
+         2 * align256(sizeof(int));
+}
+
+bt_status stein(cudaStream_t st, int bs, int batch, zd* A, zd* B, zd* X, double tol, int maxit, const int* mask,
+                int* ok, int* iters, void* ws, size_t ws_bytes, int* h_pinned, long long* lead_iterations,
+                const Engine* eng, LoopCapture* loop) {
+  const Engine fp64;
+  const Engine& E = eng ? *eng : fp64;
+  if (bs <= 0 || batch <= 0 || batch > 65535 || maxit <= 0 || !A || !X || !ok) return BT_ERR_INVALID_ARG;
+  if (!ws || ws_bytes < stein_workspace_bytes(bs, batch)) return BT_ERR_INVALID_ARG;
+  if (!loop && !h_pinned) return BT_ERR_INVALID_ARG;
+  const size_t mat = align256((size_t)batch * bs * bs * sizeof(zd));
+  char* p = static_cast<char*>(ws);
+  SteinWs w;
+  w.T = reinterpret_cast<zd*>(p); p += mat;
+  w.A2 = reinterpret_cast<zd*>(p); p += mat;
+  w.B2 = reinterpret_cast<zd*>(p); p += mat;
+  w.keys = reinterpret_cast<unsigned long long*>(p); p += align256(sizeof(unsigned long long) * 2 * batch);
+  w.flags = reinterpret_cast<int*>(p); p += align256(sizeof(int) * batch);
+  w.active = reinterpret_cast<int*>(p); p += align256(sizeof(int) * batch);
+  w.n_active = reinterpret_cast<int*>(p); p += align256(sizeof(int));
+  w.itc = reinterpret_cast<int*>(p);
+  long long body = 0;
+  BT_TRY(stein_loop(st, bs, batch, A, B, B == nullptr, X, tol, maxit, mask, ok, iters, w, h_pinned, lead_iterations,
+                    E, loop, &body));
+  if (loop) loop->body_launches += body;
+  return BT_OK;
+}
 
 bt_status invert_mask(cudaStream_t st, int batch, const int* a, int* out) {
   not_kernel<<<(batch + 255) / 256, 256, 0, st>>>(batch, a, out);

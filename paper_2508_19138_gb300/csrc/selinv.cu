@@ -45,6 +45,7 @@ struct bt_ctx {
   zd *lead_m = nullptr, *lead_n = nullptr, *lead_np = nullptr, *lead_x = nullptr, *lead_sig = nullptr;
   zd *obcL = nullptr, *obcG = nullptr;                // [2E][B2]
   int *lead_iters = nullptr, *lead_info = nullptr;    // [2E]
+  int* lead_piters = nullptr;                         // [2E] doubling iterations of the Newton step
   // contact memoization: surface functions of solved energies [cap][2][B2] + lead masks [2E]
   zd* memo_x = nullptr;
   int *lead_run = nullptr, *lead_conv = nullptr, *lead_dec = nullptr;
@@ -85,15 +86,18 @@ struct bt_ctx {
     double flops = 0.0;             // model flops without the decimation iterations
     long long launches = 0;         // kernels outside the decimation loop
     long long body_launches = 0;    // kernels per decimation iteration
+    long long polish_body = 0;      // kernels per doubling iteration of the Newton step
     bool decim = false;
   };
   std::vector<Captured> graphs;
   cudaStream_t body_st = nullptr;
   bt::LoopCapture* loop = nullptr;  // non-null while a chunk is being captured
-  int* h_iters = nullptr;           // [2E] pinned
+  int* h_iters = nullptr;           // [4E] pinned: decimation, then Newton-step iterations per lead
+  long long cap_polish_body = 0;    // kernels of one pass of the Newton step's doubling loop (capture)
   bool pending = false;
   int pending_Ec = 0;
   long long pending_body = 0;
+  long long pending_polish_body = 0;
   long long uncounted = 0;          // launches recorded during capture (not executed)
 };
 
@@ -160,6 +164,7 @@ size_t layout(bt_ctx* c, const bt_selinv_desc& d, char* base) {
     x->obcG = cv.take<zd>(2 * E * B2);
     x->lead_iters = cv.take<int>(2 * E);
     x->lead_info = cv.take<int>(2 * E);
+    x->lead_piters = cv.take<int>(2 * E);
     x->dec_bytes = bt::decimate_workspace_bytes(d.bs, (int)(2 * E), is_split(d) && d.split_scope == 1);
     x->dec_ws = cv.take<char>(x->dec_bytes);
     if (d.obc_memo) {
@@ -423,6 +428,7 @@ bt_status ctx_create(const bt_selinv_desc* desc, void* cuda_stream, void* ext_ws
   if (d.decim_maxit <= 0) d.decim_maxit = 100;
   if (d.memo_nfpi <= 0) d.memo_nfpi = 20;
   if (d.memo_capacity <= 0) d.memo_capacity = 4 * d.max_energies;
+  if (d.decim_newton_after == 0) d.decim_newton_after = 14;
   const size_t need = layout(nullptr, d, nullptr);
   if (d.hbm_budget_bytes && need > d.hbm_budget_bytes) {
     *err = "workspace exceeds hbm_budget_bytes";
@@ -465,8 +471,8 @@ bt_status ctx_create(const bt_selinv_desc* desc, void* cuda_stream, void* ext_ws
       return BT_ERR_INVALID_ARG;
     }
     if (cudaStreamCreateWithFlags(&c->body_st, cudaStreamNonBlocking) != cudaSuccess ||
-        (c->pinned ? cudaMallocHost(&c->h_iters, sizeof(int) * 2 * d.max_energies) != cudaSuccess
-                   : (c->h_iters = new int[2 * d.max_energies]) == nullptr)) {
+        (c->pinned ? cudaMallocHost(&c->h_iters, sizeof(int) * 4 * d.max_energies) != cudaSuccess
+                   : (c->h_iters = new int[4 * d.max_energies]) == nullptr)) {
       cudaGetLastError();
       bt_selinv_destroy(c);
       *err = "graph mode set-up failed";
@@ -533,17 +539,25 @@ namespace {
 void fold_pending(bt_ctx* c) {
   if (!c->pending) return;
   c->pending = false;
-  long long it_max = 0, lead_its = 0;
-  for (int l = 0; l < 2 * c->pending_Ec; ++l) {
+  long long it_max = 0, lead_its = 0, pit_max = 0, p_its = 0, p_leads = 0;
+  const int L = 2 * c->pending_Ec;
+  for (int l = 0; l < L; ++l) {
     const long long v = c->h_iters[l] > 0 ? c->h_iters[l] : 0;
     it_max = v > it_max ? v : it_max;
     lead_its += v;
+    const long long p = c->h_iters[L + l] > 0 ? c->h_iters[L + l] : 0;
+    pit_max = p > pit_max ? p : pit_max;
+    p_its += p;
+    p_leads += p > 0;
   }
   const double U = 8.0 * c->d.bs * (double)c->d.bs * c->d.bs;
   c->stats.decim_iterations += it_max;
   c->stats.lead_iterations += lead_its;
-  c->stats.kernel_launches += c->pending_body * it_max;
-  c->flops += 7.0 * U * (double)lead_its;
+  c->stats.newton_leads += p_leads;
+  c->stats.newton_iterations += p_its;
+  // the doubling loop body runs at least once per replay
+  c->stats.kernel_launches += c->pending_body * it_max + c->pending_polish_body * (pit_max > 0 ? pit_max : 1);
+  c->flops += 7.0 * U * (double)lead_its + 4.0 * U * (double)(p_its + p_leads);
   c->stats.flops_model = c->flops;
 }
 
@@ -743,15 +757,27 @@ bt_status solve_chunk_g(bt_ctx* c, const bt_bt* H, const bt_bt* S, const bt_bt* 
       dec_mask = c->lead_dec;
       c->flops += 3.0 * U * (double)fpi_its;
     }
+    bt::Polish pol;
+    pol.after = d.decim_newton_after;
+    pol.iters = c->lead_piters;
     bt_status s = bt::decimate(st, bs, 2 * Ec, c->lead_m, c->lead_n, c->lead_np, d.decim_tol, d.decim_maxit, c->lead_x,
                                c->lead_sig, c->lead_iters, c->lead_info, c->dec_ws, c->dec_bytes, &it_max,
-                               c->h_pinned, dec_mask, &lead_its, &c->eng_kept, c->loop);
+                               c->h_pinned, dec_mask, &lead_its, &c->eng_kept, c->loop, &pol);
     if (s != BT_OK) return set_err(c, s, "decimation failed to launch");
     c->stats.decim_iterations += it_max;
     c->stats.lead_iterations += lead_its;
     c->stats.fpi_iterations += fpi_its;
     // 7 products per lead-iteration, then x = e_s^{-1} and n x n' for every lead
     c->flops += 7.0 * U * (double)lead_its + 3.0 * U * 2.0 * Ec;
+    if (c->loop) {
+      c->cap_polish_body = pol.body_launches;
+    } else if (pol.after >= 0) {
+      // Newton step: 4 products per doubling iteration; n x, x n', n x n' and the inverse per lead
+      const long long p_leads = pol.lead_iterations > 0 ? pol.selected : 0;
+      c->stats.newton_leads += p_leads;
+      c->stats.newton_iterations += pol.lead_iterations;
+      c->flops += 4.0 * U * (double)(pol.lead_iterations + p_leads);
+    }
     if (d.obc_memo) {
       // keep this chunk's surface functions (oldest entries evicted first)
       for (int e = 0; e < Ec; ++e) {
@@ -1138,7 +1164,9 @@ bt_status run_chunk_graph(bt_ctx* c, const bt_bt* H, const bt_bt* S, const bt_bt
     g.flops = c->flops - f0;
     c->flops = f0;  // counted again below, as for every replay
     g.body_launches = loop.body_launches;
-    g.launches = recorded - loop.body_launches;
+    g.polish_body = c->cap_polish_body;
+    g.launches = recorded - loop.body_launches - c->cap_polish_body;
+    c->cap_polish_body = 0;
     g.decim = c->d.obc != 0;
     if (c->graphs.size() >= kMaxCaptured) {
       cudaGraphExecDestroy(c->graphs.front().exec);
@@ -1158,9 +1186,17 @@ bt_status run_chunk_graph(bt_ctx* c, const bt_bt* H, const bt_bt* S, const bt_bt
   if (g.decim) {
     if (cudaMemcpyAsync(c->h_iters, c->lead_iters, sizeof(int) * 2 * Ec, cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
       return set_err(c, BT_ERR_CUDA, "iteration read-back failed");
+    if (c->d.decim_newton_after >= 0) {
+      if (cudaMemcpyAsync(c->h_iters + 2 * Ec, c->lead_piters, sizeof(int) * 2 * Ec, cudaMemcpyDeviceToHost,
+                          c->st) != cudaSuccess)
+        return set_err(c, BT_ERR_CUDA, "iteration read-back failed");
+    } else {
+      std::memset(c->h_iters + 2 * Ec, 0, sizeof(int) * 2 * Ec);
+    }
     c->pending = true;
     c->pending_Ec = Ec;
     c->pending_body = g.body_launches;
+    c->pending_polish_body = g.polish_body;
   }
   return BT_OK;
 }

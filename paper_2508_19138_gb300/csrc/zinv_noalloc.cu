@@ -11,7 +11,11 @@
 //   * the array has BT_ZINV_NOALLOC_SCRATCH_BYTES bytes and exists on every GPU that loads the
 //     library, for the life of the process;
 //   * its device address is looked up once per device (cudaGetSymbolAddress) on the first call
-//     made with that device current, so make that first call before any stream capture;
+//     made with that device current.  Under CUDA's default lazy module loading, that lookup is
+//     also what loads this file's device code on the device, and with it reserves the array:
+//     the driver allocates then, and can fail with BT_ERR_CUDA if the device is already full.
+//     So make the first call on each device before any pool or arena takes the free memory, and
+//     before any stream capture; later calls allocate nothing;
 //   * all calls share the array: two calls whose work overlaps on the GPU (different streams,
 //     or different host threads) race on it; calls on one stream are ordered and safe;
 //   * nothing in the array needs to start at zero: every word is written before it is read,

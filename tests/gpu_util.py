@@ -1,5 +1,8 @@
 """Shared helpers of the GPU parity tests: run a synthetic system through the C ABI and compare
-block by block with the CPU oracle (relative Frobenius error with the C1 floor)."""
+block by block with the CPU oracle (relative Frobenius error per block, at the fixed tolerances
+below; lesser / greater blocks with the absolute allowance of lesser_floor).  The oracle's lead
+surface functions come from the eigen route (Eq. 6), which the CPU tests pin against an
+extended-precision decimation; FP64 decimation alone is up to ~1e-8 off near band edges."""
 import numpy as np
 
 import oracle
@@ -19,6 +22,19 @@ def lesser_floor(ref):
     info = ref.get("info") or {}
     sig = max([np.linalg.norm(info[k]) for k in ("R_L", "R_R") if k in info] + [0.0])
     return xr * xr * sig
+
+
+def unpack_upper(packed, bs):
+    """Full anti-Hermitian blocks from BT_LAYOUT_PACKED_UPPER storage, for the comparisons:
+    packed [..., bs (bs + 1) / 2] -> [..., bs, bs] with X_cr = -conj(X_rc) (Sec. 5.2)."""
+    packed = np.asarray(packed)
+    iu = np.triu_indices(bs)
+    out = np.zeros(packed.shape[:-1] + (bs, bs), dtype=np.complex128)
+    out[..., iu[0], iu[1]] = packed
+    low = -np.conj(np.swapaxes(out, -1, -2))
+    il = np.tril_indices(bs, -1)
+    out[..., il[0], il[1]] = low[..., il[0], il[1]]
+    return out
 
 
 def block_errors(gpu, ref, floor_frac=1e-14, abs_floor=0.0):
@@ -68,54 +84,45 @@ def run_g(sysg, max_energies=None, precision=0, split_slices=0, symmetrize=True,
     return res
 
 
-def compare_g(res, sysg, e_gpu, e_ref, tol=TOL_FP64, symmetrize=True, keys=None):
-    """Max per-block error of one energy against the dense oracle."""
-    ref = oracle.solve_g(sysg, e_ref, symmetrize=symmetrize)
+# Every comparison of the parity tests is recorded here; conftest prints a summary at the end of
+# the run: blocks compared per output, the largest relative error, and how many blocks passed
+# only through the absolute lesser/greater allowance of lesser_floor (with the largest own-norm
+# relative error among them).
+PARITY_LOG = []
+
+
+def record(test, key, e, own_rel, judged, tol, floor_used):
+    PARITY_LOG.append(dict(test=test, key=key, energy=int(e), own_rel=float(own_rel), judged=float(judged),
+                           tol=float(tol), floor_used=bool(floor_used)))
+
+
+def _current_test():
+    import os
+    return os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0]
+
+
+def compare_blocks(got, ref_blocks, key, e, tol, abs_floor=0.0):
+    """Per-block comparison of one output with the oracle: the error judged is relative to
+    max(|ref block|, 1e-14 max |ref|, abs_floor); every block is recorded in PARITY_LOG with its
+    error relative to its own norm.  Returns the worst judged error."""
+    judged = block_errors(got, ref_blocks, abs_floor=abs_floor)
+    own = block_errors(got, ref_blocks)
+    t = _current_test()
+    for j, o in zip(judged, own):
+        record(t, key, e, o, j, tol, floor_used=(o > tol and j <= tol))
+    return float(judged.max()) if judged.size else 0.0
+
+
+def compare_g(res, sysg, e_gpu, e_ref, tol=TOL_FP64, symmetrize=True, keys=None, surface="eig"):
+    """Worst per-block error of one energy against the dense oracle (contacts by the eigen route,
+    which the CPU tests check against extended precision).  Returns ({key: worst}, {key: worst}
+    for the outputs above tol)."""
+    ref = oracle.solve_g(sysg, e_ref, symmetrize=symmetrize, surface=surface)
     lg_floor = 0.01 * lesser_floor(ref)
     worst = {}
     for k in (keys or ("R_diag", "R_upper", "R_lower", "L_diag", "L_upper", "G_diag", "G_upper")):
         if k not in res or ref[k].shape[0] == 0:
             continue
-        errs = block_errors(res[k][e_gpu], ref[k], abs_floor=lg_floor if k[0] in "LG" else 0.0)
-        worst[k] = float(errs.max())
+        worst[k] = compare_blocks(res[k][e_gpu], ref[k], k, e_ref, tol, abs_floor=lg_floor if k[0] in "LG" else 0.0)
     bad = {k: v for k, v in worst.items() if not v <= tol}
-    return worst, bad
-
-
-def route_discrepancy(sysg, e, symmetrize=True):
-    """Per-output disagreement of two independent FP64 routes of the oracle at energy index e:
-    contacts by Sancho-Rubio decimation vs by the eigen (polynomial eigenproblem) route.  It
-    measures how far FP64 rounding alone moves the exact answer at this energy (large near
-    band edges at small eta).  Returns {key: max per-block relative difference} or {} when the
-    system has no contacts or the eigen route is not applicable."""
-    if not sysg.obc:
-        return {}
-    ref = oracle.solve_g(sysg, e, symmetrize=symmetrize)
-    orig = oracle.negf.sancho_rubio
-    oracle.negf.sancho_rubio = lambda m, n, np_, tol=1e-14, maxit=100: (oracle.surface_gf_eig(m, n, np_), 0, True)
-    try:
-        alt = oracle.solve_g(sysg, e, symmetrize=symmetrize)
-    except ValueError:
-        return {}
-    finally:
-        oracle.negf.sancho_rubio = orig
-    floor = 0.01 * lesser_floor(ref)
-    out = {}
-    for k in ("R_diag", "R_upper", "R_lower", "L_diag", "L_upper", "G_diag", "G_upper"):
-        if ref[k].shape[0] == 0:
-            continue
-        out[k] = float(block_errors(alt[k], ref[k], abs_floor=floor if k[0] in "LG" else 0.0).max())
-    return out
-
-
-def compare_g_derived(res, sysg, e_gpu, e_ref, tol=TOL_FP64, symmetrize=True, margin=10.0):
-    """compare_g with the tolerance of each output raised to margin x the FP64 route
-    discrepancy of the oracle at that energy (never below tol)."""
-    worst, _ = compare_g(res, sysg, e_gpu, e_ref, tol=np.inf, symmetrize=symmetrize)
-    disc = route_discrepancy(sysg, e_ref, symmetrize=symmetrize)
-    bad = {}
-    for k, v in worst.items():
-        lim = max(tol, margin * disc.get(k, 0.0))
-        if not v <= lim:
-            bad[k] = (v, lim)
     return worst, bad

@@ -107,7 +107,7 @@ def test_packed_upper_layout_formula():
     """BT_LAYOUT_PACKED_UPPER as the header states it: entry (r, c >= r) at r bs - r (r - 1) / 2 + (c - r);
     unpack_upper rebuilds the anti-Hermitian block from it."""
     import numpy as np
-    import paper_2508_19138_gb300 as pkg
+    from gpu_util import unpack_upper
     bs = 7
     rng = np.random.default_rng(3)
     X = rng.standard_normal((bs, bs)) + 1j * rng.standard_normal((bs, bs))
@@ -116,4 +116,4 @@ def test_packed_upper_layout_formula():
     for r in range(bs):
         for c in range(r, bs):
             packed[r * bs - r * (r - 1) // 2 + (c - r)] = A[r, c]
-    assert np.array_equal(pkg.unpack_upper(packed, bs), A)
+    assert np.array_equal(unpack_upper(packed, bs), A)

@@ -1,7 +1,7 @@
 """Stored expected values (tests/golden/, written by tests/golden/make_golden.py from the oracle
 only): the oracle must keep reproducing them (CPU), and the CUDA path must match them block by
-block (GPU) without running the oracle, under the stored per-energy floors and tolerances (the
-FP64 tolerance, raised only where the oracle's two contact routes themselves disagree)."""
+block (GPU) without running the oracle, under the stored per-energy floors at the FP64
+tolerance."""
 import json
 import os
 
@@ -30,7 +30,7 @@ def test_golden_oracle_reproduces_stored_values():
     s, d, blocks = load()
     assert np.array_equal(s.energies, np.array(d["energies"]))
     for e in range(len(s.energies)):
-        ref = oracle.solve_g(s, e)
+        ref = oracle.solve_g(s, e, surface="eig")
         for k in KEYS:
             errs = block_errors(ref[k], blocks[k][e], abs_floor=d["lesser_abs_floor"][e] if k[0] in "LG" else 0.0)
             assert errs.max() <= 1e-12, (k, e, errs.max())
@@ -61,5 +61,5 @@ def test_golden_gpu_matches_stored_values():
         for k in KEYS:
             errs = block_errors(res[k][e], blocks[k][e], abs_floor=d["lesser_abs_floor"][e] if k[0] in "LG" else 0.0)
             tol = d["tol"][e][k]
-            assert TOL_FP64 <= tol <= 1e-8
+            assert tol == TOL_FP64
             assert errs.max() <= tol, (k, e, errs.max(), tol)

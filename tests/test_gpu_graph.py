@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import synthetic
-from gpu_util import compare_g_derived
+from gpu_util import compare_g
 
 pytestmark = pytest.mark.gpu
 
@@ -62,13 +62,16 @@ def test_graph_replay_equals_direct_random_8x32():
         assert_identical(d, g)
         assert d["stats"]["decim_iterations"] == g["stats"]["decim_iterations"]
         assert d["stats"]["lead_iterations"] == g["stats"]["lead_iterations"]
+        # the Newton step after decimation (near-band-edge leads), captured as a second loop
+        assert d["stats"]["newton_leads"] == g["stats"]["newton_leads"] > 0
+        assert d["stats"]["newton_iterations"] == g["stats"]["newton_iterations"]
         assert d["stats"]["flops_model"] == pytest.approx(g["stats"]["flops_model"], rel=1e-12)
     # the replayed results are also right (not just repeatable)
     r = res[True][1]
     s1 = synthetic.random_device(synthetic.BASE_SEED, 8, 32, 64)
     s1.energies = E1
     for e in (0, 17, 40, 63):
-        _, bad = compare_g_derived(r, s1, e, e)
+        _, bad = compare_g(r, s1, e, e)
         assert not bad, (e, bad)
 
 

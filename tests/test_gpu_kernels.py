@@ -128,18 +128,17 @@ def test_decimation_matches_oracle(pkg, bs):
     import torch
     rng = np.random.default_rng(bs)
     batch = 3
-    ms, ns, nps, refs, its, disc = [], [], [], [], [], []
+    ms, ns, nps, refs, its = [], [], [], [], []
     for b in range(batch):
         h00 = cplx(rng, (bs, bs))
         h00 = (h00 + h00.conj().T) / 2 / np.sqrt(bs)
         h01 = 0.5 * cplx(rng, (bs, bs)) / np.sqrt(bs)
         z = (-0.5 + 0.5 * b) + 1e-4j
         m, n, n_ = z * np.eye(bs) - h00, -h01, -h01.conj().T
-        x, it, ok = oracle.sancho_rubio(m, n, n_)
+        _, it, ok = oracle.sancho_rubio(m, n, n_)
         assert ok
-        # FP64 sensitivity of the surface function at this z: the two oracle routes' disagreement
-        x_eig = oracle.surface_gf_eig(m, n, n_)
-        disc.append(np.linalg.norm(x - x_eig) / np.linalg.norm(x))
+        # reference: the direct route (Eq. 6); at eta = 1e-4 plain FP64 decimation is accurate
+        x = oracle.surface_gf_eig(m, n, n_)
         ms.append(m); ns.append(n); nps.append(n_); refs.append(x); its.append(it)
     dm, dn, dnp = (torch.from_numpy(np.ascontiguousarray(np.stack(a))).cuda() for a in (ms, ns, nps))
     x = torch.empty_like(dm)
@@ -151,7 +150,7 @@ def test_decimation_matches_oracle(pkg, bs):
     got = x.cpu().numpy()
     gi = iters.cpu().numpy()
     for b in range(batch):
-        tol = max(1e-10, 10 * disc[b])
+        tol = 1e-10
         assert np.linalg.norm(got[b] - refs[b]) / np.linalg.norm(refs[b]) < tol
         assert abs(int(gi[b]) - its[b]) <= 1
         sref = ns[b] @ refs[b] @ nps[b]

@@ -1,11 +1,11 @@
 """Contact memoization (Sec. 5.3): a second solve of the same energies starts the fixed-point
-iteration of Eq. 5 from the kept surface functions instead of decimating; the results agree
-with a fresh solve, and far fewer decimation iterations run."""
+iteration of Eq. 5 from the kept surface functions instead of decimating; every solve matches
+the oracle at the FP64 tolerance, and far fewer decimation iterations run."""
 import numpy as np
 import pytest
 
 import synthetic
-from gpu_util import block_errors
+from gpu_util import TOL_FP64, block_errors, compare_g
 
 pytestmark = pytest.mark.gpu
 
@@ -14,7 +14,19 @@ def _solve(solver, s):
     import torch
     outs, status = solver.solve(s.energies)
     torch.cuda.synchronize()
-    return {w: o.diag.cpu().numpy() for w, o in outs.items()}, status.cpu().numpy()
+    res = {}
+    for w, o in outs.items():
+        res[w + "_diag"] = o.diag.cpu().numpy()
+        res[w + "_upper"] = o.upper.cpu().numpy()
+        if o.lower is not None:
+            res[w + "_lower"] = o.lower.cpu().numpy()
+    return res, status.cpu().numpy()
+
+
+def _against_oracle(res, s):
+    for e in range(len(s.energies)):
+        _, bad = compare_g(res, s, e, e, tol=TOL_FP64)
+        assert not bad, (e, bad)
 
 
 def test_memoized_contacts_repeat_and_perturbed():
@@ -34,9 +46,10 @@ def test_memoized_contacts_repeat_and_perturbed():
     # update stalls at the FP64 noise floor (near band edges) fall back to decimation
     assert b["lead_iterations"] - a["lead_iterations"] <= 0.25 * a["lead_iterations"]
     assert b["fpi_iterations"] > 0
-    for w in "RLG":
-        for e in range(len(s.energies)):
-            assert block_errors(second[w][e], first[w][e]).max() < 1e-11
+    _against_oracle(first, s)
+    _against_oracle(second, s)
+    for k in first:
+        assert block_errors(second[k], first[k]).max() < 1e-11
     # SCBA-like step: scattering self-energy changed by 1 %; memoized vs fresh solve
     s2 = synthetic.nanoribbon(nb=5, n_puc=2, puc=26, n_energies=8)
     s2.sigR_diag = s2.sigR_diag * 1.01
@@ -52,9 +65,8 @@ def test_memoized_contacts_repeat_and_perturbed():
     assert (st3 == 0).all() and (st4 == 0).all()
     decim_memo = c["lead_iterations"] - b["lead_iterations"]
     assert decim_memo < f["lead_iterations"]
-    for w in "RLG":
-        for e in range(len(s2.energies)):
-            assert block_errors(third[w][e], ref[w][e]).max() < 1e-9
+    _against_oracle(third, s2)
+    _against_oracle(ref, s2)
     memo.close()
     fresh.close()
     torch.cuda.synchronize()

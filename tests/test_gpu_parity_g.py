@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 import synthetic
-from gpu_util import TOL_FP64, TOL_SPLIT, block_errors, compare_g, compare_g_derived, run_g
+from gpu_util import TOL_FP64, TOL_SPLIT, block_errors, compare_g, run_g
 
 pytestmark = pytest.mark.gpu
 
@@ -17,7 +17,7 @@ def test_random_device_8x32_all_energies():
     assert (res["status"] == 0).all()
     worst_all = {}
     for e in range(len(s.energies)):
-        worst, bad = compare_g_derived(res, s, e, e)
+        worst, bad = compare_g(res, s, e, e)
         assert not bad, f"energy {e}: {bad}"
         for k, v in worst.items():
             worst_all[k] = max(worst_all.get(k, 0.0), v)
@@ -30,7 +30,7 @@ def test_ragged_sizes(nb, bs):
     res = run_g(s)
     assert (res["status"] == 0).all()
     for e in range(5):
-        _, bad = compare_g_derived(res, s, e, e)
+        _, bad = compare_g(res, s, e, e)
         assert not bad, f"nb={nb} bs={bs} e={e}: {bad}"
 
 
@@ -39,7 +39,7 @@ def test_chunking_ragged_last_chunk():
     res = run_g(s, max_energies=4)  # chunks 4 + 4 + 3
     assert (res["status"] == 0).all()
     for e in range(11):
-        _, bad = compare_g_derived(res, s, e, e)
+        _, bad = compare_g(res, s, e, e)
         assert not bad
 
 
@@ -60,7 +60,7 @@ def test_nanoribbon_wide_blocks_cluster_panels():
         res = run_g(s, precision=precision)
         assert (res["status"] == 0).all()
         for e in range(3):
-            _, bad = compare_g_derived(res, s, e, e, tol=tol)
+            _, bad = compare_g(res, s, e, e, tol=tol)
             assert not bad, f"precision={precision} e={e}: {bad}"
 
 
@@ -70,7 +70,7 @@ def test_nanoribbon_diagonal_sigma():
     res = run_g(s)
     assert (res["status"] == 0).all()
     for e in range(6):
-        _, bad = compare_g_derived(res, s, e, e)
+        _, bad = compare_g(res, s, e, e)
         assert not bad, f"e={e}: {bad}"
 
 
@@ -117,8 +117,8 @@ def test_block_sigma_with_off_diagonals():
         M = oracle.bt_dense(z * np.eye(bs)[None] - s.H_diag - Rd[e], -s.H_upper - Ru[e],
                             -np.conj(np.swapaxes(s.H_upper, 1, 2)) - Rl[e])
         Mb = lambda i, j: M[i * bs:(i + 1) * bs, j * bs:(j + 1) * bs]
-        xL, _, _ = oracle.sancho_rubio(Mb(0, 0), Mb(1, 0), Mb(0, 1))
-        xR, _, _ = oracle.sancho_rubio(Mb(nb - 1, nb - 1), Mb(nb - 2, nb - 1), Mb(nb - 1, nb - 2))
+        xL = oracle.surface_gf_eig(Mb(0, 0), Mb(1, 0), Mb(0, 1))
+        xR = oracle.surface_gf_eig(Mb(nb - 1, nb - 1), Mb(nb - 2, nb - 1), Mb(nb - 1, nb - 2))
         SL = Mb(1, 0) @ xL @ Mb(0, 1)
         SR = Mb(nb - 2, nb - 1) @ xR @ Mb(nb - 1, nb - 2)
         fL = float(oracle.fermi(s.energies[e], s.mu_left, s.kT))
@@ -156,7 +156,7 @@ def test_unsymmetrized_output_is_anti_hermitian_and_symmetrized_matches():
         X = raw["L_diag"][e]
         want = 0.5 * (X - np.conj(np.swapaxes(X, 1, 2)))
         assert block_errors(sym["L_diag"][e], want, abs_floor=fl).max() <= 1e-11
-        _, bad = compare_g_derived(raw, s, e, e, symmetrize=False)
+        _, bad = compare_g(raw, s, e, e, symmetrize=False)
         assert not bad
 
 
@@ -176,7 +176,7 @@ def test_antihermitian_sandwiches_match_full_products():
             want = 0.5 * (X - np.conj(np.swapaxes(X, 1, 2)))
             assert block_errors(sym[key + "_diag"][e], want, abs_floor=fl).max() <= 1e-11
             assert block_errors(sym[key + "_upper"][e], raw[key + "_upper"][e], abs_floor=fl).max() <= 1e-11
-        _, bad = compare_g_derived(sym, s, e, e)
+        _, bad = compare_g(sym, s, e, e)
         assert not bad, (e, bad)
 
 
@@ -253,7 +253,7 @@ def test_split_precision_path(maker):
     res = run_g(s, precision=1)
     assert (res["status"] == 0).all()
     for e in range(len(s.energies)):
-        _, bad = compare_g_derived(res, s, e, e, tol=TOL_SPLIT)
+        _, bad = compare_g(res, s, e, e, tol=TOL_SPLIT)
         assert not bad, f"e={e}: {bad}"
 
 
@@ -276,15 +276,17 @@ def test_split_scope_all_products():
     solver.close()
     assert (res["status"] == 0).all()
     for e in range(len(s.energies)):
-        _, bad = compare_g_derived(res, s, e, e, tol=TOL_SPLIT)
+        _, bad = compare_g(res, s, e, e, tol=TOL_SPLIT)
         assert not bad, f"e={e}: {bad}"
 
 
 def test_packed_upper_storage_of_lesser_greater():
-    """Sec. 5.2 storage: lesser/greater diagonal blocks written as packed upper triangles equal the
-    full symmetrised blocks exactly; the packed layout is refused for G^R and unsymmetrised runs."""
+    """Sec. 5.2 storage: lesser/greater diagonal blocks written as packed upper triangles match
+    the oracle's symmetrised blocks at the FP64 tolerance (and the full-layout run exactly); the
+    packed layout is refused for G^R and unsymmetrised runs."""
     import torch
     import paper_2508_19138_gb300 as pkg
+    from gpu_util import unpack_upper
     from paper_2508_19138_gb300.highlevel import GSolver
     s = synthetic.random_device(61, 4, 70, 3)
     solver = GSolver(s.nb, s.bs, 3, s.eta, s.kT, s.mu_left, s.mu_right, obc=True)
@@ -295,10 +297,15 @@ def test_packed_upper_storage_of_lesser_greater():
     solver.solve(s.energies, packed, st2)
     torch.cuda.synchronize()
     assert packed["L"].diag.shape == (3, s.nb, s.bs * (s.bs + 1) // 2)
+    res = {"R_diag": packed["R"].diag.cpu().numpy(), "R_upper": packed["R"].upper.cpu().numpy()}
     for w in ("L", "G"):
-        got = pkg.unpack_upper(packed[w].diag.cpu().numpy(), s.bs)
+        got = unpack_upper(packed[w].diag.cpu().numpy(), s.bs)
         assert np.array_equal(got, full[w].diag.cpu().numpy())
         assert np.array_equal(packed[w].upper.cpu().numpy(), full[w].upper.cpu().numpy())
+        res[w + "_diag"], res[w + "_upper"] = got, packed[w].upper.cpu().numpy()
+    for e in range(3):
+        _, bad = compare_g(res, s, e, e)
+        assert not bad, (e, bad)
     bad = {"R": pkg.BTOut(packed["L"].diag, None, None, pkg.BT_LAYOUT_PACKED_UPPER)}
     with pytest.raises(pkg.BTError):
         solver.solve(s.energies, bad, st1)

@@ -4,9 +4,8 @@ the arena budget, and latency statistics are reported."""
 import numpy as np
 import pytest
 
-import oracle
 import synthetic
-from gpu_util import block_errors
+from gpu_util import compare_g
 
 pytestmark = pytest.mark.gpu
 
@@ -72,10 +71,16 @@ def test_mixed_stream_equals_alone():
         for w in "RLG":
             assert np.array_equal(outs[w].diag.cpu().numpy(), alone[w][0])
             assert np.array_equal(outs[w].upper.cpu().numpy(), alone[w][1])
-    # and one request against the oracle
-    s, (outs, _) = systems[0], held[0]
-    ref = oracle.solve_g(s, 2)
-    assert block_errors(outs["R"].diag.cpu().numpy()[2], ref["R_diag"]).max() < 1e-9
+    # and every block of every request against the oracle
+    for s, (outs, _) in zip(systems, held):
+        res = {}
+        for w in "RLG":
+            res[w + "_diag"] = outs[w].diag.cpu().numpy()
+            res[w + "_upper"] = outs[w].upper.cpu().numpy()
+        res["R_lower"] = outs["R"].lower.cpu().numpy()
+        for e in range(len(s.energies)):
+            _, bad = compare_g(res, s, e, e)
+            assert not bad, (s.nb, s.bs, e, bad)
 
 
 def test_failed_request_is_reported_and_others_complete():

@@ -35,6 +35,9 @@ def test_noalloc_matches_allocating_entry_point_on_two_calls(n, batch):
         r, g = ref.cpu().numpy(), got.cpu().numpy()
         for b in range(batch):
             assert np.linalg.norm(g[b] - r[b]) / np.linalg.norm(r[b]) < 1e-12, (call, b)
+            # and independently of the library: LAPACK's inverse of the same matrix
+            want = np.linalg.inv(A[b])
+            assert np.linalg.norm(g[b] - want) / np.linalg.norm(want) < 1e-11, (call, b)
 
 
 def test_noalloc_rejects_requests_beyond_its_scratch():
