@@ -71,6 +71,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-blocks", type=int, default=10)
+    p.add_argument("--no-errors", action="store_true", help="skip the per-result errors against the oracle")
+    p.add_argument("--no-sublines", action="store_true",
+                   help="default workload: skip the 8x32 and W 16x1024 sub-lines")
     return p.parse_args()
 
 
@@ -171,6 +174,34 @@ def cpu_oracle_sample(sysg, sample_blocks: int, energy_index: int):
     return dt, (nb / k) ** 3, k
 
 
+SAMPLED_KEYS = ("R_diag", "R_upper", "R_lower", "L_diag", "L_upper", "G_diag", "G_upper")
+
+
+def _nanoribbon_reference(e_orig, rows, threads):
+    """Worker (spawned process): the oracle's selected blocks of the 40 x 416 nanoribbon at grid
+    energy e_orig for block rows `rows` (banded LU, contacts by the eigen route), and the absolute
+    lesser / greater allowance 0.01 |X^R|^2 |B^R_OBC| of the comparisons."""
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = str(threads)
+    import numpy as np
+
+    import oracle
+    import synthetic
+    s = synthetic.nanoribbon_40x416()
+    ref = oracle.solve_g_sampled(s, e_orig, list(rows), surface="eig")
+    o = oracle.obc_self_energies(s, e_orig, surface="eig")
+    xr = max(np.linalg.norm(ref[i]["R_diag"]) for i in ref)
+    floor = 0.01 * xr * xr * max(np.linalg.norm(o["R_L"]), np.linalg.norm(o["R_R"]))
+    return ref, floor
+
+
+def block_err(got, ref, floor=0.0):
+    """Relative Frobenius error of one block, the denominator at least `floor`."""
+    import numpy as np
+    den = max(float(np.linalg.norm(ref)), floor)
+    return float(np.linalg.norm(got - ref)) / den if den > 0 else float(np.linalg.norm(got))
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -253,6 +284,32 @@ def run_ours(args):
         outs, status = solver.allocate_outputs(eps)
     torch.cuda.synchronize()
     n_batches = max(1, nE // eps)
+    # ---- per-result errors against the oracle (outside the timed region) ----
+    # the last timed step's energies are known now; the oracle's reference for the large workload
+    # is computed by a spawned CPU process while the GPU runs (half the host cores)
+    j_last = replicas.batch_index(rank, args.warmup + args.steps - 1, n_batches)
+    big = args.workload == "nanoribbon"
+    err_rows = (0, sysg.nb // 2 - 1, sysg.nb - 2) if big else tuple(range(sysg.nb))
+    ref_job = None
+    if rank == 0 and big and not args.no_errors:
+        import multiprocessing as mp
+        ref_pool = mp.get_context("spawn").Pool(1)
+        ref_job = ref_pool.apply_async(_nanoribbon_reference,
+                                       (int(perm[j_last * eps]), err_rows, max(1, host_cores() // 2)))
+    snaps = {}
+
+    def snapshot():
+        """Host copies of the blocks the error check reads: the large workload's first energy of
+        the last step on rows err_rows; small workloads every block of every energy."""
+        snap = {}
+        for w, o in outs.items():
+            for part in ("diag", "upper", "lower"):
+                t = getattr(o, part)
+                if t is None:
+                    continue
+                snap[f"{w}_{part}"] = ({i: t[0, i].cpu().numpy() for i in err_rows if i < t.shape[1]} if big
+                                       else t.cpu().numpy())
+        return snap
     # bytes the step touches: x^R, x^<, x^> and the outputs, 16 B per complex element
     step_bytes = 7 * eps * sysg.nb * sysg.bs * sysg.bs * 16
     l2_small = step_bytes < 4 * 129e6
@@ -298,6 +355,8 @@ def run_ours(args):
     step_ms = timed_steps(one_step)
     clk = clocks.stop()
     st1 = solver.stats()
+    if rank == 0 and not args.no_errors:
+        snaps["fp64" if precision == pkg.BT_FP64 else "split"] = snapshot()
     total_ms = sum(step_ms)
     bad = int((status.cpu().numpy() != 0).sum())
     total_ms_max = replicas.max_over_ranks(total_ms, dist, device="cuda")
@@ -326,6 +385,9 @@ def run_ours(args):
     achieved = 8.0 * bs ** 3 * eps / (kms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS,
+                # DFMA work actually issued: 3 real multiply-adds per complex multiply-add (6 b^3 flops
+                # per b x b x b complex product instead of the algorithmic 8 b^3)
+                "dfma_issue_frac": 0.75 * achieved / FP64_PEAK_TFLOPS,
                 "traffic": ZGEMM_TRAFFIC_BYTES if (bs, eps) == ZGEMM_TRAFFIC_SHAPE else None,
                 "kernel": f"zgemm_kernel (FP64 DFMA) {bs}^3 x {eps}", "launch_ms": kms,
                 "peak_source": "nominal GB300 FP64: 152 SMs x 2 DFMA/clk x 2.07 GHz = 1.25 TFLOP/s; 1.20 attainable"}
@@ -365,6 +427,8 @@ def run_ours(args):
             for w in range(args.warmup):
                 sp_step(w)
             ms = replicas.max_over_ranks(sum(timed_steps(sp_step)), dist, device="cuda")
+            if rank == 0 and not args.no_errors:
+                snaps[f"split_scope{scope}"] = snapshot()
             flops_sp = sp.stats()["flops_model"]
             split_lines[f"scope{scope}"] = {
                 "value": eps * args.steps * world / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
@@ -373,54 +437,7 @@ def run_ours(args):
                 "what": ("sweep products sliced (bf16 tcgen05, 6 slices); inversions and decimation FP64"
                          if scope == 0 else "every block product sliced; inversion panels and pivots FP64")}
             sp.close()
-        # tensor-core GEMM at the sweep's launch shape, slicing kernels included.  The calls are
-        # captured into a CUDA graph and replayed, so that the host's per-call cost (ctypes,
-        # tensor-map encoding) does not starve the device between the short launches.
-        A = torch.randn(eps, bs, bs, dtype=torch.complex128, device="cuda")
-        B = torch.randn(eps, bs, bs, dtype=torch.complex128, device="cuda")
-        Cm = torch.empty_like(A)
-        S = args.slices or 6
-        ws = torch.empty(pkg.bt_split_zgemm_workspace_bytes(bs, bs, bs, S, eps), dtype=torch.uint8, device="cuda")
-
-        def split_call():
-            pkg.bt_split_zgemm_batched(bs, bs, bs, 1.0, A, bs, bs * bs, 0, B, bs, bs * bs, 0, 0.0, Cm, bs, bs * bs,
-                                       eps, S, workspace=ws, stream=torch.cuda.current_stream())
-
-        with torch.cuda.stream(stream):
-            split_call()
-        torch.cuda.synchronize()
-        timing = "graph-replayed"
-        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        try:
-            cg = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(cg):
-                for _ in range(reps):
-                    split_call()
-            cg.replay()
-            torch.cuda.synchronize()
-            k0.record()
-            cg.replay()
-            k1.record()
-            torch.cuda.synchronize()
-            del cg
-        except RuntimeError:
-            timing = "direct launches (graph capture failed)"
-            torch.cuda.synchronize()
-            with torch.cuda.stream(stream):
-                k0.record(stream)
-                for _ in range(reps):
-                    split_call()
-                k1.record(stream)
-            torch.cuda.synchronize()
-        sms = k0.elapsed_time(k1) / reps
-        pairs = S * (S + 1) // 2
-        bf16 = pairs * 2.0 * (2 * bs) * bs * (2 * bs) * eps / (sms / 1e3) / 1e12
-        split_lines["roofline"] = {"bound": "tensor", "achieved": bf16, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
-                                   "frac": bf16 / BF16_PEAK_TFLOPS, "traffic": None,
-                                   "kernel": f"bt_split_zgemm_batched {bs}^3 x {eps}, {S} slices ({pairs} bf16 products), slicing included, {timing}",
-                                   "fp64_eq_tflops": 8.0 * bs ** 3 * eps / (sms / 1e3) / 1e12, "launch_ms": sms,
-                                   "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)"}
-        del A, B, Cm, ws
+        split_lines["roofline"] = split_gemm_roofline(pkg, bs, eps, args.slices or 6, stream, reps)
 
     line = None
     if rank == 0:
@@ -436,11 +453,19 @@ def run_ours(args):
                                   else f"per-step working set ~{step_bytes / 1e9:.0f} GB exceeds L2; no flush"),
                            "parallelism": f"energy replicas x{world} (no collective)"},
                 "fp64_eq_tflops": flops_step / (statistics.median(step_ms) / 1e3) / 1e12,
-                "fp64_eq_frac_of_peak": flops_step / (statistics.median(step_ms) / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                # model flops (8 b^3 per block product of Eq. 9-12, however the kernels compute it) over
+                # the nominal FP64 rate: above 1 because the GEMM issues 3 real products per complex one
+                # and the anti-Hermitian sandwiches compute half of each block (roofline.dfma_issue_frac
+                # is the hardware fraction)
+                "fp64_eq_vs_nominal_peak": flops_step / (statistics.median(step_ms) / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
                 "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
                 "decim_iterations_per_step": (st1["decim_iterations"] - st0["decim_iterations"]) / args.steps,
                 "nonzero_status": bad, "roofline": roofline, "clocks": clk, "gpu_launches": launches,
                 "e2e": e2e, "split": split_lines}
+        if not args.no_errors:
+            line["errors"] = result_errors(args, snaps, ref_job, sysg, perm, j_last, eps, err_rows)
+            if ref_job is not None:
+                ref_pool.close()
         if not args.no_cpu_baseline and world == 1:
             dt, scale, k = cpu_oracle_sample(sysg, args.cpu_sample_blocks, 101 % nE)
             line["cpu_baseline"] = {
@@ -451,9 +476,98 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
-    if line is not None:
-        print(json.dumps(line), flush=True)
-    return 0
+    return line
+
+
+def result_errors(args, snaps, ref_job, sysg, perm, j_last, eps, rows):
+    """Largest per-block relative Frobenius error of each measured path's last step against the
+    oracle (contacts by the eigen route; lesser / greater blocks with the absolute allowance
+    0.01 |X^R|^2 |B^R_OBC|): the large workload on the first energy of the step and block rows
+    `rows` (banded-LU oracle), the small one on every block of every energy."""
+    import numpy as np
+
+    import oracle
+    out = {"tolerance": {"fp64": 1e-10, "split": 1e-8}}
+    if ref_job is not None:
+        ref, floor = ref_job.get(timeout=1800)
+        for path, snap in snaps.items():
+            worst = 0.0
+            for key, blocks in snap.items():
+                for i, got in blocks.items():
+                    if key in ref[i]:
+                        worst = max(worst, block_err(got, ref[i][key], floor if key[0] in "LG" else 0.0))
+            out[path] = worst
+        out["sample"] = (f"grid energy {int(perm[j_last * eps])} (first of the last timed step), block rows "
+                         f"{list(rows)}, every output; oracle: banded LU of the whole system")
+        return out
+    sub = sysg.subset(np.arange(j_last * eps, j_last * eps + eps))
+    refs = [oracle.solve_g(sub, p, surface="eig") for p in range(eps)]
+    floors = []
+    for r in refs:
+        xr = max(np.linalg.norm(b) for b in r["R_diag"])
+        floors.append(0.01 * xr * xr * max(np.linalg.norm(r["info"]["R_L"]), np.linalg.norm(r["info"]["R_R"])))
+    for path, snap in snaps.items():
+        worst = 0.0
+        for key, arr in snap.items():
+            for p in range(eps):
+                for i in range(refs[p][key].shape[0]):
+                    worst = max(worst, block_err(arr[p, i], refs[p][key][i], floors[p] if key[0] in "LG" else 0.0))
+        out[path] = worst
+    out["sample"] = f"every block of the {eps} energies of the last timed step; oracle: dense inverse"
+    return out
+
+
+def split_gemm_roofline(pkg, bs, eps, S, stream, reps=5):
+    """The tensor-core complex GEMM (bt_split_zgemm_batched, slicing kernels included) at a
+    sweep's launch shape, bs^3 x eps, against the measured bf16 peak.  The calls are captured into
+    a CUDA graph and replayed, so that the host's per-call cost (ctypes, tensor-map encoding) does
+    not starve the device between the short launches."""
+    import torch
+    A = torch.randn(eps, bs, bs, dtype=torch.complex128, device="cuda")
+    B = torch.randn(eps, bs, bs, dtype=torch.complex128, device="cuda")
+    Cm = torch.empty_like(A)
+    ws = torch.empty(pkg.bt_split_zgemm_workspace_bytes(bs, bs, bs, S, eps), dtype=torch.uint8, device="cuda")
+
+    def split_call():
+        pkg.bt_split_zgemm_batched(bs, bs, bs, 1.0, A, bs, bs * bs, 0, B, bs, bs * bs, 0, 0.0, Cm, bs, bs * bs,
+                                   eps, S, workspace=ws, stream=torch.cuda.current_stream())
+
+    with torch.cuda.stream(stream):
+        split_call()
+    torch.cuda.synchronize()
+    timing = "graph-replayed"
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    try:
+        cg = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(cg):
+            for _ in range(reps):
+                split_call()
+        cg.replay()
+        torch.cuda.synchronize()
+        k0.record()
+        cg.replay()
+        k1.record()
+        torch.cuda.synchronize()
+        del cg
+    except RuntimeError:
+        timing = "direct launches (graph capture failed)"
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            k0.record(stream)
+            for _ in range(reps):
+                split_call()
+            k1.record(stream)
+        torch.cuda.synchronize()
+    sms = k0.elapsed_time(k1) / reps
+    pairs = S * (S + 1) // 2
+    bf16 = pairs * 2.0 * (2 * bs) * bs * (2 * bs) * eps / (sms / 1e3) / 1e12
+    del A, B, Cm, ws
+    return {"bound": "tensor", "achieved": bf16, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": bf16 / BF16_PEAK_TFLOPS, "traffic": None,
+            "kernel": f"bt_split_zgemm_batched {bs}^3 x {eps}, {S} slices ({pairs} bf16 products), slicing "
+                      f"included, {timing}",
+            "fp64_eq_tflops": 8.0 * bs ** 3 * eps / (sms / 1e3) / 1e12, "launch_ms": sms,
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)"}
 
 
 def run_e2e(args, pkg, sysg, solver, eps, rank, world, barrier, dist, n_chunks=2):
@@ -513,6 +627,43 @@ def run_e2e(args, pkg, sysg, solver, eps, rank, world, barrier, dist, n_chunks=2
             "entry_point": f"bt_selinv_solve_host (pinned host buffers), one call over {nst} steps x {eps} energies"}
 
 
+def w_golden_errors(pkg, V, batches, ws, eps, solve_batch, oR, oL, oG):
+    """Energy 64 of the W system against the stored oracle values (tests/golden/w16x1024_e64.npz,
+    oracle.solve_w_sampled: block rows 0, 7, 15; per block its Frobenius norm and 512 seeded
+    entries): the Frobenius error estimated from the sampled entries, relative to the block norm.
+    The batch holding energy 64 is solved once more outside the timed region."""
+    import importlib.util
+
+    import numpy as np
+    here = os.path.join(ROOT, "tests", "golden")
+    path = os.path.join(here, "w16x1024_e64.npz")
+    if not os.path.exists(path):
+        return {"unavailable": "tests/golden/w16x1024_e64.npz missing"}
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(here, "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    gold = np.load(path)
+    e_star = int(gold["energy"])
+    for j, b in enumerate(batches):
+        if e_star in b[0]:
+            break
+    else:
+        return {"unavailable": f"energy {e_star} is in no batch"}
+    solve_batch(j)
+    import torch
+    torch.cuda.synchronize()
+    pos = int(np.nonzero(batches[j][0] == e_star)[0][0])
+    outs = {"R": oR, "L": oL, "G": oG}
+    worst = 0.0
+    for name, fro, vals in zip(gold["names"], gold["fro"], gold["vals"]):
+        i, key = str(name).split(":")
+        blk = getattr(outs[key[0]], key.split("_")[1])[pos, int(i)].cpu().numpy()
+        d = np.abs(blk.reshape(-1)[mg.w_sample_indices(ws.bs, int(i), key)] - vals)
+        worst = max(worst, float(np.sqrt(np.mean(d * d)) * ws.bs / fro))
+    return {"max_block_err_est": worst, "sample": (f"energy {e_star}, block rows 0, 7, 15, every output: Frobenius "
+                                                   "error estimated from 512 stored oracle entries per block")}
+
+
 def run_w(args):
     """W system (16 cells of 1024 atoms, 256 energies): P^R, P^<> per energy built on the device
     from the seeded bases before the timed region; one step = one solve over a batch."""
@@ -563,6 +714,10 @@ def run_w(args):
         idx, PR, PL, PG = batches[j % len(batches)]
         pkg.bt_selinv_solve(ctx, V, None, PR, PL, PG, ws.energies[idx], oR, oL, oG, status)
 
+    def solve_batch(j):
+        with torch.cuda.stream(stream):
+            step(j)
+
     for w in range(args.warmup):
         step(w)
     torch.cuda.synchronize()
@@ -589,9 +744,13 @@ def run_w(args):
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
             "nonzero_status": int((status.cpu().numpy() != 0).sum()), "clocks": clk,
             "gpu_launches": int(st1["kernel_launches"] - st0["kernel_launches"])}
+    if precision == pkg.BT_SPLIT:
+        line["roofline"] = split_gemm_roofline(pkg, bs, eps, args.slices or 6, stream)
+    if not args.no_errors:
+        line["errors"] = w_golden_errors(pkg, V, batches, ws, eps, solve_batch, oR, oL, oG)
+        line["errors"]["tolerance"] = 1e-10 if precision == pkg.BT_FP64 else 1e-8
     ctx.close()
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def run_serving(args):
@@ -669,15 +828,44 @@ def run_serving(args):
     return 0
 
 
+def sublines(args):
+    """Lines of the other workloads, measured after the default one (one GPU): the 8 x 32 random
+    device (all 64 energies per step; FP64 and both split scopes) and the W system 16 x 1024
+    (split, steps of 4 energies), each with its own step counts and errors against the oracle."""
+    import copy
+    out = {}
+    a0 = copy.copy(args)
+    a0.workload, a0.energies_per_step, a0.steps, a0.warmup = "random8x32", 0, 20, 3
+    a0.no_e2e, a0.no_cpu_baseline = True, True
+    try:
+        out["random8x32"] = run_ours(a0)
+    except Exception as exc:  # a sub-line never takes the main line down
+        out["random8x32"] = {"unavailable": f"{type(exc).__name__}: {exc}"[:300]}
+    a2 = copy.copy(args)
+    a2.workload, a2.energies_per_step, a2.steps, a2.warmup, a2.precision = "w16x1024", 4, 2, 1, "split"
+    try:
+        out["w16x1024_split"] = run_w(a2)
+    except Exception as exc:
+        out["w16x1024_split"] = {"unavailable": f"{type(exc).__name__}: {exc}"[:300]}
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "w16x1024":
-        return run_w(args)
-    if args.workload == "serving":
+        line = run_w(args)
+    elif args.workload == "serving":
         return run_serving(args)
-    return run_ours(args)
+    else:
+        line = run_ours(args)
+        if (line is not None and args.workload == "nanoribbon" and not args.no_sublines
+                and int(os.environ.get("WORLD_SIZE", "1")) == 1):
+            line["sublines"] = sublines(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    return 0
 
 
 if __name__ == "__main__":

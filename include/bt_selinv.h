@@ -111,7 +111,13 @@ typedef struct {
                           symmetrisation stay FP64                                              */
   int split_slices;    /* BT_SPLIT: slices per operand (0 = default 6, range 2..8)            */
   int symmetrize;      /* 1: lesser/greater diagonal blocks returned as (X - X^H)/2 (Sec. 5.2) */
-  int obc;             /* 1: Sancho-Rubio contacts on both ends (G only, nb >= 2)             */
+  int obc;             /* 1: contacts on both ends (nb >= 2), each lead repeating the device's
+                          edge cell.  G: Sancho-Rubio surface functions and fluctuation-
+                          dissipation (Sec. 4.2, Eq. 4).  W: the lead cells repeat the edge
+                          cell of V and P and its coupling inward; retarded boundary by
+                          decimation (Eq. 4), lesser / greater boundary by the Stein equation
+                          w = q + a w a^H (Eq. 7; solved by doubling), plus the edge cells'
+                          products with the first lead cell                                   */
   double eta;          /* G: z = E + i eta                                                     */
   double kT;           /* contact temperature (energy units of H)                              */
   double mu_left;      /* contact Fermi levels                                                 */
@@ -326,7 +332,9 @@ BT_API bt_status bt_zinv_batched_noalloc(int n, void* A, long long strideA, int 
                                          void* stream);
 
 /* Surface Green's function of semi-infinite leads, x = (m - n x n')^{-1} (Eq. 4), by
- * Sancho-Rubio decimation for `batch` independent leads (m, n, n' each [batch][bs][bs]).
+ * Sancho-Rubio decimation for `batch` independent leads (m, n, n' each [batch][bs][bs]); leads
+ * that needed more than 14 iterations then get one Newton step on x^{-1} (see
+ * bt_selinv_desc.decim_newton_after), which restores FP64 accuracy near band edges.
  * Writes x [batch][bs][bs] and the boundary block sigma = n x n' [batch][bs][bs];
  * iters_device[b] = iterations used, info_device[b] = 0 / BT_ERR_NOT_CONVERGED / _SINGULAR /
  * _NONFINITE (x and sigma of lead b are then undefined).
@@ -335,6 +343,17 @@ BT_API bt_status bt_decimate_workspace_bytes(int bs, int batch, size_t* bytes);
 BT_API bt_status bt_decimate_batched(int bs, int batch, const void* m, const void* n, const void* n_prime,
                               double tol, int maxit, void* x, void* sigma, int* iters_device,
                               int* info_device, void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Test hook (no counterpart in the paper).  Every wait of the tensor-core GEMM's pipeline on a
+ * shared-memory barrier is bounded (2 s); when one expires, the CTA records BT_ERR_TIMEOUT, stops
+ * issuing work, waits (bounded) for the copies and products it already issued, frees its tensor
+ * memory and exits, and every energy of the chunk gets BT_ERR_TIMEOUT in the solve's status.
+ * With ns > 0, the MMA warp of every later launch first waits up to ns nanoseconds on a barrier
+ * that nothing completes, so that this path runs on demand; 0 turns the hook off.  Process-wide,
+ * read when a launch is issued (a captured graph keeps the value it was captured with).
+ * ------------------------------------------------------------------------------------- */
+BT_API void bt_debug_split_stall_ns(unsigned long long ns);
 
 #ifdef __cplusplus
 }

@@ -70,10 +70,11 @@ SIGNATURES = {
     "bt_zinv_workspace_bytes": [_I, _I, C.POINTER(C.c_size_t)],
     "bt_zinv_batched": [_I, _P, _LL, _I, _P, _P, _SZ, _P],
     "bt_zinv_batched_noalloc": [_I, _P, _LL, _I, _P, _P],
+    "bt_debug_split_stall_ns": [C.c_ulonglong],
     "bt_decimate_workspace_bytes": [_I, _I, C.POINTER(C.c_size_t)],
     "bt_decimate_batched": [_I, _I, _P, _P, _P, _D, _I, _P, _P, _P, _P, _P, _SZ, _P],
 }
-RESTYPES = {"bt_selinv_last_error": C.c_char_p}
+RESTYPES = {"bt_selinv_last_error": C.c_char_p, "bt_debug_split_stall_ns": None}
 
 _lib = None
 

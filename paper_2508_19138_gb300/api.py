@@ -17,6 +17,7 @@ __all__ = [
     "bt_selinv_solve", "bt_selinv_solve_host", "bt_selinv_destroy", "bt_selinv_last_error", "bt_selinv_get_stats",
     "bt_zgemm_batched", "bt_split_zgemm_workspace_bytes", "bt_split_zgemm_batched", "bt_zinv_workspace_bytes",
     "bt_zinv_batched", "bt_zinv_batched_noalloc", "bt_decimate_workspace_bytes", "bt_decimate_batched", "library",
+    "bt_debug_split_stall_ns",
 ]
 
 
@@ -257,6 +258,12 @@ def bt_zinv_batched_noalloc(n, A, strideA, batch, info, stream=None) -> None:
     rc = N.load().bt_zinv_batched_noalloc(n, _ptr(A, torch.complex128), strideA, batch, _ptr(info, torch.int32),
                                           _stream(stream))
     _check(rc, None, "zinv_noalloc")
+
+
+def bt_debug_split_stall_ns(ns: int) -> None:
+    """Test hook: later tensor-core GEMM launches first stall their MMA warp up to ns nanoseconds on
+    a barrier nothing completes, so that the bounded-wait timeout path runs (0 = off)."""
+    N.load().bt_debug_split_stall_ns(int(ns))
 
 
 def bt_decimate_workspace_bytes(bs, batch) -> int:

@@ -297,6 +297,19 @@ bt_status write_diagvec(cudaStream_t st, int bs, int nblk, int batch, const zd* 
   return BT_OK;
 }
 
+__global__ void flag_status_kernel(int E, const int* __restrict__ flag, int* __restrict__ status) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  // a timed-out product leaves everything computed after it meaningless: the flag takes precedence
+  if (e < E && *flag != 0) status[e] = *flag;
+}
+
+bt_status flag_status(cudaStream_t st, int E, const int* flag, int* status) {
+  if (E <= 0) return BT_OK;
+  flag_status_kernel<<<(E + 127) / 128, 128, 0, st>>>(E, flag, status); count_launch();
+  BT_CUDA_TRY(cudaGetLastError());
+  return BT_OK;
+}
+
 bt_status merge_status(cudaStream_t st, int E, const int* info, int n_sources, long long src_stride, int* status) {
   if (E <= 0) return BT_OK;
   merge_status_kernel<<<(E + 127) / 128, 128, 0, st>>>(E, info, n_sources, src_stride, status); count_launch();

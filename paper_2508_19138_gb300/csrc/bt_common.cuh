@@ -82,13 +82,16 @@ struct Engine {
   int slices = 0;
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  int* err = nullptr;  // sliced products: one device word set to BT_ERR_TIMEOUT by a bounded wait
 };
 
 // Split-precision (sliced bf16 tensor-core) variant of zgemm; see split_gemm.cu.
 size_t split_workspace_bytes(int m, int n, int k, int slices, int batch);
+// A bounded wait that expires sets err[b * err_stride] = BT_ERR_TIMEOUT for the batch entry b of
+// the CTA (err may be null; err_stride 0 makes it one word for the whole call).
 bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A, Operand B, zd beta,
                       zd* C, int ldc, long long strideC, int batch, int slices, void* ws,
-                      size_t ws_bytes, const int* active);
+                      size_t ws_bytes, const int* active, int* err = nullptr, long long err_stride = 0);
 
 // C = alpha op(A) op(B) + beta C on the engine's kernel.
 bt_status gemm(const Engine& eng, cudaStream_t st, int m, int n, int k, zd alpha, Operand A, Operand B, zd beta,
@@ -137,13 +140,16 @@ bt_status decimate(cudaStream_t st, int bs, int batch, const zd* m, const zd* n,
 // X <- X + A X B, A <- A A, B <- B B until bs^2 max|A| max|B| <= tol.  X holds R on entry; A and B
 // are overwritten.  mask[l] == 0 leaves problem l alone (mask may be null); ok[l] = 1 where the
 // doubling converged within maxit, else 0 (X is then a partial sum); iters[l] = doublings.
-// With `loop` (graph capture) the doubling loop is a conditional while node and the counts are
-// left on the device; otherwise *lead_iterations = doublings summed over the problems.
+// With `loop` (graph capture) the doubling loop is a conditional while node (its body's kernel
+// count in *body_launches) and the counts are left on the device; otherwise *lead_iterations =
+// doublings summed over the problems.
 size_t stein_workspace_bytes(int bs, int batch);
 bt_status stein(cudaStream_t st, int bs, int batch, zd* A, zd* B, zd* X, double tol, int maxit, const int* mask,
                 int* ok, int* iters, void* ws, size_t ws_bytes, int* h_pinned, long long* lead_iterations,
-                const Engine* eng = nullptr, LoopCapture* loop = nullptr);
+                const Engine* eng = nullptr, LoopCapture* loop = nullptr, long long* body_launches = nullptr);
 bt_status invert_mask(cudaStream_t st, int batch, const int* a, int* out);  // out = !a
+// info[l] = ok[l] ? 0 : code (masked-out problems, mask[l] == 0, get 0)
+bt_status status_from_ok(cudaStream_t st, int batch, const int* ok, const int* mask, int code, int* info);
 // Fixed-point iteration x <- (m - n x n')^{-1} (Eq. 5) from the given x for leads with run[l];
 // conv[l] = 1 where it converged to tol within nfpi iterations.
 bt_status fixed_point(cudaStream_t st, int bs, int batch, const zd* m, const zd* n, const zd* np, zd* x,

@@ -633,8 +633,11 @@ bt_status decimate(cudaStream_t st, int bs, int batch, const zd* m, const zd* n,
   const zd one = zmake(1.0, 0.0), zero = zmake(0.0, 0.0);
   BT_TRY(zinv(st, bs, x, S, batch, info, w.inv_ws, w.inv_bytes, mask, &E));
   if (polish && polish->after >= 0) {
-    if (!loop && !h_pinned) return BT_ERR_INVALID_ARG;
-    BT_TRY(polish_step(st, bs, batch, m, n, np, x, mask, iters, info, w, h_pinned, E, loop, *polish));
+    int* hp = h_pinned;
+    if (!loop && !hp && cudaMallocHost(&hp, 64) != cudaSuccess) return BT_ERR_CUDA;
+    const bt_status ps = polish_step(st, bs, batch, m, n, np, x, mask, iters, info, w, hp, E, loop, *polish);
+    if (hp != h_pinned) cudaFreeHost(hp);
+    BT_TRY(ps);
   }
   if (sigma) {
     BT_TRY(gemm(E, st, bs, bs, bs, one, Operand{n, bs, S, BT_OP_N}, Operand{x, bs, S, BT_OP_N}, zero, w.t, bs, S, batch, nullptr));
@@ -652,7 +655,7 @@ size_t stein_workspace_bytes(int bs, int batch) {
 
 bt_status stein(cudaStream_t st, int bs, int batch, zd* A, zd* B, zd* X, double tol, int maxit, const int* mask,
                 int* ok, int* iters, void* ws, size_t ws_bytes, int* h_pinned, long long* lead_iterations,
-                const Engine* eng, LoopCapture* loop) {
+                const Engine* eng, LoopCapture* loop, long long* body_launches) {
   const Engine fp64;
   const Engine& E = eng ? *eng : fp64;
   if (bs <= 0 || batch <= 0 || batch > 65535 || maxit <= 0 || !A || !X || !ok) return BT_ERR_INVALID_ARG;
@@ -672,7 +675,20 @@ bt_status stein(cudaStream_t st, int bs, int batch, zd* A, zd* B, zd* X, double 
   long long body = 0;
   BT_TRY(stein_loop(st, bs, batch, A, B, B == nullptr, X, tol, maxit, mask, ok, iters, w, h_pinned, lead_iterations,
                     E, loop, &body));
-  if (loop) loop->body_launches += body;
+  if (body_launches) *body_launches = body;
+  return BT_OK;
+}
+
+__global__ void status_from_ok_kernel(int batch, const int* __restrict__ ok, const int* __restrict__ mask, int code,
+                                      int* __restrict__ info) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l < batch) info[l] = (mask && mask[l] == 0) || ok[l] ? 0 : code;
+}
+
+bt_status status_from_ok(cudaStream_t st, int batch, const int* ok, const int* mask, int code, int* info) {
+  status_from_ok_kernel<<<(batch + 255) / 256, 256, 0, st>>>(batch, ok, mask, code, info);
+  count_launch();
+  BT_CUDA_TRY(cudaGetLastError());
   return BT_OK;
 }
 
@@ -746,8 +762,10 @@ extern "C" bt_status bt_decimate_batched(int bs, int batch, const void* m, const
   if (!m || !n || !n_prime || !x || !iters_device || !info_device) return BT_ERR_INVALID_ARG;
   if (!(tol > 0.0)) tol = 1e-14;
   if (maxit <= 0) maxit = 100;
+  bt::Polish pol;
+  pol.after = 14;  // leads with more decimation iterations get the Newton step
   return bt::decimate(static_cast<cudaStream_t>(stream), bs, batch, static_cast<const zd*>(m),
                       static_cast<const zd*>(n), static_cast<const zd*>(n_prime), tol, maxit, static_cast<zd*>(x),
                       static_cast<zd*>(sigma), iters_device, info_device, workspace, workspace_bytes, nullptr, nullptr,
-                      nullptr, nullptr);
+                      nullptr, nullptr, nullptr, nullptr, &pol);
 }

@@ -65,5 +65,8 @@ bt_status write_packed(cudaStream_t st, int bs, int nblk, int batch, const zd* s
                        zd* dst, long long d_e);
 bt_status shift_diag(cudaStream_t st, int bs, int batch, zd* X, long long sX, double v);  // X += v I
 bt_status merge_status(cudaStream_t st, int E, const int* info, int n_sources, long long src_stride, int* status);
+// status[e] = *flag for every e when *flag != 0 (a chunk-wide error word that overrides the
+// numerical failures recorded after it)
+bt_status flag_status(cudaStream_t st, int E, const int* flag, int* status);
 
 }  // namespace bt

@@ -41,6 +41,8 @@ struct bt_ctx {
   zd *BdL = nullptr, *BdG = nullptr, *BuL = nullptr, *BuG = nullptr;  // W: B^<> blocks
   zd *Td = nullptr, *Tu = nullptr, *Tl = nullptr;     // W: V P products [E][N or N-1][B2]
   zd *X2u = nullptr, *X2l = nullptr;                  // W: X^R_{i,i+2}, X^R_{i+2,i} [E][N-2][B2]
+  zd* wl[11] = {};                                    // W contacts: lead temporaries [2E][B2]
+  int *w_ok = nullptr, *w_info = nullptr;             // W contacts: Stein convergence, status [2E]
   zd* t[12] = {};                                     // [E][B2] temporaries
   zd *lead_m = nullptr, *lead_n = nullptr, *lead_np = nullptr, *lead_x = nullptr, *lead_sig = nullptr;
   zd *obcL = nullptr, *obcG = nullptr;                // [2E][B2]
@@ -55,6 +57,7 @@ struct bt_ctx {
   int memo_next = 0;
   zd* z = nullptr;
   double *fL = nullptr, *fR = nullptr, *Edev = nullptr;
+  int* tflag = nullptr;  // BT_ERR_TIMEOUT from a bounded wait of a sliced product in this chunk
   void* inv_ws = nullptr;
   size_t inv_bytes = 0;
   void* dec_ws = nullptr;
@@ -153,6 +156,11 @@ size_t layout(bt_ctx* c, const bt_selinv_desc& d, char* base) {
     const size_t N2 = N > 2 ? N - 2 : 1;
     x->X2u = cv.take<zd>(E * N2 * B2);
     x->X2l = cv.take<zd>(E * N2 * B2);
+    if (d.obc) {
+      for (int i = 0; i < 11; ++i) x->wl[i] = cv.take<zd>(2 * E * B2);
+      x->w_ok = cv.take<int>(2 * E);
+      x->w_info = cv.take<int>(2 * E);
+    }
   }
   if (d.obc) {
     x->lead_m = cv.take<zd>(2 * E * B2);
@@ -176,6 +184,7 @@ size_t layout(bt_ctx* c, const bt_selinv_desc& d, char* base) {
     }
   }
   x->z = cv.take<zd>(E);
+  x->tflag = cv.take<int>(1);
   x->fL = cv.take<double>(E);
   x->fR = cv.take<double>(E);
   x->Edev = cv.take<double>(E);
@@ -200,10 +209,10 @@ bt_status validate_desc(const bt_selinv_desc* d, std::string* why) {
   if (d->precision != BT_FP64 && d->precision != BT_SPLIT) return fail("unknown precision");
   if (d->precision == BT_SPLIT && (d->split_slices != 0 && (d->split_slices < 2 || d->split_slices > 8)))
     return fail("split_slices must be 0 or in [2, 8]");
-  if (d->obc && d->system != BT_SYS_G) return fail("Sancho-Rubio contacts are defined for the G system only");
   if (d->obc && d->nb < 2) return fail("contacts from the edge blocks need nb >= 2");
-  if (d->obc && !(d->kT > 0.0)) return fail("kT must be > 0 with contacts");
+  if (d->obc && d->system == BT_SYS_G && !(d->kT > 0.0)) return fail("kT must be > 0 with contacts");
   if (d->obc_memo && !d->obc) return fail("contact memoization needs obc = 1");
+  if (d->obc_memo && d->system != BT_SYS_G) return fail("contact memoization is for the G system");
   if (d->graph != 0 && d->graph != 1) return fail("graph must be 0 or 1");
   if (d->graph && d->obc_memo) return fail("graph mode and contact memoization are exclusive");
   if (d->split_scope != 0 && d->split_scope != 1) return fail("split_scope must be 0 or 1");
@@ -261,7 +270,7 @@ bt_status prod(bt_ctx* c, int Ec, double alpha, const Blk& A, const Blk& B, doub
   c->flops += units * 8.0 * bs * (double)bs * bs * Ec;
   if (is_split(c->d)) {
     BT_TRY(bt::split_zgemm(c->st, bs, bs, bs, zmake(a, 0.0), opnd(A, bs), opnd(B, bs), zmake(beta, 0.0), C, bs, sC,
-                           Ec, slices_of(c->d), c->split_ws, c->split_bytes, nullptr));
+                           Ec, slices_of(c->d), c->split_ws, c->split_bytes, nullptr, c->tflag, 0));
     // the sliced product computes every entry; its result is projected onto the anti-Hermitian
     // matrices so that, as on the FP64 engine, the sandwiches come out exactly anti-Hermitian
     if (antiherm && c->d.symmetrize) return bt::antiherm_project(c->st, bs, Ec, C, sC);
@@ -480,7 +489,8 @@ bt_status ctx_create(const bt_selinv_desc* desc, void* cuda_stream, void* ext_ws
     }
   }
   c->stats.workspace_bytes = need;
-  if (is_split(d) && d.split_scope == 1) c->eng_kept = bt::Engine{kept_slices_of(d), c->split_ws, c->split_bytes};
+  if (is_split(d) && d.split_scope == 1)
+    c->eng_kept = bt::Engine{kept_slices_of(d), c->split_ws, c->split_bytes, c->tflag};
   if (d.obc_memo) {
     c->memo_key.assign(d.memo_capacity, 0);
     c->memo_used.assign(d.memo_capacity, 0);
@@ -619,6 +629,37 @@ bt_status write_diag_out(bt_ctx* c, int Ec, const zd* src, const bt_bt_out* o, l
   return bt::write_blocks(c->st, bs, N, Ec, src, B2, NB2, static_cast<zd*>(o->diag) + e0 * NB2, B2, NB2, mode);
 }
 
+// a2: Sancho-Rubio decimation of the chunk's 2 Ec leads (c->lead_m, lead_n, lead_np -> lead_x and
+// lead_sig = n x n'), with the Newton step for slowly decaying leads; statistics and model flops.
+bt_status decimate_leads(bt_ctx* c, int Ec, const int* dec_mask) {
+  const bt_selinv_desc& d = c->d;
+  const int bs = d.bs;
+  const double U = 8.0 * bs * (double)bs * bs;
+  int it_max = 0;
+  long long lead_its = 0;
+  bt::Polish pol;
+  pol.after = d.decim_newton_after;
+  pol.iters = c->lead_piters;
+  bt_status s = bt::decimate(c->st, bs, 2 * Ec, c->lead_m, c->lead_n, c->lead_np, d.decim_tol, d.decim_maxit, c->lead_x,
+                             c->lead_sig, c->lead_iters, c->lead_info, c->dec_ws, c->dec_bytes, &it_max, c->h_pinned,
+                             dec_mask, &lead_its, &c->eng_kept, c->loop, &pol);
+  if (s != BT_OK) return set_err(c, s, "decimation failed to launch");
+  c->stats.decim_iterations += it_max;
+  c->stats.lead_iterations += lead_its;
+  // 7 products per lead-iteration, then x = e_s^{-1} and n x n' for every lead
+  c->flops += 7.0 * U * (double)lead_its + 3.0 * U * 2.0 * Ec;
+  if (c->loop) {
+    c->cap_polish_body += pol.body_launches;
+  } else if (pol.after >= 0) {
+    // Newton step: 4 products per doubling iteration; n x, x n', n x n' and the inverse per lead
+    const long long p_leads = pol.lead_iterations > 0 ? pol.selected : 0;
+    c->stats.newton_leads += p_leads;
+    c->stats.newton_iterations += pol.lead_iterations;
+    c->flops += 4.0 * U * (double)(pol.lead_iterations + p_leads);
+  }
+  return BT_OK;
+}
+
 bt_status solve_chunk_g(bt_ctx* c, const bt_bt* H, const bt_bt* S, const bt_bt* sR, const bt_bt* sL, const bt_bt* sG,
                         long long e0, int Ec, const bt_bt_out* oR, const bt_bt_out* oL, const bt_bt_out* oG,
                         int* status) {
@@ -722,8 +763,7 @@ bt_status solve_chunk_g(bt_ctx* c, const bt_bt* H, const bt_bt* S, const bt_bt* 
     BT_TRY(bt::assemble_m(st, bs, Ec, off_args(0, true, c->lead_np, B2)));
     BT_TRY(bt::assemble_m(st, bs, Ec, off_args(N - 2, true, c->lead_n + Ec * B2, B2)));
     BT_TRY(bt::assemble_m(st, bs, Ec, off_args(N - 2, false, c->lead_np + Ec * B2, B2)));
-    int it_max = 0;
-    long long lead_its = 0, fpi_its = 0;
+    long long fpi_its = 0;
     const double U = 8.0 * bs * (double)bs * bs;
     const int* dec_mask = nullptr;
     std::vector<int> slots;
@@ -757,27 +797,8 @@ bt_status solve_chunk_g(bt_ctx* c, const bt_bt* H, const bt_bt* S, const bt_bt* 
       dec_mask = c->lead_dec;
       c->flops += 3.0 * U * (double)fpi_its;
     }
-    bt::Polish pol;
-    pol.after = d.decim_newton_after;
-    pol.iters = c->lead_piters;
-    bt_status s = bt::decimate(st, bs, 2 * Ec, c->lead_m, c->lead_n, c->lead_np, d.decim_tol, d.decim_maxit, c->lead_x,
-                               c->lead_sig, c->lead_iters, c->lead_info, c->dec_ws, c->dec_bytes, &it_max,
-                               c->h_pinned, dec_mask, &lead_its, &c->eng_kept, c->loop, &pol);
-    if (s != BT_OK) return set_err(c, s, "decimation failed to launch");
-    c->stats.decim_iterations += it_max;
-    c->stats.lead_iterations += lead_its;
+    BT_TRY(decimate_leads(c, Ec, dec_mask));
     c->stats.fpi_iterations += fpi_its;
-    // 7 products per lead-iteration, then x = e_s^{-1} and n x n' for every lead
-    c->flops += 7.0 * U * (double)lead_its + 3.0 * U * 2.0 * Ec;
-    if (c->loop) {
-      c->cap_polish_body = pol.body_launches;
-    } else if (pol.after >= 0) {
-      // Newton step: 4 products per doubling iteration; n x, x n', n x n' and the inverse per lead
-      const long long p_leads = pol.lead_iterations > 0 ? pol.selected : 0;
-      c->stats.newton_leads += p_leads;
-      c->stats.newton_iterations += pol.lead_iterations;
-      c->flops += 4.0 * U * (double)(pol.lead_iterations + p_leads);
-    }
     if (d.obc_memo) {
       // keep this chunk's surface functions (oldest entries evicted first)
       for (int e = 0; e < Ec; ++e) {
@@ -910,6 +931,7 @@ bt_status solve_chunk_w(bt_ctx* c, const bt_bt* V, const bt_bt* PR, const bt_bt*
 
   // ---- a1 (W): M~ = I - V P^R ----
   const PT pr = mkP(PR);
+  const bool wobc = d.obc != 0;
   for (int i = 0; i < N; ++i) {
     zd* md = c->Md + i * B2;
     BT_TRY(prod(c, Ec, -1.0, Vb(i, i), Pb(pr, i, i), 0.0, md, NB2));
@@ -925,13 +947,122 @@ bt_status solve_chunk_w(bt_ctx* c, const bt_bt* V, const bt_bt* PR, const bt_bt*
       BT_TRY(prod(c, Ec, -1.0, Vb(i + 1, i + 1), Pb(pr, i + 1, i), 1.0, ml, N1B2));
     }
   }
-  // ---- a1 (W): B^<> = (V P^<>) V^H, diagonal and upper blocks ----
   const bool needL = oL && (oL->diag || oL->upper);
   const bool needG = oG && (oG->diag || oG->upper);
   const bool need[2] = {needL, needG};
   const PT plg[2] = {mkP(PL), mkP(PG)};
   zd* Bd[2] = {c->BdL, c->BdG};
   zd* Bu[2] = {c->BuL, c->BuG};
+
+  // ---- W contacts (Sec. 4.2: the retarded boundary by Eq. 4, the lesser / greater boundary by
+  // the Stein equation of Eq. 7) ----
+  // Each lead repeats the device's edge cell of V and P and its coupling to the next cell inward:
+  // the left lead cell 0 and coupling (0,1), the right lead cell N-1 and coupling (N-2,N-1).  M and
+  // B^<> stay block-tridiagonal over the whole chain.  For a bulk lead cell k (virtual index 1,
+  // neighbours 0 and 2; "away" is 0 on the left, 2 on the right), with m = M_kk, n = M_{k,away},
+  // n' = M_{away,k}, b = B_kk and c = B_{away,k}:
+  //   x = (m - n x n')^{-1} (decimation),  y = n x c,  a = x n,  q = x (b - y + y^H) x^H,
+  //   w = q + a w a^H (Stein equation, doubling),  B^R_OBC = n x n',  B^<>_OBC = n w n^H - (y - y^H)
+  // (the fixed point of the forward recursion of Eq. 9-10 run along the lead).  The edge cells'
+  // own blocks of M and B^<> also take the products with the first lead cell, and the edge
+  // blocks of W^R the term X^R_{0,-1} V_{-1,0} with X^R_{0,-1} = -X^R_00 M_{0,-1} x (mirrored on
+  // the right).
+  struct Rep { int d, u; };
+  const Rep rep[2] = {{0, 0}, {N - 1, N - 2}};
+  auto LV = [&](const Rep& r, int i, int j) {
+    return i == j ? Vb(r.d, r.d) : (j == i + 1 ? Vb(r.u, r.u + 1) : Vb(r.u + 1, r.u));
+  };
+  auto LP = [&](const PT& p, const Rep& r, int i, int j) {
+    return i == j ? Pb(p, r.d, r.d) : (j == i + 1 ? Pb(p, r.u, r.u + 1) : Pb(p, r.u + 1, r.u));
+  };
+  auto lead = [&](zd* base, int side) { return base + (long long)side * Ec * B2; };
+  zd** wl = c->wl;
+  zd* const nx = wl[5];  // n x per lead, kept for the W^R edge terms
+  if (wobc) {
+    for (int side = 0; side < 2; ++side) {
+      const Rep& r = rep[side];
+      const int away = side == 0 ? 0 : 2;
+      zd* m = lead(c->lead_m, side);
+      for (int a = 0; a < 3; ++a) BT_TRY(prod(c, Ec, -1.0, LV(r, 1, a), LP(pr, r, a, 1), a ? 1.0 : 0.0, m, B2));
+      BT_TRY(bt::shift_diag(st, bs, Ec, m, B2, 1.0));
+      bool first = true;
+      for (int a = 0; a < 3; ++a)
+        if (std::abs(a - away) <= 1) {
+          BT_TRY(prod(c, Ec, -1.0, LV(r, 1, a), LP(pr, r, a, away), first ? 0.0 : 1.0, lead(c->lead_n, side), B2));
+          first = false;
+        }
+      first = true;
+      for (int a = 0; a < 3; ++a)
+        if (std::abs(away - a) <= 1) {
+          BT_TRY(prod(c, Ec, -1.0, LV(r, away, a), LP(pr, r, a, 1), first ? 0.0 : 1.0, lead(c->lead_np, side), B2));
+          first = false;
+        }
+    }
+    BT_TRY(decimate_leads(c, Ec, nullptr));
+    BT_TRY(bt::merge_status(st, Ec, c->lead_info, 2, Ec, status));
+    for (int side = 0; side < 2; ++side) {
+      BT_TRY(prod(c, Ec, 1.0, W(lead(c->lead_n, side), B2), W(lead(c->lead_x, side), B2), 0.0, lead(nx, side), B2));
+      BT_TRY(prod(c, Ec, 1.0, W(lead(c->lead_x, side), B2), W(lead(c->lead_n, side), B2), 0.0, lead(wl[6], side), B2));
+    }
+    const double U = 8.0 * bs * (double)bs * bs;
+    for (int w = 0; w < 2; ++w) {
+      if (!need[w]) continue;
+      const PT& p = plg[w];
+      zd* obc = w == 0 ? c->obcL : c->obcG;
+      for (int side = 0; side < 2; ++side) {
+        const Rep& r = rep[side];
+        zd *T0 = lead(wl[0], side), *T1 = lead(wl[1], side), *T2 = lead(wl[2], side);
+        zd *b = lead(wl[3], side), *cc = lead(wl[4], side);
+        // T_{k,k-1}, T_kk, T_{k,k+1} of T = V P^<> in the lead
+        BT_TRY(prod(c, Ec, 1.0, LV(r, 1, 0), LP(p, r, 0, 0), 0.0, T0, B2));
+        BT_TRY(prod(c, Ec, 1.0, LV(r, 1, 1), LP(p, r, 1, 0), 1.0, T0, B2));
+        for (int a = 0; a < 3; ++a) BT_TRY(prod(c, Ec, 1.0, LV(r, 1, a), LP(p, r, a, 1), a ? 1.0 : 0.0, T1, B2));
+        BT_TRY(prod(c, Ec, 1.0, LV(r, 1, 1), LP(p, r, 1, 2), 0.0, T2, B2));
+        BT_TRY(prod(c, Ec, 1.0, LV(r, 1, 2), LP(p, r, 2, 2), 1.0, T2, B2));
+        // b = B_kk = sum_c T_{k,c} (V_{k,c})^H; c = B_{away,k} (periodic lead: T_{k-1,.} = T_{k,.+1})
+        BT_TRY(prod(c, Ec, 1.0, W(T0, B2), flip(LV(r, 1, 0)), 0.0, b, B2));
+        BT_TRY(prod(c, Ec, 1.0, W(T1, B2), flip(LV(r, 1, 1)), 1.0, b, B2));
+        BT_TRY(prod(c, Ec, 1.0, W(T2, B2), flip(LV(r, 1, 2)), 1.0, b, B2));
+        if (c->d.symmetrize) BT_TRY(bt::antiherm_project(st, bs, Ec, b, B2));
+        if (side == 0) {
+          BT_TRY(prod(c, Ec, 1.0, W(T1, B2), flip(LV(r, 1, 0)), 0.0, cc, B2));
+          BT_TRY(prod(c, Ec, 1.0, W(T2, B2), flip(LV(r, 1, 1)), 1.0, cc, B2));
+        } else {
+          BT_TRY(prod(c, Ec, 1.0, W(T0, B2), flip(LV(r, 1, 1)), 0.0, cc, B2));
+          BT_TRY(prod(c, Ec, 1.0, W(T1, B2), flip(LV(r, 1, 2)), 1.0, cc, B2));
+        }
+        // y = n x c;  b - (y - y^H);  q = x (b - y + y^H) x^H
+        zd *y = lead(wl[7], side), *tq = lead(wl[8], side), *q = lead(wl[9], side);
+        BT_TRY(prod(c, Ec, 1.0, W(lead(nx, side), B2), W(cc, B2), 0.0, y, B2));
+        BT_TRY(bt::add_antiherm(st, bs, Ec, b, B2, y, B2, -1.0));
+        BT_TRY(prod(c, Ec, 1.0, W(lead(c->lead_x, side), B2), W(b, B2), 0.0, tq, B2));
+        BT_TRY(prod(c, Ec, 1.0, W(tq, B2), flip(W(lead(c->lead_x, side), B2)), 0.0, q, B2, true));
+      }
+      // w = q + a w a^H for all 2 Ec leads (a is consumed: copied first)
+      BT_CUDA_TRY(cudaMemcpyAsync(wl[10], wl[6], sizeof(zd) * 2 * Ec * B2, cudaMemcpyDeviceToDevice, st));
+      long long its = 0, body = 0;
+      BT_TRY(bt::stein(st, bs, 2 * Ec, wl[10], nullptr, wl[9], 1e-14, 64, nullptr, c->w_ok, nullptr, c->dec_ws,
+                       c->dec_bytes, c->h_pinned, &its, &c->eng_kept, c->loop, &body));
+      c->cap_polish_body += body;
+      c->flops += 3.0 * U * (double)its;
+      BT_TRY(bt::status_from_ok(st, 2 * Ec, c->w_ok, nullptr, BT_ERR_NOT_CONVERGED, c->w_info));
+      BT_TRY(bt::merge_status(st, Ec, c->w_info, 2, Ec, status));
+      // B^<>_OBC = n w n^H - (y - y^H)
+      for (int side = 0; side < 2; ++side) {
+        zd* o = lead(obc, side);
+        BT_TRY(prod(c, Ec, 1.0, W(lead(c->lead_n, side), B2), W(lead(wl[9], side), B2), 0.0, lead(wl[8], side), B2));
+        BT_TRY(prod(c, Ec, 1.0, W(lead(wl[8], side), B2), flip(W(lead(c->lead_n, side), B2)), 0.0, o, B2, true));
+        BT_TRY(bt::add_antiherm(st, bs, Ec, o, B2, lead(wl[7], side), B2, -1.0));
+      }
+    }
+    // edge cells of M~: the products with the first lead cell, then - B^R_OBC
+    BT_TRY(prod(c, Ec, -1.0, Vb(1, 0), Pb(pr, 0, 1), 1.0, c->Md, NB2));
+    BT_TRY(prod(c, Ec, -1.0, Vb(N - 2, N - 1), Pb(pr, N - 1, N - 2), 1.0, c->Md + (N - 1) * B2, NB2));
+    BT_TRY(bt::axpby(st, B2, Ec, -1.0, lead(c->lead_sig, 0), B2, 1.0, c->Md, NB2));
+    BT_TRY(bt::axpby(st, B2, Ec, -1.0, lead(c->lead_sig, 1), B2, 1.0, c->Md + (N - 1) * B2, NB2));
+  }
+
+  // ---- a1 (W): B^<> = (V P^<>) V^H, diagonal and upper blocks ----
   for (int w = 0; w < 2; ++w) {
     if (!need[w]) continue;
     const PT& p = plg[w];
@@ -949,11 +1080,30 @@ bt_status solve_chunk_w(bt_ctx* c, const bt_bt* V, const bt_bt* PR, const bt_bt*
         BT_TRY(prod(c, Ec, 1.0, Vb(i + 1, i + 1), Pb(p, i + 1, i), 1.0, tl, N1B2));
       }
     }
+    if (wobc) {
+      // T_00 += V_{0,-1} P_{-1,0}, T_{N-1,N-1} += V_{N-1,N} P_{N,N-1};
+      // T_{0,-1} = V_{0,-1} P_{-1,-1} + V_00 P_{0,-1},  T_{N-1,N} = V_{N-1,N} P_{N,N} + V_{N-1,N-1} P_{N-1,N}
+      BT_TRY(prod(c, Ec, 1.0, Vb(1, 0), Pb(p, 0, 1), 1.0, c->Td, NB2));
+      BT_TRY(prod(c, Ec, 1.0, Vb(N - 2, N - 1), Pb(p, N - 1, N - 2), 1.0, c->Td + (N - 1) * B2, NB2));
+      BT_TRY(prod(c, Ec, 1.0, Vb(1, 0), Pb(p, 0, 0), 0.0, c->t[0], B2));
+      BT_TRY(prod(c, Ec, 1.0, Vb(0, 0), Pb(p, 1, 0), 1.0, c->t[0], B2));
+      BT_TRY(prod(c, Ec, 1.0, Vb(N - 2, N - 1), Pb(p, N - 1, N - 1), 0.0, c->t[1], B2));
+      BT_TRY(prod(c, Ec, 1.0, Vb(N - 1, N - 1), Pb(p, N - 2, N - 1), 1.0, c->t[1], B2));
+    }
     for (int i = 0; i < N; ++i) {  // B = T V^H
       zd* bd = Bd[w] + i * B2;
       BT_TRY(prod(c, Ec, 1.0, W(c->Td + i * B2, NB2), Vh(i, i), 0.0, bd, NB2));
       if (i > 0) BT_TRY(prod(c, Ec, 1.0, W(c->Tl + (i - 1) * B2, N1B2), Vh(i, i - 1), 1.0, bd, NB2));
       if (i + 1 < N) BT_TRY(prod(c, Ec, 1.0, W(c->Tu + i * B2, N1B2), Vh(i, i + 1), 1.0, bd, NB2));
+      if (wobc && (i == 0 || i == N - 1)) {
+        // T_{0,-1} (V_{0,-1})^H or T_{N-1,N} (V_{N-1,N})^H, and the boundary block B^<>_OBC
+        const zd* obc = w == 0 ? c->obcL : c->obcG;
+        for (int side = 0; side < 2; ++side) {
+          if ((side == 0 && i != 0) || (side == 1 && i != N - 1)) continue;
+          BT_TRY(prod(c, Ec, 1.0, W(c->t[side], B2), side == 0 ? Vh(1, 0) : Vh(N - 2, N - 1), 1.0, bd, NB2));
+          BT_TRY(bt::axpby(st, B2, Ec, 1.0, lead(const_cast<zd*>(obc), side), B2, 1.0, bd, NB2));
+        }
+      }
       // B^<>_ii is anti-Hermitian as a sum of three products: made exactly so (Sec. 5.2) before the
       // sweep's anti-Hermitian products take it as an operand
       if (c->d.symmetrize) BT_TRY(bt::antiherm_project(c->st, bs, Ec, bd, NB2));
@@ -1000,6 +1150,13 @@ bt_status solve_chunk_w(bt_ctx* c, const bt_bt* V, const bt_bt* PR, const bt_bt*
     auto X2u = [&](int i) { return W(c->X2u + i * B2, N2B2); };
     auto X2l = [&](int i) { return W(c->X2l + i * B2, N2B2); };
     const bool rvec = oR->layout == BT_LAYOUT_DIAGVEC;
+    // contacts: Q_L = n_L x_L V_{-1,0}, Q_R = n_R x_R V_{N,N-1}; W^R_{i,0} -= X^R_{i,0} Q_L and
+    // W^R_{i,N-1} -= X^R_{i,N-1} Q_R for the selected blocks i (the lead cell's column of X^R V)
+    zd* Q[2] = {lead(wl[10], 0), lead(wl[10], 1)};
+    if (wobc) {
+      BT_TRY(prod(c, Ec, 1.0, W(lead(nx, 0), B2), Vb(0, 1), 0.0, Q[0], B2));
+      BT_TRY(prod(c, Ec, 1.0, W(lead(nx, 1), B2), Vb(N - 1, N - 2), 0.0, Q[1], B2));
+    }
     for (int i = 0; i < N; ++i) {
       if (oR->diag) {
         // diagonal-vector output: form the block in a temporary, keep its diagonal
@@ -1008,6 +1165,8 @@ bt_status solve_chunk_w(bt_ctx* c, const bt_bt* V, const bt_bt* PR, const bt_bt*
         BT_TRY(prod(c, Ec, 1.0, XRd(i), Vb(i, i), 0.0, o, es));
         if (i > 0) BT_TRY(prod(c, Ec, 1.0, XRl(i - 1), Vb(i - 1, i), 1.0, o, es));
         if (i + 1 < N) BT_TRY(prod(c, Ec, 1.0, XRu(i), Vb(i + 1, i), 1.0, o, es));
+        if (wobc && i == 0) BT_TRY(prod(c, Ec, -1.0, XRd(0), W(Q[0], B2), 1.0, o, es));
+        if (wobc && i == N - 1) BT_TRY(prod(c, Ec, -1.0, XRd(N - 1), W(Q[1], B2), 1.0, o, es));
         if (rvec)
           BT_TRY(bt::write_diagvec(st, bs, 1, Ec, o, 0, B2, static_cast<zd*>(oR->diag) + (e0 * N + i) * bs, 0,
                                    (long long)N * bs, 0));
@@ -1017,19 +1176,20 @@ bt_status solve_chunk_w(bt_ctx* c, const bt_bt* V, const bt_bt* PR, const bt_bt*
         BT_TRY(prod(c, Ec, 1.0, XRd(i), Vb(i, i + 1), 0.0, o, N1B2));
         BT_TRY(prod(c, Ec, 1.0, XRu(i), Vb(i + 1, i + 1), 1.0, o, N1B2));
         if (i + 2 < N) BT_TRY(prod(c, Ec, 1.0, X2u(i), Vb(i + 2, i + 1), 1.0, o, N1B2));
+        if (wobc && i == N - 2) BT_TRY(prod(c, Ec, -1.0, XRu(N - 2), W(Q[1], B2), 1.0, o, N1B2));
       }
       if (i + 1 < N && oR->lower) {
         zd* o = static_cast<zd*>(oR->lower) + (e0 * (N - 1) + i) * B2;
         BT_TRY(prod(c, Ec, 1.0, XRl(i), Vb(i, i), 0.0, o, N1B2));
         BT_TRY(prod(c, Ec, 1.0, XRd(i + 1), Vb(i + 1, i), 1.0, o, N1B2));
         if (i > 0) BT_TRY(prod(c, Ec, 1.0, X2l(i - 1), Vb(i - 1, i), 1.0, o, N1B2));
+        if (wobc && i == 0) BT_TRY(prod(c, Ec, -1.0, XRl(0), W(Q[0], B2), 1.0, o, N1B2));
       }
     }
   }
   // ---- a5 ----
   BT_TRY(write_diag_out(c, Ec, c->xL, oL, e0, d.symmetrize ? 1 : 0));
   BT_TRY(write_diag_out(c, Ec, c->xG, oG, e0, d.symmetrize ? 1 : 0));
-  (void)status;
   return BT_OK;
 }
 
@@ -1236,8 +1396,13 @@ extern "C" bt_status bt_selinv_solve(bt_ctx* c, const bt_bt* H, const bt_bt* S, 
     fold_pending(c);  // the stream is idle here
     bt_status s;
     auto direct = [&]() {
-      return c->d.system == BT_SYS_G ? solve_chunk_g(c, H, S, sigR, sigL, sigG, e0, Ec, outR, outL, outG, status_device + e0)
-                                     : solve_chunk_w(c, H, sigR, sigL, sigG, e0, Ec, outR, outL, outG, status_device + e0);
+      // a bounded wait of a sliced product that expires marks every energy of the chunk
+      if (cudaMemsetAsync(c->tflag, 0, sizeof(int), c->st) != cudaSuccess) return BT_ERR_CUDA;
+      const bt_status r =
+          c->d.system == BT_SYS_G ? solve_chunk_g(c, H, S, sigR, sigL, sigG, e0, Ec, outR, outL, outG, status_device + e0)
+                                  : solve_chunk_w(c, H, sigR, sigL, sigG, e0, Ec, outR, outL, outG, status_device + e0);
+      if (r != BT_OK) return r;
+      return bt::flag_status(c->st, Ec, c->tflag, status_device + e0);
     };
     if (c->d.graph)
       s = run_chunk_graph(c, H, S, sigR, sigL, sigG, e0, Ec, outR, outL, outG, status_device + e0, direct);

@@ -43,6 +43,7 @@
 
 #include <mutex>
 
+#include <atomic>
 #include "bt_common.cuh"
 #include "sm103_ptx.cuh"
 
@@ -106,7 +107,10 @@ struct MmaParams {
   int negate;                 // alpha = -1 (kCoefUnit / kCoefUnitAcc)
   unsigned long long bias;    // sum over groups of kMagicBits * weight (mod 2^64)
   int fix_bits;               // F: fixed-point units of 2^-F of a leading digit product
-  int* err;          // per batch entry error slot (may be null)
+  int* err;          // error slots (may be null): batch entry b writes err[b * err_stride]
+  long long err_stride;
+  unsigned long long stall_ns;  // test hook: the MMA warp first waits this long on a barrier
+                                // that nothing completes (0: off)
   const int* active; // batch entries with active[b] == 0 are skipped (may be null)
   int a_shared;      // op(A) / op(B) shared by every batch entry: sliced once (batch index 0)
   int b_shared;
@@ -209,7 +213,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   // every role walks the same tiles in the same order and skips the same inactive entries
   auto fail = [&](int b) {
     *abort_flag = 1;
-    if (p.err) atomicCAS(&p.err[b], 0, (int)BT_ERR_TIMEOUT);
+    if (p.err) atomicCAS(&p.err[(long long)b * p.err_stride], 0, (int)BT_ERR_TIMEOUT);
   };
 
   if (warp == 0) {
@@ -262,6 +266,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t phase = 0;
       uint32_t gc = 0;  // jobs started so far (all tiles)
       bool ok = true;
+      if (p.stall_ns) {
+        // test hook: wait on `drain`, which nothing completes before the commit below, so the
+        // bounded wait expires and the CTA takes its timeout path (abort, drain, free TMEM)
+        for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) {
+          int m0, n0, b;
+          if (!tile_coords(p, NT, tile, m0, n0, b)) continue;
+          if (!ptx::mbar_wait_bounded(drain, 0, abort_flag, p.stall_ns)) {
+            fail(b);
+            ok = false;
+          }
+          break;
+        }
+      }
       for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
         int m0, n0, b;
         if (!tile_coords(p, NT, tile, m0, n0, b)) continue;
@@ -838,8 +855,12 @@ size_t split_workspace_bytes(int m, int n, int k, int slices, int batch) {
   return carve_ws(nullptr, m, n, kc, S, batch, &w);
 }
 
+// test hook (bt_debug_split_stall_ns): the MMA warp's stall before its first MMA, 0 = off
+std::atomic<unsigned long long> g_stall_ns{0};
+
 bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A, Operand B, zd beta, zd* C, int ldc,
-                      long long strideC, int batch, int slices, void* ws, size_t ws_bytes, const int* active) {
+                      long long strideC, int batch, int slices, void* ws, size_t ws_bytes, const int* active,
+                      int* err, long long err_stride) {
   const int S = slices > 0 ? slices : 6;
   if (S < 2 || S > kMaxSlices) return BT_ERR_INVALID_ARG;
   if (m < 0 || n < 0 || k < 0 || batch < 0) return BT_ERR_INVALID_ARG;
@@ -900,7 +921,9 @@ bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A,
     else if (unit && p.beta.x == 1.0) p.coef_mode = kCoefUnitAcc;
     else p.coef_mode = kCoefReal;
     p.negate = (unit && alpha.x == -1.0) ? 1 : 0;
-    p.err = nullptr;
+    p.err = err;
+    p.err_stride = err_stride;
+    p.stall_ns = g_stall_ns.load(std::memory_order_relaxed);
     p.active = active;
     p.a_shared = a_shared ? 1 : 0;
     p.b_shared = b_shared ? 1 : 0;
@@ -911,6 +934,8 @@ bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A,
 }
 
 }  // namespace bt
+
+extern "C" void bt_debug_split_stall_ns(unsigned long long ns) { bt::g_stall_ns.store(ns); }
 
 extern "C" bt_status bt_split_zgemm_workspace_bytes(int m, int n, int k, int slices, int batch, size_t* bytes) {
   if (!bytes || m < 0 || n < 0 || k < 0 || batch < 0) return BT_ERR_INVALID_ARG;
@@ -935,5 +960,5 @@ extern "C" bt_status bt_split_zgemm_batched(int m, int n, int k, double alpha_re
   bt::Operand b{static_cast<const zd*>(B), ldb, strideB, opB};
   return bt::split_zgemm(static_cast<cudaStream_t>(stream), m, n, k, zmake(alpha_re, alpha_im), a, b,
                          zmake(beta_re, beta_im), static_cast<zd*>(C), ldc, strideC, batch, slices, workspace,
-                         workspace_bytes, nullptr);
+                         workspace_bytes, nullptr, nullptr, 0);
 }

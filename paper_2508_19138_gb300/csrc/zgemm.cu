@@ -302,7 +302,7 @@ bt_status gemm_antiherm(const Engine& eng, cudaStream_t st, int n, int k, zd alp
                        zd* C, int ldc, long long strideC, int batch, const int* active) {
   if (eng.slices > 0)
     return split_zgemm(st, n, n, k, alpha, A, B, beta, C, ldc, strideC, batch, eng.slices, eng.ws, eng.ws_bytes,
-                       active);
+                       active, eng.err, 0);
   return zgemm_antiherm(st, n, k, alpha, A, B, beta, C, ldc, strideC, batch, active);
 }
 
@@ -310,7 +310,7 @@ bt_status gemm(const Engine& eng, cudaStream_t st, int m, int n, int k, zd alpha
                zd* C, int ldc, long long strideC, int batch, const int* active) {
   if (eng.slices > 0)
     return split_zgemm(st, m, n, k, alpha, A, B, beta, C, ldc, strideC, batch, eng.slices, eng.ws, eng.ws_bytes,
-                       active);
+                       active, eng.err, 0);
   return zgemm(st, m, n, k, alpha, A, B, beta, C, ldc, strideC, batch, active);
 }
 

@@ -36,12 +36,13 @@ def pytest_terminal_summary(terminalreporter, exitstatus, config):
         return
     tr = terminalreporter
     tr.section("parity summary (CUDA path vs oracle, per block)")
-    keys = sorted({r["key"] for r in log})
-    for k in keys:
-        rows = [r for r in log if r["key"] == k]
-        worst = max(r["judged"] for r in rows)
-        tr.write_line(f"{k:8s} blocks {len(rows):6d}  worst judged {worst:.2e}  "
-                      f"worst own-norm {max(r['own_rel'] for r in rows):.2e}")
+    for tol in sorted({r["tol"] for r in log}):
+        tr.write_line(f"tolerance {tol:.0e}:")
+        for k in sorted({r["key"] for r in log if r["tol"] == tol}):
+            rows = [r for r in log if r["key"] == k and r["tol"] == tol]
+            worst = max(r["judged"] for r in rows)
+            tr.write_line(f"  {k:8s} blocks {len(rows):6d}  worst judged {worst:.2e}  "
+                          f"worst own-norm {max(r['own_rel'] for r in rows):.2e}")
     fl = [r for r in log if r["floor_used"]]
     tr.write_line(f"blocks above the tolerance relative to their own norm, passed by the absolute "
                   f"lesser/greater allowance: {len(fl)} of {len(log)}")

@@ -59,7 +59,7 @@ def test_workspace_sizes_host_logic(lib):
 
 @pytest.mark.parametrize("kw,needle", [
     (dict(nb=0), "nb"), (dict(bs=0), "bs"), (dict(max_energies=0), "max_energies"),
-    (dict(nb=1, obc=True), "nb >= 2"), (dict(system=1, obc=True), "G system"),
+    (dict(nb=1, obc=True), "nb >= 2"), (dict(system=1, obc=True, obc_memo=True), "G system"),
     (dict(precision=1, split_slices=12), "split_slices"), (dict(kT=0.0), "kT"),
 ])
 def test_create_rejects_bad_descriptors_on_host(lib, kw, needle):
@@ -67,7 +67,7 @@ def test_create_rejects_bad_descriptors_on_host(lib, kw, needle):
     base = dict(nb=4, bs=8, max_energies=4, system=0, precision=0, split_slices=0, obc=True, kT=0.025)
     base.update(kw)
     d = pkg.make_desc(base["nb"], base["bs"], base["max_energies"], base["system"], base["precision"],
-                      base["split_slices"], True, base["obc"], 1e-6, base["kT"])
+                      base["split_slices"], True, base["obc"], 1e-6, base["kT"], obc_memo=base.get("obc_memo", False))
     with pytest.raises(pkg.BTError) as ei:
         pkg.bt_selinv_create(d, stream=0)
     assert ei.value.status == pkg.BT_ERR_INVALID_ARG

@@ -103,8 +103,11 @@ def test_graph_split_precision():
         assert_identical(d, g)
 
 
-def test_graph_w_system():
-    """W system (no contacts, no decimation loop): graph replay equals direct launches."""
+@pytest.mark.parametrize("obc", [False, True])
+def test_graph_w_system(obc):
+    """W system: graph replay equals direct launches, without contacts and with them (the
+    decimation loop and the Stein doubling loops of the lesser / greater boundary captured as
+    conditional while nodes)."""
     import torch
     import paper_2508_19138_gb300 as pkg
     from paper_2508_19138_gb300 import BT, BTOut
@@ -120,7 +123,7 @@ def test_graph_w_system():
     got = {}
     for graph in (False, True):
         stream = torch.cuda.Stream()
-        desc = pkg.make_desc(nb, bs, E, system=pkg.BT_SYS_W, obc=False, eta=0.0, graph=graph)
+        desc = pkg.make_desc(nb, bs, E, system=pkg.BT_SYS_W, obc=obc, eta=0.0, graph=graph)
         ctx = pkg.bt_selinv_create(desc, stream)
         mk = lambda *sh: torch.empty(sh, dtype=torch.complex128, device="cuda")
         oR = BTOut(mk(E, nb, bs, bs), mk(E, nb - 1, bs, bs), mk(E, nb - 1, bs, bs))

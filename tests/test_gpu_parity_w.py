@@ -1,17 +1,19 @@
 """Parity of the W (screened interaction) path with the dense oracle: M~ = I - V P^R and
 B^<> = V P^<> V^H assembled as block-tridiagonal products on the GPU, RGF sweep, W^R = X^R V
-on the selected blocks (needs X^R_{i,i+-2}), W^<> = X^<>."""
+on the selected blocks (needs X^R_{i,i+-2}), W^<> = X^<>; and with contacts (Sec. 4.2: leads
+repeating the edge cells, retarded boundary by decimation, lesser / greater boundary by the Stein
+equation of Eq. 7) against the oracle's folded-lead route."""
 import numpy as np
 import pytest
 
 import oracle
 import synthetic
-from gpu_util import TOL_FP64, TOL_SPLIT, block_errors
+from gpu_util import TOL_FP64, TOL_SPLIT, block_errors, compare_blocks
 
 pytestmark = pytest.mark.gpu
 
 
-def run_w(ws, idx, precision=0, max_energies=None, symmetrize=True):
+def run_w(ws, idx, precision=0, max_energies=None, symmetrize=True, obc=False, split_scope=0):
     import torch
     import paper_2508_19138_gb300 as pkg
     from paper_2508_19138_gb300 import BT, BTOut
@@ -27,7 +29,7 @@ def run_w(ws, idx, precision=0, max_energies=None, symmetrize=True):
     PGd = t(np.stack([p[5] for p in parts]))
     PGu = t(np.stack([p[6] for p in parts]))
     desc = pkg.make_desc(nb, bs, max_energies or E, system=pkg.BT_SYS_W, precision=precision,
-                         symmetrize=symmetrize, obc=False, eta=0.0)
+                         symmetrize=symmetrize, obc=obc, eta=0.0, split_scope=split_scope)
     ctx = pkg.bt_selinv_create(desc)
     V = BT(t(ws.V_diag), t(ws.V_upper), None, pkg.BT_LAYOUT_BLOCKS, pkg.BT_SYM_HERMITIAN, False)
     PR = BT(PRd, PRu, PRl, pkg.BT_LAYOUT_BLOCKS, pkg.BT_SYM_GENERAL, True)
@@ -70,3 +72,31 @@ def test_w_identity_on_gpu_output():
             R = res["R_diag"][j, i]
             lhs = res["G_diag"][j, i] - res["L_diag"][j, i]
             assert np.abs(lhs - (R - R.conj().T)).max() <= 1e-11 * np.abs(R).max()
+
+
+@pytest.mark.parametrize("geom", [dict(nb=3, ny=2, nz=2, nx=8, r_cut=5.0),
+                                  dict(nb=5, ny=3, nz=2, nx=6, r_cut=4.0)])
+@pytest.mark.parametrize("precision,scope,tol", [(0, 0, TOL_FP64), (1, 0, TOL_SPLIT), (1, 1, TOL_SPLIT)])
+def test_w_contacts_match_oracle(geom, precision, scope, tol):
+    """W system with both leads attached (obc = 1), chunks of 3 over 5 energies: every selected
+    block against oracle.solve_w_contacts (edge cells with the first lead cell's products, the
+    folded lead blocks B^R_OBC and B^<>_OBC, W^R's lead-column terms)."""
+    ws = synthetic.w_system(spacing=2.2, n_energies=5, **geom)
+    idx = np.arange(5)
+    res, status = run_w(ws, idx, precision=precision, max_energies=3, obc=True, split_scope=scope)
+    assert (status == 0).all()
+    for j, e in enumerate(idx):
+        ref = oracle.solve_w_contacts(ws, e)
+        for k in ("R_diag", "R_upper", "R_lower", "L_diag", "L_upper", "G_diag", "G_upper"):
+            worst = compare_blocks(res[k][j], ref[k], k, e, tol)
+            assert worst <= tol, (k, e, worst)
+
+
+def test_w_contacts_change_the_edge_blocks():
+    """The contacts matter: the device without leads differs from the one with leads in the edge
+    blocks by far more than the tolerance (so the test above cannot pass on the closed device)."""
+    ws = synthetic.w_system(spacing=2.2, n_energies=2, nb=3, ny=2, nz=2, nx=8, r_cut=5.0)
+    res, _ = run_w(ws, np.arange(2), obc=True)
+    closed = oracle.solve_w(ws, 1)
+    assert block_errors(res["L_diag"][1][:1], closed["L_diag"][:1]).max() > 1e-3
+    assert block_errors(res["R_diag"][1][:1], closed["R_diag"][:1]).max() > 1e-3
