@@ -16,9 +16,11 @@ What it computes (the plain definitions the recursive Green's function method re
   * Table 2, right column: the W system M = I, B^R = V P^R, B^<> = V P^<> V^H, W^R = X^R V;
     with contacts (Sec. 4.2, Eq. 4 and 7), the leads folded into the edge cells by the retarded
     recursion and a Stein (discrete Lyapunov) equation for the lesser / greater boundary.
+  * Sec. 4.4, Eq. 3: the element-wise energy convolution, as its explicit sum (energy_conv.py).
 
 Pins (tests/test_oracle_pins.py) tie every function to something other than itself: closed
 forms of the 1D chain, integer transmission, the eigen-route surface function, algebraic
 identities, brute force on tiny cases.
 """
 from .negf import *  # noqa: F401,F403
+from .energy_conv import *  # noqa: F401,F403
