@@ -56,7 +56,8 @@ typedef enum {
                             /* P^R or V); non-finite lesser/greater inputs are not scanned:  */
                             /* they reach the lesser/greater outputs with status BT_OK       */
   BT_ERR_TIMEOUT = 8,       /* a bounded device wait expired                                 */
-  BT_ERR_UNSUPPORTED = 9    /* valid request this build does not implement                   */
+  BT_ERR_UNSUPPORTED = 9,   /* valid request this build does not implement                   */
+  BT_ERR_CANCELLED = 10     /* serving: the request was cancelled (server destroyed)         */
 } bt_status;
 
 typedef enum { BT_SYS_G = 0, BT_SYS_W = 1 } bt_system;           /* Table 2 columns      */
@@ -217,14 +218,20 @@ BT_API const char* bt_selinv_last_error(const bt_ctx* ctx);
 
 /* ---------------------------------------------------------------------------------------
  * Serving: solves of different device sizes arriving over time (G system).  The paper has no
- * counterpart (its energies are distributed over ranks, Sec. 4.4); each request is the solve
- * of bt_selinv_solve (Sec. 3, Eq. 1; Sec. 4.3.2).
- *   - bt_server_create allocates ONE device arena of hbm_budget_bytes; each admitted request
- *     borrows its workspace (as bt_selinv_workspace_bytes for a chunk of
- *     max_energies_per_chunk energies) from it; requests are admitted in arrival order as soon
- *     as their workspace fits, so memory freed by a finished request admits the next one;
- *   - max_active worker threads, each with its own stream, run admitted requests concurrently
- *     (continuous batching: new requests start while earlier ones are still on the GPU);
+ * counterpart (its energies are distributed over ranks, Sec. 4.4); each unit of work is the
+ * solve of bt_selinv_solve (Sec. 3, Eq. 1; Sec. 4.3.2).
+ *   - a request is split into work units of max_energies_per_chunk energies each;
+ *   - bt_server_create allocates ONE device arena of hbm_budget_bytes; each unit borrows its
+ *     workspace (bt_selinv_workspace_bytes for one chunk) from it while it runs;
+ *   - a free worker starts the next unit chosen round robin over the requests with units left
+ *     (every admitted request progresses chunk by chunk); a unit that does not fit in the free
+ *     memory now is passed by smaller ones, at most max_skips times (<= 0: 2 max_active) for the
+ *     oldest waiting request;
+ *   - max_active worker threads, each with its own stream, run units concurrently (continuous
+ *     batching: new requests start while earlier ones are still on the GPU);
+ *   - a unit whose solve reports BT_ERR_TIMEOUT (a bounded device wait expired) is started
+ *     again, up to max_retries times; requests not started when the server is destroyed end
+ *     with BT_ERR_CANCELLED;
  *   - a request's inputs / outputs are the caller's device buffers and must stay valid until
  *     the request is done; results equal those of bt_selinv_solve with the same chunking.
  * ------------------------------------------------------------------------------------- */
@@ -237,6 +244,9 @@ typedef struct {
   int precision;              /* bt_precision                                              */
   int split_slices;           /* BT_SPLIT slices (0 = default)                             */
   int device;                 /* CUDA device ordinal                                       */
+  int split_scope;            /* BT_SPLIT: as bt_selinv_desc.split_scope (0 or 1)          */
+  int max_retries;            /* restarts of a unit that timed out (>= 0)                  */
+  int max_skips;              /* passes of the oldest waiting request (<= 0: 2 max_active) */
 } bt_server_desc;
 
 typedef struct {
@@ -257,17 +267,21 @@ typedef struct {
   double busy_seconds;        /* first admission to last completion                        */
   double energies_per_s;      /* energies_done / busy_seconds                              */
   size_t peak_bytes;          /* largest arena occupancy                                   */
+  long long units_done;       /* work units (energy chunks) completed                      */
+  long long retries;          /* units started again after a device timeout                */
 } bt_server_stats;
 
 BT_API bt_status bt_server_create(const bt_server_desc* desc, bt_server** out);
 /* Queue a request; returns a ticket.  BT_ERR_BUDGET if its workspace can never fit. */
 BT_API bt_status bt_server_submit(bt_server* srv, const bt_request* req, long long* ticket);
-/* state: 0 queued, 1 running, 2 done, 3 failed (the return code is then the failure). */
+/* state: 0 queued, 1 running, 2 done, 3 failed or cancelled (the return code is then the
+ * failure, BT_ERR_CANCELLED for a cancelled request). */
 BT_API bt_status bt_server_poll(bt_server* srv, long long ticket, int* state);
 /* Block until the request is done or failed, or timeout_s passed (BT_ERR_TIMEOUT). */
 BT_API bt_status bt_server_wait(bt_server* srv, long long ticket, double timeout_s, int* state);
 BT_API bt_status bt_server_get_stats(bt_server* srv, bt_server_stats* out);
-/* Cancels queued requests, waits for running ones, frees the arena. */
+/* Cancels requests with units not yet started (BT_ERR_CANCELLED), waits for running units,
+ * frees the arena. */
 BT_API bt_status bt_server_destroy(bt_server* srv);
 
 /* ---------------------------------------------------------------------------------------
@@ -345,15 +359,36 @@ BT_API bt_status bt_decimate_batched(int bs, int batch, const void* m, const voi
                               int* info_device, void* workspace, size_t workspace_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Element-wise energy convolution (Sec. 4.4, Eq. 3): the scattering self-energy / polarization of
+ * an (i, j) entry is an energy integral of products of two particle descriptors, each entry
+ * independent of the others.  On a uniform grid it is, for every element series e < n_elem,
+ *     C[m - m0][e] = s * sum_k A[m - k][e] * B'[k][e],      m0 <= m < m0 + n_out,
+ * with A[i][e] = 0 outside 0 <= i < na and B'[k][e] = B[k][e] (or B[nb - 1 - k][e] with
+ * BT_CONV_REVERSE_B, a cross-correlation; conjugated with BT_CONV_CONJ_B) zero outside
+ * 0 <= k < nb; the full result has na + nb - 1 entries (m0 + n_out must not exceed that).  The
+ * factor s = scale_re + i scale_im carries the proportionality constant and the energy step.
+ * Layout: energy-major complex128, element e of energy k at A + k lda + e (lda >= n_elem; the
+ * outputs of bt_selinv_solve are element series with lda = nb bs^2, or nb bs (bs + 1) / 2 for
+ * packed upper triangles).  Device pointers; C must not alias A or B.  Computed by FFTs of
+ * length L = the power of two >= na + nb - 1 in FP64 (L <= 4096, else BT_ERR_UNSUPPORTED);
+ * asynchronous on `stream`; allocates nothing.
+ * ------------------------------------------------------------------------------------- */
+enum { BT_CONV_REVERSE_B = 1, BT_CONV_CONJ_B = 2 };
+BT_API bt_status bt_energy_convolve(int n_elem, int na, int nb, int m0, int n_out, const void* A, long long lda,
+                                    const void* B, long long ldb, void* C, long long ldc, double scale_re,
+                                    double scale_im, int flags, void* stream);
+
+/* ---------------------------------------------------------------------------------------
  * Test hook (no counterpart in the paper).  Every wait of the tensor-core GEMM's pipeline on a
  * shared-memory barrier is bounded (2 s); when one expires, the CTA records BT_ERR_TIMEOUT, stops
  * issuing work, waits (bounded) for the copies and products it already issued, frees its tensor
  * memory and exits, and every energy of the chunk gets BT_ERR_TIMEOUT in the solve's status.
- * With ns > 0, the MMA warp of every later launch first waits up to ns nanoseconds on a barrier
- * that nothing completes, so that this path runs on demand; 0 turns the hook off.  Process-wide,
- * read when a launch is issued (a captured graph keeps the value it was captured with).
+ * With ns > 0, the MMA warp of the next `launches` launches of that GEMM (every later launch when
+ * launches < 0) first waits up to ns nanoseconds on a barrier that nothing completes, so that
+ * this path runs on demand; ns = 0 turns the hook off.  Process-wide, read when a launch is
+ * issued (a captured graph keeps the value it was captured with).
  * ------------------------------------------------------------------------------------- */
-BT_API void bt_debug_split_stall_ns(unsigned long long ns);
+BT_API void bt_debug_split_stall(unsigned long long ns, long long launches);
 
 #ifdef __cplusplus
 }

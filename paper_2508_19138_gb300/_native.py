@@ -10,10 +10,12 @@ from . import build as _build
 
 BT_OK, BT_ERR_INVALID_ARG, BT_ERR_OOM, BT_ERR_BUDGET, BT_ERR_CUDA = 0, 1, 2, 3, 4
 BT_ERR_SINGULAR, BT_ERR_NOT_CONVERGED, BT_ERR_NONFINITE, BT_ERR_TIMEOUT, BT_ERR_UNSUPPORTED = 5, 6, 7, 8, 9
+BT_ERR_CANCELLED = 10
 STATUS_NAMES = {0: "BT_OK", 1: "BT_ERR_INVALID_ARG", 2: "BT_ERR_OOM", 3: "BT_ERR_BUDGET", 4: "BT_ERR_CUDA",
                 5: "BT_ERR_SINGULAR", 6: "BT_ERR_NOT_CONVERGED", 7: "BT_ERR_NONFINITE", 8: "BT_ERR_TIMEOUT",
-                9: "BT_ERR_UNSUPPORTED"}
+                9: "BT_ERR_UNSUPPORTED", 10: "BT_ERR_CANCELLED"}
 BT_SYS_G, BT_SYS_W = 0, 1
+BT_CONV_REVERSE_B, BT_CONV_CONJ_B = 1, 2
 BT_FP64, BT_SPLIT = 0, 1
 BT_LAYOUT_BLOCKS, BT_LAYOUT_DIAGVEC, BT_LAYOUT_PACKED_UPPER = 0, 1, 2
 BT_SYM_GENERAL, BT_SYM_HERMITIAN, BT_SYM_ANTIHERMITIAN = 0, 1, 2
@@ -70,11 +72,12 @@ SIGNATURES = {
     "bt_zinv_workspace_bytes": [_I, _I, C.POINTER(C.c_size_t)],
     "bt_zinv_batched": [_I, _P, _LL, _I, _P, _P, _SZ, _P],
     "bt_zinv_batched_noalloc": [_I, _P, _LL, _I, _P, _P],
-    "bt_debug_split_stall_ns": [C.c_ulonglong],
+    "bt_debug_split_stall": [C.c_ulonglong, C.c_longlong],
+    "bt_energy_convolve": [_I, _I, _I, _I, _I, _P, _LL, _P, _LL, _P, _LL, _D, _D, _I, _P],
     "bt_decimate_workspace_bytes": [_I, _I, C.POINTER(C.c_size_t)],
     "bt_decimate_batched": [_I, _I, _P, _P, _P, _D, _I, _P, _P, _P, _P, _P, _SZ, _P],
 }
-RESTYPES = {"bt_selinv_last_error": C.c_char_p, "bt_debug_split_stall_ns": None}
+RESTYPES = {"bt_selinv_last_error": C.c_char_p, "bt_debug_split_stall": None}
 
 _lib = None
 
@@ -107,7 +110,8 @@ def load(build_if_missing: bool = False) -> C.CDLL:
 # ---- serving ----
 class bt_server_desc(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_active", C.c_int), ("max_energies_per_chunk", C.c_int),
-                ("precision", C.c_int), ("split_slices", C.c_int), ("device", C.c_int)]
+                ("precision", C.c_int), ("split_slices", C.c_int), ("device", C.c_int), ("split_scope", C.c_int),
+                ("max_retries", C.c_int), ("max_skips", C.c_int)]
 
 
 class bt_request(C.Structure):
@@ -123,7 +127,8 @@ class bt_server_stats(C.Structure):
                 ("rejected", C.c_longlong), ("energies_done", C.c_longlong), ("queued", C.c_longlong),
                 ("active", C.c_int), ("peak_active", C.c_int), ("p50_latency_s", C.c_double),
                 ("p99_latency_s", C.c_double), ("mean_latency_s", C.c_double), ("busy_seconds", C.c_double),
-                ("energies_per_s", C.c_double), ("peak_bytes", C.c_size_t)]
+                ("energies_per_s", C.c_double), ("peak_bytes", C.c_size_t), ("units_done", C.c_longlong),
+                ("retries", C.c_longlong)]
 
 
 SIGNATURES.update({

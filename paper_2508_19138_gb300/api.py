@@ -17,7 +17,7 @@ __all__ = [
     "bt_selinv_solve", "bt_selinv_solve_host", "bt_selinv_destroy", "bt_selinv_last_error", "bt_selinv_get_stats",
     "bt_zgemm_batched", "bt_split_zgemm_workspace_bytes", "bt_split_zgemm_batched", "bt_zinv_workspace_bytes",
     "bt_zinv_batched", "bt_zinv_batched_noalloc", "bt_decimate_workspace_bytes", "bt_decimate_batched", "library",
-    "bt_debug_split_stall_ns",
+    "bt_debug_split_stall", "bt_energy_convolve",
 ]
 
 
@@ -260,10 +260,25 @@ def bt_zinv_batched_noalloc(n, A, strideA, batch, info, stream=None) -> None:
     _check(rc, None, "zinv_noalloc")
 
 
-def bt_debug_split_stall_ns(ns: int) -> None:
-    """Test hook: later tensor-core GEMM launches first stall their MMA warp up to ns nanoseconds on
-    a barrier nothing completes, so that the bounded-wait timeout path runs (0 = off)."""
-    N.load().bt_debug_split_stall_ns(int(ns))
+def bt_energy_convolve(n_elem, na, nb, A, lda, B, ldb, C, ldc, scale=1.0, m0=0, n_out=None, flags=0,
+                       stream=None) -> None:
+    """Element-wise energy convolution (Sec. 4.4, Eq. 3) of energy-major complex128 device arrays:
+    C[m - m0][e] = scale * sum_k A[m - k][e] * B'[k][e] for m0 <= m < m0 + n_out (see the header)."""
+    torch = _torch()
+    if n_out is None:
+        n_out = na + nb - 1 - m0
+    sc = complex(scale)
+    rc = N.load().bt_energy_convolve(n_elem, na, nb, m0, n_out, _ptr(A, torch.complex128), lda,
+                                     _ptr(B, torch.complex128), ldb, _ptr(C, torch.complex128), ldc, sc.real, sc.imag,
+                                     flags, _stream(stream))
+    _check(rc, None, "energy_convolve")
+
+
+def bt_debug_split_stall(ns: int, launches: int = -1) -> None:
+    """Test hook: the next `launches` tensor-core GEMM launches (all when negative) first stall
+    their MMA warp up to ns nanoseconds on a barrier nothing completes, so that the bounded-wait
+    timeout path runs (ns = 0: off)."""
+    N.load().bt_debug_split_stall(int(ns), int(launches))
 
 
 def bt_decimate_workspace_bytes(bs, batch) -> int:

@@ -31,6 +31,13 @@ class Arena {
     }
     return SIZE_MAX;
   }
+  // whether alloc(bytes) would succeed now
+  bool can_alloc(size_t bytes) const {
+    bytes = (bytes + 255) / 256 * 256;
+    for (const auto& kv : free_)
+      if (kv.second >= bytes) return true;
+    return false;
+  }
   void release(size_t off, size_t bytes) {
     bytes = (bytes + 255) / 256 * 256;
     auto it = free_.emplace(off, bytes).first;

@@ -855,8 +855,21 @@ size_t split_workspace_bytes(int m, int n, int k, int slices, int batch) {
   return carve_ws(nullptr, m, n, kc, S, batch, &w);
 }
 
-// test hook (bt_debug_split_stall_ns): the MMA warp's stall before its first MMA, 0 = off
+// test hook (bt_debug_split_stall): the MMA warp's stall before its first MMA (0 = off), for the
+// next g_stall_left launches (negative: every launch)
 std::atomic<unsigned long long> g_stall_ns{0};
+std::atomic<long long> g_stall_left{0};
+
+unsigned long long stall_for_launch() {
+  const unsigned long long ns = g_stall_ns.load();
+  if (ns == 0) return 0;
+  long long left = g_stall_left.load();
+  while (left != 0) {
+    if (left < 0) return ns;
+    if (g_stall_left.compare_exchange_weak(left, left - 1)) return ns;
+  }
+  return 0;
+}
 
 bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A, Operand B, zd beta, zd* C, int ldc,
                       long long strideC, int batch, int slices, void* ws, size_t ws_bytes, const int* active,
@@ -923,7 +936,7 @@ bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A,
     p.negate = (unit && alpha.x == -1.0) ? 1 : 0;
     p.err = err;
     p.err_stride = err_stride;
-    p.stall_ns = g_stall_ns.load(std::memory_order_relaxed);
+    p.stall_ns = stall_for_launch();
     p.active = active;
     p.a_shared = a_shared ? 1 : 0;
     p.b_shared = b_shared ? 1 : 0;
@@ -935,7 +948,10 @@ bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A,
 
 }  // namespace bt
 
-extern "C" void bt_debug_split_stall_ns(unsigned long long ns) { bt::g_stall_ns.store(ns); }
+extern "C" void bt_debug_split_stall(unsigned long long ns, long long launches) {
+  bt::g_stall_left.store(launches);
+  bt::g_stall_ns.store(ns);
+}
 
 extern "C" bt_status bt_split_zgemm_workspace_bytes(int m, int n, int k, int slices, int batch, size_t* bytes) {
   if (!bytes || m < 0 || n < 0 || k < 0 || batch < 0) return BT_ERR_INVALID_ARG;

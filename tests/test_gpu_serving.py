@@ -134,3 +134,63 @@ def test_budget_admission_and_rejection():
     assert ei.value.status == pkg.BT_ERR_BUDGET
     assert pkg.bt_server_get_stats(srv)["rejected"] == 1
     pkg.bt_server_destroy(srv)
+
+
+def test_timed_out_unit_is_started_again():
+    """Host watchdog of the work units: the first tensor-core GEMM launch of the server stalls on a
+    barrier nothing completes (test hook, 20 ms), so its unit's solve reports BT_ERR_TIMEOUT; the
+    server starts that unit again and the request completes, every block against the oracle at the
+    split tolerance.  With no retries allowed the same stall fails the request."""
+    import torch
+    import paper_2508_19138_gb300 as pkg
+    from gpu_util import TOL_SPLIT
+    s = _request_inputs(80, 3, 32, 6)
+    for retries, want_state in ((1, 2), (0, 3)):
+        srv = pkg.bt_server_create(hbm_budget_bytes=1 << 30, max_active=1, max_energies_per_chunk=CHUNK,
+                                   precision=pkg.BT_SPLIT, max_retries=retries)
+        H, outs, status = _tensors(s)
+        try:
+            pkg.bt_debug_split_stall(20_000_000, 1)
+            t = pkg.bt_server_submit(srv, s.nb, s.bs, H, s.energies, status, outs["R"], outs["L"], outs["G"],
+                                     eta=s.eta, kT=s.kT, mu_left=s.mu_left, mu_right=s.mu_right)
+            if want_state == 2:
+                assert pkg.bt_server_wait(srv, t, 300.0) == 2
+            else:
+                with pytest.raises(pkg.BTError) as ei:
+                    pkg.bt_server_wait(srv, t, 300.0)
+                assert ei.value.status == pkg.BT_ERR_TIMEOUT
+        finally:
+            pkg.bt_debug_split_stall(0, 0)
+        st = pkg.bt_server_get_stats(srv)
+        assert st["retries"] == retries
+        pkg.bt_server_destroy(srv)
+        torch.cuda.synchronize()
+        if want_state == 2:
+            assert (status.cpu().numpy() == 0).all()
+            res = {w + "_diag": outs[w].diag.cpu().numpy() for w in "RLG"}
+            res.update({w + "_upper": outs[w].upper.cpu().numpy() for w in "RLG"})
+            res["R_lower"] = outs["R"].lower.cpu().numpy()
+            for e in range(len(s.energies)):
+                _, bad = compare_g(res, s, e, e, tol=TOL_SPLIT)
+                assert not bad, (e, bad)
+
+
+def test_units_of_a_request_run_concurrently_and_match_alone():
+    """One request of 5 chunks on 3 workers: its units run side by side (peak_active 3) and the
+    result equals the request solved alone with the same chunking, bitwise."""
+    import torch
+    import paper_2508_19138_gb300 as pkg
+    s = _request_inputs(90, 4, 48, 5 * CHUNK)
+    srv = pkg.bt_server_create(hbm_budget_bytes=2 << 30, max_active=3, max_energies_per_chunk=CHUNK)
+    H, outs, status = _tensors(s)
+    t = pkg.bt_server_submit(srv, s.nb, s.bs, H, s.energies, status, outs["R"], outs["L"], outs["G"],
+                             eta=s.eta, kT=s.kT, mu_left=s.mu_left, mu_right=s.mu_right)
+    assert pkg.bt_server_wait(srv, t, 300.0) == 2
+    st = pkg.bt_server_get_stats(srv)
+    assert st["units_done"] == 5 and st["peak_active"] >= 2
+    pkg.bt_server_destroy(srv)
+    torch.cuda.synchronize()
+    alone = _alone(s)
+    for w in "RLG":
+        assert np.array_equal(outs[w].diag.cpu().numpy(), alone[w][0])
+        assert np.array_equal(outs[w].upper.cpu().numpy(), alone[w][1])

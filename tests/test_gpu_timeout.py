@@ -1,7 +1,7 @@
 """Bounded device waits driven to expiry (failure detection without a GPU fault).
 
 The tensor-core GEMM's pipeline waits on shared-memory barriers are bounded.  The test hook
-bt_debug_split_stall_ns makes the MMA warp wait on a barrier that nothing completes, with a short
+bt_debug_split_stall makes the MMA warp wait on a barrier that nothing completes, with a short
 limit: every CTA then records BT_ERR_TIMEOUT, stops issuing, waits for the copies and products it
 already issued, frees its tensor memory and exits.  The solve reports BT_ERR_TIMEOUT for every
 energy of the chunk through the C ABI, and the next solve on the same context (hook off) is
@@ -27,11 +27,11 @@ def test_split_timeout_reported_then_context_recovers(scope):
     solver.set_inputs(s.H_diag, s.H_upper)
     outs, status = solver.allocate_outputs(2)
     try:
-        pkg.bt_debug_split_stall_ns(20_000_000)  # 20 ms on a barrier nothing completes
+        pkg.bt_debug_split_stall(20_000_000, -1)  # 20 ms on a barrier nothing completes
         solver.solve(s.energies, outs, status)
         torch.cuda.synchronize()
     finally:
-        pkg.bt_debug_split_stall_ns(0)
+        pkg.bt_debug_split_stall(0, 0)
     assert status.cpu().numpy().tolist() == [pkg.BT_ERR_TIMEOUT] * 2
     solver.solve(s.energies, outs, status)
     torch.cuda.synchronize()
