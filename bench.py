@@ -828,10 +828,68 @@ def run_serving(args):
     return 0
 
 
+def run_conv(args, n_elem=416 * 416, ne=512, steps=5, warmup=3):
+    """Energy convolution (Sec. 4.4, Eq. 3) of the element series of one 416 x 416 diagonal block
+    over the 512-energy grid (the nanoribbon's G^< and G^> stand-ins: seeded complex normal on the
+    device), full linear result of 1023 energies; errors against the oracle's explicit sum on 128
+    sampled series."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2508_19138_gb300 as pkg
+    from paper_2508_19138_gb300.kernel_driver import conv_flops
+    g = torch.Generator(device="cuda").manual_seed(20250826)
+    A = torch.randn(ne, n_elem, dtype=torch.complex128, device="cuda", generator=g)
+    B = torch.randn(ne, n_elem, dtype=torch.complex128, device="cuda", generator=g)
+    C = torch.empty(2 * ne - 1, n_elem, dtype=torch.complex128, device="cuda")
+    stream = torch.cuda.Stream()
+
+    def step():
+        pkg.bt_energy_convolve(n_elem, ne, ne, A, n_elem, B, n_elem, C, n_elem, scale=1.0, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        for i in range(steps):
+            step()
+            ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+    med = statistics.median(ms)
+    L = 1 << (2 * ne - 2).bit_length()
+    flops = conv_flops(L) * n_elem
+    moved = 16.0 * n_elem * (ne + ne + 2 * ne - 1)
+    idx = np.random.default_rng(7).choice(n_elem, size=128, replace=False)
+    a, b, c = (x[:, idx].cpu().numpy() for x in (A, B, C))
+    want = oracle.energy_convolve(a, b)
+    err = float((np.linalg.norm(c - want, axis=0) / np.linalg.norm(want, axis=0)).max())
+    return {"value": n_elem / (med / 1e3), "unit": "element series/s", "ms_per_step": med, "steps": steps,
+            "warmup": warmup,
+            "config": {"workload": f"energy convolution (Eq. 3) of {n_elem} element series (one 416x416 block) x "
+                                   f"{ne} energies, full linear result, FFT length {L}"},
+            "roofline": {"bound": "alu", "achieved": flops / (med / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": flops / (med / 1e3) / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+                         "kernel": "conv_kernel (FP64 radix-2 FFT in shared memory)",
+                         "flop_count": "per series 3 x 5 L log2 L + 6 L",
+                         "hbm_gbs": moved / (med / 1e3) / 1e9},
+            "errors": {"max_series_rel_err": err, "tolerance": 1e-10,
+                       "sample": "128 seeded element series against oracle.energy_convolve"},
+            "clocks": clk}
+
+
 def sublines(args):
     """Lines of the other workloads, measured after the default one (one GPU): the 8 x 32 random
-    device (all 64 energies per step; FP64 and both split scopes) and the W system 16 x 1024
-    (split, steps of 4 energies), each with its own step counts and errors against the oracle."""
+    device (all 64 energies per step; FP64 and both split scopes), the energy convolution of one
+    416 x 416 block over 512 energies, and the W system 16 x 1024 (split, steps of 4 energies),
+    each with its own step counts and errors against the oracle."""
     import copy
     out = {}
     a0 = copy.copy(args)
@@ -841,6 +899,10 @@ def sublines(args):
         out["random8x32"] = run_ours(a0)
     except Exception as exc:  # a sub-line never takes the main line down
         out["random8x32"] = {"unavailable": f"{type(exc).__name__}: {exc}"[:300]}
+    try:
+        out["energy_convolution"] = run_conv(args)
+    except Exception as exc:
+        out["energy_convolution"] = {"unavailable": f"{type(exc).__name__}: {exc}"[:300]}
     a2 = copy.copy(args)
     a2.workload, a2.energies_per_step, a2.steps, a2.warmup, a2.precision = "w16x1024", 4, 2, 1, "split"
     try:

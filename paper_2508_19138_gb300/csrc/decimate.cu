@@ -635,7 +635,10 @@ bt_status decimate(cudaStream_t st, int bs, int batch, const zd* m, const zd* n,
   if (polish && polish->after >= 0) {
     int* hp = h_pinned;
     if (!loop && !hp && cudaMallocHost(&hp, 64) != cudaSuccess) return BT_ERR_CUDA;
-    const bt_status ps = polish_step(st, bs, batch, m, n, np, x, mask, iters, info, w, hp, E, loop, *polish);
+    // the Newton step runs in FP64 whatever engine the decimation used: it is what brings the
+    // surface function to FP64 accuracy, and a sliced residual would limit that
+    const Engine fp64_step;
+    const bt_status ps = polish_step(st, bs, batch, m, n, np, x, mask, iters, info, w, hp, fp64_step, loop, *polish);
     if (hp != h_pinned) cudaFreeHost(hp);
     BT_TRY(ps);
   }

@@ -4,6 +4,8 @@
     python -m paper_2508_19138_gb300.kernel_driver --kernel split --bs 416 --batch 32 --slices 6
     python -m paper_2508_19138_gb300.kernel_driver --kernel zinv --bs 416 --batch 32
     python -m paper_2508_19138_gb300.kernel_driver --kernel cublas --bs 416 --batch 16   # library reference
+    python -m paper_2508_19138_gb300.kernel_driver --kernel conv --bs 416 --batch 512    # energy convolution of
+        # the bs^2 element series of one diagonal block over `batch` energies (na = nb = batch)
 
 Inputs are random complex128 blocks already on the device; each kernel is launched `--reps`
 times on the current stream and its mean time is printed (CUDA events)."""
@@ -18,7 +20,7 @@ def main():
 
     import paper_2508_19138_gb300 as pkg
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kernel", choices=["zgemm", "split", "zinv", "cublas"], required=True)
+    ap.add_argument("--kernel", choices=["zgemm", "split", "zinv", "cublas", "conv"], required=True)
     ap.add_argument("--bs", type=int, default=416)
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--reps", type=int, default=3)
@@ -28,6 +30,8 @@ def main():
     if a.kernel == "cublas":
         return cublas_reference(a)
     pkg.library()
+    if a.kernel == "conv":
+        return conv_driver(a, pkg)
     b, n = a.batch, a.bs
     kk = a.k if a.k > 0 and a.kernel != "zinv" else n
     g = torch.Generator(device="cuda").manual_seed(1)
@@ -65,6 +69,41 @@ def main():
     flops = 8.0 * n * n * kk * b
     print(json.dumps({"kernel": a.kernel, "bs": n, "k": kk, "batch": b, "ms": ms, "fp64_eq_tflops": flops / ms / 1e9,
                       "slices": a.slices if a.kernel == "split" else None}))
+
+
+def conv_flops(L):
+    """Flops of one series' convolution by FFT: three transforms of 5 L log2 L and the spectral
+    product (6 L), the usual count for radix-2 complex FFTs."""
+    import math
+    return 3 * 5 * L * math.log2(L) + 6 * L
+
+
+def conv_driver(a, pkg):
+    """bt_energy_convolve on bs^2 element series (one diagonal block) of `batch` energies each."""
+    import torch
+    n_elem, ne = a.bs * a.bs, a.batch
+    g = torch.Generator(device="cuda").manual_seed(1)
+    A = torch.randn(ne, n_elem, dtype=torch.complex128, device="cuda", generator=g)
+    B = torch.randn(ne, n_elem, dtype=torch.complex128, device="cuda", generator=g)
+    C = torch.empty(2 * ne - 1, n_elem, dtype=torch.complex128, device="cuda")
+
+    def run():
+        pkg.bt_energy_convolve(n_elem, ne, ne, A, n_elem, B, n_elem, C, n_elem)
+
+    run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.reps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.reps
+    L = 1 << (2 * ne - 2).bit_length()
+    flops = conv_flops(L) * n_elem
+    moved = 16.0 * n_elem * (ne + ne + 2 * ne - 1)
+    print(json.dumps({"kernel": "conv", "series": n_elem, "energies": ne, "L": L, "ms": ms,
+                      "fp64_tflops": flops / ms / 1e9, "hbm_gbs": moved / ms / 1e6}))
 
 
 def cublas_reference(a):
