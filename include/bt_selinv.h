@@ -69,6 +69,11 @@ typedef enum { BT_SYM_GENERAL = 0, BT_SYM_HERMITIAN = 1, BT_SYM_ANTIHERMITIAN = 
  *   diag   BT_LAYOUT_BLOCKS : [nb][bs][bs] diagonal blocks
  *          BT_LAYOUT_DIAGVEC: [nb][bs] the diagonal entries only (a diagonal matrix; upper and
  *                             lower must be NULL)
+ *          BT_LAYOUT_PACKED_UPPER (Sigma^< / Sigma^> of the G system, P^< / P^> of the W system,
+ *                             symmetry BT_SYM_ANTIHERMITIAN; Sec. 5.2): [nb][bs (bs + 1) / 2]
+ *                             the upper triangle of each anti-Hermitian diagonal block, row by
+ *                             row, entry (r, c >= r) at r bs - r (r - 1) / 2 + (c - r); upper
+ *                             blocks in full
  *   upper  [nb-1][bs][bs] blocks (i,i+1); NULL means all off-diagonal blocks are zero
  *   lower  [nb-1][bs][bs] blocks (i+1,i); read only when symmetry == BT_SYM_GENERAL, else
  *          block (i+1,i) is upper[i]^H (HERMITIAN) or -upper[i]^H (ANTIHERMITIAN)

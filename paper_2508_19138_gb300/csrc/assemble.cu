@@ -65,7 +65,12 @@ __global__ void assemble_b_kernel(int bs, BBlockArgs a) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < bs2; i += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(i / bs), c = (int)(i - (long long)r * bs);
     zd v = zmake(0.0, 0.0);
-    if (a.sig) v = a.sig[a.sig_stride * e + i];
+    if (a.sig && !a.sig_packed) v = a.sig[a.sig_stride * e + i];
+    if (a.sig && a.sig_packed) {
+      const int lo = r < c ? r : c, hi = r < c ? c : r;
+      const zd u = a.sig[a.sig_stride * e + (long long)lo * bs - (long long)lo * (lo - 1) / 2 + (hi - lo)];
+      v = r <= c ? u : zmake(-u.x, u.y);  // lower triangle: -conj(upper)
+    }
     if (a.sigvec && r == c) v = a.sigvec[a.sigvec_stride * e + r];
     if (a.obc1) v = zadd(v, a.obc1[a.obc_stride * e + i]);
     if (a.obc2) v = zadd(v, a.obc2[a.obc_stride * e + i]);
@@ -150,6 +155,21 @@ __global__ void write_packed_kernel(int bs, int nblk, const zd* __restrict__ src
   }
 }
 
+// Full anti-Hermitian blocks from their packed upper triangles.
+__global__ void unpack_antiherm_kernel(int bs, const zd* __restrict__ src, long long s_e, zd* __restrict__ dst,
+                                       long long d_blk, long long d_e) {
+  const int e = blockIdx.z, blk = blockIdx.y;
+  const long long bs2 = (long long)bs * bs, pk = (long long)bs * (bs + 1) / 2;
+  const zd* s = src + s_e * e + pk * blk;
+  zd* d = dst + d_e * e + d_blk * blk;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < bs2; i += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(i / bs), c = (int)(i - (long long)r * bs);
+    const int lo = r < c ? r : c, hi = r < c ? c : r;
+    const zd u = s[(long long)lo * bs - (long long)lo * (lo - 1) / 2 + (hi - lo)];
+    d[i] = r <= c ? u : zmake(-u.x, u.y);
+  }
+}
+
 // Write nblk blocks per batch entry: mode 0 copy, mode 1 (X - X^H)/2.
 __global__ void write_blocks_kernel(int bs, int nblk, const zd* __restrict__ src, long long s_blk, long long s_e,
                                     zd* __restrict__ dst, long long d_blk, long long d_e, int mode) {
@@ -224,6 +244,18 @@ bt_status assemble_m(cudaStream_t st, int bs, int batch, const MBlockArgs& a) {
 bt_status assemble_b(cudaStream_t st, int bs, int batch, const BBlockArgs& a) {
   if (batch <= 0) return BT_OK;
   assemble_b_kernel<<<grid_for((long long)bs * bs, batch), 256, 0, st>>>(bs, a); count_launch();
+  BT_CUDA_TRY(cudaGetLastError());
+  return BT_OK;
+}
+
+bt_status unpack_antiherm(cudaStream_t st, int bs, int nblk, int batch, const zd* src, long long s_e, zd* dst,
+                          long long d_blk, long long d_e) {
+  if (batch <= 0 || nblk <= 0) return BT_OK;
+  const long long bs2 = (long long)bs * bs;
+  long long gx = (bs2 + 255) / 256;
+  if (gx > 64) gx = 64;
+  unpack_antiherm_kernel<<<dim3((unsigned)gx, nblk, batch), 256, 0, st>>>(bs, src, s_e, dst, d_blk, d_e);
+  count_launch();
   BT_CUDA_TRY(cudaGetLastError());
   return BT_OK;
 }

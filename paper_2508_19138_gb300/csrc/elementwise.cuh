@@ -32,12 +32,14 @@ struct MBlockArgs {
   long long obc_stride = 0;
 };
 
-// out[e] = sig (+ diag(sigvec)) + obc1 + obc2
+// out[e] = sig (+ diag(sigvec)) + obc1 + obc2; with sig_packed, sig is an anti-Hermitian block
+// stored by its upper triangle (entry (r, c >= r) at r bs - r (r - 1) / 2 + (c - r)).
 struct BBlockArgs {
   zd* out = nullptr;
   long long out_stride = 0;
   const zd* sig = nullptr;
   long long sig_stride = 0;
+  int sig_packed = 0;
   const zd* sigvec = nullptr;
   long long sigvec_stride = 0;
   const zd* obc1 = nullptr;
@@ -64,6 +66,10 @@ bt_status write_diagvec(cudaStream_t st, int bs, int nblk, int batch, const zd* 
 bt_status write_packed(cudaStream_t st, int bs, int nblk, int batch, const zd* src, long long s_blk, long long s_e,
                        zd* dst, long long d_e);
 bt_status shift_diag(cudaStream_t st, int bs, int batch, zd* X, long long sX, double v);  // X += v I
+// full anti-Hermitian blocks from packed upper triangles: nblk blocks per batch entry, the packed
+// blocks bs (bs + 1) / 2 apart (s_e per entry), the full ones d_blk apart (d_e per entry)
+bt_status unpack_antiherm(cudaStream_t st, int bs, int nblk, int batch, const zd* src, long long s_e, zd* dst,
+                          long long d_blk, long long d_e);
 bt_status merge_status(cudaStream_t st, int E, const int* info, int n_sources, long long src_stride, int* status);
 // status[e] = *flag for every e when *flag != 0 (a chunk-wide error word that overrides the
 // numerical failures recorded after it)

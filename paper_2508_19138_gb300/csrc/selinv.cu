@@ -588,16 +588,27 @@ namespace {
 
 // per-energy element extents of a bt_bt operand
 long long diag_extent(const bt_bt& b, int nb, int bs) {
-  return b.layout == BT_LAYOUT_DIAGVEC ? (long long)nb * bs : (long long)nb * bs * bs;
+  if (b.layout == BT_LAYOUT_DIAGVEC) return (long long)nb * bs;
+  if (b.layout == BT_LAYOUT_PACKED_UPPER) return (long long)nb * bs * (bs + 1) / 2;
+  return (long long)nb * bs * bs;
 }
 long long off_extent(int nb, int bs) { return (long long)(nb > 1 ? nb - 1 : 0) * bs * bs; }
 
-bt_status validate_operand(const bt_bt* b, bool required, bool allow_diagvec, const char* name, std::string* why) {
+bt_status validate_operand(const bt_bt* b, bool required, bool allow_diagvec, const char* name, std::string* why,
+                           bool allow_packed = false) {
   if (!b) {
     if (required) { *why = std::string(name) + " is required"; return BT_ERR_INVALID_ARG; }
     return BT_OK;
   }
   if (!b->diag && required) { *why = std::string(name) + ".diag is required"; return BT_ERR_INVALID_ARG; }
+  if (b->layout == BT_LAYOUT_PACKED_UPPER) {
+    // Sec. 5.2: an anti-Hermitian operand stored by the upper triangles of its diagonal blocks
+    if (!allow_packed || b->symmetry != BT_SYM_ANTIHERMITIAN) {
+      *why = std::string(name) + ": packed upper-triangle input is for anti-Hermitian lesser / greater operands";
+      return BT_ERR_INVALID_ARG;
+    }
+    return BT_OK;
+  }
   if (b->layout != BT_LAYOUT_BLOCKS && b->layout != BT_LAYOUT_DIAGVEC) { *why = std::string(name) + ": bad layout"; return BT_ERR_INVALID_ARG; }
   if (b->layout == BT_LAYOUT_DIAGVEC && !allow_diagvec) { *why = std::string(name) + ": diagonal-vector layout not accepted"; return BT_ERR_INVALID_ARG; }
   if (b->layout == BT_LAYOUT_DIAGVEC && (b->upper || b->lower)) { *why = std::string(name) + ": diagonal-vector layout has no off-diagonal blocks"; return BT_ERR_INVALID_ARG; }
@@ -847,7 +858,11 @@ bt_status solve_chunk_g(bt_ctx* c, const bt_bt* H, const bt_bt* S, const bt_bt* 
     a.out_stride = es;
     if (LGd[w]) {
       if (sLG[w]->layout == BT_LAYOUT_DIAGVEC) { a.sigvec = LGd[w] + (long long)i * bs; a.sigvec_stride = dstride(sLG[w]); }
-      else { a.sig = LGd[w] + i * B2; a.sig_stride = dstride(sLG[w]); }
+      else if (sLG[w]->layout == BT_LAYOUT_PACKED_UPPER) {
+        a.sig = LGd[w] + (long long)i * bs * (bs + 1) / 2;
+        a.sig_stride = dstride(sLG[w]);
+        a.sig_packed = 1;
+      } else { a.sig = LGd[w] + i * B2; a.sig_stride = dstride(sLG[w]); }
     }
     if (d.obc) {
       const zd* ob = w == 0 ? c->obcL : c->obcG;
@@ -911,9 +926,9 @@ bt_status solve_chunk_w(bt_ctx* c, const bt_bt* V, const bt_bt* PR, const bt_bt*
   auto mkP = [&](const bt_bt* P) {
     PT p{};
     if (!P) return p;
-    p.ed = P->per_energy ? NB2 : 0;
+    p.ed = P->per_energy ? diag_extent(*P, N, bs) : 0;
     p.eo = P->per_energy ? N1B2 : 0;
-    p.d = at_energy(P->diag, P->per_energy, NB2, e0);
+    p.d = at_energy(P->diag, P->per_energy, diag_extent(*P, N, bs), e0);
     p.u = at_energy(P->upper, P->per_energy, N1B2, e0);
     p.l = at_energy(P->lower, P->per_energy, N1B2, e0);
     p.sym = P->symmetry;
@@ -950,9 +965,19 @@ bt_status solve_chunk_w(bt_ctx* c, const bt_bt* V, const bt_bt* PR, const bt_bt*
   const bool needL = oL && (oL->diag || oL->upper);
   const bool needG = oG && (oG->diag || oG->upper);
   const bool need[2] = {needL, needG};
-  const PT plg[2] = {mkP(PL), mkP(PG)};
+  PT plg[2] = {mkP(PL), mkP(PG)};
   zd* Bd[2] = {c->BdL, c->BdG};
   zd* Bu[2] = {c->BuL, c->BuG};
+  // P^<> given by the upper triangles of its diagonal blocks (Sec. 5.2): the chunk's diagonal
+  // blocks are unpacked into the B^<> buffer, which is free until the B^<> assembly (the products
+  // that read P^<> all run before it)
+  const bt_bt* Plg[2] = {PL, PG};
+  for (int w = 0; w < 2; ++w) {
+    if (!need[w] || !Plg[w] || Plg[w]->layout != BT_LAYOUT_PACKED_UPPER) continue;
+    BT_TRY(bt::unpack_antiherm(st, bs, N, Ec, plg[w].d, plg[w].ed, Bd[w], B2, NB2));
+    plg[w].d = Bd[w];
+    plg[w].ed = NB2;
+  }
 
   // ---- W contacts (Sec. 4.2: the retarded boundary by Eq. 4, the lesser / greater boundary by
   // the Stein equation of Eq. 7) ----
@@ -1207,8 +1232,8 @@ bt_status check_solve_args(bt_ctx* c, const bt_bt* H, const bt_bt* S, const bt_b
   if (c->d.system == BT_SYS_G) {
     if ((s = validate_operand(S, false, false, "S", &why)) != BT_OK) return fail(why);
     if ((s = validate_operand(sR, false, true, "sigR", &why)) != BT_OK) return fail(why);
-    if ((s = validate_operand(sL, false, true, "sigL", &why)) != BT_OK) return fail(why);
-    if ((s = validate_operand(sG, false, true, "sigG", &why)) != BT_OK) return fail(why);
+    if ((s = validate_operand(sL, false, true, "sigL", &why, true)) != BT_OK) return fail(why);
+    if ((s = validate_operand(sG, false, true, "sigG", &why, true)) != BT_OK) return fail(why);
     if (sL && sL->upper && sL->symmetry != BT_SYM_ANTIHERMITIAN) return fail("sigL off-diagonal blocks must be anti-Hermitian");
     if (sG && sG->upper && sG->symmetry != BT_SYM_ANTIHERMITIAN) return fail("sigG off-diagonal blocks must be anti-Hermitian");
   } else {
@@ -1217,8 +1242,8 @@ bt_status check_solve_args(bt_ctx* c, const bt_bt* H, const bt_bt* S, const bt_b
     if (H->symmetry != BT_SYM_HERMITIAN) return fail("V must be Hermitian");
     if ((s = validate_operand(sR, true, false, "P^R", &why)) != BT_OK) return fail(why);
     if (c->d.nb > 1 && (!sR->upper || (sR->symmetry == BT_SYM_GENERAL && !sR->lower))) return fail("P^R off-diagonal blocks are required");
-    if ((s = validate_operand(sL, false, false, "P^<", &why)) != BT_OK) return fail(why);
-    if ((s = validate_operand(sG, false, false, "P^>", &why)) != BT_OK) return fail(why);
+    if ((s = validate_operand(sL, false, false, "P^<", &why, true)) != BT_OK) return fail(why);
+    if ((s = validate_operand(sG, false, false, "P^>", &why, true)) != BT_OK) return fail(why);
     if ((oL && (oL->diag || oL->upper) && !sL) || (oG && (oG->diag || oG->upper) && !sG))
       return fail("W^<> outputs need P^<>");
     if (c->d.nb > 1 && ((sL && (!sL->upper || sL->symmetry != BT_SYM_ANTIHERMITIAN)) ||

@@ -310,3 +310,53 @@ def test_packed_upper_storage_of_lesser_greater():
     with pytest.raises(pkg.BTError):
         solver.solve(s.energies, bad, st1)
     solver.close()
+
+
+def test_packed_lesser_greater_inputs():
+    """Sec. 5.2 storage of the inputs: Sigma^<> diagonal blocks given by their upper triangles
+    (BT_LAYOUT_PACKED_UPPER, anti-Hermitian), off-diagonal blocks in full.  The solve equals the
+    one with the full blocks bitwise (the blocks are exactly anti-Hermitian) and the oracle."""
+    import torch
+    from paper_2508_19138_gb300 import highlevel, BT, BT_LAYOUT_BLOCKS, BT_LAYOUT_PACKED_UPPER, BT_SYM_ANTIHERMITIAN
+    rng = np.random.default_rng(23)
+    s = synthetic.random_device(23, 4, 20, 3)
+    nb, bs, E = s.nb, s.bs, 3
+
+    def antiherm(shape, scale):
+        X = synthetic.cn(rng, shape) * scale
+        return X - np.conj(np.swapaxes(X, -1, -2))
+
+    Ld, Lu = antiherm((E, nb, bs, bs), 0.01), synthetic.cn(rng, (E, nb - 1, bs, bs)) * 0.01
+    Gd, Gu = antiherm((E, nb, bs, bs), 0.01), synthetic.cn(rng, (E, nb - 1, bs, bs)) * 0.01
+    iu = np.triu_indices(bs)
+    pack = lambda A: np.ascontiguousarray(A[..., iu[0], iu[1]])
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    runs = {}
+    for packed in (False, True):
+        solver = highlevel.GSolver(nb, bs, E, s.eta, s.kT, s.mu_left, s.mu_right, obc=True)
+        solver.set_inputs(s.H_diag, s.H_upper)
+        lay = BT_LAYOUT_PACKED_UPPER if packed else BT_LAYOUT_BLOCKS
+        solver.sigL = BT(t(pack(Ld) if packed else Ld), t(Lu), None, lay, BT_SYM_ANTIHERMITIAN, True)
+        solver.sigG = BT(t(pack(Gd) if packed else Gd), t(Gu), None, lay, BT_SYM_ANTIHERMITIAN, True)
+        outs, status = solver.allocate_outputs(E)
+        solver.solve(s.energies, outs, status)
+        torch.cuda.synchronize()
+        assert (status.cpu().numpy() == 0).all()
+        runs[packed] = {w + "_" + k: getattr(o, k).cpu().numpy() for w, o in outs.items()
+                        for k in ("diag", "upper", "lower") if getattr(o, k) is not None}
+        solver.close()
+    for k in runs[False]:
+        assert np.array_equal(runs[False][k], runs[True][k]), k
+    for e in range(E):
+        z = s.energies[e] + 1j * s.eta
+        M, BL, BG, info = oracle.assemble_g(s, e, surface="eig")
+        BL = BL + oracle.bt_dense(Ld[e], Lu[e], lower_sign=-1.0)
+        BG = BG + oracle.bt_dense(Gd[e], Gu[e], lower_sign=-1.0)
+        XR = np.linalg.inv(M)
+        for key, B in (("L", BL), ("G", BG)):
+            X = oracle.symmetrize_lesser(XR @ B @ XR.conj().T)
+            d, u, _ = oracle.selected_blocks(X, nb, bs)
+            from gpu_util import compare_blocks, lesser_floor
+            fl = 0.01 * lesser_floor(dict(R_diag=oracle.selected_blocks(XR, nb, bs)[0], info=info))
+            assert compare_blocks(runs[True][key + "_diag"][e], d, key + "_diag", e, TOL_FP64, fl) <= TOL_FP64
+            assert compare_blocks(runs[True][key + "_upper"][e], u, key + "_upper", e, TOL_FP64, fl) <= TOL_FP64

@@ -100,3 +100,39 @@ def test_w_contacts_change_the_edge_blocks():
     closed = oracle.solve_w(ws, 1)
     assert block_errors(res["L_diag"][1][:1], closed["L_diag"][:1]).max() > 1e-3
     assert block_errors(res["R_diag"][1][:1], closed["R_diag"][:1]).max() > 1e-3
+
+
+def test_packed_polarization_inputs():
+    """P^<> diagonal blocks given by their upper triangles (Sec. 5.2): the same W^R, W^<> as with
+    the full blocks, bitwise (P^<> here is exactly anti-Hermitian)."""
+    import torch
+    import paper_2508_19138_gb300 as pkg
+    from paper_2508_19138_gb300 import BT, BTOut
+    ws = synthetic.w_system(spacing=2.2, n_energies=3, nb=4, ny=2, nz=2, nx=8, r_cut=5.0)
+    nb, bs, E = ws.nb, ws.bs, 3
+    parts = [ws.P_blocks(e) for e in range(E)]
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    P = [np.stack([p[j] for p in parts]) for j in range(7)]
+    iu = np.triu_indices(bs)
+    pack = lambda A: np.ascontiguousarray(A[..., iu[0], iu[1]])
+    got = {}
+    for packed in (False, True):
+        lay = pkg.BT_LAYOUT_PACKED_UPPER if packed else pkg.BT_LAYOUT_BLOCKS
+        V = BT(t(ws.V_diag), t(ws.V_upper), None, pkg.BT_LAYOUT_BLOCKS, pkg.BT_SYM_HERMITIAN, False)
+        PR = BT(t(P[0]), t(P[1]), t(P[2]), pkg.BT_LAYOUT_BLOCKS, pkg.BT_SYM_GENERAL, True)
+        PL = BT(t(pack(P[3]) if packed else P[3]), t(P[4]), None, lay, pkg.BT_SYM_ANTIHERMITIAN, True)
+        PG = BT(t(pack(P[5]) if packed else P[5]), t(P[6]), None, lay, pkg.BT_SYM_ANTIHERMITIAN, True)
+        mk = lambda *sh: torch.empty(sh, dtype=torch.complex128, device="cuda")
+        oR = BTOut(mk(E, nb, bs, bs), mk(E, nb - 1, bs, bs), mk(E, nb - 1, bs, bs))
+        oL = BTOut(mk(E, nb, bs, bs), mk(E, nb - 1, bs, bs), None)
+        oG = BTOut(mk(E, nb, bs, bs), mk(E, nb - 1, bs, bs), None)
+        status = torch.zeros(E, dtype=torch.int32, device="cuda")
+        ctx = pkg.bt_selinv_create(pkg.make_desc(nb, bs, E, system=pkg.BT_SYS_W, obc=False, eta=0.0))
+        pkg.bt_selinv_solve(ctx, V, None, PR, PL, PG, ws.energies[:E], oR, oL, oG, status)
+        torch.cuda.synchronize()
+        ctx.close()
+        got[packed] = [x.cpu().numpy() for x in (oR.diag, oR.upper, oR.lower, oL.diag, oL.upper, oG.diag, oG.upper)]
+    for a, b in zip(got[False], got[True]):
+        assert np.array_equal(a, b)
+    ref = oracle.solve_w(ws, 1)
+    assert block_errors(got[True][3][1], ref["L_diag"]).max() < TOL_FP64
