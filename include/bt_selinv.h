@@ -158,6 +158,12 @@ typedef struct {
    * iterations get one Newton step on x^{-1} (a Stein equation solved by doubling), which brings
    * the surface function back to FP64 accuracy.  0: 14; negative: never.                        */
   int decim_newton_after;
+  /* Kernel shape overrides (the autotuner's knobs; 0 = the built-in rule).  gemm_tile: output
+   * tile of the FP64 products, 16 or 32 (rule: 32 unless that leaves SMs idle).  inv_panel:
+   * panel width of the blocked inversions, 4, 8, 16 or 32, used only when narrower than the
+   * built-in width (16 with FP64 updates, 32 with sliced ones).                                 */
+  int gemm_tile;
+  int inv_panel;
 } bt_selinv_desc;
 
 typedef struct bt_ctx bt_ctx;

@@ -37,7 +37,7 @@ class bt_selinv_desc(C.Structure):
                 ("eta", C.c_double), ("kT", C.c_double), ("mu_left", C.c_double), ("mu_right", C.c_double),
                 ("decim_tol", C.c_double), ("decim_maxit", C.c_int), ("hbm_budget_bytes", C.c_size_t),
                 ("obc_memo", C.c_int), ("memo_nfpi", C.c_int), ("memo_capacity", C.c_int), ("split_scope", C.c_int),
-                ("graph", C.c_int), ("decim_newton_after", C.c_int)]
+                ("graph", C.c_int), ("decim_newton_after", C.c_int), ("gemm_tile", C.c_int), ("inv_panel", C.c_int)]
 
 
 class bt_stats(C.Structure):

@@ -104,11 +104,11 @@ def make_desc(nb: int, bs: int, max_energies: int, system: int = N.BT_SYS_G, pre
               kT: float = 0.025, mu_left: float = 0.0, mu_right: float = 0.0, decim_tol: float = 1e-14,
               decim_maxit: int = 100, hbm_budget_bytes: int = 0, obc_memo: bool = False, memo_nfpi: int = 0,
               memo_capacity: int = 0, split_scope: int = 0, graph: bool = False,
-              decim_newton_after: int = 0) -> N.bt_selinv_desc:
+              decim_newton_after: int = 0, gemm_tile: int = 0, inv_panel: int = 0) -> N.bt_selinv_desc:
     return N.bt_selinv_desc(nb, bs, max_energies, system, precision, split_slices, 1 if symmetrize else 0,
                             1 if obc else 0, eta, kT, mu_left, mu_right, decim_tol, decim_maxit, hbm_budget_bytes,
                             1 if obc_memo else 0, memo_nfpi, memo_capacity, split_scope, 1 if graph else 0,
-                            decim_newton_after)
+                            decim_newton_after, gemm_tile, inv_panel)
 
 
 class Context:

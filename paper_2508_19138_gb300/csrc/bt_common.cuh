@@ -68,13 +68,13 @@ struct Operand {
 // C[b] = alpha op(A[b]) op(B[b]) + beta C[b]; rows m, cols n, depth k.  active[b] == 0 skips
 // batch entry b (active may be null).  FP64 (DFMA) kernel.
 bt_status zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A, Operand B, zd beta,
-                zd* C, int ldc, long long strideC, int batch, const int* active);
+                zd* C, int ldc, long long strideC, int batch, const int* active, int tile = 0);
 
 // C = alpha op(A) op(B) + beta C for a square n x n C whose exact value is anti-Hermitian
 // (alpha real, beta C anti-Hermitian, op(A) op(B) anti-Hermitian): the tiles on and above the
 // diagonal are computed, the others written as -(upper)^H.  Complex alpha: plain zgemm.
 bt_status zgemm_antiherm(cudaStream_t st, int n, int k, zd alpha, Operand A, Operand B, zd beta, zd* C, int ldc,
-                         long long strideC, int batch, const int* active);
+                         long long strideC, int batch, const int* active, int tile = 0);
 
 // Which kernel runs a complex product: FP64 DFMA (slices == 0) or the sliced bf16 tensor-core
 // product with `slices` slices per operand and its workspace.
@@ -83,6 +83,8 @@ struct Engine {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   int* err = nullptr;  // sliced products: one device word set to BT_ERR_TIMEOUT by a bounded wait
+  int tile = 0;        // FP64 products: output tile 16 or 32 (0: 32 unless that leaves SMs idle)
+  int panel = 0;       // inversions: panel width below the default (0: the default)
 };
 
 // Split-precision (sliced bf16 tensor-core) variant of zgemm; see split_gemm.cu.

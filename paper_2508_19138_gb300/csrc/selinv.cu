@@ -216,6 +216,9 @@ bt_status validate_desc(const bt_selinv_desc* d, std::string* why) {
   if (d->graph != 0 && d->graph != 1) return fail("graph must be 0 or 1");
   if (d->graph && d->obc_memo) return fail("graph mode and contact memoization are exclusive");
   if (d->split_scope != 0 && d->split_scope != 1) return fail("split_scope must be 0 or 1");
+  if (d->gemm_tile != 0 && d->gemm_tile != 16 && d->gemm_tile != 32) return fail("gemm_tile must be 0, 16 or 32");
+  if (d->inv_panel != 0 && d->inv_panel != 4 && d->inv_panel != 8 && d->inv_panel != 16 && d->inv_panel != 32)
+    return fail("inv_panel must be 0, 4, 8, 16 or 32");
   if (d->obc_memo && d->memo_capacity > 1000000) return fail("memo_capacity too large");
   if (!(d->eta >= 0.0)) return fail("eta must be >= 0");
   if ((double)d->bs * d->bs * d->nb > 4.0e12) return fail("problem too large");
@@ -278,9 +281,9 @@ bt_status prod(bt_ctx* c, int Ec, double alpha, const Blk& A, const Blk& B, doub
   }
   if (antiherm && c->d.symmetrize)
     return bt::zgemm_antiherm(c->st, bs, bs, zmake(a, 0.0), opnd(A, bs), opnd(B, bs), zmake(beta, 0.0), C, bs, sC, Ec,
-                              nullptr);
+                              nullptr, c->d.gemm_tile);
   return bt::zgemm(c->st, bs, bs, bs, zmake(a, 0.0), opnd(A, bs), opnd(B, bs), zmake(beta, 0.0), C, bs, sC, Ec,
-                   nullptr);
+                   nullptr, c->d.gemm_tile);
 }
 
 bt_status inv(bt_ctx* c, int Ec, zd* A, long long sA, int* info) {
@@ -491,6 +494,8 @@ bt_status ctx_create(const bt_selinv_desc* desc, void* cuda_stream, void* ext_ws
   c->stats.workspace_bytes = need;
   if (is_split(d) && d.split_scope == 1)
     c->eng_kept = bt::Engine{kept_slices_of(d), c->split_ws, c->split_bytes, c->tflag};
+  c->eng_kept.tile = d.gemm_tile;
+  c->eng_kept.panel = d.inv_panel;
   if (d.obc_memo) {
     c->memo_key.assign(d.memo_capacity, 0);
     c->memo_used.assign(d.memo_capacity, 0);

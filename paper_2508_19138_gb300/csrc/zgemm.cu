@@ -252,15 +252,17 @@ int sm_count() {
   return v;
 }
 
-// Tiles of 32 unless they would leave SMs idle (fewer than two tiles per SM), then 16.
+// Tiles of 32 unless they would leave SMs idle (fewer than two tiles per SM), then 16; `tile`
+// (16 or 32, from the autotuner) overrides the rule.
 template <bool TRI>
 bt_status launch_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, const Operand& A, const Operand& B, zd beta,
-                       zd* C, int ldc, long long strideC, int batch, const int* active) {
+                       zd* C, int ldc, long long strideC, int batch, const int* active, int tile) {
   auto tiles = [&](int tl) {
     const long long tm = (m + tl - 1) / tl, tn = (n + tl - 1) / tl;
     return TRI ? tn * (tn + 1) / 2 : tm * tn;
   };
-  if (tiles(32) * batch < 2LL * sm_count()) {
+  const bool use16 = tile == 16 || (tile != 32 && tiles(32) * batch < 2LL * sm_count());
+  if (use16) {
     const long long t16 = tiles(16);
     dim3 grid = TRI ? dim3((unsigned)t16, 1, batch) : dim3((n + 15) / 16, (m + 15) / 16, batch);
     return launch_tile<TRI, 16>(st, grid, m, n, k, alpha, A, B, beta, C, ldc, strideC, active);
@@ -272,7 +274,7 @@ bt_status launch_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, const Ope
 }  // namespace
 
 bt_status zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A, Operand B, zd beta, zd* C,
-                int ldc, long long strideC, int batch, const int* active) {
+                int ldc, long long strideC, int batch, const int* active, int tile) {
   if (m < 0 || n < 0 || k < 0 || batch < 0) return BT_ERR_INVALID_ARG;
   if (m == 0 || n == 0 || batch == 0) return BT_OK;
   if (batch > 65535) {
@@ -283,19 +285,20 @@ bt_status zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A, Opera
       a.p += A.stride * b0;
       b.p += B.stride * b0;
       BT_TRY(zgemm(st, m, n, k, alpha, a, b, beta, C + strideC * b0, ldc, strideC, nbatch,
-                   active ? active + b0 : nullptr));
+                   active ? active + b0 : nullptr, tile));
     }
     return BT_OK;
   }
-  return launch_zgemm<false>(st, m, n, k, alpha, A, B, beta, C, ldc, strideC, batch, active);
+  return launch_zgemm<false>(st, m, n, k, alpha, A, B, beta, C, ldc, strideC, batch, active, tile);
 }
 
 bt_status zgemm_antiherm(cudaStream_t st, int n, int k, zd alpha, Operand A, Operand B, zd beta, zd* C, int ldc,
-                         long long strideC, int batch, const int* active) {
+                         long long strideC, int batch, const int* active, int tile) {
   if (n < 0 || k < 0 || batch < 0) return BT_ERR_INVALID_ARG;
   if (n == 0 || batch == 0) return BT_OK;
-  if (alpha.y != 0.0 || batch > 65535) return zgemm(st, n, n, k, alpha, A, B, beta, C, ldc, strideC, batch, active);
-  return launch_zgemm<true>(st, n, n, k, alpha, A, B, beta, C, ldc, strideC, batch, active);
+  if (alpha.y != 0.0 || batch > 65535)
+    return zgemm(st, n, n, k, alpha, A, B, beta, C, ldc, strideC, batch, active, tile);
+  return launch_zgemm<true>(st, n, n, k, alpha, A, B, beta, C, ldc, strideC, batch, active, tile);
 }
 
 bt_status gemm_antiherm(const Engine& eng, cudaStream_t st, int n, int k, zd alpha, Operand A, Operand B, zd beta,
@@ -303,7 +306,7 @@ bt_status gemm_antiherm(const Engine& eng, cudaStream_t st, int n, int k, zd alp
   if (eng.slices > 0)
     return split_zgemm(st, n, n, k, alpha, A, B, beta, C, ldc, strideC, batch, eng.slices, eng.ws, eng.ws_bytes,
                        active, eng.err, 0);
-  return zgemm_antiherm(st, n, k, alpha, A, B, beta, C, ldc, strideC, batch, active);
+  return zgemm_antiherm(st, n, k, alpha, A, B, beta, C, ldc, strideC, batch, active, eng.tile);
 }
 
 bt_status gemm(const Engine& eng, cudaStream_t st, int m, int n, int k, zd alpha, Operand A, Operand B, zd beta,
@@ -311,7 +314,7 @@ bt_status gemm(const Engine& eng, cudaStream_t st, int m, int n, int k, zd alpha
   if (eng.slices > 0)
     return split_zgemm(st, m, n, k, alpha, A, B, beta, C, ldc, strideC, batch, eng.slices, eng.ws, eng.ws_bytes,
                        active, eng.err, 0);
-  return zgemm(st, m, n, k, alpha, A, B, beta, C, ldc, strideC, batch, active);
+  return zgemm(st, m, n, k, alpha, A, B, beta, C, ldc, strideC, batch, active, eng.tile);
 }
 
 }  // namespace bt

@@ -555,8 +555,10 @@ bt_status zinv(cudaStream_t st, int n, zd* A, long long sA, int batch, int* info
   }
   // wide panels when the updates run sliced and the workspace was sized for them
   const bool wide = E.slices > 0 && ws_bytes >= zinv_workspace_bytes(n, batch, true);
-  const int kb = panel_width(n, wide);
+  int kb = panel_width(n, wide);
   if (kb == 0) return BT_ERR_UNSUPPORTED;
+  // a narrower panel (autotuner) fits the workspace sized for the default one
+  if (E.panel >= 4 && E.panel < kb) kb = E.panel;
   if (ws_bytes < zinv_workspace_bytes(n, batch, wide) || ws == nullptr) return BT_ERR_INVALID_ARG;
   if (batch > 65535) return BT_ERR_INVALID_ARG;
   int* perm = static_cast<int*>(ws);

@@ -38,12 +38,13 @@ class GSolver:
                  mu_right: float = 0.0, obc: bool = True, precision: int = N.BT_FP64, split_slices: int = 0,
                  symmetrize: bool = True, decim_tol: float = 1e-14, decim_maxit: int = 100, stream=None,
                  hbm_budget_bytes: int = 0, device: str = "cuda", obc_memo: bool = False, memo_nfpi: int = 0,
-                 memo_capacity: int = 0, split_scope: int = 0, graph: bool = False, decim_newton_after: int = 0):
+                 memo_capacity: int = 0, split_scope: int = 0, graph: bool = False, decim_newton_after: int = 0,
+                 gemm_tile: int = 0, inv_panel: int = 0):
         self.nb, self.bs, self.max_energies = nb, bs, max_energies
         self.device = device
         self.desc = make_desc(nb, bs, max_energies, N.BT_SYS_G, precision, split_slices, symmetrize, obc, eta, kT,
                               mu_left, mu_right, decim_tol, decim_maxit, hbm_budget_bytes, obc_memo, memo_nfpi,
-                              memo_capacity, split_scope, graph, decim_newton_after)
+                              memo_capacity, split_scope, graph, decim_newton_after, gemm_tile, inv_panel)
         self._own_stream = None
         self.graph = bool(graph)
         self._stage = None  # graph mode: fixed buffers for per-call energy slices of the self-energies

@@ -19,3 +19,26 @@ def test_cache_round_trip(tmp_path):
     autotune.save_cache({key: {"best": 16, "table": {"16": 0.1}}}, p)
     assert autotune.load_cache(p)[key]["best"] == 16
     assert autotune.load_cache(str(tmp_path / "missing.json")) == {}
+
+
+def test_coordinate_descent_tunes_one_parameter_at_a_time():
+    """A separable cost: the chunk first (with the start values of the others), then the tile with
+    the chosen chunk, then the panel; candidates outside the budget are skipped."""
+    calls = []
+
+    def cost(p):
+        calls.append(dict(p))
+        return {4: 3.0, 8: 2.0, 16: 1.5, 32: 1.0}[p["max_energies"]] + {0: 0.2, 16: 0.1, 32: 0.3}[p["gemm_tile"]] \
+            + {0: 0.05, 8: 0.0}[p["inv_panel"]]
+
+    res = autotune.coordinate_descent(cost, {"max_energies": (4, 8, 16, 32), "gemm_tile": (32, 16),
+                                             "inv_panel": (0, 8)},
+                                      {"max_energies": 4, "gemm_tile": 0, "inv_panel": 0},
+                                      fits=lambda p: p["max_energies"] <= 16)
+    assert res["best"] == {"max_energies": 16, "gemm_tile": 16, "inv_panel": 8}
+    assert set(res["table"]["max_energies"]) == {"4", "8", "16"}
+    assert len(calls) == 3 + 2 + 2
+    assert all(c["gemm_tile"] == 0 for c in calls[:3]) and all(c["max_energies"] == 16 for c in calls[3:])
+    with pytest.raises(ValueError):
+        autotune.coordinate_descent(cost, {"max_energies": (32,)}, {"max_energies": 32, "gemm_tile": 0,
+                                                                    "inv_panel": 0}, fits=lambda p: False)
