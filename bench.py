@@ -54,7 +54,8 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=["nanoribbon", "random8x32", "w16x1024", "serving"], default="nanoribbon")
     p.add_argument("--requests", type=int, default=24, help="serving: prefix of the request stream")
-    p.add_argument("--serving-max-energies", type=int, default=32, help="serving: cap per request (flagged)")
+    p.add_argument("--serving-max-energies", type=int, default=0,
+                   help="serving: cap on the energies per request (0: as drawn; a cap is flagged in the config)")
     p.add_argument("--serving-budget-gb", type=float, default=150.0)
     p.add_argument("--serving-active", type=int, default=4)
     p.add_argument("--energies-per-step", type=int, default=0,
@@ -753,21 +754,30 @@ def run_w(args):
     return line
 
 
-def run_serving(args):
-    """Serving stream prefix: Poisson arrivals submitted at their arrival times to bt_server;
-    reports p50 / p99 latency (submit -> done) and aggregate energy points/s."""
+def run_serving(args, as_subline=False):
+    """Serving stream prefix (requests 0 .. n-1 of the 2000-request stream, energy counts as drawn
+    unless --serving-max-energies caps them).  First the plain path: every request solved alone
+    through bt_selinv_solve, one after another (its energies/s is the comparison); then the served
+    stream: Poisson arrivals at 0.8 x the plain path's request rate, submitted at their arrival
+    times to bt_server (work units of one chunk, round robin, concurrent workers).  Reports p50 /
+    p99 latency (submit -> done), aggregate energy points/s of both, and the smallest request's
+    error against the dense oracle on two energies."""
     import numpy as np
     import torch
 
+    import oracle
     import paper_2508_19138_gb300 as pkg
     import synthetic
     from paper_2508_19138_gb300 import BT, BTOut
 
     precision = pkg.BT_SPLIT if args.precision == "split" else pkg.BT_FP64
+    scope = args.split_scope if precision == pkg.BT_SPLIT else 0
+    chunk = args.energies_per_step or 16
+    torch.cuda.empty_cache()
     stream = synthetic.serving_stream(n_requests=args.requests, rate_per_s=1.0)
     reqs = []
     for rq in stream:
-        nE = min(rq.n_energies, args.serving_max_energies)
+        nE = rq.n_energies if args.serving_max_energies <= 0 else min(rq.n_energies, args.serving_max_energies)
         s = synthetic.random_device(rq.seed, rq.nb, rq.bs, nE)
         t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
         H = BT(t(s.H_diag), t(s.H_upper), None, pkg.BT_LAYOUT_BLOCKS, pkg.BT_SYM_HERMITIAN, False)
@@ -776,31 +786,40 @@ def run_serving(args):
         status = torch.full((nE,), -1, dtype=torch.int32, device="cuda")
         reqs.append((rq, s, H, outs, status))
     torch.cuda.synchronize()
+    n_en = sum(len(it[1].energies) for it in reqs)
+
+    # ---- plain path: each request alone, back to back, with the server's chunking ----
+    solve_stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    for rq, s, H, outs, status in reqs:
+        ctx = pkg.bt_selinv_create(pkg.make_desc(s.nb, s.bs, min(chunk, len(s.energies)), precision=precision,
+                                                 split_slices=args.slices, split_scope=scope, eta=s.eta, kT=s.kT,
+                                                 mu_left=s.mu_left, mu_right=s.mu_right), solve_stream)
+        pkg.bt_selinv_solve(ctx, H, None, None, None, None, s.energies, outs[0], outs[1], outs[2], status)
+        solve_stream.synchronize()
+        ctx.close()
+    t_plain = time.perf_counter() - t0
+    plain = {"value": n_en / t_plain, "unit": UNIT, "seconds": t_plain,
+             "what": "each request alone through bt_selinv_solve, one after another"}
+
+    # ---- served stream ----
+    rate = 0.8 * len(reqs) / t_plain
+    rng = np.random.default_rng(synthetic.BASE_SEED + 4)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
     budget = int(args.serving_budget_gb * (1 << 30))
-    srv = pkg.bt_server_create(budget, max_active=args.serving_active, max_energies_per_chunk=args.energies_per_step or 16,
-                               precision=precision, split_slices=args.slices)
+    srv = pkg.bt_server_create(budget, max_active=args.serving_active, max_energies_per_chunk=chunk,
+                               precision=precision, split_slices=args.slices, split_scope=scope)
 
     def submit(item):
         rq, s, H, outs, status = item
         return pkg.bt_server_submit(srv, s.nb, s.bs, H, s.energies, status, outs[0], outs[1], outs[2], eta=s.eta,
                                     kT=s.kT, mu_left=s.mu_left, mu_right=s.mu_right)
 
-    # capacity calibration on the first request alone -> arrival rate 0.8 x capacity
-    t0 = time.perf_counter()
-    pkg.bt_server_wait(srv, submit(reqs[0]), 3600.0)
-    t_first = time.perf_counter() - t0
-    work = lambda it: it[1].nb * it[1].bs ** 3 * len(it[1].energies)
-    rate = 0.8 / (t_first * (np.mean([work(it) for it in reqs]) / work(reqs[0])))
-    rng = np.random.default_rng(synthetic.BASE_SEED + 4)
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs) - 1))
-    pkg.bt_server_destroy(srv)
-    srv = pkg.bt_server_create(budget, max_active=args.serving_active, max_energies_per_chunk=args.energies_per_step or 16,
-                               precision=precision, split_slices=args.slices)
     clocks = ClockSampler(0)
     clocks.start()
     start = time.perf_counter()
     tickets = []
-    for item, ta in zip(reqs[1:], arrivals):
+    for item, ta in zip(reqs, arrivals):
         now = time.perf_counter() - start
         if ta > now:
             time.sleep(ta - now)
@@ -811,19 +830,36 @@ def run_serving(args):
     clk = clocks.stop()
     st = pkg.bt_server_get_stats(srv)
     pkg.bt_server_destroy(srv)
-    bad = sum(int((it[4].cpu().numpy() != 0).sum()) for it in reqs[1:])
-    n_en = sum(len(it[1].energies) for it in reqs[1:])
-    line = {"metric": METRIC, "value": n_en / wall, "unit": UNIT, "n_gpus": 1, "steps": len(tickets), "warmup": 1,
-            "ms_per_step": wall / len(tickets) * 1e3, "higher_is_better": True, "scaling": "weak",
+    torch.cuda.synchronize()
+    bad = sum(int((it[4].cpu().numpy() != 0).sum()) for it in reqs)
+    # the smallest request against the dense oracle (diagonal entries of G^R, G^<, G^>), 2 energies
+    small = min(reqs, key=lambda it: it[1].nb * it[1].bs)
+    rq, s, H, outs, status = small
+    worst = 0.0
+    for e in (0, len(s.energies) - 1):
+        ref = oracle.solve_g(s, e, surface="eig")
+        for o, key in zip(outs, ("XR", "XL", "XG")):
+            got = o.diag[e].cpu().numpy().reshape(-1)
+            want = np.diag(ref[key])
+            worst = max(worst, float(np.linalg.norm(got - want) / np.linalg.norm(want)))
+    cap = "as drawn (32, 128 or 512)" if args.serving_max_energies <= 0 else f"capped at {args.serving_max_energies}"
+    line = {"metric": METRIC, "value": st["energies_per_s"], "unit": UNIT, "n_gpus": 1, "steps": len(tickets),
+            "warmup": 0, "ms_per_step": wall / len(tickets) * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if precision == pkg.BT_FP64 else "f64+bf16-sliced", "data": "synthetic",
-            "config": {"workload": (f"serving stream prefix: requests 1..{len(reqs) - 1} of the 2000-request stream "
-                                    f"(b in 64..832, N_B 8..64), energies per request capped at "
-                                    f"{args.serving_max_energies} (flagged), Poisson arrivals at 0.8x capacity"),
+            "config": {"workload": (f"serving stream: requests 0..{len(reqs) - 1} of the 2000-request stream "
+                                    f"(b in 64..832, N_B 8..64), energies per request {cap}, Poisson arrivals at "
+                                    f"0.8x the plain path's request rate"),
                        "arrival_rate_per_s": rate, "budget_gb": args.serving_budget_gb,
-                       "max_active": args.serving_active, "chunk": args.energies_per_step or 16,
-                       "precision": args.precision},
+                       "max_active": args.serving_active, "chunk": chunk, "precision": args.precision,
+                       "split_scope": scope},
             "latency_s": {"p50": st["p50_latency_s"], "p99": st["p99_latency_s"], "mean": st["mean_latency_s"]},
-            "server": st, "nonzero_status": bad, "clocks": clk}
+            "wall_s": wall, "plain": plain, "served_vs_plain": st["energies_per_s"] / plain["value"],
+            "server": st, "nonzero_status": bad, "clocks": clk,
+            "errors": {"max_diag_rel_err": worst, "tolerance": 1e-10 if precision == pkg.BT_FP64 else 1e-8,
+                       "sample": f"request {rq.rid} (nb {s.nb}, bs {s.bs}), energies first and last, diagonals of "
+                                 f"G^R, G^<, G^> against the dense oracle"}}
+    if as_subline:
+        return line
     print(json.dumps(line), flush=True)
     return 0
 
@@ -888,8 +924,10 @@ def run_conv(args, n_elem=416 * 416, ne=512, steps=5, warmup=3):
 def sublines(args):
     """Lines of the other workloads, measured after the default one (one GPU): the 8 x 32 random
     device (all 64 energies per step; FP64 and both split scopes), the energy convolution of one
-    416 x 416 block over 512 energies, and the W system 16 x 1024 (split, steps of 4 energies),
-    each with its own step counts and errors against the oracle."""
+    416 x 416 block over 512 energies, the serving stream (its first 12 requests, energy counts as
+    drawn, split path with every product sliced, against the plain path on the same requests) and
+    the W system 16 x 1024 (split, steps of 4 energies), each with its own step counts and errors
+    against the oracle."""
     import copy
     out = {}
     a0 = copy.copy(args)
@@ -903,6 +941,12 @@ def sublines(args):
         out["energy_convolution"] = run_conv(args)
     except Exception as exc:
         out["energy_convolution"] = {"unavailable": f"{type(exc).__name__}: {exc}"[:300]}
+    a4 = copy.copy(args)
+    a4.requests, a4.serving_max_energies, a4.precision, a4.split_scope, a4.energies_per_step = 12, 0, "split", 1, 16
+    try:
+        out["serving"] = run_serving(a4, as_subline=True)
+    except Exception as exc:
+        out["serving"] = {"unavailable": f"{type(exc).__name__}: {exc}"[:300]}
     a2 = copy.copy(args)
     a2.workload, a2.energies_per_step, a2.steps, a2.warmup, a2.precision = "w16x1024", 4, 2, 1, "split"
     try:

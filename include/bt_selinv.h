@@ -401,6 +401,12 @@ BT_API bt_status bt_energy_convolve(int n_elem, int na, int nb, int m0, int n_ou
  * ------------------------------------------------------------------------------------- */
 BT_API void bt_debug_split_stall(unsigned long long ns, long long launches);
 
+/* Measurement aid (no counterpart in the paper): the FP64 multiply-add rate of this GPU on
+ * registers only, which = 0 for DFMA (fma.rn.f64), 1 for the FP64 tensor instruction
+ * (mma.sync m8n8k4 f64); one launch of iters iterations after a warm-up launch, timed with CUDA
+ * events on `stream`.  Writes TFLOP/s (2 flops per multiply-add) and the launch time in ms. */
+BT_API bt_status bt_debug_fp64_rate(int which, int iters, double* tflops, double* ms, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -73,6 +73,7 @@ SIGNATURES = {
     "bt_zinv_batched": [_I, _P, _LL, _I, _P, _P, _SZ, _P],
     "bt_zinv_batched_noalloc": [_I, _P, _LL, _I, _P, _P],
     "bt_debug_split_stall": [C.c_ulonglong, C.c_longlong],
+    "bt_debug_fp64_rate": [_I, _I, C.POINTER(_D), C.POINTER(_D), _P],
     "bt_energy_convolve": [_I, _I, _I, _I, _I, _P, _LL, _P, _LL, _P, _LL, _D, _D, _I, _P],
     "bt_decimate_workspace_bytes": [_I, _I, C.POINTER(C.c_size_t)],
     "bt_decimate_batched": [_I, _I, _P, _P, _P, _D, _I, _P, _P, _P, _P, _P, _SZ, _P],

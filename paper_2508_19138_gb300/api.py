@@ -17,7 +17,7 @@ __all__ = [
     "bt_selinv_solve", "bt_selinv_solve_host", "bt_selinv_destroy", "bt_selinv_last_error", "bt_selinv_get_stats",
     "bt_zgemm_batched", "bt_split_zgemm_workspace_bytes", "bt_split_zgemm_batched", "bt_zinv_workspace_bytes",
     "bt_zinv_batched", "bt_zinv_batched_noalloc", "bt_decimate_workspace_bytes", "bt_decimate_batched", "library",
-    "bt_debug_split_stall", "bt_energy_convolve",
+    "bt_debug_split_stall", "bt_debug_fp64_rate", "bt_energy_convolve",
 ]
 
 
@@ -272,6 +272,13 @@ def bt_energy_convolve(n_elem, na, nb, A, lda, B, ldb, C, ldc, scale=1.0, m0=0, 
                                      _ptr(B, torch.complex128), ldb, _ptr(C, torch.complex128), ldc, sc.real, sc.imag,
                                      flags, _stream(stream))
     _check(rc, None, "energy_convolve")
+
+
+def bt_debug_fp64_rate(which: int, iters: int = 4096, stream=None) -> dict:
+    """FP64 multiply-add rate on registers only: which 0 = DFMA, 1 = DMMA (mma.sync m8n8k4 f64)."""
+    t, ms = C.c_double(0.0), C.c_double(0.0)
+    _check(N.load().bt_debug_fp64_rate(which, iters, C.byref(t), C.byref(ms), _stream(stream)), None, "fp64_rate")
+    return {"tflops": t.value, "ms": ms.value}
 
 
 def bt_debug_split_stall(ns: int, launches: int = -1) -> None:

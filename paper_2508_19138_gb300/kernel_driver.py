@@ -6,6 +6,7 @@
     python -m paper_2508_19138_gb300.kernel_driver --kernel cublas --bs 416 --batch 16   # library reference
     python -m paper_2508_19138_gb300.kernel_driver --kernel conv --bs 416 --batch 512    # energy convolution of
         # the bs^2 element series of one diagonal block over `batch` energies (na = nb = batch)
+    python -m paper_2508_19138_gb300.kernel_driver --kernel fp64rate --reps 4   # DFMA vs DMMA (FP64 tensor) rates
 
 Inputs are random complex128 blocks already on the device; each kernel is launched `--reps`
 times on the current stream and its mean time is printed (CUDA events)."""
@@ -20,7 +21,7 @@ def main():
 
     import paper_2508_19138_gb300 as pkg
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kernel", choices=["zgemm", "split", "zinv", "cublas", "conv"], required=True)
+    ap.add_argument("--kernel", choices=["zgemm", "split", "zinv", "cublas", "conv", "fp64rate"], required=True)
     ap.add_argument("--bs", type=int, default=416)
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--reps", type=int, default=3)
@@ -32,6 +33,13 @@ def main():
     pkg.library()
     if a.kernel == "conv":
         return conv_driver(a, pkg)
+    if a.kernel == "fp64rate":
+        out = {"kernel": "fp64rate"}
+        for which, name in ((0, "dfma"), (1, "dmma")):
+            r = pkg.bt_debug_fp64_rate(which, iters=max(1, a.reps) * 4096)
+            out[name + "_tflops"], out[name + "_ms"] = r["tflops"], r["ms"]
+        print(json.dumps(out))
+        return None
     b, n = a.batch, a.bs
     kk = a.k if a.k > 0 and a.kernel != "zinv" else n
     g = torch.Generator(device="cuda").manual_seed(1)
