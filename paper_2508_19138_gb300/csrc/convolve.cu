@@ -41,42 +41,101 @@ struct ConvParams {
   int reverse_b, conj_b;
 };
 
-// in-place radix-2 stages over TS series of length L held as x[t * L + i]
-// forward DIT (bit-reversed input, natural output), twiddle w = tw[r * (L / 2h)]
+__device__ __forceinline__ zd mul_mi(zd a) { return zmake(a.y, -a.x); }  // a * (-i)
+__device__ __forceinline__ zd mul_pi(zd a) { return zmake(-a.y, a.x); }  // a * (+i)
+
+// In-place FFT stages over TS series of length L held as x[t * L + i], two radix-2 stages per
+// pass over the data (each thread takes the four points i0 + {0, h, 2h, 3h}): half the shared-
+// memory round trips and barriers of single stages.  tw[r] = exp(-2 pi i r / L), r < L / 2.
+//
+// Forward, decimation in time (bit-reversed input, natural output), stages s and s + 1 (spans h
+// and 2h), w1 = W_2h^r, w2 = W_4h^r, W_4h^(r+h) = -i w2:
+//   a0 = x0 + w1 x1, a1 = x0 - w1 x1, a2 = x2 + w1 x3, a3 = x2 - w1 x3,
+//   y0 = a0 + w2 a2, y2 = a0 - w2 a2, y1 = a1 - i w2 a3, y3 = a1 + i w2 a3.
+// The first stage pair has w1 = w2 = 1 (no multiplications); an odd stage count starts with one
+// single stage of trivial twiddles.
 __device__ void fft_dit(zd* x, const zd* tw, int L, int log2L, int TS) {
-  const int half = L >> 1;
-  for (int s = 0; s < log2L; ++s) {
-    const int h = 1 << s;
-    const int tstep = half >> s;
+  const int half = L >> 1, quarter = L >> 2;
+  int s = 0;
+  if (log2L & 1) {  // one radix-2 stage with w = 1
     for (int q = threadIdx.x; q < TS * half; q += blockDim.x) {
       const int t = q / half, j = q - t * half;
+      zd* y = x + t * L + 2 * j;
+      const zd u = y[0], v = y[1];
+      y[0] = zadd(u, v);
+      y[1] = zsub(u, v);
+    }
+    __syncthreads();
+    s = 1;
+  }
+  for (; s + 1 < log2L; s += 2) {
+    const int h = 1 << s;
+    const int t1 = half >> s, t2 = half >> (s + 1);
+    for (int q = threadIdx.x; q < TS * quarter; q += blockDim.x) {
+      const int t = q / quarter, j = q - t * quarter;
       const int g = j >> s, r = j & (h - 1);
-      zd* y = x + t * L;
-      const int i0 = (g << (s + 1)) + r, i1 = i0 + h;
-      const zd w = tw[r * tstep];
-      const zd u = y[i0], v = zmul(y[i1], w);
-      y[i0] = zadd(u, v);
-      y[i1] = zsub(u, v);
+      zd* y = x + t * L + (g << (s + 2)) + r;
+      const zd x0 = y[0], x1 = y[h], x2 = y[2 * h], x3 = y[3 * h];
+      zd a0, a1, a2, a3, b2, b3;
+      if (s == 0) {
+        a0 = zadd(x0, x1); a1 = zsub(x0, x1); a2 = zadd(x2, x3); a3 = zsub(x2, x3);
+        b2 = a2; b3 = mul_mi(a3);
+      } else {
+        const zd w1 = tw[r * t1], w2 = tw[r * t2];
+        const zd v1 = zmul(x1, w1), v3 = zmul(x3, w1);
+        a0 = zadd(x0, v1); a1 = zsub(x0, v1); a2 = zadd(x2, v3); a3 = zsub(x2, v3);
+        b2 = zmul(a2, w2); b3 = mul_mi(zmul(a3, w2));
+      }
+      y[0] = zadd(a0, b2);
+      y[2 * h] = zsub(a0, b2);
+      y[h] = zadd(a1, b3);
+      y[3 * h] = zsub(a1, b3);
     }
     __syncthreads();
   }
 }
 
-// inverse DIF (natural input, bit-reversed output) with conjugate twiddles
+// Inverse, decimation in frequency (natural input, bit-reversed output), conjugate twiddles,
+// stages s + 1 then s:
+//   a0 = x0 + x2, a2 = (x0 - x2) conj(w2), a1 = x1 + x3, a3 = (x1 - x3) conj(w2) i,
+//   y0 = a0 + a1, y1 = (a0 - a1) conj(w1), y2 = a2 + a3, y3 = (a2 - a3) conj(w1).
+// The last stage pair has w1 = w2 = 1; an odd stage count ends with one single stage of w = 1.
 __device__ void ifft_dif(zd* x, const zd* tw, int L, int log2L, int TS) {
-  const int half = L >> 1;
-  for (int s = log2L - 1; s >= 0; --s) {
+  const int half = L >> 1, quarter = L >> 2;
+  for (int s = log2L - 2; s >= (log2L & 1); s -= 2) {
     const int h = 1 << s;
-    const int tstep = half >> s;
+    const int t1 = half >> s, t2 = half >> (s + 1);
+    for (int q = threadIdx.x; q < TS * quarter; q += blockDim.x) {
+      const int t = q / quarter, j = q - t * quarter;
+      const int g = j >> s, r = j & (h - 1);
+      zd* y = x + t * L + (g << (s + 2)) + r;
+      const zd x0 = y[0], x1 = y[h], x2 = y[2 * h], x3 = y[3 * h];
+      const zd a0 = zadd(x0, x2), a1 = zadd(x1, x3);
+      zd a2 = zsub(x0, x2), a3 = mul_pi(zsub(x1, x3));
+      zd y1 = zsub(a0, a1), y3;
+      if (s == 0) {
+        y3 = zsub(a2, a3);
+      } else {
+        const zd w1 = zconj(tw[r * t1]), w2 = zconj(tw[r * t2]);
+        a2 = zmul(a2, w2);
+        a3 = zmul(a3, w2);
+        y1 = zmul(y1, w1);
+        y3 = zmul(zsub(a2, a3), w1);
+      }
+      y[0] = zadd(a0, a1);
+      y[h] = y1;
+      y[2 * h] = zadd(a2, a3);
+      y[3 * h] = y3;
+    }
+    __syncthreads();
+  }
+  if (log2L & 1) {  // the last radix-2 stage, w = 1
     for (int q = threadIdx.x; q < TS * half; q += blockDim.x) {
       const int t = q / half, j = q - t * half;
-      const int g = j >> s, r = j & (h - 1);
-      zd* y = x + t * L;
-      const int i0 = (g << (s + 1)) + r, i1 = i0 + h;
-      const zd w = zconj(tw[r * tstep]);
-      const zd u = y[i0], v = y[i1];
-      y[i0] = zadd(u, v);
-      y[i1] = zmul(zsub(u, v), w);
+      zd* y = x + t * L + 2 * j;
+      const zd u = y[0], v = y[1];
+      y[0] = zadd(u, v);
+      y[1] = zsub(u, v);
     }
     __syncthreads();
   }
