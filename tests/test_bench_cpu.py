@@ -64,3 +64,25 @@ def test_reference_arm_other_ranks_exit_quietly():
     r = run_bench("--impl", "reference", "--workload", "random8x32", "--steps", "1", "--warmup", "0",
                   env={"RANK": "1"})
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_result_errors_of_the_small_workload():
+    """The per-path error field: oracle blocks fed back as a snapshot give ~0; a planted error of
+    1e-6 in one block of one path shows up as that path's error and only there."""
+    import numpy as np
+
+    import oracle
+    import synthetic
+    s = synthetic.random_device(3, 3, 8, 4)
+    eps = 4
+    perm = np.arange(4)
+    refs = [oracle.solve_g(s, e, surface="eig") for e in range(eps)]
+    keys = ("R_diag", "R_upper", "R_lower", "L_diag", "L_upper", "G_diag", "G_upper")
+    snap = {k: np.stack([r[k] for r in refs]) for k in keys}
+    bad = {k: v.copy() for k, v in snap.items()}
+    blk = bad["R_upper"][2, 1]
+    bad["R_upper"][2, 1] = blk + 1e-6 * np.linalg.norm(blk) / np.sqrt(blk.size)
+    out = bench.result_errors(None, {"fp64": snap, "split_scope0": bad}, None, s, perm, 0, eps, tuple(range(s.nb)))
+    assert out["fp64"] <= 1e-14
+    assert 0.5e-6 <= out["split_scope0"] <= 2e-6
+    assert out["tolerance"] == {"fp64": 1e-10, "split": 1e-8}
