@@ -838,10 +838,14 @@ def run_serving(args, as_subline=False):
     worst = 0.0
     for e in (0, len(s.energies) - 1):
         ref = oracle.solve_g(s, e, surface="eig")
+        # lesser / greater: the absolute allowance of the parity tests, 0.01 |X^R|^2 |B^R_OBC|
+        xr = max(np.linalg.norm(b) for b in ref["R_diag"])
+        floor = 0.01 * xr * xr * max(np.linalg.norm(ref["info"]["R_L"]), np.linalg.norm(ref["info"]["R_R"]))
         for o, key in zip(outs, ("XR", "XL", "XG")):
             got = o.diag[e].cpu().numpy().reshape(-1)
             want = np.diag(ref[key])
-            worst = max(worst, float(np.linalg.norm(got - want) / np.linalg.norm(want)))
+            den = max(float(np.linalg.norm(want)), floor if key != "XR" else 0.0, 1e-300)
+            worst = max(worst, float(np.linalg.norm(got - want)) / den)
     cap = "as drawn (32, 128 or 512)" if args.serving_max_energies <= 0 else f"capped at {args.serving_max_energies}"
     line = {"metric": METRIC, "value": st["energies_per_s"], "unit": UNIT, "n_gpus": 1, "steps": len(tickets),
             "warmup": 0, "ms_per_step": wall / len(tickets) * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -857,7 +861,8 @@ def run_serving(args, as_subline=False):
             "server": st, "nonzero_status": bad, "clocks": clk,
             "errors": {"max_diag_rel_err": worst, "tolerance": 1e-10 if precision == pkg.BT_FP64 else 1e-8,
                        "sample": f"request {rq.rid} (nb {s.nb}, bs {s.bs}), energies first and last, diagonals of "
-                                 f"G^R, G^<, G^> against the dense oracle"}}
+                                 f"G^R, G^<, G^> against the dense oracle (lesser / greater with the "
+                                 f"parity tests' absolute allowance)"}}
     if as_subline:
         return line
     print(json.dumps(line), flush=True)
@@ -924,8 +929,9 @@ def run_conv(args, n_elem=416 * 416, ne=512, steps=5, warmup=3):
 def sublines(args):
     """Lines of the other workloads, measured after the default one (one GPU): the 8 x 32 random
     device (all 64 energies per step; FP64 and both split scopes), the energy convolution of one
-    416 x 416 block over 512 energies, the serving stream (its first 12 requests, energy counts as
-    drawn, split path with every product sliced, against the plain path on the same requests) and
+    416 x 416 block over 512 energies, the serving stream (its first 12 requests, energy counts
+    capped at 32, split path with every product sliced, against the plain path on the same
+    requests) and
     the W system 16 x 1024 (split, steps of 4 energies), each with its own step counts and errors
     against the oracle."""
     import copy
@@ -942,7 +948,9 @@ def sublines(args):
     except Exception as exc:
         out["energy_convolution"] = {"unavailable": f"{type(exc).__name__}: {exc}"[:300]}
     a4 = copy.copy(args)
-    a4.requests, a4.serving_max_energies, a4.precision, a4.split_scope, a4.energies_per_step = 12, 0, "split", 1, 16
+    # a bounded prefix (the energy counts are capped, which the line's config says): the default
+    # run must stay within minutes; `--workload serving` runs the stream with the drawn counts
+    a4.requests, a4.serving_max_energies, a4.precision, a4.split_scope, a4.energies_per_step = 12, 32, "split", 1, 16
     try:
         out["serving"] = run_serving(a4, as_subline=True)
     except Exception as exc:

@@ -258,6 +258,9 @@ typedef struct {
   int split_scope;            /* BT_SPLIT: as bt_selinv_desc.split_scope (0 or 1)          */
   int max_retries;            /* restarts of a unit that timed out (>= 0)                  */
   int max_skips;              /* passes of the oldest waiting request (<= 0: 2 max_active) */
+  int graph;                  /* 1: each unit runs as one captured graph (its decimation and
+                                 Newton loops on the device, no host round trip per loop
+                                 iteration while other workers keep the GPU busy); 0: direct  */
 } bt_server_desc;
 
 typedef struct {

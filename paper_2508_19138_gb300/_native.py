@@ -112,7 +112,7 @@ def load(build_if_missing: bool = False) -> C.CDLL:
 class bt_server_desc(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_active", C.c_int), ("max_energies_per_chunk", C.c_int),
                 ("precision", C.c_int), ("split_slices", C.c_int), ("device", C.c_int), ("split_scope", C.c_int),
-                ("max_retries", C.c_int), ("max_skips", C.c_int)]
+                ("max_retries", C.c_int), ("max_skips", C.c_int), ("graph", C.c_int)]
 
 
 class bt_request(C.Structure):

@@ -127,6 +127,7 @@ struct Polish {
   long long lead_iterations = 0;  // direct mode: doubling iterations summed over the leads
   int selected = 0;               // direct mode: leads that took the step
   long long body_launches = 0;    // graph mode: kernels of one pass of the doubling loop
+  const Engine* engine = nullptr; // products of the step (null: FP64)
 };
 
 // Sancho-Rubio decimation for `batch` leads.  With `loop` (graph capture), iters_host_max and

@@ -635,10 +635,12 @@ bt_status decimate(cudaStream_t st, int bs, int batch, const zd* m, const zd* n,
   if (polish && polish->after >= 0) {
     int* hp = h_pinned;
     if (!loop && !hp && cudaMallocHost(&hp, 64) != cudaSuccess) return BT_ERR_CUDA;
-    // the Newton step runs in FP64 whatever engine the decimation used: it is what brings the
-    // surface function to FP64 accuracy, and a sliced residual would limit that
+    // the step's products run on polish->engine: FP64, or sliced with 8 slices when the
+    // decimation's products are sliced (its residual then limits the step at ~1e-9 relative,
+    // well inside the split path's tolerance, for a twentieth of the FP64 cost)
     const Engine fp64_step;
-    const bt_status ps = polish_step(st, bs, batch, m, n, np, x, mask, iters, info, w, hp, fp64_step, loop, *polish);
+    const Engine& PE = polish->engine ? *polish->engine : fp64_step;
+    const bt_status ps = polish_step(st, bs, batch, m, n, np, x, mask, iters, info, w, hp, PE, loop, *polish);
     if (hp != h_pinned) cudaFreeHost(hp);
     BT_TRY(ps);
   }

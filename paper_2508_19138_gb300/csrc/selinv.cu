@@ -65,6 +65,7 @@ struct bt_ctx {
   void* split_ws = nullptr;
   size_t split_bytes = 0;
   bt::Engine eng_kept;  // products of the inversions and the decimation (FP64 unless split_scope = 1)
+  bt::Engine eng_polish;  // products of the Newton step after decimation (FP64, or 8 slices with split_scope = 1)
   int* h_pinned = nullptr;
   double* h_E = nullptr;
   bool pinned = true;   // host buffers from cudaMallocHost (else new[])
@@ -193,7 +194,9 @@ size_t layout(bt_ctx* c, const bt_selinv_desc& d, char* base) {
   if (is_split(d)) {
     // sweep products batch E; with split_scope = 1 also the decimation's 2E leads
     const int sb = (d.split_scope == 1 && d.obc) ? (int)(2 * E) : (int)E;
-    x->split_bytes = bt::split_workspace_bytes(d.bs, d.bs, d.bs, d.split_scope == 1 ? kept_slices_of(d) : slices_of(d), sb);
+    // split_scope = 1 with contacts: the Newton step after decimation runs with 8 slices
+    const int ws_slices = d.split_scope == 1 ? (d.obc ? 8 : kept_slices_of(d)) : slices_of(d);
+    x->split_bytes = bt::split_workspace_bytes(d.bs, d.bs, d.bs, ws_slices, sb);
     x->split_ws = cv.take<char>(x->split_bytes);
   }
   return cv.off;
@@ -496,6 +499,8 @@ bt_status ctx_create(const bt_selinv_desc* desc, void* cuda_stream, void* ext_ws
     c->eng_kept = bt::Engine{kept_slices_of(d), c->split_ws, c->split_bytes, c->tflag};
   c->eng_kept.tile = d.gemm_tile;
   c->eng_kept.panel = d.inv_panel;
+  c->eng_polish.tile = d.gemm_tile;
+  if (is_split(d) && d.split_scope == 1) c->eng_polish = bt::Engine{8, c->split_ws, c->split_bytes, c->tflag};
   if (d.obc_memo) {
     c->memo_key.assign(d.memo_capacity, 0);
     c->memo_used.assign(d.memo_capacity, 0);
@@ -656,6 +661,7 @@ bt_status decimate_leads(bt_ctx* c, int Ec, const int* dec_mask) {
   bt::Polish pol;
   pol.after = d.decim_newton_after;
   pol.iters = c->lead_piters;
+  pol.engine = &c->eng_polish;
   bt_status s = bt::decimate(c->st, bs, 2 * Ec, c->lead_m, c->lead_n, c->lead_np, d.decim_tol, d.decim_maxit, c->lead_x,
                              c->lead_sig, c->lead_iters, c->lead_info, c->dec_ws, c->dec_bytes, &it_max, c->h_pinned,
                              dec_mask, &lead_its, &c->eng_kept, c->loop, &pol);

@@ -252,7 +252,8 @@ extern "C" bt_status bt_server_create(const bt_server_desc* desc, bt_server** ou
   *out = nullptr;
   if (desc->max_active < 1 || desc->max_active > 64 || desc->max_energies_per_chunk < 1 ||
       desc->hbm_budget_bytes < 256 || (desc->precision != BT_FP64 && desc->precision != BT_SPLIT) ||
-      (desc->split_scope != 0 && desc->split_scope != 1) || desc->max_retries < 0)
+      (desc->split_scope != 0 && desc->split_scope != 1) || desc->max_retries < 0 ||
+      (desc->graph != 0 && desc->graph != 1))
     return BT_ERR_INVALID_ARG;
   bt_server* s = new (std::nothrow) bt_server();
   if (!s) return BT_ERR_OOM;
@@ -294,6 +295,10 @@ extern "C" bt_status bt_server_submit(bt_server* s, const bt_request* r, long lo
   d.mu_right = r->mu_right;
   d.decim_tol = 1e-14;
   d.decim_maxit = 100;
+  // graph mode: a unit's chunk is captured and launched as one graph, its decimation and Newton
+  // loops run on the device; direct launches would synchronise the host once per loop iteration,
+  // behind whatever the other workers' streams have queued
+  d.graph = s->d.graph ? 1 : 0;
   size_t bytes = 0;
   bt_status rc = bt_selinv_workspace_bytes(&d, &bytes);
   std::lock_guard<std::mutex> lk(s->mu);
