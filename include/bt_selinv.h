@@ -278,7 +278,8 @@ typedef struct {
   long long submitted, completed, failed, rejected, energies_done, queued;
   int active, peak_active;
   double p50_latency_s, p99_latency_s, mean_latency_s; /* submit -> completion, completed  */
-  double busy_seconds;        /* first admission to last completion                        */
+  double busy_seconds;        /* time with at least one work unit running (idle gaps       */
+                              /* between arrivals excluded)                                */
   double energies_per_s;      /* energies_done / busy_seconds                              */
   size_t peak_bytes;          /* largest arena occupancy                                   */
   long long units_done;       /* work units (energy chunks) completed                      */
@@ -409,6 +410,13 @@ BT_API void bt_debug_split_stall(unsigned long long ns, long long launches);
  * (mma.sync m8n8k4 f64); one launch of iters iterations after a warm-up launch, timed with CUDA
  * events on `stream`.  Writes TFLOP/s (2 flops per multiply-add) and the launch time in ms. */
 BT_API bt_status bt_debug_fp64_rate(int which, int iters, double* tflops, double* ms, void* stream);
+
+/* Measurement aid (no counterpart in the paper): forces the cluster size of the Gauss-Jordan
+ * panel kernel of the blocked inverse (n >= 192) to cl = 2, 4 or 8 CTAs per matrix; any other
+ * value restores the default (the largest cluster for which the whole batch is resident at
+ * once, by the occupancy the device reports).  Process-wide, read when a launch is issued (a
+ * captured graph keeps the size it was captured with).  Results do not depend on it. */
+BT_API void bt_debug_panel_cluster(int cl);
 
 #ifdef __cplusplus
 }

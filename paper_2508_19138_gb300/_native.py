@@ -74,11 +74,12 @@ SIGNATURES = {
     "bt_zinv_batched_noalloc": [_I, _P, _LL, _I, _P, _P],
     "bt_debug_split_stall": [C.c_ulonglong, C.c_longlong],
     "bt_debug_fp64_rate": [_I, _I, C.POINTER(_D), C.POINTER(_D), _P],
+    "bt_debug_panel_cluster": [_I],
     "bt_energy_convolve": [_I, _I, _I, _I, _I, _P, _LL, _P, _LL, _P, _LL, _D, _D, _I, _P],
     "bt_decimate_workspace_bytes": [_I, _I, C.POINTER(C.c_size_t)],
     "bt_decimate_batched": [_I, _I, _P, _P, _P, _D, _I, _P, _P, _P, _P, _P, _SZ, _P],
 }
-RESTYPES = {"bt_selinv_last_error": C.c_char_p, "bt_debug_split_stall": None}
+RESTYPES = {"bt_selinv_last_error": C.c_char_p, "bt_debug_split_stall": None, "bt_debug_panel_cluster": None}
 
 _lib = None
 

@@ -17,7 +17,7 @@ __all__ = [
     "bt_selinv_solve", "bt_selinv_solve_host", "bt_selinv_destroy", "bt_selinv_last_error", "bt_selinv_get_stats",
     "bt_zgemm_batched", "bt_split_zgemm_workspace_bytes", "bt_split_zgemm_batched", "bt_zinv_workspace_bytes",
     "bt_zinv_batched", "bt_zinv_batched_noalloc", "bt_decimate_workspace_bytes", "bt_decimate_batched", "library",
-    "bt_debug_split_stall", "bt_debug_fp64_rate", "bt_energy_convolve",
+    "bt_debug_split_stall", "bt_debug_fp64_rate", "bt_debug_panel_cluster", "bt_energy_convolve",
 ]
 
 
@@ -279,6 +279,11 @@ def bt_debug_fp64_rate(which: int, iters: int = 4096, stream=None) -> dict:
     t, ms = C.c_double(0.0), C.c_double(0.0)
     _check(N.load().bt_debug_fp64_rate(which, iters, C.byref(t), C.byref(ms), _stream(stream)), None, "fp64_rate")
     return {"tflops": t.value, "ms": ms.value}
+
+
+def bt_debug_panel_cluster(cl: int) -> None:
+    """Measurement aid: force the Gauss-Jordan panel cluster size (2, 4 or 8; 0 = default)."""
+    N.load().bt_debug_panel_cluster(int(cl))
 
 
 def bt_debug_split_stall(ns: int, launches: int = -1) -> None:

@@ -105,6 +105,8 @@ struct bt_server {
   std::vector<double> latencies;
   bool have_start = false;
   Clock::time_point t_first_start, t_last_done;
+  double busy_acc = 0.0;          // closed intervals with active > 0
+  Clock::time_point busy_since;   // start of the open interval (active > 0)
 };
 
 namespace {
@@ -203,6 +205,7 @@ void worker_main(bt_server* s) {
       if (!s->have_start) { s->have_start = true; s->t_first_start = Clock::now(); }
       s->used += q->bytes;
       s->peak_used = std::max(s->peak_used, s->used);
+      if (s->active == 0) s->busy_since = Clock::now();
       ++s->active;
       s->peak_active = std::max(s->peak_active, s->active);
     }
@@ -211,7 +214,7 @@ void worker_main(bt_server* s) {
       std::lock_guard<std::mutex> lk(s->mu);
       s->arena.release(off, q->bytes);
       s->used -= q->bytes;
-      --s->active;
+      if (--s->active == 0) s->busy_acc += std::chrono::duration<double>(Clock::now() - s->busy_since).count();
       --q->running;
       if (rc == BT_ERR_TIMEOUT && q->tries[u] <= s->d.max_retries && !q->dead) {
         q->redo.push_front(u);  // the watchdog starts the unit again
@@ -362,9 +365,8 @@ extern "C" bt_status bt_server_get_stats(bt_server* s, bt_server_stats* out) {
   double sum = 0.0;
   for (double x : s->latencies) sum += x;
   st.mean_latency_s = s->latencies.empty() ? 0.0 : sum / (double)s->latencies.size();
-  st.busy_seconds = s->have_start && s->completed + s->failed > 0
-                        ? std::chrono::duration<double>(s->t_last_done - s->t_first_start).count()
-                        : 0.0;
+  st.busy_seconds = s->busy_acc + (s->active > 0 ? std::chrono::duration<double>(Clock::now() - s->busy_since).count()
+                                                   : 0.0);
   st.energies_per_s = st.busy_seconds > 0 ? (double)s->energies_done / st.busy_seconds : 0.0;
   st.peak_bytes = s->peak_used;
   st.peak_active = s->peak_active;

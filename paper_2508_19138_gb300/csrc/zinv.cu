@@ -17,7 +17,10 @@
 //    the GEMM kernels.
 #include <cooperative_groups.h>
 
+#include <atomic>
+#include <map>
 #include <mutex>
+#include <utility>
 
 #include "bt_common.cuh"
 
@@ -528,6 +531,51 @@ bt_status set_smem_limits() {
   return BT_OK;
 }
 
+// Cluster size of the panel kernel (2, 4 or 8 CTAs per matrix): the largest for which every
+// matrix of the batch gets its cluster at once, by the occupancy the hardware reports for that
+// cluster size and shared-memory size (the panel CTAs are small, so two clusters can share SMs:
+// 32 matrices run 8-CTA clusters at two CTAs per SM instead of 4-CTA clusters at one).
+// A test / measurement override (bt_debug_panel_cluster) forces a size.
+std::atomic<int> g_panel_cluster{0};
+
+template <int CL>
+int max_active_clusters(int n, int kb, int batch) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, int> cache;  // (device, shared bytes) -> clusters
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  const int smem = (int)cluster_panel_smem(n, kb, CL);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find({dev, smem});
+  if (it != cache.end()) return it->second;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(batch * CL));
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nc = 0;
+  if (cudaOccupancyMaxActiveClusters(&nc, gj_panel_cluster_kernel<CL>, &cfg) != cudaSuccess) {
+    (void)cudaGetLastError();
+    nc = 0;
+  }
+  cache[{dev, smem}] = nc;
+  return nc;
+}
+
+int panel_cluster_size(int n, int kb, int batch) {
+  const int forced = g_panel_cluster.load();
+  if (forced == 2 || forced == 4 || forced == 8) return forced;
+  if (max_active_clusters<8>(n, kb, batch) >= batch) return 8;
+  if (max_active_clusters<4>(n, kb, batch) >= batch) return 4;
+  return 2;
+}
+
 }  // namespace
 
 size_t zinv_workspace_bytes(int n, int batch, bool wide) {
@@ -568,17 +616,14 @@ bt_status zinv(cudaStream_t st, int n, zd* A, long long sA, int batch, int* info
   const bool clustered = n >= kClusterMinN;
   int cl = kPanelCluster;
   if (clustered) {
-    int sms = 0, dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      return BT_ERR_CUDA;
-    while (cl > 2 && (long long)batch * cl > sms) cl >>= 1;
+    cl = panel_cluster_size(n, kb, batch);
     if (cluster_panel_smem(n, kb, cl) > kSmemLimit - 1024) return BT_ERR_UNSUPPORTED;
   }
   for (int k0 = 0; k0 < n; k0 += kb) {
     const int w = (n - k0) < kb ? (n - k0) : kb;
     if (clustered) {
       // one cluster of cl CTAs per matrix (rows of the panel split across SMs): the largest
-      // cluster for which every matrix of the batch gets its own SMs at once
+      // cluster for which every matrix of the batch is resident at once
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3((unsigned)(batch * cl));
       cfg.blockDim = dim3(NT);
@@ -621,6 +666,8 @@ bt_status zinv(cudaStream_t st, int n, zd* A, long long sA, int batch, int* info
 }
 
 }  // namespace bt
+
+extern "C" void bt_debug_panel_cluster(int cl) { bt::g_panel_cluster.store(cl); }
 
 extern "C" bt_status bt_zinv_workspace_bytes(int n, int batch, size_t* bytes) {
   if (!bytes || n < 0 || batch < 0) return BT_ERR_INVALID_ARG;

@@ -7,6 +7,9 @@
     python -m paper_2508_19138_gb300.kernel_driver --kernel conv --bs 416 --batch 512    # energy convolution of
         # the bs^2 element series of one diagonal block over `batch` energies (na = nb = batch)
     python -m paper_2508_19138_gb300.kernel_driver --kernel fp64rate --reps 4   # DFMA vs DMMA (FP64 tensor) rates
+    python -m paper_2508_19138_gb300.kernel_driver --kernel steptrace --precision split --split-scope 1 --batch 32
+        # launch list of one solve step of the 40 x 416 nanoribbon (`batch` energies) from the
+        # CUPTI activity records of the PyTorch profiler: kernels, launches, device time, share
 
 Inputs are random complex128 blocks already on the device; each kernel is launched `--reps`
 times on the current stream and its mean time is printed (CUDA events)."""
@@ -21,18 +24,29 @@ def main():
 
     import paper_2508_19138_gb300 as pkg
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kernel", choices=["zgemm", "split", "zinv", "cublas", "conv", "fp64rate"], required=True)
+    ap.add_argument("--kernel", choices=["zgemm", "split", "zinv", "cublas", "conv", "fp64rate", "steptrace"],
+                    required=True)
     ap.add_argument("--bs", type=int, default=416)
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--slices", type=int, default=6)
     ap.add_argument("--k", type=int, default=0, help="inner dimension of the products (default: --bs)")
+    ap.add_argument("--precision", choices=["fp64", "split"], default="split", help="steptrace: solve precision")
+    ap.add_argument("--split-scope", type=int, default=1, help="steptrace: split scope")
+    ap.add_argument("--graph", choices=["on", "off"], default="on", help="steptrace: graph mode")
+    ap.add_argument("--warmup", type=int, default=2, help="steptrace: untraced steps first")
+    ap.add_argument("--panel-cluster", type=int, default=0,
+                    help="zinv: force the panel cluster size (2, 4 or 8; 0 = default rule)")
     a = ap.parse_args()
     if a.kernel == "cublas":
         return cublas_reference(a)
     pkg.library()
+    if a.panel_cluster:
+        pkg.bt_debug_panel_cluster(a.panel_cluster)
     if a.kernel == "conv":
         return conv_driver(a, pkg)
+    if a.kernel == "steptrace":
+        return step_trace(a, pkg)
     if a.kernel == "fp64rate":
         out = {"kernel": "fp64rate"}
         for which, name in ((0, "dfma"), (1, "dmma")):
@@ -76,7 +90,8 @@ def main():
     ms = e0.elapsed_time(e1) / a.reps
     flops = 8.0 * n * n * kk * b
     print(json.dumps({"kernel": a.kernel, "bs": n, "k": kk, "batch": b, "ms": ms, "fp64_eq_tflops": flops / ms / 1e9,
-                      "slices": a.slices if a.kernel == "split" else None}))
+                      "slices": a.slices if a.kernel == "split" else None,
+                      "panel_cluster": a.panel_cluster if a.kernel == "zinv" else None}))
 
 
 def conv_flops(L):
@@ -112,6 +127,94 @@ def conv_driver(a, pkg):
     moved = 16.0 * n_elem * (ne + ne + 2 * ne - 1)
     print(json.dumps({"kernel": "conv", "series": n_elem, "energies": ne, "L": L, "ms": ms,
                       "fp64_tflops": flops / ms / 1e9, "hbm_gbs": moved / ms / 1e6}))
+
+
+def _short_name(name: str) -> str:
+    """Kernel name without its argument list and namespaces (template arguments kept)."""
+    name = name.replace("(anonymous namespace)::", "").replace("<unnamed>::", "")
+    depth, cut = 0, len(name)
+    for i, ch in enumerate(name):  # the argument list: the first '(' outside template brackets
+        if ch == "<":
+            depth += 1
+        elif ch == ">":
+            depth -= 1
+        elif ch == "(" and depth == 0 and i > 0:
+            cut = i
+            break
+    head = name[:cut]
+    if head.startswith("void "):
+        head = head[5:]
+    base, _, targs = head.partition("<")
+    base = base.split("::")[-1]
+    return (base + ("<" + targs if targs else "")).strip()
+
+
+def step_trace(a, pkg):
+    """One solve step of the 40 x 416 nanoribbon G system (a.batch energies strided across the
+    512-energy grid, as the bench steps) after a.warmup untraced steps: the step's kernels from
+    the CUPTI activity records the PyTorch profiler collects (device start / end of every
+    kernel, graph-launched ones included), aggregated per kernel; plus the step's time without
+    the profiler (CUDA events)."""
+    import numpy as np
+    import torch
+
+    import synthetic
+    from paper_2508_19138_gb300.highlevel import GSolver
+    sysg = synthetic.nanoribbon_40x416()
+    nE, eps = len(sysg.energies), a.batch
+    nbat = max(1, nE // eps)
+    perm = (np.arange(nbat)[:, None] + nbat * np.arange(eps)[None, :]).ravel()
+    sysg = sysg.subset(perm)
+    precision = pkg.BT_SPLIT if a.precision == "split" else pkg.BT_FP64
+    stream = torch.cuda.Stream()
+    solver = GSolver(sysg.nb, sysg.bs, eps, sysg.eta, sysg.kT, sysg.mu_left, sysg.mu_right, obc=True,
+                     precision=precision, split_slices=a.slices, stream=stream, split_scope=a.split_scope,
+                     graph=a.graph == "on")
+    with torch.cuda.stream(stream):
+        solver.set_inputs(sysg.H_diag, sysg.H_upper, sysg.sigR_diag, sysg.sigL_diag, sysg.sigG_diag)
+        outs, status = solver.allocate_outputs(eps)
+    torch.cuda.synchronize()
+
+    def step(j):
+        e0 = (j % nbat) * eps
+        solver.solve(sysg.energies[e0:e0 + eps], outs, status, sig_range=(e0, e0 + eps))
+
+    for j in range(a.warmup):
+        step(j)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    step(a.warmup)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = ev0.elapsed_time(ev1)
+    from torch.autograd import DeviceType
+    from torch.profiler import ProfilerActivity, profile
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        step(a.warmup + 1)
+        torch.cuda.synchronize()
+    agg = {}
+    first, last = None, None
+    for e in prof.events():
+        if e.device_type != DeviceType.CUDA:
+            continue
+        t0, t1 = e.time_range.start, e.time_range.end
+        first = t0 if first is None else min(first, t0)
+        last = t1 if last is None else max(last, t1)
+        k = _short_name(e.name)
+        n, us = agg.get(k, (0, 0.0))
+        agg[k] = (n + 1, us + (t1 - t0))
+    total = sum(us for _, us in agg.values())
+    rows = sorted(agg.items(), key=lambda kv: -kv[1][1])
+    print(json.dumps({"kernel": "steptrace", "workload": f"nanoribbon G 40x416, {eps} energies per step",
+                      "precision": a.precision, "split_scope": a.split_scope if a.precision == "split" else None,
+                      "graph": a.graph, "step_ms_plain": plain_ms, "traced_span_ms": (last - first) / 1e3 if rows else 0,
+                      "device_ms": total / 1e3, "launches": sum(n for n, _ in agg.values()),
+                      "kernels": [{"name": k, "launches": n, "ms": us / 1e3, "share": us / total if total else 0}
+                                  for k, (n, us) in rows]}))
+    status_bad = int((status != 0).sum().item())
+    if status_bad:
+        raise SystemExit(f"{status_bad} energies with a non-zero status")
 
 
 def cublas_reference(a):
