@@ -58,7 +58,7 @@ def parse():
                    help="serving: cap on the energies per request (0: as drawn; a cap is flagged in the config)")
     p.add_argument("--serving-budget-gb", type=float, default=150.0)
     p.add_argument("--serving-active", type=int, default=4)
-    p.add_argument("--serving-graph", choices=["on", "off"], default="on",
+    p.add_argument("--serving-graph", choices=["on", "off"], default="off",
                    help="serving: work units as captured graphs (on) or direct launches (off)")
     p.add_argument("--energies-per-step", type=int, default=0,
                    help="energies per solve (0: 32 for the nanoribbon, the chunk the autotuner picks on GB300; "

@@ -260,7 +260,9 @@ typedef struct {
   int max_skips;              /* passes of the oldest waiting request (<= 0: 2 max_active) */
   int graph;                  /* 1: each unit runs as one captured graph (its decimation and
                                  Newton loops on the device, no host round trip per loop
-                                 iteration while other workers keep the GPU busy); 0: direct  */
+                                 iteration); 0: direct launches.  A unit's graph is captured
+                                 for one launch, so its capture cost is not amortised: direct
+                                 launches serve the mixed request stream faster (measured)    */
 } bt_server_desc;
 
 typedef struct {
@@ -417,6 +419,17 @@ BT_API bt_status bt_debug_fp64_rate(int which, int iters, double* tflops, double
  * once, by the occupancy the device reports).  Process-wide, read when a launch is issued (a
  * captured graph keeps the size it was captured with).  Results do not depend on it. */
 BT_API void bt_debug_panel_cluster(int cl);
+
+/* Measurement aid (no counterpart in the paper): enable = 1 zeroes a set of device counters that
+ * every later launch of the tensor-core GEMM of bt_split_zgemm_batched (and of the BT_SPLIT
+ * solves) adds to; enable = 0 stops counting, synchronizes the device and copies up to
+ * n_counters of them to host memory `counters`:
+ *   [0] SM cycles the MMA-issuing thread waited for a pipeline stage's TMA data,
+ *   [1] ... waited for an accumulator the epilogue had not drained yet,
+ *   [2] ... spent in its whole loop, [3] cycles the TMA-issuing thread waited for a free stage,
+ *   [4] cycles epilogue warp 0 spent draining accumulators, [5] ... writing C, [6] tiles,
+ * each summed over all CTAs.  Off by default; a launch reads the setting when issued. */
+BT_API bt_status bt_debug_split_profile(int enable, unsigned long long* counters, int n_counters);
 
 #ifdef __cplusplus
 }

@@ -17,7 +17,7 @@ __all__ = [
     "bt_selinv_solve", "bt_selinv_solve_host", "bt_selinv_destroy", "bt_selinv_last_error", "bt_selinv_get_stats",
     "bt_zgemm_batched", "bt_split_zgemm_workspace_bytes", "bt_split_zgemm_batched", "bt_zinv_workspace_bytes",
     "bt_zinv_batched", "bt_zinv_batched_noalloc", "bt_decimate_workspace_bytes", "bt_decimate_batched", "library",
-    "bt_debug_split_stall", "bt_debug_fp64_rate", "bt_debug_panel_cluster", "bt_energy_convolve",
+    "bt_debug_split_stall", "bt_debug_fp64_rate", "bt_debug_panel_cluster", "bt_debug_split_profile", "bt_energy_convolve",
 ]
 
 
@@ -279,6 +279,18 @@ def bt_debug_fp64_rate(which: int, iters: int = 4096, stream=None) -> dict:
     t, ms = C.c_double(0.0), C.c_double(0.0)
     _check(N.load().bt_debug_fp64_rate(which, iters, C.byref(t), C.byref(ms), _stream(stream)), None, "fp64_rate")
     return {"tflops": t.value, "ms": ms.value}
+
+
+SPLIT_PROFILE_SLOTS = ("mma_wait_full", "mma_wait_acc", "mma_loop", "tma_wait_empty", "epi_drain", "epi_write",
+                       "tiles")
+
+
+def bt_debug_split_profile(enable: bool):
+    """Measurement aid: start (True) or stop (False) the tensor-core GEMM's wait counters; on stop
+    returns them as a dict of SM cycles summed over CTAs (SPLIT_PROFILE_SLOTS)."""
+    buf = (C.c_ulonglong * len(SPLIT_PROFILE_SLOTS))()
+    _check(N.load().bt_debug_split_profile(1 if enable else 0, buf, len(SPLIT_PROFILE_SLOTS)), None, "split_profile")
+    return None if enable else dict(zip(SPLIT_PROFILE_SLOTS, [int(v) for v in buf]))
 
 
 def bt_debug_panel_cluster(cl: int) -> None:

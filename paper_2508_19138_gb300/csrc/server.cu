@@ -298,9 +298,8 @@ extern "C" bt_status bt_server_submit(bt_server* s, const bt_request* r, long lo
   d.mu_right = r->mu_right;
   d.decim_tol = 1e-14;
   d.decim_maxit = 100;
-  // graph mode: a unit's chunk is captured and launched as one graph, its decimation and Newton
-  // loops run on the device; direct launches would synchronise the host once per loop iteration,
-  // behind whatever the other workers' streams have queued
+  // graph mode (optional): a unit's chunk is captured and launched as one graph, its decimation
+  // and Newton loops on the device; the capture serves one launch only
   d.graph = s->d.graph ? 1 : 0;
   size_t bytes = 0;
   bt_status rc = bt_selinv_workspace_bytes(&d, &bytes);

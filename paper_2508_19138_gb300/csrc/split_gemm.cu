@@ -62,6 +62,11 @@ constexpr int kKBlock = 64;      // bf16 per 128-byte swizzle row
 constexpr int kEpiWarps = 16;   // 4 lane quarters x 4 column quarters of the accumulator
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
+// measurement hook slots (bt_debug_split_profile): cycles of the MMA issuer waiting for a stage's
+// TMA data / for a drained accumulator, its whole loop; the producer waiting for a free stage;
+// epilogue warp 0 draining accumulators / writing C; tiles processed
+enum ProfSlot : int { kProfMmaWaitFull = 0, kProfMmaWaitAcc, kProfMmaLoop, kProfTmaWaitEmpty, kProfEpiDrain,
+                      kProfEpiWrite, kProfTiles, kProfSlots };
 
 // One job = one accumulation round over K blocks [kb0, kb1), drained once:
 //  * dual job: two TMEM accumulators (lanes) fed by one item (t, s, s2): the pairs (s, t) and
@@ -111,6 +116,8 @@ struct MmaParams {
   long long err_stride;
   unsigned long long stall_ns;  // test hook: the MMA warp first waits this long on a barrier
                                 // that nothing completes (0: off)
+  unsigned long long* prof;     // measurement hook (may be null): SM clock cycles accumulated
+                                // over all CTAs, see kProf*
   const int* active; // batch entries with active[b] == 0 are skipped (may be null)
   int a_shared;      // op(A) / op(B) shared by every batch entry: sliced once (batch index 0)
   int b_shared;
@@ -225,6 +232,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t phase = 0;
       int issued = 0;
       bool ok = true;
+      long long t_empty = 0;
       for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
         int m0, n0, b;
         if (!tile_coords(p, NT, tile, m0, n0, b)) continue;
@@ -236,11 +244,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int it = sc.ib[g]; it < ie && ok; ++it) {
             const int ct = zA + sc.t[it], cs = zB + sc.s[it], cs2 = zB + sc.s2[it];
             for (int kb = kb0; kb < kb1; ++kb) {
+              const long long c0 = p.prof ? clock64() : 0;
               if (!ptx::mbar_wait_bounded(&empty[stage], phase ^ 1u, abort_flag, kWaitLimitNs)) {
                 fail(b);
                 ok = false;
                 break;
               }
+              if (p.prof) t_empty += clock64() - c0;
               uint8_t* st = stages + stage * kStageBytes;
               ptx::mbar_arrive_expect_tx(&full[stage], bytes);
               ptx::tma_load_3d(st, &tmA, &full[stage], kb * kKBlock, m0, ct);
@@ -252,6 +262,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
+      if (p.prof) atomicAdd(&p.prof[kProfTmaWaitEmpty], (unsigned long long)t_empty);
       if (*abort_flag) {
         // let the loads already in flight land before the CTA exits (bounded)
         volatile int never = 0;
@@ -266,6 +277,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t phase = 0;
       uint32_t gc = 0;  // jobs started so far (all tiles)
       bool ok = true;
+      long long t_full = 0, t_acc = 0, tiles = 0;
+      const long long t_loop0 = p.prof ? clock64() : 0;
       if (p.stall_ns) {
         // test hook: wait on `drain`, which nothing completes before the commit below, so the
         // bounded wait expires and the CTA takes its timeout path (abort, drain, free TMEM)
@@ -282,13 +295,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
         int m0, n0, b;
         if (!tile_coords(p, NT, tile, m0, n0, b)) continue;
+        ++tiles;
         for (int g = 0; g < sc.n_jobs && ok; ++g, ++gc) {
           const uint32_t ab = gc & 1u;
+          const long long ca = p.prof ? clock64() : 0;
           if (gc >= 2 && !ptx::mbar_wait_bounded(&tempty[ab], ((gc >> 1) - 1u) & 1u, abort_flag, kWaitLimitNs)) {
             fail(b);
             ok = false;
             break;
           }
+          if (p.prof) t_acc += clock64() - ca;
           ptx::tc_fence_after();
           const uint32_t dcol0 = tmem + (2u * ab) * (uint32_t)NT;
           const bool dual = sc.dual[g] != 0;
@@ -296,11 +312,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           uint32_t acc0 = 0u;  // the job's first MMA overwrites the accumulators
           for (int it = sc.ib[g]; it < ie && ok; ++it) {
             for (int kb = kb0; kb < kb1; ++kb) {
+              const long long cf = p.prof ? clock64() : 0;
               if (!ptx::mbar_wait_bounded(&full[stage], phase, abort_flag, kWaitLimitNs)) {
                 fail(b);
                 ok = false;
                 break;
               }
+              if (p.prof) t_full += clock64() - cf;
               ptx::tc_fence_after();
               const uint32_t a_addr = ptx::smem_u32(stages + stage * kStageBytes);
               const uint32_t b_addr = a_addr + kABytes;
@@ -325,6 +343,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       ptx::umma_commit(drain);
       volatile int never = 0;
       ptx::mbar_wait_bounded(drain, 0, &never, kWaitLimitNs);
+      if (p.prof) {
+        atomicAdd(&p.prof[kProfMmaWaitFull], (unsigned long long)t_full);
+        atomicAdd(&p.prof[kProfMmaWaitAcc], (unsigned long long)t_acc);
+        atomicAdd(&p.prof[kProfMmaLoop], (unsigned long long)(clock64() - t_loop0));
+        atomicAdd(&p.prof[kProfTiles], (unsigned long long)tiles);
+      }
     }
   } else {
     // ---------------- epilogue: TMEM -> uint64 fixed point -> C ----------------
@@ -334,6 +358,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int r = q * 32 + lane;
     uint32_t gc = 0;
     bool ok = true;
+    long long t_drain = 0, t_write = 0;
     for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
       int m0, n0, b;
       if (!tile_coords(p, NT, tile, m0, n0, b)) continue;
@@ -350,6 +375,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         ptx::tc_fence_after();
+        const long long cd = p.prof ? clock64() : 0;
         const int lanes = sc.dual[g] ? 2 : 1;
         for (int l = 0; l < lanes; ++l) {
           const float fs = sc.fscale[g][l];
@@ -379,8 +405,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         ptx::tc_fence_before();
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(&tempty[ab]);
+        if (p.prof) t_drain += clock64() - cd;
       }
       if (!ok) break;
+      const long long cw = p.prof ? clock64() : 0;
       // write this tile of C (overlaps the MMAs of the next tile)
       const int jp = m0 + r;  // row of C^T
       const bool row_ok = jp < p.n2;
@@ -447,6 +475,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
+      if (p.prof) t_write += clock64() - cw;
+    }
+    if (p.prof && ew == 0 && lane == 0) {
+      atomicAdd(&p.prof[kProfEpiDrain], (unsigned long long)t_drain);
+      atomicAdd(&p.prof[kProfEpiWrite], (unsigned long long)t_write);
     }
   }
   // ---------------- teardown ----------------
@@ -857,6 +890,7 @@ size_t split_workspace_bytes(int m, int n, int k, int slices, int batch) {
 
 // test hook (bt_debug_split_stall): the MMA warp's stall before its first MMA (0 = off), for the
 // next g_stall_left launches (negative: every launch)
+std::atomic<unsigned long long*> g_prof{nullptr};  // bt_debug_split_profile: device counters
 std::atomic<unsigned long long> g_stall_ns{0};
 std::atomic<long long> g_stall_left{0};
 
@@ -937,6 +971,7 @@ bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A,
     p.err = err;
     p.err_stride = err_stride;
     p.stall_ns = stall_for_launch();
+    p.prof = g_prof.load();
     p.active = active;
     p.a_shared = a_shared ? 1 : 0;
     p.b_shared = b_shared ? 1 : 0;
@@ -947,6 +982,30 @@ bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A,
 }
 
 }  // namespace bt
+
+extern "C" bt_status bt_debug_split_profile(int enable, unsigned long long* counters, int n_counters) {
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  unsigned long long* d = bt::g_prof.load();
+  if (enable) {
+    if (!d) {
+      if (cudaMalloc(&d, sizeof(unsigned long long) * bt::kProfSlots) != cudaSuccess) return BT_ERR_OOM;
+    }
+    if (cudaMemset(d, 0, sizeof(unsigned long long) * bt::kProfSlots) != cudaSuccess) return BT_ERR_CUDA;
+    bt::g_prof.store(d);
+    return BT_OK;
+  }
+  if (!d) return BT_ERR_INVALID_ARG;
+  bt::g_prof.store(nullptr);
+  unsigned long long h[bt::kProfSlots] = {};
+  const bool ok = cudaDeviceSynchronize() == cudaSuccess &&
+                  cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess;
+  cudaFree(d);
+  if (!ok) return BT_ERR_CUDA;
+  if (counters)
+    for (int i = 0; i < n_counters && i < bt::kProfSlots; ++i) counters[i] = h[i];
+  return BT_OK;
+}
 
 extern "C" void bt_debug_split_stall(unsigned long long ns, long long launches) {
   bt::g_stall_left.store(launches);

@@ -35,6 +35,8 @@ def main():
     ap.add_argument("--split-scope", type=int, default=1, help="steptrace: split scope")
     ap.add_argument("--graph", choices=["on", "off"], default="on", help="steptrace: graph mode")
     ap.add_argument("--warmup", type=int, default=2, help="steptrace: untraced steps first")
+    ap.add_argument("--split-profile", action="store_true",
+                    help="split: also report the GEMM's wait counters (bt_debug_split_profile)")
     ap.add_argument("--panel-cluster", type=int, default=0,
                     help="zinv: force the panel cluster size (2, 4 or 8; 0 = default rule)")
     a = ap.parse_args()
@@ -88,10 +90,20 @@ def main():
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / a.reps
+    prof = None
+    if a.kernel == "split" and a.split_profile:
+        pkg.bt_debug_split_profile(True)
+        for _ in range(a.reps):
+            run()
+        c = pkg.bt_debug_split_profile(False)
+        loop = max(1, c["mma_loop"])
+        prof = dict(c, frac_mma_wait_full=c["mma_wait_full"] / loop, frac_mma_wait_acc=c["mma_wait_acc"] / loop,
+                    frac_tma_wait_empty=c["tma_wait_empty"] / loop, frac_epi_drain=c["epi_drain"] / loop,
+                    frac_epi_write=c["epi_write"] / loop)
     flops = 8.0 * n * n * kk * b
     print(json.dumps({"kernel": a.kernel, "bs": n, "k": kk, "batch": b, "ms": ms, "fp64_eq_tflops": flops / ms / 1e9,
                       "slices": a.slices if a.kernel == "split" else None,
-                      "panel_cluster": a.panel_cluster if a.kernel == "zinv" else None}))
+                      "panel_cluster": a.panel_cluster if a.kernel == "zinv" else None, "split_profile": prof}))
 
 
 def conv_flops(L):
@@ -188,20 +200,30 @@ def step_trace(a, pkg):
     ev1.record(stream)
     torch.cuda.synchronize()
     plain_ms = ev0.elapsed_time(ev1)
-    from torch.autograd import DeviceType
+    import os
+    import tempfile
+
     from torch.profiler import ProfilerActivity, profile
-    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+    with profile(activities=[ProfilerActivity.CPU, ProfilerActivity.CUDA]) as prof:
         step(a.warmup + 1)
         torch.cuda.synchronize()
-    agg = {}
+    fd, path = tempfile.mkstemp(suffix=".json")
+    os.close(fd)
+    prof.export_chrome_trace(path)
+    with open(path) as f:
+        trace = json.load(f)
+    os.remove(path)
+    agg, cats = {}, {}
     first, last = None, None
-    for e in prof.events():
-        if e.device_type != DeviceType.CUDA:
+    for e in trace.get("traceEvents", []):
+        cat = str(e.get("cat", ""))
+        cats[cat] = cats.get(cat, 0) + 1
+        if cat.lower() not in ("kernel", "gpu_memcpy", "gpu_memset") or "dur" not in e:
             continue
-        t0, t1 = e.time_range.start, e.time_range.end
+        t0, t1 = float(e["ts"]), float(e["ts"]) + float(e["dur"])
         first = t0 if first is None else min(first, t0)
         last = t1 if last is None else max(last, t1)
-        k = _short_name(e.name)
+        k = _short_name(str(e.get("name", "")))
         n, us = agg.get(k, (0, 0.0))
         agg[k] = (n + 1, us + (t1 - t0))
     total = sum(us for _, us in agg.values())
@@ -210,6 +232,7 @@ def step_trace(a, pkg):
                       "precision": a.precision, "split_scope": a.split_scope if a.precision == "split" else None,
                       "graph": a.graph, "step_ms_plain": plain_ms, "traced_span_ms": (last - first) / 1e3 if rows else 0,
                       "device_ms": total / 1e3, "launches": sum(n for n, _ in agg.values()),
+                      "trace_categories": cats,
                       "kernels": [{"name": k, "launches": n, "ms": us / 1e3, "share": us / total if total else 0}
                                   for k, (n, us) in rows]}))
     status_bad = int((status != 0).sum().item())

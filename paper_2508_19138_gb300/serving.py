@@ -35,7 +35,7 @@ class Server:
 
 def bt_server_create(hbm_budget_bytes: int, max_active: int = 4, max_energies_per_chunk: int = 16,
                      precision: int = N.BT_FP64, split_slices: int = 0, device: int = 0, split_scope: int = 0,
-                     max_retries: int = 1, max_skips: int = 0, graph: bool = True) -> Server:
+                     max_retries: int = 1, max_skips: int = 0, graph: bool = False) -> Server:
     d = N.bt_server_desc(hbm_budget_bytes, max_active, max_energies_per_chunk, precision, split_slices, device,
                          split_scope, max_retries, max_skips, 1 if graph else 0)
     h = C.c_void_p(None)
