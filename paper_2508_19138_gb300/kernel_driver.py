@@ -8,8 +8,8 @@
         # the bs^2 element series of one diagonal block over `batch` energies (na = nb = batch)
     python -m paper_2508_19138_gb300.kernel_driver --kernel fp64rate --reps 4   # DFMA vs DMMA (FP64 tensor) rates
     python -m paper_2508_19138_gb300.kernel_driver --kernel steptrace --precision split --split-scope 1 --batch 32
-        # launch list of one solve step of the 40 x 416 nanoribbon (`batch` energies) from the
-        # CUPTI activity records of the PyTorch profiler: kernels, launches, device time, share
+        # launch list of one solve step of the 40 x 416 nanoribbon (`batch` energies) from CUPTI
+        # activity records (csrc/launch_trace.cpp): kernels, launches, device time, share
 
 Inputs are random complex128 blocks already on the device; each kernel is launched `--reps`
 times on the current stream and its mean time is printed (CUDA events)."""
@@ -161,12 +161,34 @@ def _short_name(name: str) -> str:
     return (base + ("<" + targs if targs else "")).strip()
 
 
+def _load_tracer():
+    """Builds (once) and loads the CUPTI activity collector csrc/launch_trace.cpp: g++ against the
+    toolkit's libcupti, next to the solver library."""
+    import ctypes as C
+    import os
+    import subprocess
+    here = os.path.dirname(os.path.abspath(__file__))
+    so = os.path.join(here, "libbt_trace.so")
+    src = os.path.join(here, "csrc", "launch_trace.cpp")
+    if not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+        cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+        libdirs = [d for d in (os.path.join(cuda, "lib64"), os.path.join(cuda, "extras", "CUPTI", "lib64"))
+                   if os.path.isdir(d)]
+        incs = [d for d in (os.path.join(cuda, "include"), os.path.join(cuda, "extras", "CUPTI", "include"))
+                if os.path.isdir(d)]
+        cmd = (["g++", "-O2", "-std=c++17", "-shared", "-fPIC", src, "-o", so] + [f"-I{d}" for d in incs] +
+               [f"-L{d}" for d in libdirs] + [f"-Wl,-rpath,{d}" for d in libdirs] + ["-lcupti"])
+        subprocess.run(cmd, check=True)
+    lib = C.CDLL(so)
+    lib.bt_trace_get.argtypes = [C.c_int, C.c_char_p, C.c_int, C.POINTER(C.c_ulonglong), C.POINTER(C.c_ulonglong)]
+    return lib
+
+
 def step_trace(a, pkg):
     """One solve step of the 40 x 416 nanoribbon G system (a.batch energies strided across the
     512-energy grid, as the bench steps) after a.warmup untraced steps: the step's kernels from
-    the CUPTI activity records the PyTorch profiler collects (device start / end of every
-    kernel, graph-launched ones included), aggregated per kernel; plus the step's time without
-    the profiler (CUDA events)."""
+    CUPTI activity records (device start / end of every kernel, memcpy and memset, graph-launched
+    kernels included), aggregated per kernel; plus the step's time untraced (CUDA events)."""
     import numpy as np
     import torch
 
@@ -200,39 +222,34 @@ def step_trace(a, pkg):
     ev1.record(stream)
     torch.cuda.synchronize()
     plain_ms = ev0.elapsed_time(ev1)
-    import os
-    import tempfile
-
-    from torch.profiler import ProfilerActivity, profile
-    with profile(activities=[ProfilerActivity.CPU, ProfilerActivity.CUDA]) as prof:
-        step(a.warmup + 1)
-        torch.cuda.synchronize()
-    fd, path = tempfile.mkstemp(suffix=".json")
-    os.close(fd)
-    prof.export_chrome_trace(path)
-    with open(path) as f:
-        trace = json.load(f)
-    os.remove(path)
-    agg, cats = {}, {}
+    import ctypes as C
+    tr = _load_tracer()
+    if tr.bt_trace_start() != 0:
+        raise SystemExit("CUPTI activity tracing could not be enabled")
+    step(a.warmup + 1)
+    torch.cuda.synchronize()
+    if tr.bt_trace_stop() != 0:
+        raise SystemExit("CUPTI activity flush failed")
+    agg = {}
     first, last = None, None
-    for e in trace.get("traceEvents", []):
-        cat = str(e.get("cat", ""))
-        cats[cat] = cats.get(cat, 0) + 1
-        if cat.lower() not in ("kernel", "gpu_memcpy", "gpu_memset") or "dur" not in e:
+    name = C.create_string_buffer(512)
+    t0, t1 = C.c_ulonglong(0), C.c_ulonglong(0)
+    for i in range(tr.bt_trace_count()):
+        if tr.bt_trace_get(i, name, 512, C.byref(t0), C.byref(t1)) < 0:
             continue
-        t0, t1 = float(e["ts"]), float(e["ts"]) + float(e["dur"])
-        first = t0 if first is None else min(first, t0)
-        last = t1 if last is None else max(last, t1)
-        k = _short_name(str(e.get("name", "")))
+        s_ns, e_ns = t0.value, t1.value
+        first = s_ns if first is None else min(first, s_ns)
+        last = e_ns if last is None else max(last, e_ns)
+        k = _short_name(name.value.decode(errors="replace"))
         n, us = agg.get(k, (0, 0.0))
-        agg[k] = (n + 1, us + (t1 - t0))
+        agg[k] = (n + 1, us + (e_ns - s_ns) / 1e3)
     total = sum(us for _, us in agg.values())
     rows = sorted(agg.items(), key=lambda kv: -kv[1][1])
     print(json.dumps({"kernel": "steptrace", "workload": f"nanoribbon G 40x416, {eps} energies per step",
                       "precision": a.precision, "split_scope": a.split_scope if a.precision == "split" else None,
-                      "graph": a.graph, "step_ms_plain": plain_ms, "traced_span_ms": (last - first) / 1e3 if rows else 0,
+                      "graph": a.graph, "step_ms_plain": plain_ms,
+                      "traced_span_ms": (last - first) / 1e6 if rows else 0,
                       "device_ms": total / 1e3, "launches": sum(n for n, _ in agg.values()),
-                      "trace_categories": cats,
                       "kernels": [{"name": k, "launches": n, "ms": us / 1e3, "share": us / total if total else 0}
                                   for k, (n, us) in rows]}))
     status_bad = int((status != 0).sum().item())
