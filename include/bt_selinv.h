@@ -431,6 +431,12 @@ BT_API void bt_debug_panel_cluster(int cl);
  * each summed over all CTAs.  Off by default; a launch reads the setting when issued. */
 BT_API bt_status bt_debug_split_profile(int enable, unsigned long long* counters, int n_counters);
 
+/* Measurement aid (no counterpart in the paper): the preferred L1 / shared-memory split of the
+ * current device for kernels without a carveout of their own, config = 0 no preference,
+ * 1 prefer shared memory, 2 prefer L1, 3 equal (cudaDeviceSetCacheConfig: state of the calling
+ * process's CUDA context, nothing that outlasts it). */
+BT_API bt_status bt_debug_cache_config(int config);
+
 #ifdef __cplusplus
 }
 #endif

@@ -76,6 +76,7 @@ SIGNATURES = {
     "bt_debug_fp64_rate": [_I, _I, C.POINTER(_D), C.POINTER(_D), _P],
     "bt_debug_panel_cluster": [_I],
     "bt_debug_split_profile": [_I, C.POINTER(C.c_ulonglong), _I],
+    "bt_debug_cache_config": [_I],
     "bt_energy_convolve": [_I, _I, _I, _I, _I, _P, _LL, _P, _LL, _P, _LL, _D, _D, _I, _P],
     "bt_decimate_workspace_bytes": [_I, _I, C.POINTER(C.c_size_t)],
     "bt_decimate_batched": [_I, _I, _P, _P, _P, _D, _I, _P, _P, _P, _P, _P, _SZ, _P],

@@ -82,3 +82,11 @@ extern "C" bt_status bt_debug_fp64_rate(int which, int iters, double* tflops, do
   if (ms) *ms = t;
   return BT_OK;
 }
+
+// Measurement aid: the current device's preferred L1 / shared-memory split for kernels that set
+// no carveout of their own (cudaDeviceSetCacheConfig; state of this process's context only).
+extern "C" bt_status bt_debug_cache_config(int config) {
+  if (config < 0 || config > 3) return BT_ERR_INVALID_ARG;
+  BT_CUDA_TRY(cudaDeviceSetCacheConfig(static_cast<cudaFuncCache>(config)));
+  return BT_OK;
+}

@@ -8,6 +8,7 @@
 //   bt_trace_stop()    flushes every buffer and disables them
 //   bt_trace_count() / bt_trace_get(i, ...)   the records collected, in completion order
 #include <cupti.h>
+#include <cxxabi.h>
 
 #include <cstdint>
 #include <cstdlib>
@@ -23,6 +24,15 @@ struct Rec {
   unsigned long long start, end;
   int kind;  // 0 kernel, 1 memcpy, 2 memset
 };
+
+std::string demangle(const char* n) {
+  if (!n) return "?";
+  int st = 0;
+  char* d = abi::__cxa_demangle(n, nullptr, nullptr, &st);
+  std::string out = (st == 0 && d) ? std::string(d) : std::string(n);
+  free(d);
+  return out;
+}
 
 std::mutex g_mu;
 std::vector<Rec> g_recs;
@@ -42,7 +52,7 @@ void CUPTIAPI buffer_completed(CUcontext, uint32_t, uint8_t* buffer, size_t, siz
   while (buffer && cuptiActivityGetNextRecord(buffer, valid, &rec) == CUPTI_SUCCESS) {
     if (rec->kind == CUPTI_ACTIVITY_KIND_CONCURRENT_KERNEL || rec->kind == CUPTI_ACTIVITY_KIND_KERNEL) {
       const auto* k = reinterpret_cast<const CUpti_ActivityKernel10*>(rec);
-      g_recs.push_back(Rec{k->name ? k->name : "?", (unsigned long long)k->start, (unsigned long long)k->end, 0});
+      g_recs.push_back(Rec{demangle(k->name), (unsigned long long)k->start, (unsigned long long)k->end, 0});
     } else if (rec->kind == CUPTI_ACTIVITY_KIND_MEMCPY) {
       const auto* m = reinterpret_cast<const CUpti_ActivityMemcpy6*>(rec);
       g_recs.push_back(Rec{"memcpy", (unsigned long long)m->start, (unsigned long long)m->end, 1});

@@ -35,6 +35,8 @@ def main():
     ap.add_argument("--split-scope", type=int, default=1, help="steptrace: split scope")
     ap.add_argument("--graph", choices=["on", "off"], default="on", help="steptrace: graph mode")
     ap.add_argument("--warmup", type=int, default=2, help="steptrace: untraced steps first")
+    ap.add_argument("--cache-config", type=int, default=-1,
+                    help="preferred L1 / shared split for the run (0 none, 1 shared, 2 L1, 3 equal; -1 untouched)")
     ap.add_argument("--split-profile", action="store_true",
                     help="split: also report the GEMM's wait counters (bt_debug_split_profile)")
     ap.add_argument("--panel-cluster", type=int, default=0,
@@ -45,6 +47,8 @@ def main():
     pkg.library()
     if a.panel_cluster:
         pkg.bt_debug_panel_cluster(a.panel_cluster)
+    if a.cache_config >= 0:
+        pkg.bt_debug_cache_config(a.cache_config)
     if a.kernel == "conv":
         return conv_driver(a, pkg)
     if a.kernel == "steptrace":
@@ -232,26 +236,42 @@ def step_trace(a, pkg):
         raise SystemExit("CUPTI activity flush failed")
     agg = {}
     first, last = None, None
-    name = C.create_string_buffer(512)
+    name = C.create_string_buffer(1024)
     t0, t1 = C.c_ulonglong(0), C.c_ulonglong(0)
+    recs = []
     for i in range(tr.bt_trace_count()):
-        if tr.bt_trace_get(i, name, 512, C.byref(t0), C.byref(t1)) < 0:
+        if tr.bt_trace_get(i, name, 1024, C.byref(t0), C.byref(t1)) < 0:
             continue
         s_ns, e_ns = t0.value, t1.value
         first = s_ns if first is None else min(first, s_ns)
         last = e_ns if last is None else max(last, e_ns)
         k = _short_name(name.value.decode(errors="replace"))
+        recs.append((s_ns, e_ns, k))
         n, us = agg.get(k, (0, 0.0))
         agg[k] = (n + 1, us + (e_ns - s_ns) / 1e3)
+    # idle device time between consecutive records (by start), attributed to the record after
+    # the gap: where the step waits for launches rather than for work
+    recs.sort()
+    gaps, idle, busy_to = {}, 0.0, None
+    for s_ns, e_ns, k in recs:
+        if busy_to is not None and s_ns > busy_to:
+            g = (s_ns - busy_to) / 1e3
+            idle += g
+            n, us = gaps.get(k, (0, 0.0))
+            gaps[k] = (n + 1, us + g)
+        busy_to = e_ns if busy_to is None else max(busy_to, e_ns)
     total = sum(us for _, us in agg.values())
     rows = sorted(agg.items(), key=lambda kv: -kv[1][1])
     print(json.dumps({"kernel": "steptrace", "workload": f"nanoribbon G 40x416, {eps} energies per step",
                       "precision": a.precision, "split_scope": a.split_scope if a.precision == "split" else None,
-                      "graph": a.graph, "step_ms_plain": plain_ms,
+                      "graph": a.graph, "cache_config": a.cache_config, "step_ms_plain": plain_ms,
                       "traced_span_ms": (last - first) / 1e6 if rows else 0,
                       "device_ms": total / 1e3, "launches": sum(n for n, _ in agg.values()),
+                      "idle_ms": idle / 1e3,
                       "kernels": [{"name": k, "launches": n, "ms": us / 1e3, "share": us / total if total else 0}
-                                  for k, (n, us) in rows]}))
+                                  for k, (n, us) in rows],
+                      "idle_before": [{"name": k, "gaps": n, "ms": us / 1e3}
+                                      for k, (n, us) in sorted(gaps.items(), key=lambda kv: -kv[1][1])[:20]]}))
     status_bad = int((status != 0).sum().item())
     if status_bad:
         raise SystemExit(f"{status_bad} energies with a non-zero status")
