@@ -74,6 +74,11 @@ struct bt_ctx {
   // overlap the copies of one chunk's outputs with the next chunk's compute
   char* stage = nullptr;
   size_t stage_bytes = 0;
+  // graph mode: the chunk's per-energy inputs copied to fixed addresses before each replay, so
+  // that one captured graph serves every call with the same shapes and outputs (allocated on
+  // first use)
+  char* gstage = nullptr;
+  size_t gstage_bytes = 0;
   cudaStream_t copy_st = nullptr;
   cudaEvent_t ev_done[2] = {nullptr, nullptr};
   cudaEvent_t ev_ready = nullptr;
@@ -533,6 +538,7 @@ extern "C" bt_status bt_selinv_destroy(bt_ctx* c) {
   if (c->copy_st) cudaStreamSynchronize(c->copy_st);
   if (c->ws && c->owns_ws) cudaFree(c->ws);
   if (c->stage) cudaFree(c->stage);
+  if (c->gstage) cudaFree(c->gstage);
   for (cudaEvent_t ev : {c->ev_done[0], c->ev_done[1], c->ev_ready})
     if (ev) cudaEventDestroy(ev);
   if (c->copy_st) cudaStreamDestroy(c->copy_st);
@@ -682,36 +688,37 @@ bt_status decimate_leads(bt_ctx* c, int Ec, const int* dec_mask) {
   return BT_OK;
 }
 
+// e0: the chunk's first energy in the outputs; ein: in the inputs (e0, or 0 for staged inputs)
 bt_status solve_chunk_g(bt_ctx* c, const bt_bt* H, const bt_bt* S, const bt_bt* sR, const bt_bt* sL, const bt_bt* sG,
-                        long long e0, int Ec, const bt_bt_out* oR, const bt_bt_out* oL, const bt_bt_out* oG,
-                        int* status) {
+                        long long e0, long long ein, int Ec, const bt_bt_out* oR, const bt_bt_out* oL,
+                        const bt_bt_out* oG, int* status) {
   const bt_selinv_desc& d = c->d;
   const int N = d.nb, bs = d.bs;
   const long long B2 = (long long)bs * bs, NB2 = N * B2, N1B2 = (long long)(N > 1 ? N - 1 : 0) * B2;
   cudaStream_t st = c->st;
   auto dstride = [&](const bt_bt* b) { return b && b->per_energy ? diag_extent(*b, N, bs) : 0LL; };
   auto ostride = [&](const bt_bt* b) { return b && b->per_energy ? off_extent(N, bs) : 0LL; };
-  const zd* Hd = at_energy(H->diag, H->per_energy, diag_extent(*H, N, bs), e0);
-  const zd* Hu = at_energy(H->upper, H->per_energy, off_extent(N, bs), e0);
-  const zd* Hl = at_energy(H->lower, H->per_energy, off_extent(N, bs), e0);
+  const zd* Hd = at_energy(H->diag, H->per_energy, diag_extent(*H, N, bs), ein);
+  const zd* Hu = at_energy(H->upper, H->per_energy, off_extent(N, bs), ein);
+  const zd* Hl = at_energy(H->lower, H->per_energy, off_extent(N, bs), ein);
   const zd *Sd = nullptr, *Su = nullptr, *Sl = nullptr;
   if (S) {
-    Sd = at_energy(S->diag, S->per_energy, diag_extent(*S, N, bs), e0);
-    Su = at_energy(S->upper, S->per_energy, off_extent(N, bs), e0);
-    Sl = at_energy(S->lower, S->per_energy, off_extent(N, bs), e0);
+    Sd = at_energy(S->diag, S->per_energy, diag_extent(*S, N, bs), ein);
+    Su = at_energy(S->upper, S->per_energy, off_extent(N, bs), ein);
+    Sl = at_energy(S->lower, S->per_energy, off_extent(N, bs), ein);
   }
   const zd *Rd = nullptr, *Ru = nullptr, *Rl = nullptr;
   if (sR) {
-    Rd = at_energy(sR->diag, sR->per_energy, diag_extent(*sR, N, bs), e0);
-    Ru = at_energy(sR->upper, sR->per_energy, off_extent(N, bs), e0);
-    Rl = at_energy(sR->lower, sR->per_energy, off_extent(N, bs), e0);
+    Rd = at_energy(sR->diag, sR->per_energy, diag_extent(*sR, N, bs), ein);
+    Ru = at_energy(sR->upper, sR->per_energy, off_extent(N, bs), ein);
+    Rl = at_energy(sR->lower, sR->per_energy, off_extent(N, bs), ein);
   }
   const bt_bt* sLG[2] = {sL, sG};
   const zd *LGd[2] = {nullptr, nullptr}, *LGu[2] = {nullptr, nullptr};
   for (int w = 0; w < 2; ++w)
     if (sLG[w]) {
-      LGd[w] = at_energy(sLG[w]->diag, sLG[w]->per_energy, diag_extent(*sLG[w], N, bs), e0);
-      LGu[w] = at_energy(sLG[w]->upper, sLG[w]->per_energy, off_extent(N, bs), e0);
+      LGd[w] = at_energy(sLG[w]->diag, sLG[w]->per_energy, diag_extent(*sLG[w], N, bs), ein);
+      LGu[w] = at_energy(sLG[w]->upper, sLG[w]->per_energy, off_extent(N, bs), ein);
     }
 
   // energies -> z, Fermi factors
@@ -916,7 +923,8 @@ bt_status solve_chunk_g(bt_ctx* c, const bt_bt* H, const bt_bt* S, const bt_bt* 
 // products (Sec. 4.3.1; exact when the cell is longer than 3 r_cut), the RGF sweep on them, and
 // W^R = X^R V on the selected blocks (X^R_{i,i+-2} from the backward pass).  W^<> = X^<>.
 bt_status solve_chunk_w(bt_ctx* c, const bt_bt* V, const bt_bt* PR, const bt_bt* PL, const bt_bt* PG, long long e0,
-                        int Ec, const bt_bt_out* oR, const bt_bt_out* oL, const bt_bt_out* oG, int* status) {
+                        long long ein, int Ec, const bt_bt_out* oR, const bt_bt_out* oL, const bt_bt_out* oG,
+                        int* status) {
   const bt_selinv_desc& d = c->d;
   const int N = d.nb, bs = d.bs;
   const long long B2 = (long long)bs * bs, NB2 = N * B2, N1B2 = (long long)(N > 1 ? N - 1 : 0) * B2;
@@ -939,9 +947,9 @@ bt_status solve_chunk_w(bt_ctx* c, const bt_bt* V, const bt_bt* PR, const bt_bt*
     if (!P) return p;
     p.ed = P->per_energy ? diag_extent(*P, N, bs) : 0;
     p.eo = P->per_energy ? N1B2 : 0;
-    p.d = at_energy(P->diag, P->per_energy, diag_extent(*P, N, bs), e0);
-    p.u = at_energy(P->upper, P->per_energy, N1B2, e0);
-    p.l = at_energy(P->lower, P->per_energy, N1B2, e0);
+    p.d = at_energy(P->diag, P->per_energy, diag_extent(*P, N, bs), ein);
+    p.u = at_energy(P->upper, P->per_energy, N1B2, ein);
+    p.l = at_energy(P->lower, P->per_energy, N1B2, ein);
     p.sym = P->symmetry;
     return p;
   };
@@ -1397,6 +1405,57 @@ bt_status run_chunk_graph(bt_ctx* c, const bt_bt* H, const bt_bt* S, const bt_bt
   return BT_OK;
 }
 
+// Graph mode: copies energies [e0, e0 + Ec) of every per-energy input to the context's staging
+// memory (device to device, stream-ordered before the replay) and points ins[k] at the copies, so
+// that the captured graph reads fixed addresses whichever energies the call passes.
+bt_status stage_inputs(bt_ctx* c, const bt_bt** ins, bt_bt* staged, long long e0, int Ec) {
+  const int N = c->d.nb, bs = c->d.bs, Emax = c->d.max_energies;
+  const long long oext = off_extent(N, bs);
+  size_t need = 0;
+  for (int k = 0; k < 5; ++k) {
+    const bt_bt* b = ins[k];
+    if (!b || !b->per_energy) continue;
+    if (b->diag) need += al(sizeof(zd) * diag_extent(*b, N, bs) * Emax);
+    if (b->upper) need += al(sizeof(zd) * oext * Emax);
+    if (b->lower) need += al(sizeof(zd) * oext * Emax);
+  }
+  if (need == 0) return BT_OK;
+  if (c->gstage_bytes < need) {
+    // the stream is idle here (the caller synchronised it before staging the chunk's energies);
+    // graphs captured on the old staging memory read it: they go with it
+    for (auto& g : c->graphs) {
+      cudaGraphExecDestroy(g.exec);
+      cudaGraphDestroy(g.graph);
+    }
+    c->graphs.clear();
+    if (c->gstage) cudaFree(c->gstage);
+    c->gstage = nullptr;
+    c->gstage_bytes = 0;
+    if (cudaMalloc(&c->gstage, need) != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(c, BT_ERR_OOM, "graph-mode input staging allocation failed");
+    }
+    c->gstage_bytes = need;
+  }
+  Carver cv(c->gstage);
+  auto copy = [&](const void* src, long long ext, const void** dst) -> bool {
+    zd* d = cv.take<zd>((size_t)(ext * Emax));
+    *dst = d;
+    return cudaMemcpyAsync(d, static_cast<const zd*>(src) + ext * e0, sizeof(zd) * ext * Ec, cudaMemcpyDeviceToDevice,
+                           c->st) == cudaSuccess;
+  };
+  for (int k = 0; k < 5; ++k) {
+    const bt_bt* b = ins[k];
+    if (!b || !b->per_energy) continue;
+    staged[k] = *b;
+    if (b->diag && !copy(b->diag, diag_extent(*b, N, bs), &staged[k].diag)) return set_err(c, BT_ERR_CUDA, "input staging failed");
+    if (b->upper && !copy(b->upper, oext, &staged[k].upper)) return set_err(c, BT_ERR_CUDA, "input staging failed");
+    if (b->lower && !copy(b->lower, oext, &staged[k].lower)) return set_err(c, BT_ERR_CUDA, "input staging failed");
+    ins[k] = &staged[k];
+  }
+  return BT_OK;
+}
+
 }  // namespace
 
 extern "C" bt_status bt_selinv_solve(bt_ctx* c, const bt_bt* H, const bt_bt* S, const bt_bt* sigR, const bt_bt* sigL,
@@ -1430,18 +1489,27 @@ extern "C" bt_status bt_selinv_solve(bt_ctx* c, const bt_bt* H, const bt_bt* S, 
     if (cudaMemcpyAsync(c->Edev, c->h_E, sizeof(double) * Ec, cudaMemcpyHostToDevice, c->st) != cudaSuccess)
       return set_err(c, BT_ERR_CUDA, "energy upload failed");
     fold_pending(c);  // the stream is idle here
+    const bt_bt* in[5] = {H, S, sigR, sigL, sigG};
+    bt_bt staged[5];
+    long long ein = e0;
+    if (c->d.graph) {
+      BT_TRY(stage_inputs(c, in, staged, e0, Ec));
+      ein = 0;
+    }
     bt_status s;
     auto direct = [&]() {
       // a bounded wait of a sliced product that expires marks every energy of the chunk
       if (cudaMemsetAsync(c->tflag, 0, sizeof(int), c->st) != cudaSuccess) return BT_ERR_CUDA;
-      const bt_status r =
-          c->d.system == BT_SYS_G ? solve_chunk_g(c, H, S, sigR, sigL, sigG, e0, Ec, outR, outL, outG, status_device + e0)
-                                  : solve_chunk_w(c, H, sigR, sigL, sigG, e0, Ec, outR, outL, outG, status_device + e0);
+      const bt_status r = c->d.system == BT_SYS_G
+                              ? solve_chunk_g(c, in[0], in[1], in[2], in[3], in[4], e0, ein, Ec, outR, outL, outG,
+                                              status_device + e0)
+                              : solve_chunk_w(c, in[0], in[2], in[3], in[4], e0, ein, Ec, outR, outL, outG,
+                                              status_device + e0);
       if (r != BT_OK) return r;
       return bt::flag_status(c->st, Ec, c->tflag, status_device + e0);
     };
     if (c->d.graph)
-      s = run_chunk_graph(c, H, S, sigR, sigL, sigG, e0, Ec, outR, outL, outG, status_device + e0, direct);
+      s = run_chunk_graph(c, in[0], in[1], in[2], in[3], in[4], e0, Ec, outR, outL, outG, status_device + e0, direct);
     else
       s = direct();
     if (s != BT_OK) {

@@ -11,14 +11,6 @@ from .api import (BT, BTOut, bt_selinv_create, bt_selinv_get_stats, bt_selinv_so
                   make_desc)
 
 
-class _null:
-    def __enter__(self):
-        return self
-
-    def __exit__(self, *a):
-        return False
-
-
 def _t(x, device):
     import torch
     if x is None:
@@ -47,7 +39,6 @@ class GSolver:
                               memo_capacity, split_scope, graph, decim_newton_after, gemm_tile, inv_panel)
         self._own_stream = None
         self.graph = bool(graph)
-        self._stage = None  # graph mode: fixed buffers for per-call energy slices of the self-energies
         if graph and stream is None:
             import torch
             stream = torch.cuda.Stream()  # stream capture needs a non-default stream
@@ -113,23 +104,6 @@ class GSolver:
             # the caller's stream waits for the solve at the end
             import torch
             self._own_stream.wait_stream(torch.cuda.current_stream())
-        if self.graph and sig_range is not None:
-            # graph mode replays a captured chunk only while the operand pointers stay the same:
-            # the energy slices are copied (on the solve stream) into buffers that stay put
-            import torch
-            ins = (sR, sL, sG)
-            if self._stage is None or any((a is None) != (b is None) or (a is not None and a.diag.shape != b.shape)
-                                          for a, b in zip(ins, self._stage)):
-                self._stage = [None if a is None else torch.empty_like(a.diag) for a in ins]
-            st = self.stream if self.stream is not None else torch.cuda.current_stream()
-            with torch.cuda.stream(st) if not isinstance(st, int) else _null():
-                for a, buf in zip(ins, self._stage):
-                    if a is not None:
-                        buf.copy_(a.diag, non_blocking=True)
-                        if isinstance(st, torch.cuda.Stream):
-                            buf.record_stream(st)  # allocated on the caller's stream, read on st
-            sR, sL, sG = [None if a is None else BT(buf, None, None, a.layout, a.symmetry, True)
-                          for a, buf in zip(ins, self._stage)]
         bt_selinv_solve(self.ctx, self.H, self.S, sR, sL, sG, energies, outs.get("R"), outs.get("L"),
                         outs.get("G"), status)
         if self._own_stream is not None:

@@ -253,13 +253,19 @@ def step_trace(a, pkg):
     # the gap: where the step waits for launches rather than for work
     recs.sort()
     gaps, idle, busy_to = {}, 0.0, None
-    for s_ns, e_ns, k in recs:
+    big = []  # (gap us, index of the record after it)
+    for i, (s_ns, e_ns, k) in enumerate(recs):
         if busy_to is not None and s_ns > busy_to:
             g = (s_ns - busy_to) / 1e3
             idle += g
             n, us = gaps.get(k, (0, 0.0))
             gaps[k] = (n + 1, us + g)
+            big.append((g, i))
         busy_to = e_ns if busy_to is None else max(busy_to, e_ns)
+    big.sort(reverse=True)
+    largest = [{"gap_ms": g / 1e3, "at_ms": (recs[i][0] - first) / 1e6,
+                "before": [recs[j][2] for j in range(max(0, i - 3), i)],
+                "after": [recs[j][2] for j in range(i, min(len(recs), i + 3))]} for g, i in big[:6]]
     total = sum(us for _, us in agg.values())
     rows = sorted(agg.items(), key=lambda kv: -kv[1][1])
     print(json.dumps({"kernel": "steptrace", "workload": f"nanoribbon G 40x416, {eps} energies per step",
@@ -270,6 +276,7 @@ def step_trace(a, pkg):
                       "idle_ms": idle / 1e3,
                       "kernels": [{"name": k, "launches": n, "ms": us / 1e3, "share": us / total if total else 0}
                                   for k, (n, us) in rows],
+                      "largest_gaps": largest,
                       "idle_before": [{"name": k, "gaps": n, "ms": us / 1e3}
                                       for k, (n, us) in sorted(gaps.items(), key=lambda kv: -kv[1][1])[:20]]}))
     status_bad = int((status != 0).sum().item())
