@@ -342,34 +342,6 @@ bt_status flag_status(cudaStream_t st, int E, const int* flag, int* status) {
   return BT_OK;
 }
 
-// Device-to-device copy as a kernel: 16-byte words when both pointers and the size allow it,
-// bytes otherwise.  Used where a copy is captured into a graph, in particular inside the bodies of
-// conditional loops (a memcpy node there was measured to stall the device at loop entry).
-__global__ void copy16_kernel(long long n16, const uint4* __restrict__ src, uint4* __restrict__ dst) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n16; i += (long long)gridDim.x * blockDim.x)
-    dst[i] = src[i];
-}
-__global__ void copy1_kernel(long long n, const unsigned char* __restrict__ src, unsigned char* __restrict__ dst) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    dst[i] = src[i];
-}
-
-bt_status copy_d2d(cudaStream_t st, void* dst, const void* src, size_t bytes) {
-  if (bytes == 0) return BT_OK;
-  const bool wide = ((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src) | bytes) & 15u) == 0;
-  const long long n = wide ? (long long)(bytes / 16) : (long long)bytes;
-  long long blocks = (n + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;  // grid-stride: a few waves of the 152 SMs at most
-  if (wide)
-    copy16_kernel<<<(unsigned)blocks, 256, 0, st>>>(n, static_cast<const uint4*>(src), static_cast<uint4*>(dst));
-  else
-    copy1_kernel<<<(unsigned)blocks, 256, 0, st>>>(n, static_cast<const unsigned char*>(src),
-                                                  static_cast<unsigned char*>(dst));
-  count_launch();
-  BT_CUDA_TRY(cudaGetLastError());
-  return BT_OK;
-}
-
 bt_status merge_status(cudaStream_t st, int E, const int* info, int n_sources, long long src_stride, int* status) {
   if (E <= 0) return BT_OK;
   merge_status_kernel<<<(E + 127) / 128, 128, 0, st>>>(E, info, n_sources, src_stride, status); count_launch();

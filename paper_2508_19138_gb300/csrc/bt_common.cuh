@@ -55,9 +55,6 @@ namespace bt {
 void count_launch();
 long long launches_total();
 
-// Device-to-device copy of `bytes` as a kernel on st (graph-capturable as a kernel node).
-bt_status copy_d2d(cudaStream_t st, void* dst, const void* src, size_t bytes);
-
 // One GEMM operand: element (r, c) of op(X) for batch entry b is
 //   op == BT_OP_N : X[b*stride + r*ld + c]
 //   op == BT_OP_C : conj(X[b*stride + c*ld + r])

@@ -362,7 +362,7 @@ bt_status decimate_step(cudaStream_t st, int bs, int batch, DecimWs& w, int* inf
   const long long bs2 = (long long)bs * bs, S = bs2;
   const size_t mat_bytes = (size_t)batch * bs2 * sizeof(zd);
   const zd one = zmake(1.0, 0.0), mone = zmake(-1.0, 0.0), zero = zmake(0.0, 0.0);
-  BT_TRY(copy_d2d(st, w.g, w.e, mat_bytes));
+  BT_CUDA_TRY(cudaMemcpyAsync(w.g, w.e, mat_bytes, cudaMemcpyDeviceToDevice, st));
   BT_TRY(zinv(st, bs, w.g, S, batch, info, w.inv_ws, w.inv_bytes, w.active, &E));
   // ag = a g, bg = b g
   BT_TRY(gemm(E, st, bs, bs, bs, one, Operand{w.a, bs, S, BT_OP_N}, Operand{w.g, bs, S, BT_OP_N}, zero, w.ag, bs, S, batch, w.active));
@@ -380,8 +380,8 @@ bt_status decimate_step(cudaStream_t st, int bs, int batch, DecimWs& w, int* inf
   BT_TRY(gemm(E, st, bs, bs, bs, mone, Operand{w.ag, bs, S, BT_OP_N}, Operand{w.a, bs, S, BT_OP_N}, zero, w.a2, bs, S, batch, w.active));
   BT_TRY(gemm(E, st, bs, bs, bs, mone, Operand{w.bg, bs, S, BT_OP_N}, Operand{w.b, bs, S, BT_OP_N}, zero, w.b2, bs, S, batch, w.active));
   if (fixed) {
-    BT_TRY(copy_d2d(st, w.a, w.a2, mat_bytes));
-    BT_TRY(copy_d2d(st, w.b, w.b2, mat_bytes));
+    BT_CUDA_TRY(cudaMemcpyAsync(w.a, w.a2, mat_bytes, cudaMemcpyDeviceToDevice, st));
+    BT_CUDA_TRY(cudaMemcpyAsync(w.b, w.b2, mat_bytes, cudaMemcpyDeviceToDevice, st));
   } else {
     std::swap(w.a, w.a2);
     std::swap(w.b, w.b2);
@@ -458,8 +458,8 @@ bt_status stein_step(cudaStream_t st, int bs, int batch, zd*& A, zd*& B, bool he
   if (!herm)
     BT_TRY(gemm(E, st, bs, bs, bs, one, Operand{B, bs, S, BT_OP_N}, Operand{B, bs, S, BT_OP_N}, zero, w.B2, bs, S, batch, w.active));
   if (fixed) {
-    BT_TRY(copy_d2d(st, A, w.A2, mat_bytes));
-    if (!herm) BT_TRY(copy_d2d(st, B, w.B2, mat_bytes));
+    BT_CUDA_TRY(cudaMemcpyAsync(A, w.A2, mat_bytes, cudaMemcpyDeviceToDevice, st));
+    if (!herm) BT_CUDA_TRY(cudaMemcpyAsync(B, w.B2, mat_bytes, cudaMemcpyDeviceToDevice, st));
   } else {
     std::swap(A, w.A2);
     if (!herm) std::swap(B, w.B2);
@@ -605,10 +605,10 @@ bt_status decimate(cudaStream_t st, int bs, int batch, const zd* m, const zd* n,
   carve(ws, bs, batch, wide, &w);
   const long long bs2 = (long long)bs * bs;
   const size_t mat_bytes = (size_t)batch * bs2 * sizeof(zd);
-  BT_TRY(copy_d2d(st, w.a, n, mat_bytes));
-  BT_TRY(copy_d2d(st, w.b, np, mat_bytes));
-  BT_TRY(copy_d2d(st, w.e, m, mat_bytes));
-  BT_TRY(copy_d2d(st, w.es, m, mat_bytes));
+  BT_CUDA_TRY(cudaMemcpyAsync(w.a, n, mat_bytes, cudaMemcpyDeviceToDevice, st));
+  BT_CUDA_TRY(cudaMemcpyAsync(w.b, np, mat_bytes, cudaMemcpyDeviceToDevice, st));
+  BT_CUDA_TRY(cudaMemcpyAsync(w.e, m, mat_bytes, cudaMemcpyDeviceToDevice, st));
+  BT_CUDA_TRY(cudaMemcpyAsync(w.es, m, mat_bytes, cudaMemcpyDeviceToDevice, st));
   init_kernel<<<(batch + 255) / 256, 256, 0, st>>>(batch, mask, w.active, iters, info); count_launch();
   BT_CUDA_TRY(cudaGetLastError());
   BT_TRY(lead_max(st, 0, bs2, batch, n, np, nullptr, w.keys, w.flags));
@@ -720,7 +720,7 @@ bt_status fixed_point(cudaStream_t st, int bs, int batch, const zd* m, const zd*
   const long long S = bs2;
   const zd one = zmake(1.0, 0.0), mone = zmake(-1.0, 0.0), zero = zmake(0.0, 0.0);
   BT_CUDA_TRY(cudaMemsetAsync(conv, 0, sizeof(int) * batch, st));
-  BT_TRY(copy_d2d(st, w.active, run, sizeof(int) * batch));
+  BT_CUDA_TRY(cudaMemcpyAsync(w.active, run, sizeof(int) * batch, cudaMemcpyDeviceToDevice, st));
   BT_CUDA_TRY(cudaMemsetAsync(w.ref, 0, sizeof(double) * batch, st));  // previous update sizes
   std::vector<int> hm(batch);
   if (cudaMemcpyAsync(hm.data(), run, sizeof(int) * batch, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -734,7 +734,7 @@ bt_status fixed_point(cudaStream_t st, int bs, int batch, const zd* m, const zd*
     lead_its += running;
     // x_new = (m - n x n')^{-1}   (Eq. 5)
     BT_TRY(gemm(E, st, bs, bs, bs, one, Operand{n, bs, S, BT_OP_N}, Operand{x, bs, S, BT_OP_N}, zero, w.t, bs, S, batch, w.active));
-    BT_TRY(copy_d2d(st, w.g, m, mat_bytes));
+    BT_CUDA_TRY(cudaMemcpyAsync(w.g, m, mat_bytes, cudaMemcpyDeviceToDevice, st));
     BT_TRY(gemm(E, st, bs, bs, bs, mone, Operand{w.t, bs, S, BT_OP_N}, Operand{np, bs, S, BT_OP_N}, one, w.g, bs, S, batch, w.active));
     BT_TRY(zinv(st, bs, w.g, S, batch, info, w.inv_ws, w.inv_bytes, w.active, &E));
     // the test reads the current mask; copy x_new -> x for the leads still iterating first

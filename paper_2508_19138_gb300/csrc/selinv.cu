@@ -1083,7 +1083,7 @@ bt_status solve_chunk_w(bt_ctx* c, const bt_bt* V, const bt_bt* PR, const bt_bt*
         BT_TRY(prod(c, Ec, 1.0, W(tq, B2), flip(W(lead(c->lead_x, side), B2)), 0.0, q, B2, true));
       }
       // w = q + a w a^H for all 2 Ec leads (a is consumed: copied first)
-      BT_TRY(copy_d2d(st, wl[10], wl[6], sizeof(zd) * 2 * Ec * B2));
+      BT_CUDA_TRY(cudaMemcpyAsync(wl[10], wl[6], sizeof(zd) * 2 * Ec * B2, cudaMemcpyDeviceToDevice, st));
       long long its = 0, body = 0;
       BT_TRY(bt::stein(st, bs, 2 * Ec, wl[10], nullptr, wl[9], 1e-14, 64, nullptr, c->w_ok, nullptr, c->dec_ws,
                        c->dec_bytes, c->h_pinned, &its, &c->eng_kept, c->loop, &body));
