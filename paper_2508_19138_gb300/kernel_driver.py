@@ -192,7 +192,11 @@ def step_trace(a, pkg):
     """One solve step of the 40 x 416 nanoribbon G system (a.batch energies strided across the
     512-energy grid, as the bench steps) after a.warmup untraced steps: the step's kernels from
     CUPTI activity records (device start / end of every kernel, memcpy and memset, graph-launched
-    kernels included), aggregated per kernel; plus the step's time untraced (CUDA events)."""
+    kernels included), aggregated per kernel; plus the step's time untraced (CUDA events).
+    Kernels that run inside the body of a device-side conditional loop of a graph (the
+    decimation, Newton and Stein loops of graph mode) produce no records: their time shows as
+    one idle gap at the loop's entry.  --graph off lists every kernel (the loops then run from
+    the host)."""
     import numpy as np
     import torch
 
@@ -249,8 +253,8 @@ def step_trace(a, pkg):
         recs.append((s_ns, e_ns, k))
         n, us = agg.get(k, (0, 0.0))
         agg[k] = (n + 1, us + (e_ns - s_ns) / 1e3)
-    # idle device time between consecutive records (by start), attributed to the record after
-    # the gap: where the step waits for launches rather than for work
+    # device time between consecutive records (by start) with no record running, attributed to the
+    # record after the gap: launch waits, or (graph mode) the device-side loop bodies
     recs.sort()
     gaps, idle, busy_to = {}, 0.0, None
     big = []  # (gap us, index of the record after it)
