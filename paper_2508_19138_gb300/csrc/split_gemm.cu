@@ -102,6 +102,9 @@ struct MmaParams {
   int tiles_x;    // tiles along the 2n rows of C^T
   int tiles_y;    // tiles along the m rows of C
   int n_tiles;    // tiles_x * tiles_y * batch
+  int pair;       // 1: CTA pairs (cta_group::2), a unit = two M tiles of one N tile
+  int tiles_xu;   // units along the 2n rows: tiles_x, or ceil(tiles_x / 2) for pairs
+  int n_units;    // tiles_xu * tiles_y * batch
   const int* eA;  // [batch][m] biased exponents of op(A) rows
   const int* eB;  // [batch][n] biased exponents of op(B) columns
   zd* C;
@@ -142,47 +145,55 @@ __device__ __forceinline__ double fix_to_double(long long v, int e) {
   return __longlong_as_double(bits + ((long long)e << 52));
 }
 
-// Pipeline depth for an N tile: as many stages (Bt tile + two At tiles) as fit in 227 KB of shared
-// memory next to the 1 KB alignment pad and the barriers, at most 8.
-__host__ __device__ constexpr int stages_for(int nt) {
-  return (227 * 1024 - 1024 - 256) / (kTileM * 128 + 2 * nt * 128) < 8
-             ? (227 * 1024 - 1024 - 256) / (kTileM * 128 + 2 * nt * 128)
+// Pipeline depth for an N tile: as many stages as fit in 227 KB of shared memory next to the
+// 1 KB alignment pad and the barriers, at most 8.  A stage holds the Bt tile (128 rows) and the At
+// rows of this CTA: both At tiles of a dual job on one CTA, one of them on each CTA of a pair.
+__host__ __device__ constexpr int stage_bytes_for(int nt, int pair) {
+  return kTileM * 128 + (pair ? 1 : 2) * nt * 128;
+}
+__host__ __device__ constexpr int stages_for(int nt, int pair) {
+  return (227 * 1024 - 1024 - 256) / stage_bytes_for(nt, pair) < 8
+             ? (227 * 1024 - 1024 - 256) / stage_bytes_for(nt, pair)
              : 8;
 }
-__host__ __device__ constexpr size_t smem_for(int nt) {
-  return 1024 + (size_t)stages_for(nt) * (kTileM * 128 + 2 * nt * 128) + 256;
+__host__ __device__ constexpr size_t smem_for(int nt, int pair) {
+  return 1024 + (size_t)stages_for(nt, pair) * stage_bytes_for(nt, pair) + 256;
 }
 
-// Tile t of a batched launch -> (rows of C^T, rows of C, batch entry); false for inactive entries.
-__device__ __forceinline__ bool tile_coords(const MmaParams& p, int nt, int tile, int& m0, int& n0, int& b) {
-  const int per_b = p.tiles_x * p.tiles_y;
-  b = tile / per_b;
-  const int r = tile - b * per_b;
-  const int ty = r / p.tiles_x;
-  m0 = (r - ty * p.tiles_x) * kTileM;
+// Work unit u of a batched launch -> (rows of C^T, rows of C, batch entry) of this CTA; false for
+// inactive entries.  One CTA: a unit is one 128 x NT tile.  A CTA pair: a unit is two M tiles
+// (rows m0 and m0 + 128 of C^T, one per CTA of the pair) of the same N tile.
+__device__ __forceinline__ bool unit_coords(const MmaParams& p, int nt, int u, int rank, int& m0, int& n0, int& b) {
+  const int per_b = p.tiles_xu * p.tiles_y;
+  b = u / per_b;
+  const int r = u - b * per_b;
+  const int ty = r / p.tiles_xu;
+  const int tx = r - ty * p.tiles_xu;
+  m0 = (p.pair ? 2 * tx + rank : tx) * kTileM;
   n0 = ty * nt;
   return !p.active || p.active[b] != 0;
 }
 
-template <int NT>
+template <int NT, int PAIR>
 __global__ void __launch_bounds__(kThreads, 1)
     split_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                     const MmaParams p) {
+                     const __grid_constant__ CUtensorMap tmBh, const MmaParams p) {
   constexpr int kABytes = kTileM * 128;
   constexpr int kBBytes = NT * 128;
-  constexpr int kStages = stages_for(NT);
+  constexpr int kStages = stages_for(NT, PAIR);
+  constexpr int kStageBytes = stage_bytes_for(NT, PAIR);
   constexpr int kCols = NT / 4;   // accumulator columns per epilogue thread
   constexpr int kBatch = kCols % 8 == 0 ? 8 : 4;  // columns per tcgen05.ld wait
   constexpr int kWB = 4;  // outputs per write chunk (kCols is a multiple of 4)
   static_assert(NT % 16 == 0 && NT >= 16 && NT <= 256, "UMMA N");
   static_assert(4 * NT <= 512, "two double-buffered accumulator pairs must fit in TMEM");
-  constexpr uint32_t kIdesc = ptx::idesc_bf16_f32(kTileM, NT);
-  constexpr uint32_t kIdesc2 = ptx::idesc_bf16_f32(kTileM, 2 * NT);
+  // one CTA: M = 128; a pair: M = 256, rows 0..127 in the leader (rank 0), 128..255 in its peer
+  constexpr uint32_t kIdesc = ptx::idesc_bf16_f32(PAIR ? 2 * kTileM : kTileM, NT);
+  constexpr uint32_t kIdesc2 = ptx::idesc_bf16_f32(PAIR ? 2 * kTileM : kTileM, 2 * NT);
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
-  // stage: Bt tile (A operand) + two At tiles (B operands of the two lanes of a dual job)
-  constexpr int kStageBytes = kABytes + 2 * kBBytes;
+  // stage: Bt tile (A operand) + the At rows of this CTA (B operand)
   uint8_t* stages = smem;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
   uint64_t* empty = full + kStages;
@@ -193,6 +204,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rank = PAIR ? (int)ptx::cluster_ctarank() : 0;
+  const bool leader = rank == 0;
+  const int cta_unit0 = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;  // first unit of this CTA
+  const int unit_step = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -201,61 +216,93 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int a = 0; a < 2; ++a) {
       ptx::mbar_init(&tfull[a], 1);
-      ptx::mbar_init(&tempty[a], kEpiWarps);
+      // the leader's MMA reuses an accumulator once the epilogues of both CTAs drained it
+      ptx::mbar_init(&tempty[a], PAIR ? 2 * kEpiWarps : kEpiWarps);
     }
     ptx::mbar_init(drain, 1);
     *abort_flag = 0;
     ptx::fence_barrier_init();
   }
   if (warp == 1) {
-    ptx::tmem_alloc(tmem_slot, 512);
-    ptx::tmem_relinquish();
+    if constexpr (PAIR) {
+      ptx::tmem_alloc_pair(tmem_slot, 512);
+      ptx::tmem_relinquish_pair();
+    } else {
+      ptx::tmem_alloc(tmem_slot, 512);
+      ptx::tmem_relinquish();
+    }
   }
   ptx::tc_fence_before();
-  __syncthreads();
+  // a pair: the peer's barriers and tensor memory exist before any copy or MMA targets them
+  // (the cluster barrier is warp-aligned: every warp arrives converged)
+  if constexpr (PAIR) {
+    __syncwarp();
+    ptx::cluster_sync_all();
+  } else {
+    __syncthreads();
+  }
   ptx::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
   const Schedule& sc = p.sched;
-  // every role walks the same tiles in the same order and skips the same inactive entries
+  // every role of both CTAs walks the same units in the same order and skips the same entries
   auto fail = [&](int b) {
     *abort_flag = 1;
+    if constexpr (PAIR) {  // stop the peer too (its shared memory lives until the final barrier)
+      const uint32_t peer = ptx::mapa_shared(ptx::smem_u32((const void*)abort_flag), (uint32_t)(rank ^ 1));
+      asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(peer), "r"(1) : "memory");
+    }
     if (p.err) atomicCAS(&p.err[(long long)b * p.err_stride], 0, (int)BT_ERR_TIMEOUT);
+  };
+  auto wait = [&](uint64_t* bar, uint32_t parity) {
+    if constexpr (PAIR) return ptx::mbar_wait_bounded_cluster(bar, parity, abort_flag, kWaitLimitNs);
+    else return ptx::mbar_wait_bounded(bar, parity, abort_flag, kWaitLimitNs);
   };
 
   if (warp == 0) {
-    // ---------------- TMA producer ----------------
+    // ---------------- TMA producer (each CTA loads its own rows) ----------------
     if (lane == 0) {
       ptx::prefetch_tensormap(&tmA);
       ptx::prefetch_tensormap(&tmB);
+      if constexpr (PAIR) ptx::prefetch_tensormap(&tmBh);
       int stage = 0;
       uint32_t phase = 0;
       int issued = 0;
       bool ok = true;
       long long t_empty = 0;
-      for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
+      for (int u = cta_unit0; u < p.n_units && ok; u += unit_step) {
         int m0, n0, b;
-        if (!tile_coords(p, NT, tile, m0, n0, b)) continue;
+        if (!unit_coords(p, NT, u, rank, m0, n0, b)) continue;
         const int zA = (p.b_shared ? 0 : b) * p.S - 1, zB = (p.a_shared ? 0 : b) * p.S - 1;
         for (int g = 0; g < sc.n_jobs && ok; ++g) {
           const bool dual = sc.dual[g] != 0;
-          const uint32_t bytes = (uint32_t)(kABytes + (dual ? 2 : 1) * kBBytes);
+          // bytes landing in this CTA per stage; a pair's leader expects both CTAs' bytes
+          const uint32_t own = (uint32_t)(kABytes + (PAIR ? (dual ? kBBytes : kBBytes / 2)
+                                                          : (dual ? 2 : 1) * kBBytes));
           const int ie = sc.ie[g], kb0 = sc.kb0[g], kb1 = sc.kb1[g];
           for (int it = sc.ib[g]; it < ie && ok; ++it) {
             const int ct = zA + sc.t[it], cs = zB + sc.s[it], cs2 = zB + sc.s2[it];
             for (int kb = kb0; kb < kb1; ++kb) {
               const long long c0 = p.prof ? clock64() : 0;
-              if (!ptx::mbar_wait_bounded(&empty[stage], phase ^ 1u, abort_flag, kWaitLimitNs)) {
+              if (!wait(&empty[stage], phase ^ 1u)) {
                 fail(b);
                 ok = false;
                 break;
               }
               if (p.prof) t_empty += clock64() - c0;
               uint8_t* st = stages + stage * kStageBytes;
-              ptx::mbar_arrive_expect_tx(&full[stage], bytes);
-              ptx::tma_load_3d(st, &tmA, &full[stage], kb * kKBlock, m0, ct);
-              ptx::tma_load_3d(st + kABytes, &tmB, &full[stage], kb * kKBlock, n0, cs);
-              if (dual) ptx::tma_load_3d(st + kABytes + kBBytes, &tmB, &full[stage], kb * kKBlock, n0, cs2);
+              if constexpr (PAIR) {
+                const uint32_t fb = ptx::mapa_shared(ptx::smem_u32(&full[stage]), 0u);  // the leader's
+                if (leader) ptx::mbar_arrive_expect_tx(&full[stage], 2u * own);
+                ptx::tma_load_3d_pair(st, &tmA, fb, kb * kKBlock, m0, ct);
+                if (dual) ptx::tma_load_3d_pair(st + kABytes, &tmB, fb, kb * kKBlock, n0, leader ? cs : cs2);
+                else ptx::tma_load_3d_pair(st + kABytes, &tmBh, fb, kb * kKBlock, n0 + rank * (NT / 2), cs);
+              } else {
+                ptx::mbar_arrive_expect_tx(&full[stage], own);
+                ptx::tma_load_3d(st, &tmA, &full[stage], kb * kKBlock, m0, ct);
+                ptx::tma_load_3d(st + kABytes, &tmB, &full[stage], kb * kKBlock, n0, cs);
+                if (dual) ptx::tma_load_3d(st + kABytes + kBBytes, &tmB, &full[stage], kb * kKBlock, n0, cs2);
+              }
               ++issued;
               if (++stage == kStages) { stage = 0; phase ^= 1u; }
             }
@@ -264,27 +311,34 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (p.prof) atomicAdd(&p.prof[kProfTmaWaitEmpty], (unsigned long long)t_empty);
       if (*abort_flag) {
-        // let the loads already in flight land before the CTA exits (bounded)
+        // let the loads already in flight land before the CTA exits (bounded): one CTA waits for
+        // its last stages' barriers; a pair's copies signal the leader, so both wait a while
         volatile int never = 0;
-        for (int idx = issued > kStages ? issued - kStages : 0; idx < issued; ++idx)
-          ptx::mbar_wait_bounded(&full[idx % kStages], (uint32_t)((idx / kStages) & 1), &never, kWaitLimitNs);
+        if (!PAIR) {
+          for (int idx = issued > kStages ? issued - kStages : 0; idx < issued; ++idx)
+            ptx::mbar_wait_bounded(&full[idx % kStages], (uint32_t)((idx / kStages) & 1), &never, kWaitLimitNs);
+        } else {
+          const uint64_t t0 = ptx::globaltimer_ns();
+          while (ptx::globaltimer_ns() - t0 < 2000000ull && !never) {
+          }
+        }
       }
     }
   } else if (warp == 1) {
-    // ---------------- MMA issuer ----------------
-    if (lane == 0) {
+    // ---------------- MMA issuer (one CTA's, or the pair leader's) ----------------
+    if (lane == 0 && leader) {
       int stage = 0;
       uint32_t phase = 0;
-      uint32_t gc = 0;  // jobs started so far (all tiles)
+      uint32_t gc = 0;  // jobs started so far (all units)
       bool ok = true;
       long long t_full = 0, t_acc = 0, tiles = 0;
       const long long t_loop0 = p.prof ? clock64() : 0;
       if (p.stall_ns) {
         // test hook: wait on `drain`, which nothing completes before the commit below, so the
         // bounded wait expires and the CTA takes its timeout path (abort, drain, free TMEM)
-        for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) {
+        for (int u = cta_unit0; u < p.n_units; u += unit_step) {
           int m0, n0, b;
-          if (!tile_coords(p, NT, tile, m0, n0, b)) continue;
+          if (!unit_coords(p, NT, u, rank, m0, n0, b)) continue;
           if (!ptx::mbar_wait_bounded(drain, 0, abort_flag, p.stall_ns)) {
             fail(b);
             ok = false;
@@ -292,14 +346,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
       }
-      for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
+      for (int u = cta_unit0; u < p.n_units && ok; u += unit_step) {
         int m0, n0, b;
-        if (!tile_coords(p, NT, tile, m0, n0, b)) continue;
+        if (!unit_coords(p, NT, u, rank, m0, n0, b)) continue;
         ++tiles;
         for (int g = 0; g < sc.n_jobs && ok; ++g, ++gc) {
           const uint32_t ab = gc & 1u;
           const long long ca = p.prof ? clock64() : 0;
-          if (gc >= 2 && !ptx::mbar_wait_bounded(&tempty[ab], ((gc >> 1) - 1u) & 1u, abort_flag, kWaitLimitNs)) {
+          if (gc >= 2 && !wait(&tempty[ab], ((gc >> 1) - 1u) & 1u)) {
             fail(b);
             ok = false;
             break;
@@ -313,7 +367,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int it = sc.ib[g]; it < ie && ok; ++it) {
             for (int kb = kb0; kb < kb1; ++kb) {
               const long long cf = p.prof ? clock64() : 0;
-              if (!ptx::mbar_wait_bounded(&full[stage], phase, abort_flag, kWaitLimitNs)) {
+              if (!wait(&full[stage], phase)) {
                 fail(b);
                 ok = false;
                 break;
@@ -322,25 +376,34 @@ __global__ void __launch_bounds__(kThreads, 1)
               ptx::tc_fence_after();
               const uint32_t a_addr = ptx::smem_u32(stages + stage * kStageBytes);
               const uint32_t b_addr = a_addr + kABytes;
-              // a dual job's two At tiles are contiguous (rows of one 2NT-row operand) and its two
-              // accumulators adjacent in TMEM: one M = 128, N = 2 NT MMA per K step reads the Bt
-              // tile once for both lanes
+              // a dual job's two At tiles form one 2NT-row B operand (side by side in this CTA's
+              // stage, or one per CTA of a pair) and its two accumulators sit side by side in
+              // TMEM: one MMA with N = 2 NT per K step reads the Bt tile once for both lanes
               const uint32_t idesc = dual ? kIdesc2 : kIdesc;
 #pragma unroll
-              for (int k = 0; k < kKBlock / 16; ++k)
-                ptx::umma_f16(dcol0, ptx::sdesc_kmajor_sw128(a_addr + k * 32),
-                              ptx::sdesc_kmajor_sw128(b_addr + k * 32), idesc, k == 0 ? acc0 : 1u);
-
+              for (int k = 0; k < kKBlock / 16; ++k) {
+                if constexpr (PAIR)
+                  ptx::umma_f16_pair(dcol0, ptx::sdesc_kmajor_sw128(a_addr + k * 32),
+                                     ptx::sdesc_kmajor_sw128(b_addr + k * 32), idesc, k == 0 ? acc0 : 1u);
+                else
+                  ptx::umma_f16(dcol0, ptx::sdesc_kmajor_sw128(a_addr + k * 32),
+                                ptx::sdesc_kmajor_sw128(b_addr + k * 32), idesc, k == 0 ? acc0 : 1u);
+              }
               acc0 = 1u;
-              ptx::umma_commit(&empty[stage]);
+              if constexpr (PAIR) ptx::umma_commit_pair_mc(&empty[stage], (uint16_t)0x3);
+              else ptx::umma_commit(&empty[stage]);
               if (++stage == kStages) { stage = 0; phase ^= 1u; }
             }
           }
-          if (ok) ptx::umma_commit(&tfull[ab]);
+          if (ok) {
+            if constexpr (PAIR) ptx::umma_commit_pair_mc(&tfull[ab], (uint16_t)0x3);
+            else ptx::umma_commit(&tfull[ab]);
+          }
         }
       }
       // every MMA this thread issued has completed once `drain` fires
-      ptx::umma_commit(drain);
+      if constexpr (PAIR) ptx::umma_commit_pair_mc(drain, (uint16_t)0x1);
+      else ptx::umma_commit(drain);
       volatile int never = 0;
       ptx::mbar_wait_bounded(drain, 0, &never, kWaitLimitNs);
       if (p.prof) {
@@ -351,7 +414,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {
-    // ---------------- epilogue: TMEM -> uint64 fixed point -> C ----------------
+    // ---------------- epilogue: TMEM -> uint64 fixed point -> C (each CTA its own rows) ----------
     const int ew = warp - 2;
     const int q = warp & 3;  // TMEM lanes [32q, 32q+32) are accessible to this warp
     const int cq = ew >> 2;  // column quarter
@@ -359,15 +422,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t gc = 0;
     bool ok = true;
     long long t_drain = 0, t_write = 0;
-    for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
+    for (int u = cta_unit0; u < p.n_units && ok; u += unit_step) {
       int m0, n0, b;
-      if (!tile_coords(p, NT, tile, m0, n0, b)) continue;
+      if (!unit_coords(p, NT, u, rank, m0, n0, b)) continue;
       unsigned long long acc[kCols];
 #pragma unroll
       for (int c = 0; c < kCols; ++c) acc[c] = 0ull;
       for (int g = 0; g < sc.n_jobs; ++g, ++gc) {
         const uint32_t ab = gc & 1u;
-        const bool got = ptx::mbar_wait_bounded(&tfull[ab], (gc >> 1) & 1u, abort_flag, kWaitLimitNs);
+        const bool got = wait(&tfull[ab], (gc >> 1) & 1u);
         // the warp-collective tcgen05.ld below needs every lane: one lane's timeout stops the warp
         if (!__all_sync(0xffffffffu, got)) {
           if (!got) fail(b);
@@ -404,7 +467,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         ptx::tc_fence_before();
         __syncwarp();
-        if (lane == 0) ptx::mbar_arrive(&tempty[ab]);
+        if (lane == 0) {
+          if constexpr (PAIR) ptx::mbar_arrive_remote(ptx::mapa_shared(ptx::smem_u32(&tempty[ab]), 0u));
+          else ptx::mbar_arrive(&tempty[ab]);
+        }
         if (p.prof) t_drain += clock64() - cd;
       }
       if (!ok) break;
@@ -484,10 +550,23 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   // ---------------- teardown ----------------
   ptx::tc_fence_before();
-  __syncthreads();
-  if (warp == 1) {
-    ptx::tc_fence_after();
-    ptx::tmem_dealloc(tmem, 512);
+  if constexpr (PAIR) {
+    // the leader's MMAs write the peer's tensor memory and its commits signal the peer's
+    // barriers: both CTAs are done with both before either frees its tensor memory
+    __syncwarp();
+    ptx::cluster_sync_all();
+    if (warp == 1) {
+      ptx::tc_fence_after();
+      ptx::tmem_dealloc_pair(tmem, 512);
+    }
+    __syncwarp();
+    ptx::cluster_sync_all();  // no CTA leaves while its peer may still address its shared memory
+  } else {
+    __syncthreads();
+    if (warp == 1) {
+      ptx::tc_fence_after();
+      ptx::tmem_dealloc(tmem, 512);
+    }
   }
 }
 
@@ -835,9 +914,43 @@ int num_sms() {
   return sms[dev];
 }
 
+// Clusters of two CTAs of the pair kernel that can be resident at once (per device and N tile).
 template <int NT>
-bt_status launch_mma(cudaStream_t st, const CUtensorMap& mA, const CUtensorMap& mB, const MmaParams& p) {
-  const size_t smem = smem_for(NT);
+int pair_clusters() {
+  static std::mutex mu;
+  static int val[64];
+  static bool done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return val[dev];
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem_for(NT, 1);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nc = 0;
+  if (cudaFuncSetAttribute(split_mma_kernel<NT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem_for(NT, 1)) != cudaSuccess ||
+      cudaOccupancyMaxActiveClusters(&nc, split_mma_kernel<NT, 1>, &cfg) != cudaSuccess) {
+    (void)cudaGetLastError();
+    nc = 0;
+  }
+  val[dev] = nc;
+  done[dev] = true;
+  return nc;
+}
+
+template <int NT, int PAIR>
+bt_status launch_mma(cudaStream_t st, const CUtensorMap& mA, const CUtensorMap& mB, const CUtensorMap& mBh,
+                     const MmaParams& p) {
+  const size_t smem = smem_for(NT, PAIR);
   // per-function device state: set once per device (the value never changes for one NT)
   static std::mutex mu;
   static bool attr_set[64] = {};
@@ -846,35 +959,75 @@ bt_status launch_mma(cudaStream_t st, const CUtensorMap& mA, const CUtensorMap& 
   {
     std::lock_guard<std::mutex> lock(mu);
     if (!attr_set[dev]) {
-      if (cudaFuncSetAttribute(split_mma_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-          cudaSuccess)
+      if (cudaFuncSetAttribute(split_mma_kernel<NT, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem) != cudaSuccess)
         return BT_ERR_CUDA;
       attr_set[dev] = true;
     }
   }
   const int sms = num_sms();
   if (sms <= 0) return BT_ERR_CUDA;
-  // persistent: one CTA per SM (1 CTA fits per SM by shared memory), tiles walked in order
-  const int grid = p.n_tiles < sms ? p.n_tiles : sms;
-  split_mma_kernel<NT><<<grid, kThreads, smem, st>>>(mA, mB, p);
+  if constexpr (PAIR) {
+    // persistent: as many CTA pairs as can be resident, units walked in order
+    const int nc = pair_clusters<NT>();
+    if (nc <= 0) return BT_ERR_UNSUPPORTED;
+    const int clusters = p.n_units < nc ? p.n_units : nc;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(2 * clusters));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    BT_CUDA_TRY(cudaLaunchKernelEx(&cfg, split_mma_kernel<NT, 1>, mA, mB, mBh, p));
+  } else {
+    // persistent: one CTA per SM (1 CTA fits per SM by shared memory), tiles walked in order
+    const int grid = p.n_units < sms ? p.n_units : sms;
+    split_mma_kernel<NT, 0><<<grid, kThreads, smem, st>>>(mA, mB, mBh, p);
+  }
   count_launch();
   BT_CUDA_TRY(cudaGetLastError());
   return BT_OK;
 }
 
-bt_status launch_mma_nt(int nt, cudaStream_t st, const CUtensorMap& mA, const CUtensorMap& mB, const MmaParams& p) {
+template <int PAIR>
+bt_status launch_mma_nt(int nt, cudaStream_t st, const CUtensorMap& mA, const CUtensorMap& mB,
+                        const CUtensorMap& mBh, const MmaParams& p) {
   switch (nt) {
-    case 16: return launch_mma<16>(st, mA, mB, p);
-    case 32: return launch_mma<32>(st, mA, mB, p);
-    case 48: return launch_mma<48>(st, mA, mB, p);
-    case 64: return launch_mma<64>(st, mA, mB, p);
-    case 80: return launch_mma<80>(st, mA, mB, p);
-    case 96: return launch_mma<96>(st, mA, mB, p);
-    case 112: return launch_mma<112>(st, mA, mB, p);
-    case 128: return launch_mma<128>(st, mA, mB, p);
+    case 16: return launch_mma<16, PAIR>(st, mA, mB, mBh, p);
+    case 32: return launch_mma<32, PAIR>(st, mA, mB, mBh, p);
+    case 48: return launch_mma<48, PAIR>(st, mA, mB, mBh, p);
+    case 64: return launch_mma<64, PAIR>(st, mA, mB, mBh, p);
+    case 80: return launch_mma<80, PAIR>(st, mA, mB, mBh, p);
+    case 96: return launch_mma<96, PAIR>(st, mA, mB, mBh, p);
+    case 112: return launch_mma<112, PAIR>(st, mA, mB, mBh, p);
+    case 128: return launch_mma<128, PAIR>(st, mA, mB, mBh, p);
     default: return BT_ERR_UNSUPPORTED;
   }
 }
+
+int pair_clusters_nt(int nt) {
+  switch (nt) {
+    case 16: return pair_clusters<16>();
+    case 32: return pair_clusters<32>();
+    case 48: return pair_clusters<48>();
+    case 64: return pair_clusters<64>();
+    case 80: return pair_clusters<80>();
+    case 96: return pair_clusters<96>();
+    case 112: return pair_clusters<112>();
+    case 128: return pair_clusters<128>();
+    default: return 0;
+  }
+}
+
+// CTA-pair mode (bt_debug_split_pair): 0 = the default rule, 1 = one CTA per tile always,
+// 2 = pairs whenever the shape allows them
+std::atomic<int> g_pair_mode{0};
 
 constexpr int kMaxKc = 1024;  // complex k per launch (slice workspace); K' = 2k <= 2048 = 32 K blocks
 
@@ -944,17 +1097,31 @@ bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A,
                               w.At, ba, act_a));
     BT_TRY(slice_lines<true>(st, bop.op == BT_OP_C, n, n2p / 2, kc, Kp / 2, bop.p, bop.ld, bop.stride,
                              bop.op == BT_OP_C, S, w.eB, w.Bt, bb, act_b));
-    CUtensorMap mA, mB;
+    // CTA pairs (cta_group::2: two M tiles share each At tile, half of it in each CTA) when the
+    // 2n rows of C^T span at least two M tiles and the device holds most of its SMs as pairs
+    const int tiles_x = n2p / kTileM;
+    const int mode = g_pair_mode.load();
+    bool pair = false;
+    if (mode == 2 && tiles_x >= 2) {
+      const int nc = pair_clusters_nt(nt);
+      pair = nc > 0 && 2 * nc >= (num_sms() * 9) / 10;
+    }
+    CUtensorMap mA, mB, mBh;
     if (!encode_slices_map(&mA, w.Bt, Kp, 2 * n, n2p, batch * S, kTileM)) return BT_ERR_CUDA;
     if (!encode_slices_map(&mB, w.At, Kp, m, mp, batch * S, nt)) return BT_ERR_CUDA;
+    // pairs: a single job's At tile is split in halves, one per CTA
+    if (!encode_slices_map(&mBh, w.At, Kp, m, mp, batch * S, pair ? nt / 2 : nt)) return BT_ERR_CUDA;
     MmaParams p{};
     p.m = m;
     p.n2 = 2 * n;
     p.Kp = Kp;
     p.S = S;
-    p.tiles_x = n2p / kTileM;
+    p.tiles_x = tiles_x;
     p.tiles_y = mp / nt;
     p.n_tiles = p.tiles_x * p.tiles_y * batch;
+    p.pair = pair ? 1 : 0;
+    p.tiles_xu = pair ? (tiles_x + 1) / 2 : tiles_x;
+    p.n_units = p.tiles_xu * p.tiles_y * batch;
     p.eA = w.eA;
     p.eB = w.eB;
     p.C = C;
@@ -976,7 +1143,8 @@ bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A,
     p.a_shared = a_shared ? 1 : 0;
     p.b_shared = b_shared ? 1 : 0;
     if (!make_schedule(S, Kp / kKBlock, &p.sched, &p.bias, &p.fix_bits)) return BT_ERR_UNSUPPORTED;
-    BT_TRY(launch_mma_nt(nt, st, mA, mB, p));
+    if (pair) BT_TRY(launch_mma_nt<1>(nt, st, mA, mB, mBh, p));
+    else BT_TRY(launch_mma_nt<0>(nt, st, mA, mB, mBh, p));
   }
   return BT_OK;
 }
@@ -1006,6 +1174,8 @@ extern "C" bt_status bt_debug_split_profile(int enable, unsigned long long* coun
     for (int i = 0; i < n_counters && i < bt::kProfSlots; ++i) counters[i] = h[i];
   return BT_OK;
 }
+
+extern "C" void bt_debug_split_pair(int mode) { bt::g_pair_mode.store(mode == 1 || mode == 2 ? mode : 0); }
 
 extern "C" void bt_debug_split_stall(unsigned long long ns, long long launches) {
   bt::g_stall_left.store(launches);

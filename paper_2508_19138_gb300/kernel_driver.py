@@ -37,6 +37,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=2, help="steptrace: untraced steps first")
     ap.add_argument("--cache-config", type=int, default=-1,
                     help="preferred L1 / shared split for the run (0 none, 1 shared, 2 L1, 3 equal; -1 untouched)")
+    ap.add_argument("--split-pair", type=int, default=0,
+                    help="split: 1 = single CTAs, 2 = CTA pairs (cta_group::2), 0 = default; with --check both")
+    ap.add_argument("--check", action="store_true",
+                    help="split: compare the result of single CTAs and CTA pairs bitwise, and with torch")
     ap.add_argument("--split-profile", action="store_true",
                     help="split: also report the GEMM's wait counters (bt_debug_split_profile)")
     ap.add_argument("--panel-cluster", type=int, default=0,
@@ -75,6 +79,25 @@ def main():
         ws = torch.empty(max(1, pkg.bt_zinv_workspace_bytes(n, b)), dtype=torch.uint8, device="cuda")
     Ainv = A.clone()
 
+    if a.kernel == "split" and a.split_pair:
+        pkg.bt_debug_split_pair(a.split_pair)
+    check = None
+    if a.kernel == "split" and a.check:
+        outs = {}
+        for mode in (1, 2):
+            pkg.bt_debug_split_pair(mode)
+            C.zero_()
+            pkg.bt_split_zgemm_batched(n, n, kk, 1.0, A, kk, n * kk, 0, B, n, kk * n, 0, 0.0, C, n, n * n, b,
+                                       a.slices, workspace=ws)
+            torch.cuda.synchronize()
+            outs[mode] = C.clone()
+        ref = torch.matmul(A, B)
+        rel = (torch.linalg.norm(outs[2] - ref) / torch.linalg.norm(ref)).item()
+        check = {"bitwise_equal": bool(torch.equal(outs[1], outs[2])),
+                 "max_abs_diff": (outs[1] - outs[2]).abs().max().item(), "rel_err_vs_torch_pair": rel,
+                 "rel_err_vs_torch_single": (torch.linalg.norm(outs[1] - ref) / torch.linalg.norm(ref)).item()}
+        pkg.bt_debug_split_pair(a.split_pair)
+
     def run():
         if a.kernel == "zgemm":
             pkg.bt_zgemm_batched(n, n, kk, 1.0, A, kk, n * kk, 0, B, n, kk * n, 0, 0.0, C, n, n * n, b)
@@ -107,7 +130,8 @@ def main():
     flops = 8.0 * n * n * kk * b
     print(json.dumps({"kernel": a.kernel, "bs": n, "k": kk, "batch": b, "ms": ms, "fp64_eq_tflops": flops / ms / 1e9,
                       "slices": a.slices if a.kernel == "split" else None,
-                      "panel_cluster": a.panel_cluster if a.kernel == "zinv" else None, "split_profile": prof}))
+                      "panel_cluster": a.panel_cluster if a.kernel == "zinv" else None, "split_profile": prof,
+                      "split_pair": a.split_pair if a.kernel == "split" else None, "check": check}))
 
 
 def conv_flops(L):
