@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int kBBytes = NT * 128;
   constexpr int kStages = stages_for(NT, PAIR);
   constexpr int kStageBytes = stage_bytes_for(NT, PAIR);
-  constexpr int kCols = NT / 4;   // accumulator columns per epilogue thread
+  constexpr int kCols = NT / (kEpiWarps / 4);  // accumulator columns per epilogue thread
   constexpr int kBatch = kCols % 8 == 0 ? 8 : 4;  // columns per tcgen05.ld wait
   constexpr int kWB = 4;  // outputs per write chunk (kCols is a multiple of 4)
   static_assert(NT % 16 == 0 && NT >= 16 && NT <= 256, "UMMA N");
@@ -380,14 +380,15 @@ __global__ void __launch_bounds__(kThreads, 1)
               // stage, or one per CTA of a pair) and its two accumulators sit side by side in
               // TMEM: one MMA with N = 2 NT per K step reads the Bt tile once for both lanes
               const uint32_t idesc = dual ? kIdesc2 : kIdesc;
+              // K step k starts 32 bytes further: +2 in the descriptor's address field (units of
+              // 16 bytes; stage addresses are below 256 KB, so the field cannot carry over)
+              const uint64_t ad = ptx::sdesc_kmajor_sw128(a_addr), bd = ptx::sdesc_kmajor_sw128(b_addr);
 #pragma unroll
               for (int k = 0; k < kKBlock / 16; ++k) {
                 if constexpr (PAIR)
-                  ptx::umma_f16_pair(dcol0, ptx::sdesc_kmajor_sw128(a_addr + k * 32),
-                                     ptx::sdesc_kmajor_sw128(b_addr + k * 32), idesc, k == 0 ? acc0 : 1u);
+                  ptx::umma_f16_pair(dcol0, ad + 2u * k, bd + 2u * k, idesc, k == 0 ? acc0 : 1u);
                 else
-                  ptx::umma_f16(dcol0, ptx::sdesc_kmajor_sw128(a_addr + k * 32),
-                                ptx::sdesc_kmajor_sw128(b_addr + k * 32), idesc, k == 0 ? acc0 : 1u);
+                  ptx::umma_f16(dcol0, ad + 2u * k, bd + 2u * k, idesc, k == 0 ? acc0 : 1u);
               }
               acc0 = 1u;
               if constexpr (PAIR) ptx::umma_commit_pair_mc(&empty[stage], (uint16_t)0x3);
