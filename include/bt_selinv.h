@@ -445,6 +445,13 @@ BT_API bt_status bt_debug_cache_config(int config);
  * Process-wide, read when a launch is issued. */
 BT_API void bt_debug_split_pair(int mode);
 
+/* Measurement aid (no counterpart in the paper): the busy fraction of the tensor pipe when one
+ * thread per SM issues tcgen05.mma (M = 128, N = 224, K = 16; four per 64-deep K block and a
+ * commit, the GEMM's pattern) on operands already in shared memory, while busy_warps (0..16)
+ * other warps of the CTA run multiply-add chains and, with wait != 0, an already-completed
+ * mbarrier is waited on before each K block.  One launch on all SMs, timed with the SM clock. */
+BT_API bt_status bt_debug_mma_issue_rate(int busy_warps, int wait, double* frac, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,7 +17,7 @@ __all__ = [
     "bt_selinv_solve", "bt_selinv_solve_host", "bt_selinv_destroy", "bt_selinv_last_error", "bt_selinv_get_stats",
     "bt_zgemm_batched", "bt_split_zgemm_workspace_bytes", "bt_split_zgemm_batched", "bt_zinv_workspace_bytes",
     "bt_zinv_batched", "bt_zinv_batched_noalloc", "bt_decimate_workspace_bytes", "bt_decimate_batched", "library",
-    "bt_debug_split_stall", "bt_debug_fp64_rate", "bt_debug_panel_cluster", "bt_debug_split_profile", "bt_debug_cache_config", "bt_debug_split_pair", "bt_energy_convolve",
+    "bt_debug_split_stall", "bt_debug_fp64_rate", "bt_debug_panel_cluster", "bt_debug_split_profile", "bt_debug_cache_config", "bt_debug_split_pair", "bt_debug_mma_issue_rate", "bt_energy_convolve",
 ]
 
 
@@ -291,6 +291,15 @@ def bt_debug_split_profile(enable: bool):
     buf = (C.c_ulonglong * len(SPLIT_PROFILE_SLOTS))()
     _check(N.load().bt_debug_split_profile(1 if enable else 0, buf, len(SPLIT_PROFILE_SLOTS)), None, "split_profile")
     return None if enable else dict(zip(SPLIT_PROFILE_SLOTS, [int(v) for v in buf]))
+
+
+def bt_debug_mma_issue_rate(busy_warps: int, wait: bool = False, stream=None) -> float:
+    """Measurement aid: tensor-pipe busy fraction of one MMA-issuing thread per SM next to
+    busy_warps warps of multiply-add chains (wait: a ring-stage wait per K block)."""
+    f = C.c_double(0.0)
+    _check(N.load().bt_debug_mma_issue_rate(int(busy_warps), 1 if wait else 0, C.byref(f), _stream(stream)), None,
+           "mma_issue_rate")
+    return f.value
 
 
 def bt_debug_split_pair(mode: int) -> None:

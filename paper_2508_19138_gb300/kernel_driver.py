@@ -7,6 +7,7 @@
     python -m paper_2508_19138_gb300.kernel_driver --kernel conv --bs 416 --batch 512    # energy convolution of
         # the bs^2 element series of one diagonal block over `batch` energies (na = nb = batch)
     python -m paper_2508_19138_gb300.kernel_driver --kernel fp64rate --reps 4   # DFMA vs DMMA (FP64 tensor) rates
+    python -m paper_2508_19138_gb300.kernel_driver --kernel mmaissue   # tcgen05.mma issue rate next to busy warps
     python -m paper_2508_19138_gb300.kernel_driver --kernel steptrace --precision split --split-scope 1 --batch 32
         # launch list of one solve step of the 40 x 416 nanoribbon (`batch` energies) from CUPTI
         # activity records (csrc/launch_trace.cpp): kernels, launches, device time, share
@@ -24,7 +25,8 @@ def main():
 
     import paper_2508_19138_gb300 as pkg
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kernel", choices=["zgemm", "split", "zinv", "cublas", "conv", "fp64rate", "steptrace"],
+    ap.add_argument("--kernel", choices=["zgemm", "split", "zinv", "cublas", "conv", "fp64rate", "steptrace",
+                                                 "mmaissue"],
                     required=True)
     ap.add_argument("--bs", type=int, default=416)
     ap.add_argument("--batch", type=int, default=32)
@@ -57,6 +59,11 @@ def main():
         return conv_driver(a, pkg)
     if a.kernel == "steptrace":
         return step_trace(a, pkg)
+    if a.kernel == "mmaissue":
+        rows = [{"busy_warps": bw, "wait": wt, "tensor_busy": pkg.bt_debug_mma_issue_rate(bw, wt)}
+                for wt in (False, True) for bw in (0, 4, 8, 16)]
+        print(json.dumps({"kernel": "mmaissue", "rows": rows}))
+        return None
     if a.kernel == "fp64rate":
         out = {"kernel": "fp64rate"}
         for which, name in ((0, "dfma"), (1, "dmma")):
