@@ -120,7 +120,7 @@ struct MmaParams {
   unsigned long long stall_ns;  // test hook: the MMA warp first waits this long on a barrier
                                 // that nothing completes (0: off)
   unsigned long long* prof;     // measurement hook (may be null): SM clock cycles accumulated
-                                // over all CTAs, see kProf*
+                                // over all CTAs, see kProf* (counted by the PROF instantiations)
   const int* active; // batch entries with active[b] == 0 are skipped (may be null)
   int a_shared;      // op(A) / op(B) shared by every batch entry: sliced once (batch index 0)
   int b_shared;
@@ -174,7 +174,7 @@ __device__ __forceinline__ bool unit_coords(const MmaParams& p, int nt, int u, i
   return !p.active || p.active[b] != 0;
 }
 
-template <int NT, int PAIR>
+template <int NT, int PAIR, bool PROF>
 __global__ void __launch_bounds__(kThreads, 1)
     split_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      const __grid_constant__ CUtensorMap tmBh, const MmaParams p) {
@@ -283,13 +283,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int it = sc.ib[g]; it < ie && ok; ++it) {
             const int ct = zA + sc.t[it], cs = zB + sc.s[it], cs2 = zB + sc.s2[it];
             for (int kb = kb0; kb < kb1; ++kb) {
-              const long long c0 = p.prof ? clock64() : 0;
+              const long long c0 = PROF ? clock64() : 0;
               if (!wait(&empty[stage], phase ^ 1u)) {
                 fail(b);
                 ok = false;
                 break;
               }
-              if (p.prof) t_empty += clock64() - c0;
+              if constexpr (PROF) t_empty += clock64() - c0;
               uint8_t* st = stages + stage * kStageBytes;
               if constexpr (PAIR) {
                 const uint32_t fb = ptx::mapa_shared(ptx::smem_u32(&full[stage]), 0u);  // the leader's
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
-      if (p.prof) atomicAdd(&p.prof[kProfTmaWaitEmpty], (unsigned long long)t_empty);
+      if constexpr (PROF) atomicAdd(&p.prof[kProfTmaWaitEmpty], (unsigned long long)t_empty);
       if (*abort_flag) {
         // let the loads already in flight land before the CTA exits (bounded): one CTA waits for
         // its last stages' barriers; a pair's copies signal the leader, so both wait a while
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t gc = 0;  // jobs started so far (all units)
       bool ok = true;
       long long t_full = 0, t_acc = 0, tiles = 0;
-      const long long t_loop0 = p.prof ? clock64() : 0;
+      const long long t_loop0 = PROF ? clock64() : 0;
       if (p.stall_ns) {
         // test hook: wait on `drain`, which nothing completes before the commit below, so the
         // bounded wait expires and the CTA takes its timeout path (abort, drain, free TMEM)
@@ -352,13 +352,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         ++tiles;
         for (int g = 0; g < sc.n_jobs && ok; ++g, ++gc) {
           const uint32_t ab = gc & 1u;
-          const long long ca = p.prof ? clock64() : 0;
+          const long long ca = PROF ? clock64() : 0;
           if (gc >= 2 && !wait(&tempty[ab], ((gc >> 1) - 1u) & 1u)) {
             fail(b);
             ok = false;
             break;
           }
-          if (p.prof) t_acc += clock64() - ca;
+          if constexpr (PROF) t_acc += clock64() - ca;
           ptx::tc_fence_after();
           const uint32_t dcol0 = tmem + (2u * ab) * (uint32_t)NT;
           const bool dual = sc.dual[g] != 0;
@@ -366,13 +366,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           uint32_t acc0 = 0u;  // the job's first MMA overwrites the accumulators
           for (int it = sc.ib[g]; it < ie && ok; ++it) {
             for (int kb = kb0; kb < kb1; ++kb) {
-              const long long cf = p.prof ? clock64() : 0;
+              const long long cf = PROF ? clock64() : 0;
               if (!wait(&full[stage], phase)) {
                 fail(b);
                 ok = false;
                 break;
               }
-              if (p.prof) t_full += clock64() - cf;
+              if constexpr (PROF) t_full += clock64() - cf;
               ptx::tc_fence_after();
               const uint32_t a_addr = ptx::smem_u32(stages + stage * kStageBytes);
               const uint32_t b_addr = a_addr + kABytes;
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       else ptx::umma_commit(drain);
       volatile int never = 0;
       ptx::mbar_wait_bounded(drain, 0, &never, kWaitLimitNs);
-      if (p.prof) {
+      if constexpr (PROF) {
         atomicAdd(&p.prof[kProfMmaWaitFull], (unsigned long long)t_full);
         atomicAdd(&p.prof[kProfMmaWaitAcc], (unsigned long long)t_acc);
         atomicAdd(&p.prof[kProfMmaLoop], (unsigned long long)(clock64() - t_loop0));
@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         ptx::tc_fence_after();
-        const long long cd = p.prof ? clock64() : 0;
+        const long long cd = PROF ? clock64() : 0;
         const int lanes = sc.dual[g] ? 2 : 1;
         for (int l = 0; l < lanes; ++l) {
           const float fs = sc.fscale[g][l];
@@ -472,10 +472,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           if constexpr (PAIR) ptx::mbar_arrive_remote(ptx::mapa_shared(ptx::smem_u32(&tempty[ab]), 0u));
           else ptx::mbar_arrive(&tempty[ab]);
         }
-        if (p.prof) t_drain += clock64() - cd;
+        if constexpr (PROF) t_drain += clock64() - cd;
       }
       if (!ok) break;
-      const long long cw = p.prof ? clock64() : 0;
+      const long long cw = PROF ? clock64() : 0;
       // write this tile of C (overlaps the MMAs of the next tile)
       const int jp = m0 + r;  // row of C^T
       const bool row_ok = jp < p.n2;
@@ -542,11 +542,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
-      if (p.prof) t_write += clock64() - cw;
+      if constexpr (PROF) t_write += clock64() - cw;
     }
-    if (p.prof && ew == 0 && lane == 0) {
-      atomicAdd(&p.prof[kProfEpiDrain], (unsigned long long)t_drain);
-      atomicAdd(&p.prof[kProfEpiWrite], (unsigned long long)t_write);
+    if constexpr (PROF) {
+      if (ew == 0 && lane == 0) {
+        atomicAdd(&p.prof[kProfEpiDrain], (unsigned long long)t_drain);
+        atomicAdd(&p.prof[kProfEpiWrite], (unsigned long long)t_write);
+      }
     }
   }
   // ---------------- teardown ----------------
@@ -937,9 +939,9 @@ int pair_clusters() {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int nc = 0;
-  if (cudaFuncSetAttribute(split_mma_kernel<NT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(split_mma_kernel<NT, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem_for(NT, 1)) != cudaSuccess ||
-      cudaOccupancyMaxActiveClusters(&nc, split_mma_kernel<NT, 1>, &cfg) != cudaSuccess) {
+      cudaOccupancyMaxActiveClusters(&nc, split_mma_kernel<NT, 1, false>, &cfg) != cudaSuccess) {
     (void)cudaGetLastError();
     nc = 0;
   }
@@ -948,7 +950,7 @@ int pair_clusters() {
   return nc;
 }
 
-template <int NT, int PAIR>
+template <int NT, int PAIR, bool PROF>
 bt_status launch_mma(cudaStream_t st, const CUtensorMap& mA, const CUtensorMap& mB, const CUtensorMap& mBh,
                      const MmaParams& p) {
   const size_t smem = smem_for(NT, PAIR);
@@ -960,7 +962,7 @@ bt_status launch_mma(cudaStream_t st, const CUtensorMap& mA, const CUtensorMap& 
   {
     std::lock_guard<std::mutex> lock(mu);
     if (!attr_set[dev]) {
-      if (cudaFuncSetAttribute(split_mma_kernel<NT, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      if (cudaFuncSetAttribute(split_mma_kernel<NT, PAIR, PROF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem) != cudaSuccess)
         return BT_ERR_CUDA;
       attr_set[dev] = true;
@@ -985,11 +987,11 @@ bt_status launch_mma(cudaStream_t st, const CUtensorMap& mA, const CUtensorMap& 
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    BT_CUDA_TRY(cudaLaunchKernelEx(&cfg, split_mma_kernel<NT, 1>, mA, mB, mBh, p));
+    BT_CUDA_TRY(cudaLaunchKernelEx(&cfg, split_mma_kernel<NT, 1, PROF>, mA, mB, mBh, p));
   } else {
     // persistent: one CTA per SM (1 CTA fits per SM by shared memory), tiles walked in order
     const int grid = p.n_units < sms ? p.n_units : sms;
-    split_mma_kernel<NT, 0><<<grid, kThreads, smem, st>>>(mA, mB, mBh, p);
+    split_mma_kernel<NT, 0, PROF><<<grid, kThreads, smem, st>>>(mA, mB, mBh, p);
   }
   count_launch();
   BT_CUDA_TRY(cudaGetLastError());
@@ -999,15 +1001,19 @@ bt_status launch_mma(cudaStream_t st, const CUtensorMap& mA, const CUtensorMap& 
 template <int PAIR>
 bt_status launch_mma_nt(int nt, cudaStream_t st, const CUtensorMap& mA, const CUtensorMap& mB,
                         const CUtensorMap& mBh, const MmaParams& p) {
+  // the measurement hook's counters are compiled into the block sizes of the measured workloads
+  // only (N tiles of 112 and 128); other launches run uninstrumented
+  if (p.prof && nt == 112) return launch_mma<112, PAIR, true>(st, mA, mB, mBh, p);
+  if (p.prof && nt == 128) return launch_mma<128, PAIR, true>(st, mA, mB, mBh, p);
   switch (nt) {
-    case 16: return launch_mma<16, PAIR>(st, mA, mB, mBh, p);
-    case 32: return launch_mma<32, PAIR>(st, mA, mB, mBh, p);
-    case 48: return launch_mma<48, PAIR>(st, mA, mB, mBh, p);
-    case 64: return launch_mma<64, PAIR>(st, mA, mB, mBh, p);
-    case 80: return launch_mma<80, PAIR>(st, mA, mB, mBh, p);
-    case 96: return launch_mma<96, PAIR>(st, mA, mB, mBh, p);
-    case 112: return launch_mma<112, PAIR>(st, mA, mB, mBh, p);
-    case 128: return launch_mma<128, PAIR>(st, mA, mB, mBh, p);
+    case 16: return launch_mma<16, PAIR, false>(st, mA, mB, mBh, p);
+    case 32: return launch_mma<32, PAIR, false>(st, mA, mB, mBh, p);
+    case 48: return launch_mma<48, PAIR, false>(st, mA, mB, mBh, p);
+    case 64: return launch_mma<64, PAIR, false>(st, mA, mB, mBh, p);
+    case 80: return launch_mma<80, PAIR, false>(st, mA, mB, mBh, p);
+    case 96: return launch_mma<96, PAIR, false>(st, mA, mB, mBh, p);
+    case 112: return launch_mma<112, PAIR, false>(st, mA, mB, mBh, p);
+    case 128: return launch_mma<128, PAIR, false>(st, mA, mB, mBh, p);
     default: return BT_ERR_UNSUPPORTED;
   }
 }
