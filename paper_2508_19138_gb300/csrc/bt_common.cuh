@@ -91,9 +91,25 @@ struct Engine {
 size_t split_workspace_bytes(int m, int n, int k, int slices, int batch);
 // A bounded wait that expires sets err[b * err_stride] = BT_ERR_TIMEOUT for the batch entry b of
 // the CTA (err may be null; err_stride 0 makes it one word for the whole call).
+//
+// An operand may come pre-sliced (SlicedOp: sliced once by slice_op, reused by every product it
+// enters while its values stay the same); its shape, slice count, batch and k must match the
+// product's, and k <= 1024 (one K chunk).
+struct SlicedOp {
+  uint32_t* t = nullptr;  // slice words
+  int* e = nullptr;       // line exponents
+  int role = -1;          // 0: rows of op(A) (At operand), 1: columns of op(B) (Bt operand)
+  int lines = 0, kc = 0, S = 0, batch = 0;
+  bool shared = false;    // one operand for every batch entry (sliced once)
+  bool valid() const { return t != nullptr; }
+};
+size_t sliced_op_bytes(int role, int lines, int k, int slices, int batch);
+bt_status slice_op(cudaStream_t st, int role, int lines, int k, Operand X, int batch, int slices, void* buf,
+                   size_t bytes, SlicedOp* out);
 bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A, Operand B, zd beta,
                       zd* C, int ldc, long long strideC, int batch, int slices, void* ws,
-                      size_t ws_bytes, const int* active, int* err = nullptr, long long err_stride = 0);
+                      size_t ws_bytes, const int* active, int* err = nullptr, long long err_stride = 0,
+                      const SlicedOp* preA = nullptr, const SlicedOp* preB = nullptr);
 
 // C = alpha op(A) op(B) + beta C on the engine's kernel.
 bt_status gemm(const Engine& eng, cudaStream_t st, int m, int n, int k, zd alpha, Operand A, Operand B, zd beta,

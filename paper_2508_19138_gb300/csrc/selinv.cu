@@ -64,6 +64,10 @@ struct bt_ctx {
   size_t dec_bytes = 0;
   void* split_ws = nullptr;
   size_t split_bytes = 0;
+  // sliced products: operands sliced once per sweep step and reused by the products they enter
+  char* pre_a[2] = {nullptr, nullptr};
+  char* pre_b[3] = {nullptr, nullptr, nullptr};
+  size_t pre_a_bytes = 0, pre_b_bytes = 0;
   bt::Engine eng_kept;  // products of the inversions and the decimation (FP64 unless split_scope = 1)
   bt::Engine eng_polish;  // products of the Newton step after decimation (FP64, or 8 slices with split_scope = 1)
   int* h_pinned = nullptr;
@@ -203,6 +207,12 @@ size_t layout(bt_ctx* c, const bt_selinv_desc& d, char* base) {
     const int ws_slices = d.split_scope == 1 ? (d.obc ? 8 : kept_slices_of(d)) : slices_of(d);
     x->split_bytes = bt::split_workspace_bytes(d.bs, d.bs, d.bs, ws_slices, sb);
     x->split_ws = cv.take<char>(x->split_bytes);
+    if (d.bs <= 1024) {
+      x->pre_a_bytes = bt::sliced_op_bytes(0, d.bs, d.bs, slices_of(d), (int)E);
+      x->pre_b_bytes = bt::sliced_op_bytes(1, d.bs, d.bs, slices_of(d), (int)E);
+      for (int i = 0; i < 2; ++i) x->pre_a[i] = cv.take<char>(x->pre_a_bytes);
+      for (int i = 0; i < 3; ++i) x->pre_b[i] = cv.take<char>(x->pre_b_bytes);
+    }
   }
   return cv.off;
 }
@@ -274,14 +284,16 @@ bt_status set_err(bt_ctx* c, bt_status s, const char* what) {
 // the sliced engine projects its full result.
 // `units`: block products of the paper's formulation that this product stands for (the model
 // flop count is 8 b^3 per such product, however the kernels compute it).
+// preA / preB: the operand already sliced (sliced products only; ignored by the FP64 engine).
 bt_status prod(bt_ctx* c, int Ec, double alpha, const Blk& A, const Blk& B, double beta, zd* C, long long sC,
-               bool antiherm = false, double units = 1.0) {
+               bool antiherm = false, double units = 1.0, const bt::SlicedOp* preA = nullptr,
+               const bt::SlicedOp* preB = nullptr) {
   const int bs = c->d.bs;
   const double a = alpha * A.f * B.f;
   c->flops += units * 8.0 * bs * (double)bs * bs * Ec;
   if (is_split(c->d)) {
     BT_TRY(bt::split_zgemm(c->st, bs, bs, bs, zmake(a, 0.0), opnd(A, bs), opnd(B, bs), zmake(beta, 0.0), C, bs, sC,
-                           Ec, slices_of(c->d), c->split_ws, c->split_bytes, nullptr, c->tflag, 0));
+                           Ec, slices_of(c->d), c->split_ws, c->split_bytes, nullptr, c->tflag, 0, preA, preB));
     // the sliced product computes every entry; its result is projected onto the anti-Hermitian
     // matrices so that, as on the FP64 engine, the sandwiches come out exactly anti-Hermitian
     if (antiherm && c->d.symmetrize) return bt::antiherm_project(c->st, bs, Ec, C, sC);
@@ -311,6 +323,13 @@ bt_status run_sweep(Sweep& s, int* status) {
   auto xLG = [&](int w, int i) { return (w == 0 ? c->xL : c->xG) + i * B2; };
   auto X = [&](zd* p, long long es) { return ws_blk(p, es); };
   const bool need[2] = {s.needL, s.needG};
+  // sliced products: an operand that enters several products of a step is sliced once
+  const bool reuse = is_split(c->d) && c->pre_a[0] != nullptr;
+  auto slice_blk = [&](int role, const Blk& b, int slot, bt::SlicedOp* o) -> bt_status {
+    char* buf = role == 0 ? c->pre_a[slot] : c->pre_b[slot];
+    const size_t bytes = role == 0 ? c->pre_a_bytes : c->pre_b_bytes;
+    return bt::slice_op(c->st, role, bs, bs, opnd(b, bs), Ec, slices_of(c->d), buf, bytes, o);
+  };
 
   // ---------------- forward pass ----------------
   for (int i = 0; i < N; ++i) {
@@ -319,6 +338,12 @@ bt_status run_sweep(Sweep& s, int* status) {
     BT_TRY(s.asmM(i, xR(i), NB2));
     if (i > 0) BT_TRY(prod(c, Ec, -1.0, X(T1, B2), s.Mu(i - 1), 1.0, xR(i), NB2));      // - ... M~_{i-1,i}
     BT_TRY(inv(c, Ec, xR(i), NB2, status));
+    // x^R_i enters both the lesser and the greater sandwich, as op(A) and as op(B)^H
+    bt::SlicedOp sxa, sxh;
+    if (reuse && need[0] && need[1]) {
+      BT_TRY(slice_blk(0, X(xR(i), NB2), 0, &sxa));
+      BT_TRY(slice_blk(1, flip(X(xR(i), NB2)), 0, &sxh));
+    }
     for (int w = 0; w < 2; ++w) {
       if (!need[w]) continue;
       zd *Bt = t[1], *Tq = t[2], *Y = t[3];
@@ -334,8 +359,9 @@ bt_status run_sweep(Sweep& s, int* status) {
           }
         }
       }
-      BT_TRY(prod(c, Ec, 1.0, X(xR(i), NB2), X(Bt, B2), 0.0, Tq, B2));
-      BT_TRY(prod(c, Ec, 1.0, X(Tq, B2), flip(X(xR(i), NB2)), 0.0, xLG(w, i), NB2, true));  // x^R (...) x^R^H
+      BT_TRY(prod(c, Ec, 1.0, X(xR(i), NB2), X(Bt, B2), 0.0, Tq, B2, false, 1.0, &sxa));
+      BT_TRY(prod(c, Ec, 1.0, X(Tq, B2), flip(X(xR(i), NB2)), 0.0, xLG(w, i), NB2, true, 1.0, nullptr,
+                  &sxh));  // x^R (...) x^R^H
     }
   }
   // ---------------- backward pass ----------------
@@ -346,30 +372,47 @@ bt_status run_sweep(Sweep& s, int* status) {
     zd* XRn = xR(i + 1);
     BT_TRY(prod(c, Ec, 1.0, X(xR(i), NB2), s.Mu(i), 0.0, U1, B2));                 // x^R_i M~_{i,i+1}
     BT_TRY(prod(c, Ec, 1.0, s.Ml(i), X(xR(i), NB2), 0.0, W1, B2));                 // M~_{i+1,i} x^R_i
+    const bool anyLG = s.needL || s.needG;
+    const bool both = s.needL && s.needG;
+    const bool rl = s.needRlower || s.keepRoff;
+    // operands of several products of this step, sliced once: U1 (op(A) of X^R_{i,i+1}, X^R_{i,i+2}
+    // and both outputs' x^R M X^<> and Z_i), X^R_{i+1} (op(A) of X^R_{i+1,i} and V1), W1 (op(B)
+    // of X^R_{i+1,i}, X^R_{i+2,i} and X^R_i), V1^H and U1^H (op(B) of both outputs' products)
+    bt::SlicedOp su1, sxrn, sw1, sv1h, su1h;
+    if (reuse) {
+      if (anyLG || (s.X2u && i + 2 < N)) BT_TRY(slice_blk(0, X(U1, B2), 0, &su1));
+      if (rl && anyLG) BT_TRY(slice_blk(0, X(XRn, NB2), 1, &sxrn));
+      if (rl) BT_TRY(slice_blk(1, X(W1, B2), 0, &sw1));
+    }
     // X^R_{i,i+1}
     zd* XRu;
     long long esu;
     if (s.keepRoff) { XRu = c->XRu + i * B2; esu = N1B2; }
     else if (s.oRu) { XRu = s.oRu + i * B2; esu = s.oes_u; }
     else { XRu = t[9]; esu = B2; }
-    BT_TRY(prod(c, Ec, -1.0, X(U1, B2), X(XRn, NB2), 0.0, XRu, esu));
+    BT_TRY(prod(c, Ec, -1.0, X(U1, B2), X(XRn, NB2), 0.0, XRu, esu, false, 1.0, &su1));
     if (s.keepRoff && s.oRu) BT_TRY(bt::write_blocks(c->st, bs, 1, Ec, XRu, 0, esu, s.oRu + i * B2, 0, s.oes_u, 0));
     if (s.needRlower || s.keepRoff) {
       zd* XRl;
       long long esl;
       if (s.keepRoff) { XRl = c->XRl + i * B2; esl = N1B2; }
       else { XRl = s.oRl + i * B2; esl = s.oes_u; }
-      BT_TRY(prod(c, Ec, -1.0, X(XRn, NB2), X(W1, B2), 0.0, XRl, esl));
+      BT_TRY(prod(c, Ec, -1.0, X(XRn, NB2), X(W1, B2), 0.0, XRl, esl, false, 1.0, &sxrn, &sw1));
       if (s.keepRoff && s.oRl) BT_TRY(bt::write_blocks(c->st, bs, 1, Ec, XRl, 0, esl, s.oRl + i * B2, 0, s.oes_u, 0));
     }
     if (s.X2u && i + 2 < N) {
       // X^R_{i,i+2} = -x^R_i M~_{i,i+1} X^R_{i+1,i+2};  X^R_{i+2,i} = -X^R_{i+2,i+1} M~_{i+1,i} x^R_i
       const long long N2B2 = (long long)(N - 2) * B2;
-      BT_TRY(prod(c, Ec, -1.0, X(U1, B2), X(c->XRu + (i + 1) * B2, N1B2), 0.0, s.X2u + i * B2, N2B2));
-      BT_TRY(prod(c, Ec, -1.0, X(c->XRl + (i + 1) * B2, N1B2), X(W1, B2), 0.0, s.X2l + i * B2, N2B2));
+      BT_TRY(prod(c, Ec, -1.0, X(U1, B2), X(c->XRu + (i + 1) * B2, N1B2), 0.0, s.X2u + i * B2, N2B2, false, 1.0,
+                  &su1));
+      BT_TRY(prod(c, Ec, -1.0, X(c->XRl + (i + 1) * B2, N1B2), X(W1, B2), 0.0, s.X2l + i * B2, N2B2, false, 1.0,
+                  nullptr, &sw1));
     }
-    const bool anyLG = s.needL || s.needG;
-    if (anyLG) BT_TRY(prod(c, Ec, 1.0, X(XRn, NB2), s.Ml(i), 0.0, V1, B2));        // X^R_{i+1} M~_{i+1,i}
+    if (anyLG) BT_TRY(prod(c, Ec, 1.0, X(XRn, NB2), s.Ml(i), 0.0, V1, B2, false, 1.0, &sxrn));  // X^R_{i+1} M~_{i+1,i}
+    if (reuse && both) {
+      BT_TRY(slice_blk(1, flip(X(V1, B2)), 1, &sv1h));
+      BT_TRY(slice_blk(1, flip(X(U1, B2)), 2, &su1h));
+    }
     if (anyLG && s.has_boff) {
       for (int w = 0; w < 2; ++w) {
         if (!need[w]) continue;
@@ -377,14 +420,14 @@ bt_status run_sweep(Sweep& s, int* status) {
         if (bu.valid()) BT_TRY(prod(c, Ec, 1.0, X(xR(i), NB2), bu, 0.0, XB[w], B2)); // x^R_i B_{i,i+1}
       }
     }
-    BT_TRY(prod(c, Ec, -1.0, X(XRu, esu), X(W1, B2), 1.0, xR(i), NB2));            // X^R_i (Eq. 11)
+    BT_TRY(prod(c, Ec, -1.0, X(XRu, esu), X(W1, B2), 1.0, xR(i), NB2, false, 1.0, nullptr, &sw1));  // X^R_i (Eq. 11)
     for (int w = 0; w < 2; ++w) {
       if (!need[w]) continue;
       zd* xLi = xLG(w, i);
       zd* XLn = xLG(w, i + 1);
       zd* oU = w == 0 ? s.oLu : s.oGu;
       const bool bu_valid = s.has_boff && s.Bu(i, w).valid();
-      BT_TRY(prod(c, Ec, 1.0, X(U1, B2), X(XLn, NB2), 0.0, P, B2));                 // x^R M X^<>_{i+1}
+      BT_TRY(prod(c, Ec, 1.0, X(U1, B2), X(XLn, NB2), 0.0, P, B2, false, 1.0, &su1));  // x^R M X^<>_{i+1}
       // With exactly anti-Hermitian x^<>_i (symmetrised outputs: the sandwiches above are computed
       // so), Z_i = -X^R_{i,i+1} M~_{i+1,i} x^<>_i = U1 V1 x^<>_i = U1 D^H with
       // D = -x^<>_i V1^H, the first term of X^<>_{i,i+1}: one product instead of two.
@@ -393,8 +436,9 @@ bt_status run_sweep(Sweep& s, int* status) {
       const long long des = oU ? s.oes_u : B2;
       if (oU || z_from_d) {
         BT_TRY(prod(c, Ec, -1.0, X(xLi, NB2), flip(X(V1, B2)), 0.0, d, des, false,    // D = - x^<> (X^R M)^H
-                    oU ? 1.0 : 0.0));
-        if (z_from_d) BT_TRY(prod(c, Ec, 1.0, X(U1, B2), flip(X(d, des)), 0.0, Z, B2, false, 2.0));  // Z_i
+                    oU ? 1.0 : 0.0, nullptr, &sv1h));
+        if (z_from_d)
+          BT_TRY(prod(c, Ec, 1.0, X(U1, B2), flip(X(d, des)), 0.0, Z, B2, false, 2.0, &su1));  // Z_i
       }
       if (oU) {
         BT_TRY(bt::axpby(c->st, B2, Ec, -1.0, P, B2, 1.0, d, s.oes_u));             // - x^R M X^<>
@@ -405,7 +449,7 @@ bt_status run_sweep(Sweep& s, int* status) {
         BT_TRY(prod(c, Ec, 1.0, s.Ml(i), X(xLi, NB2), 0.0, Zt, B2));                // M~_{i+1,i} x^<>_i
         BT_TRY(prod(c, Ec, -1.0, X(XRu, esu), X(Zt, B2), 0.0, Z, B2));              // Z_i
       }
-      BT_TRY(prod(c, Ec, 1.0, X(P, B2), flip(X(U1, B2)), 1.0, xLi, NB2, true));     // + x M X M^H x^H
+      BT_TRY(prod(c, Ec, 1.0, X(P, B2), flip(X(U1, B2)), 1.0, xLi, NB2, true, 1.0, nullptr, &su1h));  // + x M X M^H x^H
       BT_TRY(bt::add_antiherm(c->st, bs, Ec, xLi, NB2, Z, B2, 1.0));                // + (Z - Z^H)
       if (bu_valid) {
         BT_TRY(prod(c, Ec, -1.0, X(XB[w], B2), flip(X(XRu, esu)), 0.0, Yb, B2));    // Y_i

@@ -1065,9 +1065,48 @@ unsigned long long stall_for_launch() {
   return 0;
 }
 
+size_t sliced_op_bytes(int role, int lines, int k, int slices, int batch) {
+  if (lines <= 0 || k <= 0 || k > kMaxKc || batch <= 0 || (role != 0 && role != 1)) return 0;
+  const int S = slices > 0 ? slices : 6;
+  const int Kp = pad_k(k);
+  const int rows = role == 0 ? pad_rows_n(lines, pick_nt(lines)) : pad_rows_m(lines);
+  return al256(sizeof(int) * (size_t)batch * lines) + al256((size_t)batch * S * rows * Kp * 2);
+}
+
+bt_status slice_op(cudaStream_t st, int role, int lines, int k, Operand X, int batch, int slices, void* buf,
+                   size_t bytes, SlicedOp* out) {
+  const int S = slices > 0 ? slices : 6;
+  if (!out || S < 2 || S > kMaxSlices || batch <= 0 || batch > 65535 || lines <= 0 || k <= 0 || k > kMaxKc ||
+      (role != 0 && role != 1))
+    return BT_ERR_INVALID_ARG;
+  if (!buf || bytes < sliced_op_bytes(role, lines, k, S, batch)) return BT_ERR_INVALID_ARG;
+  const int Kp = pad_k(k);
+  SlicedOp o;
+  o.role = role;
+  o.lines = lines;
+  o.kc = k;
+  o.S = S;
+  o.batch = batch;
+  o.shared = X.stride == 0 && batch > 1;
+  o.e = static_cast<int*>(buf);
+  o.t = reinterpret_cast<uint32_t*>(static_cast<char*>(buf) + al256(sizeof(int) * (size_t)batch * lines));
+  const int nb = o.shared ? 1 : batch;
+  if (role == 0) {
+    const int mp = pad_rows_n(lines, pick_nt(lines));
+    BT_TRY(slice_lines<false>(st, X.op == BT_OP_N, lines, mp, k, Kp / 2, X.p, X.ld, X.stride, X.op == BT_OP_C, S, o.e,
+                              o.t, nb, nullptr));
+  } else {
+    const int n2p = pad_rows_m(lines);
+    BT_TRY(slice_lines<true>(st, X.op == BT_OP_C, lines, n2p / 2, k, Kp / 2, X.p, X.ld, X.stride, X.op == BT_OP_C, S,
+                             o.e, o.t, nb, nullptr));
+  }
+  *out = o;
+  return BT_OK;
+}
+
 bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A, Operand B, zd beta, zd* C, int ldc,
                       long long strideC, int batch, int slices, void* ws, size_t ws_bytes, const int* active,
-                      int* err, long long err_stride) {
+                      int* err, long long err_stride, const SlicedOp* preA, const SlicedOp* preB) {
   const int S = slices > 0 ? slices : 6;
   if (S < 2 || S > kMaxSlices) return BT_ERR_INVALID_ARG;
   if (m < 0 || n < 0 || k < 0 || batch < 0) return BT_ERR_INVALID_ARG;
@@ -1083,6 +1122,13 @@ bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A,
   }
   if (!ws || ws_bytes < split_workspace_bytes(m, n, k, S, batch)) return BT_ERR_INVALID_ARG;
   if (!get_encode()) return BT_ERR_UNSUPPORTED;
+  if (preA && preA->valid() && (preA->role != 0 || preA->lines != m || preA->kc != k || preA->S != S ||
+                                preA->batch != batch || k > kMaxKc || active))
+    return BT_ERR_INVALID_ARG;
+  if (preB && preB->valid() && (preB->role != 1 || preB->lines != n || preB->kc != k || preB->S != S ||
+                                preB->batch != batch || k > kMaxKc || active))
+    return BT_ERR_INVALID_ARG;
+  const bool useA = preA && preA->valid(), useB = preB && preB->valid();
   // K' = 2k must stay <= 1040 per launch for exact slice products: chunk k, accumulate into C
   for (int k0 = 0; k0 < k; k0 += kMaxKc) {
     const int kc = (k - k0) < kMaxKc ? (k - k0) : kMaxKc;
@@ -1095,15 +1141,26 @@ bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A,
     a.p = A.op == BT_OP_N ? A.p + k0 : A.p + (long long)k0 * A.ld;
     bop.p = B.op == BT_OP_N ? B.p + (long long)k0 * B.ld : B.p + k0;
     // an operand shared by every batch entry (stride 0, e.g. a Hamiltonian block) is sliced once
-    const bool a_shared = A.stride == 0 && batch > 1, b_shared = B.stride == 0 && batch > 1;
+    const bool a_shared = useA ? preA->shared : (A.stride == 0 && batch > 1);
+    const bool b_shared = useB ? preB->shared : (B.stride == 0 && batch > 1);
     const int ba = a_shared ? 1 : batch, bb = b_shared ? 1 : batch;
     const int* act_a = a_shared ? nullptr : active;
     const int* act_b = b_shared ? nullptr : active;
     // At from the rows of op(A): contiguous for op N;  Bt from the columns of op(B): contiguous for op C
-    BT_TRY(slice_lines<false>(st, a.op == BT_OP_N, m, mp, kc, Kp / 2, a.p, a.ld, a.stride, a.op == BT_OP_C, S, w.eA,
-                              w.At, ba, act_a));
-    BT_TRY(slice_lines<true>(st, bop.op == BT_OP_C, n, n2p / 2, kc, Kp / 2, bop.p, bop.ld, bop.stride,
-                             bop.op == BT_OP_C, S, w.eB, w.Bt, bb, act_b));
+    if (useA) {
+      w.At = preA->t;
+      w.eA = preA->e;
+    } else {
+      BT_TRY(slice_lines<false>(st, a.op == BT_OP_N, m, mp, kc, Kp / 2, a.p, a.ld, a.stride, a.op == BT_OP_C, S, w.eA,
+                                w.At, ba, act_a));
+    }
+    if (useB) {
+      w.Bt = preB->t;
+      w.eB = preB->e;
+    } else {
+      BT_TRY(slice_lines<true>(st, bop.op == BT_OP_C, n, n2p / 2, kc, Kp / 2, bop.p, bop.ld, bop.stride,
+                               bop.op == BT_OP_C, S, w.eB, w.Bt, bb, act_b));
+    }
     // CTA pairs (cta_group::2: two M tiles share each At tile, half of it in each CTA) when the
     // 2n rows of C^T span at least two M tiles and the device holds most of its SMs as pairs
     const int tiles_x = n2p / kTileM;
