@@ -37,6 +37,7 @@ def main():
     ap.add_argument("--split-scope", type=int, default=1, help="steptrace: split scope")
     ap.add_argument("--graph", choices=["on", "off"], default="on", help="steptrace: graph mode")
     ap.add_argument("--warmup", type=int, default=2, help="steptrace: untraced steps first")
+    ap.add_argument("--inv-panel", type=int, default=0, help="steptrace: inversion panel width (0 = default)")
     ap.add_argument("--cache-config", type=int, default=-1,
                     help="preferred L1 / shared split for the run (0 none, 1 shared, 2 L1, 3 equal; -1 untouched)")
     ap.add_argument("--split-pair", type=int, default=0,
@@ -242,7 +243,7 @@ def step_trace(a, pkg):
     stream = torch.cuda.Stream()
     solver = GSolver(sysg.nb, sysg.bs, eps, sysg.eta, sysg.kT, sysg.mu_left, sysg.mu_right, obc=True,
                      precision=precision, split_slices=a.slices, stream=stream, split_scope=a.split_scope,
-                     graph=a.graph == "on")
+                     graph=a.graph == "on", inv_panel=a.inv_panel)
     with torch.cuda.stream(stream):
         solver.set_inputs(sysg.H_diag, sysg.H_upper, sysg.sigR_diag, sysg.sigL_diag, sysg.sigG_diag)
         outs, status = solver.allocate_outputs(eps)
@@ -305,7 +306,8 @@ def step_trace(a, pkg):
     rows = sorted(agg.items(), key=lambda kv: -kv[1][1])
     print(json.dumps({"kernel": "steptrace", "workload": f"nanoribbon G 40x416, {eps} energies per step",
                       "precision": a.precision, "split_scope": a.split_scope if a.precision == "split" else None,
-                      "graph": a.graph, "cache_config": a.cache_config, "step_ms_plain": plain_ms,
+                      "graph": a.graph, "cache_config": a.cache_config, "inv_panel": a.inv_panel,
+                      "step_ms_plain": plain_ms,
                       "traced_span_ms": (last - first) / 1e6 if rows else 0,
                       "device_ms": total / 1e3, "launches": sum(n for n, _ in agg.values()),
                       "idle_ms": idle / 1e3,
