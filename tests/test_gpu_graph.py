@@ -175,3 +175,55 @@ def test_graph_wide_blocks_staged_sigma(precision, scope):
         for x, y in zip(a, b):
             assert np.array_equal(x, y)
     assert got[False][1]["decim_iterations"] == got[True][1]["decim_iterations"]
+
+
+def test_graph_input_staging_grows_and_replays():
+    """Graph mode copies each chunk's per-energy inputs to the context's staging memory: a solve
+    with a larger input layout (block self-energies after diagonal-vector ones) grows it, which
+    drops the graphs captured on the old staging; solves with new energy batches of the same
+    layout then replay.  Every result is bitwise equal to direct launches."""
+    import torch
+    import paper_2508_19138_gb300 as pkg
+    from paper_2508_19138_gb300 import BT, BTOut
+    s = synthetic.random_device(23, 4, 48, 9)
+    nb, bs, E = s.nb, s.bs, 3
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    rng = np.random.default_rng(5)
+    # per-energy scattering self-energies: diagonal vectors, and full diagonal blocks
+    gam = 0.02 * (1.0 + rng.random((9, nb, bs)))
+    sig_vec = t(-0.5j * gam)
+    blk = np.zeros((9, nb, bs, bs), dtype=np.complex128)
+    for e in range(9):
+        for i in range(nb):
+            a = 0.01 * (rng.standard_normal((bs, bs)) + 1j * rng.standard_normal((bs, bs)))
+            blk[e, i] = -0.5j * (a @ a.conj().T + np.diag(gam[e, i]))  # anti-Hermitian part: -i/2 Gamma
+    sig_blk = t(blk)
+    H = BT(t(s.H_diag), t(s.H_upper), None, pkg.BT_LAYOUT_BLOCKS, pkg.BT_SYM_HERMITIAN, False)
+
+    def sigma(kind, e0):
+        if kind == "vec":
+            return BT(sig_vec[e0:e0 + E], None, None, pkg.BT_LAYOUT_DIAGVEC, pkg.BT_SYM_GENERAL, True)
+        return BT(sig_blk[e0:e0 + E], None, None, pkg.BT_LAYOUT_BLOCKS, pkg.BT_SYM_GENERAL, True)
+
+    calls = [("vec", 0), ("vec", 3), ("blk", 0), ("blk", 6), ("blk", 3)]
+    got = {}
+    for graph in (False, True):
+        stream = torch.cuda.Stream()
+        desc = pkg.make_desc(nb, bs, E, obc=True, eta=s.eta, kT=s.kT, mu_left=s.mu_left, mu_right=s.mu_right,
+                             graph=graph)
+        ctx = pkg.bt_selinv_create(desc, stream)
+        mk = lambda *sh: torch.empty(sh, dtype=torch.complex128, device="cuda")
+        oR = BTOut(mk(E, nb, bs, bs), mk(E, nb - 1, bs, bs), mk(E, nb - 1, bs, bs))
+        status = torch.zeros(E, dtype=torch.int32, device="cuda")
+        outs = []
+        for kind, e0 in calls:
+            sg = sigma(kind, e0)
+            pkg.bt_selinv_solve(ctx, H, None, sg, None, None, s.energies[e0:e0 + E], oR, None, None, status)
+            torch.cuda.synchronize()
+            outs.append([x.cpu().numpy() for x in (oR.diag, oR.upper, oR.lower, status)])
+        ctx.close()
+        got[graph] = outs
+    for a, b in zip(got[False], got[True]):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    assert all((o[3] == 0).all() for o in got[True])
