@@ -332,6 +332,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t gc = 0;  // jobs started so far (all units)
       bool ok = true;
       long long t_full = 0, t_acc = 0, tiles = 0;
+      // shared-memory descriptors of the current stage, kept as their low words (the start
+      // address field, units of 16 bytes, and the leading byte offset) and advanced by adds: the
+      // issuing thread's instructions per K block bound the tensor pipe's rate next to the
+      // epilogue warps, so the loop below carries as few as possible
+      const uint64_t d_stage0 = ptx::sdesc_kmajor_sw128(ptx::smem_u32(stages));
+      const uint32_t d_hi = (uint32_t)(d_stage0 >> 32), a_lo0 = (uint32_t)d_stage0;
+      constexpr uint32_t kStageLo = (uint32_t)kStageBytes >> 4, kBLo = (uint32_t)kABytes >> 4;
+      uint32_t a_lo = a_lo0;
       const long long t_loop0 = PROF ? clock64() : 0;
       if (p.stall_ns) {
         // test hook: wait on `drain`, which nothing completes before the commit below, so the
@@ -361,7 +369,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           if constexpr (PROF) t_acc += clock64() - ca;
           ptx::tc_fence_after();
           const uint32_t dcol0 = tmem + (2u * ab) * (uint32_t)NT;
-          const bool dual = sc.dual[g] != 0;
+          // a dual job's two At tiles form one 2NT-row B operand (side by side in this CTA's
+          // stage, or one per CTA of a pair) and its two accumulators sit side by side in TMEM:
+          // one MMA with N = 2 NT per K step reads the Bt tile once for both lanes
+          const uint32_t idesc = sc.dual[g] != 0 ? kIdesc2 : kIdesc;
           const int ie = sc.ie[g], kb0 = sc.kb0[g], kb1 = sc.kb1[g];
           uint32_t acc0 = 0u;  // the job's first MMA overwrites the accumulators
           for (int it = sc.ib[g]; it < ie && ok; ++it) {
@@ -374,26 +385,27 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
               if constexpr (PROF) t_full += clock64() - cf;
               ptx::tc_fence_after();
-              const uint32_t a_addr = ptx::smem_u32(stages + stage * kStageBytes);
-              const uint32_t b_addr = a_addr + kABytes;
-              // a dual job's two At tiles form one 2NT-row B operand (side by side in this CTA's
-              // stage, or one per CTA of a pair) and its two accumulators sit side by side in
-              // TMEM: one MMA with N = 2 NT per K step reads the Bt tile once for both lanes
-              const uint32_t idesc = dual ? kIdesc2 : kIdesc;
-              // K step k starts 32 bytes further: +2 in the descriptor's address field (units of
-              // 16 bytes; stage addresses are below 256 KB, so the field cannot carry over)
-              const uint64_t ad = ptx::sdesc_kmajor_sw128(a_addr), bd = ptx::sdesc_kmajor_sw128(b_addr);
+              // K step k starts 32 bytes further: +2 in the descriptor's address field (stage
+              // addresses are below 256 KB, so the 14-bit field cannot carry into the next one)
 #pragma unroll
               for (int k = 0; k < kKBlock / 16; ++k) {
+                const uint64_t ad = ((uint64_t)d_hi << 32) | (uint64_t)(a_lo + 2u * k);
+                const uint64_t bd = ((uint64_t)d_hi << 32) | (uint64_t)(a_lo + kBLo + 2u * k);
                 if constexpr (PAIR)
-                  ptx::umma_f16_pair(dcol0, ad + 2u * k, bd + 2u * k, idesc, k == 0 ? acc0 : 1u);
+                  ptx::umma_f16_pair(dcol0, ad, bd, idesc, k == 0 ? acc0 : 1u);
                 else
-                  ptx::umma_f16(dcol0, ad + 2u * k, bd + 2u * k, idesc, k == 0 ? acc0 : 1u);
+                  ptx::umma_f16(dcol0, ad, bd, idesc, k == 0 ? acc0 : 1u);
               }
               acc0 = 1u;
               if constexpr (PAIR) ptx::umma_commit_pair_mc(&empty[stage], (uint16_t)0x3);
               else ptx::umma_commit(&empty[stage]);
-              if (++stage == kStages) { stage = 0; phase ^= 1u; }
+              if (++stage == kStages) {
+                stage = 0;
+                phase ^= 1u;
+                a_lo = a_lo0;
+              } else {
+                a_lo += kStageLo;
+              }
             }
           }
           if (ok) {
