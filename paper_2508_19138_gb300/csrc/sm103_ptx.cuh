@@ -122,54 +122,6 @@ __device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t adesc, uint64
       : "memory");
 }
 
-// Four K = 16 steps of one 64-deep K block, D (+)= A B^T, in one statement: descriptors from their
-// low words (start address field and leading byte offset; step k adds 2, i.e. 32 bytes) and the
-// common high word; the first step accumulates when `accumulate` != 0, the other three always.
-// cta_group::1 (PAIR = 0) or the pair form issued by the pair leader (PAIR = 1).
-template <int PAIR>
-__device__ __forceinline__ void umma_f16_kblock(uint32_t tmem_d, uint32_t a_lo, uint32_t b_lo, uint32_t d_hi,
-                                                uint32_t idesc, uint32_t accumulate) {
-  if constexpr (PAIR) {
-    asm volatile(
-        "{\n"
-        " .reg .pred p0, p1;\n"
-        " .reg .b32 a1, a2, a3, b1, b2, b3;\n"
-        " .reg .b64 da0, da1, da2, da3, db0, db1, db2, db3;\n"
-        " setp.ne.b32 p0, %5, 0;\n"
-        " setp.eq.b32 p1, %5, %5;\n"
-        " add.u32 a1, %1, 2; add.u32 a2, %1, 4; add.u32 a3, %1, 6;\n"
-        " add.u32 b1, %2, 2; add.u32 b2, %2, 4; add.u32 b3, %2, 6;\n"
-        " mov.b64 da0, {%1, %3}; mov.b64 da1, {a1, %3}; mov.b64 da2, {a2, %3}; mov.b64 da3, {a3, %3};\n"
-        " mov.b64 db0, {%2, %3}; mov.b64 db1, {b1, %3}; mov.b64 db2, {b2, %3}; mov.b64 db3, {b3, %3};\n"
-        " tcgen05.mma.cta_group::2.kind::f16 [%0], da0, db0, %4, p0;\n"
-        " tcgen05.mma.cta_group::2.kind::f16 [%0], da1, db1, %4, p1;\n"
-        " tcgen05.mma.cta_group::2.kind::f16 [%0], da2, db2, %4, p1;\n"
-        " tcgen05.mma.cta_group::2.kind::f16 [%0], da3, db3, %4, p1;\n"
-        "}\n" ::"r"(tmem_d),
-        "r"(a_lo), "r"(b_lo), "r"(d_hi), "r"(idesc), "r"(accumulate)
-        : "memory");
-  } else {
-    asm volatile(
-        "{\n"
-        " .reg .pred p0, p1;\n"
-        " .reg .b32 a1, a2, a3, b1, b2, b3;\n"
-        " .reg .b64 da0, da1, da2, da3, db0, db1, db2, db3;\n"
-        " setp.ne.b32 p0, %5, 0;\n"
-        " setp.eq.b32 p1, %5, %5;\n"
-        " add.u32 a1, %1, 2; add.u32 a2, %1, 4; add.u32 a3, %1, 6;\n"
-        " add.u32 b1, %2, 2; add.u32 b2, %2, 4; add.u32 b3, %2, 6;\n"
-        " mov.b64 da0, {%1, %3}; mov.b64 da1, {a1, %3}; mov.b64 da2, {a2, %3}; mov.b64 da3, {a3, %3};\n"
-        " mov.b64 db0, {%2, %3}; mov.b64 db1, {b1, %3}; mov.b64 db2, {b2, %3}; mov.b64 db3, {b3, %3};\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], da0, db0, %4, p0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], da1, db1, %4, p1;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], da2, db2, %4, p1;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], da3, db3, %4, p1;\n"
-        "}\n" ::"r"(tmem_d),
-        "r"(a_lo), "r"(b_lo), "r"(d_hi), "r"(idesc), "r"(accumulate)
-        : "memory");
-  }
-}
-
 // arrive on `bar` once every tcgen05 operation issued so far by this thread has completed
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))

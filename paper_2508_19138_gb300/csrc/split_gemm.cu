@@ -387,8 +387,15 @@ __global__ void __launch_bounds__(kThreads, 1)
               ptx::tc_fence_after();
               // K step k starts 32 bytes further: +2 in the descriptor's address field (stage
               // addresses are below 256 KB, so the 14-bit field cannot carry into the next one)
-              static_assert(kKBlock == 64, "four K = 16 steps per K block");
-              ptx::umma_f16_kblock<PAIR>(dcol0, a_lo, a_lo + kBLo, d_hi, idesc, acc0);
+#pragma unroll
+              for (int k = 0; k < kKBlock / 16; ++k) {
+                const uint64_t ad = ((uint64_t)d_hi << 32) | (uint64_t)(a_lo + 2u * k);
+                const uint64_t bd = ((uint64_t)d_hi << 32) | (uint64_t)(a_lo + kBLo + 2u * k);
+                if constexpr (PAIR)
+                  ptx::umma_f16_pair(dcol0, ad, bd, idesc, k == 0 ? acc0 : 1u);
+                else
+                  ptx::umma_f16(dcol0, ad, bd, idesc, k == 0 ? acc0 : 1u);
+              }
               acc0 = 1u;
               if constexpr (PAIR) ptx::umma_commit_pair_mc(&empty[stage], (uint16_t)0x3);
               else ptx::umma_commit(&empty[stage]);
