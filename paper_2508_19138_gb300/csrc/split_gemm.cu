@@ -183,8 +183,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int kStages = stages_for(NT, PAIR);
   constexpr int kStageBytes = stage_bytes_for(NT, PAIR);
   constexpr int kCols = NT / (kEpiWarps / 4);  // accumulator columns per epilogue thread
-  constexpr int kBatch = kCols % 8 == 0 ? 8 : 4;  // columns per tcgen05.ld wait
   constexpr int kWB = 4;  // outputs per write chunk (kCols is a multiple of 4)
+  static_assert(kCols % 4 == 0, "accumulator columns per thread: a multiple of 4");
   static_assert(NT % 16 == 0 && NT >= 16 && NT <= 256, "UMMA N");
   static_assert(4 * NT <= 512, "two double-buffered accumulator pairs must fit in TMEM");
   // one CTA: M = 128; a pair: M = 256, rows 0..127 in the leader (rank 0), 128..255 in its peer
@@ -460,22 +460,36 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (2u * ab + (uint32_t)l) * (uint32_t)NT +
                                 (uint32_t)(cq * kCols);
 #pragma unroll
-          for (int c0 = 0; c0 < kCols; c0 += kBatch) {
-            uint32_t v[kBatch];
-#pragma unroll
-            for (int c = 0; c < kBatch; c += 4) ptx::tmem_ld_x4(base + c0 + c, v + c);
-            ptx::tmem_wait_ld();
+          // 8 columns per tcgen05.ld (and per wait), a last load of 4 when kCols is not a multiple
+          // of 8: the fewer instructions the epilogue warps issue, the less they slow the MMA issuer
+          auto add_cols = [&](int c0, const uint32_t* v, int w) {
             if (lsh == 0) {
 #pragma unroll
-              for (int c = 0; c < kBatch; ++c) {
-                const float t = fmaf(__uint_as_float(v[c]), fs, kMagic);
-                acc[c0 + c] += (unsigned long long)__float_as_uint(t) * (unsigned long long)mu;
+              for (int c = 0; c < 8; ++c) {
+                if (c < w) {
+                  const float t = fmaf(__uint_as_float(v[c]), fs, kMagic);
+                  acc[c0 + c] += (unsigned long long)__float_as_uint(t) * (unsigned long long)mu;
+                }
               }
             } else {
 #pragma unroll
-              for (int c = 0; c < kBatch; ++c)
-                acc[c0 + c] += (unsigned long long)__float_as_uint(__uint_as_float(v[c]) + kMagic) << lsh;
+              for (int c = 0; c < 8; ++c)
+                if (c < w) acc[c0 + c] += (unsigned long long)__float_as_uint(__uint_as_float(v[c]) + kMagic) << lsh;
             }
+          };
+#pragma unroll
+          for (int c0 = 0; c0 + 8 <= kCols; c0 += 8) {
+            uint32_t v[8];
+            ptx::tmem_ld_x8(base + c0, v);
+            ptx::tmem_wait_ld();
+            add_cols(c0, v, 8);
+          }
+          if constexpr (kCols % 8 != 0) {
+            constexpr int c0 = kCols - 4;
+            uint32_t v[8];
+            ptx::tmem_ld_x4(base + c0, v);
+            ptx::tmem_wait_ld();
+            add_cols(c0, v, 4);
           }
         }
         ptx::tc_fence_before();
