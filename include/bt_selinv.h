@@ -441,7 +441,8 @@ BT_API bt_status bt_debug_cache_config(int config);
  * launches, mode 1 = one CTA per 128-row tile, 2 = CTA pairs (tcgen05 cta_group::2: a pair of
  * CTAs on two SMs computes two 128-row tiles that share their At tile, each CTA holding half of
  * it) wherever the shape has two or more 128-row tiles and the device holds most SMs as pairs,
- * 0 = the default.  Results are bitwise the same either way (exact fixed-point accumulation).
+ * 3 = CTA pairs whose pipeline stages hold two 64-deep K blocks (half the waits and commits per
+ * MMA, three stages), 0 = the default.  Results are bitwise the same either way (exact fixed-point accumulation).
  * Process-wide, read when a launch is issued. */
 BT_API void bt_debug_split_pair(int mode);
 

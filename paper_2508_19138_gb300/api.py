@@ -303,7 +303,8 @@ def bt_debug_mma_issue_rate(busy_warps: int, wait: bool = False, stream=None) ->
 
 
 def bt_debug_split_pair(mode: int) -> None:
-    """Measurement aid: tensor-core GEMM CTA arrangement (1 = single CTAs, 2 = CTA pairs, 0 = default)."""
+    """Measurement aid: tensor-core GEMM CTA arrangement (1 = single CTAs, 2 = CTA pairs, 3 = CTA pairs
+    with two K blocks per stage, 0 = default)."""
     N.load().bt_debug_split_pair(int(mode))
 
 

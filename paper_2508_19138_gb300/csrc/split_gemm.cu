@@ -149,7 +149,8 @@ __device__ __forceinline__ double fix_to_double(long long v, int e) {
 // 1 KB alignment pad and the barriers, at most 8.  A stage holds the Bt tile (128 rows) and the At
 // rows of this CTA: both At tiles of a dual job on one CTA, one of them on each CTA of a pair.
 __host__ __device__ constexpr int stage_bytes_for(int nt, int pair) {
-  return kTileM * 128 + (pair ? 1 : 2) * nt * 128;
+  // pair 2: CTA pairs whose stages hold two K blocks
+  return pair == 2 ? 2 * (kTileM * 128 + nt * 128) : kTileM * 128 + (pair ? 1 : 2) * nt * 128;
 }
 __host__ __device__ constexpr int stages_for(int nt, int pair) {
   return (227 * 1024 - 1024 - 256) / stage_bytes_for(nt, pair) < 8
@@ -180,6 +181,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                      const __grid_constant__ CUtensorMap tmBh, const MmaParams p) {
   constexpr int kABytes = kTileM * 128;
   constexpr int kBBytes = NT * 128;
+  // PAIR: 0 one CTA per tile; 1 CTA pairs; 2 CTA pairs with two K blocks per pipeline stage
+  constexpr bool PAIRED = PAIR != 0;
+  constexpr int KPS = PAIR == 2 ? 2 : 1;  // K blocks per stage
   constexpr int kStages = stages_for(NT, PAIR);
   constexpr int kStageBytes = stage_bytes_for(NT, PAIR);
   constexpr int kCols = NT / (kEpiWarps / 4);  // accumulator columns per epilogue thread
@@ -188,8 +192,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   static_assert(NT % 16 == 0 && NT >= 16 && NT <= 256, "UMMA N");
   static_assert(4 * NT <= 512, "two double-buffered accumulator pairs must fit in TMEM");
   // one CTA: M = 128; a pair: M = 256, rows 0..127 in the leader (rank 0), 128..255 in its peer
-  constexpr uint32_t kIdesc = ptx::idesc_bf16_f32(PAIR ? 2 * kTileM : kTileM, NT);
-  constexpr uint32_t kIdesc2 = ptx::idesc_bf16_f32(PAIR ? 2 * kTileM : kTileM, 2 * NT);
+  constexpr uint32_t kIdesc = ptx::idesc_bf16_f32(PAIRED ? 2 * kTileM : kTileM, NT);
+  constexpr uint32_t kIdesc2 = ptx::idesc_bf16_f32(PAIRED ? 2 * kTileM : kTileM, 2 * NT);
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
@@ -204,10 +208,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rank = PAIR ? (int)ptx::cluster_ctarank() : 0;
+  const int rank = PAIRED ? (int)ptx::cluster_ctarank() : 0;
   const bool leader = rank == 0;
-  const int cta_unit0 = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;  // first unit of this CTA
-  const int unit_step = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+  const int cta_unit0 = PAIRED ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;  // first unit of this CTA
+  const int unit_step = PAIRED ? (int)(gridDim.x >> 1) : (int)gridDim.x;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -217,14 +221,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int a = 0; a < 2; ++a) {
       ptx::mbar_init(&tfull[a], 1);
       // the leader's MMA reuses an accumulator once the epilogues of both CTAs drained it
-      ptx::mbar_init(&tempty[a], PAIR ? 2 * kEpiWarps : kEpiWarps);
+      ptx::mbar_init(&tempty[a], PAIRED ? 2 * kEpiWarps : kEpiWarps);
     }
     ptx::mbar_init(drain, 1);
     *abort_flag = 0;
     ptx::fence_barrier_init();
   }
   if (warp == 1) {
-    if constexpr (PAIR) {
+    if constexpr (PAIRED) {
       ptx::tmem_alloc_pair(tmem_slot, 512);
       ptx::tmem_relinquish_pair();
     } else {
@@ -235,7 +239,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   ptx::tc_fence_before();
   // a pair: the peer's barriers and tensor memory exist before any copy or MMA targets them
   // (the cluster barrier is warp-aligned: every warp arrives converged)
-  if constexpr (PAIR) {
+  if constexpr (PAIRED) {
     __syncwarp();
     ptx::cluster_sync_all();
   } else {
@@ -248,14 +252,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   // every role of both CTAs walks the same units in the same order and skips the same entries
   auto fail = [&](int b) {
     *abort_flag = 1;
-    if constexpr (PAIR) {  // stop the peer too (its shared memory lives until the final barrier)
+    if constexpr (PAIRED) {  // stop the peer too (its shared memory lives until the final barrier)
       const uint32_t peer = ptx::mapa_shared(ptx::smem_u32((const void*)abort_flag), (uint32_t)(rank ^ 1));
       asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(peer), "r"(1) : "memory");
     }
     if (p.err) atomicCAS(&p.err[(long long)b * p.err_stride], 0, (int)BT_ERR_TIMEOUT);
   };
   auto wait = [&](uint64_t* bar, uint32_t parity) {
-    if constexpr (PAIR) return ptx::mbar_wait_bounded_cluster(bar, parity, abort_flag, kWaitLimitNs);
+    if constexpr (PAIRED) return ptx::mbar_wait_bounded_cluster(bar, parity, abort_flag, kWaitLimitNs);
     else return ptx::mbar_wait_bounded(bar, parity, abort_flag, kWaitLimitNs);
   };
 
@@ -264,7 +268,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       ptx::prefetch_tensormap(&tmA);
       ptx::prefetch_tensormap(&tmB);
-      if constexpr (PAIR) ptx::prefetch_tensormap(&tmBh);
+      if constexpr (PAIRED) ptx::prefetch_tensormap(&tmBh);
       int stage = 0;
       uint32_t phase = 0;
       int issued = 0;
@@ -277,12 +281,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int g = 0; g < sc.n_jobs && ok; ++g) {
           const bool dual = sc.dual[g] != 0;
           // bytes landing in this CTA per stage; a pair's leader expects both CTAs' bytes
-          const uint32_t own = (uint32_t)(kABytes + (PAIR ? (dual ? kBBytes : kBBytes / 2)
+          const uint32_t own = (uint32_t)(kABytes + (PAIRED ? (dual ? kBBytes : kBBytes / 2)
                                                           : (dual ? 2 : 1) * kBBytes));
           const int ie = sc.ie[g], kb0 = sc.kb0[g], kb1 = sc.kb1[g];
           for (int it = sc.ib[g]; it < ie && ok; ++it) {
             const int ct = zA + sc.t[it], cs = zB + sc.s[it], cs2 = zB + sc.s2[it];
-            for (int kb = kb0; kb < kb1; ++kb) {
+            for (int kb = kb0; kb < kb1; kb += KPS) {
+              const int nk = (KPS == 2 && kb + 1 < kb1) ? 2 : 1;  // K blocks in this stage
               const long long c0 = PROF ? clock64() : 0;
               if (!wait(&empty[stage], phase ^ 1u)) {
                 fail(b);
@@ -291,12 +296,17 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
               if constexpr (PROF) t_empty += clock64() - c0;
               uint8_t* st = stages + stage * kStageBytes;
-              if constexpr (PAIR) {
+              if constexpr (PAIRED) {
+                // stage: the Bt tiles of its K blocks, then their At tiles
                 const uint32_t fb = ptx::mapa_shared(ptx::smem_u32(&full[stage]), 0u);  // the leader's
-                if (leader) ptx::mbar_arrive_expect_tx(&full[stage], 2u * own);
-                ptx::tma_load_3d_pair(st, &tmA, fb, kb * kKBlock, m0, ct);
-                if (dual) ptx::tma_load_3d_pair(st + kABytes, &tmB, fb, kb * kKBlock, n0, leader ? cs : cs2);
-                else ptx::tma_load_3d_pair(st + kABytes, &tmBh, fb, kb * kKBlock, n0 + rank * (NT / 2), cs);
+                if (leader) ptx::mbar_arrive_expect_tx(&full[stage], 2u * own * (uint32_t)nk);
+                for (int h = 0; h < nk; ++h) {
+                  const int kx = (kb + h) * kKBlock;
+                  uint8_t* sb = st + KPS * kABytes + h * kBBytes;
+                  ptx::tma_load_3d_pair(st + h * kABytes, &tmA, fb, kx, m0, ct);
+                  if (dual) ptx::tma_load_3d_pair(sb, &tmB, fb, kx, n0, leader ? cs : cs2);
+                  else ptx::tma_load_3d_pair(sb, &tmBh, fb, kx, n0 + rank * (NT / 2), cs);
+                }
               } else {
                 ptx::mbar_arrive_expect_tx(&full[stage], own);
                 ptx::tma_load_3d(st, &tmA, &full[stage], kb * kKBlock, m0, ct);
@@ -314,7 +324,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // let the loads already in flight land before the CTA exits (bounded): one CTA waits for
         // its last stages' barriers; a pair's copies signal the leader, so both wait a while
         volatile int never = 0;
-        if (!PAIR) {
+        if (!PAIRED) {
           for (int idx = issued > kStages ? issued - kStages : 0; idx < issued; ++idx)
             ptx::mbar_wait_bounded(&full[idx % kStages], (uint32_t)((idx / kStages) & 1), &never, kWaitLimitNs);
         } else {
@@ -376,7 +386,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int ie = sc.ie[g], kb0 = sc.kb0[g], kb1 = sc.kb1[g];
           uint32_t acc0 = 0u;  // the job's first MMA overwrites the accumulators
           for (int it = sc.ib[g]; it < ie && ok; ++it) {
-            for (int kb = kb0; kb < kb1; ++kb) {
+            for (int kb = kb0; kb < kb1; kb += KPS) {
+              const int nk = (KPS == 2 && kb + 1 < kb1) ? 2 : 1;  // K blocks in this stage
               const long long cf = PROF ? clock64() : 0;
               if (!wait(&full[stage], phase)) {
                 fail(b);
@@ -388,16 +399,24 @@ __global__ void __launch_bounds__(kThreads, 1)
               // K step k starts 32 bytes further: +2 in the descriptor's address field (stage
               // addresses are below 256 KB, so the 14-bit field cannot carry into the next one)
 #pragma unroll
-              for (int k = 0; k < kKBlock / 16; ++k) {
-                const uint64_t ad = ((uint64_t)d_hi << 32) | (uint64_t)(a_lo + 2u * k);
-                const uint64_t bd = ((uint64_t)d_hi << 32) | (uint64_t)(a_lo + kBLo + 2u * k);
-                if constexpr (PAIR)
-                  ptx::umma_f16_pair(dcol0, ad, bd, idesc, k == 0 ? acc0 : 1u);
-                else
-                  ptx::umma_f16(dcol0, ad, bd, idesc, k == 0 ? acc0 : 1u);
+              for (int h = 0; h < KPS; ++h) {
+                if (h < nk) {
+                  const uint32_t alo = a_lo + (uint32_t)h * kBLo;
+                  const uint32_t blo = a_lo + (uint32_t)KPS * kBLo + (uint32_t)h * ((uint32_t)kBBytes >> 4);
+#pragma unroll
+                  for (int k = 0; k < kKBlock / 16; ++k) {
+                    const uint64_t ad = ((uint64_t)d_hi << 32) | (uint64_t)(alo + 2u * k);
+                    const uint64_t bd = ((uint64_t)d_hi << 32) | (uint64_t)(blo + 2u * k);
+                    const uint32_t acc = (h == 0 && k == 0) ? acc0 : 1u;
+                    if constexpr (PAIRED)
+                      ptx::umma_f16_pair(dcol0, ad, bd, idesc, acc);
+                    else
+                      ptx::umma_f16(dcol0, ad, bd, idesc, acc);
+                  }
+                }
               }
               acc0 = 1u;
-              if constexpr (PAIR) ptx::umma_commit_pair_mc(&empty[stage], (uint16_t)0x3);
+              if constexpr (PAIRED) ptx::umma_commit_pair_mc(&empty[stage], (uint16_t)0x3);
               else ptx::umma_commit(&empty[stage]);
               if (++stage == kStages) {
                 stage = 0;
@@ -409,13 +428,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
           if (ok) {
-            if constexpr (PAIR) ptx::umma_commit_pair_mc(&tfull[ab], (uint16_t)0x3);
+            if constexpr (PAIRED) ptx::umma_commit_pair_mc(&tfull[ab], (uint16_t)0x3);
             else ptx::umma_commit(&tfull[ab]);
           }
         }
       }
       // every MMA this thread issued has completed once `drain` fires
-      if constexpr (PAIR) ptx::umma_commit_pair_mc(drain, (uint16_t)0x1);
+      if constexpr (PAIRED) ptx::umma_commit_pair_mc(drain, (uint16_t)0x1);
       else ptx::umma_commit(drain);
       volatile int never = 0;
       ptx::mbar_wait_bounded(drain, 0, &never, kWaitLimitNs);
@@ -495,7 +514,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         ptx::tc_fence_before();
         __syncwarp();
         if (lane == 0) {
-          if constexpr (PAIR) ptx::mbar_arrive_remote(ptx::mapa_shared(ptx::smem_u32(&tempty[ab]), 0u));
+          if constexpr (PAIRED) ptx::mbar_arrive_remote(ptx::mapa_shared(ptx::smem_u32(&tempty[ab]), 0u));
           else ptx::mbar_arrive(&tempty[ab]);
         }
         if constexpr (PROF) t_drain += clock64() - cd;
@@ -579,7 +598,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   // ---------------- teardown ----------------
   ptx::tc_fence_before();
-  if constexpr (PAIR) {
+  if constexpr (PAIRED) {
     // the leader's MMAs write the peer's tensor memory and its commits signal the peer's
     // barriers: both CTAs are done with both before either frees its tensor memory
     __syncwarp();
@@ -944,7 +963,7 @@ int num_sms() {
 }
 
 // Clusters of two CTAs of the pair kernel that can be resident at once (per device and N tile).
-template <int NT>
+template <int NT, int PAIR>
 int pair_clusters() {
   static std::mutex mu;
   static int val[64];
@@ -956,7 +975,7 @@ int pair_clusters() {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(2);
   cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = smem_for(NT, 1);
+  cfg.dynamicSmemBytes = smem_for(NT, PAIR);
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = 2;
@@ -965,9 +984,9 @@ int pair_clusters() {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int nc = 0;
-  if (cudaFuncSetAttribute(split_mma_kernel<NT, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem_for(NT, 1)) != cudaSuccess ||
-      cudaOccupancyMaxActiveClusters(&nc, split_mma_kernel<NT, 1, false>, &cfg) != cudaSuccess) {
+  if (cudaFuncSetAttribute(split_mma_kernel<NT, PAIR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem_for(NT, PAIR)) != cudaSuccess ||
+      cudaOccupancyMaxActiveClusters(&nc, split_mma_kernel<NT, PAIR, false>, &cfg) != cudaSuccess) {
     (void)cudaGetLastError();
     nc = 0;
   }
@@ -996,9 +1015,9 @@ bt_status launch_mma(cudaStream_t st, const CUtensorMap& mA, const CUtensorMap& 
   }
   const int sms = num_sms();
   if (sms <= 0) return BT_ERR_CUDA;
-  if constexpr (PAIR) {
+  if constexpr (PAIR != 0) {
     // persistent: as many CTA pairs as can be resident, units walked in order
-    const int nc = pair_clusters<NT>();
+    const int nc = pair_clusters<NT, PAIR>();
     if (nc <= 0) return BT_ERR_UNSUPPORTED;
     const int clusters = p.n_units < nc ? p.n_units : nc;
     cudaLaunchConfig_t cfg = {};
@@ -1013,7 +1032,7 @@ bt_status launch_mma(cudaStream_t st, const CUtensorMap& mA, const CUtensorMap& 
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    BT_CUDA_TRY(cudaLaunchKernelEx(&cfg, split_mma_kernel<NT, 1, PROF>, mA, mB, mBh, p));
+    BT_CUDA_TRY(cudaLaunchKernelEx(&cfg, split_mma_kernel<NT, PAIR, PROF>, mA, mB, mBh, p));
   } else {
     // persistent: one CTA per SM (1 CTA fits per SM by shared memory), tiles walked in order
     const int grid = p.n_units < sms ? p.n_units : sms;
@@ -1044,22 +1063,20 @@ bt_status launch_mma_nt(int nt, cudaStream_t st, const CUtensorMap& mA, const CU
   }
 }
 
-int pair_clusters_nt(int nt) {
-  switch (nt) {
-    case 16: return pair_clusters<16>();
-    case 32: return pair_clusters<32>();
-    case 48: return pair_clusters<48>();
-    case 64: return pair_clusters<64>();
-    case 80: return pair_clusters<80>();
-    case 96: return pair_clusters<96>();
-    case 112: return pair_clusters<112>();
-    case 128: return pair_clusters<128>();
+int pair_clusters_nt(int nt, int pair) {
+  switch (nt * 4 + pair) {
+#define BT_PAIR_CASE(N)                                 \
+  case N * 4 + 1: return pair_clusters<N, 1>();        \
+  case N * 4 + 2: return pair_clusters<N, 2>();
+    BT_PAIR_CASE(16) BT_PAIR_CASE(32) BT_PAIR_CASE(48) BT_PAIR_CASE(64)
+    BT_PAIR_CASE(80) BT_PAIR_CASE(96) BT_PAIR_CASE(112) BT_PAIR_CASE(128)
+#undef BT_PAIR_CASE
     default: return 0;
   }
 }
 
 // CTA-pair mode (bt_debug_split_pair): 0 = the default rule, 1 = one CTA per tile always,
-// 2 = pairs whenever the shape allows them
+// 2 = pairs whenever the shape allows them, 3 = pairs with two K blocks per pipeline stage
 std::atomic<int> g_pair_mode{0};
 
 constexpr int kMaxKc = 1024;  // complex k per launch (slice workspace); K' = 2k <= 2048 = 32 K blocks
@@ -1192,8 +1209,9 @@ bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A,
     const int tiles_x = n2p / kTileM;
     const int mode = g_pair_mode.load();
     bool pair = false;
-    if (mode == 2 && tiles_x >= 2) {
-      const int nc = pair_clusters_nt(nt);
+    const int pair_kind = mode == 3 ? 2 : 1;
+    if ((mode == 2 || mode == 3) && tiles_x >= 2) {
+      const int nc = pair_clusters_nt(nt, pair_kind);
       pair = nc > 0 && 2 * nc >= (num_sms() * 9) / 10;
     }
     CUtensorMap mA, mB, mBh;
@@ -1233,7 +1251,8 @@ bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A,
     p.a_shared = a_shared ? 1 : 0;
     p.b_shared = b_shared ? 1 : 0;
     if (!make_schedule(S, Kp / kKBlock, &p.sched, &p.bias, &p.fix_bits)) return BT_ERR_UNSUPPORTED;
-    if (pair) BT_TRY(launch_mma_nt<1>(nt, st, mA, mB, mBh, p));
+    if (pair && pair_kind == 2) BT_TRY(launch_mma_nt<2>(nt, st, mA, mB, mBh, p));
+    else if (pair) BT_TRY(launch_mma_nt<1>(nt, st, mA, mB, mBh, p));
     else BT_TRY(launch_mma_nt<0>(nt, st, mA, mB, mBh, p));
   }
   return BT_OK;
@@ -1265,7 +1284,7 @@ extern "C" bt_status bt_debug_split_profile(int enable, unsigned long long* coun
   return BT_OK;
 }
 
-extern "C" void bt_debug_split_pair(int mode) { bt::g_pair_mode.store(mode == 1 || mode == 2 ? mode : 0); }
+extern "C" void bt_debug_split_pair(int mode) { bt::g_pair_mode.store(mode >= 1 && mode <= 3 ? mode : 0); }
 
 extern "C" void bt_debug_split_stall(unsigned long long ns, long long launches) {
   bt::g_stall_left.store(launches);

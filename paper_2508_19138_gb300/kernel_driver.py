@@ -41,7 +41,8 @@ def main():
     ap.add_argument("--cache-config", type=int, default=-1,
                     help="preferred L1 / shared split for the run (0 none, 1 shared, 2 L1, 3 equal; -1 untouched)")
     ap.add_argument("--split-pair", type=int, default=0,
-                    help="split: 1 = single CTAs, 2 = CTA pairs (cta_group::2), 0 = default; with --check both")
+                    help="split: 1 = single CTAs, 2 = CTA pairs (cta_group::2), 3 = pairs with two K blocks per "
+                         "stage, 0 = default; with --check all three")
     ap.add_argument("--check", action="store_true",
                     help="split: compare the result of single CTAs and CTA pairs bitwise, and with torch")
     ap.add_argument("--split-profile", action="store_true",
@@ -92,7 +93,7 @@ def main():
     check = None
     if a.kernel == "split" and a.check:
         outs = {}
-        for mode in (1, 2):
+        for mode in (1, 2, 3):
             pkg.bt_debug_split_pair(mode)
             C.zero_()
             pkg.bt_split_zgemm_batched(n, n, kk, 1.0, A, kk, n * kk, 0, B, n, kk * n, 0, 0.0, C, n, n * n, b,
@@ -102,6 +103,7 @@ def main():
         ref = torch.matmul(A, B)
         rel = (torch.linalg.norm(outs[2] - ref) / torch.linalg.norm(ref)).item()
         check = {"bitwise_equal": bool(torch.equal(outs[1], outs[2])),
+                 "bitwise_equal_pair_kps2": bool(torch.equal(outs[1], outs[3])),
                  "max_abs_diff": (outs[1] - outs[2]).abs().max().item(), "rel_err_vs_torch_pair": rel,
                  "rel_err_vs_torch_single": (torch.linalg.norm(outs[1] - ref) / torch.linalg.norm(ref)).item()}
         pkg.bt_debug_split_pair(a.split_pair)

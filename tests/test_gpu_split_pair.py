@@ -1,4 +1,5 @@
-"""The tensor-core GEMM on CTA pairs (tcgen05 cta_group::2) against the one-CTA kernel.
+"""The tensor-core GEMM on CTA pairs (tcgen05 cta_group::2; pipeline stages of one or two K
+blocks) against the one-CTA kernel.
 
 Both compute every slice-pair product exactly in fp32 and sum them in the same uint64 fixed point,
 so their results are bitwise equal, whatever the shape (an odd number of 128-row tiles pads the
@@ -45,7 +46,9 @@ def test_pair_bitwise_equals_single_cta(m, n, k, batch, opA, opB, alpha, beta):
     C0 = torch.randn(batch, m, n, dtype=torch.complex128, device="cuda", generator=g)
     c1 = _run(pkg, torch, 1, m, n, k, batch, opA, opB, alpha, beta, A, B, C0)
     c2 = _run(pkg, torch, 2, m, n, k, batch, opA, opB, alpha, beta, A, B, C0)
+    c3 = _run(pkg, torch, 3, m, n, k, batch, opA, opB, alpha, beta, A, B, C0)  # two K blocks per stage
     assert torch.equal(c1, c2), (c1 - c2).abs().max().item()
+    assert torch.equal(c1, c3), (c1 - c3).abs().max().item()
     # against the exact product (FP64 on the host)
     a = A.cpu().numpy()
     b = B.cpu().numpy()
