@@ -442,7 +442,8 @@ BT_API bt_status bt_debug_cache_config(int config);
  * CTAs on two SMs computes two 128-row tiles that share their At tile, each CTA holding half of
  * it) wherever the shape has two or more 128-row tiles and the device holds most SMs as pairs,
  * 3 = CTA pairs whose pipeline stages hold two 64-deep K blocks (half the waits and commits per
- * MMA, three stages), 0 = the default.  Results are bitwise the same either way (exact fixed-point accumulation).
+ * MMA, three stages), 0 = the default (mode 3 when the 2n rows of C^T are an even number of
+ * 128-row tiles, else mode 1).  Results are bitwise the same either way (exact fixed-point accumulation).
  * Process-wide, read when a launch is issued. */
 BT_API void bt_debug_split_pair(int mode);
 
