@@ -447,6 +447,27 @@ BT_API bt_status bt_debug_cache_config(int config);
  * Process-wide, read when a launch is issued. */
 BT_API void bt_debug_split_pair(int mode);
 
+/* Measurement aid (no counterpart in the paper): how the tensor-core GEMM groups the slice-pair
+ * products of one K segment into TMEM accumulators for later launches.  mode 0 (default): the
+ * pairs of one weight class s + t share an accumulator while its fp32 sum stays an exact integer
+ * (below 2^24), classes two by two in dual jobs, a lane of several pairs drained by an exact
+ * float -> int conversion; mode 1: one pair per accumulator (several only in short segments, below
+ * 2^22).  Both sum the same exact products into the same fixed point; they round the classes of
+ * weight below 2^-F (F = the fixed point's fraction bits) at different points, so results agree
+ * to that resolution, not bitwise.  Process-wide, read when a launch is issued. */
+BT_API void bt_debug_split_sched(int mode);
+
+/* Host-only query (no GPU work): the accumulation schedule of the tensor-core GEMM for `slices`
+ * slices per operand and k_blocks 64-deep K blocks (K' = 64 k_blocks real terms), mode as in
+ * bt_debug_split_sched.  Writes up to max_jobs rows of 8 ints to `jobs` (dual, first item, end
+ * item, first K block, end K block, lane 0 converted exactly, lane 1 converted exactly, 0), up to
+ * max_items rows of 3 ints to `items` (slice s of op(A) for lane 0, slice s2 for lane 1, slice t
+ * of op(B); 1-based), and the fixed point's fraction bits F to *fix_bits (any pointer may be
+ * NULL).  Returns the number of jobs, or -1 for unsupported arguments (slices outside 2..8,
+ * k_blocks outside 1..255, or a schedule beyond the kernel's job or item capacity). */
+BT_API int bt_debug_split_schedule(int slices, int k_blocks, int mode, int* jobs, int max_jobs, int* items,
+                                   int max_items, int* fix_bits);
+
 /* Measurement aid (no counterpart in the paper): the busy fraction of the tensor pipe when one
  * thread per SM issues tcgen05.mma (M = 128, N = 224, K = 16; four per 64-deep K block and a
  * commit, the GEMM's pattern) on operands already in shared memory, while busy_warps (0..16)

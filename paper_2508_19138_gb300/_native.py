@@ -78,12 +78,15 @@ SIGNATURES = {
     "bt_debug_split_profile": [_I, C.POINTER(C.c_ulonglong), _I],
     "bt_debug_cache_config": [_I],
     "bt_debug_split_pair": [_I],
+    "bt_debug_split_sched": [_I],
+    "bt_debug_split_schedule": [_I, _I, _I, C.POINTER(_I), _I, C.POINTER(_I), _I, C.POINTER(_I)],
     "bt_debug_mma_issue_rate": [_I, _I, C.POINTER(_D), _P],
     "bt_energy_convolve": [_I, _I, _I, _I, _I, _P, _LL, _P, _LL, _P, _LL, _D, _D, _I, _P],
     "bt_decimate_workspace_bytes": [_I, _I, C.POINTER(C.c_size_t)],
     "bt_decimate_batched": [_I, _I, _P, _P, _P, _D, _I, _P, _P, _P, _P, _P, _SZ, _P],
 }
-RESTYPES = {"bt_selinv_last_error": C.c_char_p, "bt_debug_split_stall": None, "bt_debug_panel_cluster": None, "bt_debug_split_pair": None}
+RESTYPES = {"bt_selinv_last_error": C.c_char_p, "bt_debug_split_stall": None, "bt_debug_panel_cluster": None, "bt_debug_split_pair": None,
+            "bt_debug_split_sched": None}
 
 _lib = None
 

@@ -17,7 +17,7 @@ __all__ = [
     "bt_selinv_solve", "bt_selinv_solve_host", "bt_selinv_destroy", "bt_selinv_last_error", "bt_selinv_get_stats",
     "bt_zgemm_batched", "bt_split_zgemm_workspace_bytes", "bt_split_zgemm_batched", "bt_zinv_workspace_bytes",
     "bt_zinv_batched", "bt_zinv_batched_noalloc", "bt_decimate_workspace_bytes", "bt_decimate_batched", "library",
-    "bt_debug_split_stall", "bt_debug_fp64_rate", "bt_debug_panel_cluster", "bt_debug_split_profile", "bt_debug_cache_config", "bt_debug_split_pair", "bt_debug_mma_issue_rate", "bt_energy_convolve",
+    "bt_debug_split_stall", "bt_debug_fp64_rate", "bt_debug_panel_cluster", "bt_debug_split_profile", "bt_debug_cache_config", "bt_debug_split_pair", "bt_debug_split_sched", "bt_debug_split_schedule", "bt_debug_mma_issue_rate", "bt_energy_convolve",
 ]
 
 
@@ -306,6 +306,29 @@ def bt_debug_split_pair(mode: int) -> None:
     """Measurement aid: tensor-core GEMM CTA arrangement (1 = single CTAs, 2 = CTA pairs, 3 = CTA pairs
     with two K blocks per stage, 0 = default)."""
     N.load().bt_debug_split_pair(int(mode))
+
+
+def bt_debug_split_sched(mode: int) -> None:
+    """Measurement aid: tensor-core GEMM accumulation schedule (0 = merged weight classes, the
+    default; 1 = one slice pair per accumulator)."""
+    N.load().bt_debug_split_sched(int(mode))
+
+
+def bt_debug_split_schedule(slices: int, k_blocks: int, mode: int = 0):
+    """Host-only query of the tensor-core GEMM's accumulation schedule: (jobs, items, F) with jobs
+    as rows (dual, first item, end item, first K block, end K block, cvt lane 0, cvt lane 1, 0)
+    and items as rows (s, s2, t); None for unsupported arguments."""
+    cap_j, cap_i = 256, 256
+    jobs = (C.c_int * (8 * cap_j))()
+    items = (C.c_int * (3 * cap_i))()
+    F = C.c_int(0)
+    n = N.load().bt_debug_split_schedule(int(slices), int(k_blocks), int(mode), jobs, cap_j, items, cap_i,
+                                         C.byref(F))
+    if n < 0:
+        return None
+    rows = [tuple(jobs[8 * g:8 * g + 8]) for g in range(n)]
+    n_items = rows[-1][2] if rows else 0
+    return rows, [tuple(items[3 * i:3 * i + 3]) for i in range(n_items)], F.value
 
 
 def bt_debug_cache_config(config: int) -> None:

@@ -17,19 +17,22 @@
 //     v ~= R * 2^-6 * sum_s d_s 2^(-7(s-1)),
 // and a product of digits is an integer of magnitude <= 2^12.
 //
-// Accumulation.  Pairs (s, t) with s + t <= S + 1 are used.  Each pair, over one K segment of at
-// most 960 real terms, is accumulated in a TMEM fp32 accumulator (short segments sum several
-// pairs of equal weight in one): its value is an integer below 2^22, so the tensor core's fp32
-// sum is exact.  The drain adds 1.5 * 2^23 to it (one FFMA, which also applies the 2^-p
-// pre-scale of the low-order pairs); the bits of that float are then 0x4B400000 + the integer,
-// and one 32 x 32 -> 64-bit multiply-add accumulates them with the pair's weight 2^(F - 7w + p)
-// into a per-thread uint64 fixed-point sum (units of 2^-F of a leading digit product,
-// arithmetic mod 2^64).  The known sum of the 0x4B400000 biases is subtracted once at the end,
-// giving the exact (to 2^-F) two's-complement value, converted to double once per output.
+// Accumulation.  Pairs (s, t) with s + t <= S + 1 are used.  Over one K segment of at most 960
+// real terms, the pairs of one weight class w = s + t - 2 are summed in TMEM fp32 accumulators,
+// as many per accumulator as keep its value an integer below 2^24, so the tensor core's fp32
+// sum is exact.  An accumulator holding one pair (below 2^22) is drained by adding 1.5 * 2^23
+// (one FFMA, which also applies the 2^-p pre-scale of the low-order pairs): the bits of that
+// float are then 0x4B400000 + the integer, and one 32 x 32 -> 64-bit multiply-add accumulates
+// them with the class weight 2^(F - 7w + p) into a per-thread uint64 fixed-point sum (units of
+// 2^-F of a leading digit product, arithmetic mod 2^64); one holding several pairs is converted
+// exactly (float -> int32) and added as a signed integer.  The known sum of the 0x4B400000
+// biases is subtracted once at the end, giving the exact (to 2^-F) two's-complement value,
+// converted to double once per output.
 //
-// Pairs (s, t), (s + 1, t) of a long segment form a dual job: their At tiles are adjacent in a
-// pipeline stage and their accumulators adjacent in TMEM, so one M = 128, N = 2 NT MMA per K
-// step serves both and reads the Bt tile once.
+// Classes go two by two (w, w + 1) into dual jobs: item t holds the pairs (s, t) and (s + 1, t)
+// of the two classes, whose At tiles are adjacent in a pipeline stage and whose accumulators are
+// adjacent in TMEM, so one M = 128, N = 2 NT MMA per K step serves both and reads the Bt tile
+// once.
 //
 // Kernel shape: a persistent grid of one CTA per SM walks the 128 x NT output tiles of C^T
 // (all batch entries); warp 0 issues TMA loads (3-D tensor maps over [batch*S][rows][K'],
@@ -41,7 +44,9 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include <atomic>
 #include "bt_common.cuh"
@@ -68,10 +73,11 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
 enum ProfSlot : int { kProfMmaWaitFull = 0, kProfMmaWaitAcc, kProfMmaLoop, kProfTmaWaitEmpty, kProfEpiDrain,
                       kProfEpiWrite, kProfTiles, kProfSlots };
 
-// One job = one accumulation round over K blocks [kb0, kb1), drained once:
-//  * dual job: two TMEM accumulators (lanes) fed by one item (t, s, s2): the pairs (s, t) and
+// One job = one accumulation round over K blocks [kb0, kb1) and the items [ib, ie), drained once:
+//  * dual job: two TMEM accumulators (lanes) fed by items (t, s, s2): the pairs (s, t) and
 //    (s2, t) share op(B)'s slice t, so each K block loads the Bt tile once for eight MMAs;
-//  * single job: one accumulator summing the pairs of items [ib, ie) (equal weights).
+//  * single job: one accumulator summing the pairs (s, t) of its items.
+// The pairs summed in one lane have equal weights.
 struct Schedule {
   int n_jobs;
   unsigned char dual[kMaxJobs];
@@ -79,7 +85,8 @@ struct Schedule {
   unsigned char ie[kMaxJobs];
   unsigned char kb0[kMaxJobs];
   unsigned char kb1[kMaxJobs];
-  unsigned char lsh[kMaxJobs][2];  // weight 2^(F - 7w) > 2^31: shift instead of multiply
+  unsigned char lsh[kMaxJobs][2];  // weight 2^(F - 7w) > 2^31 (2^30 for cvt): shift, not multiply
+  unsigned char cvt[kMaxJobs][2];  // lane sums several pairs (may exceed 2^22): exact float -> int
   uint32_t mult[kMaxJobs][2];      // weight 2^(F - 7w) <= 2^31 (after the pre-scale)
   float fscale[kMaxJobs][2];       // 2^-p: pre-scale of pairs with F - 7w < 0
   unsigned char s[kMaxItems];      // slice of op(A) (1-based), lane 0
@@ -476,13 +483,30 @@ __global__ void __launch_bounds__(kThreads, 1)
           const float fs = sc.fscale[g][l];
           const uint32_t mu = sc.mult[g][l];
           const int lsh = sc.lsh[g][l];
+          const bool cvt = sc.cvt[g][l] != 0;
           const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (2u * ab + (uint32_t)l) * (uint32_t)NT +
                                 (uint32_t)(cq * kCols);
 #pragma unroll
           // 8 columns per tcgen05.ld (and per wait), a last load of 4 when kCols is not a multiple
           // of 8: the fewer instructions the epilogue warps issue, the less they slow the MMA issuer
           auto add_cols = [&](int c0, const uint32_t* v, int w) {
-            if (lsh == 0) {
+            if (cvt) {
+              // several pairs: an integer below 2^24, pre-scaled and rounded to int32 (exact for
+              // the classes of weight >= 2^-F, as in the FFMA path otherwise)
+              if (lsh == 0) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                  if (c < w) {
+                    const int iv = __float2int_rn(__uint_as_float(v[c]) * fs);
+                    acc[c0 + c] += (unsigned long long)((long long)iv * (long long)(int)mu);
+                  }
+                }
+              } else {
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                  if (c < w) acc[c0 + c] += (unsigned long long)(long long)__float2int_rn(__uint_as_float(v[c])) << lsh;
+              }
+            } else if (lsh == 0) {
 #pragma unroll
               for (int c = 0; c < 8; ++c) {
                 if (c < w) {
@@ -833,80 +857,149 @@ bool encode_slices_map(CUtensorMap* map, void* base, int Kp, int rows, int rows_
   return r == CUDA_SUCCESS;
 }
 
-// Jobs for every slice pair (s, t) with s + t <= S + 1 over each K segment of at most kSegBlocks
-// blocks (balanced).  An accumulator stays an exact fp32 integer below 2^22 while n pairs over L
-// blocks of 64 real terms satisfy n * L < 16 (each term is at most 2^12).
-//  * Long segments (L >= 8, one pair per accumulator): pairs of equal t and consecutive s go two
-//    by two into dual jobs (one Bt tile per K block for both), a leftover pair into a single job.
-//  * Short segments: single jobs summing up to 15 / L pairs of equal weight.
-// A pair of weight w = s + t - 2 enters the fixed-point sum with factor 2^(F - 7w): a shift for
-// factors above 2^31, a 32-bit multiplier down to 2^0, and below that a pre-scale 2^(F - 7w) in
-// the drain's FFMA (rounding below 2^-F of a leading digit product).
+// Jobs for every slice pair (s, t) with s + t <= S + 1 over each K segment of L <= kSegBlocks
+// blocks (balanced).  A term of a pair's sum is a digit product of magnitude <= 2^12, so n pairs
+// over L blocks of 64 real terms sum to an integer below n L 2^18: exact in the fp32 accumulator
+// while n L < 64 (below 2^24), and inside the drain's magic-number range (below 2^22) while
+// n L < 16.
+//  * merged (default): the pairs of one weight class d = s + t share accumulators, up to 63 / L
+//    each.  In long segments (L >= 8) classes go two by two (d, d + 1) into dual jobs: item
+//    t = 1 .. d - 1 holds the pairs (d - t, t) (lane 0) and (d + 1 - t, t) (lane 1), which share
+//    op(B)'s slice t; the pair (1, d) of class d + 1 left over goes into a single job, and so does
+//    a class without a partner.  S = 6, L = 13: 7 jobs and 11 drains per tile instead of 12 and
+//    21.  In short segments, where the drains outweigh the MMAs, one single job per class (S
+//    drains).  Jobs are ordered longest first: a tile's C write overlaps the MMAs of the next
+//    tile's first jobs.
+//  * one pair per accumulator: in long segments (L >= 8) pairs of equal t and consecutive s go
+//    two by two into dual jobs, a leftover pair into a single job; short segments: single jobs
+//    summing up to 15 / L pairs of equal weight.
+// A pair of weight class d enters the fixed-point sum with factor 2^(F - 7(d - 2)): a shift for
+// factors above 2^31 (2^30 for a lane converted to a signed integer), a 32-bit multiplier down
+// to 2^0, and below that a pre-scale 2^(F - 7(d - 2)) before the rounding to an integer
+// (rounding below 2^-F of a leading digit product).
 // F = min(7S - 9, 50 - log2(K')): resolution below the slicing error, and
 // |sum| <= K' * 2^12 * 2^F * (1 + 2^-6) < 2^63.
-bool make_schedule(int S, int KB, Schedule* sc, unsigned long long* bias, int* fix_bits) {
+bool make_schedule(int S, int KB, bool merge, Schedule* sc, unsigned long long* bias, int* fix_bits) {
   *sc = Schedule{};
   int lg = 0;
   while ((1 << lg) < KB * kKBlock) ++lg;
   int F = kDigitBits * S - 9;
   if (F > 50 - lg) F = 50 - lg;
-  unsigned long long bs = 0;
-  int ni = 0, nj = 0;
-  auto set_lane = [&](int j, int l, int d) {
-    const int e = F - kDigitBits * (d - 2);
-    sc->lsh[j][l] = (unsigned char)(e > 31 ? e : 0);
-    sc->mult[j][l] = e > 31 ? 1u : (e >= 0 ? (1u << e) : 1u);
-    sc->fscale[j][l] = e >= 0 ? 1.0f : ldexpf(1.0f, e);
-    bs += (unsigned long long)kMagicBits * ((unsigned long long)sc->mult[j][l] << sc->lsh[j][l]);
+  struct Spec {
+    int kb0, kb1, dual, n;
+    int d[2], cvt[2];
+    int s[kMaxSlices], s2[kMaxSlices], t[kMaxSlices];  // a job holds at most S items
   };
-  auto new_job = [&](int kb0, int kb1, bool dual) {
-    if (nj >= kMaxJobs) return -1;
-    sc->dual[nj] = dual ? 1 : 0;
-    sc->ib[nj] = (unsigned char)ni;
-    sc->ie[nj] = (unsigned char)ni;
-    sc->kb0[nj] = (unsigned char)kb0;
-    sc->kb1[nj] = (unsigned char)kb1;
-    return nj++;
+  std::vector<Spec> jobs;
+  auto open_job = [&](int kb0, int kb1, bool dual, int d0, int d1) -> Spec& {
+    Spec j{};
+    j.kb0 = kb0;
+    j.kb1 = kb1;
+    j.dual = dual ? 1 : 0;
+    j.d[0] = d0;
+    j.d[1] = d1;
+    jobs.push_back(j);
+    return jobs.back();
+  };
+  auto add_item = [](Spec& j, int s, int s2, int t) {
+    if (j.n >= kMaxSlices) return false;
+    j.s[j.n] = s;
+    j.s2[j.n] = s2;
+    j.t[j.n] = t;
+    ++j.n;
+    return true;
   };
   const int nseg = (KB + kSegBlocks - 1) / kSegBlocks;
   for (int seg = 0; seg < nseg; ++seg) {
     const int kb0 = (int)((long long)KB * seg / nseg), kb1 = (int)((long long)KB * (seg + 1) / nseg);
-    const int per_group = 15 / (kb1 - kb0);
-    if (per_group == 1) {
-      for (int t = 1; t <= S; ++t)
-        for (int s = 1; s + t <= S + 1; s += 2) {
-          const bool two = s + 1 + t <= S + 1;
-          const int j = new_job(kb0, kb1, two);
-          if (j < 0 || ni >= kMaxItems) return false;
-          sc->s[ni] = (unsigned char)s;
-          sc->s2[ni] = (unsigned char)(two ? s + 1 : s);
-          sc->t[ni] = (unsigned char)t;
-          sc->ie[j] = (unsigned char)++ni;
-          set_lane(j, 0, s + t);
-          if (two) set_lane(j, 1, s + 1 + t);
-        }
-    } else {
+    const int L = kb1 - kb0;
+    if (merge && L < 8) {
+      // short segment: the drains outweigh the MMAs, so one accumulator per class (S drains)
+      const int nmax = 63 / L;
       for (int d = 2; d <= S + 1; ++d) {
-        int j = -1, in_job = 0;
+        Spec* j = nullptr;
         for (int s = 1; s <= S; ++s) {
           const int t = d - s;
           if (t < 1 || t > S) continue;
-          if (in_job == 0) {
-            j = new_job(kb0, kb1, false);
-            if (j < 0) return false;
-            set_lane(j, 0, d);
+          if (!j || j->n == nmax) j = &open_job(kb0, kb1, false, d, 0);
+          if (!add_item(*j, s, s, t)) return false;
+        }
+      }
+    } else if (merge) {
+      const int nmax = 63 / L;
+      for (int d = 2; d <= S + 1; d += 2) {
+        if (d + 1 <= S + 1) {
+          for (int t0 = 1; t0 <= d - 1; t0 += nmax) {
+            Spec& j = open_job(kb0, kb1, true, d, d + 1);
+            for (int t = t0; t <= d - 1 && t < t0 + nmax; ++t)
+              if (!add_item(j, d - t, d + 1 - t, t)) return false;
           }
-          if (ni >= kMaxItems) return false;
-          sc->s[ni] = (unsigned char)s;
-          sc->s2[ni] = (unsigned char)s;
-          sc->t[ni] = (unsigned char)t;
-          sc->ie[j] = (unsigned char)++ni;
-          if (++in_job == per_group) in_job = 0;
+          Spec& j = open_job(kb0, kb1, false, d + 1, 0);
+          if (!add_item(j, 1, 1, d)) return false;
+        } else {
+          for (int s0 = 1; s0 <= d - 1; s0 += nmax) {
+            Spec& j = open_job(kb0, kb1, false, d, 0);
+            for (int s = s0; s <= d - 1 && s < s0 + nmax; ++s)
+              if (!add_item(j, s, s, d - s)) return false;
+          }
+        }
+      }
+    } else if (15 / L == 1) {
+      for (int t = 1; t <= S; ++t)
+        for (int s = 1; s + t <= S + 1; s += 2) {
+          const bool two = s + 1 + t <= S + 1;
+          Spec& j = open_job(kb0, kb1, two, s + t, s + 1 + t);
+          if (!add_item(j, s, two ? s + 1 : s, t)) return false;
+        }
+    } else {
+      const int per_group = 15 / L;
+      for (int d = 2; d <= S + 1; ++d) {
+        Spec* j = nullptr;
+        for (int s = 1; s <= S; ++s) {
+          const int t = d - s;
+          if (t < 1 || t > S) continue;
+          if (!j || j->n == per_group) j = &open_job(kb0, kb1, false, d, 0);
+          if (!add_item(*j, s, s, t)) return false;
         }
       }
     }
   }
-  sc->n_jobs = nj;
+  for (Spec& j : jobs) {
+    const bool exact_magic = j.n * (j.kb1 - j.kb0) < 16;
+    j.cvt[0] = j.cvt[1] = exact_magic ? 0 : 1;
+  }
+  if (merge)
+    std::stable_sort(jobs.begin(), jobs.end(), [](const Spec& a, const Spec& b) {
+      return a.n * (a.kb1 - a.kb0) * (1 + a.dual) > b.n * (b.kb1 - b.kb0) * (1 + b.dual);
+    });
+  if ((int)jobs.size() > kMaxJobs) return false;
+  unsigned long long bs = 0;
+  int ni = 0;
+  for (int g = 0; g < (int)jobs.size(); ++g) {
+    const Spec& j = jobs[g];
+    if (ni + j.n > kMaxItems) return false;
+    sc->dual[g] = (unsigned char)j.dual;
+    sc->kb0[g] = (unsigned char)j.kb0;
+    sc->kb1[g] = (unsigned char)j.kb1;
+    sc->ib[g] = (unsigned char)ni;
+    for (int i = 0; i < j.n; ++i, ++ni) {
+      sc->s[ni] = (unsigned char)j.s[i];
+      sc->s2[ni] = (unsigned char)j.s2[i];
+      sc->t[ni] = (unsigned char)j.t[i];
+    }
+    sc->ie[g] = (unsigned char)ni;
+    for (int l = 0; l < 1 + j.dual; ++l) {
+      const int e = F - kDigitBits * (j.d[l] - 2);
+      const bool cvt = j.cvt[l] != 0;
+      const int shift_above = cvt ? 30 : 31;  // a signed int32 multiplier stays below 2^31
+      sc->cvt[g][l] = cvt ? 1 : 0;
+      sc->lsh[g][l] = (unsigned char)(e > shift_above ? e : 0);
+      sc->mult[g][l] = e > shift_above ? 1u : (e >= 0 ? (1u << e) : 1u);
+      sc->fscale[g][l] = e >= 0 ? 1.0f : ldexpf(1.0f, e);
+      if (!cvt) bs += (unsigned long long)kMagicBits * ((unsigned long long)sc->mult[g][l] << sc->lsh[g][l]);
+    }
+  }
+  sc->n_jobs = (int)jobs.size();
   *bias = bs;
   *fix_bits = F;
   return true;
@@ -1078,6 +1171,7 @@ int pair_clusters_nt(int nt, int pair) {
 // CTA-pair mode (bt_debug_split_pair): 0 = the default rule, 1 = one CTA per tile always,
 // 2 = pairs whenever the shape allows them, 3 = pairs with two K blocks per pipeline stage
 std::atomic<int> g_pair_mode{0};
+std::atomic<int> g_sched_mode{0};  // 0: merged class accumulators, 1: one pair per accumulator
 
 constexpr int kMaxKc = 1024;  // complex k per launch (slice workspace); K' = 2k <= 2048 = 32 K blocks
 
@@ -1254,7 +1348,8 @@ bt_status split_zgemm(cudaStream_t st, int m, int n, int k, zd alpha, Operand A,
     p.active = active;
     p.a_shared = a_shared ? 1 : 0;
     p.b_shared = b_shared ? 1 : 0;
-    if (!make_schedule(S, Kp / kKBlock, &p.sched, &p.bias, &p.fix_bits)) return BT_ERR_UNSUPPORTED;
+    if (!make_schedule(S, Kp / kKBlock, g_sched_mode.load() == 0, &p.sched, &p.bias, &p.fix_bits))
+      return BT_ERR_UNSUPPORTED;
     if (pair && pair_kind == 2) BT_TRY(launch_mma_nt<2>(nt, st, mA, mB, mBh, p));
     else if (pair) BT_TRY(launch_mma_nt<1>(nt, st, mA, mB, mBh, p));
     else BT_TRY(launch_mma_nt<0>(nt, st, mA, mB, mBh, p));
@@ -1289,6 +1384,37 @@ extern "C" bt_status bt_debug_split_profile(int enable, unsigned long long* coun
 }
 
 extern "C" void bt_debug_split_pair(int mode) { bt::g_pair_mode.store(mode >= 1 && mode <= 3 ? mode : 0); }
+
+extern "C" void bt_debug_split_sched(int mode) { bt::g_sched_mode.store(mode == 1 ? 1 : 0); }
+
+extern "C" int bt_debug_split_schedule(int slices, int k_blocks, int mode, int* jobs, int max_jobs, int* items,
+                                       int max_items, int* fix_bits) {
+  if (slices < 2 || slices > bt::kMaxSlices || k_blocks < 1 || k_blocks > 255) return -1;
+  bt::Schedule sc;
+  unsigned long long bias = 0;
+  int F = 0;
+  if (!bt::make_schedule(slices, k_blocks, mode != 1, &sc, &bias, &F)) return -1;
+  if (fix_bits) *fix_bits = F;
+  if (jobs)
+    for (int g = 0; g < sc.n_jobs && g < max_jobs; ++g) {
+      int* r = jobs + 8 * g;
+      r[0] = sc.dual[g];
+      r[1] = sc.ib[g];
+      r[2] = sc.ie[g];
+      r[3] = sc.kb0[g];
+      r[4] = sc.kb1[g];
+      r[5] = sc.cvt[g][0];
+      r[6] = sc.cvt[g][1];
+      r[7] = 0;
+    }
+  if (items)
+    for (int i = 0; i < (sc.n_jobs ? sc.ie[sc.n_jobs - 1] : 0) && i < max_items; ++i) {
+      items[3 * i] = sc.s[i];
+      items[3 * i + 1] = sc.s2[i];
+      items[3 * i + 2] = sc.t[i];
+    }
+  return sc.n_jobs;
+}
 
 extern "C" void bt_debug_split_stall(unsigned long long ns, long long launches) {
   bt::g_stall_left.store(launches);

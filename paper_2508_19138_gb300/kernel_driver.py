@@ -43,6 +43,9 @@ def main():
     ap.add_argument("--split-pair", type=int, default=0,
                     help="split: 1 = single CTAs, 2 = CTA pairs (cta_group::2), 3 = pairs with two K blocks per "
                          "stage, 0 = default; with --check all three")
+    ap.add_argument("--split-sched", type=int, default=0,
+                    help="split: accumulation schedule, 0 = merged weight classes (default), 1 = one slice pair "
+                         "per accumulator; --check compares both")
     ap.add_argument("--check", action="store_true",
                     help="split: compare the result of single CTAs and CTA pairs bitwise, and with torch")
     ap.add_argument("--split-profile", action="store_true",
@@ -90,6 +93,8 @@ def main():
 
     if a.kernel == "split" and a.split_pair:
         pkg.bt_debug_split_pair(a.split_pair)
+    if a.kernel == "split":
+        pkg.bt_debug_split_sched(a.split_sched)
     check = None
     if a.kernel == "split" and a.check:
         outs = {}
@@ -106,7 +111,21 @@ def main():
                  "bitwise_equal_pair_kps2": bool(torch.equal(outs[1], outs[3])),
                  "max_abs_diff": (outs[1] - outs[2]).abs().max().item(), "rel_err_vs_torch_pair": rel,
                  "rel_err_vs_torch_single": (torch.linalg.norm(outs[1] - ref) / torch.linalg.norm(ref)).item()}
+        # the other accumulation schedule (same CTA arrangement as the run)
         pkg.bt_debug_split_pair(a.split_pair)
+        pkg.bt_debug_split_sched(1 - a.split_sched)
+        C.zero_()
+        pkg.bt_split_zgemm_batched(n, n, kk, 1.0, A, kk, n * kk, 0, B, n, kk * n, 0, 0.0, C, n, n * n, b,
+                                   a.slices, workspace=ws)
+        torch.cuda.synchronize()
+        other = C.clone()
+        pkg.bt_debug_split_sched(a.split_sched)
+        C.zero_()
+        pkg.bt_split_zgemm_batched(n, n, kk, 1.0, A, kk, n * kk, 0, B, n, kk * n, 0, 0.0, C, n, n * n, b,
+                                   a.slices, workspace=ws)
+        torch.cuda.synchronize()
+        check["rel_err_vs_torch_other_sched"] = (torch.linalg.norm(other - ref) / torch.linalg.norm(ref)).item()
+        check["rel_diff_between_scheds"] = (torch.linalg.norm(other - C) / torch.linalg.norm(C)).item()
 
     def run():
         if a.kernel == "zgemm":
@@ -141,7 +160,8 @@ def main():
     print(json.dumps({"kernel": a.kernel, "bs": n, "k": kk, "batch": b, "ms": ms, "fp64_eq_tflops": flops / ms / 1e9,
                       "slices": a.slices if a.kernel == "split" else None,
                       "panel_cluster": a.panel_cluster if a.kernel == "zinv" else None, "split_profile": prof,
-                      "split_pair": a.split_pair if a.kernel == "split" else None, "check": check}))
+                      "split_pair": a.split_pair if a.kernel == "split" else None,
+                      "split_sched": a.split_sched if a.kernel == "split" else None, "check": check}))
 
 
 def conv_flops(L):

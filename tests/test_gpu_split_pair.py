@@ -61,6 +61,40 @@ def test_pair_bitwise_equals_single_cta(m, n, k, batch, opA, opB, alpha, beta):
         assert err < 1e-11, (i, err)
 
 
+@pytest.mark.parametrize("m,n,k,batch,opA,opB", CASES + [(416, 416, 416, 2, 0, 0), (256, 256, 1024, 2, 0, 1)])
+def test_merged_accumulators_match_one_pair_per_accumulator(m, n, k, batch, opA, opB):
+    """The default schedule (pairs of one weight class summed in one accumulator) against one pair
+    per accumulator: the same exact products in the same fixed point, rounded at different points
+    only for the classes below the fixed point's resolution, so the results agree far below the
+    split path's error; both against the exact product."""
+    import torch
+    import paper_2508_19138_gb300 as pkg
+    g = torch.Generator(device="cuda").manual_seed(m * 5 + n + k * 3 + batch)
+    shA = (batch, m, k) if opA == 0 else (batch, k, m)
+    shB = (batch, k, n) if opB == 0 else (batch, n, k)
+    A = torch.randn(shA, dtype=torch.complex128, device="cuda", generator=g)
+    B = torch.randn(shB, dtype=torch.complex128, device="cuda", generator=g)
+    C0 = torch.randn(batch, m, n, dtype=torch.complex128, device="cuda", generator=g)
+    got = {}
+    for sched in (0, 1):
+        pkg.bt_debug_split_sched(sched)
+        try:
+            got[sched] = _run(pkg, torch, 0, m, n, k, batch, opA, opB, 1.0, 0.0, A, B, C0)
+        finally:
+            pkg.bt_debug_split_sched(0)
+    a = A.cpu().numpy()
+    b = B.cpu().numpy()
+    opa = a if opA == 0 else np.conj(np.transpose(a, (0, 2, 1)))
+    opb = b if opB == 0 else np.conj(np.transpose(b, (0, 2, 1)))
+    ref = np.matmul(opa, opb)
+    g0, g1 = got[0].cpu().numpy(), got[1].cpu().numpy()
+    for i in range(batch):
+        nr = np.linalg.norm(ref[i])
+        assert np.linalg.norm(g0[i] - g1[i]) / nr < 1e-12, i
+        assert np.linalg.norm(g0[i] - ref[i]) / nr < 1e-11, i
+        assert np.linalg.norm(g1[i] - ref[i]) / nr < 1e-11, i
+
+
 def test_pair_timeout_reported_then_context_recovers():
     """b = 130: the products of the solve have 2n = 260 rows of C^T (three 128-row tiles) and run
     on CTA pairs; the stall hook makes the pair leader's MMA warp time out."""
