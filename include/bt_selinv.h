@@ -321,7 +321,9 @@ BT_API bt_status bt_zgemm_batched(int m, int n, int k, double alpha_re, double a
 /* Same product with the sliced split-precision scheme used by BT_SPLIT: each operand is
  * scaled per row (A) / per column (B) by a power of two and cut into `slices` 7-bit integer
  * slices held exactly in bf16; slice products run on the tcgen05 tensor cores with fp32
- * accumulation that is exact for k <= 1024 (per k-chunk), and are summed in FP64.
+ * accumulation that is exact (K segments of at most 480 complex terms; the slice pairs of one
+ * weight class share an accumulator while its sum stays an integer below 2^24), and are summed
+ * exactly in a 64-bit fixed point per output, converted to FP64 once.
  * Any m, n, k >= 1: ragged edges are zero padded.
  * `workspace` must hold bt_split_zgemm_workspace_bytes(m, n, k, slices, batch) bytes. */
 BT_API bt_status bt_split_zgemm_workspace_bytes(int m, int n, int k, int slices, int batch, size_t* bytes);
